@@ -1,0 +1,216 @@
+/*
+ * qsim.h -- C ABI of the GB300 quantum-circuit hot path.
+ *
+ * What it computes (the thesis "Supercomputer simulations of transmon quantum
+ * computers", D. Willsch, 2020):
+ *   - an n-qubit state vector of 2^n complex amplitudes a_J
+ *     (Eq. (multiqubitstate), section "Multiple qubits");
+ *   - circuits as ordered products of one- and two-qubit gates
+ *     (section "Quantum circuits": time runs left to right, so the matrices
+ *     multiply in reversed order), gates from Tab. (elementarygateset) plus
+ *     the rotations of Eqs. (singlequbitrotationx)-(singlequbitrotationz),
+ *     CNOT of Eq. (cnotgate), CZ = diag(1,1,1,-1), controlled phase, SWAP
+ *     and explicit 2x2 / 4x4 matrices;
+ *   - outcome probabilities p_J = |a_J|^2 (Born rule);
+ *   - batches of small density matrices evolved by gates and noise channels
+ *     written as Pauli transfer matrices (Eq. (paulitransfermatrix)), with
+ *     probabilities p_J = <<E_J|G|rho>> (Eq. (GSTBornRuleVectorized)), the
+ *     multinomial log-likelihood and its gradient.
+ *
+ * Conventions
+ *   - A qubit is named by its BIT POSITION b in the amplitude index J
+ *     (b = 0 is the least significant bit).  The thesis's qubit i (i-th tensor
+ *     factor, j_0 most significant) is bit n-1-i.
+ *   - Gate matrices act as U[out][in].  For a two-qubit gate q[0] is the most
+ *     significant bit of the gate's local index (the control of CNOT/CZ/CP),
+ *     matching the 4x4 CNOT layout of Eq. (cnotgate).
+ *   - Amplitudes are stored interleaved (re, im); complex64 = 2 x float,
+ *     complex128 = 2 x double.
+ *   - Every call is asynchronous on the state's CUDA stream unless it returns
+ *     a value through a HOST pointer (then it synchronises that stream).
+ *
+ * Errors: every entry point returns a qs_status and never throws.  On an error
+ * the state is left unchanged (QS_EINVAL, QS_ENOMEM are detected before any
+ * kernel is launched); qs_last_error() returns a thread-local message.
+ * Ownership: a qs_state_t owns its device memory (obtained from the caller's
+ * allocator, or cudaMalloc when none is given) until sv_destroy.  Output
+ * buffers are always caller-owned.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QS_OK = 0,
+  QS_EINVAL = 1,        /* invalid argument: bad qubit, duplicate qubits, n out of range, NaN angle */
+  QS_ENOMEM = 2,        /* device allocation failed; nothing was changed */
+  QS_ECUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error string) */
+  QS_ETIMEOUT = 4,      /* a bounded device-side wait gave up (status word set by a kernel) */
+  QS_EUNSUPPORTED = 5   /* valid request this build does not implement */
+} qs_status;
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_prec;
+
+/* Gate kinds.  One-qubit kinds use q[0] only. */
+typedef enum {
+  QS_I = 0, QS_X = 1, QS_Y = 2, QS_Z = 3, QS_H = 4, QS_S = 5, QS_SDG = 6, QS_T = 7, QS_TDG = 8,
+  QS_PX = 9,   /* +X = R^x(-pi/2) */
+  QS_MX = 10,  /* -X = R^x(+pi/2) */
+  QS_PY = 11,  /* +Y = R^y(-pi/2) */
+  QS_MY = 12,  /* -Y = R^y(+pi/2) */
+  QS_RX = 13, QS_RY = 14, QS_RZ = 15,     /* param[0] = theta, Eqs. (singlequbitrotationx-z) */
+  QS_U1 = 16,                             /* param[0] = lambda */
+  QS_U2 = 17,                             /* param = (phi, lambda) */
+  QS_U3 = 18,                             /* param = (theta, phi, lambda) */
+  QS_RK = 19,                             /* param[0] = k, R(k) = U1(2 pi / 2^k) */
+  QS_MAT1 = 20,                           /* explicit 2x2 in m[0..7] */
+  QS_CNOT = 32,                           /* q[0] control, q[1] target */
+  QS_CZ = 33,
+  QS_CP = 34,                             /* diag(1,1,1,e^{i param[0]}) */
+  QS_SWAP = 35,
+  QS_MAT2 = 36                            /* explicit 4x4 in m[0..31] */
+} qs_gate_kind;
+
+/* One gate (296 bytes, 8-byte aligned).  m: explicit matrix, complex128
+ * row-major U[out][in], (re, im) interleaved; only read for QS_MAT1/QS_MAT2. */
+typedef struct {
+  int32_t kind;
+  int32_t q[2];
+  int32_t reserved;
+  double param[3];
+  double m[32];
+} qs_gate;
+
+/* Device allocator supplied by the caller (e.g. PyTorch's caching allocator).
+ * alloc returns NULL on failure.  stream is the state's cudaStream_t. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* ctx;
+} qs_allocator;
+
+typedef struct qs_state_s* qs_state_t;
+
+typedef enum {
+  QS_METHOD_TILED = 0,  /* fused shared-memory tile passes (default) */
+  QS_METHOD_PLAIN = 1   /* one kernel launch per gate (comparison baseline) */
+} qs_method;
+
+typedef struct {
+  int32_t method;       /* qs_method */
+  int32_t reserved[7];
+} qs_opts;
+
+/* Per-call statistics (filled when a non-NULL pointer is given). */
+typedef struct {
+  int64_t gates_in;        /* gates given */
+  int64_t ops_fused;       /* device ops after fusion / folding */
+  int64_t passes;          /* full-state read+write sweeps */
+  int64_t launches;        /* kernel launches */
+  double bytes_moved;      /* algorithmic bytes: passes * 2 * 2^n * sizeof(amplitude) */
+} qs_stats;
+
+/* ---- state vector ------------------------------------------------------ */
+
+/* Allocate an n-qubit state (1 <= n <= 36) of precision prec on the current
+ * device and set it to |0...0>.  alloc may be NULL (cudaMalloc).  stream is a
+ * cudaStream_t (NULL = legacy default stream). */
+qs_status sv_create(int n, int prec, const qs_allocator* alloc, void* stream, qs_state_t* out);
+qs_status sv_destroy(qs_state_t st);
+qs_status sv_set_stream(qs_state_t st, void* stream);
+qs_status sv_info(qs_state_t st, int* n, int* prec, void** device_ptr);
+
+/* |J> (basis state, Eq. (multiqubitstate)). */
+qs_status sv_set_basis(qs_state_t st, uint64_t J);
+/* Copy 2^n interleaved amplitudes in/out; buf is a device pointer when
+ * on_device != 0 (no synchronisation), else a host pointer (synchronises). */
+qs_status sv_copy_in(qs_state_t st, const void* buf, int on_device);
+qs_status sv_copy_out(qs_state_t st, void* buf, int on_device);
+
+/* psi <- U_L ... U_1 psi for gates[0..ngates) in time order (section "Quantum
+ * circuits", Eq. (twoqubitqft) shows the reversal).  opts may be NULL. */
+qs_status sv_apply_circuit(qs_state_t st, const qs_gate* gates, size_t ngates,
+                           const qs_opts* opts, qs_stats* stats);
+
+/* Born rule p_J = |a_J|^2.  out: device buffer of float (out_fp64 = 0) or
+ * double; with marg_mask == 0 or all n bits set, 2^n values in index order;
+ * otherwise the marginal over the bits in marg_mask, 2^popcount(mask) values
+ * indexed by those bits packed in increasing bit order.  out may be NULL.
+ * norm_out (HOST, may be NULL) receives sum_J p_J accumulated in fp64 and
+ * makes the call synchronous. */
+qs_status sv_probs(qs_state_t st, void* out, int out_fp64, uint64_t marg_mask, double* norm_out);
+
+/* Multinomial log-likelihood l = sum_J n_J log p_J (terms with n_J = 0 are 0;
+ * p_J <= 0 with n_J > 0 is clamped to 1e-300 and counted).  counts: DEVICE,
+ * 2^n uint32.  out (HOST) receives l; clamped (HOST, may be NULL) the count
+ * of clamped terms.  Synchronises. */
+qs_status sv_loglik(qs_state_t st, const uint32_t* counts, double* out, int64_t* clamped);
+
+/* Adjoint gradient of L(p(psi)) with respect to every gate angle, where
+ * psi = U_L...U_1 psi_0 and psi_0 is the current content of st:
+ *   mode 0: L = sum_J w_J p_J, w = weights (DEVICE, 2^n doubles);
+ *   mode 1: L = sum_J n_J log p_J, weights = counts as DEVICE 2^n doubles.
+ * dtheta (HOST, ngates*3 doubles): dL/dparam[k] of gate g at [3g+k], 0 for
+ * unparameterised gates.  loss (HOST, may be NULL) receives L.  On return st
+ * holds the final state U psi_0.  checkpoint_every = 0 uncomputes states with
+ * U^dagger; k > 0 stores a device copy every k gates and recomputes forward
+ * from it (deep circuits).  Synchronises. */
+qs_status sv_grad(qs_state_t st, const qs_gate* gates, size_t ngates, const double* weights,
+                  int mode, int checkpoint_every, double* dtheta, double* loss);
+
+/* ---- batched density matrices / Pauli transfer matrices ---------------- */
+
+/* Op codes of a batched noisy circuit (rows of 4 int32: code, q0, q1, aux).
+ * After X90/Y90/CZ/IDLE the circuit's noise channel acts on every qubit the op
+ * touches (IDLE: all): symmetric depolarizing (p_x = p_y = p_z = p/3, Eq.
+ * (singletDepolarizingChannel)) and then amplitude damping with decay
+ * parameter 1 and rate gamma (Eqs. (singletAmplitudeDampingChannel1-2)). */
+enum {
+  QS_DM_X90 = 0,   /* R^x(theta_x) on q0 */
+  QS_DM_Y90 = 1,   /* R^y(theta_y) on q0 */
+  QS_DM_CZ = 2,    /* CZ on (q0, q1) */
+  QS_DM_IDLE = 3,  /* identity on the register */
+  QS_DM_PTM1 = 4,  /* user 4x4 PTM ptm1[aux] on q0, no channel */
+  QS_DM_PTM2 = 5   /* user 16x16 PTM ptm2[aux] on (q0 most significant digit, q1), no channel */
+};
+
+/* A batch of small noisy circuits; every pointer is DEVICE memory.
+ * State of circuit c: Pauli vector r_i = Tr(P^_i rho) of its nq[c] qubits
+ * (Eqs. (paulibasis), (GSTVectorizedRho); base-4 digit b of i belongs to
+ * bit b), initial rho = |0...0><0...0|, measurement E_J = |J><J|. */
+typedef struct {
+  int32_t n_circuits;
+  int32_t max_qubits;      /* <= 6 */
+  const int32_t* nq;       /* [C] 1..6 */
+  const int64_t* op_off;   /* [C+1] rows of ops for circuit c: op_off[c]..op_off[c+1] */
+  const int32_t* ops;      /* [rows*4] (code, q0, q1, aux) */
+  const double* params;    /* [C*4] theta_x, theta_y, p, gamma */
+  const int64_t* out_off;  /* [C+1] offsets of circuit c's 2^nq outcomes in probs/counts */
+  const int32_t* counts;   /* [out_off[C]] or NULL (no likelihood / gradient) */
+  const double* ptm1;      /* user 4x4 PTMs, row-major, or NULL */
+  const double* ptm2;      /* user 16x16 PTMs, row-major, or NULL */
+} qs_dm_batch;
+
+/* Forward (and optionally adjoint) pass of a batch.  probs (DEVICE, float,
+ * out_off[C] values, may be NULL); loglik (DEVICE, double [C], may be NULL;
+ * needs counts); grad (DEVICE, double [C*4] = d loglik / d(theta_x, theta_y,
+ * p, gamma), may be NULL; needs counts).  Asynchronous on stream. */
+qs_status dm_apply_channels(const qs_dm_batch* batch, float* probs, double* loglik, double* grad,
+                            void* stream);
+
+/* ---- misc -------------------------------------------------------------- */
+
+const char* qs_last_error(void);
+const char* qs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_H */

@@ -1,0 +1,320 @@
+"""Python binding of the qsim C ABI (include/qsim.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library ``libqsim.so`` built
+in-tree for sm_103a; there is no Python or CPU fallback.  PyTorch provides
+device memory (its caching allocator backs the states) and CUDA streams.
+
+Names follow the C ABI: :func:`sv_create`, :func:`sv_apply_circuit`,
+:func:`sv_probs`, :func:`sv_loglik`, :func:`sv_grad`,
+:func:`dm_apply_channels`, ...
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqsim.so")
+
+QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
+QS_C64, QS_C128 = 0, 1
+METHOD_TILED, METHOD_PLAIN = 0, 1
+
+KIND = {
+    "I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,
+    "PX": 9, "MX": 10, "PY": 11, "MY": 12, "RX": 13, "RY": 14, "RZ": 15,
+    "U1": 16, "U2": 17, "U3": 18, "RK": 19, "MAT1": 20,
+    "CNOT": 32, "CZ": 33, "CP": 34, "SWAP": 35, "MAT2": 36,
+}
+
+# qs_gate (296 bytes)
+GATE_DTYPE = np.dtype([("kind", "<i4"), ("q", "<i4", (2,)), ("reserved", "<i4"),
+                       ("param", "<f8", (3,)), ("m", "<f8", (32,))])
+assert GATE_DTYPE.itemsize == 296
+
+
+class QsimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"qsim status {status}: {msg}")
+        self.status = status
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("gates_in", ctypes.c_int64), ("ops_fused", ctypes.c_int64),
+                ("passes", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("bytes_moved", ctypes.c_double)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_T), ("free", _FREE_T), ("ctx", ctypes.c_void_p)]
+
+
+class DMBatch(ctypes.Structure):
+    _fields_ = [("n_circuits", ctypes.c_int32), ("max_qubits", ctypes.c_int32),
+                ("nq", ctypes.c_void_p), ("op_off", ctypes.c_void_p), ("ops", ctypes.c_void_p),
+                ("params", ctypes.c_void_p), ("out_off", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p), ("ptm1", ctypes.c_void_p), ("ptm2", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load():
+    """Load libqsim.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, u64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t
+    sig = {
+        "sv_create": (i32, [i32, i32, ctypes.POINTER(_Allocator), vp, ctypes.POINTER(vp)]),
+        "sv_destroy": (i32, [vp]),
+        "sv_set_stream": (i32, [vp, vp]),
+        "sv_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(vp)]),
+        "sv_set_basis": (i32, [vp, u64]),
+        "sv_copy_in": (i32, [vp, vp, i32]),
+        "sv_copy_out": (i32, [vp, vp, i32]),
+        "sv_apply_circuit": (i32, [vp, vp, sz, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats)]),
+        "sv_probs": (i32, [vp, vp, i32, u64, ctypes.POINTER(ctypes.c_double)]),
+        "sv_loglik": (i32, [vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+        "sv_grad": (i32, [vp, vp, sz, vp, i32, i32, ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double)]),
+        "dm_apply_channels": (i32, [ctypes.POINTER(DMBatch), vp, vp, vp, vp]),
+        "qs_last_error": (ctypes.c_char_p, []),
+        "qs_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
+            "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
+            "dm_apply_channels", "qs_last_error", "qs_version"]
+
+
+def _check(status: int):
+    if status != QS_OK:
+        raise QsimError(status, load().qs_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("qsim needs a CUDA device")
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- allocator
+def _make_torch_allocator():
+    torch = _torch()
+
+    @_ALLOC_T
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                          stream or 0))
+        except Exception:   # out of memory -> NULL -> QS_ENOMEM
+            return None
+
+    @_FREE_T
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a = _Allocator(_alloc, _free, None)
+    a._keep = (_alloc, _free)
+    return a
+
+
+_TORCH_ALLOC = None
+
+
+def torch_allocator():
+    global _TORCH_ALLOC
+    if _TORCH_ALLOC is None:
+        _TORCH_ALLOC = _make_torch_allocator()
+    return _TORCH_ALLOC
+
+
+# ---------------------------------------------------------------- gates
+def gates_array(ops) -> np.ndarray:
+    """Gate records ``(name, qubits, params, matrix)`` -> qs_gate array."""
+    arr = np.zeros(len(ops), dtype=GATE_DTYPE)
+    for i, (name, qubits, params, mat) in enumerate(ops):
+        arr[i]["kind"] = KIND[name]
+        arr[i]["q"][: len(qubits)] = qubits
+        if params:
+            arr[i]["param"][: len(params)] = params
+        if mat is not None:
+            m = np.asarray(mat, dtype=np.complex128).reshape(-1)
+            flat = np.empty(2 * m.size)
+            flat[0::2] = m.real
+            flat[1::2] = m.imag
+            arr[i]["m"][: flat.size] = flat
+    return arr
+
+
+# ---------------------------------------------------------------- state vector
+class State:
+    """Owns a qs_state_t.  Device memory comes from PyTorch's caching allocator."""
+
+    def __init__(self, n: int, prec: int = QS_C64, stream=None, use_torch_allocator: bool = True):
+        lib = load()
+        _torch()
+        self.n = n
+        self.prec = prec
+        h = ctypes.c_void_p()
+        alloc = ctypes.byref(torch_allocator()) if use_torch_allocator else None
+        _check(lib.sv_create(n, prec, alloc, _stream_ptr(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().sv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def amp_dtype(self):
+        return np.complex64 if self.prec == QS_C64 else np.complex128
+
+    def device_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        _check(load().sv_info(self.handle, None, None, ctypes.byref(p)))
+        return int(p.value)
+
+
+def sv_create(n: int, prec: int = QS_C64, stream=None) -> State:
+    return State(n, prec, stream)
+
+
+def sv_destroy(st: State):
+    st.close()
+
+
+def sv_set_stream(st: State, stream):
+    _check(load().sv_set_stream(st.handle, _stream_ptr(stream)))
+
+
+def sv_set_basis(st: State, J: int):
+    _check(load().sv_set_basis(st.handle, int(J)))
+
+
+def sv_copy_in(st: State, amps):
+    """amps: numpy array (host) or torch tensor (device) of 2^n complex values."""
+    torch = _torch()
+    if isinstance(amps, torch.Tensor):
+        t = amps.contiguous()
+        _check(load().sv_copy_in(st.handle, t.data_ptr(), 1 if t.is_cuda else 0))
+        return
+    a = np.ascontiguousarray(amps, dtype=st.amp_dtype)
+    _check(load().sv_copy_in(st.handle, a.ctypes.data, 0))
+
+
+def sv_copy_out(st: State, out=None):
+    """Returns a host numpy array, or fills a torch device tensor ``out``."""
+    torch = _torch()
+    if out is not None and isinstance(out, torch.Tensor):
+        _check(load().sv_copy_out(st.handle, out.data_ptr(), 1 if out.is_cuda else 0))
+        return out
+    a = np.empty(1 << st.n, dtype=st.amp_dtype)
+    _check(load().sv_copy_out(st.handle, a.ctypes.data, 0))
+    return a
+
+
+def sv_apply_circuit(st: State, gates, method: int = METHOD_TILED) -> dict:
+    arr = gates if isinstance(gates, np.ndarray) else gates_array(gates)
+    arr = np.ascontiguousarray(arr, dtype=GATE_DTYPE)
+    opts = _Opts(method)
+    stats = _Stats()
+    _check(load().sv_apply_circuit(st.handle, arr.ctypes.data, len(arr), ctypes.byref(opts),
+                                   ctypes.byref(stats)))
+    return {k: getattr(stats, k) for k, _ in _Stats._fields_}
+
+
+def sv_probs(st: State, out=None, fp64: bool = False, marg_mask: int = 0, want_norm: bool = True):
+    """Born-rule probabilities into the device tensor ``out`` (or a new one).
+
+    Returns (out, norm) with norm = sum_J p_J accumulated in fp64 (None if
+    want_norm is False, which keeps the call asynchronous)."""
+    torch = _torch()
+    k = bin(marg_mask).count("1") if marg_mask else st.n
+    if out is None:
+        out = torch.empty(1 << k, dtype=torch.float64 if fp64 else torch.float32, device="cuda")
+    norm = ctypes.c_double()
+    _check(load().sv_probs(st.handle, out.data_ptr(), 1 if fp64 else 0, int(marg_mask),
+                           ctypes.byref(norm) if want_norm else None))
+    return out, (norm.value if want_norm else None)
+
+
+def sv_loglik(st: State, counts) -> tuple[float, int]:
+    """counts: device uint32/int32 tensor of 2^n outcome counts."""
+    out = ctypes.c_double()
+    clamped = ctypes.c_int64()
+    _check(load().sv_loglik(st.handle, counts.data_ptr(), ctypes.byref(out), ctypes.byref(clamped)))
+    return out.value, clamped.value
+
+
+def sv_grad(st: State, gates, weights, mode: int = 0, checkpoint_every: int = 0):
+    """Adjoint gradient; weights: device float64 tensor (weights or counts).
+
+    Returns (loss, dtheta[n_gates, 3])."""
+    arr = gates if isinstance(gates, np.ndarray) else gates_array(gates)
+    arr = np.ascontiguousarray(arr, dtype=GATE_DTYPE)
+    g = np.zeros((len(arr), 3), dtype=np.float64)
+    loss = ctypes.c_double()
+    _check(load().sv_grad(st.handle, arr.ctypes.data, len(arr), weights.data_ptr(), int(mode),
+                          int(checkpoint_every),
+                          g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(loss)))
+    return loss.value, g
+
+
+# ---------------------------------------------------------------- density matrices
+def dm_apply_channels(nq, op_off, ops, params, out_off, counts=None, ptm1=None, ptm2=None,
+                      probs=None, loglik=None, grad=None, stream=None):
+    """All arrays are torch device tensors (see qs_dm_batch in include/qsim.h)."""
+    b = DMBatch()
+    b.n_circuits = int(nq.numel())
+    b.max_qubits = 6
+    b.nq = nq.data_ptr()
+    b.op_off = op_off.data_ptr()
+    b.ops = ops.data_ptr()
+    b.params = params.data_ptr()
+    b.out_off = out_off.data_ptr()
+    b.counts = counts.data_ptr() if counts is not None else None
+    b.ptm1 = ptm1.data_ptr() if ptm1 is not None else None
+    b.ptm2 = ptm2.data_ptr() if ptm2 is not None else None
+    ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
+    _check(load().dm_apply_channels(ctypes.byref(b), ptr(probs), ptr(loglik), ptr(grad),
+                                    _stream_ptr(stream)))
+
+
+def version() -> str:
+    return load().qs_version().decode()

@@ -1,0 +1,482 @@
+// C ABI entry points of the state-vector path (see include/qsim.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace qs {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+qs_status cuda_status(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return QS_ENOMEM;
+  }
+  return QS_ECUDA;
+}
+
+void* dev_alloc(State* st, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (st->has_alloc) return st->alloc.alloc(bytes, (void*)st->stream, st->alloc.ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(State* st, void* p, size_t bytes) {
+  if (!p) return;
+  if (st->has_alloc) st->alloc.free(p, bytes, (void*)st->stream, st->alloc.ctx);
+  else cudaFree(p);
+}
+
+qs_status ensure_opbuf(State* st, size_t bytes) {
+  if (bytes <= st->opbuf_bytes) return QS_OK;
+  size_t want = 64 * 1024;
+  while (want < bytes) want *= 2;
+  // the old buffer may still be read by queued kernels
+  QS_CUDA(cudaStreamSynchronize(st->stream));
+  dev_free(st, st->opbuf, st->opbuf_bytes);
+  st->opbuf = dev_alloc(st, want);
+  if (!st->opbuf) {
+    st->opbuf_bytes = 0;
+    set_error("device allocation of %zu bytes for op descriptors failed", want);
+    return QS_ENOMEM;
+  }
+  st->opbuf_bytes = want;
+  return QS_OK;
+}
+
+// staging of op descriptors: host (pinned) -> device in one copy
+qs_status upload(State* st, const std::vector<unsigned char>& blob) {
+  if (blob.empty()) return QS_OK;
+  qs_status s = ensure_opbuf(st, blob.size());
+  if (s != QS_OK) return s;
+  if (st->hostbuf_bytes < blob.size()) {
+    if (st->hostbuf) {
+      QS_CUDA(cudaEventSynchronize(st->upload_done));
+      cudaFreeHost(st->hostbuf);
+    }
+    size_t want = 64 * 1024;
+    while (want < blob.size()) want *= 2;
+    if (cudaMallocHost(&st->hostbuf, want) != cudaSuccess) {
+      cudaGetLastError();
+      st->hostbuf = nullptr;
+      st->hostbuf_bytes = 0;
+      set_error("pinned host allocation failed");
+      return QS_ENOMEM;
+    }
+    st->hostbuf_bytes = want;
+  } else {
+    QS_CUDA(cudaEventSynchronize(st->upload_done));   // previous copy has read the buffer
+  }
+  std::memcpy(st->hostbuf, blob.data(), blob.size());
+  QS_CUDA(cudaMemcpyAsync(st->opbuf, st->hostbuf, blob.size(), cudaMemcpyHostToDevice, st->stream));
+  QS_CUDA(cudaEventRecord(st->upload_done, st->stream));
+  return QS_OK;
+}
+
+namespace {
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <typename R>
+C2<R> c2(cd z) {
+  C2<R> r;
+  r.x = (R)z.real();
+  r.y = (R)z.imag();
+  return r;
+}
+
+template <typename R>
+PlainOp<R> to_plain(const FOp& o) {
+  PlainOp<R> p;
+  std::memset(&p, 0, sizeof(p));
+  p.type = o.type;
+  p.t = o.t;
+  p.c = o.c;
+  p.a = o.a;
+  p.b = o.b;
+  switch (o.type) {
+    case F_G1:
+      for (int i = 0; i < 4; ++i) p.m[i] = c2<R>(o.m0[i]);
+      break;
+    case F_G1C:
+      for (int i = 0; i < 4; ++i) {
+        p.m[i] = c2<R>(o.m0[i]);
+        p.m[4 + i] = c2<R>(o.m1[i]);
+      }
+      break;
+    case F_D:
+      for (int i = 0; i < 4; ++i) p.m[i] = c2<R>(o.d[i]);
+      break;
+    default:
+      for (int i = 0; i < 16; ++i) p.m[i] = c2<R>(o.g[i]);
+  }
+  return p;
+}
+
+template <typename R>
+TileOp<R> to_tile(const Plan& pl, size_t i) {
+  TileOp<R> t;
+  std::memset(&t, 0, sizeof(t));
+  const FOp& o = pl.tile_fops[i];
+  t.kind = pl.tile_kind[i];
+  t.slot = pl.tile_slot[i];
+  t.csrc = pl.tile_csrc[i];
+  t.cbit = pl.tile_cbit[i];
+  t.dsrc = pl.tile_dsrc[i];
+  t.dbit = pl.tile_dbit[i];
+  if (o.type == F_D) {
+    for (int k = 0; k < 4; ++k) t.m0[k] = c2<R>(o.d[k]);
+  } else {
+    for (int k = 0; k < 4; ++k) {
+      t.m0[k] = c2<R>(o.m0[k]);
+      t.m1[k] = c2<R>(o.type == F_G1C ? o.m1[k] : o.m0[k]);
+    }
+  }
+  return t;
+}
+
+template <typename T>
+size_t put(std::vector<unsigned char>& blob, const T* p, size_t count) {
+  size_t off = align16(blob.size());
+  blob.resize(off + sizeof(T) * count);
+  if (count) std::memcpy(blob.data() + off, p, sizeof(T) * count);
+  return off;
+}
+
+template <typename R>
+qs_status run_plain(State* st, const std::vector<FOp>& fops, qs_stats* stats) {
+  for (const FOp& o : fops) {
+    PlainOp<R> p = to_plain<R>(o);
+    qs_status s = launch_plain_op(st, &p, o.type);
+    if (s != QS_OK) return s;
+  }
+  if (stats) {
+    stats->ops_fused = (int64_t)fops.size();
+    stats->passes = (int64_t)fops.size();
+    stats->launches = (int64_t)fops.size();
+  }
+  return QS_OK;
+}
+
+template <typename R>
+qs_status run_small(State* st, const std::vector<FOp>& fops, qs_stats* stats) {
+  std::vector<PlainOp<R>> ops;
+  ops.reserve(fops.size());
+  for (const FOp& o : fops) ops.push_back(to_plain<R>(o));
+  std::vector<unsigned char> blob;
+  size_t off = put(blob, ops.data(), ops.size());
+  qs_status s = upload(st, blob);
+  if (s != QS_OK) return s;
+  s = launch_small(st, (unsigned char*)st->opbuf + off, (int)ops.size());
+  if (s != QS_OK) return s;
+  if (stats) {
+    stats->ops_fused = (int64_t)fops.size();
+    stats->passes = 1;
+    stats->launches = 1;
+  }
+  return QS_OK;
+}
+
+template <typename R>
+qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<int>& vmap,
+                    qs_stats* stats) {
+  Plan pl;
+  plan_circuit(fops, st->n, vmap, pl);
+  std::vector<TileOp<R>> tops;
+  tops.reserve(pl.tile_fops.size());
+  for (size_t i = 0; i < pl.tile_fops.size(); ++i) tops.push_back(to_tile<R>(pl, i));
+  std::vector<unsigned char> blob;
+  const size_t off_pass = put(blob, pl.passes.data(), pl.passes.size());
+  const size_t off_stage = put(blob, pl.stages.data(), pl.stages.size());
+  const size_t off_ops = put(blob, tops.data(), tops.size());
+  const size_t off_remap = put(blob, pl.remaps.data(), pl.remaps.size());
+  qs_status s = upload(st, blob);
+  if (s != QS_OK) return s;
+  unsigned char* dev = (unsigned char*)st->opbuf;
+  int64_t passes = 0, launches = 0;
+  for (const PlanStep& step : pl.steps) {
+    switch (step.kind) {
+      case PlanStep::TILE:
+        s = launch_tile_pass(st, dev + off_pass + sizeof(TilePass) * step.index, dev + off_stage,
+                             dev + off_ops, pl.passes[step.index].n_stages);
+        break;
+      case PlanStep::PLAIN: {
+        PlainOp<R> p = to_plain<R>(pl.plain_fops[step.index]);
+        s = launch_plain_op(st, &p, p.type);
+        break;
+      }
+      case PlanStep::REMAP:
+        s = launch_remap(st, dev + off_remap + sizeof(RemapDesc) * step.index, nullptr);
+        break;
+      default:
+        break;
+    }
+    if (s != QS_OK) return s;
+    ++passes;
+    ++launches;
+  }
+  if (stats) {
+    stats->ops_fused = (int64_t)fops.size();
+    stats->passes = passes;
+    stats->launches = launches;
+  }
+  return QS_OK;
+}
+
+qs_status check_state(qs_state_t st) {
+  if (!st) {
+    set_error("state is NULL");
+    return QS_EINVAL;
+  }
+  return QS_OK;
+}
+
+}  // namespace
+
+}  // namespace qs
+
+using namespace qs;
+
+struct qs_state_s : public State {};
+
+extern "C" {
+
+const char* qs_last_error(void) { return g_err.c_str(); }
+
+const char* qs_version(void) { return "qsim-gb300 0.1 (sm_103a)"; }
+
+qs_status sv_create(int n, int prec, const qs_allocator* alloc, void* stream, qs_state_t* out) {
+  if (!out) {
+    set_error("out is NULL");
+    return QS_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 1 || n > 36) {
+    set_error("n = %d outside [1, 36]", n);
+    return QS_EINVAL;
+  }
+  if (prec != QS_C64 && prec != QS_C128) {
+    set_error("bad precision %d", prec);
+    return QS_EINVAL;
+  }
+  qs_state_s* st = new (std::nothrow) qs_state_s();
+  if (!st) return QS_ENOMEM;
+  st->n = n;
+  st->prec = prec;
+  st->amp_bytes = prec == QS_C64 ? 8 : 16;
+  st->stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    st->alloc = *alloc;
+    st->has_alloc = true;
+  }
+  cudaGetDevice(&st->device);
+  st->data_bytes = st->amp_bytes << n;
+  st->data = dev_alloc(st, st->data_bytes);
+  if (!st->data) {
+    set_error("device allocation of %zu bytes for a %d-qubit state failed", st->data_bytes, n);
+    delete st;
+    return QS_ENOMEM;
+  }
+  st->scratch_bytes = kScratchBytes;
+  st->scratch = dev_alloc(st, st->scratch_bytes);
+  if (!st->scratch) {
+    dev_free(st, st->data, st->data_bytes);
+    set_error("scratch allocation failed");
+    delete st;
+    return QS_ENOMEM;
+  }
+  if (cudaEventCreateWithFlags(&st->upload_done, cudaEventDisableTiming) != cudaSuccess) {
+    dev_free(st, st->scratch, st->scratch_bytes);
+    dev_free(st, st->data, st->data_bytes);
+    qs_status s = cuda_status(cudaGetLastError(), "cudaEventCreate");
+    delete st;
+    return s;
+  }
+  qs_status s = launch_set_basis(st, 0);
+  if (s != QS_OK) {
+    sv_destroy(st);
+    return s;
+  }
+  *out = st;
+  return QS_OK;
+}
+
+qs_status sv_destroy(qs_state_t st) {
+  if (!st) return QS_OK;
+  cudaStreamSynchronize(st->stream);
+  dev_free(st, st->opbuf, st->opbuf_bytes);
+  dev_free(st, st->scratch, st->scratch_bytes);
+  dev_free(st, st->data, st->data_bytes);
+  if (st->hostbuf) cudaFreeHost(st->hostbuf);
+  if (st->upload_done) cudaEventDestroy(st->upload_done);
+  delete st;
+  return QS_OK;
+}
+
+qs_status sv_set_stream(qs_state_t st, void* stream) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  QS_CUDA(cudaStreamSynchronize(st->stream));
+  st->stream = (cudaStream_t)stream;
+  return QS_OK;
+}
+
+qs_status sv_info(qs_state_t st, int* n, int* prec, void** device_ptr) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (n) *n = st->n;
+  if (prec) *prec = st->prec;
+  if (device_ptr) *device_ptr = st->data;
+  return QS_OK;
+}
+
+qs_status sv_set_basis(qs_state_t st, uint64_t J) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (J >> st->n) {
+    set_error("basis index %llu out of range for n = %d", (unsigned long long)J, st->n);
+    return QS_EINVAL;
+  }
+  return launch_set_basis(st, J);
+}
+
+qs_status sv_copy_in(qs_state_t st, const void* buf, int on_device) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (!buf) {
+    set_error("buf is NULL");
+    return QS_EINVAL;
+  }
+  if (on_device) {
+    QS_CUDA(cudaMemcpyAsync(st->data, buf, st->data_bytes, cudaMemcpyDeviceToDevice, st->stream));
+  } else {
+    QS_CUDA(cudaMemcpyAsync(st->data, buf, st->data_bytes, cudaMemcpyHostToDevice, st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+  }
+  return QS_OK;
+}
+
+qs_status sv_copy_out(qs_state_t st, void* buf, int on_device) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (!buf) {
+    set_error("buf is NULL");
+    return QS_EINVAL;
+  }
+  if (on_device) {
+    QS_CUDA(cudaMemcpyAsync(buf, st->data, st->data_bytes, cudaMemcpyDeviceToDevice, st->stream));
+  } else {
+    QS_CUDA(cudaMemcpyAsync(buf, st->data, st->data_bytes, cudaMemcpyDeviceToHost, st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+  }
+  return QS_OK;
+}
+
+qs_status sv_apply_circuit(qs_state_t st, const qs_gate* gates, size_t ngates, const qs_opts* opts,
+                           qs_stats* stats) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  s = validate_gates(gates, ngates, st->n);
+  if (s != QS_OK) return s;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  const int method = opts ? opts->method : QS_METHOD_TILED;
+  if (method != QS_METHOD_TILED && method != QS_METHOD_PLAIN) {
+    set_error("unknown method %d", method);
+    return QS_EINVAL;
+  }
+  if (ngates == 0) return QS_OK;
+  std::vector<FOp> fops;
+  std::vector<int> vmap;
+  const bool c64 = st->prec == QS_C64;
+  if (method == QS_METHOD_PLAIN) {
+    build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/false, /*relabel=*/false);
+    s = c64 ? run_plain<float>(st, fops, stats) : run_plain<double>(st, fops, stats);
+  } else if (st->n < kTileBits) {
+    build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/false);
+    s = c64 ? run_small<float>(st, fops, stats) : run_small<double>(st, fops, stats);
+  } else {
+    build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/true);
+    s = c64 ? run_tiled<float>(st, fops, vmap, stats) : run_tiled<double>(st, fops, vmap, stats);
+  }
+  if (stats) {
+    stats->gates_in = (int64_t)ngates;
+    stats->bytes_moved = (double)stats->passes * 2.0 * (double)st->data_bytes;
+  }
+  return s;
+}
+
+qs_status sv_probs(qs_state_t st, void* out, int out_fp64, uint64_t marg_mask, double* norm_out) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (marg_mask >> st->n) {
+    set_error("marginal mask has bits beyond n = %d", st->n);
+    return QS_EINVAL;
+  }
+  int k = __builtin_popcountll(marg_mask);
+  const bool marginal = marg_mask != 0 && k != st->n;
+  if (marginal && k > kScratchMargLog2) {
+    set_error("marginal over %d qubits exceeds the %d-qubit scratch limit", k, kScratchMargLog2);
+    return QS_EUNSUPPORTED;
+  }
+  if (!marginal && out && !out_fp64 && st->prec == QS_C64 && ((uintptr_t)out & 7)) {
+    set_error("float output buffer must be 8-byte aligned");
+    return QS_EINVAL;
+  }
+  unsigned char* sc = (unsigned char*)st->scratch;
+  double* partials = (double*)(sc + kScratchPartials);
+  s = launch_probs(st, out, out_fp64, marginal ? marg_mask : 0, partials,
+                   (uint8_t*)(sc + kScratchBits), (double*)(sc + kScratchMarg));
+  if (s != QS_OK) return s;
+  if (norm_out) {
+    double* res = (double*)(sc + kScratchResult);
+    s = launch_reduce_partials(st, partials, kReduceBlocks, res);
+    if (s != QS_OK) return s;
+    QS_CUDA(cudaMemcpyAsync(norm_out, res, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+  }
+  return QS_OK;
+}
+
+qs_status sv_loglik(qs_state_t st, const uint32_t* counts, double* out, int64_t* clamped) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (!counts || !out) {
+    set_error("counts and out are required");
+    return QS_EINVAL;
+  }
+  unsigned char* sc = (unsigned char*)st->scratch;
+  double* partials = (double*)(sc + kScratchPartials);
+  s = launch_loglik(st, counts, partials, (unsigned long long*)(sc + kScratchClamps));
+  if (s != QS_OK) return s;
+  double* res = (double*)(sc + kScratchResult);
+  s = launch_reduce_partials(st, partials, kReduceBlocks, res);
+  if (s != QS_OK) return s;
+  unsigned long long nc = 0;
+  QS_CUDA(cudaMemcpyAsync(out, res, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+  QS_CUDA(cudaMemcpyAsync(&nc, sc + kScratchClamps, sizeof(nc), cudaMemcpyDeviceToHost, st->stream));
+  QS_CUDA(cudaStreamSynchronize(st->stream));
+  if (clamped) *clamped = (int64_t)nc;
+  return QS_OK;
+}
+
+}  // extern "C"

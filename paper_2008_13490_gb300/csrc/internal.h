@@ -1,0 +1,197 @@
+// Internal declarations shared by the host runtime (.cpp) and the kernels (.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "qsim.h"
+
+namespace qs {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+qs_status cuda_status(cudaError_t e, const char* what);
+
+#define QS_CUDA(call)                                           \
+  do {                                                          \
+    cudaError_t e__ = (call);                                   \
+    if (e__ != cudaSuccess) return ::qs::cuda_status(e__, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------- state
+struct State {
+  int n = 0;
+  int prec = QS_C64;
+  size_t amp_bytes = 8;         // bytes per amplitude
+  void* data = nullptr;         // 2^n amplitudes
+  size_t data_bytes = 0;
+  void* scratch = nullptr;      // reduction partials + small device tables
+  size_t scratch_bytes = 0;
+  cudaStream_t stream = nullptr;
+  qs_allocator alloc{};
+  bool has_alloc = false;
+  int device = 0;
+  // device op buffer reused between calls (grown on demand)
+  void* opbuf = nullptr;
+  size_t opbuf_bytes = 0;
+  // pinned host staging buffer for op uploads
+  void* hostbuf = nullptr;
+  size_t hostbuf_bytes = 0;
+  cudaEvent_t upload_done = nullptr;
+};
+
+void* dev_alloc(State* st, size_t bytes);
+void dev_free(State* st, void* p, size_t bytes);
+qs_status ensure_opbuf(State* st, size_t bytes);
+
+// Per-state scratch (device): reduction partials, counters, small tables.
+constexpr int kReduceBlocks = 1024;               // partial sums written by reduction kernels
+constexpr size_t kScratchPartials = 0;            // kReduceBlocks doubles
+constexpr size_t kScratchClamps = 8192;           // one 64-bit counter
+constexpr size_t kScratchResult = 8448;           // 16 doubles
+constexpr size_t kScratchBits = 8704;             // 64 bytes of bit positions
+constexpr size_t kScratchMarg = 16384;            // marginal accumulators (doubles)
+constexpr int kScratchMargLog2 = 16;              // largest marginal kept in scratch
+constexpr size_t kScratchBytes = kScratchMarg + (sizeof(double) << kScratchMargLog2);
+
+// ---------------------------------------------------------------- gates
+// Host-side gate matrices, written from the thesis's definitions (rotations,
+// U gates, Tab. (elementarygateset), CNOT, CZ, CP, SWAP).  dim = 2 or 4.
+bool gate_matrix(const qs_gate& g, cd* m, int* dim);
+// d/dparam[k] of the gate matrix (parameterised kinds only).
+bool gate_dmatrix(const qs_gate& g, int k, cd* m);
+int gate_nparams(int kind);
+bool gate_is_two_qubit(int kind);
+qs_status validate_gates(const qs_gate* gates, size_t ngates, int n);
+
+// ---------------------------------------------------------------- fused ops
+// Device-independent op after fusion, on *virtual* qubits.
+enum FOpType : int { F_G1 = 0, F_G1C = 1, F_D = 2, F_G2 = 3 };
+
+struct FOp {
+  FOpType type;
+  int t = -1;      // G1/G1C target
+  int c = -1;      // G1C choice qubit: matrix m1 when its bit is 1, m0 otherwise
+  int a = -1;      // D: first qubit (most significant of the diagonal index); G2: first qubit
+  int b = -1;      // D: second qubit or -1 (one-qubit diagonal); G2: second qubit
+  cd m0[4], m1[4]; // G1/G1C matrices U[out][in]
+  cd d[4];         // D: entries, index 2*bit_a + bit_b (or bit_a when b < 0)
+  cd g[16];        // G2 4x4
+};
+
+// Converts gates into fused ops.  vmap_out[q] = virtual qubit that holds logical
+// qubit q at the end (SWAPs become relabelings).
+// fuse: merge one-qubit runs and fold diagonals; relabel: SWAPs become
+// relabelings (else they are dense two-qubit ops).
+void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp>& out,
+                     std::vector<int>& vmap_out, bool fuse, bool relabel);
+
+// ---------------------------------------------------------------- device ops
+template <typename R>
+struct alignas(2 * sizeof(R)) C2 {
+  R x, y;
+};
+
+// kinds of a tile op
+enum : uint8_t { TK_REG = 0, TK_LANE = 1, TK_DIAG = 2 };
+// sources of a choice / diagonal bit
+enum : uint8_t { CS_NONE = 0, CS_TILE = 1, CS_LANE = 2, CS_WARP = 3, CS_REG = 4, CS_ONE = 5 };
+
+template <typename R>
+struct alignas(16) TileOp {
+  uint8_t kind;    // TK_*
+  uint8_t slot;    // register slot (TK_REG) or lane bit (TK_LANE)
+  uint8_t csrc;    // choice source (TK_REG/TK_LANE) or source of diag bit a (TK_DIAG)
+  uint8_t cbit;
+  uint8_t dsrc;    // TK_DIAG: source of bit b (CS_NONE for one-qubit diagonals)
+  uint8_t dbit;
+  uint8_t pad[10];
+  C2<R> m0[4];     // matrix (choice bit 0) or diagonal d[0..3]
+  C2<R> m1[4];     // matrix (choice bit 1)
+};
+
+constexpr int kTileBits = 12;     // 4096 amplitudes per tile
+constexpr int kLaneBits = 5;
+constexpr int kRegBits = 4;       // 16 amplitudes per thread
+constexpr int kWarpBits = 3;      // 8 warps, 256 threads
+constexpr int kTileThreads = 1 << (kLaneBits + kWarpBits);
+
+struct TileStage {
+  uint8_t reg[kRegBits];    // local bit in register slot k
+  uint8_t warp[kWarpBits];  // local bit of warp-id bit k
+  uint8_t pad;
+  int32_t op_begin, op_end;
+};
+
+struct TilePass {
+  int32_t n_stages;
+  int32_t stage_begin;
+  int32_t n_nt;                 // number of non-tile bits
+  uint8_t pos[kTileBits];       // physical bit of local bit i (ascending)
+  uint8_t nt_pos[48];           // physical bits outside the tile (ascending)
+};
+
+// Device-side plain op (one launch per op; also the small-state kernel's op).
+template <typename R>
+struct alignas(16) PlainOp {
+  int32_t type;    // FOpType
+  int32_t t, c, a, b;
+  int32_t pad[3];
+  C2<R> m[16];     // G1: m[0..3]; G1C: m[0..3] choice 0, m[4..7] choice 1; D: m[0..3]; G2: m[0..15]
+};
+
+// ---------------------------------------------------------------- plan
+struct PlanStep {
+  enum Kind { TILE, PLAIN, REMAP, SMALL } kind;
+  int index;          // TILE: pass index; PLAIN: op index into plain list; REMAP: remap index
+};
+
+struct RemapDesc {
+  // A permutation of the bit positions pos[0..11] (ascending): the amplitude
+  // bit at local position src[j] moves to local position j.  Positions outside
+  // the tile are unchanged, so every CTA reads and writes the same addresses.
+  int32_t n_t;                  // tile bits (= kTileBits)
+  uint8_t pos[kTileBits];       // physical positions of the tile (ascending)
+  uint8_t src[kTileBits];       // local source bit of local destination bit j
+  int32_t n_nt;
+  uint8_t nt_pos[48];
+};
+
+struct Plan {
+  std::vector<TilePass> passes;
+  std::vector<TileStage> stages;
+  std::vector<FOp> tile_fops;       // ops in tile order (converted per precision later)
+  std::vector<uint8_t> tile_kind, tile_slot, tile_csrc, tile_cbit, tile_dsrc, tile_dbit;
+  std::vector<FOp> plain_fops;      // plain-kernel ops (physical qubit ids)
+  std::vector<RemapDesc> remaps;
+  std::vector<PlanStep> steps;
+  int64_t n_ops = 0;
+};
+
+// Plans tile passes for n >= kTileBits.  Ops refer to virtual qubits; l2p maps
+// virtual -> physical (updated by remaps); final layout is canonical
+// (physical position q holds logical qubit q).
+void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vmap_final,
+                  Plan& plan);
+
+// ---------------------------------------------------------------- launchers
+// (sv_kernels.cu)
+qs_status launch_set_basis(State* st, uint64_t J);
+qs_status launch_tile_pass(State* st, const void* pass_dev, const void* stages_dev,
+                           const void* ops_dev, int n_stages);
+qs_status launch_plain_op(State* st, const void* op_dev, int type);
+qs_status launch_small(State* st, const void* ops_dev, int nops);
+qs_status launch_remap(State* st, const void* desc_dev, void* tmp);
+qs_status launch_probs(State* st, void* out, int out_fp64, uint64_t mask, double* partials,
+                       uint8_t* bits_dev, double* marg_acc);
+qs_status launch_reduce_partials(State* st, const double* partials, int count, double* out);
+qs_status launch_loglik(State* st, const uint32_t* counts, double* partials,
+                        unsigned long long* clamps);
+
+}  // namespace qs

@@ -1,0 +1,587 @@
+// Host fusion planner: gates -> fused ops -> tile passes (+ plain ops, remaps).
+//
+// The circuit is the ordered product of gates (section "Quantum circuits").
+// The planner only regroups that product where it is exact:
+//   * consecutive one-qubit gates on a qubit are multiplied;
+//   * diagonal gates (CZ, CP, Z, S, T, R^z, U1, R(k)) are diagonal in the
+//     computational basis, so they are evaluated from index bits -- the same
+//     idea as the diagonal factors of the thesis's product formula (Eq.
+//     (HtotalDecompositionH0DiagonalImplementation)) -- and are folded into a
+//     neighbouring one-qubit gate as a choice between two matrices selected by
+//     a bit ("controlled" form), moved only across gates they commute with;
+//   * CNOT and other block-diagonal two-qubit gates become "choice" gates
+//     (target matrix selected by the control bit);
+//   * SWAP is a relabeling of qubits; the final layout is restored by remaps.
+// A tile pass then applies every op whose non-diagonal qubit lies in a set of
+// 12 qubits (the tile) in one read+write of the state.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+namespace qs {
+
+namespace {
+
+constexpr double kTiny = 0.0;   // exact zero tests: gate tables give exact zeros
+
+bool is_zero(cd z) { return z.real() == kTiny && z.imag() == kTiny; }
+
+void mat2_mul(const cd* A, const cd* B, cd* C) {   // C = A B (2x2)
+  cd r[4];
+  r[0] = A[0] * B[0] + A[1] * B[2];
+  r[1] = A[0] * B[1] + A[1] * B[3];
+  r[2] = A[2] * B[0] + A[3] * B[2];
+  r[3] = A[2] * B[1] + A[3] * B[3];
+  for (int i = 0; i < 4; ++i) C[i] = r[i];
+}
+
+void diag_mul_right(const cd* U, cd d0, cd d1, cd* out) {   // U diag(d0, d1)
+  out[0] = U[0] * d0;
+  out[1] = U[1] * d1;
+  out[2] = U[2] * d0;
+  out[3] = U[3] * d1;
+}
+
+void diag_mul_left(cd d0, cd d1, const cd* U, cd* out) {    // diag(d0, d1) U
+  out[0] = d0 * U[0];
+  out[1] = d0 * U[1];
+  out[2] = d1 * U[2];
+  out[3] = d1 * U[3];
+}
+
+uint64_t nd_mask(const FOp& o) {
+  switch (o.type) {
+    case F_G1: case F_G1C: return 1ull << o.t;
+    case F_G2: return (1ull << o.a) | (1ull << o.b);
+    default: return 0;
+  }
+}
+
+uint64_t d_mask(const FOp& o) {
+  switch (o.type) {
+    case F_G1C: return 1ull << o.c;
+    case F_D: return (1ull << o.a) | (o.b >= 0 ? (1ull << o.b) : 0);
+    default: return 0;
+  }
+}
+
+// diagonal entries of a one-qubit D op or of the part of a two-qubit D op
+// acting on `t` when the other qubit's bit is v.
+void d_restrict(const FOp& D, int t, int v, cd* d0, cd* d1) {
+  if (D.b < 0) {
+    *d0 = D.d[0];
+    *d1 = D.d[1];
+  } else if (t == D.a) {
+    *d0 = D.d[0 * 2 + v];
+    *d1 = D.d[1 * 2 + v];
+  } else {
+    *d0 = D.d[v * 2 + 0];
+    *d1 = D.d[v * 2 + 1];
+  }
+}
+
+// Try to fold diagonal op D into G (a G1 or G1C acting non-diagonally on a
+// qubit of D).  after = true: D acts after G (D G); else D acts before G (G D).
+bool fold_into(const FOp& D, FOp& G, bool after) {
+  int t = G.t;
+  bool t_in = (t == D.a) || (t == D.b);
+  if (!t_in) return false;
+  int other = (D.b < 0) ? -1 : (t == D.a ? D.b : D.a);
+  if (G.type == F_G1) {
+    if (other < 0) {
+      cd d0, d1;
+      d_restrict(D, t, 0, &d0, &d1);
+      if (after) diag_mul_left(d0, d1, G.m0, G.m0);
+      else diag_mul_right(G.m0, d0, d1, G.m0);
+      return true;
+    }
+    cd U[4];
+    for (int i = 0; i < 4; ++i) U[i] = G.m0[i];
+    for (int v = 0; v < 2; ++v) {
+      cd d0, d1;
+      d_restrict(D, t, v, &d0, &d1);
+      cd* M = v ? G.m1 : G.m0;
+      if (after) diag_mul_left(d0, d1, U, M);
+      else diag_mul_right(U, d0, d1, M);
+    }
+    G.type = F_G1C;
+    G.c = other;
+    return true;
+  }
+  if (G.type == F_G1C) {
+    if (other >= 0 && other != G.c) return false;
+    for (int v = 0; v < 2; ++v) {
+      cd d0, d1;
+      d_restrict(D, t, other < 0 ? 0 : v, &d0, &d1);
+      cd* M = v ? G.m1 : G.m0;
+      if (after) diag_mul_left(d0, d1, M, M);
+      else diag_mul_right(M, d0, d1, M);
+    }
+    return true;
+  }
+  return false;
+}
+
+// Does op X commute with diagonal op D?  (shared qubits must all be diagonal in X)
+bool commutes_with_diag(const FOp& X, const FOp& D) {
+  uint64_t dq = d_mask(D);
+  return (nd_mask(X) & dq) == 0;
+}
+
+}  // namespace
+
+void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp>& out,
+                     std::vector<int>& vmap_out, bool fuse, bool relabel) {
+  out.clear();
+  std::vector<int> cur(n);
+  for (int q = 0; q < n; ++q) cur[q] = q;
+  for (size_t i = 0; i < ngates; ++i) {
+    const qs_gate& g = gates[i];
+    cd m[16];
+    int dim = 0;
+    gate_matrix(g, m, &dim);
+    FOp o{};
+    if (dim == 2) {
+      int v = cur[g.q[0]];
+      if (is_zero(m[1]) && is_zero(m[2])) {
+        o.type = F_D;
+        o.a = v;
+        o.b = -1;
+        o.d[0] = m[0];
+        o.d[1] = m[3];
+      } else {
+        o.type = F_G1;
+        o.t = v;
+        for (int k = 0; k < 4; ++k) o.m0[k] = m[k];
+      }
+      out.push_back(o);
+      continue;
+    }
+    if (g.kind == QS_SWAP && relabel) {
+      std::swap(cur[g.q[0]], cur[g.q[1]]);
+      continue;
+    }
+    int v0 = cur[g.q[0]], v1 = cur[g.q[1]];
+    bool diag = true, blk0 = true, blk1 = true;
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) {
+        if (is_zero(m[4 * r + c])) continue;
+        if (r != c) diag = false;
+        if ((r >> 1) != (c >> 1)) blk0 = false;   // block-diagonal in qubit 0 (msb)
+        if ((r & 1) != (c & 1)) blk1 = false;     // block-diagonal in qubit 1 (lsb)
+      }
+    if (diag) {
+      o.type = F_D;
+      o.a = v0;
+      o.b = v1;
+      for (int k = 0; k < 4; ++k) o.d[k] = m[5 * k];
+    } else if (blk0) {   // target q1, choice q0
+      o.type = F_G1C;
+      o.t = v1;
+      o.c = v0;
+      o.m0[0] = m[0]; o.m0[1] = m[1]; o.m0[2] = m[4]; o.m0[3] = m[5];
+      o.m1[0] = m[10]; o.m1[1] = m[11]; o.m1[2] = m[14]; o.m1[3] = m[15];
+    } else if (blk1) {   // target q0, choice q1
+      o.type = F_G1C;
+      o.t = v0;
+      o.c = v1;
+      o.m0[0] = m[0]; o.m0[1] = m[2]; o.m0[2] = m[8]; o.m0[3] = m[10];
+      o.m1[0] = m[5]; o.m1[1] = m[7]; o.m1[2] = m[13]; o.m1[3] = m[15];
+    } else {
+      o.type = F_G2;
+      o.a = v0;
+      o.b = v1;
+      for (int k = 0; k < 16; ++k) o.g[k] = m[k];
+    }
+    if (o.type == F_G1C) {
+      bool same = true;
+      for (int k = 0; k < 4; ++k) same = same && (o.m0[k] == o.m1[k]);
+      if (same) {
+        o.type = F_G1;
+        o.c = -1;
+      }
+    }
+    out.push_back(o);
+  }
+  vmap_out = cur;
+  if (!fuse) return;
+
+  // (1) multiply runs of one-qubit ops (G1 / one-qubit D) on the same qubit
+  {
+    std::vector<FOp> merged;
+    std::vector<int> last1(n, -1);   // index in merged of the open one-qubit op on q
+    for (const FOp& o : out) {
+      bool one_q = (o.type == F_G1) || (o.type == F_D && o.b < 0);
+      if (one_q) {
+        int q = (o.type == F_G1) ? o.t : o.a;
+        int j = last1[q];
+        if (j >= 0) {
+          FOp& p = merged[j];
+          cd A[4], B[4];
+          if (p.type == F_G1) for (int k = 0; k < 4; ++k) A[k] = p.m0[k];
+          else { A[0] = p.d[0]; A[1] = 0; A[2] = 0; A[3] = p.d[1]; }
+          if (o.type == F_G1) for (int k = 0; k < 4; ++k) B[k] = o.m0[k];
+          else { B[0] = o.d[0]; B[1] = 0; B[2] = 0; B[3] = o.d[1]; }
+          cd C[4];
+          mat2_mul(B, A, C);   // later op on the left
+          if (is_zero(C[1]) && is_zero(C[2])) {
+            p.type = F_D; p.a = q; p.b = -1; p.t = -1; p.d[0] = C[0]; p.d[1] = C[3];
+          } else {
+            p.type = F_G1; p.t = q; p.a = -1; for (int k = 0; k < 4; ++k) p.m0[k] = C[k];
+          }
+          continue;
+        }
+        merged.push_back(o);
+        last1[q] = (int)merged.size() - 1;
+        continue;
+      }
+      uint64_t touched = nd_mask(o) | d_mask(o);
+      for (int q = 0; q < n; ++q)
+        if ((touched >> q) & 1) last1[q] = -1;
+      merged.push_back(o);
+    }
+    out.swap(merged);
+  }
+
+  // (2) fold diagonal ops into a neighbouring non-diagonal one-qubit op
+  {
+    std::vector<char> dead(out.size(), 0);
+    for (size_t i = 0; i < out.size(); ++i) {
+      if (out[i].type != F_D) continue;
+      const FOp D = out[i];
+      uint64_t dq = d_mask(D);
+      bool done = false;
+      for (size_t j = i + 1; j < out.size() && !done; ++j) {      // forward
+        if (dead[j]) continue;
+        FOp& X = out[j];
+        if (((nd_mask(X) | d_mask(X)) & dq) == 0) continue;
+        if (commutes_with_diag(X, D)) continue;
+        done = fold_into(D, X, /*after=*/false);
+        break;
+      }
+      for (size_t j = i; j-- > 0 && !done;) {                      // backward
+        if (dead[j]) continue;
+        FOp& X = out[j];
+        if (((nd_mask(X) | d_mask(X)) & dq) == 0) continue;
+        if (commutes_with_diag(X, D)) continue;
+        done = fold_into(D, X, /*after=*/true);
+        break;
+      }
+      if (done) dead[i] = 1;
+    }
+    std::vector<FOp> kept;
+    for (size_t i = 0; i < out.size(); ++i)
+      if (!dead[i]) kept.push_back(out[i]);
+    out.swap(kept);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tile-pass planning
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Encoder {
+  // physical layout for the pass
+  int n;
+  uint8_t pos[kTileBits];
+  int local_of_phys[64];   // -1 if not in tile
+  int nt_rank[64];         // rank among non-tile positions
+  const int* l2p;          // virtual -> physical
+  int reg[kRegBits];
+  int warp[kWarpBits];
+
+  void src_of(int v, uint8_t* src, uint8_t* bit) const {
+    int p = l2p[v];
+    int loc = local_of_phys[p];
+    if (loc < 0) {
+      *src = CS_TILE;
+      *bit = (uint8_t)nt_rank[p];
+      return;
+    }
+    if (loc < kLaneBits) {
+      *src = CS_LANE;
+      *bit = (uint8_t)loc;
+      return;
+    }
+    for (int k = 0; k < kRegBits; ++k)
+      if (reg[k] == loc) {
+        *src = CS_REG;
+        *bit = (uint8_t)k;
+        return;
+      }
+    for (int k = 0; k < kWarpBits; ++k)
+      if (warp[k] == loc) {
+        *src = CS_WARP;
+        *bit = (uint8_t)k;
+        return;
+      }
+    *src = CS_NONE;
+    *bit = 0;
+  }
+};
+
+int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+}  // namespace
+
+void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vmap_final,
+                  Plan& plan) {
+  plan = Plan{};
+  std::vector<int> l2p(n), p2l(n);
+  for (int q = 0; q < n; ++q) l2p[q] = p2l[q] = q;
+
+  std::vector<int> remaining;
+  remaining.reserve(ops.size());
+  for (size_t i = 0; i < ops.size(); ++i) remaining.push_back((int)i);
+
+  const int kLow = 2;   // physical bits always in a tile (contiguous 32-byte sectors)
+
+  while (!remaining.empty()) {
+    // a ready two-qubit dense op goes to the plain kernel
+    if (ops[remaining[0]].type == F_G2) {
+      FOp o = ops[remaining[0]];
+      o.a = l2p[o.a];
+      o.b = l2p[o.b];
+      plan.plain_fops.push_back(o);
+      plan.steps.push_back({PlanStep::PLAIN, (int)plan.plain_fops.size() - 1});
+      remaining.erase(remaining.begin());
+      continue;
+    }
+    // ---- choose the tile's qubits and the ops of this pass
+    uint64_t T = 0;
+    for (int p = 0; p < kLow; ++p) T |= 1ull << p2l[p];
+    uint64_t nd_blk = 0, d_blk = 0;
+    std::vector<int> sel;
+    std::vector<int> rest;
+    for (int idx : remaining) {
+      const FOp& o = ops[idx];
+      uint64_t ndq = nd_mask(o), dq = d_mask(o);
+      bool conflict = (ndq & (nd_blk | d_blk)) || (dq & nd_blk);
+      if (!conflict && o.type != F_G2) {
+        uint64_t need = ndq & ~T;
+        if (popc(T | need) <= kTileBits) {
+          T |= need;
+          sel.push_back(idx);
+          continue;
+        }
+      }
+      nd_blk |= ndq;
+      d_blk |= dq;
+      rest.push_back(idx);
+    }
+    // fill the tile up to kTileBits with the lowest remaining physical positions
+    for (int p = 0; p < n && popc(T) < kTileBits; ++p) T |= 1ull << p2l[p];
+
+    // ---- layout
+    Encoder enc{};
+    enc.n = n;
+    enc.l2p = l2p.data();
+    for (int p = 0; p < 64; ++p) enc.local_of_phys[p] = -1, enc.nt_rank[p] = -1;
+    TilePass tp{};
+    {
+      int k = 0, r = 0;
+      for (int p = 0; p < n; ++p) {
+        if ((T >> p2l[p]) & 1) {
+          enc.pos[k] = (uint8_t)p;
+          tp.pos[k] = (uint8_t)p;
+          enc.local_of_phys[p] = k++;
+        } else {
+          tp.nt_pos[r] = (uint8_t)p;
+          enc.nt_rank[p] = r++;
+        }
+      }
+      tp.n_nt = r;
+    }
+    tp.stage_begin = (int)plan.stages.size();
+
+    // ---- stages
+    std::vector<int> pending = sel;
+    while (!pending.empty()) {
+      int R[kRegBits];
+      int nR = 0;
+      uint64_t snd = 0, sd = 0;
+      std::vector<int> stage_ops, later;
+      for (int idx : pending) {
+        const FOp& o = ops[idx];
+        uint64_t ndq = nd_mask(o), dq = d_mask(o);
+        bool conflict = (ndq & (snd | sd)) || (dq & snd);
+        bool ok = false;
+        if (!conflict) {
+          if (o.type == F_D) {
+            ok = true;
+          } else {
+            int loc = enc.local_of_phys[l2p[o.t]];
+            if (loc < kLaneBits) {
+              ok = true;
+            } else {
+              bool in = false;
+              for (int k = 0; k < nR; ++k) in = in || (R[k] == loc);
+              if (in) ok = true;
+              else if (nR < kRegBits) {
+                R[nR++] = loc;
+                ok = true;
+              }
+            }
+          }
+        }
+        if (ok) stage_ops.push_back(idx);
+        else {
+          snd |= ndq;
+          sd |= dq;
+          later.push_back(idx);
+        }
+      }
+      // complete the register set (prefer targets needed next)
+      for (int idx : later) {
+        if (nR >= kRegBits) break;
+        const FOp& o = ops[idx];
+        if (o.type == F_D) continue;
+        int loc = enc.local_of_phys[l2p[o.t]];
+        if (loc < kLaneBits) continue;
+        bool in = false;
+        for (int k = 0; k < nR; ++k) in = in || (R[k] == loc);
+        if (!in) R[nR++] = loc;
+      }
+      for (int loc = kLaneBits; loc < kTileBits && nR < kRegBits; ++loc) {
+        bool in = false;
+        for (int k = 0; k < nR; ++k) in = in || (R[k] == loc);
+        if (!in) R[nR++] = loc;
+      }
+      TileStage ts{};
+      for (int k = 0; k < kRegBits; ++k) ts.reg[k] = (uint8_t)R[k], enc.reg[k] = R[k];
+      {
+        int w = 0;
+        for (int loc = kLaneBits; loc < kTileBits; ++loc) {
+          bool in = false;
+          for (int k = 0; k < kRegBits; ++k) in = in || (R[k] == loc);
+          if (!in) {
+            ts.warp[w] = (uint8_t)loc;
+            enc.warp[w++] = loc;
+          }
+        }
+      }
+      ts.op_begin = (int)plan.tile_fops.size();
+      for (int idx : stage_ops) {
+        const FOp& o = ops[idx];
+        uint8_t kind = TK_DIAG, slot = 0, csrc = CS_NONE, cbit = 0, dsrc = CS_NONE, dbit = 0;
+        if (o.type == F_D) {
+          enc.src_of(o.a, &csrc, &cbit);
+          if (o.b >= 0) enc.src_of(o.b, &dsrc, &dbit);
+        } else {
+          int loc = enc.local_of_phys[l2p[o.t]];
+          if (loc < kLaneBits) {
+            kind = TK_LANE;
+            slot = (uint8_t)loc;
+          } else {
+            kind = TK_REG;
+            for (int k = 0; k < kRegBits; ++k)
+              if (R[k] == loc) slot = (uint8_t)k;
+          }
+          if (o.type == F_G1C) enc.src_of(o.c, &csrc, &cbit);
+        }
+        plan.tile_fops.push_back(o);
+        plan.tile_kind.push_back(kind);
+        plan.tile_slot.push_back(slot);
+        plan.tile_csrc.push_back(csrc);
+        plan.tile_cbit.push_back(cbit);
+        plan.tile_dsrc.push_back(dsrc);
+        plan.tile_dbit.push_back(dbit);
+      }
+      ts.op_end = (int)plan.tile_fops.size();
+      plan.stages.push_back(ts);
+      pending.swap(later);
+    }
+    tp.n_stages = (int)plan.stages.size() - tp.stage_begin;
+    plan.passes.push_back(tp);
+    plan.steps.push_back({PlanStep::TILE, (int)plan.passes.size() - 1});
+    remaining.swap(rest);
+  }
+
+  // ---- restore the canonical layout: logical q must sit at physical q.
+  // Virtual vmap_final[q] holds logical q and sits at physical l2p[...].
+  std::vector<int> where(n);   // where[q] = current physical position of logical q
+  for (int q = 0; q < n; ++q) where[q] = l2p[vmap_final[q]];
+  for (int guard = 0; guard < 4 * n + 8; ++guard) {
+    bool ok = true;
+    for (int q = 0; q < n; ++q) ok = ok && (where[q] == q);
+    if (ok) break;
+    // content at physical p is logical who[p]; it must move to physical who[p]
+    std::vector<int> who(n);
+    for (int q = 0; q < n; ++q) who[where[q]] = q;
+    // positions taking part; the two lowest stay in for contiguous sectors
+    uint64_t S = 3;
+    std::vector<char> seen(n, 0);
+    for (int p = 0; p < n; ++p) {
+      if (seen[p] || who[p] == p) continue;
+      std::vector<int> cyc;
+      int x = p;
+      while (!seen[x]) {
+        seen[x] = 1;
+        cyc.push_back(x);
+        x = who[x];   // content of x goes to who[x]
+      }
+      uint64_t cm = 0;
+      for (int y : cyc) cm |= 1ull << y;
+      int room = kTileBits - popc(S);
+      if (popc(cm & ~S) <= room) {
+        S |= cm;
+      } else {
+        // a prefix of the cycle: all but its last element land correctly
+        for (int y : cyc) {
+          if (popc(S) >= kTileBits) break;
+          S |= 1ull << y;
+        }
+      }
+    }
+    // low positions keep loads/stores contiguous: fill with the lowest ones
+    for (int p = 0; p < n && popc(S) < kTileBits; ++p) S |= 1ull << p;
+    RemapDesc rd{};
+    int k = 0, r = 0;
+    int loc[64];
+    for (int p = 0; p < n; ++p) {
+      if ((S >> p) & 1) {
+        rd.pos[k] = (uint8_t)p;
+        loc[p] = k++;
+      } else {
+        rd.nt_pos[r++] = (uint8_t)p;
+        loc[p] = -1;
+      }
+    }
+    rd.n_t = k;
+    rd.n_nt = r;
+    // destination inside S for every source position in S
+    std::vector<int> dest(n, -1);
+    std::vector<char> taken(n, 0);
+    for (int p = 0; p < n; ++p)
+      if (((S >> p) & 1) && ((S >> who[p]) & 1)) {
+        dest[p] = who[p];
+        taken[who[p]] = 1;
+      }
+    for (int p = 0; p < n; ++p)
+      if (((S >> p) & 1) && dest[p] < 0) {
+        for (int t = 0; t < n; ++t)
+          if (((S >> t) & 1) && !taken[t]) {
+            dest[p] = t;
+            taken[t] = 1;
+            break;
+          }
+      }
+    // src_of_out: the remap kernel reads local in-bit src[j] for out-local bit j
+    for (int p = 0; p < n; ++p)
+      if ((S >> p) & 1) rd.src[loc[dest[p]]] = (uint8_t)loc[p];
+    plan.remaps.push_back(rd);
+    plan.steps.push_back({PlanStep::REMAP, (int)plan.remaps.size() - 1});
+    std::vector<int> nw(n);
+    for (int q = 0; q < n; ++q) {
+      int p = where[q];
+      nw[q] = ((S >> p) & 1) ? dest[p] : p;
+    }
+    where.swap(nw);
+  }
+  plan.n_ops = (int64_t)ops.size();
+}
+
+}  // namespace qs

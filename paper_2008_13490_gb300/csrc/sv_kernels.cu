@@ -1,0 +1,761 @@
+// State-vector kernels for sm_103a.
+//
+//  tile_pass_kernel   one HBM read+write of the state applies every op of a
+//                     pass: a CTA owns a tile of 2^12 amplitudes (12 qubits,
+//                     any bit positions that include bits 0,1), lanes hold the 5
+//                     lowest tile bits (gates there use warp shuffles), each
+//                     thread holds 16 amplitudes in registers (4 tile bits),
+//                     and shared memory transposes swap register and warp bits
+//                     between stages.
+//  plain_*_kernel     one launch per gate, the pair/quad update of the thesis's
+//                     four-component loops (Eq. (psioft4componentupdates)) with
+//                     the bit-insert index of its reduced loop, 64-bit indices.
+//  small_state_kernel whole state in one CTA's shared memory (n < 12).
+//  remap_kernel       permutes bit positions inside a 12-bit tile (in place).
+//  probs / marginal / loglik / reduce: Born rule p_J = |a_J|^2 with fp64
+//                     accumulation of the sums.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace qs {
+
+// ------------------------------------------------------------------ helpers
+
+template <typename R>
+__device__ __forceinline__ C2<R> cfma2(C2<R> m0, C2<R> a, C2<R> m1, C2<R> b) {
+  // m0*a + m1*b
+  C2<R> r;
+  r.x = m0.x * a.x;
+  r.x = fma(-m0.y, a.y, r.x);
+  r.x = fma(m1.x, b.x, r.x);
+  r.x = fma(-m1.y, b.y, r.x);
+  r.y = m0.x * a.y;
+  r.y = fma(m0.y, a.x, r.y);
+  r.y = fma(m1.x, b.y, r.y);
+  r.y = fma(m1.y, b.x, r.y);
+  return r;
+}
+
+template <typename R>
+__device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
+  C2<R> r;
+  r.x = a.x * b.x;
+  r.x = fma(-a.y, b.y, r.x);
+  r.y = a.x * b.y;
+  r.y = fma(a.y, b.x, r.y);
+  return r;
+}
+
+template <typename R>
+__device__ __forceinline__ C2<R> csel(bool s, C2<R> a, C2<R> b) {
+  C2<R> r;
+  r.x = s ? a.x : b.x;
+  r.y = s ? a.y : b.y;
+  return r;
+}
+
+template <typename R>
+__device__ __forceinline__ C2<R> shfl_xor_c(C2<R> v, int m) {
+  C2<R> r;
+  r.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  r.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return r;
+}
+
+// ------------------------------------------------------------------ tile pass
+
+template <int J, typename R>
+__device__ __forceinline__ void reg_gate(C2<R>* v, const C2<R>* m) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    if (r & (1 << J)) continue;
+    const C2<R> a = v[r], b = v[r | (1 << J)];
+    v[r] = cfma2(m[0], a, m[1], b);
+    v[r | (1 << J)] = cfma2(m[2], a, m[3], b);
+  }
+}
+
+template <int J, int K, typename R>
+__device__ __forceinline__ void reg_gate_choice(C2<R>* v, const C2<R>* m0, const C2<R>* m1) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    if (r & (1 << J)) continue;
+    const C2<R>* m = ((r >> K) & 1) ? m1 : m0;
+    const C2<R> a = v[r], b = v[r | (1 << J)];
+    v[r] = cfma2(m[0], a, m[1], b);
+    v[r | (1 << J)] = cfma2(m[2], a, m[3], b);
+  }
+}
+
+template <int K, typename R>
+__device__ __forceinline__ void lane_gate_choice(C2<R>* v, int mask, C2<R> o0, C2<R> p0, C2<R> o1,
+                                                 C2<R> p1) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const C2<R> q = shfl_xor_c(v[r], mask);
+    if ((r >> K) & 1) v[r] = cfma2(o1, v[r], p1, q);
+    else v[r] = cfma2(o0, v[r], p0, q);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ int src_bit(uint8_t src, uint8_t bit, uint64_t tile, int lane, int warp) {
+  switch (src) {
+    case CS_TILE: return (int)((tile >> bit) & 1ull);
+    case CS_LANE: return (lane >> bit) & 1;
+    case CS_WARP: return (warp >> bit) & 1;
+    default: return 0;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_tile_op(C2<R>* v, const TileOp<R>* __restrict__ opp,
+                                              uint64_t tile, int lane, int warp) {
+  const uint8_t kind = opp->kind, slot = opp->slot, csrc = opp->csrc, cbit = opp->cbit;
+  C2<R> m0[4], m1[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    m0[i] = opp->m0[i];
+    m1[i] = opp->m1[i];
+  }
+  if (kind == TK_REG) {
+    if (csrc == CS_REG) {
+      switch (slot * 4 + cbit) {
+        case 1: reg_gate_choice<0, 1>(v, m0, m1); break;
+        case 2: reg_gate_choice<0, 2>(v, m0, m1); break;
+        case 3: reg_gate_choice<0, 3>(v, m0, m1); break;
+        case 4: reg_gate_choice<1, 0>(v, m0, m1); break;
+        case 6: reg_gate_choice<1, 2>(v, m0, m1); break;
+        case 7: reg_gate_choice<1, 3>(v, m0, m1); break;
+        case 8: reg_gate_choice<2, 0>(v, m0, m1); break;
+        case 9: reg_gate_choice<2, 1>(v, m0, m1); break;
+        case 11: reg_gate_choice<2, 3>(v, m0, m1); break;
+        case 12: reg_gate_choice<3, 0>(v, m0, m1); break;
+        case 13: reg_gate_choice<3, 1>(v, m0, m1); break;
+        case 14: reg_gate_choice<3, 2>(v, m0, m1); break;
+        default: break;
+      }
+      return;
+    }
+    const bool s = (csrc != CS_NONE) && src_bit<R>(csrc, cbit, tile, lane, warp);
+    C2<R> m[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) m[i] = csel(s, m1[i], m0[i]);
+    switch (slot) {
+      case 0: reg_gate<0>(v, m); break;
+      case 1: reg_gate<1>(v, m); break;
+      case 2: reg_gate<2>(v, m); break;
+      default: reg_gate<3>(v, m); break;
+    }
+    return;
+  }
+  if (kind == TK_LANE) {
+    const int mask = 1 << slot;
+    const bool b = (lane >> slot) & 1;
+    // out = own-coefficient * own + partner-coefficient * partner
+    const C2<R> o0 = csel(b, m0[3], m0[0]), p0 = csel(b, m0[2], m0[1]);
+    const C2<R> o1 = csel(b, m1[3], m1[0]), p1 = csel(b, m1[2], m1[1]);
+    if (csrc == CS_REG) {
+      switch (cbit) {
+        case 0: lane_gate_choice<0>(v, mask, o0, p0, o1, p1); break;
+        case 1: lane_gate_choice<1>(v, mask, o0, p0, o1, p1); break;
+        case 2: lane_gate_choice<2>(v, mask, o0, p0, o1, p1); break;
+        default: lane_gate_choice<3>(v, mask, o0, p0, o1, p1); break;
+      }
+      return;
+    }
+    const bool s = (csrc != CS_NONE) && src_bit<R>(csrc, cbit, tile, lane, warp);
+    const C2<R> o = csel(s, o1, o0), p = csel(s, p1, p0);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const C2<R> q = shfl_xor_c(v[r], mask);
+      v[r] = cfma2(o, v[r], p, q);
+    }
+    return;
+  }
+  // TK_DIAG: v *= d[2*bit_a + bit_b] (or d[bit_a] for one-qubit diagonals)
+  const uint8_t dsrc = opp->dsrc, dbit = opp->dbit;
+  const bool two = dsrc != CS_NONE;
+  const int ua = src_bit<R>(csrc, cbit, tile, lane, warp);
+  const int ub = two ? src_bit<R>(dsrc, dbit, tile, lane, warp) : 0;
+  if (csrc != CS_REG && dsrc != CS_REG) {
+    const int idx = two ? (ua * 2 + ub) : ua;
+    const C2<R> d = csel(idx >= 2, csel(idx == 3, m0[3], m0[2]), csel(idx == 1, m0[1], m0[0]));
+    if (d.x == R(1) && d.y == R(0)) return;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], d);
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int ba = (csrc == CS_REG) ? ((r >> cbit) & 1) : ua;
+    const int bb = two ? ((dsrc == CS_REG) ? ((r >> dbit) & 1) : ub) : 0;
+    const int idx = two ? (ba * 2 + bb) : ba;
+    const C2<R> d = csel(idx >= 2, csel(idx == 3, m0[3], m0[2]), csel(idx == 1, m0[1], m0[0]));
+    v[r] = cmul(v[r], d);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kTileThreads)
+    tile_pass_kernel(C2<R>* __restrict__ psi, const TilePass* __restrict__ P,
+                     const TileStage* __restrict__ stages, const TileOp<R>* __restrict__ ops) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<R>* sm = reinterpret_cast<C2<R>*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t tile = blockIdx.x;
+
+  __shared__ uint8_t s_pos[kTileBits];
+  __shared__ uint64_t s_base;
+  if (tid == 0) {
+    const int n_nt = P->n_nt;
+    uint64_t base = 0;
+    for (int j = 0; j < n_nt; ++j) base |= ((tile >> j) & 1ull) << P->nt_pos[j];
+    s_base = base;
+  }
+  if (tid < kTileBits) s_pos[tid] = P->pos[tid];
+  __syncthreads();
+  const uint64_t base = s_base;
+  uint64_t loff = 0;
+#pragma unroll
+  for (int k = 0; k < kLaneBits; ++k)
+    if ((lane >> k) & 1) loff |= 1ull << s_pos[k];
+
+  const int nst = P->n_stages;
+  const TileStage* __restrict__ S = stages + P->stage_begin;
+  C2<R> v[16];
+  {
+    const TileStage s0 = S[0];
+    uint64_t g[kRegBits];
+#pragma unroll
+    for (int k = 0; k < kRegBits; ++k) g[k] = 1ull << s_pos[s0.reg[k]];
+    uint64_t woff = 0;
+#pragma unroll
+    for (int k = 0; k < kWarpBits; ++k)
+      if ((warp >> k) & 1) woff |= 1ull << s_pos[s0.warp[k]];
+    const C2<R>* __restrict__ src = psi + (base | loff | woff);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      uint64_t o = 0;
+#pragma unroll
+      for (int k = 0; k < kRegBits; ++k)
+        if ((r >> k) & 1) o |= g[k];
+      v[r] = src[o];
+    }
+  }
+  for (int s = 0; s < nst; ++s) {
+    const TileStage cur = S[s];
+    if (s > 0) {
+      const TileStage prev = S[s - 1];
+      int rb[kRegBits];
+      int wo = lane;
+#pragma unroll
+      for (int k = 0; k < kRegBits; ++k) rb[k] = 1 << prev.reg[k];
+#pragma unroll
+      for (int k = 0; k < kWarpBits; ++k)
+        if ((warp >> k) & 1) wo |= 1 << prev.warp[k];
+      if (s > 1) __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        int o = wo;
+#pragma unroll
+        for (int k = 0; k < kRegBits; ++k)
+          if ((r >> k) & 1) o |= rb[k];
+        sm[o] = v[r];
+      }
+      __syncthreads();
+      int ro = lane;
+#pragma unroll
+      for (int k = 0; k < kRegBits; ++k) rb[k] = 1 << cur.reg[k];
+#pragma unroll
+      for (int k = 0; k < kWarpBits; ++k)
+        if ((warp >> k) & 1) ro |= 1 << cur.warp[k];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        int o = ro;
+#pragma unroll
+        for (int k = 0; k < kRegBits; ++k)
+          if ((r >> k) & 1) o |= rb[k];
+        v[r] = sm[o];
+      }
+    }
+    for (int o = cur.op_begin; o < cur.op_end; ++o) apply_tile_op<R>(v, ops + o, tile, lane, warp);
+  }
+  {
+    const TileStage sl = S[nst - 1];
+    uint64_t g[kRegBits];
+#pragma unroll
+    for (int k = 0; k < kRegBits; ++k) g[k] = 1ull << s_pos[sl.reg[k]];
+    uint64_t woff = 0;
+#pragma unroll
+    for (int k = 0; k < kWarpBits; ++k)
+      if ((warp >> k) & 1) woff |= 1ull << s_pos[sl.warp[k]];
+    C2<R>* __restrict__ dst = psi + (base | loff | woff);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      uint64_t o = 0;
+#pragma unroll
+      for (int k = 0; k < kRegBits; ++k)
+        if ((r >> k) & 1) o |= g[k];
+      dst[o] = v[r];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ plain per-gate
+
+__device__ __forceinline__ uint64_t insert_zero(uint64_t i, int b) {
+  // bit-insert index of the thesis's reduced loop: ((i & ~m) << 1) | (i & m), m = 2^b - 1
+  const uint64_t m = (1ull << b) - 1ull;
+  return ((i & ~m) << 1) | (i & m);
+}
+
+template <typename R>
+__global__ void plain_g1_kernel(C2<R>* __restrict__ psi, int n, PlainOp<R> op) {
+  const uint64_t half = 1ull << (n - 1);
+  const int t = op.t;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < half;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i0 = insert_zero(i, t), i1 = i0 | (1ull << t);
+    const C2<R>* m = op.m;
+    if (op.type == F_G1C && ((i0 >> op.c) & 1ull)) m = op.m + 4;
+    const C2<R> a = psi[i0], b = psi[i1];
+    psi[i0] = cfma2(m[0], a, m[1], b);
+    psi[i1] = cfma2(m[2], a, m[3], b);
+  }
+}
+
+template <typename R>
+__global__ void plain_diag_kernel(C2<R>* __restrict__ psi, int n, PlainOp<R> op) {
+  const uint64_t N = 1ull << n;
+  for (uint64_t J = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; J < N;
+       J += (uint64_t)gridDim.x * blockDim.x) {
+    const int ba = (int)((J >> op.a) & 1ull);
+    const int idx = op.b >= 0 ? ba * 2 + (int)((J >> op.b) & 1ull) : ba;
+    psi[J] = cmul(psi[J], op.m[idx]);
+  }
+}
+
+template <typename R>
+__global__ void plain_g2_kernel(C2<R>* __restrict__ psi, int n, PlainOp<R> op) {
+  const uint64_t quarter = 1ull << (n - 2);
+  const int lo = op.a < op.b ? op.a : op.b, hi = op.a < op.b ? op.b : op.a;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < quarter;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t base = insert_zero(insert_zero(i, lo), hi);
+    uint64_t idx[4];
+    C2<R> a[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {   // local index 2*bit_a + bit_b
+      idx[l] = base | ((uint64_t)(l >> 1) << op.a) | ((uint64_t)(l & 1) << op.b);
+      a[l] = psi[idx[l]];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      C2<R> acc = cfma2(op.m[4 * r + 0], a[0], op.m[4 * r + 1], a[1]);
+      const C2<R> acc2 = cfma2(op.m[4 * r + 2], a[2], op.m[4 * r + 3], a[3]);
+      acc.x += acc2.x;
+      acc.y += acc2.y;
+      psi[idx[r]] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ small states
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+    small_state_kernel(C2<R>* __restrict__ psi, int n, const PlainOp<R>* __restrict__ ops, int nops) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<R>* sm = reinterpret_cast<C2<R>*>(smem_raw);
+  const int N = 1 << n;
+  for (int J = threadIdx.x; J < N; J += blockDim.x) sm[J] = psi[J];
+  __syncthreads();
+  for (int k = 0; k < nops; ++k) {
+    const PlainOp<R>* op = ops + k;
+    const int type = op->type;
+    if (type == F_G1 || type == F_G1C) {
+      const int t = op->t, c = op->c;
+      for (int i = threadIdx.x; i < N / 2; i += blockDim.x) {
+        const int i0 = (int)insert_zero(i, t), i1 = i0 | (1 << t);
+        const C2<R>* m = op->m;
+        if (type == F_G1C && ((i0 >> c) & 1)) m = op->m + 4;
+        const C2<R> a = sm[i0], b = sm[i1];
+        sm[i0] = cfma2(m[0], a, m[1], b);
+        sm[i1] = cfma2(m[2], a, m[3], b);
+      }
+    } else if (type == F_D) {
+      for (int J = threadIdx.x; J < N; J += blockDim.x) {
+        const int ba = (J >> op->a) & 1;
+        const int idx = op->b >= 0 ? ba * 2 + ((J >> op->b) & 1) : ba;
+        sm[J] = cmul(sm[J], op->m[idx]);
+      }
+    } else {
+      const int lo = op->a < op->b ? op->a : op->b, hi = op->a < op->b ? op->b : op->a;
+      for (int i = threadIdx.x; i < N / 4; i += blockDim.x) {
+        const int base = (int)insert_zero(insert_zero(i, lo), hi);
+        int idx[4];
+        C2<R> a[4];
+        for (int l = 0; l < 4; ++l) {
+          idx[l] = base | ((l >> 1) << op->a) | ((l & 1) << op->b);
+          a[l] = sm[idx[l]];
+        }
+        for (int r = 0; r < 4; ++r) {
+          C2<R> acc = cfma2(op->m[4 * r + 0], a[0], op->m[4 * r + 1], a[1]);
+          const C2<R> acc2 = cfma2(op->m[4 * r + 2], a[2], op->m[4 * r + 3], a[3]);
+          acc.x += acc2.x;
+          acc.y += acc2.y;
+          sm[idx[r]] = acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int J = threadIdx.x; J < N; J += blockDim.x) psi[J] = sm[J];
+}
+
+// ------------------------------------------------------------------ remap
+
+template <typename R>
+__global__ void __launch_bounds__(kTileThreads)
+    remap_kernel(C2<R>* __restrict__ psi, const RemapDesc* __restrict__ d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<R>* sm = reinterpret_cast<C2<R>*>(smem_raw);
+  __shared__ uint64_t s_base;
+  __shared__ uint8_t s_pos[kTileBits], s_src[kTileBits];
+  const int tid = threadIdx.x;
+  const uint64_t tile = blockIdx.x;
+  if (tid == 0) {
+    uint64_t base = 0;
+    for (int j = 0; j < d->n_nt; ++j) base |= ((tile >> j) & 1ull) << d->nt_pos[j];
+    s_base = base;
+  }
+  if (tid < kTileBits) {
+    s_pos[tid] = d->pos[tid];
+    s_src[tid] = d->src[tid];
+  }
+  __syncthreads();
+  const uint64_t base = s_base;
+#pragma unroll 4
+  for (int r = 0; r < (1 << kTileBits) / kTileThreads; ++r) {
+    const int L = tid + r * kTileThreads;
+    uint64_t off = base;
+    for (int i = 0; i < kTileBits; ++i)
+      if ((L >> i) & 1) off |= 1ull << s_pos[i];
+    sm[L] = psi[off];
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int r = 0; r < (1 << kTileBits) / kTileThreads; ++r) {
+    const int Lout = tid + r * kTileThreads;
+    uint64_t off = base;
+    int Lin = 0;
+    for (int j = 0; j < kTileBits; ++j)
+      if ((Lout >> j) & 1) {
+        off |= 1ull << s_pos[j];
+        Lin |= 1 << s_src[j];
+      }
+    psi[off] = sm[Lin];
+  }
+}
+
+// ------------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;   // valid in thread 0
+}
+
+template <typename R, typename O>
+__global__ void __launch_bounds__(256)
+    probs_kernel(const C2<R>* __restrict__ psi, O* __restrict__ out, uint64_t N,
+                 double* __restrict__ partials) {
+  double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    const C2<R> a = psi[i];
+    const R p = a.x * a.x + a.y * a.y;
+    if (out) out[i] = (O)p;
+    acc += (double)p;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// float specialisation: two amplitudes (16 bytes) per load, two floats per store
+__global__ void __launch_bounds__(256)
+    probs_kernel_f32x2(const float4* __restrict__ psi2, float2* __restrict__ out2, uint64_t N2,
+                       double* __restrict__ partials) {
+  double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N2; i += stride) {
+    const float4 a = __ldcs(psi2 + i);
+    float2 p;
+    p.x = a.x * a.x + a.y * a.y;
+    p.y = a.z * a.z + a.w * a.w;
+    if (out2) __stcs(out2 + i, p);
+    acc += (double)p.x + (double)p.y;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+    marginal_kernel(const C2<R>* __restrict__ psi, uint64_t N, const uint8_t* __restrict__ bits,
+                    int k, double* __restrict__ acc_out, double* __restrict__ partials) {
+  extern __shared__ double hist[];
+  const int H = 1 << k;
+  const bool use_smem = k <= 12;
+  if (use_smem)
+    for (int i = threadIdx.x; i < H; i += blockDim.x) hist[i] = 0.0;
+  __shared__ uint8_t s_bits[64];
+  if (threadIdx.x < k) s_bits[threadIdx.x] = bits[threadIdx.x];
+  __syncthreads();
+  double tot = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t J = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; J < N; J += stride) {
+    const C2<R> a = psi[J];
+    const double p = (double)(a.x * a.x + a.y * a.y);
+    int K = 0;
+    for (int i = 0; i < k; ++i) K |= (int)((J >> s_bits[i]) & 1ull) << i;
+    if (use_smem) atomicAdd(hist + K, p);
+    else atomicAdd(acc_out + K, p);
+    tot += p;
+  }
+  __syncthreads();
+  if (use_smem)
+    for (int i = threadIdx.x; i < H; i += blockDim.x)
+      if (hist[i] != 0.0) atomicAdd(acc_out + i, hist[i]);
+  tot = block_sum(tot);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+template <typename O>
+__global__ void convert_kernel(const double* __restrict__ in, O* __restrict__ out, uint64_t count) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (O)in[i];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+    loglik_kernel(const C2<R>* __restrict__ psi, const uint32_t* __restrict__ counts, uint64_t N,
+                  double* __restrict__ partials, unsigned long long* __restrict__ clamps) {
+  double acc = 0.0;
+  unsigned long long nclamp = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t J = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; J < N; J += stride) {
+    const uint32_t c = counts[J];
+    if (c == 0) continue;
+    const C2<R> a = psi[J];
+    double p = (double)(a.x * a.x + a.y * a.y);
+    if (!(p > 0.0)) {
+      p = 1e-300;
+      ++nclamp;
+    }
+    acc += (double)c * log(p);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (nclamp) atomicAdd(clamps, nclamp);
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partials, int count,
+                                       double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) s += partials[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+template <typename R>
+__global__ void set_one_kernel(C2<R>* psi, uint64_t J) {
+  C2<R> one;
+  one.x = R(1);
+  one.y = R(0);
+  psi[J] = one;
+}
+
+// ------------------------------------------------------------------ launchers
+
+namespace {
+int grid_for(uint64_t work, int threads) {
+  uint64_t g = (work + threads - 1) / threads;
+  const uint64_t cap = 152ull * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename F>
+qs_status set_smem(F* f, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute");
+  }
+  return QS_OK;
+}
+}  // namespace
+
+qs_status launch_set_basis(State* st, uint64_t J) {
+  QS_CUDA(cudaMemsetAsync(st->data, 0, st->data_bytes, st->stream));
+  if (st->prec == QS_C64) set_one_kernel<float><<<1, 1, 0, st->stream>>>((C2<float>*)st->data, J);
+  else set_one_kernel<double><<<1, 1, 0, st->stream>>>((C2<double>*)st->data, J);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_tile_pass(State* st, const void* pass_dev, const void* stages_dev,
+                           const void* ops_dev, int /*n_stages*/) {
+  const uint64_t tiles = 1ull << (st->n - kTileBits);
+  if (st->prec == QS_C64) {
+    const size_t smem = sizeof(C2<float>) << kTileBits;
+    tile_pass_kernel<float><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
+        (C2<float>*)st->data, (const TilePass*)pass_dev, (const TileStage*)stages_dev,
+        (const TileOp<float>*)ops_dev);
+  } else {
+    const size_t smem = sizeof(C2<double>) << kTileBits;
+    qs_status s = set_smem(tile_pass_kernel<double>, smem);
+    if (s != QS_OK) return s;
+    tile_pass_kernel<double><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
+        (C2<double>*)st->data, (const TilePass*)pass_dev, (const TileStage*)stages_dev,
+        (const TileOp<double>*)ops_dev);
+  }
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+template <typename R>
+static qs_status plain_launch_t(State* st, const PlainOp<R>& op) {
+  const int n = st->n;
+  C2<R>* psi = (C2<R>*)st->data;
+  if (op.type == F_G1 || op.type == F_G1C)
+    plain_g1_kernel<R><<<grid_for(1ull << (n - 1), 256), 256, 0, st->stream>>>(psi, n, op);
+  else if (op.type == F_D)
+    plain_diag_kernel<R><<<grid_for(1ull << n, 256), 256, 0, st->stream>>>(psi, n, op);
+  else
+    plain_g2_kernel<R><<<grid_for(1ull << (n - 2), 256), 256, 0, st->stream>>>(psi, n, op);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_plain_op(State* st, const void* op_host, int /*type*/) {
+  if (st->prec == QS_C64) return plain_launch_t<float>(st, *(const PlainOp<float>*)op_host);
+  return plain_launch_t<double>(st, *(const PlainOp<double>*)op_host);
+}
+
+qs_status launch_small(State* st, const void* ops_dev, int nops) {
+  const size_t smem = st->amp_bytes << st->n;
+  if (st->prec == QS_C64) {
+    qs_status s = set_smem(small_state_kernel<float>, smem);
+    if (s != QS_OK) return s;
+    small_state_kernel<float><<<1, 256, smem, st->stream>>>((C2<float>*)st->data, st->n,
+                                                            (const PlainOp<float>*)ops_dev, nops);
+  } else {
+    qs_status s = set_smem(small_state_kernel<double>, smem);
+    if (s != QS_OK) return s;
+    small_state_kernel<double><<<1, 256, smem, st->stream>>>((C2<double>*)st->data, st->n,
+                                                             (const PlainOp<double>*)ops_dev, nops);
+  }
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_remap(State* st, const void* desc_dev, void* /*tmp*/) {
+  const uint64_t tiles = 1ull << (st->n - kTileBits);
+  if (st->prec == QS_C64) {
+    remap_kernel<float><<<(unsigned)tiles, kTileThreads, sizeof(C2<float>) << kTileBits, st->stream>>>(
+        (C2<float>*)st->data, (const RemapDesc*)desc_dev);
+  } else {
+    const size_t smem = sizeof(C2<double>) << kTileBits;
+    qs_status s = set_smem(remap_kernel<double>, smem);
+    if (s != QS_OK) return s;
+    remap_kernel<double><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
+        (C2<double>*)st->data, (const RemapDesc*)desc_dev);
+  }
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_probs(State* st, void* out, int out_fp64, uint64_t mask, double* partials,
+                       uint8_t* dbits, double* marg_acc) {
+  const uint64_t N = 1ull << st->n;
+  const uint64_t full = (st->n >= 64) ? ~0ull : ((1ull << st->n) - 1);
+  const bool marginal = mask != 0 && (mask & full) != full;
+  if (!marginal) {
+    if (st->prec == QS_C64 && !out_fp64 && st->n >= 1) {
+      probs_kernel_f32x2<<<kReduceBlocks, 256, 0, st->stream>>>((const float4*)st->data,
+                                                                (float2*)out, N / 2, partials);
+    } else if (st->prec == QS_C64) {
+      probs_kernel<float, double><<<kReduceBlocks, 256, 0, st->stream>>>(
+          (const C2<float>*)st->data, (double*)out, N, partials);
+    } else if (out_fp64) {
+      probs_kernel<double, double><<<kReduceBlocks, 256, 0, st->stream>>>(
+          (const C2<double>*)st->data, (double*)out, N, partials);
+    } else {
+      probs_kernel<double, float><<<kReduceBlocks, 256, 0, st->stream>>>(
+          (const C2<double>*)st->data, (float*)out, N, partials);
+    }
+    QS_CUDA(cudaGetLastError());
+    return QS_OK;
+  }
+  // marginal over the bits of mask
+  uint8_t hbits[64];
+  int k = 0;
+  for (int b = 0; b < st->n; ++b)
+    if ((mask >> b) & 1) hbits[k++] = (uint8_t)b;
+  QS_CUDA(cudaMemcpyAsync(dbits, hbits, 64, cudaMemcpyHostToDevice, st->stream));
+  const uint64_t H = 1ull << k;
+  QS_CUDA(cudaMemsetAsync(marg_acc, 0, H * sizeof(double), st->stream));
+  const size_t smem = k <= 12 ? (sizeof(double) << k) : 0;
+  if (st->prec == QS_C64)
+    marginal_kernel<float><<<kReduceBlocks, 256, smem, st->stream>>>((const C2<float>*)st->data, N,
+                                                                     dbits, k, marg_acc, partials);
+  else
+    marginal_kernel<double><<<kReduceBlocks, 256, smem, st->stream>>>((const C2<double>*)st->data,
+                                                                      N, dbits, k, marg_acc, partials);
+  QS_CUDA(cudaGetLastError());
+  if (out) {
+    if (out_fp64)
+      QS_CUDA(cudaMemcpyAsync(out, marg_acc, H * sizeof(double), cudaMemcpyDeviceToDevice, st->stream));
+    else {
+      convert_kernel<float><<<grid_for(H, 256), 256, 0, st->stream>>>(marg_acc, (float*)out, H);
+      QS_CUDA(cudaGetLastError());
+    }
+  }
+  return QS_OK;
+}
+
+qs_status launch_reduce_partials(State* st, const double* partials, int count, double* out) {
+  reduce_partials_kernel<<<1, 1024, 0, st->stream>>>(partials, count, out);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_loglik(State* st, const uint32_t* counts, double* partials,
+                        unsigned long long* clamps) {
+  const uint64_t N = 1ull << st->n;
+  QS_CUDA(cudaMemsetAsync(clamps, 0, sizeof(unsigned long long), st->stream));
+  if (st->prec == QS_C64)
+    loglik_kernel<float><<<kReduceBlocks, 256, 0, st->stream>>>((const C2<float>*)st->data, counts, N,
+                                                                partials, clamps);
+  else
+    loglik_kernel<double><<<kReduceBlocks, 256, 0, st->stream>>>((const C2<double>*)st->data, counts,
+                                                                 N, partials, clamps);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+}  // namespace qs
