@@ -186,7 +186,11 @@ enum {
  * bit b), initial rho = |0...0><0...0|, measurement E_J = |J><J|. */
 typedef struct {
   int32_t n_circuits;
-  int32_t max_qubits;      /* <= 6 */
+  int32_t max_qubits;      /* >= every nq[c], <= 6 (sizes shared memory and scratch) */
+  int32_t max_ops;         /* >= every op_off[c+1]-op_off[c] (sizes gradient checkpoints) */
+  int32_t n_ptm1;          /* entries in ptm1 (aux of QS_DM_PTM1 must be below) */
+  int32_t n_ptm2;          /* entries in ptm2 */
+  int32_t reserved;
   const int32_t* nq;       /* [C] 1..6 */
   const int64_t* op_off;   /* [C+1] rows of ops for circuit c: op_off[c]..op_off[c+1] */
   const int32_t* ops;      /* [rows*4] (code, q0, q1, aux) */
@@ -200,7 +204,12 @@ typedef struct {
 /* Forward (and optionally adjoint) pass of a batch.  probs (DEVICE, float,
  * out_off[C] values, may be NULL); loglik (DEVICE, double [C], may be NULL;
  * needs counts); grad (DEVICE, double [C*4] = d loglik / d(theta_x, theta_y,
- * p, gamma), may be NULL; needs counts).  Asynchronous on stream. */
+ * p, gamma), may be NULL; needs counts).  Asynchronous on stream.
+ * Probabilities p_J <= 0 met with n_J > 0 are clamped to 1e-300.
+ * A circuit whose nq, length, op code, qubit or PTM index is out of range is
+ * skipped and its outputs are set to NaN (checked on the device; the call
+ * still returns QS_OK).  The gradient uses device scratch for checkpoints
+ * (stream-ordered cudaMallocAsync/cudaFreeAsync inside the call). */
 qs_status dm_apply_channels(const qs_dm_batch* batch, float* probs, double* loglik, double* grad,
                             void* stream);
 

@@ -61,6 +61,8 @@ class _Allocator(ctypes.Structure):
 
 class DMBatch(ctypes.Structure):
     _fields_ = [("n_circuits", ctypes.c_int32), ("max_qubits", ctypes.c_int32),
+                ("max_ops", ctypes.c_int32), ("n_ptm1", ctypes.c_int32),
+                ("n_ptm2", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("nq", ctypes.c_void_p), ("op_off", ctypes.c_void_p), ("ops", ctypes.c_void_p),
                 ("params", ctypes.c_void_p), ("out_off", ctypes.c_void_p),
                 ("counts", ctypes.c_void_p), ("ptm1", ctypes.c_void_p), ("ptm2", ctypes.c_void_p)]
@@ -298,22 +300,57 @@ def sv_grad(st: State, gates, weights, mode: int = 0, checkpoint_every: int = 0)
 
 # ---------------------------------------------------------------- density matrices
 def dm_apply_channels(nq, op_off, ops, params, out_off, counts=None, ptm1=None, ptm2=None,
-                      probs=None, loglik=None, grad=None, stream=None):
-    """All arrays are torch device tensors (see qs_dm_batch in include/qsim.h)."""
+                      probs=None, loglik=None, grad=None, max_qubits=6, max_ops=None, stream=None):
+    """All arrays are torch device tensors (see qs_dm_batch in include/qsim.h).
+
+    ops: int32 [rows, 4] (code, q0, q1, aux).  max_ops defaults to the longest
+    circuit (computed from op_off on the host)."""
     b = DMBatch()
     b.n_circuits = int(nq.numel())
-    b.max_qubits = 6
-    b.nq = nq.data_ptr()
-    b.op_off = op_off.data_ptr()
-    b.ops = ops.data_ptr()
-    b.params = params.data_ptr()
-    b.out_off = out_off.data_ptr()
-    b.counts = counts.data_ptr() if counts is not None else None
-    b.ptm1 = ptm1.data_ptr() if ptm1 is not None else None
-    b.ptm2 = ptm2.data_ptr() if ptm2 is not None else None
+    b.max_qubits = int(max_qubits)
+    if max_ops is None:
+        oo = op_off.cpu().numpy() if hasattr(op_off, "cpu") else np.asarray(op_off)
+        max_ops = int(np.max(np.diff(oo))) if len(oo) > 1 else 0
+    b.max_ops = int(max_ops)
+    b.n_ptm1 = int(ptm1.shape[0]) if ptm1 is not None else 0
+    b.n_ptm2 = int(ptm2.shape[0]) if ptm2 is not None else 0
     ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
+    b.nq, b.op_off, b.ops, b.params, b.out_off = (ptr(nq), ptr(op_off), ptr(ops), ptr(params),
+                                                   ptr(out_off))
+    b.counts, b.ptm1, b.ptm2 = ptr(counts), ptr(ptm1), ptr(ptm2)
     _check(load().dm_apply_channels(ctypes.byref(b), ptr(probs), ptr(loglik), ptr(grad),
                                     _stream_ptr(stream)))
+
+
+class NoisyBatchDevice:
+    """Device copy of a ``workloads.NoisyBatch`` (inputs resident in HBM)."""
+
+    def __init__(self, batch, counts=True):
+        torch = _torch()
+        dev = "cuda"
+        self.size = batch.size
+        self.nq = torch.tensor(batch.nq.astype(np.int32), device=dev)
+        self.op_off = torch.tensor(batch.op_off.astype(np.int64), device=dev)
+        ops4 = np.full((batch.ops.shape[0], 4), 0, dtype=np.int32)
+        ops4[:, :3] = batch.ops
+        self.ops = torch.tensor(ops4, device=dev)
+        self.params = torch.tensor(batch.params.astype(np.float64), device=dev)
+        self.out_off = torch.tensor(batch.cnt_off.astype(np.int64), device=dev)
+        self.counts = (torch.tensor(batch.counts.astype(np.int32), device=dev)
+                       if counts and batch.counts is not None else None)
+        self.max_qubits = int(batch.nq.max()) if batch.size else 1
+        self.max_ops = int(np.max(np.diff(batch.op_off))) if batch.size else 0
+        self.n_out = int(batch.cnt_off[-1])
+
+    def run(self, probs=True, loglik=True, grad=False, stream=None):
+        torch = _torch()
+        p = torch.empty(self.n_out, dtype=torch.float32, device="cuda") if probs else None
+        ll = torch.empty(self.size, dtype=torch.float64, device="cuda") if loglik else None
+        g = torch.empty((self.size, 4), dtype=torch.float64, device="cuda") if grad else None
+        dm_apply_channels(self.nq, self.op_off, self.ops, self.params, self.out_off,
+                          counts=self.counts, probs=p, loglik=ll, grad=g,
+                          max_qubits=self.max_qubits, max_ops=self.max_ops, stream=stream)
+        return p, ll, g
 
 
 def version() -> str:

@@ -1,0 +1,566 @@
+// Batched density matrices in the Pauli basis (Pauli transfer matrices).
+//
+// A circuit's state is its Pauli vector r_i = Tr(P^_i rho), P^_i = P_i/sqrt(N)
+// (Eq. (GSTVectorizedRho)), 4^n reals kept in one CTA's shared memory.  An op
+// is a PTM acting on the base-4 digit(s) of its qubit(s); composition of maps
+// is the product of their PTMs (section "Quantum operations").  Outcome
+// probabilities p_J = <<E_J| r>> (Eq. (GSTBornRuleVectorized)): for
+// E_J = |J><J| only the {I,Z}^n entries contribute, with sign
+// (-1)^{|S & J|}, i.e. p = 2^{-n/2} WHT(r restricted to {I,Z}^n).
+//
+// PTMs of the gate set, each from G_ij = Tr(P_i E(P_j)) / 2 worked out by hand
+// (rows/columns ordered I, x, y, z):
+//   R^x(t): y -> cos t y + sin t z,  z -> cos t z - sin t y   (Eq. (singlequbitrotationx))
+//   R^y(t): z -> cos t z + sin t x,  x -> cos t x - sin t z   (Eq. (singlequbitrotationy))
+//   depolarizing, p_x = p_y = p_z = p/3 (Eq. (singletDepolarizingChannel)):
+//                     diag(1, f, f, f), f = 1 - 4p/3
+//   amplitude damping, decay parameter 1, rate g (Eqs. (singletAmplitudeDampingChannel1-2)):
+//                     I -> I + g z, x -> s x, y -> s y, z -> (1-g) z, s = sqrt(1-g)
+//   CZ: a signed permutation of the 16 two-qubit Paulis (computed on the host
+//       from the trace formula).
+// The noise channel after an op is C = AD(g) DEP(p) on each touched qubit.
+//
+// Gradient of l = sum_J n_J log p_J by an adjoint sweep: lambda_L = dl/dr =
+// 2^{-n/2} WHT(n/p) on {I,Z}^n; backwards, each sub-op contributes
+// <lambda, dG r_before> and lambda <- G^T lambda.  States before each op are
+// recomputed from checkpoints stored every K ops (K ~ sqrt(L)).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "internal.h"
+
+namespace qs {
+
+namespace {
+
+constexpr int kDmThreads = 128;
+constexpr int kDmMaxQ = 6;
+
+struct DmArgs {
+  int n_circuits, max_q, max_ops, K, nseg, n_ptm1, n_ptm2;
+  const int32_t* nq;
+  const int64_t* op_off;
+  const int32_t* ops;
+  const double* params;
+  const int64_t* out_off;
+  const int32_t* counts;
+  const double* ptm1;
+  const double* ptm2;
+  float* probs;
+  double* loglik;
+  double* grad;
+  float* scratch;              // per CTA: (nseg + K) * 4^max_q floats
+  int* work;                   // work counter (zeroed before launch)
+  int8_t cz_dst[16];
+  int8_t cz_sgn[16];
+};
+
+// tables in shared memory (16 floats each)
+enum {
+  TB_GX = 0, TB_GY, TB_C,                     // forward PTMs
+  TB_GX_T, TB_GX_P, TB_GX_G,                  // d GX / d(theta_x, p, gamma)
+  TB_GY_T, TB_GY_P, TB_GY_G,                  // d GY / d(theta_y, p, gamma)
+  TB_C_P, TB_C_G,                             // d C / d(p, gamma)
+  TB_COUNT
+};
+
+struct SubOp {
+  int kind;      // 0: 4x4 table on q; 1: CZ permutation on (a, b); 2: user 4x4; 3: user 16x16
+  int q, b;      // qubits
+  int table;     // TB_* (kind 0) or user index (kind 2, 3)
+  int dtab[4];   // derivative tables per parameter (theta_x, theta_y, p, gamma) or -1
+};
+
+__device__ __forceinline__ int op_subops(const int32_t* op, int n, SubOp* s) {
+  const int code = op[0], a = op[1], b = op[2], aux = op[3];
+  auto t4 = [](SubOp& x, int q, int tab, int d0, int d1, int d2, int d3) {
+    x.kind = 0; x.q = q; x.b = -1; x.table = tab;
+    x.dtab[0] = d0; x.dtab[1] = d1; x.dtab[2] = d2; x.dtab[3] = d3;
+  };
+  switch (code) {
+    case QS_DM_X90: t4(s[0], a, TB_GX, TB_GX_T, -1, TB_GX_P, TB_GX_G); return 1;
+    case QS_DM_Y90: t4(s[0], a, TB_GY, -1, TB_GY_T, TB_GY_P, TB_GY_G); return 1;
+    case QS_DM_CZ:
+      s[0].kind = 1; s[0].q = a; s[0].b = b; s[0].table = -1;
+      s[0].dtab[0] = s[0].dtab[1] = s[0].dtab[2] = s[0].dtab[3] = -1;
+      t4(s[1], a, TB_C, -1, -1, TB_C_P, TB_C_G);
+      t4(s[2], b, TB_C, -1, -1, TB_C_P, TB_C_G);
+      return 3;
+    case QS_DM_IDLE:
+      for (int q = 0; q < n; ++q) t4(s[q], q, TB_C, -1, -1, TB_C_P, TB_C_G);
+      return n;
+    case QS_DM_PTM1:
+      s[0].kind = 2; s[0].q = a; s[0].b = -1; s[0].table = aux;
+      s[0].dtab[0] = s[0].dtab[1] = s[0].dtab[2] = s[0].dtab[3] = -1;
+      return 1;
+    default:   // QS_DM_PTM2
+      s[0].kind = 3; s[0].q = a; s[0].b = b; s[0].table = aux;
+      s[0].dtab[0] = s[0].dtab[1] = s[0].dtab[2] = s[0].dtab[3] = -1;
+      return 1;
+  }
+}
+
+__device__ bool op_valid(const int32_t* op, int n, const DmArgs& A) {
+  const int code = op[0], a = op[1], b = op[2], aux = op[3];
+  switch (code) {
+    case QS_DM_X90: case QS_DM_Y90: return a >= 0 && a < n;
+    case QS_DM_CZ: return a >= 0 && a < n && b >= 0 && b < n && a != b;
+    case QS_DM_IDLE: return true;
+    case QS_DM_PTM1: return a >= 0 && a < n && aux >= 0 && aux < A.n_ptm1 && A.ptm1 != nullptr;
+    case QS_DM_PTM2:
+      return a >= 0 && a < n && b >= 0 && b < n && a != b && aux >= 0 && aux < A.n_ptm2 &&
+             A.ptm2 != nullptr;
+    default: return false;
+  }
+}
+
+__device__ __forceinline__ int group_base(int g, int q) {
+  // insert a zero base-4 digit at position q
+  const int lo = g & ((1 << (2 * q)) - 1);
+  return ((g >> (2 * q)) << (2 * q + 2)) | lo;
+}
+
+// r <- G r (or G^T r) on digit q; G row-major 4x4 (output digit, input digit)
+__device__ void apply4(float* r, int n, int q, const float* G, bool transpose) {
+  const int groups = 1 << (2 * (n - 1));
+  const int st = 1 << (2 * q);
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+    const int base = group_base(g, q);
+    float x[4], y[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) x[d] = r[base + d * st];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      float acc = 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc = fmaf(transpose ? G[e * 4 + d] : G[d * 4 + e], x[e], acc);
+      y[d] = acc;
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) r[base + d * st] = y[d];
+  }
+}
+
+// sum over elements of lam . (dG r) on digit q (per-thread partial, fp64)
+__device__ double dot4(const float* lam, const float* r, int n, int q, const float* dG) {
+  const int groups = 1 << (2 * (n - 1));
+  const int st = 1 << (2 * q);
+  double acc = 0.0;
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+    const int base = group_base(g, q);
+    float x[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) x[d] = r[base + d * st];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      float y = 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) y = fmaf(dG[d * 4 + e], x[e], y);
+      acc += (double)lam[base + d * st] * (double)y;
+    }
+  }
+  return acc;
+}
+
+__device__ __forceinline__ int group_base2(int g, int lo_q, int hi_q) {
+  return group_base(group_base(g, lo_q), hi_q);
+}
+
+// two-digit ops: local index 4*d_a + d_b
+__device__ void apply_cz(float* r, int n, int a, int b, const DmArgs& A, bool transpose) {
+  const int groups = 1 << (2 * (n - 2));
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  const int sa = 1 << (2 * a), sb = 1 << (2 * b);
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+    const int base = group_base2(g, lo, hi);
+    float x[16], y[16];
+#pragma unroll
+    for (int l = 0; l < 16; ++l) x[l] = r[base + (l >> 2) * sa + (l & 3) * sb];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      // forward: y[dst[j]] = sgn[j] x[j]; transpose: y[j] = sgn[j] x[dst[j]]
+      if (transpose) y[j] = A.cz_sgn[j] * x[A.cz_dst[j]];
+      else y[A.cz_dst[j]] = A.cz_sgn[j] * x[j];
+    }
+#pragma unroll
+    for (int l = 0; l < 16; ++l) r[base + (l >> 2) * sa + (l & 3) * sb] = y[l];
+  }
+}
+
+__device__ void apply16(float* r, int n, int a, int b, const double* G, bool transpose) {
+  const int groups = 1 << (2 * (n - 2));
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  const int sa = 1 << (2 * a), sb = 1 << (2 * b);
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+    const int base = group_base2(g, lo, hi);
+    float x[16];
+    for (int l = 0; l < 16; ++l) x[l] = r[base + (l >> 2) * sa + (l & 3) * sb];
+    for (int d = 0; d < 16; ++d) {
+      float acc = 0.f;
+      for (int e = 0; e < 16; ++e) acc = fmaf((float)(transpose ? G[e * 16 + d] : G[d * 16 + e]), x[e], acc);
+      r[base + (d >> 2) * sa + (d & 3) * sb] = acc;
+    }
+  }
+}
+
+__device__ void apply_sub(float* r, int n, const SubOp& s, const float* tabs, float* user4,
+                          const DmArgs& A, bool transpose) {
+  switch (s.kind) {
+    case 0: apply4(r, n, s.q, tabs + 16 * s.table, transpose); break;
+    case 1: apply_cz(r, n, s.q, s.b, A, transpose); break;
+    case 2: apply4(r, n, s.q, user4, transpose); break;
+    default: apply16(r, n, s.q, s.b, A.ptm2 + 256 * (size_t)s.table, transpose); break;
+  }
+}
+
+__device__ double block_sum_dm(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  __syncthreads();
+  return s;   // valid in every thread
+}
+
+__device__ void build_tables(float* tabs, const double* prm) {
+  // thread 0 only
+  const double tx = prm[0], ty = prm[1], p = prm[2], g = prm[3];
+  const double f = 1.0 - 4.0 * p / 3.0, s = sqrt(1.0 - g);
+  double C[16] = {1, 0, 0, 0, 0, s * f, 0, 0, 0, 0, s * f, 0, g, 0, 0, (1 - g) * f};
+  double Cp[16] = {0, 0, 0, 0, 0, -4.0 * s / 3.0, 0, 0, 0, 0, -4.0 * s / 3.0, 0, 0, 0, 0,
+                   -(1 - g) * 4.0 / 3.0};
+  double Cg[16] = {0, 0, 0, 0, 0, -f / (2 * s), 0, 0, 0, 0, -f / (2 * s), 0, 1, 0, 0, -f};
+  const double cx = cos(tx), sx = sin(tx), cy = cos(ty), sy = sin(ty);
+  double RX[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, cx, -sx, 0, 0, sx, cx};
+  double dRX[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, -sx, -cx, 0, 0, cx, -sx};
+  double RY[16] = {1, 0, 0, 0, 0, cy, 0, sy, 0, 0, 1, 0, 0, -sy, 0, cy};
+  double dRY[16] = {0, 0, 0, 0, 0, -sy, 0, cy, 0, 0, 0, 0, 0, -cy, 0, -sy};
+  auto mul = [](const double* A, const double* B, float* out) {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        double acc = 0;
+        for (int k = 0; k < 4; ++k) acc += A[i * 4 + k] * B[k * 4 + j];
+        out[i * 4 + j] = (float)acc;
+      }
+  };
+  mul(C, RX, tabs + 16 * TB_GX);
+  mul(C, RY, tabs + 16 * TB_GY);
+  for (int i = 0; i < 16; ++i) tabs[16 * TB_C + i] = (float)C[i];
+  mul(C, dRX, tabs + 16 * TB_GX_T);
+  mul(Cp, RX, tabs + 16 * TB_GX_P);
+  mul(Cg, RX, tabs + 16 * TB_GX_G);
+  mul(C, dRY, tabs + 16 * TB_GY_T);
+  mul(Cp, RY, tabs + 16 * TB_GY_P);
+  mul(Cg, RY, tabs + 16 * TB_GY_G);
+  for (int i = 0; i < 16; ++i) {
+    tabs[16 * TB_C_P + i] = (float)Cp[i];
+    tabs[16 * TB_C_G + i] = (float)Cg[i];
+  }
+}
+
+// index of the Pauli string Z_S (digit 3 at the bits of S)
+__device__ __forceinline__ int zs_index(int S, int n) {
+  int idx = 0;
+  for (int b = 0; b < n; ++b)
+    if ((S >> b) & 1) idx |= 3 << (2 * b);
+  return idx;
+}
+
+__device__ void wht(double* z, int N) {
+  for (int h = 1; h < N; h <<= 1) {
+    for (int i = threadIdx.x; i < N / 2; i += blockDim.x) {
+      const int j = ((i & ~(h - 1)) << 1) | (i & (h - 1));
+      const double a = z[j], b = z[j + h];
+      z[j] = a + b;
+      z[j + h] = a - b;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
+  extern __shared__ __align__(16) float dsm[];
+  const int D = 1 << (2 * A.max_q);
+  float* r = dsm;
+  float* lam = dsm + D;
+  float* tmp = dsm + 2 * D;
+  float* tabs = dsm + 3 * D;                 // TB_COUNT * 16
+  float* user4 = tabs + 16 * TB_COUNT;       // 16
+  double* z = (double*)(user4 + 16);         // 64 doubles (8-byte aligned: offsets are multiples of 16 floats)
+  __shared__ double red[kDmThreads / 32];
+  __shared__ int s_c, s_ok;
+  const bool want_grad = A.grad != nullptr && A.counts != nullptr;
+  float* my_scratch = A.scratch ? A.scratch + (size_t)blockIdx.x * (size_t)(A.nseg + A.K) * D : nullptr;
+  float* ckpt = my_scratch;
+  float* segbuf = my_scratch ? my_scratch + (size_t)A.nseg * D : nullptr;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_c = atomicAdd(A.work, 1);
+    __syncthreads();
+    const int c = s_c;
+    __syncthreads();
+    if (c >= A.n_circuits) break;
+    const int n = A.nq[c];
+    const int64_t o0 = A.op_off[c];
+    const int L = (int)(A.op_off[c + 1] - o0);
+    const int32_t* ops = A.ops + 4 * o0;
+    const int64_t out0 = A.out_off[c];
+    const int N = 1 << n;
+    // validation (device side: the arrays are caller-supplied device memory)
+    if (threadIdx.x == 0) {
+      int ok = (n >= 1 && n <= A.max_q && L >= 0 && L <= A.max_ops && A.out_off[c + 1] - out0 == N);
+      for (int k = 0; ok && k < L; ++k) ok = op_valid(ops + 4 * k, n, A);
+      s_ok = ok;
+      if (ok) build_tables(tabs, A.params + 4 * c);
+    }
+    __syncthreads();
+    if (!s_ok) {
+      const float nanf_ = __int_as_float(0x7fc00000);
+      if (threadIdx.x == 0) {
+        if (A.loglik) A.loglik[c] = __longlong_as_double(0x7ff8000000000000ll);
+        if (A.grad)
+          for (int k = 0; k < 4; ++k) A.grad[4 * c + k] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      if (A.probs && n >= 1 && n <= kDmMaxQ && A.out_off[c + 1] - out0 == N)
+        for (int J = threadIdx.x; J < N; J += blockDim.x) A.probs[out0 + J] = nanf_;
+      continue;
+    }
+    const int Dn = 1 << (2 * n);
+    const float amp0 = 1.0f / sqrtf((float)N);
+    // rho_0 = |0..0><0..0|: r_i = 2^{-n/2} on {I,Z}^n, 0 elsewhere
+    for (int i = threadIdx.x; i < Dn; i += blockDim.x) {
+      bool iz = true;
+      for (int b = 0; b < n; ++b) {
+        const int d = (i >> (2 * b)) & 3;
+        iz = iz && (d == 0 || d == 3);
+      }
+      r[i] = iz ? amp0 : 0.f;
+    }
+    __syncthreads();
+    // ---------------- forward
+    for (int k = 0; k < L; ++k) {
+      if (want_grad && (k % A.K) == 0) {
+        float* dst = ckpt + (size_t)(k / A.K) * D;
+        for (int i = threadIdx.x; i < Dn; i += blockDim.x) dst[i] = r[i];
+        __syncthreads();   // copies done before r is updated in place
+      }
+      const int32_t* op = ops + 4 * k;
+      if (op[0] == QS_DM_PTM1) {
+        if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
+        __syncthreads();
+      }
+      SubOp so[kDmMaxQ];
+      const int ns = op_subops(op, n, so);
+      for (int j = 0; j < ns; ++j) {
+        apply_sub(r, n, so[j], tabs, user4, A, false);
+        __syncthreads();
+      }
+    }
+    // ---------------- probabilities: p = 2^{-n/2} WHT(r on {I,Z}^n)
+    for (int S = threadIdx.x; S < N; S += blockDim.x) z[S] = (double)r[zs_index(S, n)];
+    __syncthreads();
+    wht(z, N);
+    const double scale = 1.0 / sqrt((double)N);
+    double ll = 0.0;
+    for (int J = threadIdx.x; J < N; J += blockDim.x) {
+      double p = z[J] * scale;
+      if (A.probs) A.probs[out0 + J] = (float)p;
+      if (A.counts) {
+        const int cnt = A.counts[out0 + J];
+        if (!(p > 0.0)) p = 1e-300;
+        if (cnt > 0) ll += (double)cnt * log(p);
+        z[J] = cnt > 0 ? (double)cnt / p : 0.0;   // seed weights dl/dp_J
+      }
+    }
+    if (A.counts) {
+      const double tot = block_sum_dm(ll, red);
+      if (threadIdx.x == 0 && A.loglik) A.loglik[c] = tot;
+    }
+    if (!want_grad) {
+      __syncthreads();
+      continue;
+    }
+    // ---------------- adjoint
+    __syncthreads();
+    wht(z, N);
+    for (int i = threadIdx.x; i < Dn; i += blockDim.x) lam[i] = 0.f;
+    __syncthreads();
+    for (int S = threadIdx.x; S < N; S += blockDim.x) lam[zs_index(S, n)] = (float)(z[S] * scale);
+    __syncthreads();
+    double g[4] = {0, 0, 0, 0};
+    const int nseg = (L + A.K - 1) / A.K;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+      const int k0 = sgi * A.K, k1 = min(L, k0 + A.K);
+      // recompute the states before each op of the segment
+      const float* ck = ckpt + (size_t)sgi * D;
+      for (int i = threadIdx.x; i < Dn; i += blockDim.x) r[i] = ck[i];
+      __syncthreads();
+      for (int k = k0; k < k1; ++k) {
+        float* dst = segbuf + (size_t)(k - k0) * D;
+        for (int i = threadIdx.x; i < Dn; i += blockDim.x) dst[i] = r[i];
+        if (k + 1 == k1) break;
+        const int32_t* op = ops + 4 * k;
+        if (op[0] == QS_DM_PTM1) {
+          __syncthreads();
+          if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
+          __syncthreads();
+        }
+        SubOp so[kDmMaxQ];
+        const int ns = op_subops(op, n, so);
+        __syncthreads();
+        for (int j = 0; j < ns; ++j) {
+          apply_sub(r, n, so[j], tabs, user4, A, false);
+          __syncthreads();
+        }
+      }
+      __syncthreads();
+      for (int k = k1 - 1; k >= k0; --k) {
+        const int32_t* op = ops + 4 * k;
+        if (op[0] == QS_DM_PTM1) {
+          if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
+        }
+        SubOp so[kDmMaxQ];
+        const int ns = op_subops(op, n, so);
+        const float* before = segbuf + (size_t)(k - k0) * D;
+        __syncthreads();
+        for (int j = ns - 1; j >= 0; --j) {
+          // tmp = state before sub-op j
+          for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = before[i];
+          __syncthreads();
+          for (int jj = 0; jj < j; ++jj) {
+            apply_sub(tmp, n, so[jj], tabs, user4, A, false);
+            __syncthreads();
+          }
+          if (so[j].kind == 0) {
+            for (int pidx = 0; pidx < 4; ++pidx)
+              if (so[j].dtab[pidx] >= 0) g[pidx] += dot4(lam, tmp, n, so[j].q, tabs + 16 * so[j].dtab[pidx]);
+          }
+          __syncthreads();
+          apply_sub(lam, n, so[j], tabs, user4, A, true);
+          __syncthreads();
+        }
+      }
+    }
+    for (int pidx = 0; pidx < 4; ++pidx) {
+      const double tot = block_sum_dm(g[pidx], red);
+      if (threadIdx.x == 0) A.grad[4 * c + pidx] = tot;
+    }
+    __syncthreads();
+  }
+}
+
+// CZ as a signed permutation of two-qubit Pauli strings, from
+// G_ij = Tr(P_i U P_j U^dagger) / 4 with U = diag(1, 1, 1, -1).
+void cz_table(int8_t* dst, int8_t* sgn) {
+  const cd I(0, 1);
+  const cd P[4][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}, {0, -I, I, 0}, {1, 0, 0, -1}};
+  const double u[4] = {1, 1, 1, -1};
+  auto pauli2 = [&](int idx, cd* M) {   // idx = 4*d_a + d_b, qubit a most significant
+    const cd* A = P[idx >> 2];
+    const cd* B = P[idx & 3];
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) M[r * 4 + c] = A[(r >> 1) * 2 + (c >> 1)] * B[(r & 1) * 2 + (c & 1)];
+  };
+  for (int j = 0; j < 16; ++j) {
+    cd Pj[16], Pi[16], img[16];
+    pauli2(j, Pj);
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) img[r * 4 + c] = u[r] * Pj[r * 4 + c] * u[c];
+    for (int i = 0; i < 16; ++i) {
+      pauli2(i, Pi);
+      cd tr = 0;
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) tr += Pi[r * 4 + c] * img[c * 4 + r];
+      const double v = tr.real() / 4.0;
+      if (std::fabs(v) > 0.5) {
+        dst[j] = (int8_t)i;
+        sgn[j] = (int8_t)(v > 0 ? 1 : -1);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, double* loglik,
+                                       double* grad, void* stream_) {
+  if (!b) {
+    set_error("batch is NULL");
+    return QS_EINVAL;
+  }
+  if (b->n_circuits < 0 || b->max_qubits < 1 || b->max_qubits > kDmMaxQ || b->max_ops < 0) {
+    set_error("bad batch sizes (n_circuits %d, max_qubits %d, max_ops %d)", b->n_circuits,
+              b->max_qubits, b->max_ops);
+    return QS_EINVAL;
+  }
+  if (!b->nq || !b->op_off || !b->params || !b->out_off || (b->max_ops > 0 && !b->ops)) {
+    set_error("batch arrays missing");
+    return QS_EINVAL;
+  }
+  if ((loglik || grad) && !b->counts) {
+    set_error("loglik / grad need counts");
+    return QS_EINVAL;
+  }
+  if (b->n_circuits == 0) return QS_OK;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  DmArgs A{};
+  A.n_circuits = b->n_circuits;
+  A.max_q = b->max_qubits;
+  A.max_ops = b->max_ops;
+  A.K = 1;
+  while (A.K * A.K < b->max_ops) ++A.K;
+  A.nseg = (b->max_ops + A.K - 1) / A.K + 1;
+  A.n_ptm1 = b->n_ptm1;
+  A.n_ptm2 = b->n_ptm2;
+  A.nq = b->nq;
+  A.op_off = b->op_off;
+  A.ops = b->ops;
+  A.params = b->params;
+  A.out_off = b->out_off;
+  A.counts = b->counts;
+  A.ptm1 = b->ptm1;
+  A.ptm2 = b->ptm2;
+  A.probs = probs;
+  A.loglik = loglik;
+  A.grad = grad;
+  cz_table(A.cz_dst, A.cz_sgn);
+
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int D = 1 << (2 * A.max_q);
+  const size_t smem = (size_t)(3 * D + 16 * TB_COUNT + 16) * sizeof(float) + 64 * sizeof(double);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dm_batch_kernel, kDmThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > b->n_circuits) grid = b->n_circuits;
+
+  const size_t scratch_floats = grad ? (size_t)grid * (A.nseg + A.K) * D : 0;
+  const size_t bytes = 256 + scratch_floats * sizeof(float);
+  void* mem = nullptr;
+  cudaError_t e = cudaMallocAsync(&mem, bytes, stream);
+  if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync (dm scratch)");
+  A.work = (int*)mem;
+  A.scratch = grad ? (float*)((char*)mem + 256) : nullptr;
+  e = cudaMemsetAsync(mem, 0, 256, stream);
+  if (e != cudaSuccess) return cuda_status(e, "cudaMemsetAsync");
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(dm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute");
+  }
+  dm_batch_kernel<<<grid, kDmThreads, smem, stream>>>(A);
+  e = cudaGetLastError();
+  cudaFreeAsync(mem, stream);
+  if (e != cudaSuccess) return cuda_status(e, "dm_batch_kernel launch");
+  return QS_OK;
+}

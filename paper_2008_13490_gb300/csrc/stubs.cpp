@@ -10,9 +10,4 @@ qs_status sv_grad(qs_state_t, const qs_gate*, size_t, const double*, int, int, d
   return QS_EUNSUPPORTED;
 }
 
-qs_status dm_apply_channels(const qs_dm_batch*, float*, double*, double*, void*) {
-  set_error("dm_apply_channels not built");
-  return QS_EUNSUPPORTED;
-}
-
 }  // extern "C"

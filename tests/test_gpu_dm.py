@@ -1,0 +1,168 @@
+"""GPU parity of the batched density-matrix / PTM path against the oracle.
+
+The oracle evolves 2^n x 2^n density matrices with Kraus operators (no PTMs),
+so these tests also pin the kernel's PTM tables and Pauli-basis readout.
+
+Tolerances, derived from the fp32 Pauli-vector arithmetic: each op rounds
+every entry once (unit roundoff 6e-8) and the entries are bounded by
+2^{-n/2}, so after L <= 256 ops the outcome probabilities (sums of 2^n
+entries times 2^{-n/2}) carry an absolute error below ~L * 2^n * 6e-8 *
+2^{-n} ~ 2e-5.  The log-likelihood and gradient are accumulated in fp64 from
+fp32 terms: relative 1e-4 on the likelihood, and on the gradient an error
+relative to the l1 size of the summed terms (tested against max(|g|, 1)).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import density as D
+from oracle import gates as G
+from oracle import noisy as NZ
+from oracle import statevector as SV
+
+pytestmark = pytest.mark.gpu
+
+
+def _with_counts(batch, seed):
+    probs, _ = NZ.batch_forward(batch)
+    batch.counts = W.multinomial_counts(probs, 1000, seed=seed)
+    return batch, probs
+
+
+def test_probs_loglik_vs_oracle(qs):
+    batch = W.noisy_batch(count=48, seed=4001, len_range=(1, 60))
+    batch, ref_p = _with_counts(batch, 4002)
+    dev = qs.NoisyBatchDevice(batch)
+    p, ll, _ = dev.run()
+    p = p.cpu().numpy()
+    ll = ll.cpu().numpy()
+    for c in range(batch.size):
+        got = p[batch.cnt_off[c]:batch.cnt_off[c + 1]]
+        np.testing.assert_allclose(got, ref_p[c], atol=2e-5)
+        cnt = batch.counts[batch.cnt_off[c]:batch.cnt_off[c + 1]]
+        assert ll[c] == pytest.approx(NZ.loglik(ref_p[c], cnt), rel=1e-4)
+
+
+def test_long_circuits_trace_and_sampled_parity(qs):
+    # full-length circuits (up to 256 ops): every distribution sums to 1;
+    # a sample of small circuits is checked against the oracle
+    batch = W.noisy_batch(count=256, seed=4003)
+    dev = qs.NoisyBatchDevice(batch, counts=False)
+    p, _, _ = dev.run(loglik=False)
+    p = p.cpu().numpy()
+    for c in range(batch.size):
+        seg = p[batch.cnt_off[c]:batch.cnt_off[c + 1]]
+        assert abs(seg.sum() - 1) < 1e-4 and seg.min() > -1e-5
+    small = [c for c in range(batch.size) if batch.nq[c] <= 3][:10]
+    for c in small:
+        n, ops, params = batch.circuit(c)
+        ref = NZ.circuit_probabilities(n, ops, params)
+        np.testing.assert_allclose(p[batch.cnt_off[c]:batch.cnt_off[c + 1]], ref, atol=2e-5)
+
+
+def test_gradient_vs_oracle_adjoint_and_fd(qs):
+    batch = W.noisy_batch(count=24, seed=4101, n_range=(1, 4), len_range=(1, 40))
+    batch, _ = _with_counts(batch, 4102)
+    dev = qs.NoisyBatchDevice(batch)
+    _, ll, g = dev.run(grad=True)
+    g = g.cpu().numpy()
+    ll = ll.cpu().numpy()
+    for c in range(batch.size):
+        n, ops, params = batch.circuit(c)
+        cnt = batch.counts[batch.cnt_off[c]:batch.cnt_off[c + 1]]
+        L, _, ref = NZ.grad_adjoint(n, ops, params, cnt)
+        fd = NZ.grad_fd(n, ops, params, cnt)
+        np.testing.assert_allclose(ref, fd, rtol=1e-5, atol=1e-3)      # oracle self-consistency
+        scale = np.maximum(np.abs(ref), 1.0)
+        assert np.all(np.abs(g[c] - ref) / scale < 2e-3), (c, g[c], ref)
+        assert ll[c] == pytest.approx(L, rel=1e-4)
+
+
+def test_gradient_long_circuits_use_checkpoints(qs):
+    # L up to 256: sqrt(L) checkpoints and segment recomputation
+    batch = W.noisy_batch(count=6, seed=4201, n_range=(2, 3), len_range=(200, 256))
+    batch, _ = _with_counts(batch, 4202)
+    dev = qs.NoisyBatchDevice(batch)
+    _, _, g = dev.run(grad=True)
+    g = g.cpu().numpy()
+    for c in range(batch.size):
+        n, ops, params = batch.circuit(c)
+        cnt = batch.counts[batch.cnt_off[c]:batch.cnt_off[c + 1]]
+        _, _, ref = NZ.grad_adjoint(n, ops, params, cnt)
+        scale = np.maximum(np.abs(ref), 1.0)
+        assert np.all(np.abs(g[c] - ref) / scale < 5e-3), (c, g[c], ref)
+
+
+def test_user_ptms_match_unitary_evolution(qs):
+    # PTM1 = PTM of H, PTM2 = PTM of CNOT (control = q0), built from the definition
+    H = D.ptm_unitary(G.matrix("H"))
+    CN = D.ptm_unitary(G.CNOT)
+    ptm1 = torch.tensor(H.reshape(1, 16), device="cuda")
+    ptm2 = torch.tensor(CN.reshape(1, 256), device="cuda")
+    n = 3
+    ops = np.array([[4, 2, 0, 0], [5, 2, 1, 0], [5, 1, 0, 0], [4, 0, 0, 0]], dtype=np.int32)
+    nq = torch.tensor([n], dtype=torch.int32, device="cuda")
+    op_off = torch.tensor([0, len(ops)], dtype=torch.int64, device="cuda")
+    out_off = torch.tensor([0, 1 << n], dtype=torch.int64, device="cuda")
+    params = torch.tensor([[1.0, 1.0, 1e-3, 1e-3]], dtype=torch.float64, device="cuda")
+    probs = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+    qs.dm_apply_channels(nq, op_off, torch.tensor(ops, device="cuda"), params, out_off,
+                         ptm1=ptm1, ptm2=ptm2, probs=probs, max_qubits=n)
+    circ = [("H", (2,), (), None), ("CNOT", (2, 1), (), None), ("CNOT", (1, 0), (), None),
+            ("H", (0,), (), None)]
+    ref = SV.probabilities(SV.apply_circuit(SV.basis(n), n, circ))
+    np.testing.assert_allclose(probs.cpu().numpy(), ref, atol=1e-6)
+
+
+def test_invalid_ops_give_nan_and_do_not_disturb_others(qs):
+    batch, _ = _with_counts(W.noisy_batch(count=3, seed=5, n_range=(2, 2), len_range=(3, 3)), 1)
+    good = batch.ops.copy()
+    batch.ops[batch.op_off[1]] = (0, 7, -1)      # qubit 7 on a 2-qubit circuit
+    dev = qs.NoisyBatchDevice(batch)
+    p, ll, _ = dev.run()
+    p = p.cpu().numpy()
+    ll = ll.cpu().numpy()
+    assert np.isnan(ll[1]) and np.all(np.isnan(p[batch.cnt_off[1]:batch.cnt_off[2]]))
+    batch.ops = good
+    for c in (0, 2):
+        n, ops, params = batch.circuit(c)
+        np.testing.assert_allclose(p[batch.cnt_off[c]:batch.cnt_off[c + 1]],
+                                   NZ.circuit_probabilities(n, ops, params), atol=1e-6)
+
+
+def test_empty_and_single_qubit_circuits(qs):
+    batch = W.noisy_batch(count=5, seed=8, n_range=(1, 1), len_range=(1, 5))
+    # make circuit 0 empty
+    lens = np.diff(batch.op_off)
+    lens[0] = 0
+    ops = np.concatenate([batch.ops[batch.op_off[c]:batch.op_off[c] + lens[c]] for c in range(5)])
+    batch.ops = ops
+    batch.op_off = np.concatenate([[0], np.cumsum(lens)])
+    dev = qs.NoisyBatchDevice(batch, counts=False)
+    p, _, _ = dev.run(loglik=False)
+    p = p.cpu().numpy()
+    np.testing.assert_allclose(p[0:2], [1, 0], atol=1e-7)
+    for c in range(1, 5):
+        n, o, params = batch.circuit(c)
+        np.testing.assert_allclose(p[batch.cnt_off[c]:batch.cnt_off[c + 1]],
+                                   NZ.circuit_probabilities(n, o, params), atol=1e-6)
+
+
+def test_full_batch_4096_properties(qs):
+    batch = W.noisy_batch(count=4096, seed=4001)
+    batch.counts = W.synthetic_counts(batch, 1000, seed=4002)
+    dev = qs.NoisyBatchDevice(batch)
+    p, ll, g = dev.run(grad=True)
+    p = p.cpu().numpy()
+    sums = np.add.reduceat(p, batch.cnt_off[:-1])
+    assert np.all(np.abs(sums - 1) < 1e-4)
+    assert np.all(np.isfinite(ll.cpu().numpy())) and np.all(np.isfinite(g.cpu().numpy()))
+    # sampled circuits against the oracle
+    rng = np.random.default_rng(0)
+    for c in rng.choice(np.where(batch.nq <= 2)[0], size=6, replace=False):
+        n, ops, params = batch.circuit(int(c))
+        np.testing.assert_allclose(p[batch.cnt_off[c]:batch.cnt_off[c + 1]],
+                                   NZ.circuit_probabilities(n, ops, params), atol=2e-5)
