@@ -253,11 +253,37 @@ qs_status check_state(qs_state_t st) {
 
 }  // namespace
 
+qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats) {
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (method != QS_METHOD_TILED && method != QS_METHOD_PLAIN) {
+    set_error("unknown method %d", method);
+    return QS_EINVAL;
+  }
+  if (ngates == 0) return QS_OK;
+  std::vector<FOp> fops;
+  std::vector<int> vmap;
+  const bool c64 = st->prec == QS_C64;
+  qs_status s;
+  if (method == QS_METHOD_PLAIN) {
+    build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/false, /*relabel=*/false);
+    s = c64 ? run_plain<float>(st, fops, stats) : run_plain<double>(st, fops, stats);
+  } else if (st->n < kTileBits) {
+    build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/false);
+    s = c64 ? run_small<float>(st, fops, stats) : run_small<double>(st, fops, stats);
+  } else {
+    build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/true);
+    s = c64 ? run_tiled<float>(st, fops, vmap, stats) : run_tiled<double>(st, fops, vmap, stats);
+  }
+  if (stats) {
+    stats->gates_in = (int64_t)ngates;
+    stats->bytes_moved = (double)stats->passes * 2.0 * (double)st->data_bytes;
+  }
+  return s;
+}
+
 }  // namespace qs
 
 using namespace qs;
-
-struct qs_state_s : public State {};
 
 extern "C" {
 
@@ -398,31 +424,7 @@ qs_status sv_apply_circuit(qs_state_t st, const qs_gate* gates, size_t ngates, c
   if (s != QS_OK) return s;
   s = validate_gates(gates, ngates, st->n);
   if (s != QS_OK) return s;
-  if (stats) std::memset(stats, 0, sizeof(*stats));
-  const int method = opts ? opts->method : QS_METHOD_TILED;
-  if (method != QS_METHOD_TILED && method != QS_METHOD_PLAIN) {
-    set_error("unknown method %d", method);
-    return QS_EINVAL;
-  }
-  if (ngates == 0) return QS_OK;
-  std::vector<FOp> fops;
-  std::vector<int> vmap;
-  const bool c64 = st->prec == QS_C64;
-  if (method == QS_METHOD_PLAIN) {
-    build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/false, /*relabel=*/false);
-    s = c64 ? run_plain<float>(st, fops, stats) : run_plain<double>(st, fops, stats);
-  } else if (st->n < kTileBits) {
-    build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/false);
-    s = c64 ? run_small<float>(st, fops, stats) : run_small<double>(st, fops, stats);
-  } else {
-    build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/true);
-    s = c64 ? run_tiled<float>(st, fops, vmap, stats) : run_tiled<double>(st, fops, vmap, stats);
-  }
-  if (stats) {
-    stats->gates_in = (int64_t)ngates;
-    stats->bytes_moved = (double)stats->passes * 2.0 * (double)st->data_bytes;
-  }
-  return s;
+  return apply_gates(st, gates, ngates, opts ? opts->method : QS_METHOD_TILED, stats);
 }
 
 qs_status sv_probs(qs_state_t st, void* out, int out_fp64, uint64_t marg_mask, double* norm_out) {

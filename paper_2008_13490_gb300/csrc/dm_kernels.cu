@@ -388,9 +388,14 @@ __global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
     // ---------------- adjoint
     __syncthreads();
     wht(z, N);
+    // lambda is linear in the seed: keep it in fp32 as lambda / lmax (no
+    // overflow when some n_J / p_J is huge) and scale the fp64 sums back
+    double lmax = 0.0;
+    for (int S = 0; S < N; ++S) lmax = fmax(lmax, fabs(z[S]));
+    const double lscale = lmax > 0.0 ? scale / lmax : 0.0;
     for (int i = threadIdx.x; i < Dn; i += blockDim.x) lam[i] = 0.f;
     __syncthreads();
-    for (int S = threadIdx.x; S < N; S += blockDim.x) lam[zs_index(S, n)] = (float)(z[S] * scale);
+    for (int S = threadIdx.x; S < N; S += blockDim.x) lam[zs_index(S, n)] = (float)(z[S] * lscale);
     __syncthreads();
     double g[4] = {0, 0, 0, 0};
     const int nseg = (L + A.K - 1) / A.K;
@@ -448,7 +453,7 @@ __global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
     }
     for (int pidx = 0; pidx < 4; ++pidx) {
       const double tot = block_sum_dm(g[pidx], red);
-      if (threadIdx.x == 0) A.grad[4 * c + pidx] = tot;
+      if (threadIdx.x == 0) A.grad[4 * c + pidx] = tot * lmax;
     }
     __syncthreads();
   }
@@ -539,6 +544,11 @@ extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, doubl
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int D = 1 << (2 * A.max_q);
   const size_t smem = (size_t)(3 * D + 16 * TB_COUNT + 16) * sizeof(float) + 64 * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t ea =
+        cudaFuncSetAttribute(dm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ea != cudaSuccess) return cuda_status(ea, "cudaFuncSetAttribute");
+  }
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dm_batch_kernel, kDmThreads, smem);
   if (per_sm < 1) per_sm = 1;
@@ -554,10 +564,6 @@ extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, doubl
   A.scratch = grad ? (float*)((char*)mem + 256) : nullptr;
   e = cudaMemsetAsync(mem, 0, 256, stream);
   if (e != cudaSuccess) return cuda_status(e, "cudaMemsetAsync");
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(dm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute");
-  }
   dm_batch_kernel<<<grid, kDmThreads, smem, stream>>>(A);
   e = cudaGetLastError();
   cudaFreeAsync(mem, stream);

@@ -1,0 +1,345 @@
+// Adjoint gradient of a probability functional of the final state.
+//
+// L(p) with p_J = |psi_J|^2 and psi = U_G ... U_1 psi_0.  With
+// lambda = dL/dpsi^* = (dL/dp_J) psi_J at the end, the derivative with
+// respect to an angle t of gate g is
+//     dL/dt = 2 Re <lambda_g | dU_g/dt | psi_{g-1}>,
+// where lambda_g = U_{g+1}^dagger ... U_G^dagger lambda and psi_{g-1} the
+// state before gate g.  The sweep runs backwards over the gates; one fused
+// kernel per gate computes psi_{g-1} = U_g^dagger psi_g, the derivative terms
+// (fp64 block partials) and lambda_{g-1} = U_g^dagger lambda_g.
+// Rotation derivatives follow from R(t) = exp(-i t sigma/2)
+// (Eqs. (singlequbitrotationx)-(singlequbitrotationz)): dR/dt = -i/2 sigma R.
+//
+// States before each gate come either from uncomputing (psi <- U^dagger psi)
+// or, for deep circuits, from checkpoints stored every K gates in the forward
+// pass and recomputed forward segment by segment.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "internal.h"
+
+namespace qs {
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ C2<R> cmac(C2<R> acc, C2<R> m, C2<R> a) {
+  acc.x = fma(m.x, a.x, acc.x);
+  acc.x = fma(-m.y, a.y, acc.x);
+  acc.y = fma(m.x, a.y, acc.y);
+  acc.y = fma(m.y, a.x, acc.y);
+  return acc;
+}
+
+struct GradGate {
+  int k;            // 1 or 2 qubits
+  int q0, q1;       // q0 most significant of the local index
+  int np;           // number of parameters
+  double ud[32];    // U^dagger, complex row-major (k=1: 2x2 in the first 8)
+  double du[3][32]; // dU/dt_p
+};
+
+template <typename R>
+__device__ __forceinline__ C2<R> ld(const double* m, int i) {
+  C2<R> r;
+  r.x = (R)m[2 * i];
+  r.y = (R)m[2 * i + 1];
+  return r;
+}
+
+__device__ double block_sum_g(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+__device__ __forceinline__ uint64_t ins0(uint64_t i, int b) {
+  const uint64_t m = (1ull << b) - 1ull;
+  return ((i & ~m) << 1) | (i & m);
+}
+
+// one backward step: psi <- U^dagger psi, terms, lam <- U^dagger lam
+template <typename R>
+__global__ void __launch_bounds__(256)
+    adjoint_step_kernel(C2<R>* __restrict__ psi, C2<R>* __restrict__ lam, int n, GradGate g,
+                        double* __restrict__ partials, int psi_is_before) {
+  __shared__ double red[8];
+  double acc[3] = {0, 0, 0};
+  const int d = 1 << g.k;
+  const uint64_t groups = 1ull << (n - g.k);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const int lo = g.k == 2 ? min(g.q0, g.q1) : g.q0, hi = g.k == 2 ? max(g.q0, g.q1) : g.q0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < groups; i += stride) {
+    uint64_t base = ins0(i, lo);
+    if (g.k == 2) base = ins0(base, hi);
+    uint64_t idx[4];
+    C2<R> x[4], l[4], y[4], m[4];
+    for (int a = 0; a < d; ++a) {
+      idx[a] = base;
+      if (g.k == 1) idx[a] |= (uint64_t)a << g.q0;
+      else idx[a] |= ((uint64_t)(a >> 1) << g.q0) | ((uint64_t)(a & 1) << g.q1);
+      x[a] = psi[idx[a]];
+      l[a] = lam[idx[a]];
+    }
+    // y = state before the gate (given, or U^dagger x), m = U^dagger l
+    for (int r = 0; r < d; ++r) {
+      C2<R> s{R(0), R(0)}, t{R(0), R(0)};
+      for (int c = 0; c < d; ++c) {
+        const C2<R> u = ld<R>(g.ud, r * d + c);
+        s = cmac(s, u, x[c]);
+        t = cmac(t, u, l[c]);
+      }
+      y[r] = psi_is_before ? x[r] : s;
+      m[r] = t;
+    }
+    for (int p = 0; p < g.np; ++p) {
+      double a2 = 0.0;
+      for (int r = 0; r < d; ++r) {
+        C2<R> s{R(0), R(0)};
+        for (int c = 0; c < d; ++c) s = cmac(s, ld<R>(g.du[p], r * d + c), y[c]);
+        // Re(conj(l_r) s)
+        a2 += (double)l[r].x * (double)s.x + (double)l[r].y * (double)s.y;
+      }
+      acc[p] += a2;
+    }
+    for (int a = 0; a < d; ++a) {
+      if (!psi_is_before) psi[idx[a]] = y[a];
+      lam[idx[a]] = m[a];
+    }
+  }
+  for (int p = 0; p < 3; ++p) {
+    const double s = block_sum_g(acc[p], red);
+    if (threadIdx.x == 0) partials[3 * blockIdx.x + p] = s;
+  }
+}
+
+__global__ void sum_partials3_kernel(const double* __restrict__ partials, int blocks,
+                                     double* __restrict__ out) {
+  __shared__ double red[32];
+  for (int p = 0; p < 3; ++p) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < blocks; i += blockDim.x) s += partials[3 * i + p];
+    s = block_sum_g(s, red);
+    if (threadIdx.x == 0) out[p] = 2.0 * s;
+  }
+}
+
+// lambda = (dL/dp_J) psi_J and the loss partials
+template <typename R>
+__global__ void __launch_bounds__(256)
+    seed_kernel(const C2<R>* __restrict__ psi, C2<R>* __restrict__ lam, const double* __restrict__ w,
+                int mode, uint64_t N, double* __restrict__ partials) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t J = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; J < N; J += stride) {
+    const C2<R> a = psi[J];
+    double p = (double)a.x * a.x + (double)a.y * a.y;
+    double dl;
+    if (mode == 0) {
+      dl = w[J];
+      acc += w[J] * p;
+    } else {
+      const double c = w[J];
+      if (c > 0) {
+        if (!(p > 0.0)) p = 1e-300;
+        acc += c * log(p);
+        dl = c / p;
+      } else {
+        dl = 0.0;
+      }
+    }
+    C2<R> l;
+    l.x = (R)(dl * (double)a.x);
+    l.y = (R)(dl * (double)a.y);
+    lam[J] = l;
+  }
+  const double s = block_sum_g(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void sum_partials1_kernel(const double* __restrict__ partials, int blocks,
+                                     double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < blocks; i += blockDim.x) s += partials[i];
+  s = block_sum_g(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+constexpr int kGradBlocks = 1024;
+
+GradGate make_grad_gate(const qs_gate& gate) {
+  GradGate g;
+  std::memset(&g, 0, sizeof(g));
+  cd m[16];
+  int dim = 0;
+  gate_matrix(gate, m, &dim);
+  g.k = dim == 2 ? 1 : 2;
+  g.q0 = gate.q[0];
+  g.q1 = g.k == 2 ? gate.q[1] : gate.q[0];
+  for (int r = 0; r < dim; ++r)
+    for (int c = 0; c < dim; ++c) {
+      const cd v = std::conj(m[c * dim + r]);
+      g.ud[2 * (r * dim + c)] = v.real();
+      g.ud[2 * (r * dim + c) + 1] = v.imag();
+    }
+  g.np = gate_nparams(gate.kind);
+  for (int p = 0; p < g.np; ++p) {
+    cd dm[16];
+    gate_dmatrix(gate, p, dm);
+    for (int i = 0; i < dim * dim; ++i) {
+      g.du[p][2 * i] = dm[i].real();
+      g.du[p][2 * i + 1] = dm[i].imag();
+    }
+  }
+  return g;
+}
+
+// psi: the state after the gate (uncomputed in place) or, with before = true,
+// the state before the gate (read only)
+template <typename R>
+qs_status backward_gate(State* st, C2<R>* psi, C2<R>* lam, const qs_gate& gate, double* partials,
+                        double* out3, bool before) {
+  GradGate g = make_grad_gate(gate);
+  const uint64_t groups = 1ull << (st->n - g.k);
+  int blocks = (int)((groups + 255) / 256);
+  if (blocks > kGradBlocks) blocks = kGradBlocks;
+  adjoint_step_kernel<R><<<blocks, 256, 0, st->stream>>>(psi, lam, st->n, g, partials, before ? 1 : 0);
+  QS_CUDA(cudaGetLastError());
+  sum_partials3_kernel<<<1, 256, 0, st->stream>>>(partials, blocks, out3);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+template <typename R>
+qs_status run_grad(State* st, const qs_gate* gates, size_t ng, const double* w, int mode, int K,
+                   double* dtheta, double* loss) {
+  const size_t sb = st->data_bytes;
+  std::vector<void*> bufs;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st->stream);
+    for (void* p : bufs) dev_free(st, p, sb);
+  };
+  auto alloc_state = [&]() -> void* {
+    void* p = dev_alloc(st, sb);
+    if (p) bufs.push_back(p);
+    return p;
+  };
+  qs_status s = QS_OK;
+  C2<R>* psi0 = (C2<R>*)alloc_state();
+  C2<R>* lam = (C2<R>*)alloc_state();
+  double* dth = (double*)dev_alloc(st, 3 * sizeof(double) * (ng + 1) + 8 * kGradBlocks * 3);
+  if (!psi0 || !lam || !dth) {
+    if (dth) dev_free(st, dth, 0);
+    cleanup();
+    set_error("device allocation for the gradient failed");
+    return QS_ENOMEM;
+  }
+  double* partials = dth + 3 * (ng + 1);
+  QS_CUDA(cudaMemcpyAsync(psi0, st->data, sb, cudaMemcpyDeviceToDevice, st->stream));
+  // ---------------- forward (tiled), keeping checkpoints in checkpoint mode
+  std::vector<C2<R>*> ckpt, segbuf;
+  const bool use_ckpt = K > 0;
+  if (use_ckpt) {
+    for (size_t g0 = 0; g0 < ng && s == QS_OK; g0 += (size_t)K) {
+      C2<R>* c = (C2<R>*)alloc_state();
+      if (!c) {
+        s = QS_ENOMEM;
+        set_error("checkpoint allocation failed");
+        break;
+      }
+      QS_CUDA(cudaMemcpyAsync(c, st->data, sb, cudaMemcpyDeviceToDevice, st->stream));
+      ckpt.push_back(c);
+      const size_t cnt = (g0 + K <= ng) ? (size_t)K : ng - g0;
+      s = apply_gates(st, gates + g0, cnt, QS_METHOD_TILED, nullptr);
+    }
+    for (int k = 0; k < K && s == QS_OK; ++k) {
+      C2<R>* b = (C2<R>*)alloc_state();
+      if (!b) {
+        s = QS_ENOMEM;
+        set_error("segment buffer allocation failed");
+      }
+      segbuf.push_back(b);
+    }
+  } else {
+    s = apply_gates(st, gates, ng, QS_METHOD_TILED, nullptr);
+  }
+  // ---------------- seed
+  if (s == QS_OK) {
+    const uint64_t N = 1ull << st->n;
+    int blocks = (int)((N + 255) / 256);
+    if (blocks > kGradBlocks) blocks = kGradBlocks;
+    seed_kernel<R><<<blocks, 256, 0, st->stream>>>((const C2<R>*)st->data, lam, w, mode, N, partials);
+    sum_partials1_kernel<<<1, 256, 0, st->stream>>>(partials, blocks, dth + 3 * ng);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_status(e, "seed kernel");
+  }
+  // ---------------- backward
+  if (s == QS_OK) {
+    if (!use_ckpt) {
+      for (size_t g = ng; g-- > 0 && s == QS_OK;)
+        s = backward_gate<R>(st, (C2<R>*)st->data, lam, gates[g], partials, dth + 3 * g, false);
+    } else {
+      for (size_t seg = ckpt.size(); seg-- > 0 && s == QS_OK;) {
+        const size_t g0 = seg * (size_t)K;
+        const size_t g1 = (g0 + K <= ng) ? g0 + (size_t)K : ng;
+        // states before each gate of the segment, recomputed forward from the checkpoint
+        QS_CUDA(cudaMemcpyAsync(st->data, ckpt[seg], sb, cudaMemcpyDeviceToDevice, st->stream));
+        for (size_t g = g0; g < g1 && s == QS_OK; ++g) {
+          QS_CUDA(cudaMemcpyAsync(segbuf[g - g0], st->data, sb, cudaMemcpyDeviceToDevice, st->stream));
+          if (g + 1 < g1) s = apply_gates(st, gates + g, 1, QS_METHOD_TILED, nullptr);
+        }
+        for (size_t g = g1; g-- > g0 && s == QS_OK;)
+          s = backward_gate<R>(st, segbuf[g - g0], lam, gates[g], partials, dth + 3 * g, true);
+      }
+    }
+  }
+  if (s == QS_OK) {
+    std::vector<double> host(3 * ng + 1);
+    QS_CUDA(cudaMemcpyAsync(host.data(), dth, sizeof(double) * (3 * ng + 1), cudaMemcpyDeviceToHost,
+                            st->stream));
+    QS_CUDA(cudaMemcpyAsync(st->data, psi0, sb, cudaMemcpyDeviceToDevice, st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    for (size_t g = 0; g < ng; ++g) {
+      const int np = gate_nparams(gates[g].kind);
+      for (int p = 0; p < 3; ++p) dtheta[3 * g + p] = p < np ? host[3 * g + p] : 0.0;
+    }
+    if (loss) *loss = host[3 * ng];
+  }
+  dev_free(st, dth, 0);
+  cleanup();
+  return s;
+}
+
+}  // namespace
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" qs_status sv_grad(qs_state_t h, const qs_gate* gates, size_t ngates, const double* weights,
+                             int mode, int checkpoint_every, double* dtheta, double* loss) {
+  State* st = h;
+  if (!st) {
+    set_error("state is NULL");
+    return QS_EINVAL;
+  }
+  if (!weights || (ngates > 0 && !dtheta) || (mode != 0 && mode != 1) || checkpoint_every < 0) {
+    set_error("bad sv_grad arguments");
+    return QS_EINVAL;
+  }
+  qs_status s = validate_gates(gates, ngates, st->n);
+  if (s != QS_OK) return s;
+  if (st->prec == QS_C64)
+    return run_grad<float>(st, gates, ngates, weights, mode, checkpoint_every, dtheta, loss);
+  return run_grad<double>(st, gates, ngates, weights, mode, checkpoint_every, dtheta, loss);
+}

@@ -180,6 +180,9 @@ struct Plan {
 void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vmap_final,
                   Plan& plan);
 
+// Applies gates to a state (the body of sv_apply_circuit; api.cpp).
+qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats);
+
 // ---------------------------------------------------------------- launchers
 // (sv_kernels.cu)
 qs_status launch_set_basis(State* st, uint64_t J);
@@ -195,3 +198,6 @@ qs_status launch_loglik(State* st, const uint32_t* counts, double* partials,
                         unsigned long long* clamps);
 
 }  // namespace qs
+
+// The opaque handle of the C ABI is the runtime's State.
+struct qs_state_s : public qs::State {};
