@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the state-vector hot path on one GB300 (or N replicas).
+
+Workload (the 30-qubit configuration): n = 30 qubits, complex64 (8 GiB
+state), 40 layers of Haar-random SU(2) on every qubit plus brickwork CZ
+(seed 2001) = 1800 gates, started from |0...0>, followed by the Born-rule
+probabilities (4 GiB fp32) and their fp64 norm.  One step = one such circuit.
+
+metric: "gate-passes/sec" = gates applied to the full 2^30-amplitude state per
+second (one gate pass is the work the per-gate method does in one HBM sweep).
+The JSON line also carries the real HBM sweeps and bytes, the roofline of the
+dominant kernel (the tile-pass kernel, FP32-ALU bound), the CPU oracle
+baseline, the end-to-end number through the public API with host buffers,
+launch counts and the SM clocks sampled during the timed region.
+
+Multi-GPU: replicas only (each rank simulates its own copy of the workload;
+there is no exchange), value = all ranks' gates / max rank time.
+
+--impl reference times the FP64 CPU oracle (numpy, single BLAS thread) on a
+bounded sample of the same workload (the first gates of the circuit at 24
+qubits, scaled by the state size to 30 qubits).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gate-passes/sec & HBM GB/s (% of peak) at 30 qubits; circuits/sec, p50/p99 served"
+UNIT = "gate-passes/s"
+N_QUBITS = 30
+LAYERS = 40
+SEED = 2001
+SAMPLE_N = 24          # CPU sample size
+SAMPLE_GATES = 10      # gates per CPU sample
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops x clock
+def fp32_peak_tflops(mhz):
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        loaded = [s for s in sm if s > 0.5 * (max(sm) if sm else 1)]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_sample_seconds(n=SAMPLE_N, gates=SAMPLE_GATES):
+    """Times the oracle on the first `gates` gates of the workload at n qubits in a
+    child process pinned to one BLAS thread.  Returns seconds per gate."""
+    code = (
+        "import sys,time; sys.path.insert(0, %r)\n"
+        "import workloads as W\n"
+        "from oracle import statevector as SV\n"
+        "n=%d; ops=W.layered_haar_cz(n, 1, seed=%d)[:%d]\n"
+        "psi=SV.basis(n)\n"
+        "psi=SV.apply_gate(psi,n,ops[0])\n"
+        "t=time.perf_counter()\n"
+        "for op in ops: psi=SV.apply_gate(psi,n,op)\n"
+        "print((time.perf_counter()-t)/len(ops))\n" % (ROOT, n, SEED, gates))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr)
+    return float(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_block():
+    per_gate = cpu_sample_seconds()
+    scaled = per_gate * (1 << (N_QUBITS - SAMPLE_N))
+    return {"value": 1.0 / scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, {SAMPLE_GATES} gates of the workload at {SAMPLE_N} qubits "
+                      f"({per_gate:.3f} s/gate), scaled by 2^{N_QUBITS - SAMPLE_N} to {N_QUBITS} qubits"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = cpu_sample_seconds(gates=3)
+        if i >= args.warmup:
+            times.append(t)
+    per_gate = statistics.mean(times) * (1 << (N_QUBITS - SAMPLE_N))
+    value = 1.0 / per_gate
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_gate * 1800 * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{N_QUBITS}-qubit layered Haar SU(2) + brickwork CZ, {LAYERS} layers, "
+                                   f"seed {SEED}", "sample_qubits": SAMPLE_N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: 3 gates of the workload at {SAMPLE_N} qubits, "
+                                       f"scaled by 2^{N_QUBITS - SAMPLE_N}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2008_13490_gb300 as qs
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    qs.load()
+    n = args.n
+    ops = W.layered_haar_cz(n, LAYERS, seed=SEED)
+    arr = qs.gates_array(ops)
+    gates = len(arr)
+    st = qs.State(n, qs.QS_C64)
+    probs = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        qs.sv_set_basis(st, 0)
+        s = qs.sv_apply_circuit(st, arr)
+        qs.sv_probs(st, out=probs, want_norm=False)
+        return s
+
+    for _ in range(args.warmup):
+        stats = step()
+    torch.cuda.synchronize()
+    _, norm = qs.sv_probs(st, out=probs)
+
+    # ---- timed region: K steps, CUDA events on the launching stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    qs.qs_profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        stats = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kms, kcnt = qs.qs_profile_end()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(world, ms)
+    ms_per_step = ms_max / args.steps
+
+    # ---- end to end through the public API with host buffers
+    host_probs = torch.empty(1 << n, dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(2, min(args.steps, 3))
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        qs.sv_set_basis(st, 0)
+        s2 = qs.sv_apply_circuit(st, arr)                 # host gate array -> planner -> H2D
+        qs.sv_probs(st, out=probs, want_norm=False)
+        host_probs.copy_(probs, non_blocking=True)         # D2H of the result
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks(world, e2e_s)
+
+    if rank != 0:
+        st.close()
+        return 0
+
+    peaks, peak_src = measured_peaks()
+    # roofline of the dominant kernel (tile pass): FP32-ALU bound
+    tile_ms = kms["tile"] / max(1, kcnt["tile"])
+    tile_flops = stats["tile_flops"] / max(1, stats["tile_launches"])
+    achieved_tflops = tile_flops / (tile_ms * 1e-3) / 1e12
+    fp32_peak = fp32_peak_tflops(2070.0)
+    bytes_per_pass = 2 * (1 << n) * 8
+    hbm_gbs = bytes_per_pass / (tile_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "tile_pass_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            tr = json.load(f)
+        if tr.get("kernel_rev") == qs.version():
+            traffic = tr.get("bytes_per_launch")
+    launches_per_step = 1 + stats["launches"] + 1   # set_basis, circuit, probabilities
+    gates_per_s = world * gates * args.steps / (ms_max * 1e-3)
+    line = {
+        "metric": METRIC, "value": gates_per_s, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{n}-qubit complex64 state, {LAYERS} layers Haar SU(2) + brickwork CZ "
+                               f"({gates} gates, seed {SEED}) from |0..0>, then Born-rule probabilities",
+                   "n_qubits": n, "precision": "complex64", "gates": gates,
+                   "l2": "state (8 GiB) is larger than L2; no flush needed", "parallelism": "replicas"},
+        "circuits_per_s": world * args.steps / (ms_max * 1e-3),
+        "passes_per_circuit": stats["passes"], "ops_after_fusion": stats["ops_fused"],
+        "hbm": {"sweeps_per_s": world * stats["passes"] * args.steps / (ms_max * 1e-3),
+                "tile_pass_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
+                "frac": hbm_gbs / peaks["hbm_gbs"], "bytes_per_pass": bytes_per_pass},
+        "roofline": {"bound": "alu", "kernel": "tile_pass_kernel<float>",
+                     "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / fp32_peak, "traffic": traffic,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+                     "avg_launch_ms": tile_ms, "flops_per_launch": tile_flops},
+        "e2e": {"value": world * gates / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(s2["upload_bytes"]) + gates * arr.itemsize,
+                "d2h_bytes_per_step": (1 << n) * 4},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "norm": norm,
+        "peaks_source": peak_src,
+    }
+    st.close()
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_block()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_QUBITS)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

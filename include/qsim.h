@@ -104,8 +104,14 @@ typedef enum {
 
 typedef struct {
   int32_t method;       /* qs_method */
-  int32_t reserved[7];
+  int32_t flags;        /* QS_OPT_* */
+  int32_t reserved[6];
 } qs_opts;
+
+/* Record CUDA events around every launch of the call (on the state's stream)
+ * and report per-kind device times in qs_stats.kernel_ms; makes the call
+ * synchronous. */
+#define QS_OPT_TIME_KERNELS 1
 
 /* Per-call statistics (filled when a non-NULL pointer is given). */
 typedef struct {
@@ -114,6 +120,13 @@ typedef struct {
   int64_t passes;          /* full-state read+write sweeps */
   int64_t launches;        /* kernel launches */
   double bytes_moved;      /* algorithmic bytes: passes * 2 * 2^n * sizeof(amplitude) */
+  double flops;            /* algorithmic flops: 2 per real FMA of the complex MACs;
+                              16 per amplitude per dense or controlled one-qubit op,
+                              8 per diagonal op, 32 per two-qubit dense op */
+  int64_t upload_bytes;    /* op descriptors copied host -> device */
+  int64_t tile_launches;   /* launches of the tile-pass kernel */
+  double kernel_ms[4];     /* with QS_OPT_TIME_KERNELS: tile, plain, remap, small-state */
+  double tile_flops;       /* algorithmic flops of the tile-pass launches */
 } qs_stats;
 
 /* ---- state vector ------------------------------------------------------ */
@@ -212,6 +225,17 @@ typedef struct {
  * (stream-ordered cudaMallocAsync/cudaFreeAsync inside the call). */
 qs_status dm_apply_channels(const qs_dm_batch* batch, float* probs, double* loglik, double* grad,
                             void* stream);
+
+/* ---- profiling --------------------------------------------------------- */
+
+/* Between qs_profile_begin and qs_profile_end every state-vector launch of
+ * this library is bracketed by CUDA events recorded on its stream (no
+ * synchronisation).  qs_profile_end synchronises those events and returns,
+ * per kind (0 tile pass, 1 plain per-gate, 2 remap, 3 small state), the
+ * summed device milliseconds and launch counts (HOST arrays of 4, may be
+ * NULL).  One session per process at a time. */
+qs_status qs_profile_begin(void);
+qs_status qs_profile_end(double* kernel_ms, int64_t* launches);
 
 /* ---- misc -------------------------------------------------------------- */
 

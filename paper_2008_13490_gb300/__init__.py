@@ -44,11 +44,17 @@ class QsimError(RuntimeError):
 class _Stats(ctypes.Structure):
     _fields_ = [("gates_in", ctypes.c_int64), ("ops_fused", ctypes.c_int64),
                 ("passes", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("bytes_moved", ctypes.c_double)]
+                ("bytes_moved", ctypes.c_double), ("flops", ctypes.c_double),
+                ("upload_bytes", ctypes.c_int64), ("tile_launches", ctypes.c_int64),
+                ("kernel_ms", ctypes.c_double * 4), ("tile_flops", ctypes.c_double)]
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("method", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("method", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+OPT_TIME_KERNELS = 1
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -94,6 +100,8 @@ def load():
         "sv_grad": (i32, [vp, vp, sz, vp, i32, i32, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double)]),
         "dm_apply_channels": (i32, [ctypes.POINTER(DMBatch), vp, vp, vp, vp]),
+        "qs_profile_begin": (i32, []),
+        "qs_profile_end": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "qs_last_error": (ctypes.c_char_p, []),
         "qs_version": (ctypes.c_char_p, []),
     }
@@ -108,7 +116,21 @@ def load():
 def exported_symbols():
     return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
             "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
-            "dm_apply_channels", "qs_last_error", "qs_version"]
+            "dm_apply_channels", "qs_profile_begin", "qs_profile_end", "qs_last_error",
+            "qs_version"]
+
+
+def qs_profile_begin():
+    _check(load().qs_profile_begin())
+
+
+def qs_profile_end():
+    """Returns ({kind: ms}, {kind: launches}) for kinds tile, plain, remap, small."""
+    ms = (ctypes.c_double * 4)()
+    cnt = (ctypes.c_int64 * 4)()
+    _check(load().qs_profile_end(ms, cnt))
+    kinds = ("tile", "plain", "remap", "small")
+    return dict(zip(kinds, list(ms))), dict(zip(kinds, list(cnt)))
 
 
 def _check(status: int):
@@ -251,14 +273,16 @@ def sv_copy_out(st: State, out=None):
     return a
 
 
-def sv_apply_circuit(st: State, gates, method: int = METHOD_TILED) -> dict:
+def sv_apply_circuit(st: State, gates, method: int = METHOD_TILED, time_kernels: bool = False) -> dict:
     arr = gates if isinstance(gates, np.ndarray) else gates_array(gates)
     arr = np.ascontiguousarray(arr, dtype=GATE_DTYPE)
-    opts = _Opts(method)
+    opts = _Opts(method, OPT_TIME_KERNELS if time_kernels else 0)
     stats = _Stats()
     _check(load().sv_apply_circuit(st.handle, arr.ctypes.data, len(arr), ctypes.byref(opts),
                                    ctypes.byref(stats)))
-    return {k: getattr(stats, k) for k, _ in _Stats._fields_}
+    out = {k: getattr(stats, k) for k, _ in _Stats._fields_}
+    out["kernel_ms"] = list(stats.kernel_ms)
+    return out
 
 
 def sv_probs(st: State, out=None, fp64: bool = False, marg_mask: int = 0, want_norm: bool = True):

@@ -2,6 +2,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -163,43 +164,137 @@ size_t put(std::vector<unsigned char>& blob, const T* p, size_t count) {
   return off;
 }
 
+// algorithmic flops per amplitude of a fused op (2 per real FMA of its complex MACs)
+double op_flops_per_amp(const FOp& o) {
+  switch (o.type) {
+    case F_G1: case F_G1C: return 16.0;
+    case F_D: return 8.0;
+    default: return 32.0;
+  }
+}
+
+// Process-wide profiling session (qs_profile_begin / qs_profile_end).
+struct ProfileSession {
+  std::mutex mu;
+  bool active = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+};
+ProfileSession& profile() {
+  static ProfileSession p;
+  return p;
+}
+
+// Optional CUDA-event timing of every launch, by kind (tile, plain, remap, small):
+// per call (QS_OPT_TIME_KERNELS) and/or into the profiling session.
+struct KernelTimer {
+  bool on = false;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  cudaEvent_t prof_start = nullptr;
+  void before(int k) {
+    ProfileSession& ps = profile();
+    if (ps.active) {
+      std::lock_guard<std::mutex> g(ps.mu);
+      cudaEvent_t a;
+      cudaEventCreate(&a);
+      cudaEventRecord(a, stream);
+      ps.ev.push_back(a);
+      ps.ev.push_back(nullptr);
+      ps.kind.push_back(k);
+      prof_start = a;
+    }
+    if (!on) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, stream);
+    ev.push_back(a);
+    ev.push_back(b);
+    kind.push_back(k);
+  }
+  void after() {
+    ProfileSession& ps = profile();
+    if (ps.active && prof_start) {
+      std::lock_guard<std::mutex> g(ps.mu);
+      cudaEvent_t b;
+      cudaEventCreate(&b);
+      cudaEventRecord(b, stream);
+      for (size_t i = ps.ev.size(); i >= 2; i -= 2)
+        if (ps.ev[i - 2] == prof_start) {
+          ps.ev[i - 1] = b;
+          break;
+        }
+      prof_start = nullptr;
+    }
+    if (on) cudaEventRecord(ev.back(), stream);
+  }
+  void finish(qs_stats* stats) {
+    if (!on) return;
+    cudaStreamSynchronize(stream);
+    for (size_t i = 0; i < kind.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+      if (stats) stats->kernel_ms[kind[i]] += ms;
+      cudaEventDestroy(ev[2 * i]);
+      cudaEventDestroy(ev[2 * i + 1]);
+    }
+    ev.clear();
+    kind.clear();
+  }
+};
+
 template <typename R>
-qs_status run_plain(State* st, const std::vector<FOp>& fops, qs_stats* stats) {
+qs_status run_plain(State* st, const std::vector<FOp>& fops, qs_stats* stats, KernelTimer& tm) {
+  double flops = 0.0;
   for (const FOp& o : fops) {
     PlainOp<R> p = to_plain<R>(o);
+    tm.before(1);
     qs_status s = launch_plain_op(st, &p, o.type);
+    tm.after();
     if (s != QS_OK) return s;
+    flops += op_flops_per_amp(o) * std::ldexp(1.0, st->n);
   }
   if (stats) {
     stats->ops_fused = (int64_t)fops.size();
     stats->passes = (int64_t)fops.size();
     stats->launches = (int64_t)fops.size();
+    stats->flops = flops;
   }
   return QS_OK;
 }
 
 template <typename R>
-qs_status run_small(State* st, const std::vector<FOp>& fops, qs_stats* stats) {
+qs_status run_small(State* st, const std::vector<FOp>& fops, qs_stats* stats, KernelTimer& tm) {
   std::vector<PlainOp<R>> ops;
   ops.reserve(fops.size());
-  for (const FOp& o : fops) ops.push_back(to_plain<R>(o));
+  double flops = 0.0;
+  for (const FOp& o : fops) {
+    ops.push_back(to_plain<R>(o));
+    flops += op_flops_per_amp(o) * std::ldexp(1.0, st->n);
+  }
   std::vector<unsigned char> blob;
   size_t off = put(blob, ops.data(), ops.size());
   qs_status s = upload(st, blob);
   if (s != QS_OK) return s;
+  tm.before(3);
   s = launch_small(st, (unsigned char*)st->opbuf + off, (int)ops.size());
+  tm.after();
   if (s != QS_OK) return s;
   if (stats) {
     stats->ops_fused = (int64_t)fops.size();
     stats->passes = 1;
     stats->launches = 1;
+    stats->flops = flops;
+    stats->upload_bytes = (int64_t)blob.size();
   }
   return QS_OK;
 }
 
 template <typename R>
 qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<int>& vmap,
-                    qs_stats* stats) {
+                    qs_stats* stats, KernelTimer& tm) {
   Plan pl;
   plan_circuit(fops, st->n, vmap, pl);
   std::vector<TileOp<R>> tops;
@@ -213,24 +308,33 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
   qs_status s = upload(st, blob);
   if (s != QS_OK) return s;
   unsigned char* dev = (unsigned char*)st->opbuf;
-  int64_t passes = 0, launches = 0;
+  int64_t passes = 0, launches = 0, tile_launches = 0;
+  const double N = std::ldexp(1.0, st->n);
+  double tile_flops = 0.0, plain_flops = 0.0;
+  for (const FOp& o : pl.tile_fops) tile_flops += op_flops_per_amp(o) * N;
   for (const PlanStep& step : pl.steps) {
     switch (step.kind) {
       case PlanStep::TILE:
+        tm.before(0);
         s = launch_tile_pass(st, dev + off_pass + sizeof(TilePass) * step.index, dev + off_stage,
                              dev + off_ops, pl.passes[step.index].n_stages);
+        ++tile_launches;
         break;
       case PlanStep::PLAIN: {
         PlainOp<R> p = to_plain<R>(pl.plain_fops[step.index]);
+        plain_flops += op_flops_per_amp(pl.plain_fops[step.index]) * N;
+        tm.before(1);
         s = launch_plain_op(st, &p, p.type);
         break;
       }
       case PlanStep::REMAP:
+        tm.before(2);
         s = launch_remap(st, dev + off_remap + sizeof(RemapDesc) * step.index, nullptr);
         break;
       default:
         break;
     }
+    tm.after();
     if (s != QS_OK) return s;
     ++passes;
     ++launches;
@@ -239,6 +343,10 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
     stats->ops_fused = (int64_t)fops.size();
     stats->passes = passes;
     stats->launches = launches;
+    stats->tile_launches = tile_launches;
+    stats->tile_flops = tile_flops;
+    stats->flops = tile_flops + plain_flops;
+    stats->upload_bytes = (int64_t)blob.size();
   }
   return QS_OK;
 }
@@ -253,7 +361,8 @@ qs_status check_state(qs_state_t st) {
 
 }  // namespace
 
-qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats) {
+qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats,
+                      int flags) {
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (method != QS_METHOD_TILED && method != QS_METHOD_PLAIN) {
     set_error("unknown method %d", method);
@@ -263,17 +372,22 @@ qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method
   std::vector<FOp> fops;
   std::vector<int> vmap;
   const bool c64 = st->prec == QS_C64;
+  KernelTimer tm;
+  tm.on = (flags & QS_OPT_TIME_KERNELS) != 0;
+  tm.stream = st->stream;
   qs_status s;
   if (method == QS_METHOD_PLAIN) {
     build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/false, /*relabel=*/false);
-    s = c64 ? run_plain<float>(st, fops, stats) : run_plain<double>(st, fops, stats);
+    s = c64 ? run_plain<float>(st, fops, stats, tm) : run_plain<double>(st, fops, stats, tm);
   } else if (st->n < kTileBits) {
     build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/false);
-    s = c64 ? run_small<float>(st, fops, stats) : run_small<double>(st, fops, stats);
+    s = c64 ? run_small<float>(st, fops, stats, tm) : run_small<double>(st, fops, stats, tm);
   } else {
     build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/true);
-    s = c64 ? run_tiled<float>(st, fops, vmap, stats) : run_tiled<double>(st, fops, vmap, stats);
+    s = c64 ? run_tiled<float>(st, fops, vmap, stats, tm)
+            : run_tiled<double>(st, fops, vmap, stats, tm);
   }
+  tm.finish(stats);
   if (stats) {
     stats->gates_in = (int64_t)ngates;
     stats->bytes_moved = (double)stats->passes * 2.0 * (double)st->data_bytes;
@@ -424,7 +538,8 @@ qs_status sv_apply_circuit(qs_state_t st, const qs_gate* gates, size_t ngates, c
   if (s != QS_OK) return s;
   s = validate_gates(gates, ngates, st->n);
   if (s != QS_OK) return s;
-  return apply_gates(st, gates, ngates, opts ? opts->method : QS_METHOD_TILED, stats);
+  return apply_gates(st, gates, ngates, opts ? opts->method : QS_METHOD_TILED, stats,
+                     opts ? opts->flags : 0);
 }
 
 qs_status sv_probs(qs_state_t st, void* out, int out_fp64, uint64_t marg_mask, double* norm_out) {
@@ -479,6 +594,52 @@ qs_status sv_loglik(qs_state_t st, const uint32_t* counts, double* out, int64_t*
   QS_CUDA(cudaStreamSynchronize(st->stream));
   if (clamped) *clamped = (int64_t)nc;
   return QS_OK;
+}
+
+qs_status qs_profile_begin(void) {
+  ProfileSession& ps = profile();
+  std::lock_guard<std::mutex> g(ps.mu);
+  if (ps.active) {
+    set_error("a profiling session is already active");
+    return QS_EINVAL;
+  }
+  ps.ev.clear();
+  ps.kind.clear();
+  ps.active = true;
+  return QS_OK;
+}
+
+qs_status qs_profile_end(double* kernel_ms, int64_t* launches) {
+  ProfileSession& ps = profile();
+  std::lock_guard<std::mutex> g(ps.mu);
+  if (!ps.active) {
+    set_error("no active profiling session");
+    return QS_EINVAL;
+  }
+  ps.active = false;
+  double ms[4] = {0, 0, 0, 0};
+  int64_t cnt[4] = {0, 0, 0, 0};
+  qs_status s = QS_OK;
+  for (size_t i = 0; i < ps.kind.size(); ++i) {
+    cudaEvent_t a = ps.ev[2 * i], b = ps.ev[2 * i + 1];
+    if (a && b) {
+      cudaError_t e = cudaEventSynchronize(b);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+      if (e != cudaSuccess && s == QS_OK) s = cuda_status(e, "profile events");
+      ms[ps.kind[i]] += t;
+      cnt[ps.kind[i]] += 1;
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  ps.ev.clear();
+  ps.kind.clear();
+  for (int k = 0; k < 4; ++k) {
+    if (kernel_ms) kernel_ms[k] = ms[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  return s;
 }
 
 }  // extern "C"

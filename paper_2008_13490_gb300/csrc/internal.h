@@ -181,7 +181,8 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
                   Plan& plan);
 
 // Applies gates to a state (the body of sv_apply_circuit; api.cpp).
-qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats);
+qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats,
+                      int flags = 0);
 
 // ---------------------------------------------------------------- launchers
 // (sv_kernels.cu)
