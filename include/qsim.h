@@ -226,6 +226,24 @@ typedef struct {
 qs_status dm_apply_channels(const qs_dm_batch* batch, float* probs, double* loglik, double* grad,
                             void* stream);
 
+/* ---- probabilities without allocation ------------------------------------
+ * The thesis has no counterpart of this entry point; it exists for callers
+ * that may not allocate device memory (their own allocator owns the device,
+ * or an allocation is not allowed where they call it).  It computes what
+ * sv_probs computes, but for caller-owned buffers and without any cudaMalloc /
+ * cudaFree or other allocation: amps (DEVICE, 2^n interleaved amplitudes of
+ * precision prec), out (DEVICE, float or double as out_fp64, 2^n values, or
+ * 2^popcount(mask) marginal values, may be NULL), norm_out (HOST, may be
+ * NULL; synchronises stream).  Its reduction scratch is one fixed array in
+ * device global memory (about 41 KB per device, held until the process
+ * exits): n <= 36 and marginals over at most 12 qubits, else QS_EINVAL.  The
+ * first call on each device looks up that array's device address (make it
+ * before capturing the stream into a graph).  All calls share the array and
+ * find the previous call's contents in it (the kernels clear what must start
+ * at zero); calls that overlap on the GPU race on it. */
+qs_status qs_probs_noalloc(const void* amps, int n, int prec, void* out, int out_fp64,
+                           uint64_t marg_mask, double* norm_out, void* stream);
+
 /* ---- profiling --------------------------------------------------------- */
 
 /* Between qs_profile_begin and qs_profile_end every state-vector launch of

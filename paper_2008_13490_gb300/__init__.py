@@ -100,6 +100,7 @@ def load():
         "sv_grad": (i32, [vp, vp, sz, vp, i32, i32, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double)]),
         "dm_apply_channels": (i32, [ctypes.POINTER(DMBatch), vp, vp, vp, vp]),
+        "qs_probs_noalloc": (i32, [vp, i32, i32, vp, i32, u64, ctypes.POINTER(ctypes.c_double), vp]),
         "qs_profile_begin": (i32, []),
         "qs_profile_end": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "qs_last_error": (ctypes.c_char_p, []),
@@ -116,8 +117,21 @@ def load():
 def exported_symbols():
     return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
             "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
-            "dm_apply_channels", "qs_profile_begin", "qs_profile_end", "qs_last_error",
-            "qs_version"]
+            "dm_apply_channels", "qs_probs_noalloc", "qs_profile_begin", "qs_profile_end",
+            "qs_last_error", "qs_version"]
+
+
+def qs_probs_noalloc(amps_ptr: int, n: int, prec: int, out=None, fp64: bool = False,
+                     marg_mask: int = 0, want_norm: bool = True, stream=None):
+    """Probabilities of a caller-owned device amplitude buffer, with no device
+    allocation inside the library (for callers that may not allocate).
+    ``out`` must be a preallocated device tensor; returns (out, norm)."""
+    norm = ctypes.c_double()
+    _check(load().qs_probs_noalloc(int(amps_ptr), int(n), int(prec),
+                                   out.data_ptr() if out is not None else None, 1 if fp64 else 0,
+                                   int(marg_mask), ctypes.byref(norm) if want_norm else None,
+                                   _stream_ptr(stream)))
+    return out, (norm.value if want_norm else None)
 
 
 def qs_profile_begin():
