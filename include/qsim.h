@@ -226,6 +226,49 @@ typedef struct {
 qs_status dm_apply_channels(const qs_dm_batch* batch, float* probs, double* loglik, double* grad,
                             void* stream);
 
+/* ---- serving: continuous batching of circuits ----------------------------
+ * A server owns a scheduler thread.  Submitted circuits (each from |0...0>,
+ * result = marginal outcome probabilities over marg_mask, the Born rule of
+ * section "Quantum circuits") are admitted as device memory and slots free
+ * up, while earlier ones are still running:
+ *   - circuits with n <= small_max_qubits are packed into one launch (one CTA
+ *     per circuit, its whole state in shared memory); a new packed launch
+ *     starts whenever the previous one has finished and circuits wait;
+ *   - larger circuits get a resident state (stream-ordered allocation within
+ *     mem_budget) and run the tiled pass pipeline on one of max_inflight
+ *     streams, overlapping with each other and with the packed launches.
+ * Latency = completion seen by the scheduler - submission time. */
+typedef struct qs_server_s* qs_server_t;
+
+typedef struct {
+  int32_t prec;              /* QS_C64 or QS_C128 */
+  int32_t small_max_qubits;  /* <= 14 (QS_C64) / 13 (QS_C128); 0 = largest allowed */
+  int32_t max_inflight;      /* large circuits on the device at once; 0 = 4 */
+  int32_t max_batch;         /* circuits per packed launch; 0 = 1024 */
+  uint64_t mem_budget;       /* device bytes for resident states; 0 = 80% of free memory */
+} qs_server_config;
+
+typedef struct {
+  int64_t submitted, completed, packed_launches, packed_circuits, large_circuits;
+  double p50_ms, p99_ms, mean_ms, max_ms;
+  double wall_s;             /* first submission to last completion */
+  double circuits_per_s;
+  uint64_t peak_bytes;       /* largest resident-state footprint */
+} qs_server_stats;
+
+qs_status qs_server_create(const qs_server_config* cfg, qs_server_t* out);
+/* Copies the gates; returns at once with a ticket.  marg_mask: bits of the
+ * marginal (popcount <= 12; 0 means all n bits, allowed for n <= 12).
+ * n in [1, 30]. */
+qs_status qs_server_submit(qs_server_t s, int n, const qs_gate* gates, size_t ngates,
+                           uint64_t marg_mask, int64_t* ticket);
+/* Blocks until the circuit is done; result (HOST, 2^popcount doubles, may be
+ * NULL), latency_ms (HOST, may be NULL).  Each ticket can be waited once. */
+qs_status qs_server_wait(qs_server_t s, int64_t ticket, double* result, double* latency_ms);
+qs_status qs_server_stats_get(qs_server_t s, qs_server_stats* out);
+/* Waits for all submitted circuits, stops the scheduler, frees everything. */
+qs_status qs_server_destroy(qs_server_t s);
+
 /* ---- probabilities without allocation ------------------------------------
  * The thesis has no counterpart of this entry point; it exists for callers
  * that may not allocate device memory (their own allocator owns the device,

@@ -74,6 +74,21 @@ class DMBatch(ctypes.Structure):
                 ("counts", ctypes.c_void_p), ("ptm1", ctypes.c_void_p), ("ptm2", ctypes.c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("small_max_qubits", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("mem_budget", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("packed_launches", ctypes.c_int64), ("packed_circuits", ctypes.c_int64),
+                ("large_circuits", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("circuits_per_s", ctypes.c_double), ("peak_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -101,6 +116,11 @@ def load():
                           ctypes.POINTER(ctypes.c_double)]),
         "dm_apply_channels": (i32, [ctypes.POINTER(DMBatch), vp, vp, vp, vp]),
         "qs_probs_noalloc": (i32, [vp, i32, i32, vp, i32, u64, ctypes.POINTER(ctypes.c_double), vp]),
+        "qs_server_create": (i32, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+        "qs_server_submit": (i32, [vp, i32, vp, sz, u64, ctypes.POINTER(ctypes.c_int64)]),
+        "qs_server_wait": (i32, [vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double)]),
+        "qs_server_stats_get": (i32, [vp, ctypes.POINTER(ServerStats)]),
+        "qs_server_destroy": (i32, [vp]),
         "qs_profile_begin": (i32, []),
         "qs_profile_end": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "qs_last_error": (ctypes.c_char_p, []),
@@ -118,7 +138,56 @@ def exported_symbols():
     return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
             "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
             "dm_apply_channels", "qs_probs_noalloc", "qs_profile_begin", "qs_profile_end",
-            "qs_last_error", "qs_version"]
+            "qs_server_create", "qs_server_submit", "qs_server_wait", "qs_server_stats_get",
+            "qs_server_destroy", "qs_last_error", "qs_version"]
+
+
+class Server:
+    """Continuous-batching circuit server (native scheduler thread; see qsim.h)."""
+
+    def __init__(self, prec: int = QS_C64, small_max_qubits: int = 0, max_inflight: int = 0,
+                 max_batch: int = 0, mem_budget: int = 0):
+        lib = load()
+        _torch()
+        cfg = ServerConfig(prec, small_max_qubits, max_inflight, max_batch, mem_budget)
+        h = ctypes.c_void_p()
+        _check(lib.qs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._masks = {}
+
+    def submit(self, n: int, gates, marg_mask: int = 0) -> int:
+        arr = gates if isinstance(gates, np.ndarray) else gates_array(gates)
+        arr = np.ascontiguousarray(arr, dtype=GATE_DTYPE)
+        t = ctypes.c_int64()
+        _check(load().qs_server_submit(self.handle, int(n), arr.ctypes.data, len(arr),
+                                       int(marg_mask), ctypes.byref(t)))
+        k = bin(marg_mask).count("1") if marg_mask else n
+        self._masks[t.value] = k
+        return t.value
+
+    def wait(self, ticket: int):
+        """Returns (marginal probabilities as float64 numpy, latency_ms)."""
+        k = self._masks.pop(ticket)
+        out = np.empty(1 << k, dtype=np.float64)
+        lat = ctypes.c_double()
+        _check(load().qs_server_wait(self.handle, int(ticket), out.ctypes.data, ctypes.byref(lat)))
+        return out, lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().qs_server_stats_get(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().qs_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def qs_probs_noalloc(amps_ptr: int, n: int, prec: int, out=None, fp64: bool = False,
