@@ -302,10 +302,143 @@ def run_ours(args, world, rank, local):
         "peaks_source": peak_src,
     }
     st.close()
+    del probs, host_probs
+    torch.cuda.empty_cache()
+    if not args.no_extras:
+        line["rows"] = {"small_circuits": extra_small_circuits(qs, torch),
+                        "noisy_batch": extra_noisy_batch(qs, torch),
+                        "serving": extra_serving(qs, torch)}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_block()
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------- other rows (extra keys)
+def extra_small_circuits(qs, torch):
+    """10-qubit complex128 circuits (20 layers Haar + CNOT matching), all 1024 probabilities."""
+    import workloads as W
+    ops = qs.gates_array(W.layered_haar_cnot(10, 20, seed=1001))
+    st = qs.State(10, qs.QS_C128)
+    out = torch.empty(1024, dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        qs.sv_set_basis(st, 0)
+        qs.sv_apply_circuit(st, ops)
+        qs.sv_probs(st, out=out, fp64=True, want_norm=False)
+    torch.cuda.synchronize()
+    reps = 200
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        qs.sv_set_basis(st, 0)
+        qs.sv_apply_circuit(st, ops)
+        qs.sv_probs(st, out=out, fp64=True, want_norm=False)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    st.close()
+    return {"workload": "10-qubit complex128, 20 layers Haar + CNOT matching, 1024 probabilities",
+            "us_per_circuit": dt * 1e6, "circuits_per_s": 1.0 / dt,
+            "note": "host-launch bound (planner + 3 launches per circuit)"}
+
+
+def extra_noisy_batch(qs, torch):
+    """4096 noisy circuits of 1-6 qubits (PTM kernel): probabilities, log-likelihood, gradient."""
+    import numpy as np
+
+    import workloads as W
+    batch = W.noisy_batch(count=4096, seed=4001)
+    batch.counts = W.synthetic_counts(batch, 1000, seed=4002)
+    dev = qs.NoisyBatchDevice(batch)
+    res = {"workload": "4096 circuits, n~U{1..6}, L~U{1..256}, X90/Y90/CZ/idle + depolarizing + "
+                       "amplitude damping, 1000-shot counts"}
+    # algorithmic flops: 8 per Pauli-vector entry per one-qubit PTM (4 FMA), 1 per CZ permutation entry
+    flops = 0.0
+    for c in range(batch.size):
+        n, ops, _ = batch.circuit(c)
+        D = 4 ** n
+        for code, a, b in ops:
+            if code in (0, 1):
+                flops += 8 * D
+            elif code == 2:
+                flops += D + 2 * 8 * D
+            else:
+                flops += n * 8 * D
+    for grad in (False, True):
+        for _ in range(3):
+            dev.run(grad=grad)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        reps = 5
+        for _ in range(reps):
+            dev.run(grad=grad)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        key = "with_gradient" if grad else "forward"
+        res[key] = {"ms_per_batch": ms, "circuits_per_s": batch.size / (ms * 1e-3)}
+        if not grad:
+            res[key]["fwd_gflops"] = flops / (ms * 1e-3) / 1e9
+            res[key]["alu_frac_of_fp32_peak"] = flops / (ms * 1e-3) / 1e12 / fp32_peak_tflops(2070.0)
+    return res
+
+
+def extra_serving(qs, torch, count=40, seed=5001, rate_hz=None):
+    """Poisson stream of layered Haar+CZ circuits, n~U{8..28}, depth~U{10..200}."""
+    import numpy as np
+
+    import workloads as W
+    stream = W.serving_stream(count, seed=seed, rate_hz=1.0)
+    circuits = [qs.gates_array(W.layered_haar_cz(n, d, seed=cs)) for _, n, d, cs in stream]
+    masks = [(1 << min(n, 10)) - 1 for _, n, _, _ in stream]
+    # one-at-a-time plain per-gate service times (same circuits, sequential)
+    service = []
+    for (_, n, _, _), g, m in zip(stream, circuits, masks):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = qs.State(n, qs.QS_C64)
+        qs.sv_apply_circuit(st, g, qs.METHOD_PLAIN)
+        qs.sv_probs(st, fp64=True, marg_mask=m if n > 10 else 0)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+        st.close()
+    cap = count / sum(service)
+    # fused server: warm up, then the stream at ~80% of the fused server's capacity
+    srv = qs.Server()
+    t0 = time.perf_counter()
+    for (_, n, _, _), g, m in zip(stream, circuits, masks):
+        srv.wait(srv.submit(n, g, m))
+    fused_cap = count / (time.perf_counter() - t0)
+    srv.close()
+    rate = rate_hz or 0.8 * fused_cap
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=count)
+    srv = qs.Server()
+    tickets = []
+    t_start = time.perf_counter()
+    arrivals = []
+    for i, ((_, n, _, _), g, m) in enumerate(zip(stream, circuits, masks)):
+        target = t_start + float(np.sum(gaps[: i + 1]))
+        while time.perf_counter() < target:
+            time.sleep(min(0.0005, max(0.0, target - time.perf_counter())))
+        arrivals.append(time.perf_counter() - t_start)
+        tickets.append(srv.submit(n, g, m))
+    lats = [srv.wait(t)[1] for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    # one-at-a-time plain server under the same arrivals (FIFO queue, measured service times)
+    done, plain_lat = 0.0, []
+    for a, s in zip(arrivals, service):
+        done = max(done, a) + s
+        plain_lat.append(1e3 * (done - a))
+    return {"workload": f"{count} Poisson arrivals at {rate:.1f}/s (80% of fused capacity), "
+                        f"n~U{{8..28}}, depth~U{{10..200}}, complex64, marginal over <=10 qubits",
+            "circuits_per_s": stats["circuits_per_s"], "p50_ms": stats["p50_ms"],
+            "p99_ms": stats["p99_ms"], "packed_launches": stats["packed_launches"],
+            "packed_circuits": stats["packed_circuits"], "large_circuits": stats["large_circuits"],
+            "plain_one_at_a_time": {"capacity_circuits_per_s": cap,
+                                    "p50_ms": float(np.percentile(plain_lat, 50)),
+                                    "p99_ms": float(np.percentile(plain_lat, 99))},
+            "fused_capacity_circuits_per_s": fused_cap}
 
 
 def main():
@@ -316,6 +449,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other rows' measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
