@@ -98,8 +98,16 @@ typedef struct {
 typedef struct qs_state_s* qs_state_t;
 
 typedef enum {
-  QS_METHOD_TILED = 0,  /* fused shared-memory tile passes (default) */
-  QS_METHOD_PLAIN = 1   /* one kernel launch per gate (comparison baseline) */
+  QS_METHOD_TILED = 0,       /* fused shared-memory tile passes (default) */
+  QS_METHOD_PLAIN = 1,       /* one kernel launch per gate (comparison baseline) */
+  /* gates fused into dense 5-qubit blocks (32x32 unitaries, products of the
+   * circuit's gates), each applied as a complex GEMM on the tensor cores
+   * (tcgen05) in split precision: operands = hi + lo parts, product
+   * A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation.  complex64 states
+   * with n >= 12 only (QS_EUNSUPPORTED otherwise); synchronous (the call
+   * checks the kernels' bounded-wait status word). */
+  QS_METHOD_BLOCKS_TF32 = 2, /* TF32 hi/lo split */
+  QS_METHOD_BLOCKS_BF16 = 3  /* BF16 hi/lo split (faster operands, ~1e-5 relative per block) */
 } qs_method;
 
 typedef struct {
@@ -125,7 +133,7 @@ typedef struct {
                               8 per diagonal op, 32 per two-qubit dense op */
   int64_t upload_bytes;    /* op descriptors copied host -> device */
   int64_t tile_launches;   /* launches of the tile-pass kernel */
-  double kernel_ms[4];     /* with QS_OPT_TIME_KERNELS: tile, plain, remap, small-state */
+  double kernel_ms[5];     /* with QS_OPT_TIME_KERNELS: tile, plain, remap, small-state, block GEMM */
   double tile_flops;       /* algorithmic flops of the tile-pass launches */
 } qs_stats;
 
@@ -292,8 +300,8 @@ qs_status qs_probs_noalloc(const void* amps, int n, int prec, void* out, int out
 /* Between qs_profile_begin and qs_profile_end every state-vector launch of
  * this library is bracketed by CUDA events recorded on its stream (no
  * synchronisation).  qs_profile_end synchronises those events and returns,
- * per kind (0 tile pass, 1 plain per-gate, 2 remap, 3 small state), the
- * summed device milliseconds and launch counts (HOST arrays of 4, may be
+ * per kind (0 tile pass, 1 plain per-gate, 2 remap, 3 small state, 4 block GEMM), the
+ * summed device milliseconds and launch counts (HOST arrays of 5, may be
  * NULL).  One session per process at a time. */
 qs_status qs_profile_begin(void);
 qs_status qs_profile_end(double* kernel_ms, int64_t* launches);

@@ -351,6 +351,55 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
   return QS_OK;
 }
 
+// Dense 5-qubit blocks on the tensor cores: one pass per block.
+qs_status run_blocks(State* st, const qs_gate* gates, size_t ngates, int mode, qs_stats* stats,
+                     KernelTimer& tm) {
+  std::vector<Block> blocks;
+  plan_blocks(gates, ngates, st->n, blocks);
+  std::vector<unsigned char> blob(16, 0);   // status word of the bounded waits
+  std::vector<BlockPass> passes(blocks.size());
+  for (size_t i = 0; i < blocks.size(); ++i) block_pass_desc(st->n, blocks[i].q, passes[i]);
+  const size_t off_pass = put(blob, passes.data(), passes.size());
+  const size_t bb = block_b_bytes(mode);
+  const size_t off_b = align16(blob.size());
+  blob.resize(off_b + bb * blocks.size());
+  std::vector<unsigned char> tmp;
+  for (size_t i = 0; i < blocks.size(); ++i) {
+    block_b_operand(blocks[i].U.data(), mode, tmp);
+    std::memcpy(blob.data() + off_b + i * bb, tmp.data(), bb);
+  }
+  qs_status s = upload(st, blob);
+  if (s != QS_OK) return s;
+  unsigned char* dev = (unsigned char*)st->opbuf;
+  int* status_dev = (int*)dev;
+  for (size_t i = 0; i < blocks.size(); ++i) {
+    tm.before(4);
+    s = launch_block_pass(st, dev + off_pass + i * sizeof(BlockPass), dev + off_b + i * bb, mode,
+                          status_dev);
+    tm.after();
+    if (s != QS_OK) return s;
+  }
+  int status = 0;
+  QS_CUDA(cudaMemcpyAsync(&status, status_dev, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+  QS_CUDA(cudaStreamSynchronize(st->stream));
+  if (status != 0) {
+    set_error("block GEMM kernel: bounded wait on the tensor-core barrier gave up");
+    return QS_ETIMEOUT;
+  }
+  if (stats) {
+    int64_t g = 0;
+    for (const Block& b : blocks) g += b.ngates;
+    stats->ops_fused = (int64_t)blocks.size();
+    stats->passes = (int64_t)blocks.size();
+    stats->launches = (int64_t)blocks.size();
+    // 32 complex MACs per amplitude per block = 256 flops (the split precision triples the MMAs)
+    stats->flops = 256.0 * std::ldexp(1.0, st->n) * (double)blocks.size();
+    stats->upload_bytes = (int64_t)blob.size();
+    (void)g;
+  }
+  return QS_OK;
+}
+
 qs_status check_state(qs_state_t st) {
   if (!st) {
     set_error("state is NULL");
@@ -364,9 +413,14 @@ qs_status check_state(qs_state_t st) {
 qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats,
                       int flags) {
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  if (method != QS_METHOD_TILED && method != QS_METHOD_PLAIN) {
+  if (method < QS_METHOD_TILED || method > QS_METHOD_BLOCKS_BF16) {
     set_error("unknown method %d", method);
     return QS_EINVAL;
+  }
+  const bool blocks = method == QS_METHOD_BLOCKS_TF32 || method == QS_METHOD_BLOCKS_BF16;
+  if (blocks && (st->prec != QS_C64 || st->n < kTileBits)) {
+    set_error("the tensor-core block method needs a complex64 state of at least %d qubits", kTileBits);
+    return QS_EUNSUPPORTED;
   }
   if (ngates == 0) return QS_OK;
   std::vector<FOp> fops;
@@ -376,7 +430,9 @@ qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method
   tm.on = (flags & QS_OPT_TIME_KERNELS) != 0;
   tm.stream = st->stream;
   qs_status s;
-  if (method == QS_METHOD_PLAIN) {
+  if (blocks) {
+    s = run_blocks(st, gates, ngates, method == QS_METHOD_BLOCKS_TF32 ? 0 : 1, stats, tm);
+  } else if (method == QS_METHOD_PLAIN) {
     build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/false, /*relabel=*/false);
     s = c64 ? run_plain<float>(st, fops, stats, tm) : run_plain<double>(st, fops, stats, tm);
   } else if (st->n < kTileBits) {
@@ -617,8 +673,8 @@ qs_status qs_profile_end(double* kernel_ms, int64_t* launches) {
     return QS_EINVAL;
   }
   ps.active = false;
-  double ms[4] = {0, 0, 0, 0};
-  int64_t cnt[4] = {0, 0, 0, 0};
+  double ms[5] = {0, 0, 0, 0, 0};
+  int64_t cnt[5] = {0, 0, 0, 0, 0};
   qs_status s = QS_OK;
   for (size_t i = 0; i < ps.kind.size(); ++i) {
     cudaEvent_t a = ps.ev[2 * i], b = ps.ev[2 * i + 1];
@@ -635,7 +691,7 @@ qs_status qs_profile_end(double* kernel_ms, int64_t* launches) {
   }
   ps.ev.clear();
   ps.kind.clear();
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     if (kernel_ms) kernel_ms[k] = ms[k];
     if (launches) launches[k] = cnt[k];
   }

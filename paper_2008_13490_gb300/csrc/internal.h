@@ -180,6 +180,33 @@ struct Plan {
 void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vmap_final,
                   Plan& plan);
 
+// ---------------------------------------------------------------- 5-qubit blocks (block_tc.cu)
+struct Block {
+  int q[5];              // qubits (bit positions); q[i] is bit i of the block's local index
+  std::vector<cd> U;     // 32x32 row-major, U[out][in]
+  int ngates = 0;
+};
+// Greedy frontier fusion of the circuit into 5-qubit blocks (n >= 5).
+void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>& out);
+// Tile of a block pass: 12 positions = 5 block qubits + 7 row qubits; the
+// tables map an element's "address-order" index (its 12 tile bits sorted by
+// physical position, split 6 + 6) to its address offset, row m and column c.
+struct BlockPass {
+  uint64_t addr_lo[64];
+  uint64_t addr_hi[64];
+  uint8_t m_lo[64], m_hi[64];
+  uint8_t c_lo[64], c_hi[64];
+  uint8_t nt_pos[48];           // physical positions outside the tile (ascending)
+  int32_t n_nt;
+  int32_t pad[3];
+};
+void block_pass_desc(int n, const int* bpos, BlockPass& P);
+size_t block_pass_bytes();
+void block_b_operand(const cd* U, int mode, std::vector<unsigned char>& out);
+size_t block_b_bytes(int mode);
+qs_status launch_block_pass(State* st, const void* pass_dev, const void* b_dev, int mode,
+                            int* status_dev);
+
 // Applies gates to a state (the body of sv_apply_circuit; api.cpp).
 qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats,
                       int flags = 0);
