@@ -46,7 +46,7 @@ class _Stats(ctypes.Structure):
                 ("passes", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("bytes_moved", ctypes.c_double), ("flops", ctypes.c_double),
                 ("upload_bytes", ctypes.c_int64), ("tile_launches", ctypes.c_int64),
-                ("kernel_ms", ctypes.c_double * 4), ("tile_flops", ctypes.c_double)]
+                ("kernel_ms", ctypes.c_double * 5), ("tile_flops", ctypes.c_double)]
 
 
 class _Opts(ctypes.Structure):
@@ -208,11 +208,11 @@ def qs_profile_begin():
 
 
 def qs_profile_end():
-    """Returns ({kind: ms}, {kind: launches}) for kinds tile, plain, remap, small."""
-    ms = (ctypes.c_double * 4)()
-    cnt = (ctypes.c_int64 * 4)()
+    """Returns ({kind: ms}, {kind: launches}) for kinds tile, plain, remap, small, block."""
+    ms = (ctypes.c_double * 5)()
+    cnt = (ctypes.c_int64 * 5)()
     _check(load().qs_profile_end(ms, cnt))
-    kinds = ("tile", "plain", "remap", "small")
+    kinds = ("tile", "plain", "remap", "small", "block")
     return dict(zip(kinds, list(ms))), dict(zip(kinds, list(cnt)))
 
 

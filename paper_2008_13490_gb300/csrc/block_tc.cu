@@ -118,6 +118,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
   uint32_t r[64];
   asm volatile(
@@ -190,7 +207,7 @@ __global__ void __launch_bounds__(kBlkThreads)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
                      smem_u32(&tmem_base_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -206,14 +223,21 @@ __global__ void __launch_bounds__(kBlkThreads)
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     uint64_t base = 0;
     for (int j = 0; j < s_nnt; ++j) base |= ((tile >> j) & 1ull) << s_nt[j];
-    // ---- load (consecutive threads = consecutive low physical bits) and split
-#pragma unroll 4
+    // ---- load (consecutive threads = consecutive low physical bits; all 32
+    // loads in flight before the first use) and split
+    float2 ld[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int e = i * kBlkThreads + tid;
+      ld[i] = __ldcs(psi + (base | s_addr_lo[e & 63] | s_addr_hi[e >> 6]));
+    }
+#pragma unroll
     for (int i = 0; i < 32; ++i) {
       const int e = i * kBlkThreads + tid;
       const int lo = e & 63, hi = e >> 6;
       const int m = s_m_lo[lo] | s_m_hi[hi];
       const int c = s_c_lo[lo] | s_c_hi[hi];
-      const float2 a = __ldcs(psi + (base | s_addr_lo[lo] | s_addr_hi[hi]));
+      const float2 a = ld[i];
       if (MODE == BM_TF32) {
         const uint32_t hx = tf32_rna(a.x), hy = tf32_rna(a.y);
         const uint32_t lx = tf32_rna(a.x - __uint_as_float(hx)), ly = tf32_rna(a.y - __uint_as_float(hy));
@@ -236,24 +260,30 @@ __global__ void __launch_bounds__(kBlkThreads)
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    // ---- MMAs: D = A_hi B_hi + A_hi B_lo + A_lo B_hi
+    // ---- MMAs into three FP32 accumulators: D1a / D1b = A_hi B_hi over the low /
+    // high half of K (columns 0..63 / 128..191) and D2 = A_lo B_lo + A_hi B_lo +
+    // A_lo B_hi (columns 64..127, smallest first).  The large product is summed
+    // in short chains, so accumulator rounding adds few steps to it.
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a_hi = smem_u32(A_hi), a_lo = smem_u32(A_lo);
       const uint32_t b_hi = smem_u32(B_hi), b_lo = smem_u32(B_lo);
       constexpr int ksteps = 64 / O::kKStep;
       constexpr uint32_t kstep_bytes = 256;   // two K-adjacent core matrices
-      uint32_t acc = 0;
-      for (int p = 0; p < 3; ++p) {
-        const uint32_t a = p == 2 ? a_lo : a_hi;
-        const uint32_t b = p == 1 ? b_lo : b_hi;
-        for (int ks = 0; ks < ksteps; ++ks) {
-          const uint64_t da = make_desc(a + ks * kstep_bytes, 128, O::kSBO_A);
-          const uint64_t db = make_desc(b + ks * kstep_bytes, 128, O::kSBO_A);   // same K = 64
-          mma<MODE>(tmem_d, da, db, idesc, acc);
-          acc = 1;
-        }
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const uint32_t d = ks < ksteps / 2 ? tmem_d : tmem_d + 128;
+        const uint64_t da = make_desc(a_hi + ks * kstep_bytes, 128, O::kSBO_A);
+        const uint64_t db = make_desc(b_hi + ks * kstep_bytes, 128, O::kSBO_A);   // same K = 64
+        mma<MODE>(d, da, db, idesc, (ks % (ksteps / 2)) ? 1u : 0u);
       }
+      const uint32_t pa[3] = {a_lo, a_hi, a_lo};
+      const uint32_t pb[3] = {b_lo, b_lo, b_hi};
+      for (int p = 0; p < 3; ++p)
+        for (int ks = 0; ks < ksteps; ++ks) {
+          const uint64_t da = make_desc(pa[p] + ks * kstep_bytes, 128, O::kSBO_A);
+          const uint64_t db = make_desc(pb[p] + ks * kstep_bytes, 128, O::kSBO_A);
+          mma<MODE>(tmem_d + 64, da, db, idesc, (p > 0 || ks > 0) ? 1u : 0u);
+        }
       mma_commit(smem_u32(&mbar));
     }
     // ---- wait (bounded) for the MMAs
@@ -269,13 +299,24 @@ __global__ void __launch_bounds__(kBlkThreads)
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- D row (thread = row m) -> staging in shared memory
-    float d[64];
-    tmem_ld64(tmem_d + ((uint32_t)(warp * 32) << 16), d);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    // ---- D = D1 + D2, row per thread -> staging in shared memory
     const int m = tid;
+    const uint32_t lane_base = tmem_d + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-    for (int r = 0; r < 32; ++r) stage[m * 32 + (r ^ (m & 31))] = make_float2(d[2 * r], d[2 * r + 1]);
+    for (int h = 0; h < 2; ++h) {
+      float d1[32], d2[32];
+      tmem_ld32(lane_base + 32 * h, d1);
+      tmem_ld32(lane_base + 64 + 32 * h, d2);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) d2[j] += d1[j];    // corrections + low-K half
+      tmem_ld32(lane_base + 128 + 32 * h, d1);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int r = 16 * h + j;
+        stage[m * 32 + (r ^ (m & 31))] = make_float2(d1[2 * j] + d2[2 * j], d1[2 * j + 1] + d2[2 * j + 1]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     // ---- store in the load order
 #pragma unroll 4
@@ -291,7 +332,7 @@ __global__ void __launch_bounds__(kBlkThreads)
   if (failed && tid == 0) atomicExch(status, (int)QS_ETIMEOUT);
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem_d) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem_d) : "memory");
 }
 
 // ---------------------------------------------------------------- host side
@@ -434,22 +475,24 @@ qs_status launch_block_pass(State* st, const void* pass_dev, const void* b_dev, 
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  size_t smem;
+  // Each CTA holds 256 tensor-memory columns (three 64-column accumulators), so
+  // at most 2 CTAs may share an SM (512 columns): the dynamic shared memory is
+  // sized to enforce that residency limit, and the grid is 2 CTAs per SM.
+  constexpr size_t kTwoPerSm = 96 * 1024;
+  uint64_t grid = (uint64_t)sms * 2;
+  if (grid > ntiles) grid = ntiles;
   if (mode == BM_TF32) {
-    smem = 2 * BOps<BM_TF32>::kA + 2 * BOps<BM_TF32>::kB;
+    size_t smem = 2 * BOps<BM_TF32>::kA + 2 * BOps<BM_TF32>::kB;
+    if (smem < kTwoPerSm) smem = kTwoPerSm;
     QS_CUDA(cudaFuncSetAttribute(block_gemm_kernel<BM_TF32>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    uint64_t grid = (uint64_t)sms * 2;
-    if (grid > ntiles) grid = ntiles;
     block_gemm_kernel<BM_TF32><<<(unsigned)grid, kBlkThreads, smem, st->stream>>>(
         (float2*)st->data, (const BlockPass*)pass_dev, (const unsigned char*)b_dev, ntiles, status_dev);
   } else {
-    smem = 2 * BOps<BM_BF16>::kA + 2 * BOps<BM_BF16>::kB;
-    if (smem < 32 * 1024) smem = 32 * 1024;   // staging reuses the A region
+    size_t smem = 2 * BOps<BM_BF16>::kA + 2 * BOps<BM_BF16>::kB;
+    if (smem < kTwoPerSm) smem = kTwoPerSm;   // also covers the 32 KiB staging
     QS_CUDA(cudaFuncSetAttribute(block_gemm_kernel<BM_BF16>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    uint64_t grid = (uint64_t)sms * 3;
-    if (grid > ntiles) grid = ntiles;
     block_gemm_kernel<BM_BF16><<<(unsigned)grid, kBlkThreads, smem, st->stream>>>(
         (float2*)st->data, (const BlockPass*)pass_dev, (const unsigned char*)b_dev, ntiles, status_dev);
   }
