@@ -2,6 +2,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 
@@ -296,14 +297,8 @@ template <typename R>
 qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<int>& vmap,
                     qs_stats* stats, KernelTimer& tm) {
   Plan pl;
-  plan_circuit(fops, st->n, vmap, pl);
-  std::vector<TileOp<R>> tops;
-  tops.reserve(pl.tile_fops.size());
-  for (size_t i = 0; i < pl.tile_fops.size(); ++i) tops.push_back(to_tile<R>(pl, i));
+  plan_circuit(fops, st->n, vmap, pl, TileLimits<R>::kMaxOps, kMaxTileStages);
   std::vector<unsigned char> blob;
-  const size_t off_pass = put(blob, pl.passes.data(), pl.passes.size());
-  const size_t off_stage = put(blob, pl.stages.data(), pl.stages.size());
-  const size_t off_ops = put(blob, tops.data(), tops.size());
   const size_t off_remap = put(blob, pl.remaps.data(), pl.remaps.size());
   qs_status s = upload(st, blob);
   if (s != QS_OK) return s;
@@ -312,14 +307,28 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
   const double N = std::ldexp(1.0, st->n);
   double tile_flops = 0.0, plain_flops = 0.0;
   for (const FOp& o : pl.tile_fops) tile_flops += op_flops_per_amp(o) * N;
+  // kernel-parameter image of one pass (stage op ranges relative to the pass)
+  std::unique_ptr<TileParams<R>> tp(new TileParams<R>());
   for (const PlanStep& step : pl.steps) {
     switch (step.kind) {
-      case PlanStep::TILE:
+      case PlanStep::TILE: {
+        const TilePass& pass = pl.passes[step.index];
+        std::memset(tp.get(), 0, sizeof(TileParams<R>));
+        tp->pass = pass;
+        const int op0 = pl.stages[pass.stage_begin].op_begin;
+        for (int s2 = 0; s2 < pass.n_stages; ++s2) {
+          TileStage ts = pl.stages[pass.stage_begin + s2];
+          for (int o = ts.op_begin; o < ts.op_end; ++o) tp->ops[o - op0] = to_tile<R>(pl, (size_t)o);
+          ts.op_begin -= op0;
+          ts.op_end -= op0;
+          tp->stages[s2] = ts;
+        }
+        tp->pass.stage_begin = 0;
         tm.before(0);
-        s = launch_tile_pass(st, dev + off_pass + sizeof(TilePass) * step.index, dev + off_stage,
-                             dev + off_ops, pl.passes[step.index].n_stages);
+        s = launch_tile_pass(st, tp.get());
         ++tile_launches;
         break;
+      }
       case PlanStep::PLAIN: {
         PlainOp<R> p = to_plain<R>(pl.plain_fops[step.index]);
         plain_flops += op_flops_per_amp(pl.plain_fops[step.index]) * N;

@@ -137,6 +137,21 @@ struct TilePass {
   uint8_t nt_pos[48];           // physical bits outside the tile (ascending)
 };
 
+// Everything one tile-pass launch reads, passed by value as a kernel parameter
+// (constant bank; < 32 KiB): the pass, its stages (op ranges relative to the
+// pass) and its ops.  The planner keeps passes within these limits.
+constexpr int kMaxTileStages = 48;
+template <typename R>
+struct TileLimits {
+  static constexpr int kMaxOps = sizeof(R) == 4 ? 352 : 196;
+};
+template <typename R>
+struct TileParams {
+  TilePass pass;
+  TileStage stages[kMaxTileStages];
+  TileOp<R> ops[TileLimits<R>::kMaxOps];
+};
+
 // Device-side plain op (one launch per op; also the small-state kernel's op).
 template <typename R>
 struct alignas(16) PlainOp {
@@ -178,7 +193,7 @@ struct Plan {
 // virtual -> physical (updated by remaps); final layout is canonical
 // (physical position q holds logical qubit q).
 void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vmap_final,
-                  Plan& plan);
+                  Plan& plan, int max_ops_per_pass, int max_stages_per_pass);
 
 // ---------------------------------------------------------------- 5-qubit blocks (block_tc.cu)
 struct Block {
@@ -214,8 +229,8 @@ qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method
 // ---------------------------------------------------------------- launchers
 // (sv_kernels.cu)
 qs_status launch_set_basis(State* st, uint64_t J);
-qs_status launch_tile_pass(State* st, const void* pass_dev, const void* stages_dev,
-                           const void* ops_dev, int n_stages);
+// params: host pointer to a TileParams<float> / TileParams<double> (by value to the kernel)
+qs_status launch_tile_pass(State* st, const void* params);
 qs_status launch_plain_op(State* st, const void* op_dev, int type);
 qs_status launch_small(State* st, const void* ops_dev, int nops);
 qs_status launch_remap(State* st, const void* desc_dev, void* tmp);

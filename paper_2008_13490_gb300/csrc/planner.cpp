@@ -328,7 +328,7 @@ int popc(uint64_t x) { return __builtin_popcountll(x); }
 }  // namespace
 
 void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vmap_final,
-                  Plan& plan) {
+                  Plan& plan, int max_ops_per_pass, int max_stages_per_pass) {
   plan = Plan{};
   std::vector<int> l2p(n), p2l(n);
   for (int q = 0; q < n; ++q) l2p[q] = p2l[q] = q;
@@ -360,7 +360,7 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
       const FOp& o = ops[idx];
       uint64_t ndq = nd_mask(o), dq = d_mask(o);
       bool conflict = (ndq & (nd_blk | d_blk)) || (dq & nd_blk);
-      if (!conflict && o.type != F_G2) {
+      if (!conflict && o.type != F_G2 && (int)sel.size() < max_ops_per_pass) {
         uint64_t need = ndq & ~T;
         if (popc(T | need) <= kTileBits) {
           T |= need;
@@ -400,6 +400,13 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
     // ---- stages
     std::vector<int> pending = sel;
     while (!pending.empty()) {
+      if ((int)plan.stages.size() - tp.stage_begin >= max_stages_per_pass) {
+        // stage budget of the pass used up: the rest waits for the next pass
+        // (merging by op index keeps program order)
+        rest.insert(rest.end(), pending.begin(), pending.end());
+        std::sort(rest.begin(), rest.end());
+        break;
+      }
       int R[kRegBits];
       int nR = 0;
       uint64_t snd = 0, sd = 0;

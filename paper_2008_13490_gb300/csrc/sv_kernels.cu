@@ -157,8 +157,7 @@ __device__ __forceinline__ void apply_tile_op(C2<R>* v, const TileOp<R>* __restr
 
 template <typename R>
 __global__ void __launch_bounds__(kTileThreads)
-    tile_pass_kernel(C2<R>* __restrict__ psi, const TilePass* __restrict__ P,
-                     const TileStage* __restrict__ stages, const TileOp<R>* __restrict__ ops) {
+    tile_pass_kernel(C2<R>* __restrict__ psi, const __grid_constant__ TileParams<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<R>* sm = reinterpret_cast<C2<R>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -167,12 +166,12 @@ __global__ void __launch_bounds__(kTileThreads)
   __shared__ uint8_t s_pos[kTileBits];
   __shared__ uint64_t s_base;
   if (tid == 0) {
-    const int n_nt = P->n_nt;
+    const int n_nt = P.pass.n_nt;
     uint64_t base = 0;
-    for (int j = 0; j < n_nt; ++j) base |= ((tile >> j) & 1ull) << P->nt_pos[j];
+    for (int j = 0; j < n_nt; ++j) base |= ((tile >> j) & 1ull) << P.pass.nt_pos[j];
     s_base = base;
   }
-  if (tid < kTileBits) s_pos[tid] = P->pos[tid];
+  if (tid < kTileBits) s_pos[tid] = P.pass.pos[tid];
   __syncthreads();
   const uint64_t base = s_base;
   uint64_t loff = 0;
@@ -180,8 +179,9 @@ __global__ void __launch_bounds__(kTileThreads)
   for (int k = 0; k < kLaneBits; ++k)
     if ((lane >> k) & 1) loff |= 1ull << s_pos[k];
 
-  const int nst = P->n_stages;
-  const TileStage* __restrict__ S = stages + P->stage_begin;
+  const int nst = P.pass.n_stages;
+  const TileStage* __restrict__ S = P.stages;
+  const TileOp<R>* __restrict__ ops = P.ops;
   C2<R> v[16];
   {
     const TileStage s0 = S[0];
@@ -515,21 +515,18 @@ qs_status launch_set_basis(State* st, uint64_t J) {
   return QS_OK;
 }
 
-qs_status launch_tile_pass(State* st, const void* pass_dev, const void* stages_dev,
-                           const void* ops_dev, int /*n_stages*/) {
+qs_status launch_tile_pass(State* st, const void* params) {
   const uint64_t tiles = 1ull << (st->n - kTileBits);
   if (st->prec == QS_C64) {
     const size_t smem = sizeof(C2<float>) << kTileBits;
     tile_pass_kernel<float><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
-        (C2<float>*)st->data, (const TilePass*)pass_dev, (const TileStage*)stages_dev,
-        (const TileOp<float>*)ops_dev);
+        (C2<float>*)st->data, *(const TileParams<float>*)params);
   } else {
     const size_t smem = sizeof(C2<double>) << kTileBits;
     qs_status s = set_smem(tile_pass_kernel<double>, smem);
     if (s != QS_OK) return s;
     tile_pass_kernel<double><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
-        (C2<double>*)st->data, (const TilePass*)pass_dev, (const TileStage*)stages_dev,
-        (const TileOp<double>*)ops_dev);
+        (C2<double>*)st->data, *(const TileParams<double>*)params);
   }
   QS_CUDA(cudaGetLastError());
   return QS_OK;
