@@ -207,9 +207,12 @@ def run_ours(args, world, rank, local):
     probs = torch.empty(1 << n, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    method = {"tiled": qs.METHOD_TILED, "plain": qs.METHOD_PLAIN,
+              "blocks_tf32": qs.METHOD_BLOCKS_TF32, "blocks_bf16": qs.METHOD_BLOCKS_BF16}[args.method]
+
     def step():
         qs.sv_set_basis(st, 0)
-        s = qs.sv_apply_circuit(st, arr)
+        s = qs.sv_apply_circuit(st, arr, method)
         qs.sv_probs(st, out=probs, want_norm=False)
         return s
 
@@ -307,7 +310,8 @@ def run_ours(args, world, rank, local):
     if not args.no_extras:
         line["rows"] = {"small_circuits": extra_small_circuits(qs, torch),
                         "noisy_batch": extra_noisy_batch(qs, torch),
-                        "serving": extra_serving(qs, torch)}
+                        "serving": extra_serving(qs, torch),
+                        "fused_blocks": extra_fused_blocks(qs, torch)}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_block()
     print(json.dumps(line), flush=True)
@@ -383,6 +387,43 @@ def extra_noisy_batch(qs, torch):
     return res
 
 
+def extra_fused_blocks(qs, torch, n=32, layers=60, seed=3001):
+    """32-qubit complex64, depth-60 Haar + brickwork CZ fused into 5-qubit blocks on the
+    tensor cores (TF32 and BF16 splits), beside the tiled FP32 path on the same state."""
+    import workloads as W
+    ops = qs.gates_array(W.layered_haar_cz(n, layers, seed=seed))
+    st = qs.State(n, qs.QS_C64)
+    warm = qs.State(14, qs.QS_C64)
+    out = {"workload": f"{n}-qubit complex64 ({8 << (n - 30)} GiB), {layers} layers Haar + brickwork CZ "
+                       f"({len(ops)} gates, seed {seed})",
+           "error_vs_fp64_oracle_at_20_qubits": {"tf32": 1.26e-5, "bf16": 4.22e-5,
+                                                 "source": "tests/test_gpu_blocks.py (depth 60, seed 3002)"}}
+    tf32_peak = 1926.3 / 2   # TF32 dense = half the measured BF16 rate (nominal ratio)
+    bf16_peak = 1926.3
+    for name, method in (("tf32", qs.METHOD_BLOCKS_TF32), ("bf16", qs.METHOD_BLOCKS_BF16),
+                         ("tiled_fp32", qs.METHOD_TILED)):
+        qs.sv_apply_circuit(warm, qs.gates_array(W.layered_haar_cz(14, 2, seed=1)), method)
+        qs.sv_set_basis(st, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = qs.sv_apply_circuit(st, ops, method, time_kernels=True)
+        dt = time.perf_counter() - t0
+        kms = sum(s["kernel_ms"])
+        row = {"s_per_circuit": dt, "passes": s["passes"], "kernel_ms": kms,
+               "gates_per_s": len(ops) / dt,
+               "hbm_gbs_per_pass": s["passes"] * 2 * 8 * (1 << n) / (kms * 1e-3) / 1e9}
+        if method in (qs.METHOD_BLOCKS_TF32, qs.METHOD_BLOCKS_BF16):
+            # tensor work: 4 split products of a [2^n/32 x 64] x [64 x 64] real GEMM per block
+            tflops = s["passes"] * 4 * 2 * (1 << n) * 2 * 64 / (kms * 1e-3) / 1e12
+            peak = tf32_peak if method == qs.METHOD_BLOCKS_TF32 else bf16_peak
+            row["tensor_tflops"] = tflops
+            row["tensor_frac"] = tflops / peak
+        out[name] = row
+    warm.close()
+    st.close()
+    return out
+
+
 def extra_serving(qs, torch, count=40, seed=5001, rate_hz=None):
     """Poisson stream of layered Haar+CZ circuits, n~U{8..28}, depth~U{10..200}."""
     import numpy as np
@@ -450,7 +491,20 @@ def main():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other rows' measurements")
+    ap.add_argument("--method", default="tiled", choices=["tiled", "plain", "blocks_tf32", "blocks_bf16"],
+                    help="state-vector method of the timed workload (the default line uses tiled)")
+    ap.add_argument("--only", default=None, choices=["dm", "serve", "blocks", "small"],
+                    help="run one extra row alone (for profiling) and print it")
     args = ap.parse_args()
+    if args.only:
+        import torch
+
+        import paper_2008_13490_gb300 as qs
+        qs.load()
+        fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
+              "small": extra_small_circuits}[args.only]
+        print(json.dumps({"only": args.only, "row": fn(qs, torch)}), flush=True)
+        return 0
     world, rank, local = dist_setup()
     if args.impl == "reference":
         rc = run_reference(args, world, rank)

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libqsim.so")
 
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
 QS_C64, QS_C128 = 0, 1
-METHOD_TILED, METHOD_PLAIN = 0, 1
+METHOD_TILED, METHOD_PLAIN, METHOD_BLOCKS_TF32, METHOD_BLOCKS_BF16 = 0, 1, 2, 3
 
 KIND = {
     "I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,
