@@ -261,15 +261,31 @@ def run_ours(args, world, rank, local):
         return 0
 
     peaks, peak_src = measured_peaks()
-    # roofline of the dominant kernel (tile pass): FP32-ALU bound
-    tile_ms = kms["tile"] / max(1, kcnt["tile"])
-    tile_flops = stats["tile_flops"] / max(1, stats["tile_launches"])
-    achieved_tflops = tile_flops / (tile_ms * 1e-3) / 1e12
-    fp32_peak = fp32_peak_tflops(2070.0)
     bytes_per_pass = 2 * (1 << n) * 8
-    hbm_gbs = bytes_per_pass / (tile_ms * 1e-3) / 1e9
+    dominant = max(kms, key=lambda k: kms[k])
+    avg_ms = kms[dominant] / max(1, kcnt[dominant])
+    hbm_gbs = bytes_per_pass / (avg_ms * 1e-3) / 1e9
+    if dominant == "tile":
+        # tile pass: FP32-ALU bound; flops counted per amplitude per fused op
+        per_launch = stats["tile_flops"] / max(1, stats["tile_launches"])
+        roof = {"bound": "alu", "kernel": "tile_pass_kernel<float>", "unit": "TFLOP/s",
+                "peak": fp32_peak_tflops(2070.0),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
+    elif dominant == "block":
+        # block GEMM: 4 split products of [2^n/32 x 64] x [64 x 64] per launch
+        per_launch = 4 * 2 * (1 << n) * 64
+        tf32 = args.method == "blocks_tf32"
+        roof = {"bound": "tensor", "kernel": "block_gemm_kernel<%s>" % ("TF32" if tf32 else "BF16"),
+                "unit": "TFLOP/s", "peak": peaks["bf16_tflops"] / (2 if tf32 else 1),
+                "peak_source": "measured bf16 burst" + (" / 2 (TF32 nominal ratio)" if tf32 else "")}
+    else:
+        per_launch = bytes_per_pass * 1e-12 * 1e12
+        roof = {"bound": "hbm", "kernel": dominant, "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                "peak_source": "measured copy bandwidth"}
+    scale = 1e9 if roof["unit"] == "GB/s" else 1e12
+    achieved = per_launch / (avg_ms * 1e-3) / scale
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "tile_pass_traffic.json")
+    prof = os.path.join(ROOT, "profiles", "tile_pass_kernel_traffic_n30_layered_haar_cz.json")
     if os.path.exists(prof):
         with open(prof) as f:
             tr = json.load(f)
@@ -291,11 +307,9 @@ def run_ours(args, world, rank, local):
         "hbm": {"sweeps_per_s": world * stats["passes"] * args.steps / (ms_max * 1e-3),
                 "tile_pass_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
                 "frac": hbm_gbs / peaks["hbm_gbs"], "bytes_per_pass": bytes_per_pass},
-        "roofline": {"bound": "alu", "kernel": "tile_pass_kernel<float>",
-                     "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / fp32_peak, "traffic": traffic,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-                     "avg_launch_ms": tile_ms, "flops_per_launch": tile_flops},
+        "roofline": dict(roof, achieved=achieved, frac=achieved / roof["peak"],
+                         traffic=traffic if dominant == "tile" else None,
+                         avg_launch_ms=avg_ms, work_per_launch=per_launch),
         "e2e": {"value": world * gates / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(s2["upload_bytes"]) + gates * arr.itemsize,
                 "d2h_bytes_per_step": (1 << n) * 4},
