@@ -367,7 +367,13 @@ qs_status run_blocks(State* st, const qs_gate* gates, size_t ngates, int mode, q
   plan_blocks(gates, ngates, st->n, blocks);
   std::vector<unsigned char> blob(16, 0);   // status word of the bounded waits
   std::vector<BlockPass> passes(blocks.size());
-  for (size_t i = 0; i < blocks.size(); ++i) block_pass_desc(st->n, blocks[i].q, passes[i]);
+  for (size_t i = 0; i < blocks.size(); ++i) {
+    block_pass_desc(st->n, blocks[i].q, passes[i]);
+    if (!block_pass_runs_contiguous(passes[i])) {
+      set_error("block pass: tile layout without contiguous low bits");
+      return QS_EUNSUPPORTED;
+    }
+  }
   const size_t off_pass = put(blob, passes.data(), passes.size());
   const size_t bb = block_b_bytes(mode);
   const size_t off_b = align16(blob.size());

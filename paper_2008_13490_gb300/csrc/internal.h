@@ -216,6 +216,7 @@ struct BlockPass {
   int32_t pad[3];
 };
 void block_pass_desc(int n, const int* bpos, BlockPass& P);
+bool block_pass_runs_contiguous(const BlockPass& P);
 size_t block_pass_bytes();
 void block_b_operand(const cd* U, int mode, std::vector<unsigned char>& out);
 size_t block_b_bytes(int mode);
