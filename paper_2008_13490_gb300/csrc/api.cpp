@@ -369,6 +369,7 @@ qs_status run_blocks(State* st, const qs_gate* gates, size_t ngates, int mode, q
   std::vector<BlockPass> passes(blocks.size());
   for (size_t i = 0; i < blocks.size(); ++i) {
     block_pass_desc(st->n, blocks[i].q, passes[i]);
+    if (block_is_unitary(blocks[i].U.data())) passes[i].flags |= 1;
     if (!block_pass_runs_contiguous(passes[i])) {
       set_error("block pass: tile layout without contiguous low bits");
       return QS_EUNSUPPORTED;

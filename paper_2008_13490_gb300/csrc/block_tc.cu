@@ -8,14 +8,14 @@
 // GEMM  D[128 x 64] = A[128 x 64] . B^T, A = (Re x_c, Im x_c) interleaved,
 // B[n][k] = the real 64x64 form of U:
 //   B[2r][2c] = Re U_rc,  B[2r][2c+1] = -Im U_rc,  B[2r+1][2c] = Im U_rc,  B[2r+1][2c+1] = Re U_rc.
-// Operands are split into hi + lo parts (TF32 or BF16) and the product is
-// A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in tensor memory.
+// Operands are split into two TF32 or three BF16 parts and the product keeps
+// the part products down to FP32 size, accumulated in FP32 in tensor memory.
 //
-// Per tile (persistent CTAs, one per SM, the three stages overlapped over
-// consecutive tiles by warp specialisation, see the kernel):
-//   global -> registers (coalesced order) -> split -> shared memory (K-major,
-//   no-swizzle core-matrix layout) -> tcgen05.mma x (K/8 or K/16) x 4 -> commit
-//   to an mbarrier -> tcgen05.ld (thread = row) -> shared staging -> global.
+// Per tile (persistent CTAs, one per SM, the stages overlapped over consecutive
+// tiles by warp specialisation, see the kernel):
+//   global -> bulk copy -> shared memory -> split -> shared memory (K-major,
+//   no-swizzle core-matrix layout) -> tcgen05.mma -> commit to an mbarrier ->
+//   tcgen05.ld (thread = row) -> shared staging -> global.
 // Every mbarrier wait is bounded; on timeout the kernel records QS_ETIMEOUT in
 // a status word, frees its tensor memory and returns.
 #include <cuda_bf16.h>
@@ -34,7 +34,11 @@ enum : int { BM_TF32 = 0, BM_BF16 = 1 };
 constexpr int kBlkRows = 128;
 constexpr uint32_t kWaitLimit = 1u << 20;   // mbarrier polls before giving up (well under a second)
 
-// byte sizes of one operand buffer
+// Operand formats.  An FP32 value x is split into parts x = x_0 + x_1 (+ x_2),
+// each rounded to the MMA's input type: TF32 (11 significant bits) in two parts,
+// BF16 (8 significant bits) in three, both keeping about 22-24 bits.  The
+// product A.B keeps the part products down to about 2^-22 (TF32) or 2^-24 (BF16)
+// relative size: A_0 B_0 and kNCorr correction products (a-part, b-part).
 template <int MODE>
 struct BOps;
 template <>
@@ -42,8 +46,10 @@ struct BOps<BM_TF32> {
   static constexpr int kElem = 4;
   static constexpr int kKStep = 8;                 // K per tcgen05.mma (tf32)
   static constexpr int kSBO_A = 2048;              // 8-row group stride of A (K = 64 tf32)
-  static constexpr int kA = kBlkRows * 64 * 4;     // 32 KiB
-  static constexpr int kB = 64 * 64 * 4;           // 16 KiB
+  static constexpr int kA = kBlkRows * 64 * 4;     // one part of A: 32 KiB
+  static constexpr int kB = 64 * 64 * 4;           // one part of B: 16 KiB
+  static constexpr int kParts = 2;
+  static constexpr int kNCorr = 3;                 // (1,1) (0,1) (1,0)
 };
 template <>
 struct BOps<BM_BF16> {
@@ -52,7 +58,18 @@ struct BOps<BM_BF16> {
   static constexpr int kSBO_A = 1024;
   static constexpr int kA = kBlkRows * 64 * 2;     // 16 KiB
   static constexpr int kB = 64 * 64 * 2;           // 8 KiB
+  static constexpr int kParts = 3;
+  static constexpr int kNCorr = 5;                 // (2,0) (0,2) (1,1) (1,0) (0,1)
 };
+// correction product p (smallest first): parts of A and B
+template <int MODE>
+__host__ __device__ constexpr int corr_a(int p) {
+  return MODE == BM_TF32 ? (p == 1 ? 0 : 1) : (p == 0 ? 2 : p == 1 ? 0 : p == 4 ? 0 : 1);
+}
+template <int MODE>
+__host__ __device__ constexpr int corr_b(int p) {
+  return MODE == BM_TF32 ? (p == 2 ? 0 : 1) : (p == 0 ? 0 : p == 1 ? 2 : p == 3 ? 0 : 1);
+}
 
 // byte offset of element (row, k) in a K-major no-swizzle core-matrix layout:
 // core matrices of 8 rows x 16 bytes, K-adjacent cores 128 B apart (LBO),
@@ -135,6 +152,46 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// tcgen05.ld without the wait: several loads share one tcgen05.wait::ld, after
+// which reg_after_wait32 ties the registers to the wait (their uses cannot be
+// scheduled before it)
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void reg_after_wait32(uint32_t* r) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                 "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+                 "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]),
+                 "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]),
+                 "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]),
+                 "+r"(r[31]));
+}
+
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -144,49 +201,49 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 // ---------------------------------------------------------------- kernel
 //
 // One persistent CTA per SM, four roles that overlap consecutive tiles:
-//   warp 9, one thread  loader: bulk-copies tile i into raw stage i % kStages of
-//                       a shared-memory ring.  The 7 lowest physical bits are
-//                       always tile bits (each is a block bit or one of the 7
-//                       lowest others), so a tile is 32 contiguous runs of 128
-//                       amplitudes (1 KiB each).
-//   warps 0-3           producers: thread = row m; split row m of tile i into
-//                       hi/lo parts, write it to operand buffer i % kABuf and
-//                       free the raw stage for the loader
+//   warp 9              loader: lane j bulk-copies run j of tile i into raw stage
+//                       i % kStages of a shared-memory ring.  The 7 lowest
+//                       physical bits are always tile bits (each is a block bit
+//                       or one of the 7 lowest others), so a tile is 32
+//                       contiguous runs of 128 amplitudes (1 KiB each).
+//   warps 0-3           producers: thread = row m; split row m of tile i into its
+//                       parts, write them to the operand buffer, note the row's
+//                       squared norm and free the raw stage for the loader
 //   warp 8, one thread  MMA issuer: products of tile i into accumulator set i % 2
 //   warps 4-7           epilogue: thread = row m = tensor-memory lane (warp w
-//                       reads lanes 32*(w%4)..); add the partial sums, stage the
-//                       rows in shared memory, store them to global memory in
-//                       address order
+//                       reads lanes 32*(w%4)..); add the partial sums, rescale
+//                       the row, stage the rows in shared memory, store them to
+//                       global memory in address order
 // Hand-offs are mbarriers (full/empty per raw stage, per operand buffer and per
 // accumulator set).  Every wait is bounded; a role that gives up sets a shared
 // failure flag (which ends the other roles' waits early), the loader and the
 // MMA issuer drain what they issued, and the kernel records QS_ETIMEOUT, frees
 // its tensor memory and returns.
+//
+// Norm correction: a unitary block maps every row x_m to a row U x_m of the same
+// norm.  The tensor cores' FP32 accumulation loses a little magnitude on every
+// pass (a bias that grows linearly with the number of blocks), so for blocks
+// the host found unitary the epilogue rescales each output row to the squared
+// norm of its input row, computed by the producer in FP32.
 
 constexpr int kPipeThreads = 320;
 constexpr int kTileBytes = 4096 * 8;          // one raw tile (complex64)
 constexpr int kRun = 1024;                    // bytes of one contiguous run
 constexpr int kEpiBarrier = 1;                // named barriers of the 128 epilogue threads:
 constexpr int kEpiSync = 2;                   // reduction (kEpiBarrier) and plain sync
+constexpr int kNormSlots = 3;                 // row norms in flight (producer -> epilogue)
 
-// Raw stages in flight and operand buffers (hi + lo each), within 224 KiB of
-// shared memory together with B (hi + lo) and the 32 KiB output staging.
+// Raw stages in flight, within 224 KiB of shared memory together with the
+// operand buffer, B and the 32 KiB output staging (TF32: 96 + 64 + 32 + 32 KiB;
+// BF16: 96 + 48 + 24 + 32 KiB).
 template <int MODE>
-struct Pipe;
-template <>
-struct Pipe<BM_TF32> {
+struct Pipe {
   static constexpr int kStages = 3;
-  static constexpr int kABuf = 1;
-};
-template <>
-struct Pipe<BM_BF16> {
-  static constexpr int kStages = 4;
-  static constexpr int kABuf = 1;
 };
 template <int MODE>
 constexpr size_t pipe_smem_bytes() {
-  return (size_t)(Pipe<MODE>::kStages + 1) * kTileBytes + (size_t)Pipe<MODE>::kABuf * 2 * BOps<MODE>::kA +
-         2 * (size_t)BOps<MODE>::kB;
+  return (size_t)(Pipe<MODE>::kStages + 1) * kTileBytes +
+         (size_t)BOps<MODE>::kParts * (BOps<MODE>::kA + BOps<MODE>::kB);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
@@ -226,42 +283,49 @@ __device__ __forceinline__ bool bar_or(int id, int nthreads, bool v) {
       : "memory");
   return r != 0;
 }
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     block_pipe_kernel(float2* __restrict__ psi, const BlockPass* __restrict__ P,
                       const unsigned char* __restrict__ bmat, uint64_t ntiles, int* __restrict__ status) {
   using O = BOps<MODE>;
-  constexpr int kABuf = Pipe<MODE>::kABuf;
   constexpr int kStages = Pipe<MODE>::kStages;
+  constexpr int kParts = O::kParts;
   extern __shared__ __align__(1024) unsigned char smem[];
-  // raw stage s at smem + s kTileBytes; operand buffer b: A_hi at abase + 2b kA,
-  // A_lo at abase + (2b + 1) kA; then B_hi, B_lo
+  // raw stage s at smem + s kTileBytes; then the operand buffer (part p of A at
+  // abase + p kA), B (part p at bbase + p kB) and the output staging
   unsigned char* abase = smem + kStages * kTileBytes;
-  unsigned char* B_hi = abase + kABuf * 2 * O::kA;
-  unsigned char* B_lo = B_hi + O::kB;
-  float2* stage = reinterpret_cast<float2*>(B_lo + O::kB);   // 128 x 32 output amplitudes
-  __shared__ __align__(8) uint64_t rfull[kStages], rempty[kStages], afull[2], aempty[2], tfull[2],
-      tempty[2], drain;
+  unsigned char* bbase = abase + kParts * O::kA;
+  float2* stage = reinterpret_cast<float2*>(bbase + kParts * O::kB);   // 128 x 32 amplitudes
+  // tables used only while the roles set up their registers, kept in the staging
+  unsigned char* tab = reinterpret_cast<unsigned char*>(stage);
+  uint64_t* t_addr_hi = reinterpret_cast<uint64_t*>(tab);              // 64 x 8 B
+  uint8_t* t_m_lo = tab + 512;
+  uint8_t* t_m_hi = tab + 576;
+  uint8_t* t_c_lo = tab + 640;
+  uint8_t* t_c_hi = tab + 704;
+  uint16_t* t_em = reinterpret_cast<uint16_t*>(tab + 768);              // 128 x 2 B
+  uint16_t* t_ec = reinterpret_cast<uint16_t*>(tab + 1024);             // 32 x 2 B
+  uint16_t* t_sh = reinterpret_cast<uint16_t*>(tab + 1088);             // 64 x 2 B
+  __shared__ __align__(8) uint64_t rfull[kStages], rempty[kStages], afull, aempty, tfull[2], tempty[2],
+      drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
-  __shared__ uint64_t s_addr_lo[64], s_addr_hi[64];
-  __shared__ uint8_t s_m_lo[64], s_m_hi[64], s_c_lo[64], s_c_hi[64], s_nt[48];
-  __shared__ uint16_t s_em[128], s_ec[32];   // address-order index = s_em[m] | s_ec[c]
-  // staging index m*32 + (c ^ (m & 31)) of the element with address-order
-  // index e = the XOR of a term of its low 6 bits and s_sh[e >> 6] (the row and
-  // column bits of the two halves are disjoint, so | and + become ^)
-  __shared__ uint16_t s_sh[64];
+  __shared__ uint8_t s_nt[48];
   __shared__ int s_nnt;
+  __shared__ float s_norm[kNormSlots][128];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool unitary = (P->flags & 1) != 0;
 
-  for (int i = tid; i < 64; i += kPipeThreads) {
-    s_addr_lo[i] = P->addr_lo[i];
-    s_addr_hi[i] = P->addr_hi[i];
-    s_m_lo[i] = P->m_lo[i];
-    s_m_hi[i] = P->m_hi[i];
-    s_c_lo[i] = P->c_lo[i];
-    s_c_hi[i] = P->c_hi[i];
+  if (tid < 64) {
+    t_addr_hi[tid] = P->addr_hi[tid];
+    t_m_lo[tid] = P->m_lo[tid];
+    t_m_hi[tid] = P->m_hi[tid];
+    t_c_lo[tid] = P->c_lo[tid];
+    t_c_hi[tid] = P->c_hi[tid];
   }
   if (tid < 48) s_nt[tid] = P->nt_pos[tid];
   if (tid == 0) {
@@ -271,9 +335,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       mbar_init(&rfull[s], 1);
       mbar_init(&rempty[s], 128);   // producers
     }
+    mbar_init(&afull, 128);
+    mbar_init(&aempty, 1);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&afull[b], 128);
-      mbar_init(&aempty[b], 1);
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 128);
     }
@@ -282,8 +346,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   }
   {
     const uint4* src = reinterpret_cast<const uint4*>(bmat);
-    uint4* dst = reinterpret_cast<uint4*>(B_hi);
-    for (int i = tid; i < 2 * O::kB / 16; i += kPipeThreads) dst[i] = src[i];
+    uint4* dst = reinterpret_cast<uint4*>(bbase);
+    for (int i = tid; i < kParts * O::kB / 16; i += kPipeThreads) dst[i] = src[i];
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -293,11 +357,49 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   }
   __syncthreads();
   for (int e = tid; e < 4096; e += kPipeThreads) {
-    const int m = s_m_lo[e & 63] | s_m_hi[e >> 6], c = s_c_lo[e & 63] | s_c_hi[e >> 6];
-    if (c == 0) s_em[m] = (uint16_t)e;
-    if (m == 0) s_ec[c] = (uint16_t)e;
+    const int m = t_m_lo[e & 63] | t_m_hi[e >> 6], c = t_c_lo[e & 63] | t_c_hi[e >> 6];
+    if (c == 0) t_em[m] = (uint16_t)e;
+    if (m == 0) t_ec[c] = (uint16_t)e;
   }
-  if (tid < 64) s_sh[tid] = (uint16_t)((s_m_hi[tid] << 5) ^ s_c_hi[tid] ^ (s_m_hi[tid] & 31));
+  // staging index m*32 + (c ^ (m & 31)) of the element with address-order index
+  // e = (term of its low 6 bits) ^ t_sh[e >> 6]: the row and column bits of the
+  // two halves are disjoint, so | and + become ^
+  if (tid < 64) t_sh[tid] = (uint16_t)((t_m_hi[tid] << 5) ^ t_c_hi[tid] ^ (t_m_hi[tid] & 31));
+  __syncthreads();
+
+  // ---- per-role registers (from the tables; the staging is free after this)
+  // producers: the address-order index of (m, c) is em[m] | ec[c], and ec
+  // deposits the bits of c, so it is linear over XOR: the index of column
+  // (jj ^ rot) G + u is e0 ^ ecg[jj] ^ ecu[u]
+  constexpr int G = MODE == BM_TF32 ? 2 : 4;   // columns per 16-byte core-matrix row
+  constexpr int NG = 32 / G;
+  uint32_t ecg[NG], ecu[G], e0 = 0;
+  // epilogue: run k = 0 of the thread and the change of address / staging index
+  // when bit b of k flips (element bit 7 + b = bit 1 + b of the high half)
+  uint64_t addr0 = 0, dA[5];
+  uint32_t idx0 = 0, dS[5];
+  // loader: offset of run `lane`
+  uint64_t run_off = 0;
+  if (warp < 4) {
+    const int rot = tid & (NG - 1);
+#pragma unroll
+    for (int jj = 0; jj < NG; ++jj) ecg[jj] = t_ec[jj * G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) ecu[u] = t_ec[u];
+    e0 = t_em[tid] ^ t_ec[rot * G];
+  } else if (warp < 8) {
+    const int et = tid - 128;
+    const int m_lo = t_m_lo[et & 63], c_lo = t_c_lo[et & 63];
+    addr0 = (uint64_t)(et & 63) | t_addr_hi[et >> 6];   // low 6 bits: physical bits 0..5
+    idx0 = (uint32_t)((m_lo << 5) ^ c_lo ^ (m_lo & 31)) ^ t_sh[et >> 6];
+#pragma unroll
+    for (int bit = 0; bit < 5; ++bit) {
+      dA[bit] = t_addr_hi[2 << bit];
+      dS[bit] = t_sh[2 << bit];
+    }
+  } else if (warp == 9) {
+    run_off = t_addr_hi[2 * lane];
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -311,9 +413,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   };
 
   if (warp == 9) {
-    // ---------------- loader (one warp; lane j copies run j of the tile)
+    // ---------------- loader
     uint64_t issued = 0;
-    const uint64_t run_off = s_addr_hi[2 * lane];
     for (uint64_t i = 0; i < my_tiles; ++i) {
       const int s = (int)(i % kStages);
       const uint32_t ph = (uint32_t)((i / kStages) & 1);
@@ -335,107 +436,105 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
           atomicExch(&s_fail, 1);
   } else if (warp < 4) {
     // ---------------- producers: thread = row m; groups of G columns fill one
-    // 16-byte core-matrix row each, groups in a lane-rotated order (the 32 lanes
-    // of a write then cover the 8 rows of a core matrix 4 times: no conflicts
-    // beyond the 4 wavefronts of 512 bytes)
-    constexpr int G = MODE == BM_TF32 ? 2 : 4;
-    constexpr int NG = 32 / G;
+    // 16-byte core-matrix row per part, groups in a lane-rotated order (the 32
+    // lanes of a write cover the 8 rows of a core matrix 4 times: 4 wavefronts
+    // for 512 bytes, no conflicts beyond that)
     const int m = tid;
     const int rot = m & (NG - 1);
-    // The address-order index of (m, c) is s_em[m] | s_ec[c], and s_ec deposits
-    // the bits of c, so it is linear over XOR: the index of column
-    // (jj ^ rot) G + u is e0 ^ ecg[jj] ^ ecu[u] with per-thread registers.
-    uint32_t ecg[NG], ecu[G];
-#pragma unroll
-    for (int jj = 0; jj < NG; ++jj) ecg[jj] = s_ec[jj * G];
-#pragma unroll
-    for (int u = 0; u < G; ++u) ecu[u] = s_ec[u];
-    const uint32_t e0 = s_em[m] ^ s_ec[rot * G];
-    // byte offset of group g in row m: core_off(m, 2 G g) = row_off + 128 g
-    const uint32_t row_off = core_off<MODE>(m, 0);
+    unsigned char* arow = abase + core_off<MODE>(m, 0);   // group g at + 128 g
     for (uint64_t i = 0; i < my_tiles; ++i) {
       const int s = (int)(i % kStages);
       const uint32_t ph = (uint32_t)((i / kStages) & 1);
-      const int b = (int)(i % kABuf);
-      const uint32_t pa = (uint32_t)((i / kABuf) & 1);
-      if (!mbar_wait(&rfull[s], ph, &s_fail) || !mbar_wait(&aempty[b], pa ^ 1u, &s_fail)) {
+      const uint32_t pa = (uint32_t)(i & 1);
+      if (!mbar_wait(&rfull[s], ph, &s_fail) || !mbar_wait(&aempty, pa ^ 1u, &s_fail)) {
         atomicExch(&s_fail, 1);
         break;
       }
       const float2* raw = reinterpret_cast<const float2*>(smem + s * kTileBytes);
-      unsigned char* Ah = abase + b * 2 * O::kA + row_off;
-      unsigned char* Al = Ah + O::kA;
+      // the whole row first (all shared-memory loads in flight), then its norm
+      float2 xr[32];   // column (jj ^ rot) G + u at xr[jj G + u]
+#pragma unroll
+      for (int jj = 0; jj < NG; ++jj)
+#pragma unroll
+        for (int u = 0; u < G; ++u) xr[jj * G + u] = raw[e0 ^ ecg[jj] ^ ecu[u]];
+      float nrm[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        nrm[(2 * j) & 3] = fmaf(xr[j].x, xr[j].x, nrm[(2 * j) & 3]);
+        nrm[(2 * j + 1) & 3] = fmaf(xr[j].y, xr[j].y, nrm[(2 * j + 1) & 3]);
+      }
 #pragma unroll
       for (int jj = 0; jj < NG; ++jj) {
-        float v[2 * G];   // Re, Im of columns gG .. gG+G-1, g = jj ^ rot
-#pragma unroll
-        for (int u = 0; u < G; ++u) {
-          const float2 a = raw[e0 ^ ecg[jj] ^ ecu[u]];
-          v[2 * u] = a.x;
-          v[2 * u + 1] = a.y;
-        }
-        uint32_t hw[4], lw[4];
-        if (MODE == BM_TF32) {
+        uint32_t w[kParts][4];
+        if constexpr (MODE == BM_TF32) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            hw[q] = tf32_rna(v[q]);
-            lw[q] = tf32_rna(v[q] - __uint_as_float(hw[q]));
+            const float v = (q & 1) ? xr[jj * G + (q >> 1)].y : xr[jj * G + (q >> 1)].x;
+            w[0][q] = tf32_rna(v);
+            w[1][q] = tf32_rna(v - __uint_as_float(w[0][q]));
           }
         } else {
+          // three bf16 parts: every residual is exact in FP32
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-            const float2 hf = __bfloat1622float2(h2);
-            const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
-            hw[q] = *reinterpret_cast<const uint32_t*>(&h2);
-            lw[q] = *reinterpret_cast<const uint32_t*>(&l2);
+            const float2 x = xr[jj * G + q];
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+            const float2 hf = __bfloat1622float2(h);
+            const float2 r1 = make_float2(x.x - hf.x, x.y - hf.y);
+            const __nv_bfloat162 md = __floats2bfloat162_rn(r1.x, r1.y);
+            const float2 mf = __bfloat1622float2(md);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(r1.x - mf.x, r1.y - mf.y);
+            w[0][q] = bf16x2_bits(h);
+            w[1][q] = bf16x2_bits(md);
+            w[kParts - 1][q] = bf16x2_bits(lo);
           }
         }
         const uint32_t off = (uint32_t)(jj ^ rot) << 7;   // 16-byte aligned
-        *reinterpret_cast<uint4*>(Ah + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(Al + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+#pragma unroll
+        for (int p = 0; p < kParts; ++p)
+          *reinterpret_cast<uint4*>(arow + p * O::kA + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
       }
+      s_norm[i % kNormSlots][m] = (nrm[0] + nrm[1]) + (nrm[2] + nrm[3]);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&afull[b]);
+      mbar_arrive(&afull);
       mbar_arrive(&rempty[s]);   // raw stage s may be refilled
     }
   } else if (warp == 8) {
     // ---------------- MMA issuer (one thread)
     if (lane == 0) {
       const uint32_t idesc = make_idesc<MODE>();
-      const uint32_t b_hi = smem_u32(B_hi), b_lo = smem_u32(B_lo);
+      const uint32_t a0 = smem_u32(abase), b0 = smem_u32(bbase);
       constexpr int ksteps = 64 / O::kKStep;
       constexpr uint32_t kstep_bytes = 256;   // two K-adjacent core matrices
       for (uint64_t i = 0; i < my_tiles; ++i) {
-        const int b = (int)(i % kABuf);
-        const uint32_t pa = (uint32_t)((i / kABuf) & 1);
+        const uint32_t pa = (uint32_t)(i & 1);
         const int tb = (int)(i & 1);
         const uint32_t pt = (uint32_t)((i >> 1) & 1);
-        if (!mbar_wait(&afull[b], pa, &s_fail) || !mbar_wait(&tempty[tb], pt ^ 1u, &s_fail)) {
+        if (!mbar_wait(&afull, pa, &s_fail) || !mbar_wait(&tempty[tb], pt ^ 1u, &s_fail)) {
           atomicExch(&s_fail, 1);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a_hi = smem_u32(abase) + (uint32_t)(b * 2 * O::kA), a_lo = a_hi + O::kA;
-        // three FP32 accumulators: D1a / D1b = A_hi B_hi over the low / high half
-        // of K (columns +0 / +128), D2 = A_lo B_lo + A_hi B_lo + A_lo B_hi (+64,
-        // smallest first); the large product is summed in short chains
+        // three FP32 accumulators: D1a / D1b = A_0 B_0 over the low / high half
+        // of K (columns +0 / +128) and D2 = the correction products, smallest
+        // first (+64); the large product is summed in short chains
         const uint32_t d = tmem + 256u * (uint32_t)tb;
         for (int ks = 0; ks < ksteps; ++ks) {
           const uint32_t dd = ks < ksteps / 2 ? d : d + 128;
-          mma<MODE>(dd, make_desc(a_hi + ks * kstep_bytes, 128, O::kSBO_A),
-                    make_desc(b_hi + ks * kstep_bytes, 128, O::kSBO_A), idesc,
+          mma<MODE>(dd, make_desc(a0 + ks * kstep_bytes, 128, O::kSBO_A),
+                    make_desc(b0 + ks * kstep_bytes, 128, O::kSBO_A), idesc,
                     (ks % (ksteps / 2)) ? 1u : 0u);
         }
-        const uint32_t pa3[3] = {a_lo, a_hi, a_lo};
-        const uint32_t pb3[3] = {b_lo, b_lo, b_hi};
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
+        for (int p = 0; p < O::kNCorr; ++p) {
+          const uint32_t ap = a0 + (uint32_t)(corr_a<MODE>(p) * O::kA);
+          const uint32_t bp = b0 + (uint32_t)(corr_b<MODE>(p) * O::kB);
           for (int ks = 0; ks < ksteps; ++ks)
-            mma<MODE>(d + 64, make_desc(pa3[p] + ks * kstep_bytes, 128, O::kSBO_A),
-                      make_desc(pb3[p] + ks * kstep_bytes, 128, O::kSBO_A), idesc,
+            mma<MODE>(d + 64, make_desc(ap + ks * kstep_bytes, 128, O::kSBO_A),
+                      make_desc(bp + ks * kstep_bytes, 128, O::kSBO_A), idesc,
                       (p > 0 || ks > 0) ? 1u : 0u);
-        mma_commit(smem_u32(&aempty[b]));   // operand buffer b may be refilled
+        }
+        mma_commit(smem_u32(&aempty));      // the operand buffer may be refilled
         mma_commit(smem_u32(&tfull[tb]));   // accumulator set tb is ready
       }
       // every product issued above has finished before the tensor memory is freed
@@ -445,21 +544,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   } else {
     // ---------------- epilogue (warps 4..7)
     const int m = (warp & 3) * 32 + lane;   // row of the tile = tensor-memory lane
-    const int et = tid - 128;               // 0..127, store order
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    const int m_lo = s_m_lo[et & 63], c_lo = s_c_lo[et & 63];
-    const uint32_t sh_lo = (uint32_t)((m_lo << 5) ^ c_lo ^ (m_lo & 31));
-    // run k = 0 of this thread, and the change of address / staging index when
-    // bit b of k flips (element index bit 7 + b = address-order high half bit 1 + b)
-    const uint64_t addr0 = s_addr_lo[et & 63] | s_addr_hi[et >> 6];
-    const uint32_t idx0 = sh_lo ^ s_sh[et >> 6];
-    uint64_t dA[5];
-    uint32_t dS[5];
-#pragma unroll
-    for (int bit = 0; bit < 5; ++bit) {
-      dA[bit] = s_addr_hi[2 << bit];
-      dS[bit] = s_sh[2 << bit];
-    }
     for (uint64_t i = 0; i < my_tiles; ++i) {
       const int tb = (int)(i & 1);
       const uint32_t pt = (uint32_t)((i >> 1) & 1);
@@ -471,36 +556,74 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const float nx = s_norm[i % kNormSlots][m];
       const uint32_t d = tmem + lane_base + 256u * (uint32_t)tb;
+      // y = (D2 + D1a) + D1b: the corrections first, two loads per wait
+      float y[64];
+      {
+        uint32_t a[32], b[32];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float d1[32], d2[32];
-        tmem_ld32(d + 32 * h, d1);
-        tmem_ld32(d + 64 + 32 * h, d2);
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld32_nowait(d + 64 + 32 * h, a);
+          tmem_ld32_nowait(d + 32 * h, b);
+          tmem_wait_ld();
+          reg_after_wait32(a);
+          reg_after_wait32(b);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) d2[j] += d1[j];    // corrections + low-K half
-        tmem_ld32(d + 128 + 32 * h, d1);
+          for (int j = 0; j < 32; ++j) y[32 * h + j] = __uint_as_float(a[j]) + __uint_as_float(b[j]);
+        }
+        tmem_ld32_nowait(d + 128, a);
+        tmem_ld32_nowait(d + 160, b);
+        tmem_wait_ld();
+        reg_after_wait32(a);
+        reg_after_wait32(b);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int c = 16 * h + j;
-          stage[m * 32 + (c ^ (m & 31))] = make_float2(d1[2 * j] + d2[2 * j], d1[2 * j + 1] + d2[2 * j + 1]);
+        for (int j = 0; j < 32; ++j) {
+          y[j] += __uint_as_float(a[j]);
+          y[32 + j] += __uint_as_float(b[j]);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&tempty[tb]);   // accumulator set tb may be overwritten
+      // y <- y (1 + delta), 1 + delta = sqrt(nx / ny).  delta is formed as
+      // (nx - ny) / (ny + sqrt(nx ny)) (nx - ny is exact when they are close) and
+      // added with one fma: a factor rounded to FP32 near 1 (spacing 2^-23 above
+      // 1, and sqrt(1 + 2^-23) rounds back to 1) would drop the small
+      // corrections systematically.
+      float delta = 0.f;
+      if (unitary) {
+        float sq[32];   // pairwise sum of the 64 squares
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sq[j] = fmaf(y[2 * j], y[2 * j], y[2 * j + 1] * y[2 * j + 1]);
+#pragma unroll
+        for (int w = 16; w >= 1; w >>= 1)
+#pragma unroll
+          for (int j = 0; j < w; ++j) sq[j] += sq[j + w];
+        const float ny = sq[0];
+        if (ny > 0.f) delta = (nx - ny) / (ny + sqrtf(nx) * sqrtf(ny));
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        stage[m * 32 + (c ^ (m & 31))] =
+            make_float2(fmaf(y[2 * c], delta, y[2 * c]), fmaf(y[2 * c + 1], delta, y[2 * c + 1]));
       asm volatile("bar.sync %0, %1;" ::"r"(kEpiSync), "r"(128) : "memory");
       // element k * 128 + et for the runs k in Gray-code order: the address and
       // the staging index are XOR-linear in the bits of k, so each step flips one
-      uint64_t addr = tile_base(i) | addr0;
-      uint32_t idx = idx0;
+      // (all staging reads first, then all stores)
+      float2 v[32];
+      {
+        uint32_t idx = idx0;
 #pragma unroll
-      for (int t = 0; t < 32; ++t) {
-        if (t) {
-          const int bit = (t & 1) ? 0 : (t & 2) ? 1 : (t & 4) ? 2 : (t & 8) ? 3 : 4;   // lowest set bit
-          addr ^= dA[bit];
-          idx ^= dS[bit];
+        for (int k = 0; k < 32; ++k) {
+          if (k) idx ^= dS[(k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : (k & 8) ? 3 : 4];   // lowest set bit
+          v[k] = stage[idx];
         }
-        __stcs(psi + addr, stage[idx]);
+      }
+      uint64_t addr = tile_base(i) | addr0;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (k) addr ^= dA[(k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : (k & 8) ? 3 : 4];
+        __stcs(psi + addr, v[k]);
       }
     }
   }
@@ -545,7 +668,8 @@ float bf16_to_float(uint16_t h) {
 
 }  // namespace
 
-// Fills the B operand (hi then lo) of a block in the kernel's shared-memory layout.
+// Fills the B operand of a block (its parts one after another) in the kernel's
+// shared-memory layout; the parts are split from the FP64 matrix.
 void block_b_operand(const cd* U, int mode, std::vector<unsigned char>& out) {
   double W[64][64];   // W[n][k] (B is N x K, K-major)
   for (int r = 0; r < 32; ++r)
@@ -570,19 +694,34 @@ void block_b_operand(const cd* U, int mode, std::vector<unsigned char>& out) {
       }
   } else {
     const int kB = BOps<BM_BF16>::kB;
-    out.assign(2 * kB, 0);
+    out.assign(3 * kB, 0);
     for (int n = 0; n < 64; ++n)
       for (int k = 0; k < 64; ++k) {
-        const uint16_t h = bf16_round_host((float)W[n][k]);
-        const uint16_t l = bf16_round_host((float)(W[n][k] - (double)bf16_to_float(h)));
+        double r = W[n][k];
         const uint32_t off = core_off<BM_BF16>(n, k);
-        std::memcpy(out.data() + off, &h, 2);
-        std::memcpy(out.data() + kB + off, &l, 2);
+        for (int p = 0; p < 3; ++p) {
+          const uint16_t h = bf16_round_host((float)r);
+          r -= (double)bf16_to_float(h);
+          std::memcpy(out.data() + p * kB + off, &h, 2);
+        }
       }
   }
 }
 
-size_t block_b_bytes(int mode) { return mode == BM_TF32 ? 2 * BOps<BM_TF32>::kB : 2 * BOps<BM_BF16>::kB; }
+size_t block_b_bytes(int mode) {
+  return mode == BM_TF32 ? BOps<BM_TF32>::kParts * BOps<BM_TF32>::kB
+                         : BOps<BM_BF16>::kParts * BOps<BM_BF16>::kB;
+}
+
+bool block_is_unitary(const cd* U) {
+  for (int i = 0; i < 32; ++i)
+    for (int j = 0; j < 32; ++j) {
+      cd s = 0;
+      for (int k = 0; k < 32; ++k) s += std::conj(U[k * 32 + i]) * U[k * 32 + j];
+      if (std::abs(s - (i == j ? 1.0 : 0.0)) > 1e-10) return false;
+    }
+  return true;
+}
 
 // Tile bookkeeping: block bits (5 physical positions, local block bit i = bit i
 // of the column index) and 7 row positions (the lowest other positions).

@@ -213,10 +213,13 @@ struct BlockPass {
   uint8_t c_lo[64], c_hi[64];
   uint8_t nt_pos[48];           // physical positions outside the tile (ascending)
   int32_t n_nt;
-  int32_t pad[3];
+  int32_t flags;                // bit 0: the block is unitary (rows keep their norm)
+  int32_t pad[2];
 };
 void block_pass_desc(int n, const int* bpos, BlockPass& P);
 bool block_pass_runs_contiguous(const BlockPass& P);
+// U^dagger U = I within 1e-10 (32x32, row-major)
+bool block_is_unitary(const cd* U);
 size_t block_pass_bytes();
 void block_b_operand(const cd* U, int mode, std::vector<unsigned char>& out);
 size_t block_b_bytes(int mode);
