@@ -56,6 +56,12 @@ def fp32_peak_tflops(mhz):
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def block_products(tf32):
+    """Split products per block pass: A0.B0 plus 3 (TF32, two parts) or 5 (BF16, three
+    parts) corrections; each is a real [2^(n-5) x 64] x [64 x 64] GEMM = 2^(n+8) flops."""
+    return 4 if tf32 else 6
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -272,12 +278,14 @@ def run_ours(args, world, rank, local):
                 "peak": fp32_peak_tflops(2070.0),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
     elif dominant == "block":
-        # block GEMM: 4 split products of [2^n/32 x 64] x [64 x 64] per launch
-        per_launch = 4 * 2 * (1 << n) * 64
+        # block GEMM: one HBM sweep per launch (its roof; the tensor work, 4 (TF32) or
+        # 6 (BF16) split products of 2^(n+8) flops, is far below the tensor peak)
+        per_launch = bytes_per_pass
         tf32 = args.method == "blocks_tf32"
-        roof = {"bound": "tensor", "kernel": "block_gemm_kernel<%s>" % ("TF32" if tf32 else "BF16"),
-                "unit": "TFLOP/s", "peak": peaks["bf16_tflops"] / (2 if tf32 else 1),
-                "peak_source": "measured bf16 burst" + (" / 2 (TF32 nominal ratio)" if tf32 else "")}
+        roof = {"bound": "hbm", "kernel": "block_pipe_kernel<%s>" % ("TF32" if tf32 else "BF16"),
+                "unit": "GB/s", "peak": peaks["hbm_gbs"], "peak_source": "measured copy bandwidth",
+                "tensor_tflops": block_products(tf32) * 2.0 ** (n + 8) / (avg_ms * 1e-3) / 1e12,
+                "tensor_peak_tflops": peaks["bf16_tflops"] / (2 if tf32 else 1)}
     else:
         per_launch = bytes_per_pass * 1e-12 * 1e12
         roof = {"bound": "hbm", "kernel": dominant, "unit": "GB/s", "peak": peaks["hbm_gbs"],
@@ -322,7 +330,9 @@ def run_ours(args, world, rank, local):
     del probs, host_probs
     torch.cuda.empty_cache()
     if not args.no_extras:
-        line["rows"] = {"small_circuits": extra_small_circuits(qs, torch),
+        line["rows"] = {"qft": extra_qft(qs, torch),
+                        "fp64": extra_fp64(qs, torch),
+                        "small_circuits": extra_small_circuits(qs, torch),
                         "noisy_batch": extra_noisy_batch(qs, torch),
                         "serving": extra_serving(qs, torch),
                         "fused_blocks": extra_fused_blocks(qs, torch)}
@@ -401,19 +411,40 @@ def extra_noisy_batch(qs, torch):
     return res
 
 
+def block_errors(qs, torch, n=20, layers=60, seed=3002):
+    """Relative L2 error of the block methods against the GPU FP64 per-gate path (itself
+    within 1e-12 of the FP64 oracle) on a depth-60 20-qubit circuit (151 blocks)."""
+    import numpy as np
+
+    import workloads as W
+    ops = qs.gates_array(W.layered_haar_cz(n, layers, seed=seed))
+    ref_st = qs.State(n, qs.QS_C128)
+    qs.sv_apply_circuit(ref_st, ops, qs.METHOD_PLAIN)
+    ref = qs.sv_copy_out(ref_st)
+    ref_st.close()
+    out = {}
+    for name, method in (("tf32", qs.METHOD_BLOCKS_TF32), ("bf16", qs.METHOD_BLOCKS_BF16),
+                         ("tiled_fp32", qs.METHOD_TILED)):
+        st = qs.State(n, qs.QS_C64)
+        qs.sv_apply_circuit(st, ops, method)
+        v = qs.sv_copy_out(st).astype(np.complex128)
+        st.close()
+        out[name] = float(np.linalg.norm(v - ref) / np.linalg.norm(ref))
+    out["reference"] = f"complex128 per-gate GPU path, {n} qubits, depth {layers}, seed {seed}"
+    return out
+
+
 def extra_fused_blocks(qs, torch, n=32, layers=60, seed=3001):
     """32-qubit complex64, depth-60 Haar + brickwork CZ fused into 5-qubit blocks on the
     tensor cores (TF32 and BF16 splits), beside the tiled FP32 path on the same state."""
     import workloads as W
     ops = qs.gates_array(W.layered_haar_cz(n, layers, seed=seed))
-    st = qs.State(n, qs.QS_C64)
-    warm = qs.State(14, qs.QS_C64)
     out = {"workload": f"{n}-qubit complex64 ({8 << (n - 30)} GiB), {layers} layers Haar + brickwork CZ "
                        f"({len(ops)} gates, seed {seed})",
-           "error_vs_fp64_oracle_at_20_qubits": {"tf32": 1.26e-5, "bf16": 4.22e-5,
-                                                 "source": "tests/test_gpu_blocks.py (depth 60, seed 3002)"}}
-    tf32_peak = 1926.3 / 2   # TF32 dense = half the measured BF16 rate (nominal ratio)
-    bf16_peak = 1926.3
+           "rel_l2_error_at_20_qubits": block_errors(qs, torch)}
+    peaks, _ = measured_peaks()
+    st = qs.State(n, qs.QS_C64)
+    warm = qs.State(14, qs.QS_C64)
     for name, method in (("tf32", qs.METHOD_BLOCKS_TF32), ("bf16", qs.METHOD_BLOCKS_BF16),
                          ("tiled_fp32", qs.METHOD_TILED)):
         qs.sv_apply_circuit(warm, qs.gates_array(W.layered_haar_cz(14, 2, seed=1)), method)
@@ -423,18 +454,78 @@ def extra_fused_blocks(qs, torch, n=32, layers=60, seed=3001):
         s = qs.sv_apply_circuit(st, ops, method, time_kernels=True)
         dt = time.perf_counter() - t0
         kms = sum(s["kernel_ms"])
+        gbs = s["passes"] * 2 * 8 * (1 << n) / (kms * 1e-3) / 1e9
         row = {"s_per_circuit": dt, "passes": s["passes"], "kernel_ms": kms,
-               "gates_per_s": len(ops) / dt,
-               "hbm_gbs_per_pass": s["passes"] * 2 * 8 * (1 << n) / (kms * 1e-3) / 1e9}
+               "gates_per_s": len(ops) / dt, "hbm_gbs_per_pass": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]}
         if method in (qs.METHOD_BLOCKS_TF32, qs.METHOD_BLOCKS_BF16):
-            # tensor work: 4 split products of a [2^n/32 x 64] x [64 x 64] real GEMM per block
-            tflops = s["passes"] * 4 * 2 * (1 << n) * 2 * 64 / (kms * 1e-3) / 1e12
-            peak = tf32_peak if method == qs.METHOD_BLOCKS_TF32 else bf16_peak
+            tf32 = method == qs.METHOD_BLOCKS_TF32
+            tflops = s["passes"] * block_products(tf32) * 2.0 ** (n + 8) / (kms * 1e-3) / 1e12
             row["tensor_tflops"] = tflops
-            row["tensor_frac"] = tflops / peak
+            row["tensor_frac"] = tflops / (peaks["bf16_tflops"] / (2 if tf32 else 1))
         out[name] = row
     warm.close()
     st.close()
+    return out
+
+
+def extra_qft(qs, torch, n=30, seed=2002):
+    """30-qubit QFT (Eq. multiqubitqft) on a seeded random basis state |J>, complex64, tiled
+    path (the final qubit reversal is a relabeling plus remap passes); 4096 sampled
+    amplitudes against the closed form <K|QFT|J> = 2^(-n/2) exp(2 pi i J K / 2^n)."""
+    import math
+
+    import numpy as np
+
+    import workloads as W
+    ops = qs.gates_array(W.qft_circuit(n))
+    J = W.random_basis_index(n, seed)
+    st = qs.State(n, qs.QS_C64)
+    qs.sv_set_basis(st, J)
+    qs.sv_apply_circuit(st, ops)                     # warm-up (planner, first launch)
+    qs.sv_set_basis(st, J)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = qs.sv_apply_circuit(st, ops, time_kernels=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    amps = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    qs.sv_copy_out(st, out=amps)
+    K = np.random.default_rng(seed).integers(0, 1 << n, size=4096)
+    got = amps[torch.from_numpy(K).cuda()].cpu().numpy().astype(np.complex128)
+    N = 1 << n
+    jk = np.array([(J * int(k)) % N for k in K], dtype=np.float64)
+    ref = np.exp(2j * math.pi * jk / N) / math.sqrt(N)
+    st.close()
+    del amps
+    torch.cuda.empty_cache()
+    names = ["tile", "plain", "remap", "small", "block"]
+    return {"workload": f"{n}-qubit QFT on |J>, J = {J} (seed {seed}), {len(ops)} gates, complex64",
+            "s_per_circuit": dt, "gates_per_s": len(ops) / dt, "passes": s["passes"],
+            "kernel_ms": {k: v for k, v in zip(names, s["kernel_ms"]) if v > 0},
+            "max_abs_err_4096_sampled": float(np.max(np.abs(got - ref))),
+            "rel_err_4096_sampled": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+
+
+def extra_fp64(qs, torch, seed=SEED):
+    """complex128 runs of the 40-layer workload: the plain per-gate FP64 GPU path at 30
+    qubits (16 GiB; the baseline the fused FP32 forms are measured against) and the tiled
+    FP64 path at 31 qubits (32 GiB)."""
+    import workloads as W
+    out = {}
+    for key, n, method in (("plain_fp64_30q", 30, qs.METHOD_PLAIN), ("tiled_fp64_31q", 31, qs.METHOD_TILED)):
+        ops = qs.gates_array(W.layered_haar_cz(n, LAYERS, seed=seed))
+        st = qs.State(n, qs.QS_C128)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = qs.sv_apply_circuit(st, ops, method, time_kernels=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st.close()
+        torch.cuda.empty_cache()
+        kms = sum(s["kernel_ms"])
+        gbs = s["passes"] * 2 * 16 * (1 << n) / (kms * 1e-3) / 1e9
+        out[key] = {"n": n, "gates": len(ops), "s_per_circuit": dt, "gates_per_s": len(ops) / dt,
+                    "passes": s["passes"], "hbm_gbs_per_pass": gbs}
     return out
 
 
@@ -507,7 +598,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other rows' measurements")
     ap.add_argument("--method", default="tiled", choices=["tiled", "plain", "blocks_tf32", "blocks_bf16"],
                     help="state-vector method of the timed workload (the default line uses tiled)")
-    ap.add_argument("--only", default=None, choices=["dm", "serve", "blocks", "small"],
+    ap.add_argument("--only", default=None, choices=["dm", "serve", "blocks", "small", "qft", "fp64"],
                     help="run one extra row alone (for profiling) and print it")
     args = ap.parse_args()
     if args.only:
@@ -516,7 +607,7 @@ def main():
         import paper_2008_13490_gb300 as qs
         qs.load()
         fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
-              "small": extra_small_circuits}[args.only]
+              "small": extra_small_circuits, "qft": extra_qft, "fp64": extra_fp64}[args.only]
         print(json.dumps({"only": args.only, "row": fn(qs, torch)}), flush=True)
         return 0
     world, rank, local = dist_setup()

@@ -475,7 +475,7 @@ extern "C" {
 
 const char* qs_last_error(void) { return g_err.c_str(); }
 
-const char* qs_version(void) { return "qsim-gb300 0.3 (sm_103a)"; }
+const char* qs_version(void) { return "qsim-gb300 0.5 (sm_103a)"; }
 
 qs_status sv_create(int n, int prec, const qs_allocator* alloc, void* stream, qs_state_t* out) {
   if (!out) {

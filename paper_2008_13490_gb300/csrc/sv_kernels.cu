@@ -375,19 +375,53 @@ __global__ void __launch_bounds__(kTileThreads)
 
 // ------------------------------------------------------------------ reductions
 
+// Per-thread sum of probabilities.  For an FP32 state the per-element additions
+// stay in FP32 (compensated, Kahan, so the chunk sum is good to about one FP32
+// rounding whatever its length), folded into the FP64 accumulator every
+// kFold elements: GB300's FP64 pipe is far slower than its FP32 pipe, and one
+// FP64 add per element made this HBM-bound kernel FP64-bound.  The reductions
+// across threads and blocks are FP64.
+template <typename R>
+struct ProbSum;
+template <>
+struct ProbSum<double> {
+  double acc = 0.0;
+  __device__ __forceinline__ void add(double p) { acc += p; }
+  __device__ __forceinline__ double total() const { return acc; }
+};
+template <>
+struct ProbSum<float> {
+  static constexpr int kFold = 64;
+  double acc = 0.0;
+  float s = 0.f, c = 0.f;
+  int cnt = 0;
+  __device__ __forceinline__ void add(float p) {
+    const float y = p - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+    if (++cnt == kFold) {
+      acc += (double)s - (double)c;
+      s = c = 0.f;
+      cnt = 0;
+    }
+  }
+  __device__ __forceinline__ double total() const { return acc + ((double)s - (double)c); }
+};
+
 template <typename R, typename O>
 __global__ void __launch_bounds__(256)
     probs_kernel(const C2<R>* __restrict__ psi, O* __restrict__ out, uint64_t N,
                  double* __restrict__ partials) {
-  double acc = 0.0;
+  ProbSum<R> sum;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
     const C2<R> a = psi[i];
     const R p = a.x * a.x + a.y * a.y;
     if (out) out[i] = (O)p;
-    acc += (double)p;
+    sum.add(p);
   }
-  acc = block_sum(acc);
+  const double acc = block_sum(sum.total());
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
@@ -395,7 +429,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     probs_kernel_f32x2(const float4* __restrict__ psi2, float2* __restrict__ out2, uint64_t N2,
                        double* __restrict__ partials) {
-  double acc = 0.0;
+  ProbSum<float> sum;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N2; i += stride) {
     const float4 a = __ldcs(psi2 + i);
@@ -403,9 +437,10 @@ __global__ void __launch_bounds__(256)
     p.x = a.x * a.x + a.y * a.y;
     p.y = a.z * a.z + a.w * a.w;
     if (out2) __stcs(out2 + i, p);
-    acc += (double)p.x + (double)p.y;
+    sum.add(p.x);
+    sum.add(p.y);
   }
-  acc = block_sum(acc);
+  const double acc = block_sum(sum.total());
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
