@@ -56,6 +56,17 @@ def fp32_peak_tflops(mhz):
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def tile_kernel_src_hash():
+    """SHA-256 of the sources the tile-pass kernel is compiled from: a stored ncu traffic
+    figure is used only while they are unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("sv_kernels.cu", "dev_common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2008_13490_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def block_products(tf32):
     """Split products per block pass: A0.B0 plus 3 (TF32, two parts) or 5 (BF16, three
     parts) corrections; each is a real [2^(n-5) x 64] x [64 x 64] GEMM = 2^(n+8) flops."""
@@ -297,7 +308,7 @@ def run_ours(args, world, rank, local):
     if os.path.exists(prof):
         with open(prof) as f:
             tr = json.load(f)
-        if tr.get("kernel_rev") == qs.version():
+        if tr.get("kernel_src_sha256") == tile_kernel_src_hash():
             traffic = tr.get("bytes_per_launch")
     launches_per_step = 1 + stats["launches"] + 1   # set_basis, circuit, probabilities
     gates_per_s = world * gates * args.steps / (ms_max * 1e-3)

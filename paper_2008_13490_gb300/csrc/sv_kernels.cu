@@ -375,53 +375,56 @@ __global__ void __launch_bounds__(kTileThreads)
 
 // ------------------------------------------------------------------ reductions
 
-// Per-thread sum of probabilities.  For an FP32 state the per-element additions
-// stay in FP32 (compensated, Kahan, so the chunk sum is good to about one FP32
-// rounding whatever its length), folded into the FP64 accumulator every
-// kFold elements: GB300's FP64 pipe is far slower than its FP32 pipe, and one
-// FP64 add per element made this HBM-bound kernel FP64-bound.  The reductions
-// across threads and blocks are FP64.
-template <typename R>
-struct ProbSum;
-template <>
-struct ProbSum<double> {
-  double acc = 0.0;
-  __device__ __forceinline__ void add(double p) { acc += p; }
-  __device__ __forceinline__ double total() const { return acc; }
-};
-template <>
-struct ProbSum<float> {
-  static constexpr int kFold = 64;
-  double acc = 0.0;
+// Per-thread sums of probabilities.  For an FP32 state each thread adds the
+// probabilities of a chunk of kChunk of its elements in FP32 with Kahan
+// compensation (the chunk sum is good to about one FP32 rounding), and only the
+// chunk sums go into its FP64 accumulator: GB300's FP64 pipe is far slower
+// than its FP32 pipe, and one FP64 add per element made this HBM-bound kernel
+// FP64-bound.  The inner loop holds no FP64 instruction (a fold inside it is
+// predicated into every iteration).  The reductions across threads and blocks
+// are FP64.
+constexpr int kChunk = 32;
+
+struct Kahan32 {
   float s = 0.f, c = 0.f;
-  int cnt = 0;
   __device__ __forceinline__ void add(float p) {
     const float y = p - c;
     const float t = s + y;
     c = (t - s) - y;
     s = t;
-    if (++cnt == kFold) {
-      acc += (double)s - (double)c;
-      s = c = 0.f;
-      cnt = 0;
-    }
   }
-  __device__ __forceinline__ double total() const { return acc + ((double)s - (double)c); }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
 template <typename R, typename O>
 __global__ void __launch_bounds__(256)
     probs_kernel(const C2<R>* __restrict__ psi, O* __restrict__ out, uint64_t N,
                  double* __restrict__ partials) {
-  ProbSum<R> sum;
+  double acc = 0.0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
-    const C2<R> a = psi[i];
-    const R p = a.x * a.x + a.y * a.y;
-    if (out) out[i] = (O)p;
-    sum.add(p);
+  if constexpr (sizeof(R) == 8) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+      const C2<R> a = psi[i];
+      const R p = a.x * a.x + a.y * a.y;
+      if (out) out[i] = (O)p;
+      acc += p;
+    }
+  } else {
+    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < N; i0 += stride * kChunk) {
+      Kahan32 k;
+      for (int j = 0; j < kChunk; ++j) {
+        const uint64_t i = i0 + (uint64_t)j * stride;
+        if (i < N) {
+          const C2<R> a = psi[i];
+          const float p = a.x * a.x + a.y * a.y;
+          if (out) out[i] = (O)p;
+          k.add(p);
+        }
+      }
+      acc += k.value();
+    }
   }
-  const double acc = block_sum(sum.total());
+  acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
@@ -429,18 +432,33 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     probs_kernel_f32x2(const float4* __restrict__ psi2, float2* __restrict__ out2, uint64_t N2,
                        double* __restrict__ partials) {
-  ProbSum<float> sum;
+  double acc = 0.0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N2; i += stride) {
-    const float4 a = __ldcs(psi2 + i);
-    float2 p;
-    p.x = a.x * a.x + a.y * a.y;
-    p.y = a.z * a.z + a.w * a.w;
-    if (out2) __stcs(out2 + i, p);
-    sum.add(p.x);
-    sum.add(p.y);
+  constexpr int kBatch = 8;   // loads in flight per thread
+  for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < N2; i0 += stride * kChunk) {
+    Kahan32 k;
+#pragma unroll
+    for (int jb = 0; jb < kChunk; jb += kBatch) {
+      float4 a[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const uint64_t i = i0 + (uint64_t)(jb + u) * stride;
+        a[u] = i < N2 ? __ldcs(psi2 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const uint64_t i = i0 + (uint64_t)(jb + u) * stride;
+        float2 p;
+        p.x = a[u].x * a[u].x + a[u].y * a[u].y;
+        p.y = a[u].z * a[u].z + a[u].w * a[u].w;
+        if (out2 && i < N2) __stcs(out2 + i, p);
+        k.add(p.x);
+        k.add(p.y);
+      }
+    }
+    acc += k.value();
   }
-  const double acc = block_sum(sum.total());
+  acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
 
