@@ -201,24 +201,35 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 // ---------------------------------------------------------------- kernel
 //
 // One persistent CTA per SM, four roles that overlap consecutive tiles:
-//   warp 9              loader: lane j bulk-copies run j of tile i into raw stage
+//   warp 13             loader: lane j bulk-copies run j of tile i into raw stage
 //                       i % kStages of a shared-memory ring.  The 7 lowest
 //                       physical bits are always tile bits (each is a block bit
 //                       or one of the 7 lowest others), so a tile is 32
 //                       contiguous runs of 128 amplitudes (1 KiB each).
-//   warps 0-3           producers: thread = row m; split row m of tile i into its
-//                       parts, write them to the operand buffer, note the row's
-//                       squared norm and free the raw stage for the loader
-//   warp 8, one thread  MMA issuer: products of tile i into accumulator set i % 2
-//   warps 4-7           epilogue: thread = row m = tensor-memory lane (warp w
-//                       reads lanes 32*(w%4)..); add the partial sums, rescale
-//                       the row, stage the rows in shared memory, store them to
-//                       global memory in address order
-// Hand-offs are mbarriers (full/empty per raw stage, per operand buffer and per
-// accumulator set).  Every wait is bounded; a role that gives up sets a shared
-// failure flag (which ends the other roles' waits early), the loader and the
-// MMA issuer drain what they issued, and the kernel records QS_ETIMEOUT, frees
-// its tensor memory and returns.
+//   warps 0-3           producers: thread = row m = tensor-memory lane; split row
+//                       m of tile i into its parts and store them into the A
+//                       operand in tensor memory (tcgen05.st), one K half (16
+//                       columns) at a time; note the row's squared norm and free
+//                       the raw stage for the loader
+//   warp 12, one thread MMA issuer: the products of each K half of tile i (A from
+//                       tensor memory, B from shared memory) into accumulator set
+//                       i % 2, as soon as that half is stored (the producer fills
+//                       one half while the tensor cores read the other)
+//   warps 4-11          epilogue: warps w and w + 4 share the tensor-memory lanes
+//                       32*(w%4).. (thread = row m) and take 16 columns each; add
+//                       the partial sums, rescale the row, stage the rows in
+//                       shared memory, store them to global memory in address
+//                       order
+// With N = 64 an MMA that reads both operands from shared memory needs more
+// bytes per cycle than shared memory delivers; A in tensor memory leaves only B
+// (shared by all tiles) there.  Tensor-memory columns: accumulator set t at
+// 256 t (D1a +0, D2 +64, D1b +128); A parts in the free columns 192..255 and
+// 448..511.
+// Hand-offs are mbarriers (full/empty per raw stage, per K half of the operand
+// and per accumulator set).  Every wait is bounded; a role that gives up
+// sets a shared failure flag (which ends the other roles' waits early), the
+// loader and the MMA issuer drain what they issued, and the kernel records
+// QS_ETIMEOUT, frees its tensor memory and returns.
 //
 // Norm correction: a unitary block maps every row x_m to a row U x_m of the same
 // norm.  The tensor cores' FP32 accumulation loses a little magnitude on every
@@ -226,24 +237,67 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 // the host found unitary the epilogue rescales each output row to the squared
 // norm of its input row, computed by the producer in FP32.
 
-constexpr int kPipeThreads = 320;
+constexpr int kPipeThreads = 448;
+constexpr int kEpiThreads = 256;
 constexpr int kTileBytes = 4096 * 8;          // one raw tile (complex64)
 constexpr int kRun = 1024;                    // bytes of one contiguous run
-constexpr int kEpiBarrier = 1;                // named barriers of the 128 epilogue threads:
+constexpr int kEpiBarrier = 1;                // named barriers of the 256 epilogue threads:
 constexpr int kEpiSync = 2;                   // reduction (kEpiBarrier) and plain sync
 constexpr int kNormSlots = 3;                 // row norms in flight (producer -> epilogue)
+constexpr int kWarpMma = 12, kWarpLoad = 13;
 
-// Raw stages in flight, within 224 KiB of shared memory together with the
-// operand buffer, B and the 32 KiB output staging (TF32: 96 + 64 + 32 + 32 KiB;
-// BF16: 96 + 48 + 24 + 32 KiB).
+// Raw stages in flight; shared memory = the raw ring, B and the 32 KiB output
+// staging (TF32: 128 + 32 + 32 KiB; BF16: 128 + 24 + 32 KiB).
 template <int MODE>
 struct Pipe {
-  static constexpr int kStages = 3;
+  static constexpr int kStages = 4;
 };
 template <int MODE>
 constexpr size_t pipe_smem_bytes() {
-  return (size_t)(Pipe<MODE>::kStages + 1) * kTileBytes +
-         (size_t)BOps<MODE>::kParts * (BOps<MODE>::kA + BOps<MODE>::kB);
+  return (size_t)(Pipe<MODE>::kStages + 1) * kTileBytes + (size_t)BOps<MODE>::kParts * BOps<MODE>::kB;
+}
+// tensor-memory column of part p of A (BF16: 32 columns per part, two bf16 per
+// column; TF32: 64 columns per part)
+template <int MODE>
+__host__ __device__ constexpr uint32_t a_col(int p) {
+  return MODE == BM_TF32 ? (p == 0 ? 192u : 448u) : (p == 0 ? 192u : p == 1 ? 224u : 448u);
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+  if (MODE == BM_TF32) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate));
+  }
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// conditional swap of the complex entries j and j ^ 2^BIT of a 16-entry row
+template <int BIT>
+__device__ __forceinline__ void xswap16_bit(float2* x, bool sw) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << BIT)) continue;
+    const int k = j | (1 << BIT);
+    const float2 a = x[j], b = x[k];
+    x[j] = sw ? b : a;
+    x[k] = sw ? a : b;
+  }
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
@@ -283,6 +337,9 @@ __device__ __forceinline__ bool bar_or(int id, int nthreads, bool v) {
       : "memory");
   return r != 0;
 }
+__device__ __forceinline__ void bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
@@ -295,10 +352,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   constexpr int kStages = Pipe<MODE>::kStages;
   constexpr int kParts = O::kParts;
   extern __shared__ __align__(1024) unsigned char smem[];
-  // raw stage s at smem + s kTileBytes; then the operand buffer (part p of A at
-  // abase + p kA), B (part p at bbase + p kB) and the output staging
-  unsigned char* abase = smem + kStages * kTileBytes;
-  unsigned char* bbase = abase + kParts * O::kA;
+  // raw stage s at smem + s kTileBytes; then B (part p at bbase + p kB) and the
+  // output staging
+  unsigned char* bbase = smem + kStages * kTileBytes;
   float2* stage = reinterpret_cast<float2*>(bbase + kParts * O::kB);   // 128 x 32 amplitudes
   // tables used only while the roles set up their registers, kept in the staging
   unsigned char* tab = reinterpret_cast<unsigned char*>(stage);
@@ -310,13 +366,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   uint16_t* t_em = reinterpret_cast<uint16_t*>(tab + 768);              // 128 x 2 B
   uint16_t* t_ec = reinterpret_cast<uint16_t*>(tab + 1024);             // 32 x 2 B
   uint16_t* t_sh = reinterpret_cast<uint16_t*>(tab + 1088);             // 64 x 2 B
-  __shared__ __align__(8) uint64_t rfull[kStages], rempty[kStages], afull, aempty, tfull[2], tempty[2],
-      drain;
+  __shared__ __align__(8) uint64_t rfull[kStages], rempty[kStages], afull[2], aempty[2], tfull[2],
+      tempty[2], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   __shared__ uint8_t s_nt[48];
   __shared__ int s_nnt;
-  __shared__ float s_norm[kNormSlots][128];
+  __shared__ float s_norm[kNormSlots][128];   // producer -> epilogue: squared input row norms
+  __shared__ float s_part[2][128];            // epilogue column halves: squared output norms
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool unitary = (P->flags & 1) != 0;
 
@@ -335,11 +392,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       mbar_init(&rfull[s], 1);
       mbar_init(&rempty[s], 128);   // producers
     }
-    mbar_init(&afull, 128);
-    mbar_init(&aempty, 1);
     for (int b = 0; b < 2; ++b) {
+      mbar_init(&afull[b], 128);    // producers, per K half
+      mbar_init(&aempty[b], 1);     // MMA commit, per K half
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], kEpiThreads);
     }
     mbar_init(&drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -369,35 +426,44 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 
   // ---- per-role registers (from the tables; the staging is free after this)
   // producers: the address-order index of (m, c) is em[m] | ec[c], and ec
-  // deposits the bits of c, so it is linear over XOR: the index of column
-  // (jj ^ rot) G + u is e0 ^ ecg[jj] ^ ecu[u]
-  constexpr int G = MODE == BM_TF32 ? 2 : 4;   // columns per 16-byte core-matrix row
-  constexpr int NG = 32 / G;
-  uint32_t ecg[NG], ecu[G], e0 = 0;
-  // epilogue: run k = 0 of the thread and the change of address / staging index
-  // when bit b of k flips (element bit 7 + b = bit 1 + b of the high half)
-  uint64_t addr0 = 0, dA[5];
-  uint32_t idx0 = 0, dS[5];
+  // deposits the bits of c, so it is linear over XOR.  At step j of a K half the
+  // thread reads column 16 h + (j ^ sigma): sigma(lane) feeds the lane bits that
+  // the row bits leave free into the column bits sitting at address bits 0..3
+  // (with the block's qubits in ascending order those are column bits
+  // 0..ncb-1), so the 32 lanes of a read fall on 16 distinct 8-byte bank pairs;
+  // a select network then puts column 16 h + j into slot j.
+  uint32_t ecj[16], eh[2] = {0, 0};
+  int ncb = 0;
+  // epilogue: element k * 256 + et of the store loop, k in Gray-code order: its
+  // address and staging index at k = 0 and their change when bit b of k flips
+  // (element bit 8 + b = bit 2 + b of the high half)
+  uint64_t addr0 = 0, dA[4];
+  uint32_t idx0 = 0, dS[4];
   // loader: offset of run `lane`
   uint64_t run_off = 0;
   if (warp < 4) {
-    const int rot = tid & (NG - 1);
 #pragma unroll
-    for (int jj = 0; jj < NG; ++jj) ecg[jj] = t_ec[jj * G];
+    for (int a = 0; a < 4; ++a)
+      if (t_c_lo[1 << a]) ++ncb;
+    uint32_t sigma = 0;
 #pragma unroll
-    for (int u = 0; u < G; ++u) ecu[u] = t_ec[u];
-    e0 = t_em[tid] ^ t_ec[rot * G];
-  } else if (warp < 8) {
-    const int et = tid - 128;
+    for (int r = 0; r < 4; ++r)
+      if (r < ncb) sigma |= (uint32_t)((lane >> (4 - ncb + r)) & 1) << r;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) ecj[j] = t_ec[j];
+    eh[0] = t_em[tid] ^ t_ec[sigma];
+    eh[1] = eh[0] ^ t_ec[16];
+  } else if (warp < 12) {
+    const int et = tid - 128;   // 0..255
     const int m_lo = t_m_lo[et & 63], c_lo = t_c_lo[et & 63];
     addr0 = (uint64_t)(et & 63) | t_addr_hi[et >> 6];   // low 6 bits: physical bits 0..5
     idx0 = (uint32_t)((m_lo << 5) ^ c_lo ^ (m_lo & 31)) ^ t_sh[et >> 6];
 #pragma unroll
-    for (int bit = 0; bit < 5; ++bit) {
-      dA[bit] = t_addr_hi[2 << bit];
-      dS[bit] = t_sh[2 << bit];
+    for (int bit = 0; bit < 4; ++bit) {
+      dA[bit] = t_addr_hi[4 << bit];
+      dS[bit] = t_sh[4 << bit];
     }
-  } else if (warp == 9) {
+  } else if (warp == kWarpLoad) {
     run_off = t_addr_hi[2 * lane];
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -412,7 +478,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     return base;
   };
 
-  if (warp == 9) {
+  if (warp == kWarpLoad) {
     // ---------------- loader
     uint64_t issued = 0;
     for (uint64_t i = 0; i < my_tiles; ++i) {
@@ -435,106 +501,137 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         if (!mbar_wait(&rfull[t % kStages], (uint32_t)((t / kStages) & 1), nullptr))
           atomicExch(&s_fail, 1);
   } else if (warp < 4) {
-    // ---------------- producers: thread = row m; groups of G columns fill one
-    // 16-byte core-matrix row per part, groups in a lane-rotated order (the 32
-    // lanes of a write cover the 8 rows of a core matrix 4 times: 4 wavefronts
-    // for 512 bytes, no conflicts beyond that)
+    // ---------------- producers: thread = row m = tensor-memory lane
     const int m = tid;
-    const int rot = m & (NG - 1);
-    unsigned char* arow = abase + core_off<MODE>(m, 0);   // group g at + 128 g
+    const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
     for (uint64_t i = 0; i < my_tiles; ++i) {
       const int s = (int)(i % kStages);
       const uint32_t ph = (uint32_t)((i / kStages) & 1);
       const uint32_t pa = (uint32_t)(i & 1);
-      if (!mbar_wait(&rfull[s], ph, &s_fail) || !mbar_wait(&aempty, pa ^ 1u, &s_fail)) {
+      // warp-uniform outcomes: the tensor-memory stores below are warp-collective
+      const bool okr = mbar_wait(&rfull[s], ph, &s_fail);
+      if (__any_sync(0xffffffffu, !okr)) {
         atomicExch(&s_fail, 1);
         break;
       }
       const float2* raw = reinterpret_cast<const float2*>(smem + s * kTileBytes);
-      // the whole row first (all shared-memory loads in flight), then its norm
-      float2 xr[32];   // column (jj ^ rot) G + u at xr[jj G + u]
-#pragma unroll
-      for (int jj = 0; jj < NG; ++jj)
-#pragma unroll
-        for (int u = 0; u < G; ++u) xr[jj * G + u] = raw[e0 ^ ecg[jj] ^ ecu[u]];
       float nrm[4] = {0.f, 0.f, 0.f, 0.f};
+      bool ok = true;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        nrm[(2 * j) & 3] = fmaf(xr[j].x, xr[j].x, nrm[(2 * j) & 3]);
-        nrm[(2 * j + 1) & 3] = fmaf(xr[j].y, xr[j].y, nrm[(2 * j + 1) & 3]);
-      }
+      for (int h = 0; h < 2; ++h) {
+        float2 x[16];
 #pragma unroll
-      for (int jj = 0; jj < NG; ++jj) {
-        uint32_t w[kParts][4];
+        for (int j = 0; j < 16; ++j) x[j] = raw[eh[h] ^ ecj[j]];
+        if (h == 1) mbar_arrive(&rempty[s]);   // the row is in registers: raw stage s may be refilled
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          nrm[(2 * j) & 3] = fmaf(x[j].x, x[j].x, nrm[(2 * j) & 3]);
+          nrm[(2 * j + 1) & 3] = fmaf(x[j].y, x[j].y, nrm[(2 * j + 1) & 3]);
+        }
+        // slot j <- column 16 h + j
+        if (ncb > 0) xswap16_bit<0>(x, ((lane >> (4 - ncb)) & 1) != 0);
+        if (ncb > 1) xswap16_bit<1>(x, ((lane >> (5 - ncb)) & 1) != 0);
+        if (ncb > 2) xswap16_bit<2>(x, ((lane >> (6 - ncb)) & 1) != 0);
+        if (ncb > 3) xswap16_bit<3>(x, ((lane >> 3) & 1) != 0);
+        // the tensor cores have finished reading this K half of the previous tile
+        const bool oka = mbar_wait(&aempty[h], pa ^ 1u, &s_fail);
+        if (__any_sync(0xffffffffu, !oka)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if constexpr (MODE == BM_TF32) {
+          // K index 2c (Re) and 2c + 1 (Im) at columns a_col(p) + 32 h + ..
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float v = (q & 1) ? xr[jj * G + (q >> 1)].y : xr[jj * G + (q >> 1)].x;
-            w[0][q] = tf32_rna(v);
-            w[1][q] = tf32_rna(v - __uint_as_float(w[0][q]));
+          for (int q = 0; q < 2; ++q) {
+            uint32_t w0[16], w1[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float2 v = x[8 * q + j];
+              w0[2 * j] = tf32_rna(v.x);
+              w0[2 * j + 1] = tf32_rna(v.y);
+              w1[2 * j] = tf32_rna(v.x - __uint_as_float(w0[2 * j]));
+              w1[2 * j + 1] = tf32_rna(v.y - __uint_as_float(w0[2 * j + 1]));
+            }
+            tmem_st16(tmem + tlane + a_col<MODE>(0) + 32u * h + 16u * q, w0);
+            tmem_st16(tmem + tlane + a_col<MODE>(1) + 32u * h + 16u * q, w1);
           }
         } else {
-          // three bf16 parts: every residual is exact in FP32
+          // three bf16 parts (every residual is exact in FP32); column =
+          // a_col(p) + 16 h + j holds (Re, Im) of column 16 h + j
+          uint32_t w0[16], w1[16], w2[16];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float2 x = xr[jj * G + q];
-            const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
-            const float2 hf = __bfloat1622float2(h);
-            const float2 r1 = make_float2(x.x - hf.x, x.y - hf.y);
+          for (int j = 0; j < 16; ++j) {
+            const float2 v = x[j];
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(v.x, v.y);
+            const float2 hf = __bfloat1622float2(hb);
+            const float2 r1 = make_float2(v.x - hf.x, v.y - hf.y);
             const __nv_bfloat162 md = __floats2bfloat162_rn(r1.x, r1.y);
             const float2 mf = __bfloat1622float2(md);
             const __nv_bfloat162 lo = __floats2bfloat162_rn(r1.x - mf.x, r1.y - mf.y);
-            w[0][q] = bf16x2_bits(h);
-            w[1][q] = bf16x2_bits(md);
-            w[kParts - 1][q] = bf16x2_bits(lo);
+            w0[j] = bf16x2_bits(hb);
+            w1[j] = bf16x2_bits(md);
+            w2[j] = bf16x2_bits(lo);
           }
+          tmem_st16(tmem + tlane + a_col<MODE>(0) + 16u * h, w0);
+          tmem_st16(tmem + tlane + a_col<MODE>(1) + 16u * h, w1);
+          tmem_st16(tmem + tlane + a_col<MODE>(2) + 16u * h, w2);
         }
-        const uint32_t off = (uint32_t)(jj ^ rot) << 7;   // 16-byte aligned
-#pragma unroll
-        for (int p = 0; p < kParts; ++p)
-          *reinterpret_cast<uint4*>(arow + p * O::kA + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        tmem_wait_st();
+        if (h == 1) s_norm[i % kNormSlots][m] = (nrm[0] + nrm[1]) + (nrm[2] + nrm[3]);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&afull[h]);
       }
-      s_norm[i % kNormSlots][m] = (nrm[0] + nrm[1]) + (nrm[2] + nrm[3]);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&afull);
-      mbar_arrive(&rempty[s]);   // raw stage s may be refilled
+      if (!ok) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
     }
-  } else if (warp == 8) {
+  } else if (warp == kWarpMma) {
     // ---------------- MMA issuer (one thread)
     if (lane == 0) {
       const uint32_t idesc = make_idesc<MODE>();
-      const uint32_t a0 = smem_u32(abase), b0 = smem_u32(bbase);
+      const uint32_t b0 = smem_u32(bbase);
       constexpr int ksteps = 64 / O::kKStep;
+      constexpr int khalf = ksteps / 2;
       constexpr uint32_t kstep_bytes = 256;   // two K-adjacent core matrices
       for (uint64_t i = 0; i < my_tiles; ++i) {
         const uint32_t pa = (uint32_t)(i & 1);
         const int tb = (int)(i & 1);
         const uint32_t pt = (uint32_t)((i >> 1) & 1);
-        if (!mbar_wait(&afull, pa, &s_fail) || !mbar_wait(&tempty[tb], pt ^ 1u, &s_fail)) {
+        if (!mbar_wait(&tempty[tb], pt ^ 1u, &s_fail)) {
           atomicExch(&s_fail, 1);
           break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // three FP32 accumulators: D1a / D1b = A_0 B_0 over the low / high half
-        // of K (columns +0 / +128) and D2 = the correction products, smallest
-        // first (+64); the large product is summed in short chains
+        // of K (columns +0 / +128) and D2 = the correction products (+64), each
+        // half's smallest first; the large product is summed in short chains
         const uint32_t d = tmem + 256u * (uint32_t)tb;
-        for (int ks = 0; ks < ksteps; ++ks) {
-          const uint32_t dd = ks < ksteps / 2 ? d : d + 128;
-          mma<MODE>(dd, make_desc(a0 + ks * kstep_bytes, 128, O::kSBO_A),
-                    make_desc(b0 + ks * kstep_bytes, 128, O::kSBO_A), idesc,
-                    (ks % (ksteps / 2)) ? 1u : 0u);
-        }
+        bool ok = true;
+        for (int h = 0; h < 2; ++h) {
+          if (!mbar_wait(&afull[h], pa, &s_fail)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // A: 8 tensor-memory columns per K step (8 tf32 or 16 bf16)
+          for (int ks = h * khalf; ks < (h + 1) * khalf; ++ks)
+            mma_ta<MODE>(d + 128u * (uint32_t)h, tmem + a_col<MODE>(0) + 8u * ks,
+                         make_desc(b0 + ks * kstep_bytes, 128, O::kSBO_A), idesc, ks > h * khalf ? 1u : 0u);
 #pragma unroll
-        for (int p = 0; p < O::kNCorr; ++p) {
-          const uint32_t ap = a0 + (uint32_t)(corr_a<MODE>(p) * O::kA);
-          const uint32_t bp = b0 + (uint32_t)(corr_b<MODE>(p) * O::kB);
-          for (int ks = 0; ks < ksteps; ++ks)
-            mma<MODE>(d + 64, make_desc(ap + ks * kstep_bytes, 128, O::kSBO_A),
-                      make_desc(bp + ks * kstep_bytes, 128, O::kSBO_A), idesc,
-                      (p > 0 || ks > 0) ? 1u : 0u);
+          for (int p = 0; p < O::kNCorr; ++p) {
+            const uint32_t ap = tmem + a_col<MODE>(corr_a<MODE>(p));
+            const uint32_t bp = b0 + (uint32_t)(corr_b<MODE>(p) * O::kB);
+            for (int ks = h * khalf; ks < (h + 1) * khalf; ++ks)
+              mma_ta<MODE>(d + 64, ap + 8u * ks, make_desc(bp + ks * kstep_bytes, 128, O::kSBO_A), idesc,
+                           (h > 0 || p > 0 || ks > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&aempty[h]));   // this K half of the operand buffer may be refilled
         }
-        mma_commit(smem_u32(&aempty));      // the operand buffer may be refilled
+        if (!ok) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
         mma_commit(smem_u32(&tfull[tb]));   // accumulator set tb is ready
       }
       // every product issued above has finished before the tensor memory is freed
@@ -542,46 +639,39 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       if (!mbar_wait(&drain, 0, nullptr)) atomicExch(&s_fail, 1);
     }
   } else {
-    // ---------------- epilogue (warps 4..7)
-    const int m = (warp & 3) * 32 + lane;   // row of the tile = tensor-memory lane
+    // ---------------- epilogue (warps 4..11)
+    const int half = (warp - 4) >> 2;            // complex columns 16 half .. 16 half + 15
+    const int m = (warp & 3) * 32 + lane;       // row of the tile = tensor-memory lane
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     for (uint64_t i = 0; i < my_tiles; ++i) {
       const int tb = (int)(i & 1);
       const uint32_t pt = (uint32_t)((i >> 1) & 1);
-      const bool ok = mbar_wait(&tfull[tb], pt, &s_fail);
-      // collective: all 128 epilogue threads stop together (and none of them is
-      // still reading the staging of the previous tile past this point)
-      if (bar_or(kEpiBarrier, 128, !ok)) {
+      const bool okw = mbar_wait(&tfull[tb], pt, &s_fail);
+      // collective: all epilogue threads stop together (and none of them is
+      // still reading the staging or s_part of the previous tile past this point)
+      if (bar_or(kEpiBarrier, kEpiThreads, !okw)) {
         atomicExch(&s_fail, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const float nx = s_norm[i % kNormSlots][m];
-      const uint32_t d = tmem + lane_base + 256u * (uint32_t)tb;
-      // y = (D2 + D1a) + D1b: the corrections first, two loads per wait
-      float y[64];
+      const uint32_t d = tmem + lane_base + 256u * (uint32_t)tb + 32u * (uint32_t)half;
+      // y = (D2 + D1a) + D1b over this warp's 32 float columns
+      float y[32];
       {
         uint32_t a[32], b[32];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          tmem_ld32_nowait(d + 64 + 32 * h, a);
-          tmem_ld32_nowait(d + 32 * h, b);
-          tmem_wait_ld();
-          reg_after_wait32(a);
-          reg_after_wait32(b);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) y[32 * h + j] = __uint_as_float(a[j]) + __uint_as_float(b[j]);
-        }
-        tmem_ld32_nowait(d + 128, a);
-        tmem_ld32_nowait(d + 160, b);
+        tmem_ld32_nowait(d + 64, a);
+        tmem_ld32_nowait(d, b);
         tmem_wait_ld();
         reg_after_wait32(a);
         reg_after_wait32(b);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          y[j] += __uint_as_float(a[j]);
-          y[32 + j] += __uint_as_float(b[j]);
-        }
+        for (int j = 0; j < 32; ++j) y[j] = __uint_as_float(a[j]) + __uint_as_float(b[j]);
+        tmem_ld32_nowait(d + 128, b);
+        tmem_wait_ld();
+        reg_after_wait32(b);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) y[j] += __uint_as_float(b[j]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&tempty[tb]);   // accumulator set tb may be overwritten
@@ -589,40 +679,42 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       // (nx - ny) / (ny + sqrt(nx ny)) (nx - ny is exact when they are close) and
       // added with one fma: a factor rounded to FP32 near 1 (spacing 2^-23 above
       // 1, and sqrt(1 + 2^-23) rounds back to 1) would drop the small
-      // corrections systematically.
+      // corrections systematically.  ny = the two halves' sums, in a fixed order.
       float delta = 0.f;
       if (unitary) {
-        float sq[32];   // pairwise sum of the 64 squares
+        float sq[16];   // pairwise sum of this half's 32 squares
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sq[j] = fmaf(y[2 * j], y[2 * j], y[2 * j + 1] * y[2 * j + 1]);
+        for (int j = 0; j < 16; ++j) sq[j] = fmaf(y[2 * j], y[2 * j], y[2 * j + 1] * y[2 * j + 1]);
 #pragma unroll
-        for (int w = 16; w >= 1; w >>= 1)
+        for (int w = 8; w >= 1; w >>= 1)
 #pragma unroll
           for (int j = 0; j < w; ++j) sq[j] += sq[j + w];
-        const float ny = sq[0];
+        s_part[half][m] = sq[0];
+        bar_sync(kEpiSync, kEpiThreads);
+        const float ny = s_part[0][m] + s_part[1][m];
         if (ny > 0.f) delta = (nx - ny) / (ny + sqrtf(nx) * sqrtf(ny));
       }
 #pragma unroll
-      for (int c = 0; c < 32; ++c)
+      for (int j = 0; j < 16; ++j) {
+        const int c = 16 * half + j;
         stage[m * 32 + (c ^ (m & 31))] =
-            make_float2(fmaf(y[2 * c], delta, y[2 * c]), fmaf(y[2 * c + 1], delta, y[2 * c + 1]));
-      asm volatile("bar.sync %0, %1;" ::"r"(kEpiSync), "r"(128) : "memory");
-      // element k * 128 + et for the runs k in Gray-code order: the address and
-      // the staging index are XOR-linear in the bits of k, so each step flips one
+            make_float2(fmaf(y[2 * j], delta, y[2 * j]), fmaf(y[2 * j + 1], delta, y[2 * j + 1]));
+      }
+      bar_sync(kEpiSync, kEpiThreads);
       // (all staging reads first, then all stores)
-      float2 v[32];
+      float2 v[16];
       {
         uint32_t idx = idx0;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          if (k) idx ^= dS[(k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : (k & 8) ? 3 : 4];   // lowest set bit
+        for (int k = 0; k < 16; ++k) {
+          if (k) idx ^= dS[(k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : 3];   // lowest set bit
           v[k] = stage[idx];
         }
       }
       uint64_t addr = tile_base(i) | addr0;
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        if (k) addr ^= dA[(k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : (k & 8) ? 3 : 4];
+      for (int k = 0; k < 16; ++k) {
+        if (k) addr ^= dA[(k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : 3];
         __stcs(psi + addr, v[k]);
       }
     }
@@ -801,8 +893,8 @@ qs_status launch_block_pass(State* st, const void* pass_dev, const void* b_dev, 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // Each CTA holds all 512 tensor-memory columns (two sets of three 64-column
   // accumulators, 256 columns apart), so exactly one CTA may run per SM: the
-  // dynamic shared memory (raw ring, operand buffers, B: 208-224 KiB) is more
-  // than half of the SM's, and the grid is one CTA per SM.
+  // dynamic shared memory (raw ring, B, staging: 184-192 KiB) is more than half
+  // of the SM's, and the grid is one CTA per SM.
   static_assert(pipe_smem_bytes<BM_BF16>() > 120 * 1024, "one CTA per SM");
   static_assert(pipe_smem_bytes<BM_TF32>() <= 224 * 1024, "shared memory per CTA");
   uint64_t grid = (uint64_t)sms;

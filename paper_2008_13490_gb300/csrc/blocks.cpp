@@ -81,6 +81,10 @@ void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>&
         S.push_back(q);
         Smask |= 1ull << q;
       }
+    // ascending positions: local bit i of the block = its i-th lowest qubit (the
+    // kernel relies on the block qubits among the 4 lowest positions being its
+    // lowest local bits)
+    std::sort(S.begin(), S.end());
     Block b;
     for (int i = 0; i < 5; ++i) b.q[i] = S[i];
     b.U.assign(32 * 32, cd(0));
