@@ -3,15 +3,19 @@
 
 Workload (the 30-qubit configuration): n = 30 qubits, complex64 (8 GiB
 state), 40 layers of Haar-random SU(2) on every qubit plus brickwork CZ
-(seed 2001) = 1800 gates, started from |0...0>, followed by the Born-rule
-probabilities (4 GiB fp32) and their fp64 norm.  One step = one such circuit.
+(seed 2001) = 1780 gates, started from |0...0>, followed by the Born-rule
+probabilities (4 GiB fp32) and their fp64 norm.  One step = one such circuit,
+by default with the fastest complex64 method: the gates fused into 5-qubit
+blocks applied on the tcgen05 tensor cores (BF16 three-part split, FP32
+accumulation; --method selects another), the tiled FP32 SIMT path reported as
+a row of the same line.
 
 metric: "gate-passes/sec" = gates applied to the full 2^30-amplitude state per
 second (one gate pass is the work the per-gate method does in one HBM sweep).
 The JSON line also carries the real HBM sweeps and bytes, the roofline of the
-dominant kernel (the tile-pass kernel, FP32-ALU bound), the CPU oracle
-baseline, the end-to-end number through the public API with host buffers,
-launch counts and the SM clocks sampled during the timed region.
+dominant kernel (block passes: HBM-bound; tile passes: FP32-ALU bound), the
+CPU oracle baseline, the end-to-end number through the public API with host
+buffers, launch counts and the SM clocks sampled during the timed region.
 
 Multi-GPU: replicas only (each rank simulates its own copy of the workload;
 there is no exchange), value = all ranks' gates / max rank time.
@@ -56,15 +60,57 @@ def fp32_peak_tflops(mhz):
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def tile_kernel_src_hash():
-    """SHA-256 of the sources the tile-pass kernel is compiled from: a stored ncu traffic
-    figure is used only while they are unchanged."""
+METHOD_NOTE = {
+    "blocks_bf16": "5-qubit fused blocks on tcgen05 tensor cores, BF16 three-part split products, "
+                   "FP32 accumulation, per-row norm correction",
+    "blocks_tf32": "5-qubit fused blocks on tcgen05 tensor cores, TF32 two-part split products, "
+                   "FP32 accumulation, per-row norm correction",
+    "tiled": "12-qubit shared-memory tile passes, FP32 SIMT",
+    "plain": "one launch per gate, FP32",
+}
+
+# sources each kernel is compiled from: a stored ncu traffic figure is used only while
+# their hash is unchanged
+KERNEL_SOURCES = {
+    "tile": ("sv_kernels.cu", "dev_common.cuh", "internal.h"),
+    "block": ("block_tc.cu", "internal.h"),
+}
+TRAFFIC_FILES = {
+    ("tile", "tiled"): "tile_pass_kernel_traffic_n30_layered_haar_cz.json",
+    ("block", "blocks_bf16"): "block_pipe_kernel_bf16_traffic_n30_layered_haar_cz.json",
+}
+
+
+def workload_name(n, gates):
+    return (f"{n}-qubit state, {LAYERS} layers Haar SU(2) + brickwork CZ ({gates} gates, seed {SEED}) "
+            f"from |0..0>, then Born-rule probabilities")
+
+
+def kernel_src_hash(kind):
     import hashlib
     h = hashlib.sha256()
-    for f in ("sv_kernels.cu", "dev_common.cuh", "internal.h"):
+    for f in KERNEL_SOURCES[kind]:
         with open(os.path.join(ROOT, "paper_2008_13490_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def tile_kernel_src_hash():
+    return kernel_src_hash("tile")
+
+
+def stored_traffic(kind, method):
+    """DRAM bytes per launch of the dominant kernel at 30 qubits from the committed ncu
+    summary, or None when there is none or the kernel's sources have changed since."""
+    name = TRAFFIC_FILES.get((kind, method))
+    if not name:
+        return None
+    prof = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as f:
+        tr = json.load(f)
+    return tr.get("bytes_per_launch") if tr.get("kernel_src_sha256") == kernel_src_hash(kind) else None
 
 
 def block_products(tf32):
@@ -192,12 +238,16 @@ def run_reference(args, world, rank):
             times.append(t)
     per_gate = statistics.mean(times) * (1 << (N_QUBITS - SAMPLE_N))
     value = 1.0 / per_gate
+    import workloads as W
+    gates = len(W.layered_haar_cz(N_QUBITS, LAYERS, seed=SEED))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per_gate * 1800 * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": per_gate * gates * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{N_QUBITS}-qubit layered Haar SU(2) + brickwork CZ, {LAYERS} layers, "
-                                   f"seed {SEED}", "sample_qubits": SAMPLE_N},
+            "config": {"workload": workload_name(N_QUBITS, gates), "n_qubits": N_QUBITS,
+                       "precision": "complex128 (FP64 oracle)", "gates": gates,
+                       "method": "FP64 numpy oracle on the host (per-gate tensordot)",
+                       "sample_qubits": SAMPLE_N},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: 3 gates of the workload at {SAMPLE_N} qubits, "
                                        f"scaled by 2^{N_QUBITS - SAMPLE_N}"},
@@ -266,7 +316,7 @@ def run_ours(args, world, rank, local):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         qs.sv_set_basis(st, 0)
-        s2 = qs.sv_apply_circuit(st, arr)                 # host gate array -> planner -> H2D
+        s2 = qs.sv_apply_circuit(st, arr, method)         # host gate array -> planner -> H2D
         qs.sv_probs(st, out=probs, want_norm=False)
         host_probs.copy_(probs, non_blocking=True)         # D2H of the result
         torch.cuda.synchronize()
@@ -303,13 +353,7 @@ def run_ours(args, world, rank, local):
                 "peak_source": "measured copy bandwidth"}
     scale = 1e9 if roof["unit"] == "GB/s" else 1e12
     achieved = per_launch / (avg_ms * 1e-3) / scale
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "tile_pass_kernel_traffic_n30_layered_haar_cz.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            tr = json.load(f)
-        if tr.get("kernel_src_sha256") == tile_kernel_src_hash():
-            traffic = tr.get("bytes_per_launch")
+    traffic = stored_traffic(dominant, args.method) if n == N_QUBITS else None
     launches_per_step = 1 + stats["launches"] + 1   # set_basis, circuit, probabilities
     gates_per_s = world * gates * args.steps / (ms_max * 1e-3)
     line = {
@@ -317,17 +361,17 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"{n}-qubit complex64 state, {LAYERS} layers Haar SU(2) + brickwork CZ "
-                               f"({gates} gates, seed {SEED}) from |0..0>, then Born-rule probabilities",
+        "config": {"workload": workload_name(n, gates),
                    "n_qubits": n, "precision": "complex64", "gates": gates,
+                   "method": METHOD_NOTE[args.method],
                    "l2": "state (8 GiB) is larger than L2; no flush needed", "parallelism": "replicas"},
         "circuits_per_s": world * args.steps / (ms_max * 1e-3),
         "passes_per_circuit": stats["passes"], "ops_after_fusion": stats["ops_fused"],
         "hbm": {"sweeps_per_s": world * stats["passes"] * args.steps / (ms_max * 1e-3),
-                "tile_pass_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
+                "pass_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"],
                 "frac": hbm_gbs / peaks["hbm_gbs"], "bytes_per_pass": bytes_per_pass},
         "roofline": dict(roof, achieved=achieved, frac=achieved / roof["peak"],
-                         traffic=traffic if dominant == "tile" else None,
+                         traffic=traffic,
                          avg_launch_ms=avg_ms, work_per_launch=per_launch),
         "e2e": {"value": world * gates / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(s2["upload_bytes"]) + gates * arr.itemsize,
@@ -341,7 +385,8 @@ def run_ours(args, world, rank, local):
     del probs, host_probs
     torch.cuda.empty_cache()
     if not args.no_extras:
-        line["rows"] = {"qft": extra_qft(qs, torch),
+        line["rows"] = {"other_method_30q": extra_other_method(qs, torch, args.method),
+                        "qft": extra_qft(qs, torch),
                         "fp64": extra_fp64(qs, torch),
                         "small_circuits": extra_small_circuits(qs, torch),
                         "noisy_batch": extra_noisy_batch(qs, torch),
@@ -479,6 +524,49 @@ def extra_fused_blocks(qs, torch, n=32, layers=60, seed=3001):
     return out
 
 
+def extra_other_method(qs, torch, method_name, steps=3):
+    """The headline workload with the other complex64 method (tiled FP32 SIMT if the line
+    used fused blocks, else fused blocks BF16): per-step time and its dominant kernel."""
+    import workloads as W
+    other = "tiled" if method_name != "tiled" else "blocks_bf16"
+    method = {"tiled": qs.METHOD_TILED, "blocks_bf16": qs.METHOD_BLOCKS_BF16}[other]
+    arr = qs.gates_array(W.layered_haar_cz(N_QUBITS, LAYERS, seed=SEED))
+    st = qs.State(N_QUBITS, qs.QS_C64)
+    probs = torch.empty(1 << N_QUBITS, dtype=torch.float32, device="cuda")
+
+    def step():
+        qs.sv_set_basis(st, 0)
+        s = qs.sv_apply_circuit(st, arr, method)
+        qs.sv_probs(st, out=probs, want_norm=False)
+        return s
+
+    s = step()
+    torch.cuda.synchronize()
+    qs.qs_profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        s = step()
+    e1.record()
+    torch.cuda.synchronize()
+    kms, kcnt = qs.qs_profile_end()
+    ms = e0.elapsed_time(e1) / steps
+    st.close()
+    del probs
+    torch.cuda.empty_cache()
+    dom = max(kms, key=lambda k: kms[k])
+    avg = kms[dom] / max(1, kcnt[dom])
+    out = {"method": METHOD_NOTE[other], "ms_per_step": ms, "gate_passes_per_s": len(arr) / (ms * 1e-3),
+           "passes": s["passes"], "dominant_kernel": dom, "avg_launch_ms": avg,
+           "hbm_gbs_per_pass": 2 * (1 << N_QUBITS) * 8 / (avg * 1e-3) / 1e9}
+    if dom == "tile":
+        tfl = s["tile_flops"] / max(1, s["tile_launches"]) / (avg * 1e-3) / 1e12
+        out["alu_tflops"] = tfl
+        out["alu_frac"] = tfl / fp32_peak_tflops(2070.0)
+    return out
+
+
 def extra_qft(qs, torch, n=30, seed=2002):
     """30-qubit QFT (Eq. multiqubitqft) on a seeded random basis state |J>, complex64, tiled
     path (the final qubit reversal is a relabeling plus remap passes); 4096 sampled
@@ -607,8 +695,9 @@ def main():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other rows' measurements")
-    ap.add_argument("--method", default="tiled", choices=["tiled", "plain", "blocks_tf32", "blocks_bf16"],
-                    help="state-vector method of the timed workload (the default line uses tiled)")
+    ap.add_argument("--method", default="blocks_bf16", choices=["tiled", "plain", "blocks_tf32", "blocks_bf16"],
+                    help="state-vector method of the timed workload (default: the fastest, fused "
+                         "blocks with the BF16 split; the tiled path is reported as a row)")
     ap.add_argument("--only", default=None, choices=["dm", "serve", "blocks", "small", "qft", "fp64"],
                     help="run one extra row alone (for profiling) and print it")
     args = ap.parse_args()
