@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   // (with the block's qubits in ascending order those are column bits
   // 0..ncb-1), so the 32 lanes of a read fall on 16 distinct 8-byte bank pairs;
   // a select network then puts column 16 h + j into slot j.
-  uint32_t ecj[16], eh[2] = {0, 0};
+  uint32_t ecb[4], ec16 = 0, e00 = 0;   // ec[2^b], ec[16], the index of slot 0 of half 0
   int ncb = 0;
   // epilogue: element k * 256 + et of the store loop, k in Gray-code order: its
   // address and staging index at k = 0 and their change when bit b of k flips
@@ -450,9 +450,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     for (int r = 0; r < 4; ++r)
       if (r < ncb) sigma |= (uint32_t)((lane >> (4 - ncb + r)) & 1) << r;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) ecj[j] = t_ec[j];
-    eh[0] = t_em[tid] ^ t_ec[sigma];
-    eh[1] = eh[0] ^ t_ec[16];
+    for (int b = 0; b < 4; ++b) ecb[b] = t_ec[1 << b];
+    ec16 = t_ec[16];
+    e00 = t_em[tid] ^ t_ec[sigma];
   } else if (warp < 12) {
     const int et = tid - 128;   // 0..255
     const int m_lo = t_m_lo[et & 63], c_lo = t_c_lo[et & 63];
@@ -515,24 +515,40 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         break;
       }
       const float2* raw = reinterpret_cast<const float2*>(smem + s * kTileBytes);
+      // the whole row first (32 independent loads; slot j of half h at x[16 h + j],
+      // slots visited in Gray-code order: one XOR per step)
+      float2 x[32];
+      {
+        uint32_t e = e00;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          if (t) e ^= ecb[(t & 1) ? 0 : (t & 2) ? 1 : (t & 4) ? 2 : 3];
+          const int j = t ^ (t >> 1);
+          x[j] = raw[e];
+          x[16 + j] = raw[e ^ ec16];
+        }
+      }
+      mbar_arrive(&rempty[s]);   // the row is in registers: raw stage s may be refilled
       float nrm[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        nrm[(2 * j) & 3] = fmaf(x[j].x, x[j].x, nrm[(2 * j) & 3]);
+        nrm[(2 * j + 1) & 3] = fmaf(x[j].y, x[j].y, nrm[(2 * j + 1) & 3]);
+      }
+      // keep the norm here: sunk to its store it would keep a copy of the row alive
+      asm volatile("" : "+f"(nrm[0]), "+f"(nrm[1]), "+f"(nrm[2]), "+f"(nrm[3]));
+      // slot j <- column 16 h + j
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (ncb > 0) xswap16_bit<0>(x + 16 * h, ((lane >> (4 - ncb)) & 1) != 0);
+        if (ncb > 1) xswap16_bit<1>(x + 16 * h, ((lane >> (5 - ncb)) & 1) != 0);
+        if (ncb > 2) xswap16_bit<2>(x + 16 * h, ((lane >> (6 - ncb)) & 1) != 0);
+        if (ncb > 3) xswap16_bit<3>(x + 16 * h, ((lane >> 3) & 1) != 0);
+      }
       bool ok = true;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        float2 x[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) x[j] = raw[eh[h] ^ ecj[j]];
-        if (h == 1) mbar_arrive(&rempty[s]);   // the row is in registers: raw stage s may be refilled
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          nrm[(2 * j) & 3] = fmaf(x[j].x, x[j].x, nrm[(2 * j) & 3]);
-          nrm[(2 * j + 1) & 3] = fmaf(x[j].y, x[j].y, nrm[(2 * j + 1) & 3]);
-        }
-        // slot j <- column 16 h + j
-        if (ncb > 0) xswap16_bit<0>(x, ((lane >> (4 - ncb)) & 1) != 0);
-        if (ncb > 1) xswap16_bit<1>(x, ((lane >> (5 - ncb)) & 1) != 0);
-        if (ncb > 2) xswap16_bit<2>(x, ((lane >> (6 - ncb)) & 1) != 0);
-        if (ncb > 3) xswap16_bit<3>(x, ((lane >> 3) & 1) != 0);
+        float2* xh = x + 16 * h;
         // the tensor cores have finished reading this K half of the previous tile
         const bool oka = mbar_wait(&aempty[h], pa ^ 1u, &s_fail);
         if (__any_sync(0xffffffffu, !oka)) {
@@ -540,42 +556,41 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // each part is rounded from the running residual, which stays exact in
+        // FP32, and stored before the next part is formed
+        uint32_t w[16];
         if constexpr (MODE == BM_TF32) {
           // K index 2c (Re) and 2c + 1 (Im) at columns a_col(p) + 32 h + ..
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            uint32_t w0[16], w1[16];
+          for (int p = 0; p < 2; ++p)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float2 v = x[8 * q + j];
-              w0[2 * j] = tf32_rna(v.x);
-              w0[2 * j + 1] = tf32_rna(v.y);
-              w1[2 * j] = tf32_rna(v.x - __uint_as_float(w0[2 * j]));
-              w1[2 * j + 1] = tf32_rna(v.y - __uint_as_float(w0[2 * j + 1]));
+            for (int q = 0; q < 2; ++q) {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                float2& v = xh[8 * q + j];
+                w[2 * j] = tf32_rna(v.x);
+                w[2 * j + 1] = tf32_rna(v.y);
+                v.x -= __uint_as_float(w[2 * j]);
+                v.y -= __uint_as_float(w[2 * j + 1]);
+              }
+              tmem_st16(tmem + tlane + a_col<MODE>(p) + 32u * h + 16u * q, w);
             }
-            tmem_st16(tmem + tlane + a_col<MODE>(0) + 32u * h + 16u * q, w0);
-            tmem_st16(tmem + tlane + a_col<MODE>(1) + 32u * h + 16u * q, w1);
-          }
         } else {
-          // three bf16 parts (every residual is exact in FP32); column =
-          // a_col(p) + 16 h + j holds (Re, Im) of column 16 h + j
-          uint32_t w0[16], w1[16], w2[16];
+          // three bf16 parts; column a_col(p) + 16 h + j holds (Re, Im) of column 16 h + j
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float2 v = x[j];
-            const __nv_bfloat162 hb = __floats2bfloat162_rn(v.x, v.y);
-            const float2 hf = __bfloat1622float2(hb);
-            const float2 r1 = make_float2(v.x - hf.x, v.y - hf.y);
-            const __nv_bfloat162 md = __floats2bfloat162_rn(r1.x, r1.y);
-            const float2 mf = __bfloat1622float2(md);
-            const __nv_bfloat162 lo = __floats2bfloat162_rn(r1.x - mf.x, r1.y - mf.y);
-            w0[j] = bf16x2_bits(hb);
-            w1[j] = bf16x2_bits(md);
-            w2[j] = bf16x2_bits(lo);
+          for (int p = 0; p < 3; ++p) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const __nv_bfloat162 b2 = __floats2bfloat162_rn(xh[j].x, xh[j].y);
+              w[j] = bf16x2_bits(b2);
+              if (p < 2) {
+                const float2 bf = __bfloat1622float2(b2);
+                xh[j].x -= bf.x;
+                xh[j].y -= bf.y;
+              }
+            }
+            tmem_st16(tmem + tlane + a_col<MODE>(p) + 16u * h, w);
           }
-          tmem_st16(tmem + tlane + a_col<MODE>(0) + 16u * h, w0);
-          tmem_st16(tmem + tlane + a_col<MODE>(1) + 16u * h, w1);
-          tmem_st16(tmem + tlane + a_col<MODE>(2) + 16u * h, w2);
         }
         tmem_wait_st();
         if (h == 1) s_norm[i % kNormSlots][m] = (nrm[0] + nrm[1]) + (nrm[2] + nrm[3]);
