@@ -37,6 +37,7 @@ namespace {
 
 constexpr int kDmThreads = 128;
 constexpr int kDmMaxQ = 6;
+constexpr int kOpChunk = 256;   // ops staged in shared memory at a time
 
 struct DmArgs {
   int n_circuits, max_q, max_ops, K, nseg, n_ptm1, n_ptm2;
@@ -53,8 +54,10 @@ struct DmArgs {
   double* grad;
   float* scratch;              // per CTA: (nseg + K) * 4^max_q floats
   int* work;                   // work counter (zeroed before launch)
-  int8_t cz_dst[16];
+  int8_t cz_dst[16];            // CZ: Pauli string j maps to +-(string cz_dst[j])
   int8_t cz_sgn[16];
+  int8_t cz_inv[16];            // inverse: string l comes from cz_inv[l] with sign cz_isgn[l]
+  int8_t cz_isgn[16];
 };
 
 // tables in shared memory (16 floats each)
@@ -73,33 +76,61 @@ struct SubOp {
   int dtab[4];   // derivative tables per parameter (theta_x, theta_y, p, gamma) or -1
 };
 
-__device__ __forceinline__ int op_subops(const int32_t* op, int n, SubOp* s) {
-  const int code = op[0], a = op[1], b = op[2], aux = op[3];
-  auto t4 = [](SubOp& x, int q, int tab, int d0, int d1, int d2, int d3) {
-    x.kind = 0; x.q = q; x.b = -1; x.table = tab;
-    x.dtab[0] = d0; x.dtab[1] = d1; x.dtab[2] = d2; x.dtab[3] = d3;
-  };
-  switch (code) {
-    case QS_DM_X90: t4(s[0], a, TB_GX, TB_GX_T, -1, TB_GX_P, TB_GX_G); return 1;
-    case QS_DM_Y90: t4(s[0], a, TB_GY, -1, TB_GY_T, TB_GY_P, TB_GY_G); return 1;
-    case QS_DM_CZ:
-      s[0].kind = 1; s[0].q = a; s[0].b = b; s[0].table = -1;
-      s[0].dtab[0] = s[0].dtab[1] = s[0].dtab[2] = s[0].dtab[3] = -1;
-      t4(s[1], a, TB_C, -1, -1, TB_C_P, TB_C_G);
-      t4(s[2], b, TB_C, -1, -1, TB_C_P, TB_C_G);
-      return 3;
-    case QS_DM_IDLE:
-      for (int q = 0; q < n; ++q) t4(s[q], q, TB_C, -1, -1, TB_C_P, TB_C_G);
-      return n;
-    case QS_DM_PTM1:
-      s[0].kind = 2; s[0].q = a; s[0].b = -1; s[0].table = aux;
-      s[0].dtab[0] = s[0].dtab[1] = s[0].dtab[2] = s[0].dtab[3] = -1;
-      return 1;
-    default:   // QS_DM_PTM2
-      s[0].kind = 3; s[0].q = a; s[0].b = b; s[0].table = aux;
-      s[0].dtab[0] = s[0].dtab[1] = s[0].dtab[2] = s[0].dtab[3] = -1;
-      return 1;
+// number of sub-ops of an op, and sub-op j (formed on demand: an array of them
+// indexed by a loop variable would live in local memory)
+__device__ __forceinline__ int op_nsub(const int32_t* op, int n) {
+  switch (op[0]) {
+    case QS_DM_CZ: return 3;
+    case QS_DM_IDLE: return n;
+    default: return 1;
   }
+}
+__device__ __forceinline__ SubOp op_subop(const int32_t* op, int j) {
+  const int code = op[0], a = op[1], b = op[2], aux = op[3];
+  SubOp x;
+  x.kind = 0;
+  x.q = a;
+  x.b = -1;
+  x.table = TB_C;
+  x.dtab[0] = x.dtab[1] = -1;
+  x.dtab[2] = TB_C_P;
+  x.dtab[3] = TB_C_G;
+  switch (code) {
+    case QS_DM_X90:
+      x.table = TB_GX;
+      x.dtab[0] = TB_GX_T;
+      x.dtab[2] = TB_GX_P;
+      x.dtab[3] = TB_GX_G;
+      break;
+    case QS_DM_Y90:
+      x.table = TB_GY;
+      x.dtab[1] = TB_GY_T;
+      x.dtab[2] = TB_GY_P;
+      x.dtab[3] = TB_GY_G;
+      break;
+    case QS_DM_CZ:   // the permutation, then the channel on a, then on b
+      if (j == 0) {
+        x.kind = 1;
+        x.b = b;
+        x.table = -1;
+        x.dtab[2] = x.dtab[3] = -1;
+      } else if (j == 2) {
+        x.q = b;
+      }
+      break;
+    case QS_DM_IDLE: x.q = j; break;   // the channel on every qubit
+    case QS_DM_PTM1:
+      x.kind = 2;
+      x.table = aux;
+      x.dtab[2] = x.dtab[3] = -1;
+      break;
+    default:   // QS_DM_PTM2
+      x.kind = 3;
+      x.b = b;
+      x.table = aux;
+      x.dtab[2] = x.dtab[3] = -1;
+  }
+  return x;
 }
 
 __device__ bool op_valid(const int32_t* op, int n, const DmArgs& A) {
@@ -122,9 +153,28 @@ __device__ __forceinline__ int group_base(int g, int q) {
   return ((g >> (2 * q)) << (2 * q + 2)) | lo;
 }
 
-// r <- G r (or G^T r) on digit q; G row-major 4x4 (output digit, input digit)
+// r <- G r (or G^T r) on digit q; G row-major 4x4 (output digit, input digit).
+// Digit 0: one 16-byte access per group (scalar accesses 4 floats apart would
+// fall 4 lanes to a bank).
 __device__ void apply4(float* r, int n, int q, const float* G, bool transpose) {
   const int groups = 1 << (2 * (n - 1));
+  if (q == 0) {
+    float4* r4 = reinterpret_cast<float4*>(r);
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+      const float4 v = r4[g];
+      const float x[4] = {v.x, v.y, v.z, v.w};
+      float y[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        float acc = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc = fmaf(transpose ? G[e * 4 + d] : G[d * 4 + e], x[e], acc);
+        y[d] = acc;
+      }
+      r4[g] = make_float4(y[0], y[1], y[2], y[3]);
+    }
+    return;
+  }
   const int st = 1 << (2 * q);
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
     const int base = group_base(g, q);
@@ -146,8 +196,24 @@ __device__ void apply4(float* r, int n, int q, const float* G, bool transpose) {
 // sum over elements of lam . (dG r) on digit q (per-thread partial, fp64)
 __device__ double dot4(const float* lam, const float* r, int n, int q, const float* dG) {
   const int groups = 1 << (2 * (n - 1));
-  const int st = 1 << (2 * q);
   double acc = 0.0;
+  if (q == 0) {
+    const float4* r4 = reinterpret_cast<const float4*>(r);
+    const float4* l4 = reinterpret_cast<const float4*>(lam);
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+      const float4 v = r4[g], w = l4[g];
+      const float x[4] = {v.x, v.y, v.z, v.w}, l[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        float y = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) y = fmaf(dG[d * 4 + e], x[e], y);
+        acc += (double)l[d] * (double)y;
+      }
+    }
+    return acc;
+  }
+  const int st = 1 << (2 * q);
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
     const int base = group_base(g, q);
     float x[4];
@@ -175,14 +241,15 @@ __device__ void apply_cz(float* r, int n, int a, int b, const DmArgs& A, bool tr
   const int sa = 1 << (2 * a), sb = 1 << (2 * b);
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
     const int base = group_base2(g, lo, hi);
-    float x[16], y[16];
+    // forward: y[l] = isgn[l] x[inv[l]]; transpose: y[j] = sgn[j] x[dst[j]] (the
+    // permutation is applied through the shared-memory addresses of the loads, so
+    // every register index stays a compile-time constant)
+    float y[16];
 #pragma unroll
-    for (int l = 0; l < 16; ++l) x[l] = r[base + (l >> 2) * sa + (l & 3) * sb];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      // forward: y[dst[j]] = sgn[j] x[j]; transpose: y[j] = sgn[j] x[dst[j]]
-      if (transpose) y[j] = A.cz_sgn[j] * x[A.cz_dst[j]];
-      else y[A.cz_dst[j]] = A.cz_sgn[j] * x[j];
+    for (int l = 0; l < 16; ++l) {
+      const int src = transpose ? A.cz_dst[l] : A.cz_inv[l];
+      const float sg = (float)(transpose ? A.cz_sgn[l] : A.cz_isgn[l]);
+      y[l] = sg * r[base + (src >> 2) * sa + (src & 3) * sb];
     }
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[base + (l >> 2) * sa + (l & 3) * sb] = y[l];
@@ -202,6 +269,50 @@ __device__ void apply16(float* r, int n, int a, int b, const double* G, bool tra
       for (int e = 0; e < 16; ++e) acc = fmaf((float)(transpose ? G[e * 16 + d] : G[d * 16 + e]), x[e], acc);
       r[base + (d >> 2) * sa + (d & 3) * sb] = acc;
     }
+  }
+}
+
+// Forward passes over two digits a != b at once (16-element groups, local index
+// 4 d_a + d_b): an optional signed permutation applied through the load
+// addresses (CZ), then Ga on digit a, then Gb on digit b -- the same operations,
+// in the same order, as the separate one-digit passes, with one shared-memory
+// sweep and one barrier instead of two or three.
+template <bool CZ>
+__device__ void pass2(float* r, int n, int a, const float* Ga, int b, const float* Gb, const DmArgs& A) {
+  const int groups = 1 << (2 * (n - 2));
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  const int sa = 1 << (2 * a), sb = 1 << (2 * b);
+  const float* ga = Ga;   // shared memory (broadcast reads)
+  const float* gb = Gb;
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+    const int base = group_base2(g, lo, hi);
+    float x[16], y[16];
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+      const int src = CZ ? A.cz_inv[l] : l;
+      const float v = r[base + (src >> 2) * sa + (src & 3) * sb];
+      x[l] = CZ ? (float)A.cz_isgn[l] * v : v;
+    }
+#pragma unroll
+    for (int db = 0; db < 4; ++db)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        float acc = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc = fmaf(ga[d * 4 + e], x[4 * e + db], acc);
+        y[4 * d + db] = acc;
+      }
+#pragma unroll
+    for (int da = 0; da < 4; ++da)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        float acc = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc = fmaf(gb[d * 4 + e], y[4 * da + e], acc);
+        x[4 * da + d] = acc;
+      }
+#pragma unroll
+    for (int l = 0; l < 16; ++l) r[base + (l >> 2) * sa + (l & 3) * sb] = x[l];
   }
 }
 
@@ -283,18 +394,28 @@ __device__ void wht(double* z, int N) {
   }
 }
 
-__global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
+// dynamic shared memory: tables, user PTM, WHT buffer, then the Pauli vector r
+// (and, with the gradient, lambda and a scratch vector)
+constexpr int kDmHead = 16 * TB_COUNT + 16 + 128;   // floats before r (16-byte aligned)
+static_assert(kDmHead % 4 == 0, "r is accessed as float4");
+
+// GRAD: the gradient kernel (forward per sub-op with checkpoints, then the
+// adjoint sweep); otherwise probabilities / log-likelihood only, with fused
+// two-digit passes and a third of the shared memory (more CTAs per SM)
+template <bool GRAD>
+__global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmArgs A) {
   extern __shared__ __align__(16) float dsm[];
   const int D = 1 << (2 * A.max_q);
-  float* r = dsm;
-  float* lam = dsm + D;
-  float* tmp = dsm + 2 * D;
-  float* tabs = dsm + 3 * D;                 // TB_COUNT * 16
+  float* tabs = dsm;                         // TB_COUNT * 16
   float* user4 = tabs + 16 * TB_COUNT;       // 16
   double* z = (double*)(user4 + 16);         // 64 doubles (8-byte aligned: offsets are multiples of 16 floats)
+  float* r = dsm + kDmHead;
+  float* lam = r + D;                        // GRAD only
+  float* tmp = r + 2 * D;                    // GRAD only
   __shared__ double red[kDmThreads / 32];
-  __shared__ int s_c, s_ok;
-  const bool want_grad = A.grad != nullptr && A.counts != nullptr;
+  __shared__ int s_c;
+  __shared__ int4 s_ops[kOpChunk];   // the current chunk of the circuit's ops
+  constexpr bool want_grad = GRAD;
   float* my_scratch = A.scratch ? A.scratch + (size_t)blockIdx.x * (size_t)(A.nseg + A.K) * D : nullptr;
   float* ckpt = my_scratch;
   float* segbuf = my_scratch ? my_scratch + (size_t)A.nseg * D : nullptr;
@@ -311,15 +432,15 @@ __global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
     const int32_t* ops = A.ops + 4 * o0;
     const int64_t out0 = A.out_off[c];
     const int N = 1 << n;
-    // validation (device side: the arrays are caller-supplied device memory)
-    if (threadIdx.x == 0) {
-      int ok = (n >= 1 && n <= A.max_q && L >= 0 && L <= A.max_ops && A.out_off[c + 1] - out0 == N);
-      for (int k = 0; ok && k < L; ++k) ok = op_valid(ops + 4 * k, n, A);
-      s_ok = ok;
-      if (ok) build_tables(tabs, A.params + 4 * c);
-    }
+    // validation (device side: the arrays are caller-supplied device memory),
+    // ops checked by all threads in parallel
+    bool ok = n >= 1 && n <= A.max_q && L >= 0 && L <= A.max_ops && A.out_off[c + 1] - out0 == N;
+    if (ok)
+      for (int k = threadIdx.x; k < L; k += blockDim.x) ok = ok && op_valid(ops + 4 * k, n, A);
+    const bool all_ok = __syncthreads_and(ok) != 0;
+    if (all_ok && threadIdx.x == 0) build_tables(tabs, A.params + 4 * c);
     __syncthreads();
-    if (!s_ok) {
+    if (!all_ok) {
       const float nanf_ = __int_as_float(0x7fc00000);
       if (threadIdx.x == 0) {
         if (A.loglik) A.loglik[c] = __longlong_as_double(0x7ff8000000000000ll);
@@ -343,21 +464,67 @@ __global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
     }
     __syncthreads();
     // ---------------- forward
-    for (int k = 0; k < L; ++k) {
+    const int4* ops4 = reinterpret_cast<const int4*>(ops);
+    if constexpr (!GRAD) {
+      const float* C = tabs + 16 * TB_C;
+      for (int k = 0; k < L;) {
+        if ((k % kOpChunk) == 0) {   // stage the next chunk of ops (one coalesced read)
+          __syncthreads();
+          for (int t = threadIdx.x; t < kOpChunk && k + t < L; t += blockDim.x) s_ops[t] = ops4[k + t];
+          __syncthreads();
+        }
+        const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kOpChunk]);
+        const int code = op[0], a = op[1], b = op[2];
+        int used = 1;
+        if (code == QS_DM_X90 || code == QS_DM_Y90) {
+          const float* G = tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY);
+          const int32_t* nx = reinterpret_cast<const int32_t*>(&s_ops[(k + 1) % kOpChunk]);
+          if (k + 1 < L && (k + 1) % kOpChunk != 0 && (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) &&
+              nx[1] != a) {
+            // this op and the next act on different qubits: one two-digit pass
+            pass2<false>(r, n, a, G, nx[1], tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY), A);
+            used = 2;
+          } else {
+            apply4(r, n, a, G, false);
+          }
+        } else if (code == QS_DM_CZ) {
+          pass2<true>(r, n, a, C, b, C, A);
+        } else if (code == QS_DM_IDLE) {
+          for (int q = 0; q + 1 < n; q += 2) {
+            pass2<false>(r, n, q, C, q + 1, C, A);
+            __syncthreads();
+          }
+          if (n & 1) apply4(r, n, n - 1, C, false);
+        } else if (code == QS_DM_PTM1) {
+          if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
+          __syncthreads();
+          apply4(r, n, a, user4, false);
+        } else {
+          apply16(r, n, a, b, A.ptm2 + 256 * (size_t)op[3], false);
+        }
+        __syncthreads();
+        k += used;
+      }
+    }
+    for (int k = 0; GRAD && k < L; ++k) {
+      if ((k % kOpChunk) == 0) {   // stage the next chunk of ops (one coalesced read)
+        __syncthreads();
+        for (int t = threadIdx.x; t < kOpChunk && k + t < L; t += blockDim.x) s_ops[t] = ops4[k + t];
+        __syncthreads();
+      }
       if (want_grad && (k % A.K) == 0) {
         float* dst = ckpt + (size_t)(k / A.K) * D;
         for (int i = threadIdx.x; i < Dn; i += blockDim.x) dst[i] = r[i];
         __syncthreads();   // copies done before r is updated in place
       }
-      const int32_t* op = ops + 4 * k;
+      const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kOpChunk]);
       if (op[0] == QS_DM_PTM1) {
         if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
         __syncthreads();
       }
-      SubOp so[kDmMaxQ];
-      const int ns = op_subops(op, n, so);
+      const int ns = op_nsub(op, n);
       for (int j = 0; j < ns; ++j) {
-        apply_sub(r, n, so[j], tabs, user4, A, false);
+        apply_sub(r, n, op_subop(op, j), tabs, user4, A, false);
         __syncthreads();
       }
     }
@@ -381,7 +548,7 @@ __global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
       const double tot = block_sum_dm(ll, red);
       if (threadIdx.x == 0 && A.loglik) A.loglik[c] = tot;
     }
-    if (!want_grad) {
+    if constexpr (!GRAD) {
       __syncthreads();
       continue;
     }
@@ -415,11 +582,10 @@ __global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
           if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
           __syncthreads();
         }
-        SubOp so[kDmMaxQ];
-        const int ns = op_subops(op, n, so);
+        const int ns = op_nsub(op, n);
         __syncthreads();
         for (int j = 0; j < ns; ++j) {
-          apply_sub(r, n, so[j], tabs, user4, A, false);
+          apply_sub(r, n, op_subop(op, j), tabs, user4, A, false);
           __syncthreads();
         }
       }
@@ -429,8 +595,7 @@ __global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
         if (op[0] == QS_DM_PTM1) {
           if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
         }
-        SubOp so[kDmMaxQ];
-        const int ns = op_subops(op, n, so);
+        const int ns = op_nsub(op, n);
         const float* before = segbuf + (size_t)(k - k0) * D;
         __syncthreads();
         for (int j = ns - 1; j >= 0; --j) {
@@ -438,15 +603,17 @@ __global__ void __launch_bounds__(kDmThreads) dm_batch_kernel(DmArgs A) {
           for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = before[i];
           __syncthreads();
           for (int jj = 0; jj < j; ++jj) {
-            apply_sub(tmp, n, so[jj], tabs, user4, A, false);
+            apply_sub(tmp, n, op_subop(op, jj), tabs, user4, A, false);
             __syncthreads();
           }
-          if (so[j].kind == 0) {
+          const SubOp sj = op_subop(op, j);
+          if (sj.kind == 0) {
+#pragma unroll
             for (int pidx = 0; pidx < 4; ++pidx)
-              if (so[j].dtab[pidx] >= 0) g[pidx] += dot4(lam, tmp, n, so[j].q, tabs + 16 * so[j].dtab[pidx]);
+              if (sj.dtab[pidx] >= 0) g[pidx] += dot4(lam, tmp, n, sj.q, tabs + 16 * sj.dtab[pidx]);
           }
           __syncthreads();
-          apply_sub(lam, n, so[j], tabs, user4, A, true);
+          apply_sub(lam, n, sj, tabs, user4, A, true);
           __syncthreads();
         }
       }
@@ -538,19 +705,24 @@ extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, doubl
   A.loglik = loglik;
   A.grad = grad;
   cz_table(A.cz_dst, A.cz_sgn);
+  for (int j = 0; j < 16; ++j) {
+    A.cz_inv[A.cz_dst[j]] = (int8_t)j;
+    A.cz_isgn[A.cz_dst[j]] = A.cz_sgn[j];
+  }
 
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int D = 1 << (2 * A.max_q);
-  const size_t smem = (size_t)(3 * D + 16 * TB_COUNT + 16) * sizeof(float) + 64 * sizeof(double);
+  const bool with_grad = grad != nullptr;
+  const size_t smem = (size_t)(kDmHead + (with_grad ? 3 : 1) * D) * sizeof(float);
+  auto kern = with_grad ? dm_batch_kernel<true> : dm_batch_kernel<false>;
   if (smem > 48 * 1024) {
-    cudaError_t ea =
-        cudaFuncSetAttribute(dm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ea != cudaSuccess) return cuda_status(ea, "cudaFuncSetAttribute");
   }
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dm_batch_kernel, kDmThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDmThreads, smem);
   if (per_sm < 1) per_sm = 1;
   int grid = sms * per_sm;
   if (grid > b->n_circuits) grid = b->n_circuits;
@@ -564,7 +736,7 @@ extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, doubl
   A.scratch = grad ? (float*)((char*)mem + 256) : nullptr;
   e = cudaMemsetAsync(mem, 0, 256, stream);
   if (e != cudaSuccess) return cuda_status(e, "cudaMemsetAsync");
-  dm_batch_kernel<<<grid, kDmThreads, smem, stream>>>(A);
+  kern<<<grid, kDmThreads, smem, stream>>>(A);
   e = cudaGetLastError();
   cudaFreeAsync(mem, stream);
   if (e != cudaSuccess) return cuda_status(e, "dm_batch_kernel launch");
