@@ -387,6 +387,7 @@ def run_ours(args, world, rank, local):
     if not args.no_extras:
         line["rows"] = {"other_method_30q": extra_other_method(qs, torch, args.method),
                         "qft": extra_qft(qs, torch),
+                        "sv_grad": extra_sv_grad(qs, torch),
                         "fp64": extra_fp64(qs, torch),
                         "small_circuits": extra_small_circuits(qs, torch),
                         "noisy_batch": extra_noisy_batch(qs, torch),
@@ -567,6 +568,51 @@ def extra_other_method(qs, torch, method_name, steps=3):
     return out
 
 
+def extra_sv_grad(qs, torch, n=24, layers=20, seed=6001):
+    """Adjoint gradient d(sum_J w_J p_J)/d(theta) of a parameterised circuit (layers of
+    RX, RY, RZ on every qubit + brickwork CZ), complex64 at 24 qubits: time of one
+    forward pass vs one gradient (fused backward steps: uncompute, or recompute from
+    checkpoints every sqrt(L) gates)."""
+    import math
+
+    import numpy as np
+
+    import workloads as W
+    g = W.rng(seed)
+    ops = []
+    for layer in range(layers):
+        for q in range(n):
+            for name in ("RX", "RY", "RZ"):
+                ops.append((name, (q,), (float(g.uniform(-math.pi, math.pi)),), None))
+        for q in range(layer % 2, n - 1, 2):
+            ops.append(("CZ", (q, q + 1), (), None))
+    arr = qs.gates_array(ops)
+    w = torch.tensor(g.normal(size=1 << n), device="cuda")
+    st = qs.State(n, qs.QS_C64)
+    out = {"workload": f"{n}-qubit complex64, {layers} layers RX RY RZ + brickwork CZ ({len(arr)} gates, "
+                       f"{3 * n * layers} parameters), loss = sum_J w_J p_J",
+           "gates": len(arr)}
+    for key, ck in (("uncompute", 0), ("checkpoints", int(math.ceil(math.sqrt(len(arr)))))):
+        qs.sv_grad(st, arr, w, mode=0, checkpoint_every=ck)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qs.sv_grad(st, arr, w, mode=0, checkpoint_every=ck)
+        torch.cuda.synchronize()
+        out[key] = {"ms": (time.perf_counter() - t0) * 1e3, "checkpoint_every": ck}
+    qs.sv_set_basis(st, 0)
+    qs.sv_apply_circuit(st, arr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qs.sv_set_basis(st, 0)
+    qs.sv_apply_circuit(st, arr)
+    qs.sv_probs(st, want_norm=False)
+    torch.cuda.synchronize()
+    out["forward_ms"] = (time.perf_counter() - t0) * 1e3
+    out["grad_over_forward"] = out["uncompute"]["ms"] / out["forward_ms"]
+    st.close()
+    return out
+
+
 def extra_qft(qs, torch, n=30, seed=2002):
     """30-qubit QFT (Eq. multiqubitqft) on a seeded random basis state |J>, complex64, tiled
     path (the final qubit reversal is a relabeling plus remap passes); 4096 sampled
@@ -698,7 +744,8 @@ def main():
     ap.add_argument("--method", default="blocks_bf16", choices=["tiled", "plain", "blocks_tf32", "blocks_bf16"],
                     help="state-vector method of the timed workload (default: the fastest, fused "
                          "blocks with the BF16 split; the tiled path is reported as a row)")
-    ap.add_argument("--only", default=None, choices=["dm", "serve", "blocks", "small", "qft", "fp64"],
+    ap.add_argument("--only", default=None,
+                    choices=["dm", "serve", "blocks", "small", "qft", "fp64", "grad", "other"],
                     help="run one extra row alone (for profiling) and print it")
     args = ap.parse_args()
     if args.only:
@@ -707,7 +754,8 @@ def main():
         import paper_2008_13490_gb300 as qs
         qs.load()
         fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
-              "small": extra_small_circuits, "qft": extra_qft, "fp64": extra_fp64}[args.only]
+              "small": extra_small_circuits, "qft": extra_qft, "fp64": extra_fp64,
+              "grad": extra_sv_grad, "other": lambda q, t: extra_other_method(q, t, args.method)}[args.only]
         print(json.dumps({"only": args.only, "row": fn(qs, torch)}), flush=True)
         return 0
     world, rank, local = dist_setup()

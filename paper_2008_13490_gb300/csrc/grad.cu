@@ -66,58 +66,108 @@ __device__ __forceinline__ uint64_t ins0(uint64_t i, int b) {
   return ((i & ~m) << 1) | (i & m);
 }
 
-// one backward step: psi <- U^dagger psi, terms, lam <- U^dagger lam
+// Per-thread sum of the derivative terms.  For a complex64 state the terms are
+// formed in FP32 and added with Kahan compensation over chunks of kChunkG
+// groups; only the chunk sums enter FP64 (GB300's FP64 pipe is far slower than
+// its FP32 pipe, and one FP64 add per element made this HBM kernel FP64-bound).
+// For a complex128 state everything is FP64.
+constexpr int kChunkG = 32;
 template <typename R>
+struct TermSum {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct TermSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// one backward step of a K-qubit gate: psi <- U^dagger psi, the derivative
+// terms, lam <- U^dagger lam (K a template parameter so that the amplitude
+// arrays stay in registers; the matrices are converted to R once per thread)
+template <typename R, int K>
 __global__ void __launch_bounds__(256)
     adjoint_step_kernel(C2<R>* __restrict__ psi, C2<R>* __restrict__ lam, int n, GradGate g,
                         double* __restrict__ partials, int psi_is_before) {
+  constexpr int d = 1 << K;
+  constexpr int NP = K == 1 ? 3 : 1;   // parameters of the gate set: <= 3 (one-qubit), <= 1 (two-qubit)
   __shared__ double red[8];
-  double acc[3] = {0, 0, 0};
-  const int d = 1 << g.k;
-  const uint64_t groups = 1ull << (n - g.k);
+  C2<R> ud[d * d], du[NP][d * d];
+#pragma unroll
+  for (int i = 0; i < d * d; ++i) {
+    ud[i] = ld<R>(g.ud, i);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) du[p][i] = ld<R>(g.du[p], i);
+  }
+  const int np = g.np < NP ? g.np : NP;
+  double acc[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) acc[p] = 0.0;
+  const uint64_t groups = 1ull << (n - K);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const int lo = g.k == 2 ? min(g.q0, g.q1) : g.q0, hi = g.k == 2 ? max(g.q0, g.q1) : g.q0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < groups; i += stride) {
-    uint64_t base = ins0(i, lo);
-    if (g.k == 2) base = ins0(base, hi);
-    uint64_t idx[4];
-    C2<R> x[4], l[4], y[4], m[4];
-    for (int a = 0; a < d; ++a) {
-      idx[a] = base;
-      if (g.k == 1) idx[a] |= (uint64_t)a << g.q0;
-      else idx[a] |= ((uint64_t)(a >> 1) << g.q0) | ((uint64_t)(a & 1) << g.q1);
-      x[a] = psi[idx[a]];
-      l[a] = lam[idx[a]];
-    }
-    // y = state before the gate (given, or U^dagger x), m = U^dagger l
-    for (int r = 0; r < d; ++r) {
-      C2<R> s{R(0), R(0)}, t{R(0), R(0)};
-      for (int c = 0; c < d; ++c) {
-        const C2<R> u = ld<R>(g.ud, r * d + c);
-        s = cmac(s, u, x[c]);
-        t = cmac(t, u, l[c]);
+  const int lo = K == 2 ? min(g.q0, g.q1) : g.q0, hi = K == 2 ? max(g.q0, g.q1) : g.q0;
+  for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < groups; i0 += stride * kChunkG) {
+    TermSum<R> ts[NP];
+    for (int j = 0; j < kChunkG; ++j) {
+      const uint64_t i = i0 + (uint64_t)j * stride;
+      if (i >= groups) break;
+      uint64_t base = ins0(i, lo);
+      if (K == 2) base = ins0(base, hi);
+      uint64_t idx[d];
+      C2<R> x[d], l[d], y[d], m[d];
+#pragma unroll
+      for (int a = 0; a < d; ++a) {
+        idx[a] = base;
+        if (K == 1) idx[a] |= (uint64_t)a << g.q0;
+        else idx[a] |= ((uint64_t)(a >> 1) << g.q0) | ((uint64_t)(a & 1) << g.q1);
+        x[a] = psi[idx[a]];
+        l[a] = lam[idx[a]];
       }
-      y[r] = psi_is_before ? x[r] : s;
-      m[r] = t;
-    }
-    for (int p = 0; p < g.np; ++p) {
-      double a2 = 0.0;
+      // y = state before the gate (given, or U^dagger x), m = U^dagger l
+#pragma unroll
       for (int r = 0; r < d; ++r) {
-        C2<R> s{R(0), R(0)};
-        for (int c = 0; c < d; ++c) s = cmac(s, ld<R>(g.du[p], r * d + c), y[c]);
-        // Re(conj(l_r) s)
-        a2 += (double)l[r].x * (double)s.x + (double)l[r].y * (double)s.y;
+        C2<R> sy{R(0), R(0)}, t{R(0), R(0)};
+#pragma unroll
+        for (int c = 0; c < d; ++c) {
+          sy = cmac(sy, ud[r * d + c], x[c]);
+          t = cmac(t, ud[r * d + c], l[c]);
+        }
+        y[r] = psi_is_before ? x[r] : sy;
+        m[r] = t;
       }
-      acc[p] += a2;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        if (p >= np) break;
+        R a2 = R(0);
+#pragma unroll
+        for (int r = 0; r < d; ++r) {
+          C2<R> sv{R(0), R(0)};
+#pragma unroll
+          for (int c = 0; c < d; ++c) sv = cmac(sv, du[p][r * d + c], y[c]);
+          a2 = fma(l[r].x, sv.x, fma(l[r].y, sv.y, a2));   // Re(conj(l_r) sv)
+        }
+        ts[p].add(a2);
+      }
+#pragma unroll
+      for (int a = 0; a < d; ++a) {
+        if (!psi_is_before) psi[idx[a]] = y[a];
+        lam[idx[a]] = m[a];
+      }
     }
-    for (int a = 0; a < d; ++a) {
-      if (!psi_is_before) psi[idx[a]] = y[a];
-      lam[idx[a]] = m[a];
-    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] += ts[p].value();
   }
   for (int p = 0; p < 3; ++p) {
-    const double s = block_sum_g(acc[p], red);
-    if (threadIdx.x == 0) partials[3 * blockIdx.x + p] = s;
+    const double sum = block_sum_g(p < NP ? acc[p < NP ? p : 0] : 0.0, red);
+    if (threadIdx.x == 0) partials[3 * blockIdx.x + p] = sum;
   }
 }
 
@@ -213,7 +263,10 @@ qs_status backward_gate(State* st, C2<R>* psi, C2<R>* lam, const qs_gate& gate, 
   const uint64_t groups = 1ull << (st->n - g.k);
   int blocks = (int)((groups + 255) / 256);
   if (blocks > kGradBlocks) blocks = kGradBlocks;
-  adjoint_step_kernel<R><<<blocks, 256, 0, st->stream>>>(psi, lam, st->n, g, partials, before ? 1 : 0);
+  if (g.k == 1)
+    adjoint_step_kernel<R, 1><<<blocks, 256, 0, st->stream>>>(psi, lam, st->n, g, partials, before ? 1 : 0);
+  else
+    adjoint_step_kernel<R, 2><<<blocks, 256, 0, st->stream>>>(psi, lam, st->n, g, partials, before ? 1 : 0);
   QS_CUDA(cudaGetLastError());
   sum_partials3_kernel<<<1, 256, 0, st->stream>>>(partials, blocks, out3);
   QS_CUDA(cudaGetLastError());
