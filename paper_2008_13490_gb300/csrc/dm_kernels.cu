@@ -156,8 +156,14 @@ __device__ __forceinline__ int group_base(int g, int q) {
 // r <- G r (or G^T r) on digit q; G row-major 4x4 (output digit, input digit).
 // Digit 0: one 16-byte access per group (scalar accesses 4 floats apart would
 // fall 4 lanes to a bank).
-__device__ void apply4(float* r, int n, int q, const float* G, bool transpose) {
+__device__ void apply4(float* r, int n, int q, const float* Gs, bool transpose) {
   const int groups = 1 << (2 * (n - 1));
+  // the matrix in registers once per sweep
+  float G[16];
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) G[d * 4 + e] = transpose ? Gs[e * 4 + d] : Gs[d * 4 + e];
   if (q == 0) {
     float4* r4 = reinterpret_cast<float4*>(r);
     for (int g = threadIdx.x; g < groups; g += blockDim.x) {
@@ -168,7 +174,7 @@ __device__ void apply4(float* r, int n, int q, const float* G, bool transpose) {
       for (int d = 0; d < 4; ++d) {
         float acc = 0.f;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc = fmaf(transpose ? G[e * 4 + d] : G[d * 4 + e], x[e], acc);
+        for (int e = 0; e < 4; ++e) acc = fmaf(G[d * 4 + e], x[e], acc);
         y[d] = acc;
       }
       r4[g] = make_float4(y[0], y[1], y[2], y[3]);
@@ -185,7 +191,7 @@ __device__ void apply4(float* r, int n, int q, const float* G, bool transpose) {
     for (int d = 0; d < 4; ++d) {
       float acc = 0.f;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc = fmaf(transpose ? G[e * 4 + d] : G[d * 4 + e], x[e], acc);
+      for (int e = 0; e < 4; ++e) acc = fmaf(G[d * 4 + e], x[e], acc);
       y[d] = acc;
     }
 #pragma unroll
@@ -194,8 +200,11 @@ __device__ void apply4(float* r, int n, int q, const float* G, bool transpose) {
 }
 
 // sum over elements of lam . (dG r) on digit q (per-thread partial, fp64)
-__device__ double dot4(const float* lam, const float* r, int n, int q, const float* dG) {
+__device__ double dot4(const float* lam, const float* r, int n, int q, const float* dGs) {
   const int groups = 1 << (2 * (n - 1));
+  float dG[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) dG[i] = dGs[i];
   double acc = 0.0;
   if (q == 0) {
     const float4* r4 = reinterpret_cast<const float4*>(r);

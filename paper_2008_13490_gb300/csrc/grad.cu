@@ -33,21 +33,17 @@ __device__ __forceinline__ C2<R> cmac(C2<R> acc, C2<R> m, C2<R> a) {
   return acc;
 }
 
+// Gate matrices in the state's precision (converted on the host: a conversion
+// from FP64 on the device runs on the slow FP64 pipe, and the compiler may
+// repeat it at every use instead of keeping 32 values in registers).
+template <typename R>
 struct GradGate {
   int k;            // 1 or 2 qubits
   int q0, q1;       // q0 most significant of the local index
   int np;           // number of parameters
-  double ud[32];    // U^dagger, complex row-major (k=1: 2x2 in the first 8)
-  double du[3][32]; // dU/dt_p
+  C2<R> ud[16];     // U^dagger, complex row-major (k=1: 2x2 in the first 4)
+  C2<R> du[3][16];  // dU/dt_p
 };
-
-template <typename R>
-__device__ __forceinline__ C2<R> ld(const double* m, int i) {
-  C2<R> r;
-  r.x = (R)m[2 * i];
-  r.y = (R)m[2 * i + 1];
-  return r;
-}
 
 __device__ double block_sum_g(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -67,10 +63,11 @@ __device__ __forceinline__ uint64_t ins0(uint64_t i, int b) {
 }
 
 // Per-thread sum of the derivative terms.  For a complex64 state the terms are
-// formed in FP32 and added with Kahan compensation over chunks of kChunkG
-// groups; only the chunk sums enter FP64 (GB300's FP64 pipe is far slower than
-// its FP32 pipe, and one FP64 add per element made this HBM kernel FP64-bound).
-// For a complex128 state everything is FP64.
+// formed in FP32 and added with Kahan compensation, the block adds its threads'
+// sums in FP32 (pairwise) and only the per-block sums are FP64 (GB300's FP64
+// pipe is far slower than its FP32 pipe; one FP64 add per element made this
+// HBM kernel FP64-bound).  For a complex128 state everything is FP64.  Each
+// thread walks its groups in chunks of kChunkG.
 constexpr int kChunkG = 32;
 template <typename R>
 struct TermSum {
@@ -90,32 +87,47 @@ struct TermSum<float> {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// block sum of the threads' term sums, valid in thread 0: FP32 within the block
+// for a complex64 state (a pairwise tree; the blocks' sums are added in FP64),
+// FP64 throughout for a complex128 state
+__device__ __forceinline__ double block_sum_terms(float v, float* redf, double*) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) redf[w] = v;
+  __syncthreads();
+  double sum = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += (double)redf[i];
+  return sum;
+}
+__device__ __forceinline__ double block_sum_terms(double v, float*, double* red) { return block_sum_g(v, red); }
+
 // one backward step of a K-qubit gate: psi <- U^dagger psi, the derivative
 // terms, lam <- U^dagger lam (K a template parameter so that the amplitude
 // arrays stay in registers; the matrices are converted to R once per thread)
 template <typename R, int K>
 __global__ void __launch_bounds__(256)
-    adjoint_step_kernel(C2<R>* __restrict__ psi, C2<R>* __restrict__ lam, int n, GradGate g,
-                        double* __restrict__ partials, int psi_is_before) {
+    adjoint_step_kernel(C2<R>* __restrict__ psi, C2<R>* __restrict__ lam, int n, GradGate<R> g,
+                        double* __restrict__ partials, unsigned* __restrict__ done, double* __restrict__ out3,
+                        int psi_is_before) {
   constexpr int d = 1 << K;
   constexpr int NP = K == 1 ? 3 : 1;   // parameters of the gate set: <= 3 (one-qubit), <= 1 (two-qubit)
   __shared__ double red[8];
+  __shared__ float redf[8];
   C2<R> ud[d * d], du[NP][d * d];
 #pragma unroll
   for (int i = 0; i < d * d; ++i) {
-    ud[i] = ld<R>(g.ud, i);
+    ud[i] = g.ud[i];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) du[p][i] = ld<R>(g.du[p], i);
+    for (int p = 0; p < NP; ++p) du[p][i] = g.du[p][i];
   }
   const int np = g.np < NP ? g.np : NP;
-  double acc[NP];
-#pragma unroll
-  for (int p = 0; p < NP; ++p) acc[p] = 0.0;
+  TermSum<R> ts[NP];   // over all of the thread's groups (compensated for FP32)
   const uint64_t groups = 1ull << (n - K);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const int lo = K == 2 ? min(g.q0, g.q1) : g.q0, hi = K == 2 ? max(g.q0, g.q1) : g.q0;
   for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < groups; i0 += stride * kChunkG) {
-    TermSum<R> ts[NP];
     for (int j = 0; j < kChunkG; ++j) {
       const uint64_t i = i0 + (uint64_t)j * stride;
       if (i >= groups) break;
@@ -162,23 +174,30 @@ __global__ void __launch_bounds__(256)
         lam[idx[a]] = m[a];
       }
     }
-#pragma unroll
-    for (int p = 0; p < NP; ++p) acc[p] += ts[p].value();
   }
+#pragma unroll
   for (int p = 0; p < 3; ++p) {
-    const double sum = block_sum_g(p < NP ? acc[p < NP ? p : 0] : 0.0, red);
+    const R v = p < NP ? (R)ts[p < NP ? p : 0].value() : R(0);
+    const double sum = block_sum_terms(v, redf, red);
     if (threadIdx.x == 0) partials[3 * blockIdx.x + p] = sum;
   }
-}
-
-__global__ void sum_partials3_kernel(const double* __restrict__ partials, int blocks,
-                                     double* __restrict__ out) {
-  __shared__ double red[32];
-  for (int p = 0; p < 3; ++p) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < blocks; i += blockDim.x) s += partials[3 * i + p];
-    s = block_sum_g(s, red);
-    if (threadIdx.x == 0) out[p] = 2.0 * s;
+  // the last block to finish adds the blocks' sums in block order (the result
+  // does not depend on the order in which blocks finish) and resets the counter
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int p = 0; p < 3; ++p) {
+      double sum = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) sum += __ldcg(partials + 3 * b + p);
+      sum = block_sum_g(sum, red);
+      if (threadIdx.x == 0) out3[p] = 2.0 * sum;
+    }
+    if (threadIdx.x == 0) *done = 0u;
   }
 }
 
@@ -227,8 +246,9 @@ __global__ void sum_partials1_kernel(const double* __restrict__ partials, int bl
 
 constexpr int kGradBlocks = 1024;
 
-GradGate make_grad_gate(const qs_gate& gate) {
-  GradGate g;
+template <typename R>
+GradGate<R> make_grad_gate(const qs_gate& gate) {
+  GradGate<R> g;
   std::memset(&g, 0, sizeof(g));
   cd m[16];
   int dim = 0;
@@ -239,16 +259,16 @@ GradGate make_grad_gate(const qs_gate& gate) {
   for (int r = 0; r < dim; ++r)
     for (int c = 0; c < dim; ++c) {
       const cd v = std::conj(m[c * dim + r]);
-      g.ud[2 * (r * dim + c)] = v.real();
-      g.ud[2 * (r * dim + c) + 1] = v.imag();
+      g.ud[r * dim + c].x = (R)v.real();
+      g.ud[r * dim + c].y = (R)v.imag();
     }
   g.np = gate_nparams(gate.kind);
   for (int p = 0; p < g.np; ++p) {
     cd dm[16];
     gate_dmatrix(gate, p, dm);
     for (int i = 0; i < dim * dim; ++i) {
-      g.du[p][2 * i] = dm[i].real();
-      g.du[p][2 * i + 1] = dm[i].imag();
+      g.du[p][i].x = (R)dm[i].real();
+      g.du[p][i].y = (R)dm[i].imag();
     }
   }
   return g;
@@ -258,17 +278,17 @@ GradGate make_grad_gate(const qs_gate& gate) {
 // the state before the gate (read only)
 template <typename R>
 qs_status backward_gate(State* st, C2<R>* psi, C2<R>* lam, const qs_gate& gate, double* partials,
-                        double* out3, bool before) {
-  GradGate g = make_grad_gate(gate);
+                        unsigned* done, double* out3, bool before) {
+  GradGate<R> g = make_grad_gate<R>(gate);
   const uint64_t groups = 1ull << (st->n - g.k);
   int blocks = (int)((groups + 255) / 256);
   if (blocks > kGradBlocks) blocks = kGradBlocks;
   if (g.k == 1)
-    adjoint_step_kernel<R, 1><<<blocks, 256, 0, st->stream>>>(psi, lam, st->n, g, partials, before ? 1 : 0);
+    adjoint_step_kernel<R, 1><<<blocks, 256, 0, st->stream>>>(psi, lam, st->n, g, partials, done, out3,
+                                                               before ? 1 : 0);
   else
-    adjoint_step_kernel<R, 2><<<blocks, 256, 0, st->stream>>>(psi, lam, st->n, g, partials, before ? 1 : 0);
-  QS_CUDA(cudaGetLastError());
-  sum_partials3_kernel<<<1, 256, 0, st->stream>>>(partials, blocks, out3);
+    adjoint_step_kernel<R, 2><<<blocks, 256, 0, st->stream>>>(psi, lam, st->n, g, partials, done, out3,
+                                                               before ? 1 : 0);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }
@@ -290,7 +310,7 @@ qs_status run_grad(State* st, const qs_gate* gates, size_t ng, const double* w, 
   qs_status s = QS_OK;
   C2<R>* psi0 = (C2<R>*)alloc_state();
   C2<R>* lam = (C2<R>*)alloc_state();
-  double* dth = (double*)dev_alloc(st, 3 * sizeof(double) * (ng + 1) + 8 * kGradBlocks * 3);
+  double* dth = (double*)dev_alloc(st, 3 * sizeof(double) * (ng + 1) + 8 * kGradBlocks * 3 + 16);
   if (!psi0 || !lam || !dth) {
     if (dth) dev_free(st, dth, 0);
     cleanup();
@@ -298,6 +318,8 @@ qs_status run_grad(State* st, const qs_gate* gates, size_t ng, const double* w, 
     return QS_ENOMEM;
   }
   double* partials = dth + 3 * (ng + 1);
+  unsigned* done = (unsigned*)(partials + 3 * kGradBlocks);   // blocks finished (reset by the last)
+  QS_CUDA(cudaMemsetAsync(done, 0, 16, st->stream));
   QS_CUDA(cudaMemcpyAsync(psi0, st->data, sb, cudaMemcpyDeviceToDevice, st->stream));
   // ---------------- forward (tiled), keeping checkpoints in checkpoint mode
   std::vector<C2<R>*> ckpt, segbuf;
@@ -340,7 +362,7 @@ qs_status run_grad(State* st, const qs_gate* gates, size_t ng, const double* w, 
   if (s == QS_OK) {
     if (!use_ckpt) {
       for (size_t g = ng; g-- > 0 && s == QS_OK;)
-        s = backward_gate<R>(st, (C2<R>*)st->data, lam, gates[g], partials, dth + 3 * g, false);
+        s = backward_gate<R>(st, (C2<R>*)st->data, lam, gates[g], partials, done, dth + 3 * g, false);
     } else {
       for (size_t seg = ckpt.size(); seg-- > 0 && s == QS_OK;) {
         const size_t g0 = seg * (size_t)K;
@@ -352,7 +374,7 @@ qs_status run_grad(State* st, const qs_gate* gates, size_t ng, const double* w, 
           if (g + 1 < g1) s = apply_gates(st, gates + g, 1, QS_METHOD_TILED, nullptr);
         }
         for (size_t g = g1; g-- > g0 && s == QS_OK;)
-          s = backward_gate<R>(st, segbuf[g - g0], lam, gates[g], partials, dth + 3 * g, true);
+          s = backward_gate<R>(st, segbuf[g - g0], lam, gates[g], partials, done, dth + 3 * g, true);
       }
     }
   }
