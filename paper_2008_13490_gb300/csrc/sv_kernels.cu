@@ -132,28 +132,72 @@ __device__ __forceinline__ void apply_tile_op(C2<R>* v, const TileOp<R>* __restr
     }
     return;
   }
-  // TK_DIAG: v *= d[2*bit_a + bit_b] (or d[bit_a] for one-qubit diagonals)
-  const uint8_t dsrc = opp->dsrc, dbit = opp->dbit;
-  const bool two = dsrc != CS_NONE;
-  const int ua = src_bit<R>(csrc, cbit, tile, lane, warp);
-  const int ub = two ? src_bit<R>(dsrc, dbit, tile, lane, warp) : 0;
-  if (csrc != CS_REG && dsrc != CS_REG) {
-    const int idx = two ? (ua * 2 + ub) : ua;
-    const C2<R> d = csel(idx >= 2, csel(idx == 3, m0[3], m0[2]), csel(idx == 1, m0[1], m0[0]));
-    if (d.x == R(1) && d.y == R(0)) return;
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], d);
-    return;
-  }
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int ba = (csrc == CS_REG) ? ((r >> cbit) & 1) : ua;
-    const int bb = two ? ((dsrc == CS_REG) ? ((r >> dbit) & 1) : ub) : 0;
-    const int idx = two ? (ba * 2 + bb) : ba;
-    const C2<R> d = csel(idx >= 2, csel(idx == 3, m0[3], m0[2]), csel(idx == 1, m0[1], m0[0]));
-    v[r] = cmul(v[r], d);
-  }
+  // TK_DIAG ops go through DiagRun below.
 }
+
+// A run of consecutive diagonal ops (they commute) collapses, per thread, into a
+// diagonal over the 4 register bits: a scalar s (ops whose bits are all lane,
+// warp or tile-constant bits) times one 2-entry factor f[k] per register slot k
+// (ops with one bit in a register).  An op with both bits in registers
+// multiplies v directly.  flush() multiplies the collected diagonal into v once
+// the run ends.  Per op this is 1-2 complex products per thread instead of 16.
+template <typename R>
+struct DiagRun {
+  C2<R> s, f0[2], f1[2], f2[2], f3[2];   // compile-time indices only (registers)
+
+  __device__ __forceinline__ void reset() {
+    const C2<R> one{R(1), R(0)};
+    s = one;
+    f0[0] = f0[1] = f1[0] = f1[1] = f2[0] = f2[1] = f3[0] = f3[1] = one;
+  }
+  __device__ __forceinline__ void fold(int k, C2<R> e0, C2<R> e1) {
+    switch (k) {
+      case 0: f0[0] = cmul(f0[0], e0); f0[1] = cmul(f0[1], e1); break;
+      case 1: f1[0] = cmul(f1[0], e0); f1[1] = cmul(f1[1], e1); break;
+      case 2: f2[0] = cmul(f2[0], e0); f2[1] = cmul(f2[1], e1); break;
+      default: f3[0] = cmul(f3[0], e0); f3[1] = cmul(f3[1], e1); break;
+    }
+  }
+  // d[2*bit_a + bit_b] (d[bit_a] for one-qubit diagonals)
+  __device__ __forceinline__ void add(C2<R>* v, const TileOp<R>* __restrict__ opp, uint64_t tile,
+                                      int lane, int warp) {
+    const uint8_t csrc = opp->csrc, cbit = opp->cbit, dsrc = opp->dsrc, dbit = opp->dbit;
+    C2<R> d[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = opp->m0[i];
+    const bool two = dsrc != CS_NONE;
+    const bool ra = csrc == CS_REG, rb = dsrc == CS_REG;
+    if (ra && rb) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int idx = ((r >> cbit) & 1) * 2 + ((r >> dbit) & 1);
+        v[r] = cmul(v[r], csel(idx >= 2, csel(idx == 3, d[3], d[2]), csel(idx == 1, d[1], d[0])));
+      }
+      return;
+    }
+    const int ua = ra ? 0 : src_bit<R>(csrc, cbit, tile, lane, warp);
+    const int ub = (two && !rb) ? src_bit<R>(dsrc, dbit, tile, lane, warp) : 0;
+    if (ra) {   // entries for bit_a = 0 and 1 at this thread's bit_b
+      if (two) fold(cbit, csel(ub, d[1], d[0]), csel(ub, d[3], d[2]));
+      else fold(cbit, d[0], d[1]);
+    } else if (rb) {   // entries for bit_b = 0 and 1 at this thread's bit_a
+      fold(dbit, csel(ua, d[2], d[0]), csel(ua, d[3], d[1]));
+    } else {
+      const int idx = two ? (ua * 2 + ub) : ua;
+      s = cmul(s, csel(idx >= 2, csel(idx == 3, d[3], d[2]), csel(idx == 1, d[1], d[0])));
+    }
+  }
+  __device__ __forceinline__ void flush(C2<R>* v) {
+    // D(r) = s f0[r0] f1[r1] f2[r2] f3[r3] as (s f0 f1)[r & 3] * (f2 f3)[r >> 2]
+    const C2<R> a0 = cmul(s, f0[0]), a1 = cmul(s, f0[1]);
+    const C2<R> lo[4] = {cmul(a0, f1[0]), cmul(a1, f1[0]), cmul(a0, f1[1]), cmul(a1, f1[1])};
+    const C2<R> hi[4] = {cmul(f2[0], f3[0]), cmul(f2[1], f3[0]), cmul(f2[0], f3[1]),
+                         cmul(f2[1], f3[1])};
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], cmul(lo[r & 3], hi[r >> 2]));
+    reset();
+  }
+};
 
 template <typename R>
 __global__ void __launch_bounds__(kTileThreads)
@@ -238,7 +282,20 @@ __global__ void __launch_bounds__(kTileThreads)
         v[r] = sm[o];
       }
     }
-    for (int o = cur.op_begin; o < cur.op_end; ++o) apply_tile_op<R>(v, ops + o, tile, lane, warp);
+    for (int o = cur.op_begin; o < cur.op_end;) {
+      if (ops[o].kind != TK_DIAG) {
+        apply_tile_op<R>(v, ops + o, tile, lane, warp);
+        ++o;
+        continue;
+      }
+      DiagRun<R> dr;   // live only over the run
+      dr.reset();
+      do {
+        dr.add(v, ops + o, tile, lane, warp);
+        ++o;
+      } while (o < cur.op_end && ops[o].kind == TK_DIAG);
+      dr.flush(v);
+    }
   }
   {
     const TileStage sl = S[nst - 1];
@@ -335,41 +392,66 @@ __global__ void __launch_bounds__(kTileThreads)
     remap_kernel(C2<R>* __restrict__ psi, const RemapDesc* __restrict__ d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<R>* sm = reinterpret_cast<C2<R>*>(smem_raw);
+  // Every map below is linear over GF(2) in the bits of a 12-bit local index, so
+  // each is the XOR of a table entry for the low 6 and one for the high 6 bits:
+  //   address  local index -> offset in psi (deposit into the tile positions),
+  //   slot     input index -> shared-memory slot (bank swizzle, below),
+  //   gather   output index -> slot of the input amplitude it takes.
+  // The swizzle adds to every input bit i >= kB a low bit, chosen so that the
+  // kB lanes bits of a warp access hit distinct banks both when the tile is
+  // written in input order and when it is read in output order (kB = 4 bank-pair
+  // bits for 8-byte amplitudes, 3 for 16-byte ones).
+  constexpr int kB = sizeof(C2<R>) == 8 ? 4 : 3;
+  __shared__ uint64_t s_alo[64], s_ahi[64];
+  __shared__ uint16_t s_slo[64], s_shi[64], s_glo[64], s_ghi[64];
+  __shared__ uint16_t s_m[kTileBits];
   __shared__ uint64_t s_base;
-  __shared__ uint8_t s_pos[kTileBits], s_src[kTileBits];
   const int tid = threadIdx.x;
   const uint64_t tile = blockIdx.x;
   if (tid == 0) {
     uint64_t base = 0;
     for (int j = 0; j < d->n_nt; ++j) base |= ((tile >> j) & 1ull) << d->nt_pos[j];
     s_base = base;
+    int used = 0;
+    for (int k = 0; k < kB; ++k)
+      if (d->src[k] < kB) used |= 1 << d->src[k];
+    for (int i = 0; i < kTileBits; ++i) s_m[i] = (uint16_t)(1 << i);
+    for (int k = 0; k < kB; ++k) {
+      const int sk = d->src[k];
+      if (sk < kB) continue;
+      const int free_bits = ~used & ((1 << kB) - 1);
+      const int j = free_bits & -free_bits;   // lowest unused bank bit
+      used |= j;
+      s_m[sk] = (uint16_t)(s_m[sk] ^ j);
+    }
   }
-  if (tid < kTileBits) {
-    s_pos[tid] = d->pos[tid];
-    s_src[tid] = d->src[tid];
+  __syncthreads();
+  if (tid < 128) {
+    const int v = tid & 63, h = tid >> 6;   // entry v of the low (h = 0) or high table
+    uint64_t a = 0;
+    int slot = 0, gather = 0;
+    for (int i = 0; i < 6; ++i)
+      if ((v >> i) & 1) {
+        a |= 1ull << d->pos[6 * h + i];
+        slot ^= s_m[6 * h + i];
+        gather ^= s_m[d->src[6 * h + i]];
+      }
+    (h ? s_ahi : s_alo)[v] = a;
+    (h ? s_shi : s_slo)[v] = (uint16_t)slot;
+    (h ? s_ghi : s_glo)[v] = (uint16_t)gather;
   }
   __syncthreads();
   const uint64_t base = s_base;
-#pragma unroll 4
+#pragma unroll
   for (int r = 0; r < (1 << kTileBits) / kTileThreads; ++r) {
     const int L = tid + r * kTileThreads;
-    uint64_t off = base;
-    for (int i = 0; i < kTileBits; ++i)
-      if ((L >> i) & 1) off |= 1ull << s_pos[i];
-    sm[L] = psi[off];
+    sm[s_slo[L & 63] ^ s_shi[L >> 6]] = psi[base | s_alo[L & 63] | s_ahi[L >> 6]];
   }
   __syncthreads();
-#pragma unroll 4
+#pragma unroll
   for (int r = 0; r < (1 << kTileBits) / kTileThreads; ++r) {
-    const int Lout = tid + r * kTileThreads;
-    uint64_t off = base;
-    int Lin = 0;
-    for (int j = 0; j < kTileBits; ++j)
-      if ((Lout >> j) & 1) {
-        off |= 1ull << s_pos[j];
-        Lin |= 1 << s_src[j];
-      }
-    psi[off] = sm[Lin];
+    const int L = tid + r * kTileThreads;
+    psi[base | s_alo[L & 63] | s_ahi[L >> 6]] = sm[s_glo[L & 63] ^ s_ghi[L >> 6]];
   }
 }
 

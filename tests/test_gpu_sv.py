@@ -67,6 +67,23 @@ def test_tiled_all_gates(qs, n, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [12, 13, 16])
+def test_tiled_diagonal_runs(qs, n, prec):
+    # long runs of commuting diagonals (CZ, CP, RZ, S, T, U1, R(k)) on register,
+    # lane, warp and tile-constant bits, broken up by a few H gates
+    ops = W.random_gate_mix(n, 500, seed=3000 + n, two_q_fraction=0.6,
+                            names1=["RZ", "S", "T", "TDG", "U1", "RK", "Z", "H"],
+                            names2=["CZ", "CP"])
+    g = W.rng(n + 17)
+    psi0 = W.random_state(n, g)
+    if prec == 0:
+        psi0 = psi0.astype(np.complex64)
+    ref = SV.apply_circuit(psi0.astype(np.complex128), n, ops)
+    out, _ = run(qs, n, ops, prec, psi0=psi0)
+    check(out, ref, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n", [3, 12, 16])
 def test_plain_method(qs, n, prec):
     ops = W.random_gate_mix(n, 80, seed=77 + n)
