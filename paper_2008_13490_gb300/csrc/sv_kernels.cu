@@ -397,11 +397,16 @@ __global__ void __launch_bounds__(kTileThreads)
   //   address  local index -> offset in psi (deposit into the tile positions),
   //   slot     input index -> shared-memory slot (bank swizzle, below),
   //   gather   output index -> slot of the input amplitude it takes.
-  // The swizzle adds to every input bit i >= kB a low bit, chosen so that the
-  // kB lanes bits of a warp access hit distinct banks both when the tile is
-  // written in input order and when it is read in output order (kB = 4 bank-pair
-  // bits for 8-byte amplitudes, 3 for 16-byte ones).
-  constexpr int kB = sizeof(C2<R>) == 8 ? 4 : 3;
+  // complex64 moves amplitude pairs (local bit 0 = position 0, which every remap
+  // holds): one 16-byte global access per pair and one 16-byte shared store, the
+  // two gathered amplitudes read separately.  The swizzle adds to every input
+  // bit i >= kB a low slot bit, chosen so that the lanes of a wavefront hit
+  // distinct banks both when the tile is written in input order and when it is
+  // read in output order: kB = 4 bank-pair bits, output bits 1-4 over the lanes
+  // of a half-warp (8-byte reads of complex64 pairs); kB = 3, output bits 0-2
+  // over a quarter-warp (16-byte complex128 amplitudes).
+  constexpr bool kPairs = sizeof(C2<R>) == 8;
+  constexpr int kB = kPairs ? 4 : 3, kK0 = kPairs ? 1 : 0;
   __shared__ uint64_t s_alo[64], s_ahi[64];
   __shared__ uint16_t s_slo[64], s_shi[64], s_glo[64], s_ghi[64];
   __shared__ uint16_t s_m[kTileBits];
@@ -413,10 +418,10 @@ __global__ void __launch_bounds__(kTileThreads)
     for (int j = 0; j < d->n_nt; ++j) base |= ((tile >> j) & 1ull) << d->nt_pos[j];
     s_base = base;
     int used = 0;
-    for (int k = 0; k < kB; ++k)
+    for (int k = kK0; k < kK0 + kB; ++k)
       if (d->src[k] < kB) used |= 1 << d->src[k];
     for (int i = 0; i < kTileBits; ++i) s_m[i] = (uint16_t)(1 << i);
-    for (int k = 0; k < kB; ++k) {
+    for (int k = kK0; k < kK0 + kB; ++k) {
       const int sk = d->src[k];
       if (sk < kB) continue;
       const int free_bits = ~used & ((1 << kB) - 1);
@@ -442,13 +447,37 @@ __global__ void __launch_bounds__(kTileThreads)
   }
   __syncthreads();
   const uint64_t base = s_base;
+  if (kPairs && d->pos[0] == 0) {
+    // slot(L ^ 1) = slot(L) ^ 1: a pair fills one aligned 16-byte slot pair
+    float4* sm4 = reinterpret_cast<float4*>(smem_raw);
+    const float* smf = reinterpret_cast<const float*>(smem_raw);
+    float4* psi4 = reinterpret_cast<float4*>(psi);
+    const int g1 = s_glo[1];   // gather(L ^ 1) = gather(L) ^ g1
 #pragma unroll
+    for (int r = 0; r < (1 << kTileBits) / (2 * kTileThreads); ++r) {
+      const int L = 2 * (tid + r * kTileThreads);
+      const float4 q = __ldcs(psi4 + ((base | s_alo[L & 63] | s_ahi[L >> 6]) >> 1));
+      const int sl = s_slo[L & 63] ^ s_shi[L >> 6];
+      sm4[sl >> 1] = (sl & 1) ? make_float4(q.z, q.w, q.x, q.y) : q;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < (1 << kTileBits) / (2 * kTileThreads); ++r) {
+      const int L = 2 * (tid + r * kTileThreads);
+      const int g = s_glo[L & 63] ^ s_ghi[L >> 6];
+      const float2 a0 = *reinterpret_cast<const float2*>(smf + 2 * g);
+      const float2 a1 = *reinterpret_cast<const float2*>(smf + 2 * (g ^ g1));
+      __stcs(psi4 + ((base | s_alo[L & 63] | s_ahi[L >> 6]) >> 1), make_float4(a0.x, a0.y, a1.x, a1.y));
+    }
+    return;
+  }
+#pragma unroll 4
   for (int r = 0; r < (1 << kTileBits) / kTileThreads; ++r) {
     const int L = tid + r * kTileThreads;
     sm[s_slo[L & 63] ^ s_shi[L >> 6]] = psi[base | s_alo[L & 63] | s_ahi[L >> 6]];
   }
   __syncthreads();
-#pragma unroll
+#pragma unroll 4
   for (int r = 0; r < (1 << kTileBits) / kTileThreads; ++r) {
     const int L = tid + r * kTileThreads;
     psi[base | s_alo[L & 63] | s_ahi[L >> 6]] = sm[s_glo[L & 63] ^ s_ghi[L >> 6]];
