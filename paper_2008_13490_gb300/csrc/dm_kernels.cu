@@ -199,13 +199,27 @@ __device__ void apply4(float* r, int n, int q, const float* Gs, bool transpose) 
   }
 }
 
-// sum over elements of lam . (dG r) on digit q (per-thread partial, fp64)
+// FP32 sum with Kahan compensation (GB300's FP64 pipe is far slower than its
+// FP32 pipe; one FP64 multiply-add and two conversions per element made the
+// gradient sweep FP64-bound)
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// sum over elements of lam . (dG r) on digit q (per-thread partial)
 __device__ double dot4(const float* lam, const float* r, int n, int q, const float* dGs) {
   const int groups = 1 << (2 * (n - 1));
   float dG[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) dG[i] = dGs[i];
-  double acc = 0.0;
+  KahanF acc;
   if (q == 0) {
     const float4* r4 = reinterpret_cast<const float4*>(r);
     const float4* l4 = reinterpret_cast<const float4*>(lam);
@@ -217,10 +231,10 @@ __device__ double dot4(const float* lam, const float* r, int n, int q, const flo
         float y = 0.f;
 #pragma unroll
         for (int e = 0; e < 4; ++e) y = fmaf(dG[d * 4 + e], x[e], y);
-        acc += (double)l[d] * (double)y;
+        acc.add(l[d] * y);
       }
     }
-    return acc;
+    return acc.value();
   }
   const int st = 1 << (2 * q);
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
@@ -233,10 +247,10 @@ __device__ double dot4(const float* lam, const float* r, int n, int q, const flo
       float y = 0.f;
 #pragma unroll
       for (int e = 0; e < 4; ++e) y = fmaf(dG[d * 4 + e], x[e], y);
-      acc += (double)lam[base + d * st] * (double)y;
+      acc.add(lam[base + d * st] * y);
     }
   }
-  return acc;
+  return acc.value();
 }
 
 __device__ __forceinline__ int group_base2(int g, int lo_q, int hi_q) {
@@ -425,9 +439,11 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
   __shared__ int s_c;
   __shared__ int4 s_ops[kOpChunk];   // the current chunk of the circuit's ops
   constexpr bool want_grad = GRAD;
-  float* my_scratch = A.scratch ? A.scratch + (size_t)blockIdx.x * (size_t)(A.nseg + A.K) * D : nullptr;
+  float* my_scratch =
+      A.scratch ? A.scratch + (size_t)blockIdx.x * (size_t)(A.nseg + A.K + kDmMaxQ) * D : nullptr;
   float* ckpt = my_scratch;
   float* segbuf = my_scratch ? my_scratch + (size_t)A.nseg * D : nullptr;
+  float* subst = my_scratch ? my_scratch + (size_t)(A.nseg + A.K) * D : nullptr;
 
   for (;;) {
     if (threadIdx.x == 0) s_c = atomicAdd(A.work, 1);
@@ -607,16 +623,24 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
         const int ns = op_nsub(op, n);
         const float* before = segbuf + (size_t)(k - k0) * D;
         __syncthreads();
-        for (int j = ns - 1; j >= 0; --j) {
-          // tmp = state before sub-op j
-          for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = before[i];
+        // the states before the sub-ops, once: s_0 = before, s_{j+1} = sub_j s_j;
+        // the last stays in tmp, the earlier ones with parameters go to subst
+        for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = before[i];
+        __syncthreads();
+        for (int j = 0; j + 1 < ns; ++j) {
+          apply_sub(tmp, n, op_subop(op, j), tabs, user4, A, false);
           __syncthreads();
-          for (int jj = 0; jj < j; ++jj) {
-            apply_sub(tmp, n, op_subop(op, jj), tabs, user4, A, false);
-            __syncthreads();
-          }
+          if (j + 2 < ns && op_subop(op, j + 1).kind == 0)
+            for (int i = threadIdx.x; i < Dn; i += blockDim.x) subst[(size_t)(j + 1) * D + i] = tmp[i];
+        }
+        for (int j = ns - 1; j >= 0; --j) {
           const SubOp sj = op_subop(op, j);
           if (sj.kind == 0) {
+            if (j + 1 < ns) {   // tmp = s_j (the previous sub-op's reads of tmp ended at its barrier)
+              const float* sv = j == 0 ? before : subst + (size_t)j * D;
+              for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = sv[i];
+              __syncthreads();
+            }
 #pragma unroll
             for (int pidx = 0; pidx < 4; ++pidx)
               if (sj.dtab[pidx] >= 0) g[pidx] += dot4(lam, tmp, n, sj.q, tabs + 16 * sj.dtab[pidx]);
@@ -736,7 +760,7 @@ extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, doubl
   int grid = sms * per_sm;
   if (grid > b->n_circuits) grid = b->n_circuits;
 
-  const size_t scratch_floats = grad ? (size_t)grid * (A.nseg + A.K) * D : 0;
+  const size_t scratch_floats = grad ? (size_t)grid * (A.nseg + A.K + kDmMaxQ) * D : 0;
   const size_t bytes = 256 + scratch_floats * sizeof(float);
   void* mem = nullptr;
   cudaError_t e = cudaMallocAsync(&mem, bytes, stream);
