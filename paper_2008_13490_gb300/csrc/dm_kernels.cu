@@ -199,58 +199,71 @@ __device__ void apply4(float* r, int n, int q, const float* Gs, bool transpose) 
   }
 }
 
-// FP32 sum with Kahan compensation (GB300's FP64 pipe is far slower than its
-// FP32 pipe; one FP64 multiply-add and two conversions per element made the
-// gradient sweep FP64-bound)
-struct KahanF {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
-// sum over elements of lam . (dG r) on digit q (per-thread partial)
-__device__ double dot4(const float* lam, const float* r, int n, int q, const float* dGs) {
+// Adjoint of one 4x4 sub-op on digit q in one sweep.  Every derivative term
+// lam . (dG x) (lam after the sub-op, x the state before it) equals
+// sum_{d,e} dG[d][e] M[d][e] with M = sum over groups of lam x^T, so the sweep
+// accumulates M (16 FP32 sums per thread), updates lam <- G^T lam in place, and
+// contracts M with each parameter's derivative table once at the end (per-thread
+// partials added to g in FP64).  x may be global (a stored state) or shared.
+__device__ __forceinline__ void adj4(float* lam, const float* x_src, int n, int q, const float* Gs,
+                                     const float* tabs, const int* dtab, double* g) {
   const int groups = 1 << (2 * (n - 1));
-  float dG[16];
+  float G[16], M[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) dG[i] = dGs[i];
-  KahanF acc;
+  for (int i = 0; i < 16; ++i) {
+    G[i] = Gs[i];
+    M[i] = 0.f;
+  }
+  auto group = [&](const float (&x)[4], float (&l)[4]) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) M[d * 4 + e] = fmaf(l[d], x[e], M[d * 4 + e]);
+    float y[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float acc = 0.f;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) acc = fmaf(G[d * 4 + e], l[d], acc);
+      y[e] = acc;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) l[e] = y[e];
+  };
   if (q == 0) {
-    const float4* r4 = reinterpret_cast<const float4*>(r);
-    const float4* l4 = reinterpret_cast<const float4*>(lam);
-    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-      const float4 v = r4[g], w = l4[g];
-      const float x[4] = {v.x, v.y, v.z, v.w}, l[4] = {w.x, w.y, w.z, w.w};
+    const float4* x4 = reinterpret_cast<const float4*>(x_src);
+    float4* l4 = reinterpret_cast<float4*>(lam);
+    for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+      const float4 v = x4[gi], w = l4[gi];
+      const float x[4] = {v.x, v.y, v.z, v.w};
+      float l[4] = {w.x, w.y, w.z, w.w};
+      group(x, l);
+      l4[gi] = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  } else {
+    const int st = 1 << (2 * q);
+    for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+      const int base = group_base(gi, q);
+      float x[4], l[4];
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
-        float y = 0.f;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) y = fmaf(dG[d * 4 + e], x[e], y);
-        acc.add(l[d] * y);
+        x[d] = x_src[base + d * st];
+        l[d] = lam[base + d * st];
       }
-    }
-    return acc.value();
-  }
-  const int st = 1 << (2 * q);
-  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-    const int base = group_base(g, q);
-    float x[4];
+      group(x, l);
 #pragma unroll
-    for (int d = 0; d < 4; ++d) x[d] = r[base + d * st];
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      float y = 0.f;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) y = fmaf(dG[d * 4 + e], x[e], y);
-      acc.add(lam[base + d * st] * y);
+      for (int d = 0; d < 4; ++d) lam[base + d * st] = l[d];
     }
   }
-  return acc.value();
+#pragma unroll
+  for (int pidx = 0; pidx < 4; ++pidx)
+    if (dtab[pidx] >= 0) {
+      const float* dG = tabs + 16 * dtab[pidx];
+      float acc = 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc = fmaf(dG[i], M[i], acc);
+      g[pidx] += (double)acc;
+    }
 }
 
 __device__ __forceinline__ int group_base2(int g, int lo_q, int hi_q) {
@@ -417,14 +430,40 @@ __device__ void wht(double* z, int N) {
   }
 }
 
+// One op forward with the fused two-digit passes: CZ as its permutation and both
+// channels in one pass, the idle op as channel pairs -- the operations of its
+// sub-ops in the same order, with the same arithmetic.  user4 holds the op's PTM
+// for QS_DM_PTM1.  Ends with a barrier.
+__device__ void apply_op_fused(float* r, int n, const int32_t* op, const float* tabs,
+                               const float* user4, const DmArgs& A) {
+  const int code = op[0], a = op[1], b = op[2];
+  const float* C = tabs + 16 * TB_C;
+  if (code == QS_DM_X90 || code == QS_DM_Y90) {
+    apply4(r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), false);
+  } else if (code == QS_DM_CZ) {
+    pass2<true>(r, n, a, C, b, C, A);
+  } else if (code == QS_DM_IDLE) {
+    for (int q = 0; q + 1 < n; q += 2) {
+      pass2<false>(r, n, q, C, q + 1, C, A);
+      __syncthreads();
+    }
+    if (n & 1) apply4(r, n, n - 1, C, false);
+  } else if (code == QS_DM_PTM1) {
+    apply4(r, n, a, user4, false);
+  } else {
+    apply16(r, n, a, b, A.ptm2 + 256 * (size_t)op[3], false);
+  }
+  __syncthreads();
+}
+
 // dynamic shared memory: tables, user PTM, WHT buffer, then the Pauli vector r
 // (and, with the gradient, lambda and a scratch vector)
 constexpr int kDmHead = 16 * TB_COUNT + 16 + 128;   // floats before r (16-byte aligned)
 static_assert(kDmHead % 4 == 0, "r is accessed as float4");
 
-// GRAD: the gradient kernel (forward per sub-op with checkpoints, then the
-// adjoint sweep); otherwise probabilities / log-likelihood only, with fused
-// two-digit passes and a third of the shared memory (more CTAs per SM)
+// GRAD: the gradient kernel (forward with checkpoints, then the adjoint sweep);
+// otherwise probabilities / log-likelihood only, with one-qubit gate pairs fused
+// too and a third of the shared memory (more CTAs per SM)
 template <bool GRAD>
 __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmArgs A) {
   extern __shared__ __align__(16) float dsm[];
@@ -491,7 +530,6 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
     // ---------------- forward
     const int4* ops4 = reinterpret_cast<const int4*>(ops);
     if constexpr (!GRAD) {
-      const float* C = tabs + 16 * TB_C;
       for (int k = 0; k < L;) {
         if ((k % kOpChunk) == 0) {   // stage the next chunk of ops (one coalesced read)
           __syncthreads();
@@ -499,36 +537,23 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
           __syncthreads();
         }
         const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kOpChunk]);
-        const int code = op[0], a = op[1], b = op[2];
-        int used = 1;
-        if (code == QS_DM_X90 || code == QS_DM_Y90) {
-          const float* G = tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY);
-          const int32_t* nx = reinterpret_cast<const int32_t*>(&s_ops[(k + 1) % kOpChunk]);
-          if (k + 1 < L && (k + 1) % kOpChunk != 0 && (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) &&
-              nx[1] != a) {
-            // this op and the next act on different qubits: one two-digit pass
-            pass2<false>(r, n, a, G, nx[1], tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY), A);
-            used = 2;
-          } else {
-            apply4(r, n, a, G, false);
-          }
-        } else if (code == QS_DM_CZ) {
-          pass2<true>(r, n, a, C, b, C, A);
-        } else if (code == QS_DM_IDLE) {
-          for (int q = 0; q + 1 < n; q += 2) {
-            pass2<false>(r, n, q, C, q + 1, C, A);
-            __syncthreads();
-          }
-          if (n & 1) apply4(r, n, n - 1, C, false);
-        } else if (code == QS_DM_PTM1) {
+        const int code = op[0], a = op[1];
+        const int32_t* nx = reinterpret_cast<const int32_t*>(&s_ops[(k + 1) % kOpChunk]);
+        if ((code == QS_DM_X90 || code == QS_DM_Y90) && k + 1 < L && (k + 1) % kOpChunk != 0 &&
+            (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) && nx[1] != a) {
+          // this op and the next act on different qubits: one two-digit pass
+          pass2<false>(r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), nx[1],
+                       tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY), A);
+          __syncthreads();
+          k += 2;
+          continue;
+        }
+        if (code == QS_DM_PTM1) {
           if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
           __syncthreads();
-          apply4(r, n, a, user4, false);
-        } else {
-          apply16(r, n, a, b, A.ptm2 + 256 * (size_t)op[3], false);
         }
-        __syncthreads();
-        k += used;
+        apply_op_fused(r, n, op, tabs, user4, A);
+        ++k;
       }
     }
     for (int k = 0; GRAD && k < L; ++k) {
@@ -547,11 +572,7 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
         if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
         __syncthreads();
       }
-      const int ns = op_nsub(op, n);
-      for (int j = 0; j < ns; ++j) {
-        apply_sub(r, n, op_subop(op, j), tabs, user4, A, false);
-        __syncthreads();
-      }
+      apply_op_fused(r, n, op, tabs, user4, A);
     }
     // ---------------- probabilities: p = 2^{-n/2} WHT(r on {I,Z}^n)
     for (int S = threadIdx.x; S < N; S += blockDim.x) z[S] = (double)r[zs_index(S, n)];
@@ -607,12 +628,8 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
           if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
           __syncthreads();
         }
-        const int ns = op_nsub(op, n);
         __syncthreads();
-        for (int j = 0; j < ns; ++j) {
-          apply_sub(r, n, op_subop(op, j), tabs, user4, A, false);
-          __syncthreads();
-        }
+        apply_op_fused(r, n, op, tabs, user4, A);
       }
       __syncthreads();
       for (int k = k1 - 1; k >= k0; --k) {
@@ -625,28 +642,24 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
         __syncthreads();
         // the states before the sub-ops, once: s_0 = before, s_{j+1} = sub_j s_j;
         // the last stays in tmp, the earlier ones with parameters go to subst
-        for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = before[i];
-        __syncthreads();
-        for (int j = 0; j + 1 < ns; ++j) {
-          apply_sub(tmp, n, op_subop(op, j), tabs, user4, A, false);
+        if (ns > 1) {
+          for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = before[i];
           __syncthreads();
-          if (j + 2 < ns && op_subop(op, j + 1).kind == 0)
-            for (int i = threadIdx.x; i < Dn; i += blockDim.x) subst[(size_t)(j + 1) * D + i] = tmp[i];
+          for (int j = 0; j + 1 < ns; ++j) {
+            apply_sub(tmp, n, op_subop(op, j), tabs, user4, A, false);
+            __syncthreads();
+            if (j + 2 < ns && op_subop(op, j + 1).kind == 0)
+              for (int i = threadIdx.x; i < Dn; i += blockDim.x) subst[(size_t)(j + 1) * D + i] = tmp[i];
+          }
         }
         for (int j = ns - 1; j >= 0; --j) {
           const SubOp sj = op_subop(op, j);
           if (sj.kind == 0) {
-            if (j + 1 < ns) {   // tmp = s_j (the previous sub-op's reads of tmp ended at its barrier)
-              const float* sv = j == 0 ? before : subst + (size_t)j * D;
-              for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = sv[i];
-              __syncthreads();
-            }
-#pragma unroll
-            for (int pidx = 0; pidx < 4; ++pidx)
-              if (sj.dtab[pidx] >= 0) g[pidx] += dot4(lam, tmp, n, sj.q, tabs + 16 * sj.dtab[pidx]);
+            const float* sv = j + 1 == ns ? (ns > 1 ? tmp : before) : (j == 0 ? before : subst + (size_t)j * D);
+            adj4(lam, sv, n, sj.q, tabs + 16 * sj.table, tabs, sj.dtab, g);
+          } else {
+            apply_sub(lam, n, sj, tabs, user4, A, true);
           }
-          __syncthreads();
-          apply_sub(lam, n, sj, tabs, user4, A, true);
           __syncthreads();
         }
       }
