@@ -23,6 +23,8 @@ noisy        the batched noisy-circuit forward model, multinomial
              log-likelihood and its gradient (finite differences and an
              independent adjoint in the density-matrix picture).
 gradient     state-vector adjoint / finite-difference parameter gradients.
+readout      the measurement-error model (Eq. (errordetectionMeasurementError))
+             and the Bloch vectors of every qubit (Eq. (multiqubitblochvector)).
 
 Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, printed values of the thesis and brute force.
