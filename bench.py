@@ -387,6 +387,7 @@ def run_ours(args, world, rank, local):
     if not args.no_extras:
         line["rows"] = {"other_method_30q": extra_other_method(qs, torch, args.method),
                         "qft": extra_qft(qs, torch),
+                        "readout": extra_readout(qs, torch),
                         "sv_grad": extra_sv_grad(qs, torch),
                         "fp64": extra_fp64(qs, torch),
                         "small_circuits": extra_small_circuits(qs, torch),
@@ -651,6 +652,63 @@ def extra_qft(qs, torch, n=30, seed=2002):
             "rel_err_4096_sampled": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
 
 
+def extra_readout(qs, torch, n=30, seed=610, reps=5):
+    """Readout transforms at 30 qubits: the Bloch vectors of every qubit (Eq.
+    multiqubitblochvector; one read of the complex64 state per 12 or 8 qubits) of the
+    product state R^z(phi_q) R^y(theta_q)|0>, checked against the single-qubit form
+    (sin th cos ph, sin th sin ph, cos th); and the measurement-error model (Eq.
+    errordetectionMeasurementError, eps = 0.08 as in the thesis) in place on the FP32
+    probabilities (one read+write per 12 or 8 qubits).  CUDA events on the launch stream;
+    the state and probabilities exceed L2."""
+    import math
+
+    import numpy as np
+
+    import workloads as W
+    g = W.rng(seed)
+    th = g.uniform(0, math.pi, size=n)
+    ph = g.uniform(-math.pi, math.pi, size=n)
+    ops = [("RY", (q,), (float(th[q]),), None) for q in range(n)]
+    ops += [("RZ", (q,), (float(ph[q]),), None) for q in range(n)]
+    st = qs.State(n, qs.QS_C64)
+    qs.sv_apply_circuit(st, ops)
+    sweeps = 1 + math.ceil((n - 12) / 8)
+    peak = measured_peaks()[0]["hbm_gbs"]
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {}
+    ms = timed(lambda: qs.sv_bloch(st))
+    r = qs.sv_bloch(st)
+    ref = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+    byt = sweeps * (1 << n) * 8
+    out["bloch"] = {"ms": ms, "sweeps": sweeps, "gbs": byt / ms / 1e6,
+                    "hbm_frac": byt / ms / 1e6 / peak,
+                    "max_abs_err_vs_closed_form": float(np.max(np.abs(r - ref)))}
+    p, _ = qs.sv_probs(st)
+    st.close()
+    ms = timed(lambda: qs.meas_error(p, 0.08))
+    byt = sweeps * 2 * (1 << n) * 4
+    out["meas_error_fp32"] = {"ms": ms, "sweeps": sweeps, "gbs": byt / ms / 1e6,
+                              "hbm_frac": byt / ms / 1e6 / peak,
+                              "sum_after": float(p.double().sum())}
+    del p
+    torch.cuda.empty_cache()
+    out["workload"] = (f"{n}-qubit complex64 product state (seed {seed}); Bloch vectors of all "
+                       f"qubits; measurement error eps = 0.08 on the 2^{n} FP32 probabilities")
+    return out
+
+
 def extra_fp64(qs, torch, seed=SEED):
     """complex128 runs of the 40-layer workload: the plain per-gate FP64 GPU path at 30
     qubits (16 GiB; the baseline the fused FP32 forms are measured against) and the tiled
@@ -745,7 +803,8 @@ def main():
                     help="state-vector method of the timed workload (default: the fastest, fused "
                          "blocks with the BF16 split; the tiled path is reported as a row)")
     ap.add_argument("--only", default=None,
-                    choices=["dm", "serve", "blocks", "small", "qft", "fp64", "grad", "other"],
+                    choices=["dm", "serve", "blocks", "small", "qft", "fp64", "grad", "other",
+                             "readout"],
                     help="run one extra row alone (for profiling) and print it")
     args = ap.parse_args()
     if args.only:
@@ -755,7 +814,8 @@ def main():
         qs.load()
         fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
               "small": extra_small_circuits, "qft": extra_qft, "fp64": extra_fp64,
-              "grad": extra_sv_grad, "other": lambda q, t: extra_other_method(q, t, args.method)}[args.only]
+              "grad": extra_sv_grad, "readout": extra_readout,
+              "other": lambda q, t: extra_other_method(q, t, args.method)}[args.only]
         print(json.dumps({"only": args.only, "row": fn(qs, torch)}), flush=True)
         return 0
     world, rank, local = dist_setup()

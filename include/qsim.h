@@ -295,6 +295,32 @@ qs_status qs_server_destroy(qs_server_t s);
 qs_status qs_probs_noalloc(const void* amps, int n, int prec, void* out, int out_fp64,
                            uint64_t marg_mask, double* norm_out, void* stream);
 
+/* ---- readout transforms ------------------------------------------------ */
+
+/* Bloch vectors of every qubit (Eq. (multiqubitblochvector)): for q = 0..n-1
+ * (bit positions) r_out[3q], r_out[3q+1], r_out[3q+2] = <sigma^x_q>,
+ * <sigma^y_q>, <sigma^z_q> = the sums over the amplitude pairs (a0, a1) that
+ * differ only in bit q of 2 Re(a0* a1), 2 Im(a0* a1), |a0|^2 - |a1|^2 (no
+ * normalisation).  r_out: HOST, 3n doubles.  Sums in the state's precision
+ * within a tile of 4096 amplitudes, FP64 across tiles; one read of the state
+ * per 12 (first) or 8 (further) qubits.  Uses the state's scratch; synchronises
+ * its stream.  Errors: QS_EINVAL (NULL), QS_ECUDA. */
+qs_status sv_bloch(qs_state_t st, double* r_out);
+
+/* Measurement-error model (Eq. (errordetectionMeasurementError)), in place:
+ * each bit of an outcome string is misread independently, so
+ *   p_J <- sum_J' p_J' prod_q P_q(j_q | j'_q),
+ * with P_q(1 | 0) = e01[q] (a 0 counted as a 1) and P_q(0 | 1) = e10[q]; the
+ * thesis's model is e01[q] = e10[q] = eps, where the product is
+ * eps^D (1 - eps)^(n - D), D the Hamming distance of J and J'.  probs: DEVICE,
+ * 2^n floats (fp64 = 0) or doubles (fp64 = 1), bit q of the index = qubit q,
+ * 16-byte aligned; e01 (HOST, n doubles in [0, 1]), e10 (HOST, n doubles, or
+ * NULL for e10 = e01).  1 <= n <= 40.  One read+write of probs per 12 (first)
+ * or 8 (further) qubits, asynchronous on stream.  Errors: QS_EINVAL (NULL,
+ * misaligned, n or a rate out of range), QS_ECUDA. */
+qs_status qs_meas_error(void* probs, int n, int fp64, const double* e01, const double* e10,
+                        void* stream);
+
 /* ---- profiling --------------------------------------------------------- */
 
 /* Between qs_profile_begin and qs_profile_end every state-vector launch of

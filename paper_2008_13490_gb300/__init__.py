@@ -116,6 +116,9 @@ def load():
                           ctypes.POINTER(ctypes.c_double)]),
         "dm_apply_channels": (i32, [ctypes.POINTER(DMBatch), vp, vp, vp, vp]),
         "qs_probs_noalloc": (i32, [vp, i32, i32, vp, i32, u64, ctypes.POINTER(ctypes.c_double), vp]),
+        "sv_bloch": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "qs_meas_error": (i32, [vp, i32, i32, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), vp]),
         "qs_server_create": (i32, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
         "qs_server_submit": (i32, [vp, i32, vp, sz, u64, ctypes.POINTER(ctypes.c_int64)]),
         "qs_server_wait": (i32, [vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double)]),
@@ -137,7 +140,8 @@ def load():
 def exported_symbols():
     return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
             "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
-            "dm_apply_channels", "qs_probs_noalloc", "qs_profile_begin", "qs_profile_end",
+            "dm_apply_channels", "qs_probs_noalloc", "sv_bloch", "qs_meas_error",
+            "qs_profile_begin", "qs_profile_end",
             "qs_server_create", "qs_server_submit", "qs_server_wait", "qs_server_stats_get",
             "qs_server_destroy", "qs_last_error", "qs_version"]
 
@@ -381,6 +385,32 @@ def sv_probs(st: State, out=None, fp64: bool = False, marg_mask: int = 0, want_n
     _check(load().sv_probs(st.handle, out.data_ptr(), 1 if fp64 else 0, int(marg_mask),
                            ctypes.byref(norm) if want_norm else None))
     return out, (norm.value if want_norm else None)
+
+
+def sv_bloch(st: State) -> np.ndarray:
+    """Bloch vectors of every qubit: (n, 3) float64 array, row q = (<X_q>, <Y_q>, <Z_q>)."""
+    r = np.zeros(3 * st.n, dtype=np.float64)
+    _check(load().sv_bloch(st.handle, r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return r.reshape(st.n, 3)
+
+
+def meas_error(probs, e01, e10=None, stream=None):
+    """Measurement-error model in place on a device probability tensor of 2^n
+    float32/float64 values; e01, e10: per-qubit misread rates (scalars or n values;
+    e10 defaults to e01).  Returns probs."""
+    torch = _torch()
+    N = probs.numel()
+    n = N.bit_length() - 1
+    if N != 1 << n or n < 1:
+        raise ValueError("probs must hold 2^n values, n >= 1")
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(e01, dtype=np.float64), (n,)))
+    b = None if e10 is None else np.ascontiguousarray(
+        np.broadcast_to(np.asarray(e10, dtype=np.float64), (n,)))
+    dbl = ctypes.POINTER(ctypes.c_double)
+    _check(load().qs_meas_error(probs.data_ptr(), n, 1 if probs.dtype == torch.float64 else 0,
+                                a.ctypes.data_as(dbl), None if b is None else b.ctypes.data_as(dbl),
+                                _stream_ptr(stream)))
+    return probs
 
 
 def sv_loglik(st: State, counts) -> tuple[float, int]:
