@@ -814,7 +814,7 @@ def main():
         qs.load()
         fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
               "small": extra_small_circuits, "qft": extra_qft, "fp64": extra_fp64,
-              "grad": extra_sv_grad, "readout": extra_readout,
+              "grad": extra_sv_grad, "readout": lambda q, t: extra_readout(q, t, n=args.n),
               "other": lambda q, t: extra_other_method(q, t, args.method)}[args.only]
         print(json.dumps({"only": args.only, "row": fn(qs, torch)}), flush=True)
         return 0

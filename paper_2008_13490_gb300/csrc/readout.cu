@@ -74,8 +74,40 @@ __device__ __forceinline__ uint64_t tile_base(const ReadoutPass& P, uint64_t til
   return ((uint64_t)hi << 32) | lo;
 }
 
-__device__ __forceinline__ uint64_t gaddr(const uint64_t* alo, const uint64_t* ahi, uint64_t base, int L) {
-  return base | alo[L & 63] | ahi[L >> 6];
+__device__ __forceinline__ uint64_t local_off(const uint64_t* alo, const uint64_t* ahi, int L) {
+  return alo[L & 63] | ahi[L >> 6];
+}
+
+// Offsets of a layout's 16 registers: the thread's part of the local index once
+// per CTA, and register r adds the deposits g[k] of its bits (r is a
+// compile-time constant in the unrolled loops, so each offset is one OR of the
+// previous one).
+struct LayoutAddr {
+  uint64_t t;      // thread part
+  uint64_t g[4];   // deposit of register bit k
+  __device__ __forceinline__ uint64_t reg(int r) const {
+    uint64_t o = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if ((r >> k) & 1) o |= g[k];
+    return o;
+  }
+};
+// layout A: thread -> local 0..7, registers -> local 8..11
+__device__ __forceinline__ LayoutAddr addr_a(const ReadoutPass& P, const uint64_t* alo, const uint64_t* ahi) {
+  LayoutAddr a;
+  a.t = local_off(alo, ahi, lay_a(threadIdx.x, 0));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a.g[k] = 1ull << P.pos[8 + k];
+  return a;
+}
+// layout B: thread -> local 0..3, 8..11, registers -> local 4..7
+__device__ __forceinline__ LayoutAddr addr_b(const ReadoutPass& P, const uint64_t* alo, const uint64_t* ahi) {
+  LayoutAddr a;
+  a.t = local_off(alo, ahi, lay_b(threadIdx.x, 0));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a.g[k] = 1ull << P.pos[4 + k];
+  return a;
 }
 
 // streaming (evict-first) load of one complex amplitude
@@ -86,6 +118,26 @@ __device__ __forceinline__ C2<float> ldcs_c(const C2<float>* p) {
 __device__ __forceinline__ C2<double> ldcs_c(const C2<double>* p) {
   const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
   return C2<double>{t.x, t.y};
+}
+
+// asynchronous global -> shared copies (cp.async; 4 and 8 bytes go through L1)
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// the tile's 16 elements of this thread in layout A, copied into buf at their slots
+template <typename E>
+__device__ __forceinline__ void prefetch_tile(E* buf, const E* src, const LayoutAddr& la) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) cp_async<sizeof(E)>(buf + ro_slot(lay_a(threadIdx.x, r)), src + la.reg(r));
 }
 
 // ------------------------------------------------------------------ measurement error
@@ -102,16 +154,61 @@ __device__ __forceinline__ void flip_pairs(T* v, const T* m) {
   }
 }
 
+// A thread's 16 values.  FP32 values are kept as 8 float2 (register bit 0 =
+// the component) so that the pairs of register bits 1..3 are float2 registers
+// and their maps use Blackwell's packed FP32x2 multiply-adds: half the
+// instructions of this issue-bound sweep.
 template <typename T>
-__device__ __forceinline__ void flip_stage(T* v, int active, int first_local, const T (*m)[4]) {
-  if ((active >> (first_local + 0)) & 1) flip_pairs<T, 0>(v, m[first_local + 0]);
-  if ((active >> (first_local + 1)) & 1) flip_pairs<T, 1>(v, m[first_local + 1]);
-  if ((active >> (first_local + 2)) & 1) flip_pairs<T, 2>(v, m[first_local + 2]);
-  if ((active >> (first_local + 3)) & 1) flip_pairs<T, 3>(v, m[first_local + 3]);
+struct Regs16 {
+  T v[16];
+  __device__ __forceinline__ T& at(int r) { return v[r]; }
+};
+template <>
+struct Regs16<float> {
+  float2 w[8];
+  __device__ __forceinline__ float& at(int r) { return (r & 1) ? w[r >> 1].y : w[r >> 1].x; }
+};
+
+template <typename T>
+__device__ __forceinline__ void flip_stage(Regs16<T>& x, int active, int first_local, const T (*m)[4]) {
+  if ((active >> (first_local + 0)) & 1) flip_pairs<T, 0>(x.v, m[first_local + 0]);
+  if ((active >> (first_local + 1)) & 1) flip_pairs<T, 1>(x.v, m[first_local + 1]);
+  if ((active >> (first_local + 2)) & 1) flip_pairs<T, 2>(x.v, m[first_local + 2]);
+  if ((active >> (first_local + 3)) & 1) flip_pairs<T, 3>(x.v, m[first_local + 3]);
+}
+
+// register bit K >= 1 of the float2 form: float2 registers i and i | 2^(K-1)
+template <int K>
+__device__ __forceinline__ void flip_pairs2(float2* w, const float* m) {
+  const float2 m0 = make_float2(m[0], m[0]), m1 = make_float2(m[1], m[1]);
+  const float2 m2 = make_float2(m[2], m[2]), m3 = make_float2(m[3], m[3]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i & (1 << (K - 1))) continue;
+    const float2 x0 = w[i], x1 = w[i | (1 << (K - 1))];
+    w[i] = __ffma2_rn(m1, x1, __fmul2_rn(m0, x0));
+    w[i | (1 << (K - 1))] = __ffma2_rn(m3, x1, __fmul2_rn(m2, x0));
+  }
+}
+
+template <>
+__device__ __forceinline__ void flip_stage<float>(Regs16<float>& x, int active, int first_local,
+                                                  const float (*m)[4]) {
+  if ((active >> (first_local + 0)) & 1) {
+    const float* q = m[first_local];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float x0 = x.w[i].x, x1 = x.w[i].y;
+      x.w[i] = make_float2(fmaf(q[1], x1, q[0] * x0), fmaf(q[3], x1, q[2] * x0));
+    }
+  }
+  if ((active >> (first_local + 1)) & 1) flip_pairs2<1>(x.w, m[first_local + 1]);
+  if ((active >> (first_local + 2)) & 1) flip_pairs2<2>(x.w, m[first_local + 2]);
+  if ((active >> (first_local + 3)) & 1) flip_pairs2<3>(x.w, m[first_local + 3]);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kRoThreads)
+__global__ void __launch_bounds__(kRoThreads, sizeof(T) == 4 ? 3 : 2)
     meas_error_kernel(T* __restrict__ p, const ReadoutPass P, uint64_t tiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -127,30 +224,45 @@ __global__ void __launch_bounds__(kRoThreads)
   }
   __syncthreads();
   const int active = P.active;
-  for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const uint64_t base = tile_base(P, tile);
-    T v[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = __ldcs(p + gaddr(s_alo, s_ahi, base, lay_a(tid, r)));
-    flip_stage(v, active, 8, s_m);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) sm[ro_slot(lay_a(tid, r))] = v[r];
+  const LayoutAddr la = addr_a(P, s_alo, s_ahi), lb = addr_b(P, s_alo, s_ahi);
+  // two shared tiles: the next tile's copies run while this one is transformed
+  uint64_t tile = blockIdx.x;
+  if (tile < tiles) prefetch_tile(sm, p + (tile_base(P, tile) | la.t), la);
+  cp_async_commit();
+  for (int cur = 0; tile < tiles; tile += gridDim.x, cur ^= 1) {
+    T* b = sm + (cur ? kRoElems : 0);
+    const uint64_t nxt = tile + gridDim.x;
+    if (nxt < tiles) prefetch_tile(sm + (cur ? 0 : kRoElems), p + (tile_base(P, nxt) | la.t), la);
+    cp_async_commit();
+    cp_async_wait<1>();   // this tile's copies (every group but the newest) have landed
     __syncthreads();
+    const uint64_t base = tile_base(P, tile);
+    Regs16<T> v;
+    if (active & 0xf00) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v.at(r) = b[ro_slot(lay_a(tid, r))];
+      flip_stage(v, active, 8, s_m);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) b[ro_slot(lay_a(tid, r))] = v.at(r);
+      __syncthreads();
+    }
     if (active & 0xf) {
 #pragma unroll
-      for (int r = 0; r < 16; ++r) v[r] = sm[ro_slot(lay_c(tid, r))];
+      for (int r = 0; r < 16; ++r) v.at(r) = b[ro_slot(lay_c(tid, r))];
       flip_stage(v, active, 0, s_m);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) sm[ro_slot(lay_c(tid, r))] = v[r];
+      for (int r = 0; r < 16; ++r) b[ro_slot(lay_c(tid, r))] = v.at(r);
       __syncthreads();
     }
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = sm[ro_slot(lay_b(tid, r))];
+    for (int r = 0; r < 16; ++r) v.at(r) = b[ro_slot(lay_b(tid, r))];
     flip_stage(v, active, 4, s_m);
+    T* dst = p + (base | lb.t);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) __stcs(p + gaddr(s_alo, s_ahi, base, lay_b(tid, r)), v[r]);
-    __syncthreads();   // the next tile reuses the shared tile
+    for (int r = 0; r < 16; ++r) __stcs(dst + lb.reg(r), v.at(r));
+    __syncthreads();   // b is the target of the next iteration's copies
   }
+  cp_async_wait<0>();
 }
 
 // n < 12: the whole vector in one CTA's shared memory, one bit at a time
@@ -231,27 +343,30 @@ __device__ __forceinline__ R reduce_scatter16(R (&x)[16]) {
 // this lane's accumulator of the layout (value (lane >> 1) & 15).
 template <typename R>
 __device__ __forceinline__ void bloch_stage(const C2<R>* v, int active, int first, SlotAcc<R>& acc) {
-  R x[16], nrm[16];
+  // z of a bit = (all 16 norms) - 2 (the norms with the bit set)
+  R x[16], nrm[16], tot = 0;
 #pragma unroll
-  for (int r = 0; r < 16; ++r) nrm[r] = fma(v[r].x, v[r].x, v[r].y * v[r].y);
+  for (int r = 0; r < 16; ++r) {
+    nrm[r] = fma(v[r].x, v[r].x, v[r].y * v[r].y);
+    tot += nrm[r];
+  }
 #pragma unroll
   for (int i = 0; i < 16; ++i) x[i] = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (!((active >> (first + k)) & 1)) continue;
-    R re = 0, im = 0, z0 = 0, z1 = 0;
+    R re = 0, im = 0, z1 = 0;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       if (r & (1 << k)) continue;
       const C2<R> a0 = v[r], a1 = v[r | (1 << k)];
       re = fma(a0.x, a1.x, fma(a0.y, a1.y, re));
       im = fma(a0.x, a1.y, fma(-a0.y, a1.x, im));
-      z0 += nrm[r];
       z1 += nrm[r | (1 << k)];
     }
     x[3 * k] = re;
     x[3 * k + 1] = im;
-    x[3 * k + 2] = z0 - z1;
+    x[3 * k + 2] = fma(R(-2), z1, tot);
   }
   acc.add(reduce_scatter16(x));
 }
@@ -270,11 +385,13 @@ __global__ void __launch_bounds__(kRoThreads)
   __syncthreads();
   const int active = P.active;
   SlotAcc<R> acc_a, acc_b, acc_c;   // layouts A (local 8..11), B (4..7), C (0..3)
+  const LayoutAddr la = addr_a(P, s_alo, s_ahi);
   for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const uint64_t base = tile_base(P, tile);
     C2<R> v[16];
+    const C2<R>* src = psi + (base | la.t);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = ldcs_c(psi + gaddr(s_alo, s_ahi, base, lay_a(tid, r)));
+    for (int r = 0; r < 16; ++r) v[r] = ldcs_c(src + la.reg(r));
     if (active & 0xf00) bloch_stage(v, active, 8, acc_a);
     if (active & 0xff) {
 #pragma unroll
@@ -421,7 +538,7 @@ qs_status meas_error_launch(T* p, int n, const double* e01, const double* e10, c
     QS_CUDA(cudaGetLastError());
     return QS_OK;
   }
-  const size_t smem = sizeof(T) * kRoElems;
+  const size_t smem = 2 * sizeof(T) * kRoElems;
   qs_status s = smem_attr(meas_error_kernel<T>, smem);
   if (s != QS_OK) return s;
   const uint64_t tiles = 1ull << (n - kTileBits);
