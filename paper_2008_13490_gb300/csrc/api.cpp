@@ -360,6 +360,142 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
   return QS_OK;
 }
 
+// The adjoint sweep over gates [g0, g1) fused into tile passes.  The reversed
+// gate list becomes, per gate, one op per parameter carrying its derivative
+// matrix G_p = (dU/dt_p) U^dagger (a term op, not applied) followed by
+// U^dagger; the tile planner splits it into passes (an op keeps its order with
+// the ops that share a qubit), and each pass runs the adjoint pass kernel on
+// psi = st->data and lam, its per-tile terms reduced into dth.  Dense two-qubit
+// U^dagger ops (SWAP, MAT2) run as plain launches on both states.
+template <typename R>
+qs_status adjoint_tiled_t(State* st, void* lam, const qs_gate* gates, size_t g0, size_t g1, double* dth) {
+  const int n = st->n;
+  if (n < kTileBits) {
+    set_error("fused adjoint needs n >= %d", kTileBits);
+    return QS_EUNSUPPORTED;
+  }
+  std::vector<qs_gate> bw;
+  std::vector<int> slot;
+  for (size_t g = g1; g-- > g0;) {
+    const qs_gate& G = gates[g];
+    cd U[16], Ud[16];
+    int dim = 0;
+    gate_matrix(G, U, &dim);
+    for (int r = 0; r < dim; ++r)
+      for (int c = 0; c < dim; ++c) Ud[r * dim + c] = std::conj(U[c * dim + r]);
+    auto as_gate = [&](const cd* m) {
+      qs_gate x;
+      std::memset(&x, 0, sizeof(x));
+      x.kind = dim == 2 ? QS_MAT1 : QS_MAT2;
+      x.q[0] = G.q[0];
+      x.q[1] = dim == 2 ? 0 : G.q[1];
+      for (int i = 0; i < dim * dim; ++i) {
+        x.m[2 * i] = m[i].real();
+        x.m[2 * i + 1] = m[i].imag();
+      }
+      return x;
+    };
+    const int np = gate_nparams(G.kind);
+    for (int p = 0; p < np; ++p) {
+      cd dU[16], M[16];
+      gate_dmatrix(G, p, dU);
+      for (int r = 0; r < dim; ++r)
+        for (int c = 0; c < dim; ++c) {
+          cd acc = 0;
+          for (int k = 0; k < dim; ++k) acc += dU[r * dim + k] * Ud[k * dim + c];
+          M[r * dim + c] = acc;
+        }
+      bw.push_back(as_gate(M));
+      slot.push_back((int)(3 * g + p));
+    }
+    bw.push_back(as_gate(Ud));
+    slot.push_back(-1);
+  }
+  std::vector<FOp> fops;
+  std::vector<int> vmap;
+  build_fused_ops(bw.data(), bw.size(), n, fops, vmap, /*fuse=*/false, /*relabel=*/false);
+  if (fops.size() != bw.size()) {
+    set_error("adjoint op list changed size");
+    return QS_EUNSUPPORTED;
+  }
+  for (size_t i = 0; i < fops.size(); ++i) {
+    fops[i].term = slot[i];
+    if (slot[i] >= 0 && fops[i].type != F_G1 && fops[i].type != F_D) {
+      set_error("derivative matrix of gate %d is not a one-qubit or diagonal op", slot[i] / 3);
+      return QS_EUNSUPPORTED;
+    }
+  }
+  for (int q = 0; q < n; ++q) vmap[q] = q;
+  Plan pl;
+  plan_circuit(fops, n, vmap, pl, TileLimits<R>::kMaxOps, kMaxTileStages);
+  if (!pl.remaps.empty()) {
+    set_error("adjoint plan needs a remap");
+    return QS_EUNSUPPORTED;
+  }
+  const uint64_t tiles = 1ull << (n - kTileBits);
+  const size_t pbytes = sizeof(R) * tiles * TileLimits<R>::kMaxOps;
+  void* partial = dev_alloc(st, pbytes);
+  if (!partial) {
+    set_error("adjoint partials allocation failed");
+    return QS_ENOMEM;
+  }
+  // the term slots of every pass, uploaded once
+  std::vector<int> slots_all;
+  std::vector<size_t> slot_off;
+  for (const PlanStep& step : pl.steps) {
+    slot_off.push_back(slots_all.size());
+    if (step.kind != PlanStep::TILE) continue;
+    const TilePass& pass = pl.passes[step.index];
+    for (int s2 = 0; s2 < pass.n_stages; ++s2) {
+      const TileStage& ts = pl.stages[pass.stage_begin + s2];
+      for (int o = ts.op_begin; o < ts.op_end; ++o)
+        if (pl.tile_fops[o].term >= 0) slots_all.push_back(pl.tile_fops[o].term);
+    }
+  }
+  std::vector<unsigned char> blob;
+  const size_t off_slots = put(blob, slots_all.data(), slots_all.size());
+  qs_status s = upload(st, blob);
+  const int* slots_dev = (const int*)((unsigned char*)st->opbuf + off_slots);
+  std::unique_ptr<TileParams<R>> tp(new TileParams<R>());
+  for (size_t si = 0; si < pl.steps.size() && s == QS_OK; ++si) {
+    const PlanStep& step = pl.steps[si];
+    if (step.kind == PlanStep::TILE) {
+      const TilePass& pass = pl.passes[step.index];
+      std::memset(tp.get(), 0, sizeof(TileParams<R>));
+      tp->pass = pass;
+      const int op0 = pl.stages[pass.stage_begin].op_begin;
+      int nterm = 0;
+      for (int s2 = 0; s2 < pass.n_stages; ++s2) {
+        TileStage ts = pl.stages[pass.stage_begin + s2];
+        for (int o = ts.op_begin; o < ts.op_end; ++o) {
+          TileOp<R> t = to_tile<R>(pl, (size_t)o);
+          t.term = pl.tile_fops[o].term >= 0 ? (int16_t)nterm++ : (int16_t)-1;
+          tp->ops[o - op0] = t;
+        }
+        ts.op_begin -= op0;
+        ts.op_end -= op0;
+        tp->stages[s2] = ts;
+      }
+      tp->pass.stage_begin = 0;
+      s = launch_adjoint_pass(st, lam, tp.get(), partial, nterm);
+      if (s == QS_OK) s = launch_term_reduce(st, partial, nterm, slots_dev + slot_off[si], dth);
+    } else if (step.kind == PlanStep::PLAIN) {
+      PlainOp<R> p = to_plain<R>(pl.plain_fops[step.index]);
+      s = launch_plain_op(st, &p, p.type);
+      void* psi = st->data;
+      st->data = lam;
+      if (s == QS_OK) s = launch_plain_op(st, &p, p.type);
+      st->data = psi;
+    } else {
+      set_error("unexpected step in the adjoint plan");
+      s = QS_EUNSUPPORTED;
+    }
+  }
+  cudaStreamSynchronize(st->stream);
+  dev_free(st, partial, pbytes);
+  return s;
+}
+
 // Dense 5-qubit blocks on the tensor cores: one pass per block.
 qs_status run_blocks(State* st, const qs_gate* gates, size_t ngates, int mode, qs_stats* stats,
                      KernelTimer& tm) {
@@ -425,6 +561,11 @@ qs_status check_state(qs_state_t st) {
 }
 
 }  // namespace
+
+qs_status adjoint_tiled(State* st, void* lam, const qs_gate* gates, size_t g0, size_t g1, double* dth) {
+  return st->prec == QS_C64 ? adjoint_tiled_t<float>(st, lam, gates, g0, g1, dth)
+                            : adjoint_tiled_t<double>(st, lam, gates, g0, g1, dth);
+}
 
 qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats,
                       int flags) {

@@ -5,15 +5,20 @@
 // respect to an angle t of gate g is
 //     dL/dt = 2 Re <lambda_g | dU_g/dt | psi_{g-1}>,
 // where lambda_g = U_{g+1}^dagger ... U_G^dagger lambda and psi_{g-1} the
-// state before gate g.  The sweep runs backwards over the gates; one fused
-// kernel per gate computes psi_{g-1} = U_g^dagger psi_g, the derivative terms
-// (fp64 block partials) and lambda_{g-1} = U_g^dagger lambda_g.
+// state before gate g.  The sweep runs backwards over the gates.  For n >= 12
+// it runs in fused tile passes (adjoint_pass_kernel: a tile of both states in
+// registers, the U^dagger and derivative terms of all of a pass's gates in one
+// read+write of psi and lambda; dL/dt = 2 Re <lambda_g | G psi_g> with
+// G = (dU/dt) U^dagger).  Otherwise one kernel per gate computes
+// psi_{g-1} = U_g^dagger psi_g, the derivative terms (fp64 block partials) and
+// lambda_{g-1} = U_g^dagger lambda_g.
 // Rotation derivatives follow from R(t) = exp(-i t sigma/2)
 // (Eqs. (singlequbitrotationx)-(singlequbitrotationz)): dR/dt = -i/2 sigma R.
 //
-// States before each gate come either from uncomputing (psi <- U^dagger psi)
-// or, for deep circuits, from checkpoints stored every K gates in the forward
-// pass and recomputed forward segment by segment.
+// States come either from uncomputing (psi <- U^dagger psi) or, for deep
+// circuits, from checkpoints stored every K gates in the forward pass: each
+// segment's final state is recomputed from its checkpoint and the segment is
+// then swept backwards (fused), or its per-gate states are recomputed (per gate).
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -337,14 +342,6 @@ qs_status run_grad(State* st, const qs_gate* gates, size_t ng, const double* w, 
       const size_t cnt = (g0 + K <= ng) ? (size_t)K : ng - g0;
       s = apply_gates(st, gates + g0, cnt, QS_METHOD_TILED, nullptr);
     }
-    for (int k = 0; k < K && s == QS_OK; ++k) {
-      C2<R>* b = (C2<R>*)alloc_state();
-      if (!b) {
-        s = QS_ENOMEM;
-        set_error("segment buffer allocation failed");
-      }
-      segbuf.push_back(b);
-    }
   } else {
     s = apply_gates(st, gates, ng, QS_METHOD_TILED, nullptr);
   }
@@ -358,8 +355,34 @@ qs_status run_grad(State* st, const qs_gate* gates, size_t ng, const double* w, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) s = cuda_status(e, "seed kernel");
   }
-  // ---------------- backward
-  if (s == QS_OK) {
+  // ---------------- backward: fused tile passes (n >= 12), else one launch per gate
+  bool fused = st->n >= kTileBits;
+  if (s == QS_OK && fused) {
+    QS_CUDA(cudaMemsetAsync(dth, 0, sizeof(double) * 3 * ng, st->stream));
+    if (!use_ckpt) {
+      s = adjoint_tiled(st, lam, gates, 0, ng, dth);
+    } else {
+      // per segment (last first): the state after it, recomputed from its checkpoint
+      for (size_t seg = ckpt.size(); seg-- > 0 && s == QS_OK;) {
+        const size_t g0 = seg * (size_t)K;
+        const size_t g1 = (g0 + K <= ng) ? g0 + (size_t)K : ng;
+        QS_CUDA(cudaMemcpyAsync(st->data, ckpt[seg], sb, cudaMemcpyDeviceToDevice, st->stream));
+        s = apply_gates(st, gates + g0, g1 - g0, QS_METHOD_TILED, nullptr);
+        if (s == QS_OK) s = adjoint_tiled(st, lam, gates, g0, g1, dth);
+      }
+    }
+  }
+  if (s == QS_OK && !fused) {
+    for (int k = 0; use_ckpt && k < K && s == QS_OK; ++k) {
+      C2<R>* b = (C2<R>*)alloc_state();
+      if (!b) {
+        s = QS_ENOMEM;
+        set_error("segment buffer allocation failed");
+      }
+      segbuf.push_back(b);
+    }
+  }
+  if (s == QS_OK && !fused) {
     if (!use_ckpt) {
       for (size_t g = ng; g-- > 0 && s == QS_OK;)
         s = backward_gate<R>(st, (C2<R>*)st->data, lam, gates[g], partials, done, dth + 3 * g, false);

@@ -83,6 +83,7 @@ struct FOp {
   cd m0[4], m1[4]; // G1/G1C matrices U[out][in]
   cd d[4];         // D: entries, index 2*bit_a + bit_b (or bit_a when b < 0)
   cd g[16];        // G2 4x4
+  int term = -1;   // adjoint sweep: derivative-term slot (the op's matrix is dU/dt U^dagger, not applied)
 };
 
 // Converts gates into fused ops.  vmap_out[q] = virtual qubit that holds logical
@@ -111,7 +112,8 @@ struct alignas(16) TileOp {
   uint8_t cbit;
   uint8_t dsrc;    // TK_DIAG: source of bit b (CS_NONE for one-qubit diagonals)
   uint8_t dbit;
-  uint8_t pad[10];
+  int16_t term;    // adjoint pass: index of the derivative term this op forms, or -1
+  uint8_t pad[8];
   C2<R> m0[4];     // matrix (choice bit 0) or diagonal d[0..3]
   C2<R> m1[4];     // matrix (choice bit 1)
 };
@@ -235,6 +237,18 @@ qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method
 qs_status launch_set_basis(State* st, uint64_t J);
 // params: host pointer to a TileParams<float> / TileParams<double> (by value to the kernel)
 qs_status launch_tile_pass(State* st, const void* params);
+// The adjoint sweep over gates [g0, g1) in fused tile passes: on entry st->data is
+// the state after gate g1 - 1 and lam the adjoint state there; on return both are
+// the states before gate g0 and dth[3 g + p] has gained dL/dt_p of each gate g in
+// the range.  QS_EUNSUPPORTED (nothing launched) for n < 12 or a derivative
+// matrix that is not a one-qubit or diagonal op.  Synchronises the stream.
+qs_status adjoint_tiled(State* st, void* lam, const qs_gate* gates, size_t g0, size_t g1, double* dth);
+// adjoint sweep over one tile pass: st->data = psi, lam the adjoint state, params
+// a TileParams image whose ops carry term indices; partial: tiles x nterm values
+// in the state's precision
+qs_status launch_adjoint_pass(State* st, void* lam, const void* params, void* partial, int nterm);
+// dth[slots[i]] += 2 sum over tiles of partial[tile][i]
+qs_status launch_term_reduce(State* st, const void* partial, int nterm, const int* slots, double* dth);
 qs_status launch_plain_op(State* st, const void* op_dev, int type);
 qs_status launch_small(State* st, const void* ops_dev, int nops);
 qs_status launch_remap(State* st, const void* desc_dev, void* tmp);

@@ -158,9 +158,11 @@ struct DiagRun {
       default: f3[0] = cmul(f3[0], e0); f3[1] = cmul(f3[1], e1); break;
     }
   }
-  // d[2*bit_a + bit_b] (d[bit_a] for one-qubit diagonals)
+  // d[2*bit_a + bit_b] (d[bit_a] for one-qubit diagonals); with TWO the
+  // direct products go to v2 as well (the adjoint pass carries two states)
+  template <bool TWO = false>
   __device__ __forceinline__ void add(C2<R>* v, const TileOp<R>* __restrict__ opp, uint64_t tile,
-                                      int lane, int warp) {
+                                      int lane, int warp, C2<R>* v2 = nullptr) {
     const uint8_t csrc = opp->csrc, cbit = opp->cbit, dsrc = opp->dsrc, dbit = opp->dbit;
     C2<R> d[4];
 #pragma unroll
@@ -171,7 +173,9 @@ struct DiagRun {
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         const int idx = ((r >> cbit) & 1) * 2 + ((r >> dbit) & 1);
-        v[r] = cmul(v[r], csel(idx >= 2, csel(idx == 3, d[3], d[2]), csel(idx == 1, d[1], d[0])));
+        const C2<R> f = csel(idx >= 2, csel(idx == 3, d[3], d[2]), csel(idx == 1, d[1], d[0]));
+        v[r] = cmul(v[r], f);
+        if (TWO) v2[r] = cmul(v2[r], f);
       }
       return;
     }
@@ -187,14 +191,19 @@ struct DiagRun {
       s = cmul(s, csel(idx >= 2, csel(idx == 3, d[3], d[2]), csel(idx == 1, d[1], d[0])));
     }
   }
-  __device__ __forceinline__ void flush(C2<R>* v) {
+  template <bool TWO = false>
+  __device__ __forceinline__ void flush(C2<R>* v, C2<R>* v2 = nullptr) {
     // D(r) = s f0[r0] f1[r1] f2[r2] f3[r3] as (s f0 f1)[r & 3] * (f2 f3)[r >> 2]
     const C2<R> a0 = cmul(s, f0[0]), a1 = cmul(s, f0[1]);
     const C2<R> lo[4] = {cmul(a0, f1[0]), cmul(a1, f1[0]), cmul(a0, f1[1]), cmul(a1, f1[1])};
     const C2<R> hi[4] = {cmul(f2[0], f3[0]), cmul(f2[1], f3[0]), cmul(f2[0], f3[1]),
                          cmul(f2[1], f3[1])};
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], cmul(lo[r & 3], hi[r >> 2]));
+    for (int r = 0; r < 16; ++r) {
+      const C2<R> D = cmul(lo[r & 3], hi[r >> 2]);
+      v[r] = cmul(v[r], D);
+      if (TWO) v2[r] = cmul(v2[r], D);
+    }
     reset();
   }
 };
@@ -316,6 +325,237 @@ __global__ void __launch_bounds__(kTileThreads)
       dst[o] = v[r];
     }
   }
+}
+
+// ------------------------------------------------------------------ adjoint pass
+//
+// The backward sweep of the adjoint gradient over one tile pass.  With
+// lambda = dL/dpsi^* propagated backwards, dL/dt of a gate's parameter is
+// 2 Re <lambda_g | dU/dt | psi_{g-1}> = 2 Re <lambda_g | G psi_g> with
+// G = (dU/dt) U^dagger, psi_g and lambda_g the states after the gate.  The host
+// lists, for each gate from the last, one op per parameter carrying G (term >= 0)
+// and then U^dagger; the tile planner keeps the order of ops that share a qubit,
+// and a term op commutes with the U^dagger of a gate on other qubits (that unitary
+// cancels from the inner product).  Here a tile of psi and one of lambda stay in
+// registers through the pass: U^dagger ops act on both, a term op adds
+// Re sum_J conj(lambda_J) (G psi)_J over the tile into s_term[term] (warp sums,
+// shared-memory atomics), written per tile to partial[tile][term].
+
+// Re sum over this thread's 16 amplitudes of conj(l) (G p), G the op's matrix
+template <typename R>
+__device__ __forceinline__ R term_of_op(const C2<R>* vp, const C2<R>* vl, const TileOp<R>* __restrict__ opp,
+                                        uint64_t tile, int lane, int warp) {
+  C2<R> g[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) g[i] = opp->m0[i];
+  R t = 0;
+  auto dotre = [](C2<R> a, C2<R> b) { return fma(a.x, b.x, a.y * b.y); };   // Re conj(a) b
+  if (opp->kind == TK_REG) {
+    // pairs (r, r | 2^k) of register slot k; a switch keeps register indices constant
+    switch (opp->slot) {
+      case 0:
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          if (r & 1) continue;
+          t += dotre(vl[r], cfma2(g[0], vp[r], g[1], vp[r | 1])) + dotre(vl[r | 1], cfma2(g[2], vp[r], g[3], vp[r | 1]));
+        }
+        break;
+      case 1:
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          if (r & 2) continue;
+          t += dotre(vl[r], cfma2(g[0], vp[r], g[1], vp[r | 2])) + dotre(vl[r | 2], cfma2(g[2], vp[r], g[3], vp[r | 2]));
+        }
+        break;
+      case 2:
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          if (r & 4) continue;
+          t += dotre(vl[r], cfma2(g[0], vp[r], g[1], vp[r | 4])) + dotre(vl[r | 4], cfma2(g[2], vp[r], g[3], vp[r | 4]));
+        }
+        break;
+      default:
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          if (r & 8) continue;
+          t += dotre(vl[r], cfma2(g[0], vp[r], g[1], vp[r | 8])) + dotre(vl[r | 8], cfma2(g[2], vp[r], g[3], vp[r | 8]));
+        }
+    }
+    return t;
+  }
+  if (opp->kind == TK_LANE) {
+    const int mask = 1 << opp->slot;
+    const bool b = (lane & mask) != 0;
+    const C2<R> o = csel(b, g[3], g[0]), q = csel(b, g[2], g[1]);   // own and partner coefficients
+#pragma unroll
+    for (int r = 0; r < 16; ++r) t += dotre(vl[r], cfma2(o, vp[r], q, shfl_xor_c(vp[r], mask)));
+    return t;
+  }
+  // TK_DIAG: (G p)_J = d[2 bit_a + bit_b] p_J
+  const uint8_t csrc = opp->csrc, cbit = opp->cbit, dsrc = opp->dsrc, dbit = opp->dbit;
+  const bool two = dsrc != CS_NONE;
+  const int ua = csrc == CS_REG ? 0 : src_bit<R>(csrc, cbit, tile, lane, warp);
+  const int ub = (two && dsrc != CS_REG) ? src_bit<R>(dsrc, dbit, tile, lane, warp) : 0;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int ba = csrc == CS_REG ? ((r >> cbit) & 1) : ua;
+    const int bb = two ? (dsrc == CS_REG ? ((r >> dbit) & 1) : ub) : 0;
+    const int idx = two ? ba * 2 + bb : ba;
+    const C2<R> f = csel(idx >= 2, csel(idx == 3, g[3], g[2]), csel(idx == 1, g[1], g[0]));
+    t += dotre(vl[r], cmul(f, vp[r]));
+  }
+  return t;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kTileThreads)
+    adjoint_pass_kernel(C2<R>* __restrict__ psi, C2<R>* __restrict__ lam,
+                        const __grid_constant__ TileParams<R> P, R* __restrict__ partial, int nterm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<R>* smp = reinterpret_cast<C2<R>*>(smem_raw);
+  C2<R>* sml = smp + (1 << kTileBits);
+  __shared__ R s_term[TileLimits<R>::kMaxOps];   // the state's precision
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t tile = blockIdx.x;
+
+  __shared__ uint8_t s_pos[kTileBits];
+  __shared__ uint64_t s_base;
+  if (tid == 0) {
+    const int n_nt = P.pass.n_nt;
+    uint64_t base = 0;
+    for (int j = 0; j < n_nt; ++j) base |= ((tile >> j) & 1ull) << P.pass.nt_pos[j];
+    s_base = base;
+  }
+  if (tid < kTileBits) s_pos[tid] = P.pass.pos[tid];
+  for (int i = tid; i < nterm; i += kTileThreads) s_term[i] = R(0);
+  __syncthreads();
+  const uint64_t base = s_base;
+  uint64_t loff = 0;
+#pragma unroll
+  for (int k = 0; k < kLaneBits; ++k)
+    if ((lane >> k) & 1) loff |= 1ull << s_pos[k];
+
+  const int nst = P.pass.n_stages;
+  const TileStage* __restrict__ S = P.stages;
+  const TileOp<R>* __restrict__ ops = P.ops;
+  C2<R> vp[16], vl[16];
+  {
+    const TileStage s0 = S[0];
+    uint64_t g[kRegBits];
+#pragma unroll
+    for (int k = 0; k < kRegBits; ++k) g[k] = 1ull << s_pos[s0.reg[k]];
+    uint64_t woff = 0;
+#pragma unroll
+    for (int k = 0; k < kWarpBits; ++k)
+      if ((warp >> k) & 1) woff |= 1ull << s_pos[s0.warp[k]];
+    const uint64_t off0 = base | loff | woff;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      uint64_t o = 0;
+#pragma unroll
+      for (int k = 0; k < kRegBits; ++k)
+        if ((r >> k) & 1) o |= g[k];
+      vp[r] = psi[off0 + o];
+      vl[r] = lam[off0 + o];
+    }
+  }
+  for (int s = 0; s < nst; ++s) {
+    const TileStage cur = S[s];
+    if (s > 0) {
+      const TileStage prev = S[s - 1];
+      int rb[kRegBits];
+      int wo = lane;
+#pragma unroll
+      for (int k = 0; k < kRegBits; ++k) rb[k] = 1 << prev.reg[k];
+#pragma unroll
+      for (int k = 0; k < kWarpBits; ++k)
+        if ((warp >> k) & 1) wo |= 1 << prev.warp[k];
+      if (s > 1) __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        int o = wo;
+#pragma unroll
+        for (int k = 0; k < kRegBits; ++k)
+          if ((r >> k) & 1) o |= rb[k];
+        smp[o] = vp[r];
+        sml[o] = vl[r];
+      }
+      __syncthreads();
+      int ro = lane;
+#pragma unroll
+      for (int k = 0; k < kRegBits; ++k) rb[k] = 1 << cur.reg[k];
+#pragma unroll
+      for (int k = 0; k < kWarpBits; ++k)
+        if ((warp >> k) & 1) ro |= 1 << cur.warp[k];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        int o = ro;
+#pragma unroll
+        for (int k = 0; k < kRegBits; ++k)
+          if ((r >> k) & 1) o |= rb[k];
+        vp[r] = smp[o];
+        vl[r] = sml[o];
+      }
+    }
+    for (int o = cur.op_begin; o < cur.op_end;) {
+      const TileOp<R>* op = ops + o;
+      if (op->term >= 0) {
+        R t = term_of_op<R>(vp, vl, op, tile, lane, warp);
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+        if (lane == 0) atomicAdd(&s_term[op->term], t);
+        ++o;
+        continue;
+      }
+      if (op->kind != TK_DIAG) {
+        apply_tile_op<R>(vp, op, tile, lane, warp);
+        apply_tile_op<R>(vl, op, tile, lane, warp);
+        ++o;
+        continue;
+      }
+      DiagRun<R> dr;   // a run of diagonal U^dagger ops, on both states
+      dr.reset();
+      do {
+        dr.template add<true>(vp, ops + o, tile, lane, warp, vl);
+        ++o;
+      } while (o < cur.op_end && ops[o].kind == TK_DIAG && ops[o].term < 0);
+      dr.template flush<true>(vp, vl);
+    }
+  }
+  {
+    const TileStage sl = S[nst - 1];
+    uint64_t g[kRegBits];
+#pragma unroll
+    for (int k = 0; k < kRegBits; ++k) g[k] = 1ull << s_pos[sl.reg[k]];
+    uint64_t woff = 0;
+#pragma unroll
+    for (int k = 0; k < kWarpBits; ++k)
+      if ((warp >> k) & 1) woff |= 1ull << s_pos[sl.warp[k]];
+    const uint64_t off0 = base | loff | woff;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      uint64_t o = 0;
+#pragma unroll
+      for (int k = 0; k < kRegBits; ++k)
+        if ((r >> k) & 1) o |= g[k];
+      psi[off0 + o] = vp[r];
+      lam[off0 + o] = vl[r];
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < nterm; i += kTileThreads) partial[(size_t)tile * nterm + i] = s_term[i];
+}
+
+// dth[slots[i]] += 2 sum over tiles of partial[tile][i] (FP64, one block per term)
+template <typename R>
+__global__ void __launch_bounds__(256)
+    term_reduce_kernel(const R* __restrict__ partial, uint64_t tiles, int nterm,
+                       const int* __restrict__ slots, double* __restrict__ dth) {
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (uint64_t t = threadIdx.x; t < tiles; t += blockDim.x) acc += (double)partial[t * nterm + i];
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) dth[slots[i]] += 2.0 * tot;
 }
 
 // ------------------------------------------------------------------ plain per-gate
@@ -692,6 +932,34 @@ qs_status launch_tile_pass(State* st, const void* params) {
     tile_pass_kernel<double><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
         (C2<double>*)st->data, *(const TileParams<double>*)params);
   }
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+template <typename R>
+static qs_status adjoint_launch_t(State* st, void* lam, const void* params, void* partial, int nterm) {
+  const uint64_t tiles = 1ull << (st->n - kTileBits);
+  const size_t smem = 2 * (sizeof(C2<R>) << kTileBits);
+  qs_status s = set_smem(adjoint_pass_kernel<R>, smem);
+  if (s != QS_OK) return s;
+  adjoint_pass_kernel<R><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
+      (C2<R>*)st->data, (C2<R>*)lam, *(const TileParams<R>*)params, (R*)partial, nterm);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+qs_status launch_adjoint_pass(State* st, void* lam, const void* params, void* partial, int nterm) {
+  return st->prec == QS_C64 ? adjoint_launch_t<float>(st, lam, params, partial, nterm)
+                            : adjoint_launch_t<double>(st, lam, params, partial, nterm);
+}
+
+qs_status launch_term_reduce(State* st, const void* partial, int nterm, const int* slots, double* dth) {
+  if (nterm <= 0) return QS_OK;
+  const uint64_t tiles = 1ull << (st->n - kTileBits);
+  if (st->prec == QS_C64)
+    term_reduce_kernel<float><<<nterm, 256, 0, st->stream>>>((const float*)partial, tiles, nterm, slots, dth);
+  else
+    term_reduce_kernel<double><<<nterm, 256, 0, st->stream>>>((const double*)partial, tiles, nterm, slots, dth);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }

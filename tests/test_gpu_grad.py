@@ -42,6 +42,22 @@ def test_sv_grad_weights(qs, n, prec, ckpt):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,count,ckpt", [(14, 160, 0), (16, 220, 0), (16, 220, 50)])
+def test_sv_grad_fused_passes(qs, n, count, prec, ckpt):
+    # several fused backward tile passes (and checkpoint segments), every gate kind
+    ops = _circ(n, count, 700 + n + ckpt)
+    w = W.rng(n + 1).normal(size=1 << n)
+    Lref, gref = GR.grad_adjoint(ops, n, weights=w)
+    st = qs.State(n, prec)
+    L, g = qs.sv_grad(st, ops, torch.tensor(w, device="cuda"), mode=0, checkpoint_every=ckpt)
+    st.close()
+    tol = 1e-9 if prec else 2e-4
+    scale = np.maximum(np.abs(gref), 1.0)
+    assert np.all(np.abs(g - gref) / scale < tol), np.max(np.abs(g - gref) / scale)
+    assert abs(L - Lref) < (1e-10 if prec else 1e-4)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_sv_grad_loglik_vs_fd(qs, prec):
     n = 5
     ops = _circ(n, 40, 77)
