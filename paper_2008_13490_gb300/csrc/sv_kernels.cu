@@ -408,7 +408,7 @@ __device__ __forceinline__ R term_of_op(const C2<R>* vp, const C2<R>* vl, const 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, sizeof(R) == 4 ? 2 : 1)
     adjoint_pass_kernel(C2<R>* __restrict__ psi, C2<R>* __restrict__ lam,
                         const __grid_constant__ TileParams<R> P, R* __restrict__ partial, int nterm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
