@@ -23,6 +23,17 @@ __device__ __forceinline__ C2<R> cfma2(C2<R> m0, C2<R> a, C2<R> m1, C2<R> b) {
   return r;
 }
 
+// FP32: the same four products per component, in the same order, as packed
+// FP32x2 multiply-adds (half the instructions; identical rounding)
+template <>
+__device__ __forceinline__ C2<float> cfma2<float>(C2<float> m0, C2<float> a, C2<float> m1, C2<float> b) {
+  float2 r = __fmul2_rn(make_float2(m0.x, m0.x), make_float2(a.x, a.y));
+  r = __ffma2_rn(make_float2(-m0.y, m0.y), make_float2(a.y, a.x), r);
+  r = __ffma2_rn(make_float2(m1.x, m1.x), make_float2(b.x, b.y), r);
+  r = __ffma2_rn(make_float2(-m1.y, m1.y), make_float2(b.y, b.x), r);
+  return C2<float>{r.x, r.y};
+}
+
 template <typename R>
 __device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
   C2<R> r;

@@ -73,10 +73,29 @@ __device__ __forceinline__ void apply_tile_op(C2<R>* v, const TileOp<R>* __restr
   const uint8_t kind = opp->kind, slot = opp->slot, csrc = opp->csrc, cbit = opp->cbit;
   C2<R> m0[4], m1[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    m0[i] = opp->m0[i];
-    m1[i] = opp->m1[i];
+  for (int i = 0; i < 4; ++i) m0[i] = opp->m0[i];
+  if (csrc == CS_NONE && kind != TK_DIAG) {   // no choice bit: one matrix, no matrix selects
+    if (kind == TK_REG) {
+      switch (slot) {
+        case 0: reg_gate<0>(v, m0); break;
+        case 1: reg_gate<1>(v, m0); break;
+        case 2: reg_gate<2>(v, m0); break;
+        default: reg_gate<3>(v, m0); break;
+      }
+      return;
+    }
+    const int mask = 1 << slot;
+    const bool b = (lane >> slot) & 1;
+    const C2<R> o = csel(b, m0[3], m0[0]), p = csel(b, m0[2], m0[1]);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const C2<R> q = shfl_xor_c(v[r], mask);
+      v[r] = cfma2(o, v[r], p, q);
+    }
+    return;
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) m1[i] = opp->m1[i];
   if (kind == TK_REG) {
     if (csrc == CS_REG) {
       switch (slot * 4 + cbit) {
