@@ -5,6 +5,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <utility>
 
 #include "internal.h"
 
@@ -146,7 +147,27 @@ TileOp<R> to_tile(const Plan& pl, size_t i) {
   t.cbit = pl.tile_cbit[i];
   t.dsrc = pl.tile_dsrc[i];
   t.dbit = pl.tile_dbit[i];
-  if (o.type == F_D) {
+  if (t.kind == TK_G2 || t.kind == TK_G2C) {   // row-major 4x4: entries 0..7, then 8..15
+    // canonical order (the kernel has no other variants): register slots ascending,
+    // a lane qubit first; swapping a and b swaps the two bits of the local index
+    const bool swap = (t.csrc == CS_REG && t.dsrc == CS_REG && t.cbit > t.dbit) ||
+                      (t.csrc == CS_REG && t.dsrc == CS_LANE);
+    cd G[16];
+    for (int l = 0; l < 4; ++l)
+      for (int m = 0; m < 4; ++m) {
+        const int ls = swap ? ((l & 1) << 1) | (l >> 1) : l, ms = swap ? ((m & 1) << 1) | (m >> 1) : m;
+        G[4 * ls + ms] = o.g[4 * l + m];
+      }
+    if (swap) {
+      std::swap(t.csrc, t.dsrc);
+      std::swap(t.cbit, t.dbit);
+    }
+    const int base = t.kind == TK_G2 ? 0 : 8;
+    for (int k = 0; k < 4; ++k) {
+      t.m0[k] = c2<R>(G[base + k]);
+      t.m1[k] = c2<R>(G[base + 4 + k]);
+    }
+  } else if (o.type == F_D) {
     for (int k = 0; k < 4; ++k) t.m0[k] = c2<R>(o.d[k]);
   } else {
     for (int k = 0; k < 4; ++k) {
@@ -306,7 +327,8 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
   int64_t passes = 0, launches = 0, tile_launches = 0;
   const double N = std::ldexp(1.0, st->n);
   double tile_flops = 0.0, plain_flops = 0.0;
-  for (const FOp& o : pl.tile_fops) tile_flops += op_flops_per_amp(o) * N;
+  for (size_t i = 0; i < pl.tile_fops.size(); ++i)   // a dense two-qubit op has two entries
+    if (pl.tile_kind[i] != TK_G2C) tile_flops += op_flops_per_amp(pl.tile_fops[i]) * N;
   // kernel-parameter image of one pass (stage op ranges relative to the pass)
   std::unique_ptr<TileParams<R>> tp(new TileParams<R>());
   for (const PlanStep& step : pl.steps) {

@@ -100,7 +100,9 @@ struct alignas(2 * sizeof(R)) C2 {
 };
 
 // kinds of a tile op
-enum : uint8_t { TK_REG = 0, TK_LANE = 1, TK_DIAG = 2 };
+// TK_G2: dense 4x4 on qubits a (csrc, cbit) and b (dsrc, dbit), each CS_LANE or
+// CS_REG; entries 0..7 in m0, m1, entries 8..15 in the next op (TK_G2C)
+enum : uint8_t { TK_REG = 0, TK_LANE = 1, TK_DIAG = 2, TK_G2 = 3, TK_G2C = 4 };
 // sources of a choice / diagonal bit
 enum : uint8_t { CS_NONE = 0, CS_TILE = 1, CS_LANE = 2, CS_WARP = 3, CS_REG = 4, CS_ONE = 5 };
 

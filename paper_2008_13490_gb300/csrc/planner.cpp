@@ -340,31 +340,25 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
   const int kLow = 2;   // physical bits always in a tile (contiguous 32-byte sectors)
 
   while (!remaining.empty()) {
-    // a ready two-qubit dense op goes to the plain kernel
-    if (ops[remaining[0]].type == F_G2) {
-      FOp o = ops[remaining[0]];
-      o.a = l2p[o.a];
-      o.b = l2p[o.b];
-      plan.plain_fops.push_back(o);
-      plan.steps.push_back({PlanStep::PLAIN, (int)plan.plain_fops.size() - 1});
-      remaining.erase(remaining.begin());
-      continue;
-    }
-    // ---- choose the tile's qubits and the ops of this pass
+    // ---- choose the tile's qubits and the ops of this pass (a dense two-qubit
+    // op takes two op slots: its 16 entries span two tile ops)
     uint64_t T = 0;
     for (int p = 0; p < kLow; ++p) T |= 1ull << p2l[p];
     uint64_t nd_blk = 0, d_blk = 0;
     std::vector<int> sel;
     std::vector<int> rest;
+    int slots_used = 0;
     for (int idx : remaining) {
       const FOp& o = ops[idx];
       uint64_t ndq = nd_mask(o), dq = d_mask(o);
       bool conflict = (ndq & (nd_blk | d_blk)) || (dq & nd_blk);
-      if (!conflict && o.type != F_G2 && (int)sel.size() < max_ops_per_pass) {
+      const int cost = o.type == F_G2 ? 2 : 1;
+      if (!conflict && slots_used + cost <= max_ops_per_pass) {
         uint64_t need = ndq & ~T;
         if (popc(T | need) <= kTileBits) {
           T |= need;
           sel.push_back(idx);
+          slots_used += cost;
           continue;
         }
       }
@@ -416,7 +410,21 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
         uint64_t ndq = nd_mask(o), dq = d_mask(o);
         bool conflict = (ndq & (snd | sd)) || (dq & snd);
         bool ok = false;
-        if (!conflict) {
+        if (!conflict && o.type == F_G2) {
+          // both qubits on lanes or in this stage's registers
+          const int la = enc.local_of_phys[l2p[o.a]], lb = enc.local_of_phys[l2p[o.b]];
+          int add[2], na = 0;
+          for (int loc : {la, lb}) {
+            if (loc < kLaneBits) continue;
+            bool in = false;
+            for (int k = 0; k < nR; ++k) in = in || (R[k] == loc);
+            if (!in) add[na++] = loc;
+          }
+          if (nR + na <= kRegBits) {
+            for (int k = 0; k < na; ++k) R[nR++] = add[k];
+            ok = true;
+          }
+        } else if (!conflict) {
           if (o.type == F_D) {
             ok = true;
           } else {
@@ -446,11 +454,14 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
         if (nR >= kRegBits) break;
         const FOp& o = ops[idx];
         if (o.type == F_D) continue;
-        int loc = enc.local_of_phys[l2p[o.t]];
-        if (loc < kLaneBits) continue;
-        bool in = false;
-        for (int k = 0; k < nR; ++k) in = in || (R[k] == loc);
-        if (!in) R[nR++] = loc;
+        for (int v : {o.type == F_G2 ? o.a : o.t, o.type == F_G2 ? o.b : -1}) {
+          if (v < 0 || nR >= kRegBits) continue;
+          int loc = enc.local_of_phys[l2p[v]];
+          if (loc < kLaneBits) continue;
+          bool in = false;
+          for (int k = 0; k < nR; ++k) in = in || (R[k] == loc);
+          if (!in) R[nR++] = loc;
+        }
       }
       for (int loc = kLaneBits; loc < kTileBits && nR < kRegBits; ++loc) {
         bool in = false;
@@ -474,6 +485,22 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
       for (int idx : stage_ops) {
         const FOp& o = ops[idx];
         uint8_t kind = TK_DIAG, slot = 0, csrc = CS_NONE, cbit = 0, dsrc = CS_NONE, dbit = 0;
+        if (o.type == F_G2) {
+          // sources (lane or register) of qubit a (local index msb) and b; the op's
+          // 16 entries continue in a second tile op (TK_G2C)
+          enc.src_of(o.a, &csrc, &cbit);
+          enc.src_of(o.b, &dsrc, &dbit);
+          for (int part = 0; part < 2; ++part) {
+            plan.tile_fops.push_back(o);
+            plan.tile_kind.push_back(part ? TK_G2C : TK_G2);
+            plan.tile_slot.push_back(0);
+            plan.tile_csrc.push_back(csrc);
+            plan.tile_cbit.push_back(cbit);
+            plan.tile_dsrc.push_back(dsrc);
+            plan.tile_dbit.push_back(dbit);
+          }
+          continue;
+        }
         if (o.type == F_D) {
           enc.src_of(o.a, &csrc, &cbit);
           if (o.b >= 0) enc.src_of(o.b, &dsrc, &dbit);

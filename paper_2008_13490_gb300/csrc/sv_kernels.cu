@@ -57,6 +57,117 @@ __device__ __forceinline__ void lane_gate_choice(C2<R>* v, int mask, C2<R> o0, C
   }
 }
 
+// ---- dense 4x4 ops on two qubits a (local index msb) and b: y = G x on each quad
+
+template <typename R>
+__device__ __forceinline__ C2<R> sel4(int o, C2<R> g0, C2<R> g1, C2<R> g2, C2<R> g3) {
+  return csel(o >= 2, csel(o == 3, g3, g2), csel(o == 1, g1, g0));
+}
+
+// both qubits in register slots KA, KB: the quad of each r is in registers
+template <int KA, int KB, typename R>
+__device__ __forceinline__ void reg_g2(C2<R>* v, const C2<R>* g) {
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    if ((r >> KA) & 1 || (r >> KB) & 1) continue;
+    C2<R> x[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) x[l] = v[r | ((l >> 1) << KA) | ((l & 1) << KB)];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const C2<R> y0 = cfma2(g[4 * o], x[0], g[4 * o + 1], x[1]);
+      const C2<R> y1 = cfma2(g[4 * o + 2], x[2], g[4 * o + 3], x[3]);
+      v[r | ((o >> 1) << KA) | ((o & 1) << KB)] = C2<R>{y0.x + y1.x, y0.y + y1.y};
+    }
+  }
+}
+
+// one qubit on lane bit (mask), the other in register slot K; A_LANE: qubit a is
+// the lane one.  Each lane holds two of a quad's amplitudes (register bit 0, 1),
+// its partner lane the other two.
+template <int K, bool A_LANE, typename R>
+__device__ __forceinline__ void lane_reg_g2(C2<R>* v, const C2<R>* g, int mask, int u) {
+  // quad index of (lane value w, register value c)
+  auto q = [](int w, int c) { return A_LANE ? 2 * w + c : 2 * c + w; };
+  C2<R> co[2][4];   // output c: coefficients of own c'=0, own 1, partner 0, partner 1
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int cc = j & 1, partner = j >> 1;
+      // lane value of the input: own u or partner 1 - u; output at q(u, c)
+      const C2<R> at0 = g[4 * q(0, c) + q(partner ? 1 : 0, cc)];   // u = 0
+      const C2<R> at1 = g[4 * q(1, c) + q(partner ? 0 : 1, cc)];   // u = 1
+      co[c][j] = csel(u != 0, at1, at0);
+    }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    if ((r >> K) & 1) continue;
+    const C2<R> e0 = v[r], e1 = v[r | (1 << K)];
+    const C2<R> p0 = shfl_xor_c(e0, mask), p1 = shfl_xor_c(e1, mask);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const C2<R> y0 = cfma2(co[c][0], e0, co[c][1], e1);
+      const C2<R> y1 = cfma2(co[c][2], p0, co[c][3], p1);
+      v[r | (c << K)] = C2<R>{y0.x + y1.x, y0.y + y1.y};
+    }
+  }
+}
+
+// both qubits on lane bits: each lane holds one amplitude of every quad
+template <typename R>
+__device__ __forceinline__ void lane_lane_g2(C2<R>* v, const C2<R>* g, int ma, int mb, int o) {
+  // o = own quad index 2 ua + ub; the amplitude at quad index o ^ f comes from lane ^ mask(f)
+  const C2<R> c0 = sel4(o, g[0], g[5], g[10], g[15]);                    // f = 0: G[o][o]
+  const C2<R> c1 = sel4(o, g[1], g[4], g[11], g[14]);                    // f = 1: G[o][o ^ 1]
+  const C2<R> c2 = sel4(o, g[2], g[7], g[8], g[13]);                     // f = 2: G[o][o ^ 2]
+  const C2<R> c3 = sel4(o, g[3], g[6], g[9], g[12]);                     // f = 3: G[o][o ^ 3]
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const C2<R> x = v[r];
+    const C2<R> xb = shfl_xor_c(x, mb), xa = shfl_xor_c(x, ma), xab = shfl_xor_c(x, ma | mb);
+    const C2<R> y0 = cfma2(c0, x, c1, xb);
+    const C2<R> y1 = cfma2(c2, xa, c3, xab);
+    v[r] = C2<R>{y0.x + y1.x, y0.y + y1.y};
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_g2(C2<R>* v, const TileOp<R>* __restrict__ opp, int lane) {
+  C2<R> g[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    g[i] = opp[0].m0[i];
+    g[4 + i] = opp[0].m1[i];
+    g[8 + i] = opp[1].m0[i];
+    g[12 + i] = opp[1].m1[i];
+  }
+  const uint8_t sa = opp->csrc, ba = opp->cbit, sb = opp->dsrc, bb = opp->dbit;
+  // the host orders the qubits: register slots ascending, a lane qubit first
+  if (sa == CS_REG && sb == CS_REG) {
+    switch (ba * 4 + bb) {
+      case 1: reg_g2<0, 1>(v, g); break;
+      case 2: reg_g2<0, 2>(v, g); break;
+      case 3: reg_g2<0, 3>(v, g); break;
+      case 6: reg_g2<1, 2>(v, g); break;
+      case 7: reg_g2<1, 3>(v, g); break;
+      default: reg_g2<2, 3>(v, g); break;
+    }
+    return;
+  }
+  if (sb == CS_LANE) {
+    lane_lane_g2(v, g, 1 << ba, 1 << bb, 2 * ((lane >> ba) & 1) + ((lane >> bb) & 1));
+    return;
+  }
+  const int mask = 1 << ba, u = (lane >> ba) & 1;   // a on the lane, b in register slot bb
+  switch (bb) {
+    case 0: lane_reg_g2<0, true>(v, g, mask, u); break;
+    case 1: lane_reg_g2<1, true>(v, g, mask, u); break;
+    case 2: lane_reg_g2<2, true>(v, g, mask, u); break;
+    default: lane_reg_g2<3, true>(v, g, mask, u); break;
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ int src_bit(uint8_t src, uint8_t bit, uint64_t tile, int lane, int warp) {
   switch (src) {
@@ -67,10 +178,18 @@ __device__ __forceinline__ int src_bit(uint8_t src, uint8_t bit, uint64_t tile, 
   }
 }
 
-template <typename R>
+// G2: the pass holds dense two-qubit ops (a kernel variant of its own, so that
+// passes without them keep the leaner code)
+template <typename R, bool G2>
 __device__ __forceinline__ void apply_tile_op(C2<R>* v, const TileOp<R>* __restrict__ opp,
                                               uint64_t tile, int lane, int warp) {
   const uint8_t kind = opp->kind, slot = opp->slot, csrc = opp->csrc, cbit = opp->cbit;
+  if constexpr (G2) {
+    if (kind == TK_G2) {   // reads its continuation opp[1]
+      apply_g2(v, opp, lane);
+      return;
+    }
+  }
   C2<R> m0[4], m1[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) m0[i] = opp->m0[i];
@@ -227,7 +346,7 @@ struct DiagRun {
   }
 };
 
-template <typename R>
+template <typename R, bool G2>
 __global__ void __launch_bounds__(kTileThreads)
     tile_pass_kernel(C2<R>* __restrict__ psi, const __grid_constant__ TileParams<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -312,8 +431,8 @@ __global__ void __launch_bounds__(kTileThreads)
     }
     for (int o = cur.op_begin; o < cur.op_end;) {
       if (ops[o].kind != TK_DIAG) {
-        apply_tile_op<R>(v, ops + o, tile, lane, warp);
-        ++o;
+        apply_tile_op<R, G2>(v, ops + o, tile, lane, warp);
+        o += (G2 && ops[o].kind == TK_G2) ? 2 : 1;   // a dense two-qubit op spans two entries
         continue;
       }
       DiagRun<R> dr;   // live only over the run
@@ -426,7 +545,7 @@ __device__ __forceinline__ R term_of_op(const C2<R>* vp, const C2<R>* vl, const 
   return t;
 }
 
-template <typename R>
+template <typename R, bool G2>
 __global__ void __launch_bounds__(kTileThreads, sizeof(R) == 4 ? 2 : 1)
     adjoint_pass_kernel(C2<R>* __restrict__ psi, C2<R>* __restrict__ lam,
                         const __grid_constant__ TileParams<R> P, R* __restrict__ partial, int nterm) {
@@ -527,9 +646,9 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(R) == 4 ? 2 : 1)
         continue;
       }
       if (op->kind != TK_DIAG) {
-        apply_tile_op<R>(vp, op, tile, lane, warp);
-        apply_tile_op<R>(vl, op, tile, lane, warp);
-        ++o;
+        apply_tile_op<R, G2>(vp, op, tile, lane, warp);
+        apply_tile_op<R, G2>(vl, op, tile, lane, warp);
+        o += (G2 && op->kind == TK_G2) ? 2 : 1;   // a dense two-qubit op spans two entries
         continue;
       }
       DiagRun<R> dr;   // a run of diagonal U^dagger ops, on both states
@@ -938,38 +1057,56 @@ qs_status launch_set_basis(State* st, uint64_t J) {
   return QS_OK;
 }
 
-qs_status launch_tile_pass(State* st, const void* params) {
+// does the pass (a host TileParams image) hold a dense two-qubit op?
+template <typename R>
+static bool pass_has_g2(const TileParams<R>& P) {
+  const int nops = P.pass.n_stages > 0 ? P.stages[P.pass.n_stages - 1].op_end : 0;
+  for (int o = 0; o < nops; ++o)
+    if (P.ops[o].kind == TK_G2) return true;
+  return false;
+}
+
+template <typename R, bool G2>
+static qs_status tile_launch_t(State* st, const TileParams<R>& P) {
   const uint64_t tiles = 1ull << (st->n - kTileBits);
-  if (st->prec == QS_C64) {
-    const size_t smem = sizeof(C2<float>) << kTileBits;
-    tile_pass_kernel<float><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
-        (C2<float>*)st->data, *(const TileParams<float>*)params);
-  } else {
-    const size_t smem = sizeof(C2<double>) << kTileBits;
-    qs_status s = set_smem(tile_pass_kernel<double>, smem);
-    if (s != QS_OK) return s;
-    tile_pass_kernel<double><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
-        (C2<double>*)st->data, *(const TileParams<double>*)params);
-  }
+  const size_t smem = sizeof(C2<R>) << kTileBits;
+  qs_status s = set_smem(tile_pass_kernel<R, G2>, smem);
+  if (s != QS_OK) return s;
+  tile_pass_kernel<R, G2><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>((C2<R>*)st->data, P);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }
 
-template <typename R>
-static qs_status adjoint_launch_t(State* st, void* lam, const void* params, void* partial, int nterm) {
+qs_status launch_tile_pass(State* st, const void* params) {
+  if (st->prec == QS_C64) {
+    const TileParams<float>& P = *(const TileParams<float>*)params;
+    return pass_has_g2(P) ? tile_launch_t<float, true>(st, P) : tile_launch_t<float, false>(st, P);
+  }
+  const TileParams<double>& P = *(const TileParams<double>*)params;
+  return pass_has_g2(P) ? tile_launch_t<double, true>(st, P) : tile_launch_t<double, false>(st, P);
+}
+
+template <typename R, bool G2>
+static qs_status adjoint_launch_t(State* st, void* lam, const TileParams<R>& P, void* partial, int nterm) {
   const uint64_t tiles = 1ull << (st->n - kTileBits);
   const size_t smem = 2 * (sizeof(C2<R>) << kTileBits);
-  qs_status s = set_smem(adjoint_pass_kernel<R>, smem);
+  qs_status s = set_smem(adjoint_pass_kernel<R, G2>, smem);
   if (s != QS_OK) return s;
-  adjoint_pass_kernel<R><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
-      (C2<R>*)st->data, (C2<R>*)lam, *(const TileParams<R>*)params, (R*)partial, nterm);
+  adjoint_pass_kernel<R, G2><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
+      (C2<R>*)st->data, (C2<R>*)lam, P, (R*)partial, nterm);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }
 
 qs_status launch_adjoint_pass(State* st, void* lam, const void* params, void* partial, int nterm) {
-  return st->prec == QS_C64 ? adjoint_launch_t<float>(st, lam, params, partial, nterm)
-                            : adjoint_launch_t<double>(st, lam, params, partial, nterm);
+  if (st->prec == QS_C64) {
+    const TileParams<float>& P = *(const TileParams<float>*)params;
+    return pass_has_g2(P) ? adjoint_launch_t<float, true>(st, lam, P, partial, nterm)
+                          : adjoint_launch_t<float, false>(st, lam, P, partial, nterm);
+  }
+  const TileParams<double>& P = *(const TileParams<double>*)params;
+  return pass_has_g2(P) ? adjoint_launch_t<double, true>(st, lam, P, partial, nterm)
+                        : adjoint_launch_t<double, false>(st, lam, P, partial, nterm);
 }
 
 qs_status launch_term_reduce(State* st, const void* partial, int nterm, const int* slots, double* dth) {

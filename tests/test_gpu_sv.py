@@ -84,6 +84,30 @@ def test_tiled_diagonal_runs(qs, n, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n", [12, 13, 16])
+def test_tiled_dense_two_qubit_ops(qs, n, prec):
+    # dense 4x4 ops (random SU(4), SWAP without relabeling via MAT2) inside tile passes:
+    # both qubits in registers, one on a lane and one in a register (either order),
+    # or both on lanes
+    g = W.rng(4000 + n)
+    ops = []
+    for i in range(160):
+        a, b = (int(x) for x in g.choice(n, size=2, replace=False))
+        if i % 3 == 2:
+            ops.append(("MAT1", (a,), (), W.haar_su2(g)))
+            continue
+        z = g.normal(size=(4, 4)) + 1j * g.normal(size=(4, 4))
+        qm, r = np.linalg.qr(z)
+        ops.append(("MAT2", (a, b), (), qm * (np.diag(r) / np.abs(np.diag(r)))))
+    psi0 = W.random_state(n, g)
+    if prec == 0:
+        psi0 = psi0.astype(np.complex64)
+    ref = SV.apply_circuit(psi0.astype(np.complex128), n, ops)
+    out, stats = run(qs, n, ops, prec, psi0=psi0)
+    check(out, ref, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n", [3, 12, 16])
 def test_plain_method(qs, n, prec):
     ops = W.random_gate_mix(n, 80, seed=77 + n)
