@@ -388,6 +388,7 @@ def run_ours(args, world, rank, local):
         line["rows"] = {"other_method_30q": extra_other_method(qs, torch, args.method),
                         "qft": extra_qft(qs, torch),
                         "readout": extra_readout(qs, torch),
+                        "dense_2q": extra_dense2q(qs, torch),
                         "sv_grad": extra_sv_grad(qs, torch),
                         "fp64": extra_fp64(qs, torch),
                         "small_circuits": extra_small_circuits(qs, torch),
@@ -709,6 +710,37 @@ def extra_readout(qs, torch, n=30, seed=610, reps=5):
     return out
 
 
+def extra_dense2q(qs, torch, n=30, layers=12, seed=3100):
+    """30-qubit circuit of dense two-qubit gates: `layers` brickwork layers of Haar-random
+    SU(4) (MAT2), complex64, through tile passes (the 4x4 ops inside the tile) and through
+    fused blocks (BF16 split); the two final states compared on the device (relative L2)."""
+    import workloads as W
+    arr = qs.gates_array(W.layered_su4(n, layers, seed))
+    out = {"workload": f"{n}-qubit complex64, {layers} brickwork layers of random SU(4) "
+                       f"({len(arr)} gates, seed {seed})"}
+    states = []
+    for name, method in (("tiled", qs.METHOD_TILED), ("blocks_bf16", qs.METHOD_BLOCKS_BF16)):
+        st = qs.State(n, qs.QS_C64)
+        qs.sv_apply_circuit(st, arr, method)   # warm-up (planner, first launches)
+        qs.sv_set_basis(st, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = qs.sv_apply_circuit(st, arr, method)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        amps = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+        qs.sv_copy_out(st, out=amps)
+        st.close()
+        states.append(amps)
+        out[name] = {"s_per_circuit": dt, "gates_per_s": len(arr) / dt, "passes": s["passes"],
+                     "launches": s["launches"]}
+    a, b = states
+    out["rel_l2_tiled_vs_blocks"] = float((a - b).norm() / a.norm())
+    del states, a, b
+    torch.cuda.empty_cache()
+    return out
+
+
 def extra_fp64(qs, torch, seed=SEED):
     """complex128 runs of the 40-layer workload: the plain per-gate FP64 GPU path at 30
     qubits (16 GiB; the baseline the fused FP32 forms are measured against) and the tiled
@@ -804,7 +836,7 @@ def main():
                          "blocks with the BF16 split; the tiled path is reported as a row)")
     ap.add_argument("--only", default=None,
                     choices=["dm", "serve", "blocks", "small", "qft", "fp64", "grad", "other",
-                             "readout"],
+                             "readout", "dense2q"],
                     help="run one extra row alone (for profiling) and print it")
     args = ap.parse_args()
     if args.only:
@@ -815,6 +847,7 @@ def main():
         fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
               "small": extra_small_circuits, "qft": extra_qft, "fp64": extra_fp64,
               "grad": extra_sv_grad, "readout": lambda q, t: extra_readout(q, t, n=args.n),
+              "dense2q": extra_dense2q,
               "other": lambda q, t: extra_other_method(q, t, args.method)}[args.only]
         print(json.dumps({"only": args.only, "row": fn(qs, torch)}), flush=True)
         return 0

@@ -103,6 +103,25 @@ def layered_haar_cz(n: int, layers: int, seed: int):
     return ops
 
 
+def haar_su4(g: np.random.Generator) -> np.ndarray:
+    """Haar-random 4x4 unitary: QR of a complex Gaussian matrix with the phases of R's
+    diagonal moved into Q."""
+    z = g.normal(size=(4, 4)) + 1j * g.normal(size=(4, 4))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def layered_su4(n: int, depth: int, seed: int):
+    """`depth` brickwork layers of dense random two-qubit gates (MAT2): layer l acts on
+    the pairs (a, a+1), a = l % 2, l % 2 + 2, ..."""
+    g = rng(seed)
+    ops = []
+    for layer in range(depth):
+        for a in range(layer % 2, n - 1, 2):
+            ops.append(("MAT2", (a + 1, a), (), haar_su4(g)))
+    return ops
+
+
 def qft_circuit(n: int):
     """Textbook QFT on n qubits written in the thesis's gate set.
 
