@@ -295,6 +295,24 @@ qs_status qs_server_destroy(qs_server_t s);
 qs_status qs_probs_noalloc(const void* amps, int n, int prec, void* out, int out_fp64,
                            uint64_t marg_mask, double* norm_out, void* stream);
 
+/* ---- checkpoint / resume ------------------------------------------------ */
+
+/* Binary checkpoint of the state, for resuming an interrupted simulation (the
+ * thesis's solver saves its state vector in binary form for that purpose).
+ * File: a 48-byte little-endian header -- magic "QSIMSV1\0", uint32 n, uint32
+ * prec, uint64 amplitude bytes, uint64 checksum, 16 zero bytes -- then the 2^n
+ * interleaved (re, im) amplitudes in the state's precision.  The checksum is the
+ * sum mod 2^64, over the amplitude bytes as 64-bit words w_i (i from 0), of
+ * splitmix64_finaliser(w_i + (i + 1) * 0x9E3779B97F4A7C15), computed on the GPU.
+ * sv_save writes path (replacing it); the state is unchanged.  sv_load reads a
+ * checkpoint written for the same n and precision into the state.  Both stream
+ * through 2 x 64 MiB of pinned host memory and synchronise the state's stream.
+ * Errors: QS_EINVAL (NULL; file cannot be opened, written or read; not a
+ * checkpoint; n or precision differ -- the state unchanged; truncated file or
+ * checksum mismatch -- the state reset to |0...0>), QS_ENOMEM, QS_ECUDA. */
+qs_status sv_save(qs_state_t st, const char* path);
+qs_status sv_load(qs_state_t st, const char* path);
+
 /* ---- readout transforms ------------------------------------------------ */
 
 /* Bloch vectors of every qubit (Eq. (multiqubitblochvector)): for q = 0..n-1

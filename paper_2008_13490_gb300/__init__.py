@@ -117,6 +117,8 @@ def load():
         "dm_apply_channels": (i32, [ctypes.POINTER(DMBatch), vp, vp, vp, vp]),
         "qs_probs_noalloc": (i32, [vp, i32, i32, vp, i32, u64, ctypes.POINTER(ctypes.c_double), vp]),
         "sv_bloch": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "sv_save": (i32, [vp, ctypes.c_char_p]),
+        "sv_load": (i32, [vp, ctypes.c_char_p]),
         "qs_meas_error": (i32, [vp, i32, i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), vp]),
         "qs_server_create": (i32, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
@@ -140,7 +142,7 @@ def load():
 def exported_symbols():
     return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
             "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
-            "dm_apply_channels", "qs_probs_noalloc", "sv_bloch", "qs_meas_error",
+            "dm_apply_channels", "qs_probs_noalloc", "sv_bloch", "qs_meas_error", "sv_save", "sv_load",
             "qs_profile_begin", "qs_profile_end",
             "qs_server_create", "qs_server_submit", "qs_server_wait", "qs_server_stats_get",
             "qs_server_destroy", "qs_last_error", "qs_version"]
@@ -385,6 +387,16 @@ def sv_probs(st: State, out=None, fp64: bool = False, marg_mask: int = 0, want_n
     _check(load().sv_probs(st.handle, out.data_ptr(), 1 if fp64 else 0, int(marg_mask),
                            ctypes.byref(norm) if want_norm else None))
     return out, (norm.value if want_norm else None)
+
+
+def sv_save(st: State, path: str) -> None:
+    """Binary checkpoint of the state (see qsim.h for the format)."""
+    _check(load().sv_save(st.handle, os.fsencode(path)))
+
+
+def sv_load(st: State, path: str) -> None:
+    """Resume from a checkpoint written for the same n and precision."""
+    _check(load().sv_load(st.handle, os.fsencode(path)))
 
 
 def sv_bloch(st: State) -> np.ndarray:
