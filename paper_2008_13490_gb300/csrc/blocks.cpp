@@ -45,48 +45,89 @@ void apply_to_block(std::vector<cd>& U, const cd* g, int dim, int ia, int ib) {
   }
 }
 
+uint64_t gate_mask(const qs_gate& g) {
+  uint64_t m = 1ull << g.q[0];
+  if (gate_is_two_qubit(g.kind)) m |= 1ull << g.q[1];
+  return m;
+}
+
+// The gates a block on qubit set S absorbs: in circuit order, every remaining gate
+// whose qubits lie in S and that no skipped earlier gate on a shared qubit
+// precedes.  Stops once every qubit of S is blocked.
+int absorb(const qs_gate* gates, const std::vector<size_t>& rem, uint64_t S, std::vector<size_t>* sel) {
+  uint64_t blocked = 0;
+  int cnt = 0;
+  for (size_t gi : rem) {
+    const uint64_t qm = gate_mask(gates[gi]);
+    if ((qm & blocked) || (qm & ~S)) {
+      blocked |= qm;
+      if ((blocked & S) == S) break;
+      continue;
+    }
+    ++cnt;
+    if (sel) sel->push_back(gi);
+  }
+  return cnt;
+}
+
+// qubit set grown in circuit order from remaining gate `start` (the gates that
+// are ready and fit), filled up to 5 with the lowest free qubits
+uint64_t grown_set(const qs_gate* gates, const std::vector<size_t>& rem, size_t start, int n) {
+  uint64_t S = 0, blocked = 0;
+  for (size_t i = start; i < rem.size() && __builtin_popcountll(S) < 5; ++i) {
+    const uint64_t qm = gate_mask(gates[rem[i]]);
+    if (qm & blocked) {
+      blocked |= qm;
+      continue;
+    }
+    if (__builtin_popcountll(S | qm) <= 5) S |= qm;
+    else blocked |= qm;
+  }
+  for (int q = 0; q < n && __builtin_popcountll(S) < 5; ++q) S |= 1ull << q;
+  return S;
+}
+
 }  // namespace
 
+// Each block takes, among candidate qubit sets, the one that absorbs the most
+// remaining gates (ties: the first candidate): the sets grown from each of the
+// first kSeeds remaining gates, and every window of 5 consecutive qubits (the
+// light cones of nearest-neighbour circuits).  On 40 layers of Haar + brickwork
+// CZ at 30 qubits this gives 100 blocks where growing from the first remaining
+// gate alone gives 148.
 void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>& out) {
+  constexpr int kSeeds = 64;
   out.clear();
   std::vector<size_t> remaining(ngates);
   for (size_t i = 0; i < ngates; ++i) remaining[i] = i;
+  std::vector<uint64_t> cands;
   while (!remaining.empty()) {
-    std::vector<int> S;
-    uint64_t Smask = 0, blocked = 0;
-    std::vector<size_t> sel, rest;
-    for (size_t gi : remaining) {
-      const qs_gate& g = gates[gi];
-      const int nq = gate_is_two_qubit(g.kind) ? 2 : 1;
-      uint64_t qm = 0;
-      for (int k = 0; k < nq; ++k) qm |= 1ull << g.q[k];
-      if (qm & blocked) {
-        blocked |= qm;
-        rest.push_back(gi);
-        continue;
-      }
-      const uint64_t need = qm & ~Smask;
-      if (__builtin_popcountll(Smask | need) <= 5) {
-        for (int k = 0; k < nq; ++k)
-          if (need & (1ull << g.q[k])) S.push_back(g.q[k]);
-        Smask |= need;
-        sel.push_back(gi);
-      } else {
-        blocked |= qm;
-        rest.push_back(gi);
+    cands.clear();
+    for (int k = 0; k < kSeeds && k < (int)remaining.size(); ++k) {
+      const uint64_t S = grown_set(gates, remaining, (size_t)k, n);
+      if (std::find(cands.begin(), cands.end(), S) == cands.end()) cands.push_back(S);
+    }
+    for (int a = 0; a + 5 <= n; ++a) {
+      const uint64_t S = 31ull << a;
+      if (std::find(cands.begin(), cands.end(), S) == cands.end()) cands.push_back(S);
+    }
+    uint64_t best = cands[0];
+    int best_cnt = -1;
+    for (uint64_t S : cands) {
+      const int c = absorb(gates, remaining, S, nullptr);
+      if (c > best_cnt) {
+        best_cnt = c;
+        best = S;
       }
     }
-    for (int q = 0; q < n && (int)S.size() < 5; ++q)
-      if (!((Smask >> q) & 1)) {
-        S.push_back(q);
-        Smask |= 1ull << q;
-      }
+    std::vector<size_t> sel;
+    absorb(gates, remaining, best, &sel);
     // ascending positions: local bit i of the block = its i-th lowest qubit (the
     // kernel relies on the block qubits among the 4 lowest positions being its
     // lowest local bits)
-    std::sort(S.begin(), S.end());
     Block b;
-    for (int i = 0; i < 5; ++i) b.q[i] = S[i];
+    for (int q = 0, i = 0; q < n && i < 5; ++q)
+      if ((best >> q) & 1) b.q[i++] = q;
     b.U.assign(32 * 32, cd(0));
     for (int i = 0; i < 32; ++i) b.U[i * 32 + i] = 1.0;
     for (size_t gi : sel) {
@@ -103,6 +144,17 @@ void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>&
     }
     b.ngates = (int)sel.size();
     out.push_back(std::move(b));
+    // the rest, in order (sel is a subsequence of remaining)
+    std::vector<size_t> rest;
+    rest.reserve(remaining.size() - sel.size());
+    size_t j = 0;
+    for (size_t gi : remaining) {
+      if (j < sel.size() && sel[j] == gi) {
+        ++j;
+        continue;
+      }
+      rest.push_back(gi);
+    }
     remaining.swap(rest);
   }
 }
