@@ -25,6 +25,8 @@ noisy        the batched noisy-circuit forward model, multinomial
 gradient     state-vector adjoint / finite-difference parameter gradients.
 readout      the measurement-error model (Eq. (errordetectionMeasurementError))
              and the Bloch vectors of every qubit (Eq. (multiqubitblochvector)).
+gst          GST predictions for repeated gates (Eq. (GSTPrediction)) and the
+             statistical distance (Eq. (statisticaldistance)).
 
 Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, printed values of the thesis and brute force.
