@@ -389,6 +389,7 @@ def run_ours(args, world, rank, local):
                         "qft": extra_qft(qs, torch),
                         "readout": extra_readout(qs, torch),
                         "dense_2q": extra_dense2q(qs, torch),
+                        "gst_prediction": extra_gst(qs, torch),
                         "sv_grad": extra_sv_grad(qs, torch),
                         "fp64": extra_fp64(qs, torch),
                         "small_circuits": extra_small_circuits(qs, torch),
@@ -741,6 +742,94 @@ def extra_dense2q(qs, torch, n=30, layers=12, seed=3100):
     return out
 
 
+def _gst_inputs(nsets, seed):
+    """Inputs of the GST prediction row, built here with numpy: `nsets` noisy sets of the
+    thesis's GST gates XI, YI, IX, IY, II, CNOT on 2 qubits (X90 = R^x(pi/2), Y90 =
+    R^y(pi/2), qubit 0 the first tensor factor), each gate followed by depolarizing and
+    amplitude damping on both qubits with rates drawn per set; PTMs G_ij = Tr(P_i E(P_j))/4
+    in the normalised Pauli basis; the four preparations |00>, |10>, |++>, |Psi^->."""
+    import numpy as np
+
+    import workloads as W
+    I2 = np.eye(2)
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    Y = np.array([[0, -1j], [1j, 0]])
+    Z = np.diag([1.0 + 0j, -1])
+    P1 = [I2.astype(complex), X, Y, Z]
+    P2 = [np.kron(P1[i >> 2], P1[i & 3]) for i in range(16)]
+
+    def rot(Pm, t):
+        return np.cos(t / 2) * np.eye(2) - 1j * np.sin(t / 2) * Pm
+
+    def ptm(kraus):
+        return np.array([[np.real(np.trace(P2[i] @ sum(K @ P2[j] @ K.conj().T for K in kraus))) / 4
+                          for j in range(16)] for i in range(16)])
+
+    cnot = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex)
+    Us = [np.kron(rot(X, np.pi / 2), I2), np.kron(rot(Y, np.pi / 2), I2), np.kron(I2, rot(X, np.pi / 2)),
+          np.kron(I2, rot(Y, np.pi / 2)), np.eye(4, dtype=complex), cnot]
+    ideal = [ptm([U]) for U in Us]
+    g = W.rng(seed)
+    ptms = []
+    for _ in range(nsets):
+        p, gam = g.uniform(1e-3, 2e-2, size=2)
+        dep = [np.sqrt(1 - p) * I2] + [np.sqrt(p / 3) * M for M in (X, Y, Z)]
+        ad = [np.array([[1, 0], [0, np.sqrt(1 - gam)]]), np.array([[0, np.sqrt(gam)], [0, 0]])]
+        noise = [np.kron(A @ B, C @ Dm) for A in ad for B in dep for C in ad for Dm in dep]
+        N = ptm(noise)
+        ptms += [N @ T for T in ideal]
+    # |rho>> and <<E_J| in the normalised basis P_i / 2: entries <J|P_i|J> / 2
+    rho = np.array([np.real(P2[i][0, 0]) / 2 for i in range(16)])
+    E = np.array([[np.real(P2[i][J, J]) / 2 for i in range(16)] for J in range(4)])
+    preps = [[], [0, 0], [3, 1], [2, 2, 0, 0, 1, 5]]
+    gate, prep = [], []
+    for s in range(nsets):
+        for gi in range(6):
+            for pr in preps:
+                gate.append(6 * s + gi)
+                prep.append([6 * s + k for k in pr] + [-1] * (8 - len(pr)))
+    return (np.stack(ptms), rho, E, np.array(gate, dtype=np.int32), np.array(prep, dtype=np.int32))
+
+
+def extra_gst(qs, torch, nsets=1000, r_max=1000, seed=4400, reps=5):
+    """GST predictions for repeated gates (Eq. GSTPrediction): 1000 noisy 2-qubit gate sets
+    x 6 gates x 4 preparations = 24000 sequences, p_J(r) for every r = 1..1000 (the series
+    kernel, FP32) and at r = 1000 by repeated squaring (FP64); the two compared."""
+    import numpy as np
+    ptms, rho, E, gate, prep = _gst_inputs(nsets, seed)
+    f = lambda a, dt: torch.tensor(a, dtype=dt, device="cuda")  # noqa: E731
+    dev = (f(ptms, torch.float64), f(rho, torch.float64), f(E, torch.float64),
+           f(gate, torch.int32), f(prep, torch.int32))
+    count = len(gate)
+    out = torch.empty((count, r_max, 4), dtype=torch.float32, device="cuda")
+    rr = torch.full((count,), r_max, dtype=torch.int64, device="cuda")
+    pw = torch.empty((count, 4), dtype=torch.float64, device="cuda")
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_s = timed(lambda: qs.gst_series(2, *dev, r_max=r_max, out=out))
+    ms_p = timed(lambda: qs.gst_power(2, *dev, rr, out=pw))
+    diff = float((out[:, -1, :].double() - pw).abs().max())
+    tot = float(out[:, -1, :].double().sum(dim=1).sub(1).abs().max())
+    del out, pw
+    torch.cuda.empty_cache()
+    return {"workload": f"{nsets} noisy GST gate sets x 6 gates x 4 preparations = {count} "
+                        f"2-qubit sequences, r = 1..{r_max}",
+            "series": {"ms": ms_s, "repetitions_per_s": count * r_max / (ms_s * 1e-3),
+                       "output_gbs": count * r_max * 16 / (ms_s * 1e-3) / 1e9},
+            "power_r1000": {"ms": ms_p, "sequences_per_s": count / (ms_p * 1e-3)},
+            "max_abs_series_vs_power_at_r1000": diff, "max_abs_norm_error": tot}
+
+
 def extra_fp64(qs, torch, seed=SEED):
     """complex128 runs of the 40-layer workload: the plain per-gate FP64 GPU path at 30
     qubits (16 GiB; the baseline the fused FP32 forms are measured against) and the tiled
@@ -836,7 +925,7 @@ def main():
                          "blocks with the BF16 split; the tiled path is reported as a row)")
     ap.add_argument("--only", default=None,
                     choices=["dm", "serve", "blocks", "small", "qft", "fp64", "grad", "other",
-                             "readout", "dense2q"],
+                             "readout", "dense2q", "gst"],
                     help="run one extra row alone (for profiling) and print it")
     args = ap.parse_args()
     if args.only:
@@ -847,7 +936,7 @@ def main():
         fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
               "small": extra_small_circuits, "qft": extra_qft, "fp64": extra_fp64,
               "grad": extra_sv_grad, "readout": lambda q, t: extra_readout(q, t, n=args.n),
-              "dense2q": extra_dense2q,
+              "dense2q": extra_dense2q, "gst": extra_gst,
               "other": lambda q, t: extra_other_method(q, t, args.method)}[args.only]
         print(json.dumps({"only": args.only, "row": fn(qs, torch)}), flush=True)
         return 0

@@ -295,6 +295,41 @@ qs_status qs_server_destroy(qs_server_t s);
 qs_status qs_probs_noalloc(const void* amps, int n, int prec, void* out, int out_fp64,
                            uint64_t marg_mask, double* norm_out, void* stream);
 
+/* ---- GST predictions for repeated gates ---------------------------------- */
+
+/* Eq. (GSTPrediction): p_J(r) = <<E_J| (G_s)^r G_(prep) |rho>> for batches of
+ * 1- or 2-qubit sequences, with Pauli transfer matrices (Eq.
+ * (paulitransfermatrix), normalised Pauli basis of Eq. (paulibasis): base-4
+ * digit b of an index belongs to qubit b, qubit 0 the least significant) acting on
+ * Pauli vectors (Eqs. (GSTVectorizedRho), (GSTVectorizedEJ)).  All arrays are
+ * DEVICE memory, FP64: ptms n_ptm x 4^n x 4^n (G[out][in]); rho 4^n; effects
+ * 2^n x 4^n (row J = <<E_J|, J = the outcome bit string); gate count int32 (PTM
+ * index of G_s); prep count x 8 int32: the PTM indices of G_(prep) in time order
+ * (the first listed acts first), -1 ends a list.  A sequence with an index out of
+ * range (or, for the power, reps < 0) gets NaN outputs. */
+typedef struct {
+  int32_t n;              /* qubits: 1 or 2 */
+  int32_t count;          /* sequences */
+  int32_t r_max;          /* dm_gst_series: repetitions 1..r_max */
+  int32_t n_ptm;          /* PTMs in the table */
+  const double* ptms;
+  const double* rho;
+  const double* effects;
+  const int32_t* gate;
+  const int32_t* prep;
+} qs_gst_batch;
+
+/* Every r = 1..r_max: probs (DEVICE, count x r_max x 2^n float) gets
+ * p_J(r) at [(i r_max + r - 1) 2^n + J].  One warp per sequence, one
+ * matrix-vector product per repetition in FP32 (inputs converted once).
+ * Asynchronous on stream.  Errors: QS_EINVAL (NULL, n, r_max), QS_ECUDA. */
+qs_status dm_gst_series(const qs_gst_batch* b, float* probs, void* stream);
+
+/* One repetition count per sequence, reps (DEVICE, count int64 >= 0), by
+ * repeated squaring of G_s in FP64 (about 2 log2 r matrix products): probs
+ * (DEVICE, count x 2^n double).  Asynchronous on stream.  Errors: as above. */
+qs_status dm_gst_power(const qs_gst_batch* b, const int64_t* reps, double* probs, void* stream);
+
 /* ---- checkpoint / resume ------------------------------------------------ */
 
 /* Binary checkpoint of the state, for resuming an interrupted simulation (the

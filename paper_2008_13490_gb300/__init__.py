@@ -74,6 +74,12 @@ class DMBatch(ctypes.Structure):
                 ("counts", ctypes.c_void_p), ("ptm1", ctypes.c_void_p), ("ptm2", ctypes.c_void_p)]
 
 
+class GstBatch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("count", ctypes.c_int32), ("r_max", ctypes.c_int32),
+                ("n_ptm", ctypes.c_int32), ("ptms", ctypes.c_void_p), ("rho", ctypes.c_void_p),
+                ("effects", ctypes.c_void_p), ("gate", ctypes.c_void_p), ("prep", ctypes.c_void_p)]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("small_max_qubits", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("max_batch", ctypes.c_int32),
@@ -117,6 +123,8 @@ def load():
         "dm_apply_channels": (i32, [ctypes.POINTER(DMBatch), vp, vp, vp, vp]),
         "qs_probs_noalloc": (i32, [vp, i32, i32, vp, i32, u64, ctypes.POINTER(ctypes.c_double), vp]),
         "sv_bloch": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "dm_gst_series": (i32, [ctypes.POINTER(GstBatch), vp, vp]),
+        "dm_gst_power": (i32, [ctypes.POINTER(GstBatch), vp, vp, vp]),
         "sv_save": (i32, [vp, ctypes.c_char_p]),
         "sv_load": (i32, [vp, ctypes.c_char_p]),
         "qs_meas_error": (i32, [vp, i32, i32, ctypes.POINTER(ctypes.c_double),
@@ -143,6 +151,7 @@ def exported_symbols():
     return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
             "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
             "dm_apply_channels", "qs_probs_noalloc", "sv_bloch", "qs_meas_error", "sv_save", "sv_load",
+            "dm_gst_series", "dm_gst_power",
             "qs_profile_begin", "qs_profile_end",
             "qs_server_create", "qs_server_submit", "qs_server_wait", "qs_server_stats_get",
             "qs_server_destroy", "qs_last_error", "qs_version"]
@@ -387,6 +396,34 @@ def sv_probs(st: State, out=None, fp64: bool = False, marg_mask: int = 0, want_n
     _check(load().sv_probs(st.handle, out.data_ptr(), 1 if fp64 else 0, int(marg_mask),
                            ctypes.byref(norm) if want_norm else None))
     return out, (norm.value if want_norm else None)
+
+
+def _gst_batch(n, ptms, rho, effects, gate, prep, r_max=0):
+    """qs_gst_batch over device tensors: ptms (n_ptm, 4^n, 4^n) float64, rho (4^n,),
+    effects (2^n, 4^n), gate (count,) int32, prep (count, 8) int32 (-1 = end)."""
+    b = GstBatch(int(n), int(gate.numel()), int(r_max), int(ptms.shape[0]), ptms.data_ptr(),
+                 rho.data_ptr(), effects.data_ptr(), gate.data_ptr(), prep.data_ptr())
+    return b
+
+
+def gst_series(n, ptms, rho, effects, gate, prep, r_max, out=None, stream=None):
+    """p_J(r) = <<E_J| G_s^r G_prep |rho>> for r = 1..r_max: (count, r_max, 2^n) float32."""
+    torch = _torch()
+    b = _gst_batch(n, ptms, rho, effects, gate, prep, r_max)
+    if out is None:
+        out = torch.empty((b.count, r_max, 1 << n), dtype=torch.float32, device="cuda")
+    _check(load().dm_gst_series(ctypes.byref(b), out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def gst_power(n, ptms, rho, effects, gate, prep, reps, out=None, stream=None):
+    """p_J = <<E_J| G_s^reps G_prep |rho>> by repeated squaring: (count, 2^n) float64."""
+    torch = _torch()
+    b = _gst_batch(n, ptms, rho, effects, gate, prep)
+    if out is None:
+        out = torch.empty((b.count, 1 << n), dtype=torch.float64, device="cuda")
+    _check(load().dm_gst_power(ctypes.byref(b), reps.data_ptr(), out.data_ptr(), _stream_ptr(stream)))
+    return out
 
 
 def sv_save(st: State, path: str) -> None:
