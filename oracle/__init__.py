@@ -27,6 +27,9 @@ readout      the measurement-error model (Eq. (errordetectionMeasurementError))
              and the Bloch vectors of every qubit (Eq. (multiqubitblochvector)).
 gst          GST predictions for repeated gates (Eq. (GSTPrediction)) and the
              statistical distance (Eq. (statisticaldistance)).
+code422      the [[4,2,2]] error-detection experiment: bare and encoded circuits
+             (Tabs. (errordetectionstates), (errordetectiongates)), postselection
+             and D_bare/enc (Eq. (errordetectionDbareenc)).
 
 Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, printed values of the thesis and brute force.
