@@ -390,6 +390,7 @@ def run_ours(args, world, rank, local):
                         "readout": extra_readout(qs, torch),
                         "dense_2q": extra_dense2q(qs, torch),
                         "gst_prediction": extra_gst(qs, torch),
+                        "code422": extra_code422(qs, torch),
                         "sv_grad": extra_sv_grad(qs, torch),
                         "fp64": extra_fp64(qs, torch),
                         "small_circuits": extra_small_circuits(qs, torch),
@@ -830,6 +831,115 @@ def extra_gst(qs, torch, nsets=1000, r_max=1000, seed=4400, reps=5):
             "max_abs_series_vs_power_at_r1000": diff, "max_abs_norm_error": tot}
 
 
+_C422_BARE = {"X1": [("X", (3,))], "X2": [("X", (4,))], "Z1": [("Z", (3,))], "Z2": [("Z", (4,))],
+              "HHS": [("H", (3,)), ("H", (4,)), ("CNOT", (3, 4))] * 3,
+              "CZ": [("H", (4,)), ("CNOT", (3, 4)), ("H", (4,))]}
+_C422_ENC = {"X1": [("X", (1,)), ("X", (3,))], "X2": [("X", (1,)), ("X", (2,))],
+             "Z1": [("Z", (1,)), ("Z", (2,))], "Z2": [("Z", (1,)), ("Z", (3,))],
+             "HHS": [("H", (q,)) for q in (1, 2, 3, 4)],
+             "CZ": [("S", (q,)) for q in (1, 2, 3, 4)] + [("Z", (2,)), ("Z", (3,))]}
+_C422_PREP_BARE = {"00": [], "0+": [("H", (4,))], "Phi+": [("H", (3,)), ("CNOT", (3, 4))]}
+_C422_PREP_ENC = {"00": [("H", (3,)), ("CNOT", (3, 2)), ("CNOT", (2, 1)), ("CNOT", (3, 4)),
+                         ("CNOT", (1, 0)), ("CNOT", (4, 0))],
+                  "0+": [("H", (2,)), ("CNOT", (2, 1)), ("H", (3,)), ("CNOT", (3, 4))],
+                  "Phi+": [("H", (3,)), ("CNOT", (3, 2)), ("H", (1,)), ("CNOT", (1, 4))]}
+
+
+def extra_code422(qs, torch, nseq=155, settings=100, seed=4220, reps=5):
+    """[[4,2,2]] error-detection experiment, simulation side: 155 synthetic logical
+    sequences x 3 initial states = 465 circuits, each in its encoded (5 qubits) and bare
+    (2 qubits) versions plus the noiseless bare reference, for `settings` noise levels
+    (depolarizing p and amplitude damping gamma after every physical gate) through the
+    batched density-matrix kernel (gates and noise composed into PTMs here with numpy),
+    then postselection and D_bare/enc on the device."""
+    import numpy as np
+
+    import workloads as W
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    Y = np.array([[0, -1j], [1j, 0]])
+    Z = np.diag([1.0 + 0j, -1])
+    I2 = np.eye(2, dtype=complex)
+    P1 = [I2, X, Y, Z]
+    P2 = [np.kron(P1[i >> 2], P1[i & 3]) for i in range(16)]
+
+    def ptm(kraus, P):
+        d = P[0].shape[0]
+        return np.array([[np.real(np.trace(P[i] @ sum(K @ P[j] @ K.conj().T for K in kraus))) / d
+                          for j in range(len(P))] for i in range(len(P))])
+
+    U1 = {"X": X, "Z": Z, "H": np.array([[1, 1], [1, -1]]) / np.sqrt(2), "S": np.diag([1, 1j])}
+    cnot = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex)
+    names1 = ["X", "Z", "H", "S"]
+    ps = np.linspace(0.0, 0.03, settings)
+    ptm1, ptm2 = [], []
+    for p in ps:
+        gam = p / 2
+        dep = [np.sqrt(1 - p) * I2] + [np.sqrt(p / 3) * M for M in (X, Y, Z)]
+        ad = [np.array([[1, 0], [0, np.sqrt(1 - gam)]]), np.array([[0, np.sqrt(gam)], [0, 0]])]
+        N1 = ptm([A @ B for A in ad for B in dep], P1)
+        ptm1 += [N1 @ ptm([U1[g]], P1) for g in names1]
+        ptm2.append(np.kron(N1, N1) @ ptm([cnot], P2))
+    circuits = W.code422_sequences(nseq, seed)
+
+    def batch(encoded, ideal):
+        ops, off, oo = [], [0], [0]
+        n = 5 if encoded else 2
+        qmap = {b: b for b in range(5)} if encoded else {3: 1, 4: 0}
+        for si in range(settings):
+            for state, seq in circuits:
+                phys = list((_C422_PREP_ENC if encoded else _C422_PREP_BARE)[state])
+                for g in seq:
+                    phys += (_C422_ENC if encoded else _C422_BARE)[g]
+                for name, q in phys:
+                    k = 0 if ideal else si
+                    if name == "CNOT":
+                        ops.append([5, qmap[q[0]], qmap[q[1]], k])
+                    else:
+                        ops.append([4, qmap[q[0]], 0, 4 * k + names1.index(name)])
+                off.append(len(ops))
+                oo.append(oo[-1] + (1 << n))
+        C = len(off) - 1
+        t = lambda a, dt: torch.tensor(np.asarray(a), dtype=dt, device="cuda")  # noqa: E731
+        return dict(nq=t([n] * C, torch.int32), op_off=t(off, torch.int64),
+                    ops=t(ops, torch.int32).reshape(-1, 4),
+                    params=torch.zeros(4 * C, dtype=torch.float64, device="cuda"),
+                    out_off=t(oo, torch.int64), max_qubits=n,
+                    max_ops=int(np.max(np.diff(off))),
+                    probs=torch.empty(oo[-1], dtype=torch.float32, device="cuda")), C
+
+    t1 = lambda a: torch.tensor(np.stack(a), dtype=torch.float64, device="cuda")  # noqa: E731
+    tabs = dict(ptm1=t1(ptm1), ptm2=t1(ptm2))
+    (enc, C), (bare, _), (ideal, _) = batch(True, False), batch(False, False), batch(False, True)
+
+    def step():
+        for b in (enc, bare, ideal):
+            qs.dm_apply_channels(**b, **tabs)
+        return qs.code422_eval(enc["probs"].reshape(C, 32), bare["probs"].reshape(C, 4),
+                               ideal["probs"].reshape(C, 4))
+
+    step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        res = step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    p_enc, ratio, d_bare, d_enc = res
+    per = len(circuits)
+    mid = settings // 3
+    return {"workload": f"{per} logical circuits ({nseq} synthetic sequences x 3 states) x {settings} "
+                        f"noise levels (p = 0..0.03, gamma = p/2) = {C} circuits, each encoded (5 qubits), "
+                        f"bare (2) and noiseless bare",
+            "ms": ms, "logical_circuits_per_s": C / (ms * 1e-3),
+            "at_p": float(ps[mid]),
+            "mean_d_bare": float(d_bare[mid * per:(mid + 1) * per].mean()),
+            "mean_d_enc": float(d_enc[mid * per:(mid + 1) * per].mean()),
+            "mean_ratio": float(ratio[mid * per:(mid + 1) * per].mean()),
+            "noiseless_max_d_enc": float(d_enc[:per].max())}
+
+
 def extra_fp64(qs, torch, seed=SEED):
     """complex128 runs of the 40-layer workload: the plain per-gate FP64 GPU path at 30
     qubits (16 GiB; the baseline the fused FP32 forms are measured against) and the tiled
@@ -925,7 +1035,7 @@ def main():
                          "blocks with the BF16 split; the tiled path is reported as a row)")
     ap.add_argument("--only", default=None,
                     choices=["dm", "serve", "blocks", "small", "qft", "fp64", "grad", "other",
-                             "readout", "dense2q", "gst"],
+                             "readout", "dense2q", "gst", "code422"],
                     help="run one extra row alone (for profiling) and print it")
     args = ap.parse_args()
     if args.only:
@@ -936,7 +1046,7 @@ def main():
         fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
               "small": extra_small_circuits, "qft": extra_qft, "fp64": extra_fp64,
               "grad": extra_sv_grad, "readout": lambda q, t: extra_readout(q, t, n=args.n),
-              "dense2q": extra_dense2q, "gst": extra_gst,
+              "dense2q": extra_dense2q, "gst": extra_gst, "code422": extra_code422,
               "other": lambda q, t: extra_other_method(q, t, args.method)}[args.only]
         print(json.dumps({"only": args.only, "row": fn(qs, torch)}), flush=True)
         return 0

@@ -330,6 +330,24 @@ qs_status dm_gst_series(const qs_gst_batch* b, float* probs, void* stream);
  * (DEVICE, count x 2^n double).  Asynchronous on stream.  Errors: as above. */
 qs_status dm_gst_power(const qs_gst_batch* b, const int64_t* reps, double* probs, void* stream);
 
+/* ---- [[4,2,2]] error detection ----------------------------------------- */
+
+/* Evaluation of the error-detection experiment, simulation side (Eq.
+ * (errordetectionDbareenc)).  Per circuit c (all arrays DEVICE float):
+ *   enc[c*32 + J]  outcome probabilities of the encoded circuit on 5 qubits (bit b of
+ *                  J = qubit q_b: q0 the ancilla, q1..q4 the data qubits), e.g.
+ *                  from dm_apply_channels;
+ *   bare[c*4 + J], ideal[c*4 + J]  bare and noiseless bare distributions,
+ *                  J = 2 j0 + j1 (j0 = q3, j1 = q4).
+ * Outputs: p_enc[c*4 + L] the postselected logical distribution (outcomes with
+ * q0 = 1 or an odd number of 1's on q1..q4 discarded, the rest mapped onto the
+ * logical basis of Eqs. (errordetection00L)-(errordetection11L) and renormalised;
+ * zeros when nothing is kept), ratio[c] the kept fraction (postselection ratio),
+ * d_bare[c], d_enc[c] = (1/2) sum_L |p_L - ideal_L|.  Asynchronous on stream.
+ * Errors: QS_EINVAL (count < 0, NULL array), QS_ECUDA. */
+qs_status dm_code422_eval(int count, const float* enc, const float* bare, const float* ideal,
+                          float* p_enc, float* ratio, float* d_bare, float* d_enc, void* stream);
+
 /* ---- checkpoint / resume ------------------------------------------------ */
 
 /* Binary checkpoint of the state, for resuming an interrupted simulation (the

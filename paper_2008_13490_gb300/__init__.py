@@ -124,6 +124,7 @@ def load():
         "qs_probs_noalloc": (i32, [vp, i32, i32, vp, i32, u64, ctypes.POINTER(ctypes.c_double), vp]),
         "sv_bloch": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
         "dm_gst_series": (i32, [ctypes.POINTER(GstBatch), vp, vp]),
+        "dm_code422_eval": (i32, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "dm_gst_power": (i32, [ctypes.POINTER(GstBatch), vp, vp, vp]),
         "sv_save": (i32, [vp, ctypes.c_char_p]),
         "sv_load": (i32, [vp, ctypes.c_char_p]),
@@ -151,7 +152,7 @@ def exported_symbols():
     return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
             "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
             "dm_apply_channels", "qs_probs_noalloc", "sv_bloch", "qs_meas_error", "sv_save", "sv_load",
-            "dm_gst_series", "dm_gst_power",
+            "dm_gst_series", "dm_gst_power", "dm_code422_eval",
             "qs_profile_begin", "qs_profile_end",
             "qs_server_create", "qs_server_submit", "qs_server_wait", "qs_server_stats_get",
             "qs_server_destroy", "qs_last_error", "qs_version"]
@@ -424,6 +425,18 @@ def gst_power(n, ptms, rho, effects, gate, prep, reps, out=None, stream=None):
         out = torch.empty((b.count, 1 << n), dtype=torch.float64, device="cuda")
     _check(load().dm_gst_power(ctypes.byref(b), reps.data_ptr(), out.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+def code422_eval(enc, bare, ideal, stream=None):
+    """[[4,2,2]] evaluation from device float tensors enc (C, 32), bare (C, 4), ideal (C, 4):
+    returns (p_enc (C, 4), ratio (C,), d_bare (C,), d_enc (C,))."""
+    torch = _torch()
+    C = int(enc.shape[0])
+    p_enc = torch.empty((C, 4), dtype=torch.float32, device="cuda")
+    ratio, d_bare, d_enc = (torch.empty(C, dtype=torch.float32, device="cuda") for _ in range(3))
+    _check(load().dm_code422_eval(C, enc.data_ptr(), bare.data_ptr(), ideal.data_ptr(), p_enc.data_ptr(),
+                                  ratio.data_ptr(), d_bare.data_ptr(), d_enc.data_ptr(), _stream_ptr(stream)))
+    return p_enc, ratio, d_bare, d_enc
 
 
 def sv_save(st: State, path: str) -> None:

@@ -122,6 +122,17 @@ def layered_su4(n: int, depth: int, seed: int):
     return ops
 
 
+def code422_sequences(count: int, seed: int, max_len: int = 10):
+    """`count` logical gate sequences for the error-detection experiment: lengths
+    uniform in 1..max_len over {X1, X2, Z1, Z2, HHS, CZ}; each used with the three
+    initial states |00>, |0+>, |Phi+> (3 x count circuits, as (state, sequence))."""
+    g = rng(seed)
+    names = ["X1", "X2", "Z1", "Z2", "HHS", "CZ"]
+    seqs = [[names[int(k)] for k in g.integers(0, 6, size=int(g.integers(1, max_len + 1)))]
+            for _ in range(count)]
+    return [(state, seq) for state in ("00", "0+", "Phi+") for seq in seqs]
+
+
 def qft_circuit(n: int):
     """Textbook QFT on n qubits written in the thesis's gate set.
 
