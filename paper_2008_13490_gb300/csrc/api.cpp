@@ -548,8 +548,8 @@ qs_status run_blocks(State* st, const qs_gate* gates, size_t ngates, int mode, q
   int* status_dev = (int*)dev;
   for (size_t i = 0; i < blocks.size(); ++i) {
     tm.before(4);
-    s = launch_block_pass(st, dev + off_pass + i * sizeof(BlockPass), dev + off_b + i * bb, mode,
-                          status_dev);
+    s = launch_block_pass(st, passes[i], dev + off_pass + i * sizeof(BlockPass), dev + off_b + i * bb,
+                          mode, status_dev);
     tm.after();
     if (s != QS_OK) return s;
   }

@@ -18,6 +18,8 @@
 //   tcgen05.ld (thread = row) -> shared staging -> global.
 // Every mbarrier wait is bounded; on timeout the kernel records QS_ETIMEOUT in
 // a status word, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -201,11 +203,14 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
 // ---------------------------------------------------------------- kernel
 //
 // One persistent CTA per SM, four roles that overlap consecutive tiles:
-//   warp 13             loader: lane j bulk-copies run j of tile i into raw stage
-//                       i % kStages of a shared-memory ring.  The 7 lowest
-//                       physical bits are always tile bits (each is a block bit
-//                       or one of the 7 lowest others), so a tile is 32
-//                       contiguous runs of 128 amplitudes (1 KiB each).
+//   warp 13             loader: tile i into raw stage i % kStages of a
+//                       shared-memory ring, as 2^(5-g) tensor boxes.  The 7
+//                       lowest physical bits are always tile bits (each is a
+//                       block bit or one of the 7 lowest others), so a tile is
+//                       32 contiguous runs of 128 amplitudes (1 KiB each); the
+//                       other 5 tile positions hold a run of g consecutive
+//                       ones, and one box copies the 2^g runs along it
+//                       (1 KiB requests cost the copy engine far more per byte)
 //   warps 0-3           producers: thread = row m = tensor-memory lane; split row
 //                       m of tile i into its parts and store them into the A
 //                       operand in tensor memory (tcgen05.st), one K half (16
@@ -311,11 +316,13 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+// one box of a rank-4 tensor map (coordinates innermost first) into shared memory
+__device__ __forceinline__ void box_load4(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                          uint64_t* b) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(b))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(b))
       : "memory");
 }
 // bounded wait; gives up after kWaitLimit polls or, if fail is given, once
@@ -347,7 +354,8 @@ __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
 template <int MODE>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     block_pipe_kernel(float2* __restrict__ psi, const BlockPass* __restrict__ P,
-                      const unsigned char* __restrict__ bmat, uint64_t ntiles, int* __restrict__ status) {
+                      const unsigned char* __restrict__ bmat, uint64_t ntiles, int* __restrict__ status,
+                      const __grid_constant__ CUtensorMap tmap) {
   using O = BOps<MODE>;
   constexpr int kStages = Pipe<MODE>::kStages;
   constexpr int kParts = O::kParts;
@@ -371,6 +379,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   __shared__ uint8_t s_nt[48];
+  __shared__ uint8_t s_slot[32];
   __shared__ int s_nnt;
   __shared__ float s_norm[kNormSlots][128];   // producer -> epilogue: squared input row norms
   __shared__ float s_part[2][128];            // epilogue column halves: squared output norms
@@ -385,6 +394,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     t_c_hi[tid] = P->c_hi[tid];
   }
   if (tid < 48) s_nt[tid] = P->nt_pos[tid];
+  if (tid < 32) s_slot[tid] = P->run_slot[tid];
   if (tid == 0) {
     s_nnt = P->n_nt;
     s_fail = 0;
@@ -439,8 +449,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   // (element bit 8 + b = bit 2 + b of the high half)
   uint64_t addr0 = 0, dA[4];
   uint32_t idx0 = 0, dS[4];
-  // loader: offset of run `lane`
-  uint64_t run_off = 0;
+  // loader: lane q < n_copy loads box q: the address bits q_off of its runs
+  // outside the box, and the box's position (bits 7..g_lo-1 and above g_lo+g_len
+  // are the tensor coordinates 1 and 3)
+  uint64_t q_off = 0;
+  int n_copy = 0, g_lo = 7, g_len = 5;
   if (warp < 4) {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -453,6 +466,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     for (int b = 0; b < 4; ++b) ecb[b] = t_ec[1 << b];
     ec16 = t_ec[16];
     e00 = t_em[tid] ^ t_ec[sigma];
+    // raw stages hold run j (address-order bits 7..11) in slot s_slot[j]: a bit
+    // permutation, so it applies to the XOR steps as well
+    auto slot = [&](uint32_t e) { return (e & 127u) | ((uint32_t)s_slot[e >> 7] << 7); };
+#pragma unroll
+    for (int b = 0; b < 4; ++b) ecb[b] = slot(ecb[b]);
+    ec16 = slot(ec16);
+    e00 = slot(e00);
   } else if (warp < 12) {
     const int et = tid - 128;   // 0..255
     const int m_lo = t_m_lo[et & 63], c_lo = t_c_lo[et & 63];
@@ -464,7 +484,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       dS[bit] = t_sh[4 << bit];
     }
   } else if (warp == kWarpLoad) {
-    run_off = t_addr_hi[2 * lane];
+    n_copy = P->n_copy;
+    g_lo = P->g_lo;
+    g_len = P->g_len;
+    if (lane < n_copy) q_off = P->q_off[lane];
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
@@ -492,7 +515,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       const uint64_t base = tile_base(i);
       if (lane == 0) mbar_arrive_tx(&rfull[s], kTileBytes);   // before any of the copies
       __syncwarp();
-      bulk_load(smem + s * kTileBytes + lane * kRun, psi + (base | run_off), kRun, &rfull[s]);
+      if (lane < n_copy) {
+        const uint64_t a = base | q_off;
+        const int c1 = (int)((a >> 7) & ((1ull << (g_lo - 7)) - 1)), c3 = (int)(a >> (g_lo + g_len));
+        box_load4(smem + s * kTileBytes + (lane << g_len) * kRun, &tmap, 0, c1, 0, c3, &rfull[s]);
+      }
       issued = i + 1;
     }
     // no copy may still be writing shared memory when the CTA exits
@@ -888,6 +915,34 @@ void block_pass_desc(int n, const int* bpos, BlockPass& P) {
       }
     }
   }
+  // tensor-box loads: H = order[7..11]; the first longest run of consecutive
+  // positions in H becomes the box's second dimension
+  const int* H = order + 7;
+  int g0 = 0, g = 1;
+  for (int i = 0; i < 5;) {
+    int k = i + 1;
+    while (k < 5 && H[k] == H[k - 1] + 1) ++k;
+    if (k - i > g) {
+      g0 = i;
+      g = k - i;
+    }
+    i = k;
+  }
+  P.g0 = g0;
+  P.g_len = g;
+  P.g_lo = H[g0];
+  P.n_copy = 1 << (5 - g);
+  for (int j = 0; j < 32; ++j) {
+    const int lo = j & ((1 << g0) - 1), gv = (j >> g0) & ((1 << g) - 1), hi = j >> (g0 + g);
+    P.run_slot[j] = (uint8_t)(gv | (lo << g) | (hi << (g + g0)));
+  }
+  for (int q = 0; q < P.n_copy; ++q) {
+    const int j = (q & ((1 << g0) - 1)) | ((q >> g0) << (g0 + g));
+    uint64_t off = 0;
+    for (int b = 0; b < 5; ++b)
+      if ((j >> b) & 1) off |= 1ull << H[b];
+    P.q_off[q] = off;
+  }
 }
 
 size_t block_pass_bytes() { return sizeof(BlockPass); }
@@ -900,8 +955,45 @@ bool block_pass_runs_contiguous(const BlockPass& P) {
   return P.addr_hi[1] == 64;
 }
 
-qs_status launch_block_pass(State* st, const void* pass_dev, const void* b_dev, int mode,
-                            int* status_dev) {
+// The tensor map of a pass's tile loads: the state as [128 | 2^(g_lo-7) |
+// 2^g_len | 2^(n-g_lo-g_len)] amplitudes (8 bytes each), box 128 x 1 x 2^g_len x 1.
+static qs_status block_tensor_map(const State* st, const BlockPass& P, CUtensorMap* map) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      set_error("cuTensorMapEncodeTiled is not available");
+      return QS_ECUDA;
+    }
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const int a = P.g_lo, g = P.g_len, n = st->n;
+  if (a < 7 || g < 1 || a + g > n || P.n_copy != (1 << (5 - g))) {
+    set_error("block pass: invalid tile box");
+    return QS_EINVAL;
+  }
+  const cuuint64_t dims[4] = {128, 1ull << (a - 7), 1ull << g, 1ull << (n - a - g)};
+  const cuuint64_t strides[3] = {1024, 8ull << a, 8ull << (a + g)};
+  const cuuint32_t box[4] = {128, 1, 1u << g, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, st->data, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed for a block pass");
+    return QS_ECUDA;
+  }
+  return QS_OK;
+}
+
+qs_status launch_block_pass(State* st, const BlockPass& host_pass, const void* pass_dev, const void* b_dev,
+                            int mode, int* status_dev) {
+  CUtensorMap map;
+  const qs_status ms = block_tensor_map(st, host_pass, &map);
+  if (ms != QS_OK) return ms;
   const uint64_t ntiles = 1ull << (st->n - 12);
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -919,13 +1011,13 @@ qs_status launch_block_pass(State* st, const void* pass_dev, const void* b_dev, 
     QS_CUDA(cudaFuncSetAttribute(block_pipe_kernel<BM_TF32>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     block_pipe_kernel<BM_TF32><<<(unsigned)grid, kPipeThreads, smem, st->stream>>>(
-        (float2*)st->data, (const BlockPass*)pass_dev, (const unsigned char*)b_dev, ntiles, status_dev);
+        (float2*)st->data, (const BlockPass*)pass_dev, (const unsigned char*)b_dev, ntiles, status_dev, map);
   } else {
     const size_t smem = pipe_smem_bytes<BM_BF16>();
     QS_CUDA(cudaFuncSetAttribute(block_pipe_kernel<BM_BF16>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     block_pipe_kernel<BM_BF16><<<(unsigned)grid, kPipeThreads, smem, st->stream>>>(
-        (float2*)st->data, (const BlockPass*)pass_dev, (const unsigned char*)b_dev, ntiles, status_dev);
+        (float2*)st->data, (const BlockPass*)pass_dev, (const unsigned char*)b_dev, ntiles, status_dev, map);
   }
   QS_CUDA(cudaGetLastError());
   return QS_OK;

@@ -219,6 +219,15 @@ struct BlockPass {
   int32_t n_nt;
   int32_t flags;                // bit 0: the block is unitary (rows keep their norm)
   int32_t pad[2];
+  // Tile loads as tensor boxes: the 5 tile positions above bit 6 (H, ascending)
+  // hold a longest run of g consecutive positions starting at position g_lo (run
+  // bits g0 .. g0+g-1 of the run index j = address-order bits 7..11); each of
+  // the n_copy = 2^(5-g) copies loads 128 x 2^g amplitudes (bits 0..6 and the
+  // run) for one value q of the other H bits, q_off[q] = their address bits.
+  // Run j lands in shared-memory slot run_slot[j] (the run's bits lowest).
+  uint64_t q_off[16];
+  uint8_t run_slot[32];
+  int32_t n_copy, g_lo, g_len, g0;
 };
 void block_pass_desc(int n, const int* bpos, BlockPass& P);
 bool block_pass_runs_contiguous(const BlockPass& P);
@@ -227,8 +236,8 @@ bool block_is_unitary(const cd* U);
 size_t block_pass_bytes();
 void block_b_operand(const cd* U, int mode, std::vector<unsigned char>& out);
 size_t block_b_bytes(int mode);
-qs_status launch_block_pass(State* st, const void* pass_dev, const void* b_dev, int mode,
-                            int* status_dev);
+qs_status launch_block_pass(State* st, const BlockPass& host_pass, const void* pass_dev,
+                            const void* b_dev, int mode, int* status_dev);
 
 // Applies gates to a state (the body of sv_apply_circuit; api.cpp).
 qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats,

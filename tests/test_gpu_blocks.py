@@ -48,6 +48,39 @@ def test_blocks_random_gate_mix(qs, n, method):
     assert err <= TOL[method], err
 
 
+# one dense block on chosen positions of an 18-qubit random state: the tile's five
+# positions above bit 6 hold runs of every length (the tile loads as 2^(5-g)
+# tensor boxes of 2^g runs), at bit 7, in the middle and at the top of the index
+PLACEMENTS = [
+    [0, 1, 2, 3, 4],          # tile = bits 0..11: one box of 32 runs
+    [7, 8, 9, 10, 11],        # the same tile through block positions
+    [13, 14, 15, 16, 17],     # box at the top of the index
+    [0, 7, 14, 15, 17],       # runs {7,8} {14,15} {17}: four boxes
+    [2, 9, 12, 15, 17],       # no two adjacent: sixteen boxes of 2 KiB
+    [8, 10, 11, 12, 16],      # the run {10,11,12} with one position below it, one above
+    [9, 10, 13, 14, 15],      # the run {13,14,15} above the run {9,10}
+]
+
+
+@pytest.mark.parametrize("method", [2, 3])
+@pytest.mark.parametrize("q", PLACEMENTS, ids=lambda q: "-".join(map(str, q)))
+def test_blocks_tile_boxes(qs, q, method):
+    n = 18
+    g = W.rng(1800 + sum(q))
+    ops = []
+    for layer in range(3):
+        for b in q:
+            ops.append(("MAT1", (b,), (), W.haar_su2(g)))
+        for a in range(layer % 2, 4, 2):
+            ops.append(("CZ", (q[a], q[a + 1]), (), None))
+    psi0 = W.random_state(n, g).astype(np.complex64).astype(np.complex128)
+    ref = SV.apply_circuit(psi0.copy(), n, ops)
+    out, stats = _run(qs, n, ops, method, psi0)
+    assert stats["passes"] == 1
+    err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert err <= TOL[method], err
+
+
 @pytest.mark.parametrize("method", [2, 3])
 def test_blocks_depth60_n20(qs, method):
     # the 32-qubit workload's circuit family at 20 qubits (seed 3002), checked in full
