@@ -248,6 +248,7 @@ constexpr int kTileBytes = 4096 * 8;          // one raw tile (complex64)
 constexpr int kRun = 1024;                    // bytes of one contiguous run
 constexpr int kEpiBarrier = 1;                // named barriers of the 256 epilogue threads:
 constexpr int kEpiSync = 2;                   // reduction (kEpiBarrier) and plain sync
+constexpr int kEpiPair = 3;                   // 3..6: the two epilogue warps of one row range
 constexpr int kNormSlots = 3;                 // row norms in flight (producer -> epilogue)
 constexpr int kWarpMma = 12, kWarpLoad = 13;
 
@@ -380,6 +381,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   __shared__ int s_fail;
   __shared__ uint8_t s_nt[48];
   __shared__ uint8_t s_slot[32];
+  __shared__ uint8_t s_f[8];
   __shared__ int s_nnt;
   __shared__ float s_norm[kNormSlots][128];   // producer -> epilogue: squared input row norms
   __shared__ float s_part[2][128];            // epilogue column halves: squared output norms
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   }
   if (tid < 48) s_nt[tid] = P->nt_pos[tid];
   if (tid < 32) s_slot[tid] = P->run_slot[tid];
+  if (tid < 8) s_f[tid] = P->stage_f[tid];
   if (tid == 0) {
     s_nnt = P->n_nt;
     s_fail = 0;
@@ -428,10 +431,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     if (c == 0) t_em[m] = (uint16_t)e;
     if (m == 0) t_ec[c] = (uint16_t)e;
   }
-  // staging index m*32 + (c ^ (m & 31)) of the element with address-order index
+  // staging index m*32 + (c ^ F(m)) of the element with address-order index
   // e = (term of its low 6 bits) ^ t_sh[e >> 6]: the row and column bits of the
-  // two halves are disjoint, so | and + become ^
-  if (tid < 64) t_sh[tid] = (uint16_t)((t_m_hi[tid] << 5) ^ t_c_hi[tid] ^ (t_m_hi[tid] & 31));
+  // two halves are disjoint, so | and + become ^ (F is XOR-linear)
+  auto stage_F = [&](int m) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j)
+      if ((m >> j) & 1) r ^= s_f[j];
+    return r;
+  };
+  if (tid < 64) t_sh[tid] = (uint16_t)((t_m_hi[tid] << 5) ^ t_c_hi[tid] ^ stage_F(t_m_hi[tid]));
   __syncthreads();
 
   // ---- per-role registers (from the tables; the staging is free after this)
@@ -446,9 +456,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   int ncb = 0;
   // epilogue: element k * 256 + et of the store loop, k in Gray-code order: its
   // address and staging index at k = 0 and their change when bit b of k flips
-  // (element bit 8 + b = bit 2 + b of the high half)
+  // (element bit 8 + b = bit 2 + b of the high half); F(m) of the row written
   uint64_t addr0 = 0, dA[4];
-  uint32_t idx0 = 0, dS[4];
+  uint32_t idx0 = 0, dS[4], fm = 0;
   // loader: lane q < n_copy loads box q: the address bits q_off of its runs
   // outside the box, and the box's position (bits 7..g_lo-1 and above g_lo+g_len
   // are the tensor coordinates 1 and 3)
@@ -477,12 +487,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     const int et = tid - 128;   // 0..255
     const int m_lo = t_m_lo[et & 63], c_lo = t_c_lo[et & 63];
     addr0 = (uint64_t)(et & 63) | t_addr_hi[et >> 6];   // low 6 bits: physical bits 0..5
-    idx0 = (uint32_t)((m_lo << 5) ^ c_lo ^ (m_lo & 31)) ^ t_sh[et >> 6];
+    idx0 = (uint32_t)((m_lo << 5) ^ c_lo ^ stage_F(m_lo)) ^ t_sh[et >> 6];
 #pragma unroll
     for (int bit = 0; bit < 4; ++bit) {
       dA[bit] = t_addr_hi[4 << bit];
       dS[bit] = t_sh[4 << bit];
     }
+    fm = stage_F((warp & 3) * 32 + lane) & 31u;
   } else if (warp == kWarpLoad) {
     n_copy = P->n_copy;
     g_lo = P->g_lo;
@@ -732,14 +743,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 #pragma unroll
           for (int j = 0; j < w; ++j) sq[j] += sq[j + w];
         s_part[half][m] = sq[0];
-        bar_sync(kEpiSync, kEpiThreads);
+        bar_sync(kEpiPair + (warp & 3), 64);   // the two warps of these rows
         const float ny = s_part[0][m] + s_part[1][m];
         if (ny > 0.f) delta = (nx - ny) / (ny + sqrtf(nx) * sqrtf(ny));
       }
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int c = 16 * half + j;
-        stage[m * 32 + (c ^ (m & 31))] =
+        stage[m * 32 + (c ^ fm)] =
             make_float2(fmaf(y[2 * j], delta, y[2 * j]), fmaf(y[2 * j + 1], delta, y[2 * j + 1]));
       }
       bar_sync(kEpiSync, kEpiThreads);
@@ -943,6 +954,55 @@ void block_pass_desc(int n, const int* bpos, BlockPass& P) {
       if ((j >> b) & 1) off |= 1ull << H[b];
     P.q_off[q] = off;
   }
+  // staging swizzle F: the bank pair of an 8-byte staging word is its index mod 16,
+  // i.e. bits 0..3 of c ^ F(m).  Writes: a warp's lanes are row bits 0..4, so
+  // {F(2^j) mod 16, j < 5} must span the 4 bits.  Reads: a warp's lanes are
+  // physical bits 0..4; a column bit c_i there contributes 2^i (i < 4), a row bit
+  // m_j contributes F(2^j) mod 16, and these must span the 4 bits.  F(2^j) = 2^j
+  // (j < 5) is tried first, then a fixed pseudo-random sequence.
+  auto rank4 = [](const uint32_t* v, int k) {
+    uint32_t basis[4] = {0, 0, 0, 0};
+    int r = 0;
+    for (int i = 0; i < k; ++i) {
+      uint32_t x = v[i] & 15u;
+      for (int b = 3; b >= 0 && x; --b)
+        if ((x >> b) & 1) {
+          if (!basis[b]) {
+            basis[b] = x;
+            ++r;
+            x = 0;
+          } else {
+            x ^= basis[b];
+          }
+        }
+    }
+    return r;
+  };
+  uint32_t F[7];
+  uint32_t seed = 0x9e3779b9u;
+  for (int trial = 0; trial < 4096; ++trial) {
+    for (int j = 0; j < 7; ++j) {
+      if (trial == 0) {
+        F[j] = j < 5 ? (1u << j) & 15u : 0u;
+      } else {
+        seed ^= seed << 13;
+        seed ^= seed >> 17;
+        seed ^= seed << 5;
+        F[j] = seed & 15u;
+      }
+    }
+    uint32_t rd[5];
+    for (int p = 0; p < 5; ++p) {
+      int is_col = 0, idx = 0;
+      role(p, &is_col, &idx);
+      rd[p] = is_col ? (idx < 4 ? 1u << idx : 0u) : F[idx];
+    }
+    if (rank4(F, 5) == 4 && rank4(rd, 5) == 4) break;
+    if (trial == 4095)
+      for (int j = 0; j < 7; ++j) F[j] = j < 5 ? (1u << j) & 15u : 0u;   // (2-way conflicts)
+  }
+  for (int j = 0; j < 7; ++j) P.stage_f[j] = (uint8_t)F[j];
+  P.stage_f[7] = 0;
 }
 
 size_t block_pass_bytes() { return sizeof(BlockPass); }

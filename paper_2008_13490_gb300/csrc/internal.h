@@ -227,6 +227,11 @@ struct BlockPass {
   // Run j lands in shared-memory slot run_slot[j] (the run's bits lowest).
   uint64_t q_off[16];
   uint8_t run_slot[32];
+  // Output staging: row m, column c at m*32 + (c ^ F(m)), F XOR-linear with
+  // F(2^j) = stage_f[j]; chosen so that the epilogue's staging writes (a warp's
+  // lanes = row bits 0..4) and its reads in address order (a warp's lanes =
+  // physical bits 0..4) each fall on 16 distinct 8-byte bank pairs.
+  uint8_t stage_f[8];
   int32_t n_copy, g_lo, g_len, g0;
 };
 void block_pass_desc(int n, const int* bpos, BlockPass& P);
