@@ -72,7 +72,7 @@ METHOD_NOTE = {
 # sources each kernel is compiled from: a stored ncu traffic figure is used only while
 # their hash is unchanged
 KERNEL_SOURCES = {
-    "tile": ("sv_kernels.cu", "dev_common.cuh", "internal.h"),
+    "tile": ("sv_kernels.cu", "dev_common.cuh", "internal.h", "tile_cp.h"),
     "block": ("block_tc.cu", "internal.h"),
 }
 TRAFFIC_FILES = {
@@ -1044,7 +1044,7 @@ def main():
         import paper_2008_13490_gb300 as qs
         qs.load()
         fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
-              "small": extra_small_circuits, "qft": extra_qft, "fp64": extra_fp64,
+              "small": extra_small_circuits, "qft": lambda q, t: extra_qft(q, t, n=args.n), "fp64": extra_fp64,
               "grad": extra_sv_grad, "readout": lambda q, t: extra_readout(q, t, n=args.n),
               "dense2q": extra_dense2q, "gst": extra_gst, "code422": extra_code422,
               "other": lambda q, t: extra_other_method(q, t, args.method)}[args.only]

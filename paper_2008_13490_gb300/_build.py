@@ -32,7 +32,7 @@ def sources():
 def _compile(nvcc: str, src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     if os.path.exists(obj):
-        deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+        deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
         deps.append(os.path.join(ROOT, "include", "qsim.h"))
         if all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
             return obj

@@ -8,6 +8,7 @@
 #include <utility>
 
 #include "internal.h"
+#include "tile_cp.h"
 
 namespace qs {
 
@@ -178,6 +179,36 @@ TileOp<R> to_tile(const Plan& pl, size_t i) {
   return t;
 }
 
+// A diagonal whose entries are all exactly 1 but the last (a controlled phase,
+// or a one-qubit phase) becomes TK_CP: its phase and the context-word positions
+// of its bits (see TK_CP); other ops are returned unchanged.
+template <typename R>
+TileOp<R> cp_form(TileOp<R> t) {
+  if (t.kind != TK_DIAG) return t;
+  const bool two = t.dsrc != CS_NONE;
+  const int last = two ? 3 : 1;
+  for (int k = 0; k < last; ++k)
+    if (t.m0[k].x != R(1) || t.m0[k].y != R(0)) return t;
+  auto ctx_pos = [](uint8_t src, uint8_t bit) -> int {
+    switch (src) {
+      case CS_TILE: return bit < kCtxOne ? bit : -1;
+      case CS_LANE: return kCtxLane + bit;
+      case CS_WARP: return kCtxWarp + bit;
+      case CS_REG: return 0;   // (not read)
+      default: return -1;
+    }
+  };
+  const int pa = ctx_pos(t.csrc, t.cbit), pb = two ? ctx_pos(t.dsrc, t.dbit) : kCtxOne;
+  if (pa < 0 || pb < 0) return t;
+  const C2<R> p = t.m0[last];
+  t.kind = TK_CP;
+  t.m0[0] = p;
+  for (int k = 1; k < 4; ++k) t.m0[k] = C2<R>{R(0), R(0)};
+  t.pad[0] = (uint8_t)pa;
+  t.pad[1] = (uint8_t)pb;
+  return t;
+}
+
 template <typename T>
 size_t put(std::vector<unsigned char>& blob, const T* p, size_t count) {
   size_t off = align16(blob.size());
@@ -340,7 +371,7 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
         const int op0 = pl.stages[pass.stage_begin].op_begin;
         for (int s2 = 0; s2 < pass.n_stages; ++s2) {
           TileStage ts = pl.stages[pass.stage_begin + s2];
-          for (int o = ts.op_begin; o < ts.op_end; ++o) tp->ops[o - op0] = to_tile<R>(pl, (size_t)o);
+          for (int o = ts.op_begin; o < ts.op_end; ++o) tp->ops[o - op0] = cp_form(to_tile<R>(pl, (size_t)o));
           ts.op_begin -= op0;
           ts.op_end -= op0;
           tp->stages[s2] = ts;

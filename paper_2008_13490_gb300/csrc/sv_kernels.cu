@@ -18,6 +18,7 @@
 
 #include "dev_common.cuh"
 #include "internal.h"
+#include "tile_cp.h"
 
 namespace qs {
 
@@ -329,6 +330,32 @@ struct DiagRun {
       s = cmul(s, csel(idx >= 2, csel(idx == 3, d[3], d[2]), csel(idx == 1, d[1], d[0])));
     }
   }
+  // TK_CP: one complex multiply into the factor of the register bit (or into
+  // s), selected by the other bit; 16 selected multiplies when both bits are
+  // register bits
+  __device__ __forceinline__ void add_cp(C2<R>* v, const TileOp<R>* __restrict__ opp, uint64_t ctx) {
+    const uint8_t csrc = opp->csrc, cbit = opp->cbit, dsrc = opp->dsrc, dbit = opp->dbit;
+    const C2<R> p = opp->m0[0], one{R(1), R(0)};
+    const bool ra = csrc == CS_REG, rb = dsrc == CS_REG;
+    if (ra && rb) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], csel(((r >> cbit) & (r >> dbit) & 1) != 0, p, one));
+      return;
+    }
+    const int ua = ra ? 1 : (int)((ctx >> opp->pad[0]) & 1ull);
+    const int ub = rb ? 1 : (int)((ctx >> opp->pad[1]) & 1ull);
+    const C2<R> e = csel((ua & ub) != 0, p, one);
+    if (ra || rb) {
+      switch (ra ? cbit : dbit) {
+        case 0: f0[1] = cmul(f0[1], e); break;
+        case 1: f1[1] = cmul(f1[1], e); break;
+        case 2: f2[1] = cmul(f2[1], e); break;
+        default: f3[1] = cmul(f3[1], e); break;
+      }
+    } else {
+      s = cmul(s, e);
+    }
+  }
   template <bool TWO = false>
   __device__ __forceinline__ void flush(C2<R>* v, C2<R>* v2 = nullptr) {
     // D(r) = s f0[r0] f1[r1] f2[r2] f3[r3] as (s f0 f1)[r & 3] * (f2 f3)[r >> 2]
@@ -373,6 +400,8 @@ __global__ void __launch_bounds__(kTileThreads)
   const int nst = P.pass.n_stages;
   const TileStage* __restrict__ S = P.stages;
   const TileOp<R>* __restrict__ ops = P.ops;
+  // context word of TK_CP bits: tile index, a constant 1 at bit 47, lane, warp
+  const uint64_t ctx = tile | (1ull << kCtxOne) | ((uint64_t)lane << kCtxLane) | ((uint64_t)warp << kCtxWarp);
   C2<R> v[16];
   {
     const TileStage s0 = S[0];
@@ -430,7 +459,7 @@ __global__ void __launch_bounds__(kTileThreads)
       }
     }
     for (int o = cur.op_begin; o < cur.op_end;) {
-      if (ops[o].kind != TK_DIAG) {
+      if (ops[o].kind != TK_DIAG && ops[o].kind != TK_CP) {
         apply_tile_op<R, G2>(v, ops + o, tile, lane, warp);
         o += (G2 && ops[o].kind == TK_G2) ? 2 : 1;   // a dense two-qubit op spans two entries
         continue;
@@ -438,9 +467,10 @@ __global__ void __launch_bounds__(kTileThreads)
       DiagRun<R> dr;   // live only over the run
       dr.reset();
       do {
-        dr.add(v, ops + o, tile, lane, warp);
+        if (ops[o].kind == TK_CP) dr.add_cp(v, ops + o, ctx);
+        else dr.add(v, ops + o, tile, lane, warp);
         ++o;
-      } while (o < cur.op_end && ops[o].kind == TK_DIAG);
+      } while (o < cur.op_end && (ops[o].kind == TK_DIAG || ops[o].kind == TK_CP));
       dr.flush(v);
     }
   }
