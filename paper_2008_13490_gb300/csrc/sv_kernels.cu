@@ -333,8 +333,12 @@ struct DiagRun {
   // TK_CP: one complex multiply into the factor of the register bit (or into
   // s), selected by the other bit; 16 selected multiplies when both bits are
   // register bits
-  __device__ __forceinline__ void add_cp(C2<R>* v, const TileOp<R>* __restrict__ opp, uint64_t ctx) {
-    const uint8_t csrc = opp->csrc, cbit = opp->cbit, dsrc = opp->dsrc, dbit = opp->dbit;
+  // (hdr = the op's first 16 bytes, read with one load: kind, slot, csrc,
+  // cbit | dsrc, dbit, term | pad[0..3] | pad[4..7])
+  __device__ __forceinline__ void add_cp(C2<R>* v, const TileOp<R>* __restrict__ opp, uint4 hdr,
+                                         uint64_t ctx) {
+    const uint32_t csrc = (hdr.x >> 16) & 0xffu, cbit = hdr.x >> 24, dsrc = hdr.y & 0xffu,
+                   dbit = (hdr.y >> 8) & 0xffu, pa = hdr.z & 0xffu, pb = (hdr.z >> 8) & 0xffu;
     const C2<R> p = opp->m0[0], one{R(1), R(0)};
     const bool ra = csrc == CS_REG, rb = dsrc == CS_REG;
     if (ra && rb) {
@@ -342,8 +346,8 @@ struct DiagRun {
       for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], csel(((r >> cbit) & (r >> dbit) & 1) != 0, p, one));
       return;
     }
-    const int ua = ra ? 1 : (int)((ctx >> opp->pad[0]) & 1ull);
-    const int ub = rb ? 1 : (int)((ctx >> opp->pad[1]) & 1ull);
+    const int ua = ra ? 1 : (int)((ctx >> pa) & 1ull);
+    const int ub = rb ? 1 : (int)((ctx >> pb) & 1ull);
     const C2<R> e = csel((ua & ub) != 0, p, one);
     if (ra || rb) {
       switch (ra ? cbit : dbit) {
@@ -466,11 +470,14 @@ __global__ void __launch_bounds__(kTileThreads)
       }
       DiagRun<R> dr;   // live only over the run
       dr.reset();
+      uint4 hdr = *reinterpret_cast<const uint4*>(ops + o);
       do {
-        if (ops[o].kind == TK_CP) dr.add_cp(v, ops + o, ctx);
+        if ((hdr.x & 0xffu) == TK_CP) dr.add_cp(v, ops + o, hdr, ctx);
         else dr.add(v, ops + o, tile, lane, warp);
         ++o;
-      } while (o < cur.op_end && (ops[o].kind == TK_DIAG || ops[o].kind == TK_CP));
+        if (o >= cur.op_end) break;
+        hdr = *reinterpret_cast<const uint4*>(ops + o);
+      } while ((hdr.x & 0xffu) == TK_DIAG || (hdr.x & 0xffu) == TK_CP);
       dr.flush(v);
     }
   }
