@@ -859,11 +859,22 @@ size_t block_b_bytes(int mode) {
 }
 
 bool block_is_unitary(const cd* U) {
+  // (U^dagger U)_ij = sum_k conj(U_ki) U_kj in real arithmetic; Hermitian, so j >= i
+  double re[32][32], im[32][32];
+  for (int k = 0; k < 32; ++k)
+    for (int i = 0; i < 32; ++i) {
+      re[k][i] = U[k * 32 + i].real();
+      im[k][i] = U[k * 32 + i].imag();
+    }
   for (int i = 0; i < 32; ++i)
-    for (int j = 0; j < 32; ++j) {
-      cd s = 0;
-      for (int k = 0; k < 32; ++k) s += std::conj(U[k * 32 + i]) * U[k * 32 + j];
-      if (std::abs(s - (i == j ? 1.0 : 0.0)) > 1e-10) return false;
+    for (int j = i; j < 32; ++j) {
+      double sr = 0, si = 0;
+      for (int k = 0; k < 32; ++k) {
+        sr += re[k][i] * re[k][j] + im[k][i] * im[k][j];
+        si += re[k][i] * im[k][j] - im[k][i] * re[k][j];
+      }
+      if (i == j) sr -= 1.0;
+      if (sr * sr + si * si > 1e-20) return false;
     }
   return true;
 }

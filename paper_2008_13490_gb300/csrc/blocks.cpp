@@ -17,6 +17,20 @@ namespace {
 // U <- G U, G acting on the block-local bits ia (and ib, the less significant
 // bit of G's 4x4 local index) of the 32-dimensional block space.
 void apply_to_block(std::vector<cd>& U, const cd* g, int dim, int ia, int ib) {
+  // a diagonal gate scales rows (entries exactly 1 leave them alone)
+  bool diag = true;
+  for (int o = 0; o < dim; ++o)
+    for (int l = 0; l < dim; ++l)
+      if (o != l && g[o * dim + l] != cd(0)) diag = false;
+  if (diag) {
+    for (int r = 0; r < 32; ++r) {
+      const int l = dim == 2 ? ((r >> ia) & 1) : (((r >> ia) & 1) << 1) | ((r >> ib) & 1);
+      const cd d = g[l * dim + l];
+      if (d == cd(1)) continue;
+      for (int c = 0; c < 32; ++c) U[r * 32 + c] *= d;
+    }
+    return;
+  }
   if (dim == 2) {
     for (int r = 0; r < 32; ++r) {
       if ((r >> ia) & 1) continue;
