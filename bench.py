@@ -95,10 +95,6 @@ def kernel_src_hash(kind):
     return h.hexdigest()
 
 
-def tile_kernel_src_hash():
-    return kernel_src_hash("tile")
-
-
 def stored_traffic(kind, method):
     """DRAM bytes per launch of the dominant kernel at 30 qubits from the committed ncu
     summary, or None when there is none or the kernel's sources have changed since."""
