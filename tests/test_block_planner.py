@@ -1,0 +1,83 @@
+"""The host block planner on the CPU: the 5-qubit blocks it makes of a circuit,
+applied in order to a random state (each block's 32x32 matrix on its qubits,
+numpy), give the oracle's state; every block of a unitary circuit is reported
+unitary.  Covers dense one- and two-qubit gates, diagonals (which the planner
+applies by scaling rows), SWAPs, and layered and QFT circuits."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import ROOT
+from oracle import statevector as SV
+
+
+@pytest.fixture(scope="module")
+def dump_exe(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    from paper_2008_13490_gb300 import _build
+    lib = _build.build()
+    libdir = os.path.dirname(lib)
+    exe = tmp_path_factory.mktemp("planner") / "block_plan_dump"
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    subprocess.run(["g++", "-O1", "-std=c++17", os.path.join(ROOT, "tests", "block_plan_dump.cpp"),
+                    "-I", os.path.join(ROOT, "paper_2008_13490_gb300", "csrc"), "-I", os.path.join(ROOT, "include"),
+                    "-I", cuda_inc, "-o", str(exe), "-L", libdir, "-lqsim", f"-Wl,-rpath,{libdir}"],
+                   check=True, capture_output=True, text=True)
+    return exe
+
+
+def _blocks(exe, tmp_path, n, ops):
+    import paper_2008_13490_gb300 as qs
+    gin, bout = tmp_path / "g.bin", tmp_path / "b.bin"
+    qs.gates_array(ops).tofile(gin)
+    subprocess.run([str(exe), str(gin), str(n), str(bout)], check=True)
+    raw = np.fromfile(bout, dtype=np.uint8)
+    rec = 24 + 1024 * 16
+    assert raw.size % rec == 0
+    out = []
+    for k in range(raw.size // rec):
+        r = raw[k * rec:(k + 1) * rec]
+        q = r[:20].view(np.int32).tolist()
+        unitary = int(r[20:24].view(np.int32)[0])
+        U = r[24:].view(np.complex128).reshape(32, 32)
+        out.append((q, unitary, U))
+    return out
+
+
+def _apply_block(psi, n, q, U):
+    # amplitude index bit b = qubit b; local index bit i = qubit q[i]
+    t = psi.reshape([2] * n)                 # axis a <-> bit n-1-a
+    axes = [n - 1 - q[i] for i in reversed(range(5))]   # local bit 4 first (most significant)
+    t = np.moveaxis(t, axes, range(5)).reshape(32, -1)
+    t = U @ t
+    t = np.moveaxis(t.reshape([2] * n), range(5), axes)
+    return t.reshape(-1)
+
+
+@pytest.mark.parametrize("name", ["gate_mix", "diagonals", "layered", "qft"])
+def test_blocks_reproduce_the_circuit(dump_exe, tmp_path, name):
+    n = 10
+    ops = {
+        "gate_mix": lambda: W.random_gate_mix(n, 300, seed=91),
+        "diagonals": lambda: W.random_gate_mix(n, 300, seed=92, two_q_fraction=0.6,
+                                               names1=["RZ", "S", "T", "Z", "H", "U1"],
+                                               names2=["CZ", "CP", "CNOT", "SWAP"]),
+        "layered": lambda: W.layered_haar_cz(n, 12, seed=93),
+        "qft": lambda: W.qft_circuit(n),
+    }[name]()
+    blocks = _blocks(dump_exe, tmp_path, n, ops)
+    assert blocks
+    psi0 = W.random_state(n, W.rng(94))
+    ref = SV.apply_circuit(psi0.copy(), n, ops)
+    psi = psi0.copy()
+    for q, unitary, U in blocks:
+        assert sorted(q) == q and len(set(q)) == 5 and max(q) < n
+        assert unitary == 1
+        np.testing.assert_allclose(U.conj().T @ U, np.eye(32), atol=1e-12)
+        psi = _apply_block(psi, n, q, U)
+    assert np.max(np.abs(psi - ref)) < 1e-12
