@@ -1,0 +1,196 @@
+"""The host tile-pass planner on the CPU: the plan the library makes of a
+circuit (fused ops, passes with their stages, register / lane / warp / tile bit
+assignments, remaps, plain ops), executed op by op with numpy in the meaning the
+tile kernel gives each field, reproduces the oracle's state.  This pins the
+fusion (merged one-qubit runs, folded diagonals, SWAP relabelling) and the stage
+and remap bookkeeping without a GPU."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import ROOT
+from oracle import statevector as SV
+
+CS_NONE, CS_TILE, CS_LANE, CS_WARP, CS_REG = 0, 1, 2, 3, 4
+TK_REG, TK_LANE, TK_DIAG, TK_G2, TK_G2C = 0, 1, 2, 3, 4
+F_G1, F_G1C, F_D, F_G2 = 0, 1, 2, 3
+
+
+@pytest.fixture(scope="module")
+def dump_exe(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    from paper_2008_13490_gb300 import _build
+    lib = _build.build()
+    libdir = os.path.dirname(lib)
+    exe = tmp_path_factory.mktemp("tplanner") / "tile_plan_dump"
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    subprocess.run(["g++", "-O1", "-std=c++17", os.path.join(ROOT, "tests", "tile_plan_dump.cpp"),
+                    "-I", os.path.join(ROOT, "paper_2008_13490_gb300", "csrc"), "-I", os.path.join(ROOT, "include"),
+                    "-I", cuda_inc, "-o", str(exe), "-L", libdir, "-lqsim", f"-Wl,-rpath,{libdir}"],
+                   check=True, capture_output=True, text=True)
+    return exe
+
+
+def _cplx(vals, k):
+    v = np.asarray(vals[:2 * k], dtype=np.float64)
+    return v[0::2] + 1j * v[1::2], vals[2 * k:]
+
+
+def _op(vals):
+    out = {}
+    out["m0"], vals = _cplx(vals, 4)
+    out["m1"], vals = _cplx(vals, 4)
+    out["d"], vals = _cplx(vals, 4)
+    out["g"], vals = _cplx(vals, 16)
+    return out
+
+
+def _plan(exe, tmp_path, n, ops, fuse, relabel):
+    import paper_2008_13490_gb300 as qs
+    gin, out = tmp_path / "g.bin", tmp_path / "plan.txt"
+    qs.gates_array(ops).tofile(gin)
+    subprocess.run([str(exe), str(gin), str(n), str(int(fuse)), str(int(relabel)), str(out)], check=True)
+    lines = open(out).read().split("\n")
+    plan, i = {}, 0
+    for sec in ("steps", "passes", "stages", "tileops", "plainops", "remaps"):
+        head, cnt = lines[i].split()
+        assert head == sec
+        rows = [lines[i + 1 + k].split() for k in range(int(cnt))]
+        plan[sec] = rows
+        i += 1 + int(cnt)
+    return plan
+
+
+def _bits(N, p):
+    return (np.arange(N) >> p) & 1
+
+
+def _apply_1q(psi, n, t, M0, M1=None, c=None):
+    N = 1 << n
+    idx = np.arange(N)
+    i0 = idx[_bits(N, t) == 0]
+    i1 = i0 | (1 << t)
+    if c is None:
+        M = [np.full(i0.size, M0[k]) for k in range(4)]
+    else:
+        sel = ((i0 >> c) & 1).astype(bool)
+        M = [np.where(sel, M1[k], M0[k]) for k in range(4)]
+    a, b = psi[i0].copy(), psi[i1].copy()
+    psi[i0] = M[0] * a + M[1] * b
+    psi[i1] = M[2] * a + M[3] * b
+
+
+def _apply_diag(psi, n, a, b, d):
+    N = 1 << n
+    k = _bits(N, a) if b is None else 2 * _bits(N, a) + _bits(N, b)
+    psi *= np.asarray(d)[k]
+
+
+def _apply_2q(psi, n, a, b, G):
+    N = 1 << n
+    idx = np.arange(N)
+    base = idx[(_bits(N, a) == 0) & (_bits(N, b) == 0)]
+    quad = [base | (((l >> 1) & 1) << a) | ((l & 1) << b) for l in range(4)]
+    old = [psi[q].copy() for q in quad]
+    G = np.asarray(G).reshape(4, 4)
+    for o in range(4):
+        psi[quad[o]] = sum(G[o, l] * old[l] for l in range(4))
+
+
+def _remap(psi, n, pos, src):
+    N = 1 << n
+    idx = np.arange(N)
+    mask = 0
+    for p in pos:
+        mask |= 1 << p
+    new = idx & ~mask
+    for j in range(len(pos)):
+        new |= ((idx >> pos[src[j]]) & 1) << pos[j]
+    out = np.empty_like(psi)
+    out[new] = psi
+    return out
+
+
+def _execute(plan, n, psi):
+    passes = [[int(x) for x in r] for r in plan["passes"]]
+    stages = [[int(x) for x in r] for r in plan["stages"]]
+    for kind, index in ([int(x) for x in r] for r in plan["steps"]):
+        if kind == 0:
+            p = passes[index]
+            n_stages, stage_begin, n_nt = p[0], p[1], p[2]
+            pos, nt_pos = p[3:15], p[15:15 + n_nt]
+            for s in range(stage_begin, stage_begin + n_stages):
+                st = stages[s]
+                reg, warp, ob, oe = st[0:4], st[4:7], st[7], st[8]
+
+                def phys(src, bit):
+                    return {CS_TILE: lambda: nt_pos[bit], CS_LANE: lambda: pos[bit],
+                            CS_WARP: lambda: pos[warp[bit]], CS_REG: lambda: pos[reg[bit]]}[src]()
+
+                for row in plan["tileops"][ob:oe]:
+                    k, slot, csrc, cbit, dsrc, dbit, typ = (int(x) for x in row[:7])
+                    m = _op([float(x) for x in row[7:]])
+                    if k == TK_G2C:
+                        continue
+                    if k == TK_DIAG:
+                        assert typ == F_D
+                        _apply_diag(psi, n, phys(csrc, cbit), None if dsrc == CS_NONE else phys(dsrc, dbit), m["d"])
+                    elif k == TK_G2:
+                        assert typ == F_G2
+                        _apply_2q(psi, n, phys(csrc, cbit), phys(dsrc, dbit), m["g"])
+                    else:
+                        t = pos[reg[slot]] if k == TK_REG else pos[slot]
+                        if csrc == CS_NONE:
+                            assert typ == F_G1
+                            _apply_1q(psi, n, t, m["m0"])
+                        else:
+                            assert typ == F_G1C
+                            _apply_1q(psi, n, t, m["m0"], m["m1"], phys(csrc, cbit))
+        elif kind == 1:
+            row = plan["plainops"][index]
+            typ, t, c, a, b = (int(x) for x in row[:5])
+            m = _op([float(x) for x in row[5:]])
+            if typ == F_G1:
+                _apply_1q(psi, n, t, m["m0"])
+            elif typ == F_G1C:
+                _apply_1q(psi, n, t, m["m0"], m["m1"], c)
+            elif typ == F_D:
+                _apply_diag(psi, n, a, None if b < 0 else b, m["d"])
+            else:
+                _apply_2q(psi, n, a, b, m["g"])
+        elif kind == 2:
+            r = [int(x) for x in plan["remaps"][index]]
+            psi = _remap(psi, n, r[0:12], r[12:24])
+        else:
+            raise AssertionError("small-state step at n >= 12")
+    return psi
+
+
+CASES = {
+    "gate_mix": (13, lambda: W.random_gate_mix(13, 300, seed=71), True, True),
+    "gate_mix_unfused": (13, lambda: W.random_gate_mix(13, 200, seed=72), False, False),
+    "diagonals": (13, lambda: W.random_gate_mix(13, 300, seed=73, two_q_fraction=0.6,
+                                               names1=["RZ", "S", "T", "TDG", "U1", "RK", "Z", "H"],
+                                               names2=["CZ", "CP"]), True, True),
+    "layered": (14, lambda: W.layered_haar_cz(14, 10, seed=74), True, True),
+    "qft_relabel": (14, lambda: W.qft_circuit(14), True, True),
+    "swaps_dense": (13, lambda: W.random_gate_mix(13, 200, seed=75, two_q_fraction=0.5,
+                                                 names2=["SWAP", "CNOT", "CZ"]), True, False),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_tile_plan_reproduces_the_circuit(dump_exe, tmp_path, name):
+    n, make, fuse, relabel = CASES[name]
+    ops = make()
+    plan = _plan(dump_exe, tmp_path, n, ops, fuse, relabel)
+    assert plan["passes"]
+    psi0 = W.random_state(n, W.rng(76))
+    ref = SV.apply_circuit(psi0.copy(), n, ops)
+    out = _execute(plan, n, psi0.copy())
+    assert np.max(np.abs(out - ref)) < 1e-12
