@@ -101,13 +101,15 @@ typedef enum {
   QS_METHOD_TILED = 0,       /* fused shared-memory tile passes (default) */
   QS_METHOD_PLAIN = 1,       /* one kernel launch per gate (comparison baseline) */
   /* gates fused into dense 5-qubit blocks (32x32 unitaries, products of the
-   * circuit's gates), each applied as a complex GEMM on the tensor cores
-   * (tcgen05) in split precision: operands = hi + lo parts, product
-   * A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation.  complex64 states
-   * with n >= 12 only (QS_EUNSUPPORTED otherwise); synchronous (the call
-   * checks the kernels' bounded-wait status word). */
-  QS_METHOD_BLOCKS_TF32 = 2, /* TF32 hi/lo split */
-  QS_METHOD_BLOCKS_BF16 = 3  /* BF16 hi/lo split (faster operands, ~1e-5 relative per block) */
+   * circuit's gates), each applied as a real [2^(n-5) x 64] x [64 x 64] GEMM
+   * on the tensor cores (tcgen05) in split precision: each operand is the sum
+   * of its parts, the products of the parts whose order of magnitude matters
+   * are accumulated in FP32, and for a unitary block every 32-amplitude row is
+   * rescaled to its input norm.  complex64 states with n >= 12 only
+   * (QS_EUNSUPPORTED otherwise); synchronous (the call checks the kernels'
+   * bounded-wait status word). */
+  QS_METHOD_BLOCKS_TF32 = 2, /* two TF32 parts, 4 products (~1e-6 relative over 100 blocks) */
+  QS_METHOD_BLOCKS_BF16 = 3  /* three BF16 parts, 6 products (~6e-7 relative over 100 blocks) */
 } qs_method;
 
 typedef struct {
