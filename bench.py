@@ -1046,11 +1046,12 @@ def main():
               "other": lambda q, t: extra_other_method(q, t, args.method)}[args.only]
         print(json.dumps({"only": args.only, "row": fn(qs, torch)}), flush=True)
         return 0
-    world, rank, local = dist_setup()
     if args.impl == "reference":
-        rc = run_reference(args, world, rank)
-    else:
-        rc = run_ours(args, world, rank, local)
+        # the host-only arm needs no process group: rank 0 runs and prints, the
+        # other ranks exit at once
+        return run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+    world, rank, local = dist_setup()
+    rc = run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
