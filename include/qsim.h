@@ -278,6 +278,13 @@ qs_status qs_server_wait(qs_server_t s, int64_t ticket, double* result, double* 
 qs_status qs_server_stats_get(qs_server_t s, qs_server_stats* out);
 /* Waits for all submitted circuits, stops the scheduler, frees everything. */
 qs_status qs_server_destroy(qs_server_t s);
+/* Testing hook for the scheduler's error path: the next completion query of a
+ * running packed launch or large circuit reports cuda_error (a cudaError_t
+ * value other than cudaSuccess and cudaErrorNotReady) instead of asking the
+ * device.  A query that reports an error completes that work: its circuits'
+ * qs_server_wait returns QS_ECUDA with the error's name, and their slot and
+ * memory are released.  Errors: QS_EINVAL. */
+qs_status qs_server_inject_query_error(qs_server_t s, int cuda_error);
 
 /* ---- probabilities without allocation ------------------------------------
  * The thesis has no counterpart of this entry point; it exists for callers
@@ -289,8 +296,11 @@ qs_status qs_server_destroy(qs_server_t s);
  * 2^popcount(mask) marginal values, may be NULL), norm_out (HOST, may be
  * NULL; synchronises stream).  Its reduction scratch is one fixed array in
  * device global memory (about 41 KB per device, held until the process
- * exits): n <= 36 and marginals over at most 12 qubits, else QS_EINVAL.  The
- * first call on each device looks up that array's device address (make it
+ * exits): n <= 36 and marginals over at most 12 qubits, else QS_EINVAL.  Every
+ * call looks up that array's device address on the current device.  With lazy
+ * module loading (the CUDA default) the first call on each device loads the
+ * library module that holds the array, which places it in device memory: make
+ * one call per device before the regions where allocation is not allowed (and
  * before capturing the stream into a graph).  All calls share the array and
  * find the previous call's contents in it (the kernels clear what must start
  * at zero); calls that overlap on the GPU race on it. */

@@ -135,6 +135,7 @@ def load():
         "qs_server_wait": (i32, [vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double)]),
         "qs_server_stats_get": (i32, [vp, ctypes.POINTER(ServerStats)]),
         "qs_server_destroy": (i32, [vp]),
+        "qs_server_inject_query_error": (i32, [vp, i32]),
         "qs_profile_begin": (i32, []),
         "qs_profile_end": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "qs_last_error": (ctypes.c_char_p, []),
@@ -155,7 +156,7 @@ def exported_symbols():
             "dm_gst_series", "dm_gst_power", "dm_code422_eval",
             "qs_profile_begin", "qs_profile_end",
             "qs_server_create", "qs_server_submit", "qs_server_wait", "qs_server_stats_get",
-            "qs_server_destroy", "qs_last_error", "qs_version"]
+            "qs_server_destroy", "qs_server_inject_query_error", "qs_last_error", "qs_version"]
 
 
 class Server:
@@ -204,6 +205,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def server_inject_query_error(srv: Server, cuda_error: int):
+    """Testing hook: the server's next completion query reports ``cuda_error``."""
+    _check(load().qs_server_inject_query_error(srv.handle, int(cuda_error)))
 
 
 def qs_probs_noalloc(amps_ptr: int, n: int, prec: int, out=None, fp64: bool = False,

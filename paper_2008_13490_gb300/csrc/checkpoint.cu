@@ -162,6 +162,13 @@ extern "C" qs_status sv_save(qs_state_t h, const char* path) {
     set_error("write to %s failed", path);
     s = QS_EINVAL;
   }
+  // a late write error (full disk, network file system) shows up at close
+  const int closed = std::fclose(file.f);
+  file.f = nullptr;
+  if (s == QS_OK && closed != 0) {
+    set_error("closing %s failed: the checkpoint may be incomplete", path);
+    s = QS_EINVAL;
+  }
   return s;
 }
 

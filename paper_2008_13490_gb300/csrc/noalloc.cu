@@ -19,8 +19,6 @@
 // without ordering) race on it.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "internal.h"
 
 namespace qs {
@@ -36,12 +34,14 @@ constexpr int kNaDoubles = kNaMarg + (1 << kNaMaxMargBits);
 
 // The scratch array (about 41 KB).  Host code must not pass its name to a
 // kernel: on the host it is only a stand-in, so the device address is taken
-// with cudaGetSymbolAddress, once per device.
+// with cudaGetSymbolAddress on every call, for the device that is current then
+// (after a device reset the address of the reloaded module is found again).
+// With lazy module loading (CUDA_MODULE_LOADING=LAZY, the default) the driver
+// loads this file's module, and places the array in device memory, at the
+// first such lookup on each device: that first call is the one that is not
+// free of allocation, so callers make it once outside the regions where they
+// may not allocate.
 static __device__ __align__(256) double g_noalloc_scratch[kNaDoubles];
-
-constexpr int kNaMaxDevices = 64;
-std::mutex g_na_mu;
-double* g_na_ptr[kNaMaxDevices] = {};
 
 __device__ double na_block_sum(double v) {
   __shared__ double red[32];
@@ -113,24 +113,12 @@ __global__ void na_finish_kernel(double* __restrict__ scratch, int blocks, O* __
     for (int i = threadIdx.x; i < H; i += blockDim.x) marg_out[i] = (O)scratch[kNaMarg + i];
 }
 
-// Device address of the scratch array for the current device (set up on the
-// first call on each device).
+// Device address of the scratch array on the current device.
 qs_status na_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kNaMaxDevices) {
-    set_error("device index %d beyond %d", dev, kNaMaxDevices);
-    return QS_EUNSUPPORTED;
-  }
-  std::lock_guard<std::mutex> g(g_na_mu);
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_na_ptr[dev] = (double*)p;
-  }
-  *out = g_na_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+  *out = (double*)p;
   return QS_OK;
 }
 

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -315,21 +316,67 @@ struct Server {
     finish(r, QS_OK);
   }
 
+  // Event query with a testing hook: qs_server_inject_query_error makes the next
+  // query return a given error instead of asking the device.
+  std::atomic<int> injected_error{0};
+  cudaError_t query(cudaEvent_t ev) {
+    const int inj = injected_error.exchange(0);
+    if (inj != 0) return (cudaError_t)inj;
+    return cudaEventQuery(ev);
+  }
+
+  void fail_large(Req* r, cudaError_t e) {
+    cudaGetLastError();   // clears a non-sticky error
+    const qs_status st = cuda_status(e, "completion of a large circuit");
+    const std::string msg = qs_last_error();
+    cudaStreamSynchronize(streams[r->slot]);   // nothing of it may still write its buffers
+    cudaGetLastError();
+    release_large(r);
+    set_error("%s", msg.c_str());
+    finish(r, st);
+  }
+
+  void fail_batch(cudaError_t e) {
+    cudaGetLastError();
+    const qs_status st = cuda_status(e, "completion of a packed launch");
+    const std::string msg = qs_last_error();
+    cudaStreamSynchronize(small_stream);
+    cudaGetLastError();
+    for (Req* r : batch) {
+      set_error("%s", msg.c_str());
+      finish(r, st);
+    }
+    batch.clear();
+    batch_busy = false;
+  }
+
   void run() {
     cudaSetDevice(device);
     for (;;) {
       bool progress = false;
-      // 1. retire finished work
+      // 1. retire finished work; a query that reports an error (neither done nor
+      // still running) completes the work with that error
       for (size_t s = 0; s < slot_req.size(); ++s) {
         Req* r = slot_req[s];
-        if (r && cudaEventQuery(slot_ev[s]) == cudaSuccess) {
+        if (!r) continue;
+        const cudaError_t e = query(slot_ev[s]);
+        if (e == cudaSuccess) {
           finish_large(r);
+          progress = true;
+        } else if (e != cudaErrorNotReady) {
+          fail_large(r, e);
           progress = true;
         }
       }
-      if (batch_busy && cudaEventQuery(batch_ev) == cudaSuccess) {
-        finish_batch();
-        progress = true;
+      if (batch_busy) {
+        const cudaError_t e = query(batch_ev);
+        if (e == cudaSuccess) {
+          finish_batch();
+          progress = true;
+        } else if (e != cudaErrorNotReady) {
+          fail_batch(e);
+          progress = true;
+        }
       }
       // 2. admission
       std::vector<Req*> to_batch, too_big;
@@ -553,6 +600,15 @@ qs_status qs_server_stats_get(qs_server_t s, qs_server_stats* out) {
     out->wall_s = s->t_last - s->t_first;
     out->circuits_per_s = out->wall_s > 0 ? (double)s->completed / out->wall_s : 0.0;
   }
+  return QS_OK;
+}
+
+qs_status qs_server_inject_query_error(qs_server_t s, int cuda_error) {
+  if (!s || cuda_error <= 0 || cuda_error == (int)cudaErrorNotReady) {
+    set_error("server and a CUDA error code other than cudaErrorNotReady are required");
+    return QS_EINVAL;
+  }
+  s->injected_error.store(cuda_error);
   return QS_OK;
 }
 

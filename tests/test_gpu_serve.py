@@ -68,3 +68,21 @@ def test_admission_by_memory(qs):
         srv.wait(t)
     assert e.value.status == qs.QS_ENOMEM
     srv.close()
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_failed_completion_query_returns_error(qs, n):
+    # a completion query that reports an error (injected on the host: no device
+    # fault) ends that circuit's wait with QS_ECUDA (packed launch for n = 8, a
+    # resident state for n = 16); the server keeps serving afterwards
+    srv = qs.Server(max_inflight=2)
+    ops = W.layered_haar_cz(n, 4, seed=n)
+    qs.server_inject_query_error(srv, 999)   # cudaErrorUnknown
+    t = srv.submit(n, ops, _mask(n))
+    with pytest.raises(qs.QsimError) as e:
+        srv.wait(t)
+    assert e.value.status == qs.QS_ECUDA
+    res, _ = srv.wait(srv.submit(n, ops, _mask(n)))
+    np.testing.assert_allclose(res, _oracle_marginal(n, ops), atol=2e-6)
+    assert srv.stats()["completed"] == 2
+    srv.close()

@@ -52,3 +52,29 @@ def test_noalloc_rejects_sizes_beyond_its_limit(qs):
     with pytest.raises(qs.QsimError):
         qs.qs_probs_noalloc(st.device_ptr(), 37, 0, out=out)
     st.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_largest_marginal_and_optional_outputs(qs, prec):
+    # a 12-qubit marginal fills the whole shared histogram and scratch region;
+    # out=None computes only the norm; want_norm=False leaves the call asynchronous
+    n = 14
+    st = qs.State(n, prec)
+    qs.sv_apply_circuit(st, W.random_gate_mix(n, 80, seed=950 + prec))
+    tol = 1e-13 if prec else 2e-6
+    mask = 0b10111111111101          # 12 of the 14 bits
+    mref, ref_norm = qs.sv_probs(st, fp64=True, marg_mask=mask)
+    for _ in range(2):
+        out = torch.full((1 << 12,), -1.0, dtype=torch.float64, device="cuda")
+        out, norm = qs.qs_probs_noalloc(st.device_ptr(), n, prec, out=out, fp64=True, marg_mask=mask)
+        np.testing.assert_allclose(out.cpu().numpy(), mref.cpu().numpy(), atol=tol * 4)
+        assert abs(norm - ref_norm) < 1e-12
+        _, norm_only = qs.qs_probs_noalloc(st.device_ptr(), n, prec, out=None)
+        assert abs(norm_only - ref_norm) < 1e-12
+        p = torch.full((1 << n,), -1.0, dtype=torch.float32, device="cuda")
+        _, none = qs.qs_probs_noalloc(st.device_ptr(), n, prec, out=p, want_norm=False)
+        assert none is None
+        torch.cuda.current_stream().synchronize()
+        full, _ = qs.sv_probs(st, fp64=True)
+        np.testing.assert_allclose(p.double().cpu().numpy(), full.cpu().numpy(), atol=2e-6)
+    st.close()
