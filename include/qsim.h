@@ -213,7 +213,7 @@ typedef struct {
   int32_t max_ops;         /* >= every op_off[c+1]-op_off[c] (sizes gradient checkpoints) */
   int32_t n_ptm1;          /* entries in ptm1 (aux of QS_DM_PTM1 must be below) */
   int32_t n_ptm2;          /* entries in ptm2 */
-  int32_t reserved;
+  int32_t flags;           /* QS_DM_VALIDATE, or 0 */
   const int32_t* nq;       /* [C] 1..6 */
   const int64_t* op_off;   /* [C+1] rows of ops for circuit c: op_off[c]..op_off[c+1] */
   const int32_t* ops;      /* [rows*4] (code, q0, q1, aux) */
@@ -223,6 +223,18 @@ typedef struct {
   const double* ptm1;      /* user 4x4 PTMs, row-major, or NULL */
   const double* ptm2;      /* user 16x16 PTMs, row-major, or NULL */
 } qs_dm_batch;
+
+/* Opt-in check of the channels a batch describes (section "Quantum operations"):
+ * before anything is launched, every user PTM (ptm1, ptm2; gst ptms) is copied to
+ * the host and must be trace preserving -- first row (1, 0, ..., 0), the
+ * property stated after Eq. (paulitransfermatrix) -- and completely positive --
+ * its Choi matrix (Eq. (choimatrix)) positive semidefinite -- each within
+ * 1e-8; the built-in channels' parameters must have p and gamma in [0, 1] and
+ * finite angles.  A failure returns QS_EINVAL, launches nothing, and
+ * qs_last_error() names the first failing matrix (or circuit) by its index.
+ * Without the flag the inputs are used as given.  The check synchronises the
+ * stream (it reads the device arrays). */
+#define QS_DM_VALIDATE 1
 
 /* Forward (and optionally adjoint) pass of a batch.  probs (DEVICE, float,
  * out_off[C] values, may be NULL); loglik (DEVICE, double [C], may be NULL;
@@ -286,6 +298,14 @@ qs_status qs_server_destroy(qs_server_t s);
  * memory are released.  Errors: QS_EINVAL. */
 qs_status qs_server_inject_query_error(qs_server_t s, int cuda_error);
 
+/* The check of QS_DM_VALIDATE on HOST arrays: count n-qubit PTMs (n = 1 or 2,
+ * 4^n x 4^n doubles each, row-major G[out][in], the Pauli basis order of
+ * Eq. (paulibasis)).  QS_OK when every one is trace preserving and completely
+ * positive within 1e-8; otherwise QS_EINVAL, *bad_index (may be NULL) = the first
+ * failing matrix (-1 on success) and a message saying which property failed.
+ * Host only: no CUDA call. */
+qs_status qs_ptm_check(const double* ptms, int n, int count, int* bad_index);
+
 /* ---- probabilities without allocation ------------------------------------
  * The thesis has no counterpart of this entry point; it exists for callers
  * that may not allocate device memory (their own allocator owns the device,
@@ -324,6 +344,8 @@ typedef struct {
   int32_t count;          /* sequences */
   int32_t r_max;          /* dm_gst_series: repetitions 1..r_max */
   int32_t n_ptm;          /* PTMs in the table */
+  int32_t flags;          /* QS_DM_VALIDATE (checks every PTM of the table), or 0 */
+  int32_t reserved;
   const double* ptms;
   const double* rho;
   const double* effects;

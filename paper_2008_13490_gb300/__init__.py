@@ -55,6 +55,7 @@ class _Opts(ctypes.Structure):
 
 
 OPT_TIME_KERNELS = 1
+DM_VALIDATE = 1
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -68,7 +69,7 @@ class _Allocator(ctypes.Structure):
 class DMBatch(ctypes.Structure):
     _fields_ = [("n_circuits", ctypes.c_int32), ("max_qubits", ctypes.c_int32),
                 ("max_ops", ctypes.c_int32), ("n_ptm1", ctypes.c_int32),
-                ("n_ptm2", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_ptm2", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("nq", ctypes.c_void_p), ("op_off", ctypes.c_void_p), ("ops", ctypes.c_void_p),
                 ("params", ctypes.c_void_p), ("out_off", ctypes.c_void_p),
                 ("counts", ctypes.c_void_p), ("ptm1", ctypes.c_void_p), ("ptm2", ctypes.c_void_p)]
@@ -76,7 +77,8 @@ class DMBatch(ctypes.Structure):
 
 class GstBatch(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("count", ctypes.c_int32), ("r_max", ctypes.c_int32),
-                ("n_ptm", ctypes.c_int32), ("ptms", ctypes.c_void_p), ("rho", ctypes.c_void_p),
+                ("n_ptm", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ptms", ctypes.c_void_p), ("rho", ctypes.c_void_p),
                 ("effects", ctypes.c_void_p), ("gate", ctypes.c_void_p), ("prep", ctypes.c_void_p)]
 
 
@@ -123,6 +125,7 @@ def load():
         "dm_apply_channels": (i32, [ctypes.POINTER(DMBatch), vp, vp, vp, vp]),
         "qs_probs_noalloc": (i32, [vp, i32, i32, vp, i32, u64, ctypes.POINTER(ctypes.c_double), vp]),
         "sv_bloch": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "qs_ptm_check": (i32, [vp, i32, i32, ctypes.POINTER(i32)]),
         "dm_gst_series": (i32, [ctypes.POINTER(GstBatch), vp, vp]),
         "dm_code422_eval": (i32, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "dm_gst_power": (i32, [ctypes.POINTER(GstBatch), vp, vp, vp]),
@@ -152,7 +155,7 @@ def load():
 def exported_symbols():
     return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
             "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
-            "dm_apply_channels", "qs_probs_noalloc", "sv_bloch", "qs_meas_error", "sv_save", "sv_load",
+            "dm_apply_channels", "qs_ptm_check", "qs_probs_noalloc", "sv_bloch", "qs_meas_error", "sv_save", "sv_load",
             "dm_gst_series", "dm_gst_power", "dm_code422_eval",
             "qs_profile_begin", "qs_profile_end",
             "qs_server_create", "qs_server_submit", "qs_server_wait", "qs_server_stats_get",
@@ -210,6 +213,19 @@ class Server:
 def server_inject_query_error(srv: Server, cuda_error: int):
     """Testing hook: the server's next completion query reports ``cuda_error``."""
     _check(load().qs_server_inject_query_error(srv.handle, int(cuda_error)))
+
+
+def ptm_check(ptms, n: int):
+    """qs_ptm_check on host PTMs (array of shape (count, 4^n, 4^n) or (4^n, 4^n)).
+
+    Returns -1 when every matrix is trace preserving and completely positive,
+    else raises QsimError naming the first failing index."""
+    a = np.ascontiguousarray(np.asarray(ptms, dtype=np.float64))
+    D = 4 ** n
+    a = a.reshape(-1, D, D)
+    bad = ctypes.c_int()
+    _check(load().qs_ptm_check(a.ctypes.data, int(n), int(a.shape[0]), ctypes.byref(bad)))
+    return bad.value
 
 
 def qs_probs_noalloc(amps_ptr: int, n: int, prec: int, out=None, fp64: bool = False,
@@ -405,28 +421,29 @@ def sv_probs(st: State, out=None, fp64: bool = False, marg_mask: int = 0, want_n
     return out, (norm.value if want_norm else None)
 
 
-def _gst_batch(n, ptms, rho, effects, gate, prep, r_max=0):
+def _gst_batch(n, ptms, rho, effects, gate, prep, r_max=0, validate=False):
     """qs_gst_batch over device tensors: ptms (n_ptm, 4^n, 4^n) float64, rho (4^n,),
     effects (2^n, 4^n), gate (count,) int32, prep (count, 8) int32 (-1 = end)."""
-    b = GstBatch(int(n), int(gate.numel()), int(r_max), int(ptms.shape[0]), ptms.data_ptr(),
+    b = GstBatch(int(n), int(gate.numel()), int(r_max), int(ptms.shape[0]),
+                 DM_VALIDATE if validate else 0, 0, ptms.data_ptr(),
                  rho.data_ptr(), effects.data_ptr(), gate.data_ptr(), prep.data_ptr())
     return b
 
 
-def gst_series(n, ptms, rho, effects, gate, prep, r_max, out=None, stream=None):
+def gst_series(n, ptms, rho, effects, gate, prep, r_max, out=None, stream=None, validate=False):
     """p_J(r) = <<E_J| G_s^r G_prep |rho>> for r = 1..r_max: (count, r_max, 2^n) float32."""
     torch = _torch()
-    b = _gst_batch(n, ptms, rho, effects, gate, prep, r_max)
+    b = _gst_batch(n, ptms, rho, effects, gate, prep, r_max, validate)
     if out is None:
         out = torch.empty((b.count, r_max, 1 << n), dtype=torch.float32, device="cuda")
     _check(load().dm_gst_series(ctypes.byref(b), out.data_ptr(), _stream_ptr(stream)))
     return out
 
 
-def gst_power(n, ptms, rho, effects, gate, prep, reps, out=None, stream=None):
+def gst_power(n, ptms, rho, effects, gate, prep, reps, out=None, stream=None, validate=False):
     """p_J = <<E_J| G_s^reps G_prep |rho>> by repeated squaring: (count, 2^n) float64."""
     torch = _torch()
-    b = _gst_batch(n, ptms, rho, effects, gate, prep)
+    b = _gst_batch(n, ptms, rho, effects, gate, prep, validate=validate)
     if out is None:
         out = torch.empty((b.count, 1 << n), dtype=torch.float64, device="cuda")
     _check(load().dm_gst_power(ctypes.byref(b), reps.data_ptr(), out.data_ptr(), _stream_ptr(stream)))
@@ -505,7 +522,8 @@ def sv_grad(st: State, gates, weights, mode: int = 0, checkpoint_every: int = 0)
 
 # ---------------------------------------------------------------- density matrices
 def dm_apply_channels(nq, op_off, ops, params, out_off, counts=None, ptm1=None, ptm2=None,
-                      probs=None, loglik=None, grad=None, max_qubits=6, max_ops=None, stream=None):
+                      probs=None, loglik=None, grad=None, max_qubits=6, max_ops=None, stream=None,
+                      validate=False):
     """All arrays are torch device tensors (see qs_dm_batch in include/qsim.h).
 
     ops: int32 [rows, 4] (code, q0, q1, aux).  max_ops defaults to the longest
@@ -519,6 +537,7 @@ def dm_apply_channels(nq, op_off, ops, params, out_off, counts=None, ptm1=None, 
     b.max_ops = int(max_ops)
     b.n_ptm1 = int(ptm1.shape[0]) if ptm1 is not None else 0
     b.n_ptm2 = int(ptm2.shape[0]) if ptm2 is not None else 0
+    b.flags = DM_VALIDATE if validate else 0
     ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
     b.nq, b.op_off, b.ops, b.params, b.out_off = (ptr(nq), ptr(op_off), ptr(ops), ptr(params),
                                                    ptr(out_off))

@@ -27,6 +27,9 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <vector>
+
+#include <cmath>
 #include <mutex>
 
 #include "internal.h"
@@ -758,6 +761,36 @@ void cz_table(int8_t* dst, int8_t* sgn) {
 
 }  // namespace
 
+// QS_DM_VALIDATE: the user PTMs must be channels (trace preserving and completely
+// positive), the built-in channels' parameters in range (p, gamma in [0, 1],
+// finite angles); the device arrays are read on the host first.
+qs_status dm_validate_batch(const qs_dm_batch* b, cudaStream_t stream) {
+  if (b->n_ptm1 < 0 || b->n_ptm2 < 0 || (b->n_ptm1 > 0 && !b->ptm1) || (b->n_ptm2 > 0 && !b->ptm2)) {
+    set_error("PTM tables: counts %d, %d with %s", b->n_ptm1, b->n_ptm2, "a missing array");
+    return QS_EINVAL;
+  }
+  std::vector<double> h1((size_t)b->n_ptm1 * 16), h2((size_t)b->n_ptm2 * 256), par((size_t)b->n_circuits * 4);
+  if (!h1.empty())
+    QS_CUDA(cudaMemcpyAsync(h1.data(), b->ptm1, h1.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  if (!h2.empty())
+    QS_CUDA(cudaMemcpyAsync(h2.data(), b->ptm2, h2.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  QS_CUDA(cudaMemcpyAsync(par.data(), b->params, par.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  QS_CUDA(cudaStreamSynchronize(stream));
+  qs_status s = ptm_validate(h1.data(), 1, b->n_ptm1, "ptm1", nullptr);
+  if (s == QS_OK) s = ptm_validate(h2.data(), 2, b->n_ptm2, "ptm2", nullptr);
+  if (s != QS_OK) return s;
+  for (int c = 0; c < b->n_circuits; ++c) {
+    const double* q = par.data() + 4 * (size_t)c;
+    if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !(q[2] >= 0.0 && q[2] <= 1.0) ||
+        !(q[3] >= 0.0 && q[3] <= 1.0)) {
+      set_error("circuit %d: parameters (theta_x %g, theta_y %g, p %g, gamma %g) do not give channels "
+                "(p and gamma must lie in [0, 1])", c, q[0], q[1], q[2], q[3]);
+      return QS_EINVAL;
+    }
+  }
+  return QS_OK;
+}
+
 }  // namespace qs
 
 using namespace qs;
@@ -781,8 +814,16 @@ extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, doubl
     set_error("loglik / grad need counts");
     return QS_EINVAL;
   }
+  if (b->flags & ~QS_DM_VALIDATE) {
+    set_error("unknown batch flags 0x%x", b->flags);
+    return QS_EINVAL;
+  }
   if (b->n_circuits == 0) return QS_OK;
   cudaStream_t stream = (cudaStream_t)stream_;
+  if (b->flags & QS_DM_VALIDATE) {
+    const qs_status vs = dm_validate_batch(b, stream);
+    if (vs != QS_OK) return vs;
+  }
   DmArgs A{};
   A.n_circuits = b->n_circuits;
   A.max_q = b->max_qubits;

@@ -12,6 +12,8 @@
 //                     one CTA per sequence, thread (i, k) forming entry (i, k).
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "internal.h"
 
 namespace qs {
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(256) gst_power_kernel(GstArgs A, const int64_t
   }
 }
 
-qs_status gst_args(const qs_gst_batch* b, GstArgs* A) {
+qs_status gst_args(const qs_gst_batch* b, GstArgs* A, cudaStream_t stream) {
   if (!b) {
     set_error("batch is NULL");
     return QS_EINVAL;
@@ -177,6 +179,18 @@ qs_status gst_args(const qs_gst_batch* b, GstArgs* A) {
   if (!b->ptms || !b->rho || !b->effects || (b->count > 0 && (!b->gate || !b->prep))) {
     set_error("GST batch arrays missing");
     return QS_EINVAL;
+  }
+  if (b->flags & ~QS_DM_VALIDATE) {
+    set_error("unknown GST batch flags 0x%x", b->flags);
+    return QS_EINVAL;
+  }
+  if (b->flags & QS_DM_VALIDATE) {   // every PTM of the table must be a channel
+    const size_t D = (size_t)1 << (2 * b->n);
+    std::vector<double> h((size_t)b->n_ptm * D * D);
+    QS_CUDA(cudaMemcpyAsync(h.data(), b->ptms, h.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    QS_CUDA(cudaStreamSynchronize(stream));
+    const qs_status s = ptm_validate(h.data(), b->n, b->n_ptm, "ptms", nullptr);
+    if (s != QS_OK) return s;
   }
   A->n = b->n;
   A->D = 1 << (2 * b->n);
@@ -198,7 +212,7 @@ using namespace qs;
 
 extern "C" qs_status dm_gst_series(const qs_gst_batch* b, float* probs, void* stream) {
   GstArgs A;
-  qs_status s = gst_args(b, &A);
+  qs_status s = gst_args(b, &A, (cudaStream_t)stream);
   if (s != QS_OK) return s;
   if (A.r_max < 1 || !probs) {
     set_error("GST series needs r_max >= 1 and an output");
@@ -213,7 +227,7 @@ extern "C" qs_status dm_gst_series(const qs_gst_batch* b, float* probs, void* st
 
 extern "C" qs_status dm_gst_power(const qs_gst_batch* b, const int64_t* reps, double* probs, void* stream) {
   GstArgs A;
-  qs_status s = gst_args(b, &A);
+  qs_status s = gst_args(b, &A, (cudaStream_t)stream);
   if (s != QS_OK) return s;
   if (!reps || !probs) {
     set_error("GST power needs reps and an output");

@@ -244,6 +244,16 @@ size_t block_b_bytes(int mode);
 qs_status launch_block_pass(State* st, const BlockPass& host_pass, const void* pass_dev,
                             const void* b_dev, int mode, int* status_dev);
 
+// ---------------------------------------------------------------- PTM checks (ptm_check.cpp)
+// Tolerance of the opt-in channel checks: |G_0j - delta_0j| and the most negative
+// Choi eigenvalue allowed.
+constexpr double kPtmTol = 1e-8;
+double ptm_tp_deviation(const double* G, int n);
+double ptm_choi_min_eigenvalue(const double* G, int n);
+// Host arrays of count n-qubit PTMs (4^n x 4^n, row-major): QS_EINVAL naming the
+// first matrix that is not trace preserving or not completely positive.
+qs_status ptm_validate(const double* ptms, int n, int count, const char* what, int* bad_index);
+
 // Applies gates to a state (the body of sv_apply_circuit; api.cpp).
 qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats,
                       int flags = 0);

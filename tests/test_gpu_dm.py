@@ -166,3 +166,107 @@ def test_full_batch_4096_properties(qs):
         n, ops, params = batch.circuit(int(c))
         np.testing.assert_allclose(p[batch.cnt_off[c]:batch.cnt_off[c + 1]],
                                    NZ.circuit_probabilities(n, ops, params), atol=2e-5)
+
+
+def test_long_circuits_five_and_six_qubits_vs_oracle(qs):
+    # the largest registers at full length (L = 200..256): every outcome against the
+    # Kraus-map oracle, within the fp32 bound L * u ~ 1.5e-5 of the docstring
+    batch = W.noisy_batch(count=12, seed=4301, n_range=(5, 6), len_range=(200, 256))
+    dev = qs.NoisyBatchDevice(batch, counts=False)
+    p, _, _ = dev.run(loglik=False)
+    p = p.cpu().numpy()
+    assert set(int(x) for x in batch.nq) == {5, 6}
+    for c in range(batch.size):
+        n, ops, params = batch.circuit(c)
+        assert len(ops) >= 200
+        ref = NZ.circuit_probabilities(n, ops, params)
+        np.testing.assert_allclose(p[batch.cnt_off[c]:batch.cnt_off[c + 1]], ref, atol=2e-5)
+
+
+def _gradient_bound(n, ops, params, counts, h=1e-6):
+    """Error bound of the fp32 gradient from its arithmetic.
+
+    g_k = sum_J n_J (d p_J / d t_k) / p_J.  The fp32 Pauli-vector sweeps leave an
+    absolute error of at most eps = L u (u = 2^-24, L ops) on each p_J and on each
+    d p_J / d t_k, so to first order
+        |g_k - g_k,exact| <= eps sum_J n_J (1 + |d p_J / d t_k| / p_J) / p_J.
+    The derivatives come from central differences of the oracle's probabilities."""
+    eps = len(ops) * 2.0 ** -24
+    p0 = NZ.circuit_probabilities(n, ops, params)
+    bound = np.zeros(4)
+    m = counts > 0
+    for k in range(4):
+        pp = np.array(params, dtype=np.float64)
+        pm = pp.copy()
+        pp[k] += h
+        pm[k] -= h
+        dp = (NZ.circuit_probabilities(n, ops, pp) - NZ.circuit_probabilities(n, ops, pm)) / (2 * h)
+        bound[k] = eps * np.sum(counts[m] * (1 + np.abs(dp[m]) / p0[m]) / p0[m])
+    return bound
+
+
+def test_gradient_within_derived_bound_large_registers(qs):
+    # n = 5..6 and L = 200..256 (checkpointed sweeps): the gradient against the
+    # oracle's adjoint within the first-order bound of its fp32 arithmetic
+    batch = W.noisy_batch(count=4, seed=4401, n_range=(5, 6), len_range=(200, 256))
+    batch, _ = _with_counts(batch, 4402)
+    dev = qs.NoisyBatchDevice(batch)
+    _, ll, g = dev.run(grad=True)
+    g = g.cpu().numpy()
+    ll = ll.cpu().numpy()
+    for c in range(batch.size):
+        n, ops, params = batch.circuit(c)
+        cnt = batch.counts[batch.cnt_off[c]:batch.cnt_off[c + 1]]
+        L, _, ref = NZ.grad_adjoint(n, ops, params, cnt)
+        bound = _gradient_bound(n, ops, params, cnt)
+        assert np.all(np.abs(g[c] - ref) <= bound), (c, g[c], ref, bound)
+        assert ll[c] == pytest.approx(L, rel=1e-4)
+
+
+def test_gradient_within_derived_bound_small_registers(qs):
+    batch = W.noisy_batch(count=16, seed=4111, n_range=(1, 4), len_range=(1, 120))
+    batch, _ = _with_counts(batch, 4112)
+    dev = qs.NoisyBatchDevice(batch)
+    _, _, g = dev.run(grad=True)
+    g = g.cpu().numpy()
+    for c in range(batch.size):
+        n, ops, params = batch.circuit(c)
+        cnt = batch.counts[batch.cnt_off[c]:batch.cnt_off[c + 1]]
+        _, _, ref = NZ.grad_adjoint(n, ops, params, cnt)
+        bound = _gradient_bound(n, ops, params, cnt)
+        assert np.all(np.abs(g[c] - ref) <= bound), (c, g[c], ref, bound)
+
+
+def test_validate_flag(qs):
+    # QS_DM_VALIDATE: user PTMs must be channels and p, gamma in [0, 1]; a failure
+    # names the index and launches nothing (the output buffer keeps its fill value)
+    n = 2
+    good1 = D.ptm_unitary(G.matrix("H"))
+    good2 = D.ptm_unitary(G.CNOT)
+    T = D.ptm_of_map(lambda P: P.T, 1)
+    ops = torch.tensor(np.array([[4, 0, 0, 0], [5, 1, 0, 0], [4, 1, 0, 1]], dtype=np.int32), device="cuda")
+    nq = torch.tensor([n], dtype=torch.int32, device="cuda")
+    op_off = torch.tensor([0, 3], dtype=torch.int64, device="cuda")
+    out_off = torch.tensor([0, 1 << n], dtype=torch.int64, device="cuda")
+    params = torch.tensor([[1.0, 1.0, 1e-3, 1e-3]], dtype=torch.float64, device="cuda")
+    t = lambda a: torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
+
+    def run(ptm1, par, validate):
+        probs = torch.full((1 << n,), -7.0, dtype=torch.float32, device="cuda")
+        qs.dm_apply_channels(nq, op_off, ops, par, out_off, ptm1=t(ptm1), ptm2=t(good2.reshape(1, 256)),
+                             probs=probs, max_qubits=n, validate=validate)
+        return probs.cpu().numpy()
+
+    ok = np.stack([good1, good1]).reshape(2, 16)
+    np.testing.assert_array_equal(run(ok, params, True), run(ok, params, False))
+    bad = np.stack([good1, T]).reshape(2, 16)
+    with pytest.raises(qs.QsimError) as e:
+        run(bad, params, True)
+    assert e.value.status == qs.QS_EINVAL and "ptm1 1" in str(e.value)
+    assert "completely positive" in str(e.value)
+    assert np.all(run(bad, params, False) != -7.0)           # unchecked: used as given
+    bad_p = params.clone()
+    bad_p[0, 2] = 1.5
+    with pytest.raises(qs.QsimError) as e:
+        run(ok, bad_p, True)
+    assert "circuit 0" in str(e.value)

@@ -140,3 +140,25 @@ def test_bad_indices_and_arguments(qs):
     with pytest.raises(qs.QsimError) as e:
         qs.gst_series(2, *dev, r_max=0)
     assert e.value.status == qs.QS_EINVAL
+
+
+def test_validate_flag_rejects_non_channels(qs):
+    # QS_DM_VALIDATE: a table that holds a non-channel is refused before any launch,
+    # with the failing index named; the same table with only channels runs unchanged
+    ptms, rho, E, gate, prep = _batch(1, 1600)
+    dev = _dev(qs, ptms, rho, E, gate, prep)
+    plain = qs.gst_series(2, *dev, r_max=20).cpu().numpy()
+    checked = qs.gst_series(2, *dev, r_max=20, validate=True).cpu().numpy()
+    np.testing.assert_array_equal(plain, checked)
+    T2 = D.ptm_of_map(lambda P: P.T, 2)                        # positive, not completely positive
+    m0 = D.amplitude_damping_kraus(1.0, 0.3)[0]
+    lossy = np.kron(D.ptm_kraus([m0]), np.eye(4))              # trace decreasing on one qubit
+    for bad, word in ((T2, "completely positive"), (lossy, "trace preserving")):
+        table = list(ptms) + [bad]
+        devb = _dev(qs, table, rho, E, gate, prep)
+        with pytest.raises(qs.QsimError) as e:
+            qs.gst_power(2, *devb, torch.ones(len(gate), dtype=torch.int64, device="cuda"),
+                         validate=True)
+        assert e.value.status == qs.QS_EINVAL and f"ptms {len(ptms)}" in str(e.value)
+        assert word in str(e.value)
+        qs.gst_series(2, *devb, r_max=2)                          # unchecked: accepted as given
