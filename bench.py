@@ -10,19 +10,22 @@ blocks applied on the tcgen05 tensor cores (BF16 three-part split, FP32
 accumulation; --method selects another), the tiled FP32 SIMT path reported as
 a row of the same line.
 
-metric: "gate-passes/sec" = gates applied to the full 2^30-amplitude state per
-second (one gate pass is the work the per-gate method does in one HBM sweep).
+metric (BASELINE's): reported in "gates/s" = gates of the circuit applied to the
+full 2^30-amplitude state per second (the real HBM sweeps per second are in
+hbm.sweeps_per_s: fused methods apply many gates per sweep).
 The JSON line also carries the real HBM sweeps and bytes, the roofline of the
-dominant kernel (block passes: HBM-bound; tile passes: FP32-ALU bound), the
-CPU oracle baseline, the end-to-end number through the public API with host
-buffers, launch counts and the SM clocks sampled during the timed region.
+dominant kernel (block passes: HBM-bound; tile passes: FP32-ALU bound against
+the FP32 peak measured in the same run), the CPU oracle baseline, the
+end-to-end number through the public C ABI with host buffers (gates from a host
+array, probabilities into a pinned host buffer through sv_probs_host), launch
+counts and the SM clocks sampled during the timed region.
 
 Multi-GPU: replicas only (each rank simulates its own copy of the workload;
 there is no exchange), value = all ranks' gates / max rank time.
 
---impl reference times the FP64 CPU oracle (numpy, single BLAS thread) on a
-bounded sample of the same workload (the first gates of the circuit at 24
-qubits, scaled by the state size to 30 qubits).
+--impl reference times the FP64 C oracle (oracle/sv_ref.c, OpenMP on all host
+cores) on the same workload at full size: each step applies the next
+CPU_STEP_GATES gates of the 30-qubit circuit to a resident complex128 state.
 """
 from __future__ import annotations
 
@@ -39,12 +42,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "gate-passes/sec & HBM GB/s (% of peak) at 30 qubits; circuits/sec, p50/p99 served"
-UNIT = "gate-passes/s"
+UNIT = "gates/s"
 N_QUBITS = 30
 LAYERS = 40
 SEED = 2001
-SAMPLE_N = 24          # CPU sample size
-SAMPLE_GATES = 10      # gates per CPU sample
+CPU_STEP_GATES = 15    # gates per step of the CPU oracle at 30 qubits
 
 
 def measured_peaks():
@@ -55,9 +57,40 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops x clock
-def fp32_peak_tflops(mhz):
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+_PEAKS = {}
+
+
+def alu_peaks(qs, torch):
+    """Arithmetic peaks measured on this GPU in this run (cached): FP32 and FP64 FMA
+    (the library's qs_alu_peak microbenchmark: every SM full of independent FMA
+    chains, CUDA events) and TF32 tensor (cuBLAS TF32 GEMM 8192^3 through torch,
+    best of 10, CUDA events), with the SM count read from the device."""
+    if _PEAKS:
+        return _PEAKS
+    f32 = qs.alu_peak(0)
+    f64 = qs.alu_peak(1)
+    n = 8192
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    torch.matmul(a, b)
+    best = 1e30
+    for _ in range(10):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del a, b
+    _PEAKS.update({"fp32_tflops": f32["tflops"], "fp64_tflops": f64["tflops"],
+                   "tf32_tflops": 2.0 * n ** 3 / (best * 1e-3) / 1e12, "sm_count": f32["sm_count"],
+                   "how": "FP32/FP64: qs_alu_peak (8 independent FMA chains per thread, 2048 threads "
+                          "per SM, best of 3 launches); TF32: cuBLAS TF32 GEMM 8192^3, best of 10"})
+    return _PEAKS
 
 
 METHOD_NOTE = {
@@ -195,65 +228,189 @@ def max_over_ranks(world, x):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_sample_seconds(n=SAMPLE_N, gates=SAMPLE_GATES):
-    """Times the oracle on the first `gates` gates of the workload at n qubits in a
-    child process pinned to one BLAS thread.  Returns seconds per gate."""
-    code = (
-        "import sys,time; sys.path.insert(0, %r)\n"
-        "import workloads as W\n"
-        "from oracle import statevector as SV\n"
-        "n=%d; ops=W.layered_haar_cz(n, 1, seed=%d)[:%d]\n"
-        "psi=SV.basis(n)\n"
-        "psi=SV.apply_gate(psi,n,ops[0])\n"
-        "t=time.perf_counter()\n"
-        "for op in ops: psi=SV.apply_gate(psi,n,op)\n"
-        "print((time.perf_counter()-t)/len(ops))\n" % (ROOT, n, SEED, gates))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         timeout=600)
+# The FP64 oracle in plain C (oracle/sv_ref.c) with OpenMP on all host cores, in a
+# child process (its threads never share the GPU process).  Modes:
+#   steps K k   the 30-qubit workload at full size: a resident complex128 state
+#               (16 GiB) from |0..0>, each step applies the next k gates of the
+#               circuit; prints the seconds of every step
+#   full24      the same circuit family at 24 qubits, all 1420 gates, once
+#   small10     the 10-qubit complex128 circuit (20 layers Haar + CNOT matching)
+#               and its 1024 probabilities, repeated: seconds per circuit
+_CPU_CHILD = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import workloads as W
+from oracle import cstate as C
+from oracle import gates as G
+mode = sys.argv[2]
+out = {"threads": C.threads()}
+if mode == "steps":
+    K, k, n = int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5])
+    ops = W.layered_haar_cz(n, %(layers)d, seed=%(seed)d)
+    mats = [G.matrix(name, params, mat) for name, _, params, mat in ops]
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1.0
+    times, g = [], 0
+    for _ in range(K):
+        t = time.perf_counter()
+        for _ in range(k):
+            C.apply_matrix(psi, n, mats[g %% len(ops)], ops[g %% len(ops)][1])
+            g += 1
+        times.append(time.perf_counter() - t)
+    out["step_s"] = times
+    out["norm"] = float(C.probabilities(psi, n)[1])
+elif mode == "full24":
+    n = 24
+    ops = W.layered_haar_cz(n, %(layers)d, seed=%(seed)d)
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1.0
+    t = time.perf_counter()
+    for name, qubits, params, mat in ops:
+        C.apply_matrix(psi, n, G.matrix(name, params, mat), qubits)
+    C.probabilities(psi, n)
+    out["s"] = time.perf_counter() - t
+    out["gates"] = len(ops)
+else:
+    n, reps = 10, 200
+    ops = W.layered_haar_cnot(n, 20, seed=1001)
+    mats = [G.matrix(name, params, mat) for name, _, params, mat in ops]
+    t = time.perf_counter()
+    for _ in range(reps):
+        psi = np.zeros(1 << n, dtype=np.complex128)
+        psi[0] = 1.0
+        for (_, qubits, _, _), m in zip(ops, mats):
+            C.apply_matrix(psi, n, m, qubits)
+        C.probabilities(psi, n)
+    out["s_per_circuit"] = (time.perf_counter() - t) / reps
+print(json.dumps(out))
+""" % {"layers": LAYERS, "seed": SEED}
+
+
+def cpu_oracle(mode, *args, timeout=900):
+    """Runs the C oracle child (OMP threads = the host's cores) and returns its JSON."""
+    from oracle import cstate
+    cstate.build()
+    env = dict(os.environ, OMP_NUM_THREADS=str(os.cpu_count() or 1))
+    out = subprocess.run([sys.executable, "-c", _CPU_CHILD, ROOT, mode, *map(str, args)],
+                         capture_output=True, text=True, env=env, timeout=timeout)
     if out.returncode != 0:
-        raise RuntimeError(out.stderr)
-    return float(out.stdout.strip().splitlines()[-1])
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_block():
-    per_gate = cpu_sample_seconds()
-    scaled = per_gate * (1 << (N_QUBITS - SAMPLE_N))
-    return {"value": 1.0 / scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, {SAMPLE_GATES} gates of the workload at {SAMPLE_N} qubits "
-                      f"({per_gate:.3f} s/gate), scaled by 2^{N_QUBITS - SAMPLE_N} to {N_QUBITS} qubits"}
+def cpu_baseline_block(steps=3):
+    """The C oracle on all host cores: the 30-qubit workload at full size on a bounded
+    sample (`steps` x CPU_STEP_GATES gates in circuit order, gates/s), the whole
+    24-qubit circuit of the same family, and the 10-qubit circuits in full."""
+    r = cpu_oracle("steps", steps, CPU_STEP_GATES, N_QUBITS)
+    timed = r["step_s"][1:] if steps > 1 else r["step_s"]      # the first step touches the state
+    gps = CPU_STEP_GATES * len(timed) / sum(timed)
+    f24 = cpu_oracle("full24")
+    s10 = cpu_oracle("small10")
+    return {"value": gps, "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+            "sample": f"FP64 C oracle (OpenMP, {r['threads']} threads) on the {N_QUBITS}-qubit workload "
+                      f"at full size (complex128, 16 GiB host state): {len(timed)} timed steps of "
+                      f"{CPU_STEP_GATES} gates in circuit order after one untimed step",
+            "full_24_qubit_circuit": {"gates": f24["gates"], "s": f24["s"],
+                                      "gates_per_s": f24["gates"] / f24["s"]},
+            "small_10_qubit_circuit_us": s10["s_per_circuit"] * 1e6}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    times = []
-    for i in range(args.warmup + args.steps):
-        t = cpu_sample_seconds(gates=3)
-        if i >= args.warmup:
-            times.append(t)
-    per_gate = statistics.mean(times) * (1 << (N_QUBITS - SAMPLE_N))
-    value = 1.0 / per_gate
     import workloads as W
+    r = cpu_oracle("steps", args.warmup + args.steps, CPU_STEP_GATES, N_QUBITS,
+                   timeout=3600)
+    timed = r["step_s"][args.warmup:]
+    value = CPU_STEP_GATES * len(timed) / sum(timed)
     gates = len(W.layered_haar_cz(N_QUBITS, LAYERS, seed=SEED))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per_gate * gates * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * sum(timed) / len(timed), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(N_QUBITS, gates), "n_qubits": N_QUBITS,
                        "precision": "complex128 (FP64 oracle)", "gates": gates,
-                       "method": "FP64 numpy oracle on the host (per-gate tensordot)",
-                       "sample_qubits": SAMPLE_N},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: 3 gates of the workload at {SAMPLE_N} qubits, "
-                                       f"scaled by 2^{N_QUBITS - SAMPLE_N}"},
+                       "method": "FP64 C oracle on the host, OpenMP over amplitude pairs / quads",
+                       "step": f"the next {CPU_STEP_GATES} gates of the circuit applied to the resident "
+                               f"{N_QUBITS}-qubit state"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+                             "sample": f"each step: {CPU_STEP_GATES} gates of the {N_QUBITS}-qubit "
+                                       f"workload in circuit order at full size; {args.warmup} untimed "
+                                       f"steps first"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+# ---------------------------------------------------------------- noisy-batch inputs
+# Counts of the noisy batch: 1000-shot multinomial draws from the oracle's
+# probabilities at the batch's true parameters (seed 4001); the library evaluates
+# the likelihood and gradient at perturbed parameters (seed 4002).  The oracle runs
+# in a pool of spawned processes, one per host core, before the GPU is touched.
+NOISY = {"count": 4096, "seed": 4001, "perturb_seed": 4002, "shots": 1000}
+
+
+_NOISY_BATCH = []
+
+
+def _noisy_chunk(idx):
+    import time as _t
+
+    import workloads as W
+    from oracle import noisy as NZ
+    if not _NOISY_BATCH:                     # built once per worker process
+        _NOISY_BATCH.append(W.noisy_batch(count=NOISY["count"], seed=NOISY["seed"]))
+    b = _NOISY_BATCH[0]
+    out = []
+    t0 = _t.perf_counter()
+    for c in idx:
+        n, ops, params = b.circuit(int(c))
+        out.append(NZ.circuit_probabilities(n, ops, params))
+    return list(idx), out, _t.perf_counter() - t0
+
+
+def noisy_oracle_inputs():
+    import multiprocessing as mp
+
+    import numpy as np
+
+    import workloads as W
+    b = W.noisy_batch(count=NOISY["count"], seed=NOISY["seed"])
+    workers = os.cpu_count() or 1
+    # longest circuits first, dealt round-robin so the chunks cost about the same
+    cost = np.array([(np.diff(b.op_off)[c] + 1) * 4.0 ** b.nq[c] for c in range(b.size)])
+    order = np.argsort(-cost)
+    chunks = [order[i::4 * workers] for i in range(4 * workers)]
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    t0 = time.perf_counter()
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.map(_noisy_chunk, chunks)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    wall = time.perf_counter() - t0
+    probs = [None] * b.size
+    cpu_s = 0.0
+    for idx, ps, dt in res:
+        cpu_s += dt
+        for c, p in zip(idx, ps):
+            probs[c] = p
+    counts = W.multinomial_counts(probs, NOISY["shots"], seed=NOISY["seed"])
+    return {"counts": counts, "params": W.perturbed_params(b, NOISY["perturb_seed"]),
+            "oracle_forward": {"wall_s": wall, "cpu_s": cpu_s, "workers": workers,
+                               "circuits_per_s": b.size / wall}}
+
+
 # ---------------------------------------------------------------- GPU arm
-def run_ours(args, world, rank, local):
+def run_ours(args, world, rank, local, noisy_inputs=None):
     import numpy as np
     import torch
 
@@ -304,19 +461,19 @@ def run_ours(args, world, rank, local):
     ms_max = max_over_ranks(world, ms)
     ms_per_step = ms_max / args.steps
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the C ABI with host buffers: the gate array from host
+    # memory (planner + descriptor upload inside sv_apply_circuit), the probabilities
+    # into a pinned host buffer (sv_probs_host), the same number of steps as `value`
     host_probs = torch.empty(1 << n, dtype=torch.float32, pin_memory=True)
-    e2e_steps = max(2, min(args.steps, 3))
+    qs.sv_probs_host(st, out=host_probs)               # warm the device buffer of the copy
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(args.steps):
         qs.sv_set_basis(st, 0)
-        s2 = qs.sv_apply_circuit(st, arr, method)         # host gate array -> planner -> H2D
-        qs.sv_probs(st, out=probs, want_norm=False)
-        host_probs.copy_(probs, non_blocking=True)         # D2H of the result
-        torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+        s2 = qs.sv_apply_circuit(st, arr, method)
+        qs.sv_probs_host(st, out=host_probs)
+    e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_s = max_over_ranks(world, e2e_s)
 
     if rank != 0:
@@ -324,6 +481,7 @@ def run_ours(args, world, rank, local):
         return 0
 
     peaks, peak_src = measured_peaks()
+    alu = alu_peaks(qs, torch)
     bytes_per_pass = 2 * (1 << n) * 8
     dominant = max(kms, key=lambda k: kms[k])
     avg_ms = kms[dominant] / max(1, kcnt[dominant])
@@ -332,8 +490,8 @@ def run_ours(args, world, rank, local):
         # tile pass: FP32-ALU bound; flops counted per amplitude per fused op
         per_launch = stats["tile_flops"] / max(1, stats["tile_launches"])
         roof = {"bound": "alu", "kernel": "tile_pass_kernel<float>", "unit": "TFLOP/s",
-                "peak": fp32_peak_tflops(2070.0),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
+                "peak": alu["fp32_tflops"],
+                "peak_source": "FP32 FMA peak measured in this run (qs_alu_peak)"}
     elif dominant == "block":
         # block GEMM: one HBM sweep per launch (its roof; the tensor work, 4 (TF32) or
         # 6 (BF16) split products of 2^(n+8) flops, is far below the tensor peak)
@@ -342,7 +500,9 @@ def run_ours(args, world, rank, local):
         roof = {"bound": "hbm", "kernel": "block_pipe_kernel<%s>" % ("TF32" if tf32 else "BF16"),
                 "unit": "GB/s", "peak": peaks["hbm_gbs"], "peak_source": "measured copy bandwidth",
                 "tensor_tflops": block_products(tf32) * 2.0 ** (n + 8) / (avg_ms * 1e-3) / 1e12,
-                "tensor_peak_tflops": peaks["bf16_tflops"] / (2 if tf32 else 1)}
+                "tensor_peak_tflops": alu["tf32_tflops"] if tf32 else peaks["bf16_tflops"],
+                "tensor_peak_source": "TF32: cuBLAS GEMM measured in this run" if tf32
+                else "bf16 burst, MEASURED_PEAKS.json"}
     else:
         per_launch = bytes_per_pass * 1e-12 * 1e12
         roof = {"bound": "hbm", "kernel": dominant, "unit": "GB/s", "peak": peaks["hbm_gbs"],
@@ -370,12 +530,15 @@ def run_ours(args, world, rank, local):
                          traffic=traffic,
                          avg_launch_ms=avg_ms, work_per_launch=per_launch),
         "e2e": {"value": world * gates / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": int(s2["upload_bytes"]) + gates * arr.itemsize,
-                "d2h_bytes_per_step": (1 << n) * 4},
+                "h2d_bytes_per_step": int(s2["upload_bytes"]),
+                "d2h_bytes_per_step": (1 << n) * 4, "steps": args.steps,
+                "path": "sv_apply_circuit (host gate array, planner, descriptor upload) + "
+                        "sv_probs_host (4 GiB of probabilities into pinned host memory)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "norm": norm,
         "peaks_source": peak_src,
+        "measured_alu_peaks": alu,
     }
     st.close()
     del probs, host_probs
@@ -390,7 +553,7 @@ def run_ours(args, world, rank, local):
                         "sv_grad": extra_sv_grad(qs, torch),
                         "fp64": extra_fp64(qs, torch),
                         "small_circuits": extra_small_circuits(qs, torch),
-                        "noisy_batch": extra_noisy_batch(qs, torch),
+                        "noisy_batch": extra_noisy_batch(qs, torch, noisy_inputs),
                         "serving": extra_serving(qs, torch),
                         "fused_blocks": extra_fused_blocks(qs, torch)}
     if not args.no_cpu:
@@ -425,16 +588,32 @@ def extra_small_circuits(qs, torch):
             "note": "host-launch bound (planner + 3 launches per circuit)"}
 
 
-def extra_noisy_batch(qs, torch):
-    """4096 noisy circuits of 1-6 qubits (PTM kernel): probabilities, log-likelihood, gradient."""
+def extra_noisy_batch(qs, torch, inputs):
+    """4096 noisy circuits of 1-6 qubits (PTM kernel): probabilities, log-likelihood and its
+    gradient at perturbed parameters, for 1000-shot counts drawn from the oracle at the true
+    parameters (see noisy_oracle_inputs)."""
     import numpy as np
 
     import workloads as W
-    batch = W.noisy_batch(count=4096, seed=4001)
-    batch.counts = W.synthetic_counts(batch, 1000, seed=4002)
+    from oracle import noisy as NZ
+    batch = W.noisy_batch(count=NOISY["count"], seed=NOISY["seed"])
+    batch.counts = inputs["counts"]
+    batch.params = inputs["params"]
     dev = qs.NoisyBatchDevice(batch)
     res = {"workload": "4096 circuits, n~U{1..6}, L~U{1..256}, X90/Y90/CZ/idle + depolarizing + "
-                       "amplitude damping, 1000-shot counts"}
+                       "amplitude damping; 1000-shot counts from the oracle at the true parameters "
+                       "(seed 4001), evaluated at perturbed parameters (seed 4002)"}
+    # the oracle's own speed on this host: the forward pass of the whole batch (the pool
+    # that drew the counts) and the adjoint gradient on a sample of circuits (one core)
+    sample = [int(c) for c in W.rng(4003).choice(batch.size, size=8, replace=False)]
+    t0 = time.perf_counter()
+    for c in sample:
+        n, ops, params = batch.circuit(c)
+        NZ.grad_adjoint(n, ops, params, batch.counts[batch.cnt_off[c]:batch.cnt_off[c + 1]])
+    grad_s = (time.perf_counter() - t0) / len(sample)
+    res["cpu_oracle"] = dict(inputs["oracle_forward"],
+                             gradient_s_per_circuit_1_core=grad_s,
+                             gradient_sample="8 circuits drawn with seed 4003, Kraus-map adjoint")
     # algorithmic flops: 8 per Pauli-vector entry per one-qubit PTM (4 FMA), 1 per CZ permutation entry
     flops = 0.0
     for c in range(batch.size):
@@ -464,7 +643,7 @@ def extra_noisy_batch(qs, torch):
         res[key] = {"ms_per_batch": ms, "circuits_per_s": batch.size / (ms * 1e-3)}
         if not grad:
             res[key]["fwd_gflops"] = flops / (ms * 1e-3) / 1e9
-            res[key]["alu_frac_of_fp32_peak"] = flops / (ms * 1e-3) / 1e12 / fp32_peak_tflops(2070.0)
+            res[key]["alu_frac_of_fp32_peak"] = flops / (ms * 1e-3) / 1e12 / alu_peaks(qs, torch)["fp32_tflops"]
     return res
 
 
@@ -558,13 +737,13 @@ def extra_other_method(qs, torch, method_name, steps=3):
     torch.cuda.empty_cache()
     dom = max(kms, key=lambda k: kms[k])
     avg = kms[dom] / max(1, kcnt[dom])
-    out = {"method": METHOD_NOTE[other], "ms_per_step": ms, "gate_passes_per_s": len(arr) / (ms * 1e-3),
+    out = {"method": METHOD_NOTE[other], "ms_per_step": ms, "gates_per_s": len(arr) / (ms * 1e-3),
            "passes": s["passes"], "dominant_kernel": dom, "avg_launch_ms": avg,
            "hbm_gbs_per_pass": 2 * (1 << N_QUBITS) * 8 / (avg * 1e-3) / 1e9}
     if dom == "tile":
         tfl = s["tile_flops"] / max(1, s["tile_launches"]) / (avg * 1e-3) / 1e12
         out["alu_tflops"] = tfl
-        out["alu_frac"] = tfl / fp32_peak_tflops(2070.0)
+        out["alu_frac"] = tfl / alu_peaks(qs, torch)["fp32_tflops"]
     return out
 
 
@@ -1035,11 +1214,12 @@ def main():
                     help="run one extra row alone (for profiling) and print it")
     args = ap.parse_args()
     if args.only:
+        noisy_inputs = noisy_oracle_inputs() if args.only == "dm" else None
         import torch
 
         import paper_2008_13490_gb300 as qs
         qs.load()
-        fn = {"dm": extra_noisy_batch, "serve": extra_serving, "blocks": extra_fused_blocks,
+        fn = {"dm": lambda q, t: extra_noisy_batch(q, t, noisy_inputs), "serve": extra_serving, "blocks": extra_fused_blocks,
               "small": extra_small_circuits, "qft": lambda q, t: extra_qft(q, t, n=args.n), "fp64": extra_fp64,
               "grad": extra_sv_grad, "readout": lambda q, t: extra_readout(q, t, n=args.n),
               "dense2q": extra_dense2q, "gst": extra_gst, "code422": extra_code422,
@@ -1050,8 +1230,13 @@ def main():
         # the host-only arm needs no process group: rank 0 runs and prints, the
         # other ranks exit at once
         return run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+    # the oracle's process pool runs before the first GPU call (and before a process
+    # group exists): noisy-batch counts from the oracle
+    noisy_inputs = None
+    if not args.no_extras and int(os.environ.get("RANK", "0")) == 0:
+        noisy_inputs = noisy_oracle_inputs()
     world, rank, local = dist_setup()
-    rc = run_ours(args, world, rank, local)
+    rc = run_ours(args, world, rank, local, noisy_inputs)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

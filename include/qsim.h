@@ -169,6 +169,14 @@ qs_status sv_apply_circuit(qs_state_t st, const qs_gate* gates, size_t ngates,
  * makes the call synchronous. */
 qs_status sv_probs(qs_state_t st, void* out, int out_fp64, uint64_t marg_mask, double* norm_out);
 
+/* sv_probs into a HOST buffer: the same values (2^n, or 2^popcount(mask) for a
+ * marginal; float or double as out_fp64) formed on the device in a buffer from
+ * the state's allocator and copied to host_out in one transfer (page-locked
+ * host memory gives the full link bandwidth; pageable memory works, slower).
+ * norm_out as in sv_probs.  Synchronises.  Errors: QS_EINVAL, QS_ENOMEM,
+ * QS_EUNSUPPORTED (marginal over more than 16 qubits), QS_ECUDA. */
+qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t marg_mask, double* norm_out);
+
 /* Multinomial log-likelihood l = sum_J n_J log p_J (terms with n_J = 0 are 0;
  * p_J <= 0 with n_J > 0 is clamped to 1e-300 and counted).  counts: DEVICE,
  * 2^n uint32.  out (HOST) receives l; clamped (HOST, may be NULL) the count
@@ -436,6 +444,18 @@ qs_status qs_meas_error(void* probs, int n, int fp64, const double* e01, const d
  * NULL).  One session per process at a time. */
 qs_status qs_profile_begin(void);
 qs_status qs_profile_end(double* kernel_ms, int64_t* launches);
+
+/* ---- measurement -------------------------------------------------------- */
+
+/* Measured arithmetic peak of the current GPU (no thesis counterpart: the
+ * denominator of the rooflines of kernels bound by plain arithmetic).  kind 0:
+ * FP32 multiply-adds issued as packed FP32x2 instructions; kind 1: FP64
+ * multiply-adds.  Every SM runs 2048 threads of 8 independent FMA chains; the
+ * best of three timed launches (CUDA events on stream, after one warm-up) gives
+ * flops_per_s (2 per FMA).  sm_count (may be NULL): the device's SM count;
+ * ms (may be NULL): that launch's time.  Synchronises stream.  Errors:
+ * QS_EINVAL, QS_ECUDA. */
+qs_status qs_alu_peak(int kind, double* flops_per_s, int* sm_count, double* ms, void* stream);
 
 /* ---- misc -------------------------------------------------------------- */
 

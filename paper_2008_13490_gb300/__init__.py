@@ -119,6 +119,7 @@ def load():
         "sv_copy_out": (i32, [vp, vp, i32]),
         "sv_apply_circuit": (i32, [vp, vp, sz, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats)]),
         "sv_probs": (i32, [vp, vp, i32, u64, ctypes.POINTER(ctypes.c_double)]),
+        "sv_probs_host": (i32, [vp, vp, i32, u64, ctypes.POINTER(ctypes.c_double)]),
         "sv_loglik": (i32, [vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "sv_grad": (i32, [vp, vp, sz, vp, i32, i32, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double)]),
@@ -139,6 +140,8 @@ def load():
         "qs_server_stats_get": (i32, [vp, ctypes.POINTER(ServerStats)]),
         "qs_server_destroy": (i32, [vp]),
         "qs_server_inject_query_error": (i32, [vp, i32]),
+        "qs_alu_peak": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32),
+                              ctypes.POINTER(ctypes.c_double), vp]),
         "qs_profile_begin": (i32, []),
         "qs_profile_end": (i32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "qs_last_error": (ctypes.c_char_p, []),
@@ -154,10 +157,10 @@ def load():
 
 def exported_symbols():
     return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
-            "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_loglik", "sv_grad",
+            "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_probs_host", "sv_loglik", "sv_grad",
             "dm_apply_channels", "qs_ptm_check", "qs_probs_noalloc", "sv_bloch", "qs_meas_error", "sv_save", "sv_load",
             "dm_gst_series", "dm_gst_power", "dm_code422_eval",
-            "qs_profile_begin", "qs_profile_end",
+            "qs_profile_begin", "qs_profile_end", "qs_alu_peak",
             "qs_server_create", "qs_server_submit", "qs_server_wait", "qs_server_stats_get",
             "qs_server_destroy", "qs_server_inject_query_error", "qs_last_error", "qs_version"]
 
@@ -239,6 +242,16 @@ def qs_probs_noalloc(amps_ptr: int, n: int, prec: int, out=None, fp64: bool = Fa
                                    int(marg_mask), ctypes.byref(norm) if want_norm else None,
                                    _stream_ptr(stream)))
     return out, (norm.value if want_norm else None)
+
+
+def alu_peak(kind: int, stream=None) -> dict:
+    """Measured FP32 (kind 0, packed FP32x2 FMA) or FP64 (kind 1) peak of this GPU."""
+    f = ctypes.c_double()
+    sms = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(load().qs_alu_peak(int(kind), ctypes.byref(f), ctypes.byref(sms), ctypes.byref(ms),
+                              _stream_ptr(stream)))
+    return {"tflops": f.value / 1e12, "sm_count": sms.value, "ms": ms.value}
 
 
 def qs_profile_begin():
@@ -418,6 +431,19 @@ def sv_probs(st: State, out=None, fp64: bool = False, marg_mask: int = 0, want_n
     norm = ctypes.c_double()
     _check(load().sv_probs(st.handle, out.data_ptr(), 1 if fp64 else 0, int(marg_mask),
                            ctypes.byref(norm) if want_norm else None))
+    return out, (norm.value if want_norm else None)
+
+
+def sv_probs_host(st: State, out=None, fp64: bool = False, marg_mask: int = 0, want_norm: bool = False):
+    """Born-rule probabilities into a HOST buffer through the C ABI (a numpy array,
+    or a pinned CPU torch tensor ``out``).  Returns (out, norm or None); synchronises."""
+    k = bin(marg_mask).count("1") if marg_mask else st.n
+    if out is None:
+        out = np.empty(1 << k, dtype=np.float64 if fp64 else np.float32)
+    ptr = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+    norm = ctypes.c_double()
+    _check(load().sv_probs_host(st.handle, ptr, 1 if fp64 else 0, int(marg_mask),
+                                ctypes.byref(norm) if want_norm else None))
     return out, (norm.value if want_norm else None)
 
 

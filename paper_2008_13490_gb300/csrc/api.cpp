@@ -840,6 +840,47 @@ qs_status sv_probs(qs_state_t st, void* out, int out_fp64, uint64_t marg_mask, d
   return QS_OK;
 }
 
+qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t marg_mask, double* norm_out) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (!host_out) {
+    set_error("host_out is required");
+    return QS_EINVAL;
+  }
+  if (marg_mask >> st->n) {
+    set_error("marginal mask has bits beyond n = %d", st->n);
+    return QS_EINVAL;
+  }
+  const int k = __builtin_popcountll(marg_mask);
+  const int kk = (marg_mask != 0 && k != st->n) ? k : st->n;
+  const size_t bytes = (out_fp64 ? sizeof(double) : sizeof(float)) << kk;
+  // the probabilities are formed on the device in a buffer from the state's
+  // allocator, then copied to the host buffer in one transfer
+  void* dev = dev_alloc(st, bytes);
+  if (!dev) {
+    set_error("device buffer for the probabilities (%zu bytes) could not be allocated", bytes);
+    return QS_ENOMEM;
+  }
+  s = sv_probs(st, dev, out_fp64, marg_mask, nullptr);
+  if (s == QS_OK) {
+    const cudaError_t e = cudaMemcpyAsync(host_out, dev, bytes, cudaMemcpyDeviceToHost, st->stream);
+    if (e != cudaSuccess) s = cuda_status(e, "probabilities to the host");
+  }
+  if (s == QS_OK && norm_out) {
+    unsigned char* sc = (unsigned char*)st->scratch;
+    double* res = (double*)(sc + kScratchResult);
+    s = launch_reduce_partials(st, (double*)(sc + kScratchPartials), kReduceBlocks, res);
+    if (s == QS_OK) {
+      const cudaError_t e = cudaMemcpyAsync(norm_out, res, sizeof(double), cudaMemcpyDeviceToHost, st->stream);
+      if (e != cudaSuccess) s = cuda_status(e, "norm to the host");
+    }
+  }
+  const cudaError_t e = cudaStreamSynchronize(st->stream);
+  dev_free(st, dev, bytes);
+  if (s == QS_OK && e != cudaSuccess) s = cuda_status(e, "sv_probs_host");
+  return s;
+}
+
 qs_status sv_loglik(qs_state_t st, const uint32_t* counts, double* out, int64_t* clamped) {
   qs_status s = check_state(st);
   if (s != QS_OK) return s;

@@ -240,3 +240,40 @@ def test_invalid_arguments(qs):
     with pytest.raises(qs.QsimError) as e:
         qs.State(0)
     assert e.value.status == qs.QS_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_probs_to_host_buffer(qs, prec):
+    # sv_probs_host: the same values as sv_probs, delivered into host memory
+    import torch
+    n = 14
+    st = qs.State(n, prec)
+    ops = W.random_gate_mix(n, 60, seed=321)
+    qs.sv_apply_circuit(st, ops)
+    ref = SV.probabilities(SV.apply_circuit(SV.basis(n), n, ops))
+    for fp64 in (False, True):
+        dev, dnorm = qs.sv_probs(st, fp64=fp64)
+        host, norm = qs.sv_probs_host(st, fp64=fp64, want_norm=True)
+        np.testing.assert_array_equal(host, dev.cpu().numpy())
+        assert norm == dnorm
+        np.testing.assert_allclose(host, ref, atol=1e-12 if (prec and fp64) else 2e-6)
+    pinned = torch.empty(1 << n, dtype=torch.float32, pin_memory=True)
+    qs.sv_probs_host(st, out=pinned)
+    np.testing.assert_allclose(pinned.numpy(), ref, atol=2e-6)
+    mask = 0b1010110
+    m, _ = qs.sv_probs_host(st, fp64=True, marg_mask=mask)
+    np.testing.assert_allclose(m, SV.marginal(ref, n, mask), atol=1e-12 if prec else 2e-6)
+    st.close()
+
+
+def test_alu_peak_microbenchmark(qs):
+    # the measured FP32 / FP64 peaks used as roofline denominators: plausible and
+    # consistent with the device's SM count (FP32 at most 128 FMA lanes per SM at 2.1 GHz)
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    f32 = qs.alu_peak(0)
+    f64 = qs.alu_peak(1)
+    assert f32["sm_count"] == sms
+    bound32 = sms * 128 * 2 * 2.2e9 / 1e12
+    assert 0.3 * bound32 < f32["tflops"] <= bound32, f32
+    assert 0 < f64["tflops"] < f32["tflops"], (f64, f32)

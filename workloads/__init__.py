@@ -373,3 +373,14 @@ def serving_stream(count: int, seed: int, n_range=(8, 28), depth_range=(10, 200)
         d = int(g.integers(depth_range[0], depth_range[1] + 1))
         out.append((t, n, d, int(g.integers(0, 2**31 - 1))))
     return out
+
+
+def perturbed_params(batch: NoisyBatch, seed: int, theta_sigma: float = 0.01,
+                     rate_rel: float = 0.2) -> np.ndarray:
+    """Parameters near a batch's true ones, where a likelihood is evaluated:
+    theta + N(0, theta_sigma^2), p and gamma scaled by U[1 - rate_rel, 1 + rate_rel]."""
+    g = rng(seed)
+    out = batch.params.copy()
+    out[:, 0:2] += theta_sigma * g.normal(size=(batch.size, 2))
+    out[:, 2:4] *= g.uniform(1 - rate_rel, 1 + rate_rel, size=(batch.size, 2))
+    return out
