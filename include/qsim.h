@@ -170,9 +170,11 @@ qs_status sv_apply_circuit(qs_state_t st, const qs_gate* gates, size_t ngates,
 qs_status sv_probs(qs_state_t st, void* out, int out_fp64, uint64_t marg_mask, double* norm_out);
 
 /* sv_probs into a HOST buffer: the same values (2^n, or 2^popcount(mask) for a
- * marginal; float or double as out_fp64) formed on the device in a buffer from
- * the state's allocator and copied to host_out in one transfer (page-locked
- * host memory gives the full link bandwidth; pageable memory works, slower).
+ * marginal; float or double as out_fp64).  The full distribution is formed in
+ * 64 MiB chunks in a device staging buffer (obtained from the state's allocator
+ * at the first call and kept until sv_destroy) and each chunk copied to host_out
+ * (page-locked host memory gives the full link bandwidth; pageable memory works,
+ * slower).
  * norm_out as in sv_probs.  Synchronises.  Errors: QS_EINVAL, QS_ENOMEM,
  * QS_EUNSUPPORTED (marginal over more than 16 qubits), QS_ECUDA. */
 qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t marg_mask, double* norm_out);

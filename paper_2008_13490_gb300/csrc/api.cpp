@@ -731,6 +731,7 @@ qs_status sv_destroy(qs_state_t st) {
   if (!st) return QS_OK;
   cudaStreamSynchronize(st->stream);
   dev_free(st, st->opbuf, st->opbuf_bytes);
+  if (st->stage) dev_free(st, st->stage, st->stage_bytes);
   dev_free(st, st->scratch, st->scratch_bytes);
   dev_free(st, st->data, st->data_bytes);
   if (st->hostbuf) cudaFreeHost(st->hostbuf);
@@ -852,31 +853,49 @@ qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t ma
     return QS_EINVAL;
   }
   const int k = __builtin_popcountll(marg_mask);
-  const int kk = (marg_mask != 0 && k != st->n) ? k : st->n;
-  const size_t bytes = (out_fp64 ? sizeof(double) : sizeof(float)) << kk;
-  // the probabilities are formed on the device in a buffer from the state's
-  // allocator, then copied to the host buffer in one transfer
-  void* dev = dev_alloc(st, bytes);
-  if (!dev) {
-    set_error("device buffer for the probabilities (%zu bytes) could not be allocated", bytes);
-    return QS_ENOMEM;
+  unsigned char* sc = (unsigned char*)st->scratch;
+  double* partials = (double*)(sc + kScratchPartials);
+  if (marg_mask != 0 && k != st->n) {
+    // a marginal (at most 2^16 values) stays in the scratch accumulators as doubles
+    if (k > kScratchMargLog2) {
+      set_error("marginal over %d qubits exceeds the %d-qubit scratch limit", k, kScratchMargLog2);
+      return QS_EUNSUPPORTED;
+    }
+    s = sv_probs(st, nullptr, 1, marg_mask, norm_out);
+    if (s != QS_OK) return s;
+    std::vector<double> h((size_t)1 << k);
+    QS_CUDA(cudaMemcpyAsync(h.data(), sc + kScratchMarg, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                            st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    if (out_fp64) std::memcpy(host_out, h.data(), h.size() * sizeof(double));
+    else
+      for (size_t i = 0; i < h.size(); ++i) ((float*)host_out)[i] = (float)h[i];
+    return QS_OK;
   }
-  s = sv_probs(st, dev, out_fp64, marg_mask, nullptr);
-  if (s == QS_OK) {
-    const cudaError_t e = cudaMemcpyAsync(host_out, dev, bytes, cudaMemcpyDeviceToHost, st->stream);
-    if (e != cudaSuccess) s = cuda_status(e, "probabilities to the host");
+  // the whole distribution: formed chunk by chunk in a device staging buffer (kept
+  // by the state) and copied to the host buffer after each chunk
+  const size_t es = out_fp64 ? sizeof(double) : sizeof(float);
+  const uint64_t N = 1ull << st->n;
+  const uint64_t chunk = std::min<uint64_t>(N, (uint64_t)(kStageBytes / es));
+  if (!st->stage) {
+    st->stage = dev_alloc(st, kStageBytes);
+    if (!st->stage) {
+      set_error("staging buffer for the probabilities could not be allocated");
+      return QS_ENOMEM;
+    }
+    st->stage_bytes = kStageBytes;
   }
-  if (s == QS_OK && norm_out) {
-    unsigned char* sc = (unsigned char*)st->scratch;
-    double* res = (double*)(sc + kScratchResult);
-    s = launch_reduce_partials(st, (double*)(sc + kScratchPartials), kReduceBlocks, res);
+  for (uint64_t off = 0; off < N && s == QS_OK; off += chunk) {
+    const uint64_t cnt = std::min<uint64_t>(chunk, N - off);
+    s = launch_probs_range(st, off, cnt, st->stage, out_fp64, partials);
     if (s == QS_OK) {
-      const cudaError_t e = cudaMemcpyAsync(norm_out, res, sizeof(double), cudaMemcpyDeviceToHost, st->stream);
-      if (e != cudaSuccess) s = cuda_status(e, "norm to the host");
+      const cudaError_t e = cudaMemcpyAsync((unsigned char*)host_out + off * es, st->stage, cnt * es,
+                                            cudaMemcpyDeviceToHost, st->stream);
+      if (e != cudaSuccess) s = cuda_status(e, "probabilities to the host");
     }
   }
+  if (s == QS_OK && norm_out) s = sv_probs(st, nullptr, out_fp64, 0, norm_out);
   const cudaError_t e = cudaStreamSynchronize(st->stream);
-  dev_free(st, dev, bytes);
   if (s == QS_OK && e != cudaSuccess) s = cuda_status(e, "sv_probs_host");
   return s;
 }

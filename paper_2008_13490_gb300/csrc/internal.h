@@ -44,6 +44,9 @@ struct State {
   void* hostbuf = nullptr;
   size_t hostbuf_bytes = 0;
   cudaEvent_t upload_done = nullptr;
+  // device staging buffer of probabilities bound for host memory (sv_probs_host)
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
 };
 
 void* dev_alloc(State* st, size_t bytes);
@@ -59,6 +62,8 @@ constexpr size_t kScratchBits = 8704;             // 64 bytes of bit positions
 constexpr size_t kScratchMarg = 16384;            // marginal accumulators (doubles)
 constexpr int kScratchMargLog2 = 16;              // largest marginal kept in scratch
 constexpr size_t kScratchBytes = kScratchMarg + (sizeof(double) << kScratchMargLog2);
+// staging buffer of sv_probs_host (allocated at its first call, kept by the state)
+constexpr size_t kStageBytes = 64ull << 20;
 
 // ---------------------------------------------------------------- gates
 // Host-side gate matrices, written from the thesis's definitions (rotations,
@@ -280,6 +285,10 @@ qs_status launch_small(State* st, const void* ops_dev, int nops);
 qs_status launch_remap(State* st, const void* desc_dev, void* tmp);
 qs_status launch_probs(State* st, void* out, int out_fp64, uint64_t mask, double* partials,
                        uint8_t* bits_dev, double* marg_acc);
+// probabilities of amplitudes [off, off + count) of the state into out (device;
+// float or double), block partial sums of that range into partials
+qs_status launch_probs_range(State* st, uint64_t off, uint64_t count, void* out, int out_fp64,
+                             double* partials);
 qs_status launch_reduce_partials(State* st, const double* partials, int count, double* out);
 qs_status launch_loglik(State* st, const uint32_t* counts, double* partials,
                         unsigned long long* clamps);

@@ -1209,6 +1209,29 @@ qs_status launch_remap(State* st, const void* desc_dev, void* /*tmp*/) {
   return QS_OK;
 }
 
+qs_status launch_probs_range(State* st, uint64_t off, uint64_t count, void* out, int out_fp64,
+                             double* partials) {
+  if (st->prec == QS_C64 && !out_fp64 && (off % 2) == 0 && (count % 2) == 0) {
+    probs_kernel_f32x2<<<kReduceBlocks, 256, 0, st->stream>>>((const float4*)((const C2<float>*)st->data + off),
+                                                              (float2*)out, count / 2, partials);
+  } else if (st->prec == QS_C64) {
+    if (out_fp64)
+      probs_kernel<float, double><<<kReduceBlocks, 256, 0, st->stream>>>(
+          (const C2<float>*)st->data + off, (double*)out, count, partials);
+    else
+      probs_kernel<float, float><<<kReduceBlocks, 256, 0, st->stream>>>(
+          (const C2<float>*)st->data + off, (float*)out, count, partials);
+  } else if (out_fp64) {
+    probs_kernel<double, double><<<kReduceBlocks, 256, 0, st->stream>>>(
+        (const C2<double>*)st->data + off, (double*)out, count, partials);
+  } else {
+    probs_kernel<double, float><<<kReduceBlocks, 256, 0, st->stream>>>(
+        (const C2<double>*)st->data + off, (float*)out, count, partials);
+  }
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
 qs_status launch_probs(State* st, void* out, int out_fp64, uint64_t mask, double* partials,
                        uint8_t* dbits, double* marg_acc) {
   const uint64_t N = 1ull << st->n;
