@@ -258,9 +258,13 @@ template <int MODE>
 struct Pipe {
   static constexpr int kStages = 4;
 };
+// two output staging buffers (box-store passes alternate between them, so the
+// tensor store of one tile may still be reading its buffer while the next tile is
+// staged)
+constexpr int kStageBufs = 2;
 template <int MODE>
 constexpr size_t pipe_smem_bytes() {
-  return (size_t)(Pipe<MODE>::kStages + 1) * kTileBytes + (size_t)BOps<MODE>::kParts * BOps<MODE>::kB;
+  return (size_t)(Pipe<MODE>::kStages + kStageBufs) * kTileBytes + (size_t)BOps<MODE>::kParts * BOps<MODE>::kB;
 }
 // tensor-memory column of part p of A (BF16: 32 columns per part, two bf16 per
 // column; TF32: 64 columns per part)
@@ -326,6 +330,21 @@ __device__ __forceinline__ void box_load4(void* dst, const CUtensorMap* map, int
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(b))
       : "memory");
 }
+// one box of a rank-4 tensor map from shared memory to global memory (bulk group)
+__device__ __forceinline__ void box_store4(const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                           const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the bulk groups of this thread but the newest one have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every bulk group of this thread has completed (its writes are done)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // bounded wait; gives up after kWaitLimit polls or, if fail is given, once
 // another role has failed
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, const int* fail) {
@@ -352,7 +371,9 @@ __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-template <int MODE>
+// BOX: the pass writes its output back with tensor stores (BlockPass flag bit 1);
+// a separate instantiation, so that each variant keeps its own register budget
+template <int MODE, bool BOX>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     block_pipe_kernel(float2* __restrict__ psi, const BlockPass* __restrict__ P,
                       const unsigned char* __restrict__ bmat, uint64_t ntiles, int* __restrict__ status,
@@ -383,10 +404,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   __shared__ uint8_t s_slot[32];
   __shared__ uint8_t s_f[8];
   __shared__ int s_nnt;
+  __shared__ uint64_t s_qoff[16];
+  __shared__ int s_ncopy, s_glo, s_glen;
   __shared__ float s_norm[kNormSlots][128];   // producer -> epilogue: squared input row norms
   __shared__ float s_part[2][128];            // epilogue column halves: squared output norms
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool unitary = (P->flags & 1) != 0;
+  // the output is staged in the loader's box layout and written back with tensor
+  // stores (the host found the staging writes conflict-free in that layout)
+  constexpr bool boxst = BOX;
 
   if (tid < 64) {
     t_addr_hi[tid] = P->addr_hi[tid];
@@ -398,8 +424,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   if (tid < 48) s_nt[tid] = P->nt_pos[tid];
   if (tid < 32) s_slot[tid] = P->run_slot[tid];
   if (tid < 8) s_f[tid] = P->stage_f[tid];
+  if (tid < 16) s_qoff[tid] = tid < P->n_copy ? P->q_off[tid] : 0ull;
   if (tid == 0) {
     s_nnt = P->n_nt;
+    s_ncopy = P->n_copy;
+    s_glo = P->g_lo;
+    s_glen = P->g_len;
     s_fail = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&rfull[s], 1);
@@ -457,6 +487,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   // epilogue: element k * 256 + et of the store loop, k in Gray-code order: its
   // address and staging index at k = 0 and their change when bit b of k flips
   // (element bit 8 + b = bit 2 + b of the high half); F(m) of the row written
+  // (box-store passes reuse idx0 / dS for the staging index in the raw-stage slot
+  // layout of this row's first column and its change with column bits 0..3)
   uint64_t addr0 = 0, dA[4];
   uint32_t idx0 = 0, dS[4], fm = 0;
   // loader: lane q < n_copy loads box q: the address bits q_off of its runs
@@ -484,16 +516,24 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     ec16 = slot(ec16);
     e00 = slot(e00);
   } else if (warp < 12) {
-    const int et = tid - 128;   // 0..255
-    const int m_lo = t_m_lo[et & 63], c_lo = t_c_lo[et & 63];
-    addr0 = (uint64_t)(et & 63) | t_addr_hi[et >> 6];   // low 6 bits: physical bits 0..5
-    idx0 = (uint32_t)((m_lo << 5) ^ c_lo ^ stage_F(m_lo)) ^ t_sh[et >> 6];
+    if (boxst) {
+      auto slot = [&](uint32_t e) { return (e & 127u) | ((uint32_t)s_slot[e >> 7] << 7); };
+      const int half = (warp - 4) >> 2, mrow = (warp & 3) * 32 + lane;
+      idx0 = slot((uint32_t)t_em[mrow] ^ (uint32_t)t_ec[16 * half]);
 #pragma unroll
-    for (int bit = 0; bit < 4; ++bit) {
-      dA[bit] = t_addr_hi[4 << bit];
-      dS[bit] = t_sh[4 << bit];
+      for (int b = 0; b < 4; ++b) dS[b] = slot(t_ec[1 << b]);
+    } else {
+      const int et = tid - 128;   // 0..255
+      const int m_lo = t_m_lo[et & 63], c_lo = t_c_lo[et & 63];
+      addr0 = (uint64_t)(et & 63) | t_addr_hi[et >> 6];   // low 6 bits: physical bits 0..5
+      idx0 = (uint32_t)((m_lo << 5) ^ c_lo ^ stage_F(m_lo)) ^ t_sh[et >> 6];
+#pragma unroll
+      for (int bit = 0; bit < 4; ++bit) {
+        dA[bit] = t_addr_hi[4 << bit];
+        dS[bit] = t_sh[4 << bit];
+      }
+      fm = stage_F((warp & 3) * 32 + lane) & 31u;
     }
-    fm = stage_F((warp & 3) * 32 + lane) & 31u;
   } else if (warp == kWarpLoad) {
     n_copy = P->n_copy;
     g_lo = P->g_lo;
@@ -696,9 +736,13 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     const int half = (warp - 4) >> 2;            // complex columns 16 half .. 16 half + 15
     const int m = (warp & 3) * 32 + lane;       // row of the tile = tensor-memory lane
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const bool leader = tid == 128;   // issues and waits for the tensor stores
     for (uint64_t i = 0; i < my_tiles; ++i) {
       const int tb = (int)(i & 1);
       const uint32_t pt = (uint32_t)((i >> 1) & 1);
+      // box store: the store of tile i - 2 has read staging buffer i % 2 (the
+      // barrier below publishes that to the other epilogue threads)
+      if (boxst && leader) bulk_wait_read_1();
       const bool okw = mbar_wait(&tfull[tb], pt, &s_fail);
       // collective: all epilogue threads stop together (and none of them is
       // still reading the staging or s_part of the previous tile past this point)
@@ -747,6 +791,30 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         const float ny = s_part[0][m] + s_part[1][m];
         if (ny > 0.f) delta = (nx - ny) / (ny + sqrtf(nx) * sqrtf(ny));
       }
+      if (boxst) {
+        // the loader's layout: column j of this half at bx0 ^ (XOR of bxd over the
+        // set bits of j), visited in Gray-code order; lanes = rows, conflict-free
+        float2* stg = stage + (i & 1) * 4096;
+        uint32_t idx = idx0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          if (t) idx ^= dS[(t & 1) ? 0 : (t & 2) ? 1 : (t & 4) ? 2 : 3];
+          const int j = t ^ (t >> 1);
+          stg[idx] = make_float2(fmaf(y[2 * j], delta, y[2 * j]), fmaf(y[2 * j + 1], delta, y[2 * j + 1]));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor store
+        bar_sync(kEpiSync, kEpiThreads);
+        if (leader) {
+          const uint64_t base = tile_base(i);
+          for (int q = 0; q < s_ncopy; ++q) {
+            const uint64_t a = base | s_qoff[q];
+            const int c1 = (int)((a >> 7) & ((1ull << (s_glo - 7)) - 1)), c3 = (int)(a >> (s_glo + s_glen));
+            box_store4(&tmap, 0, c1, 0, c3, stg + (q << s_glen) * 128);
+          }
+          bulk_commit();
+        }
+        continue;
+      }
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int c = 16 * half + j;
@@ -771,6 +839,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         __stcs(psi + addr, v[k]);
       }
     }
+    // no tensor store may still be reading shared memory (or writing) at exit
+    if (boxst && leader) bulk_wait_all();
   }
   __syncthreads();
   if (tid == 0 && s_fail) atomicExch(status, (int)QS_ETIMEOUT);
@@ -1014,6 +1084,17 @@ void block_pass_desc(int n, const int* bpos, BlockPass& P) {
   }
   for (int j = 0; j < 7; ++j) P.stage_f[j] = (uint8_t)F[j];
   P.stage_f[7] = 0;
+  // box store: the epilogue writes row m, column c to the loader's slot of its
+  // address-order index; a warp's lanes are row bits 0..4, so the writes meet 16
+  // distinct 8-byte bank pairs when the slots of those row bits span bits 0..3
+  uint32_t rowslot[5];
+  for (int j = 0; j < 5; ++j) {
+    int a = 0;
+    while (order[a] != rows[j]) ++a;
+    const uint32_t e = 1u << a;
+    rowslot[j] = (e & 127u) | ((uint32_t)P.run_slot[e >> 7] << 7);
+  }
+  if (rank4(rowslot, 5) == 4) P.flags |= 2;
 }
 
 size_t block_pass_bytes() { return sizeof(BlockPass); }
@@ -1075,21 +1156,24 @@ qs_status launch_block_pass(State* st, const BlockPass& host_pass, const void* p
   // of the SM's, and the grid is one CTA per SM.
   static_assert(pipe_smem_bytes<BM_BF16>() > 120 * 1024, "one CTA per SM");
   static_assert(pipe_smem_bytes<BM_TF32>() <= 224 * 1024, "shared memory per CTA");
+  static_assert(pipe_smem_bytes<BM_BF16>() <= 224 * 1024, "shared memory per CTA");
   uint64_t grid = (uint64_t)sms;
   if (grid > ntiles) grid = ntiles;
-  if (mode == BM_TF32) {
-    const size_t smem = pipe_smem_bytes<BM_TF32>();
-    QS_CUDA(cudaFuncSetAttribute(block_pipe_kernel<BM_TF32>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    block_pipe_kernel<BM_TF32><<<(unsigned)grid, kPipeThreads, smem, st->stream>>>(
-        (float2*)st->data, (const BlockPass*)pass_dev, (const unsigned char*)b_dev, ntiles, status_dev, map);
-  } else {
-    const size_t smem = pipe_smem_bytes<BM_BF16>();
-    QS_CUDA(cudaFuncSetAttribute(block_pipe_kernel<BM_BF16>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    block_pipe_kernel<BM_BF16><<<(unsigned)grid, kPipeThreads, smem, st->stream>>>(
-        (float2*)st->data, (const BlockPass*)pass_dev, (const unsigned char*)b_dev, ntiles, status_dev, map);
-  }
+  const bool box = (host_pass.flags & 2) != 0;
+  auto launch = [&](auto kern, size_t smem) -> qs_status {
+    QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)grid, kPipeThreads, smem, st->stream>>>((float2*)st->data, (const BlockPass*)pass_dev,
+                                                             (const unsigned char*)b_dev, ntiles, status_dev, map);
+    return QS_OK;
+  };
+  qs_status ls;
+  if (mode == BM_TF32)
+    ls = box ? launch(block_pipe_kernel<BM_TF32, true>, pipe_smem_bytes<BM_TF32>())
+             : launch(block_pipe_kernel<BM_TF32, false>, pipe_smem_bytes<BM_TF32>());
+  else
+    ls = box ? launch(block_pipe_kernel<BM_BF16, true>, pipe_smem_bytes<BM_BF16>())
+             : launch(block_pipe_kernel<BM_BF16, false>, pipe_smem_bytes<BM_BF16>());
+  if (ls != QS_OK) return ls;
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }

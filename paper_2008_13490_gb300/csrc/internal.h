@@ -222,7 +222,8 @@ struct BlockPass {
   uint8_t c_lo[64], c_hi[64];
   uint8_t nt_pos[48];           // physical positions outside the tile (ascending)
   int32_t n_nt;
-  int32_t flags;                // bit 0: the block is unitary (rows keep their norm)
+  int32_t flags;                // bit 0: the block is unitary (rows keep their norm);
+                                // bit 1: the output goes back by tensor stores (box layout)
   int32_t pad[2];
   // Tile loads as tensor boxes: the 5 tile positions above bit 6 (H, ascending)
   // hold a longest run of g consecutive positions starting at position g_lo (run
