@@ -5,10 +5,11 @@ Workload (the 30-qubit configuration): n = 30 qubits, complex64 (8 GiB
 state), 40 layers of Haar-random SU(2) on every qubit plus brickwork CZ
 (seed 2001) = 1780 gates, started from |0...0>, followed by the Born-rule
 probabilities (4 GiB fp32) and their fp64 norm.  One step = one such circuit,
-by default with the fastest complex64 method: the gates fused into 5-qubit
-blocks applied on the tcgen05 tensor cores (BF16 three-part split, FP32
-accumulation; --method selects another), the tiled FP32 SIMT path reported as
-a row of the same line.
+by default through the library's default method (QS_METHOD_AUTO: dense 5-qubit
+blocks on the tcgen05 tensor cores with the BF16 three-part split and FP32
+accumulation, sparse stretches on tile passes; for this circuit every block is
+dense; --method selects another), the tiled FP32 SIMT path reported as a row
+of the same line.
 
 metric (BASELINE's): reported in "gates/s" = gates of the circuit applied to the
 full 2^30-amplitude state per second (the real HBM sweeps per second are in
@@ -94,6 +95,9 @@ def alu_peaks(qs, torch):
 
 
 METHOD_NOTE = {
+    "auto": "the library's default: the circuit cut into 5-qubit blocks, dense blocks as BF16-split "
+            "GEMMs on tcgen05 tensor cores (FP32 accumulation, per-row norm correction), runs of "
+            "sparse blocks replayed through 12-qubit shared-memory tile passes",
     "blocks_bf16": "5-qubit fused blocks on tcgen05 tensor cores, BF16 three-part split products, "
                    "FP32 accumulation, per-row norm correction",
     "blocks_tf32": "5-qubit fused blocks on tcgen05 tensor cores, TF32 two-part split products, "
@@ -111,6 +115,7 @@ KERNEL_SOURCES = {
 TRAFFIC_FILES = {
     ("tile", "tiled"): "tile_pass_kernel_traffic_n30_layered_haar_cz.json",
     ("block", "blocks_bf16"): "block_pipe_kernel_bf16_traffic_n30_layered_haar_cz.json",
+    ("block", "auto"): "block_pipe_kernel_bf16_traffic_n30_layered_haar_cz.json",
 }
 
 
@@ -427,7 +432,7 @@ def run_ours(args, world, rank, local, noisy_inputs=None):
     probs = torch.empty(1 << n, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    method = {"tiled": qs.METHOD_TILED, "plain": qs.METHOD_PLAIN,
+    method = {"tiled": qs.METHOD_TILED, "plain": qs.METHOD_PLAIN, "auto": qs.METHOD_AUTO,
               "blocks_tf32": qs.METHOD_BLOCKS_TF32, "blocks_bf16": qs.METHOD_BLOCKS_BF16}[args.method]
 
     def step():
@@ -496,7 +501,7 @@ def run_ours(args, world, rank, local, noisy_inputs=None):
         # block GEMM: one HBM sweep per launch (its roof; the tensor work, 4 (TF32) or
         # 6 (BF16) split products of 2^(n+8) flops, is far below the tensor peak)
         per_launch = bytes_per_pass
-        tf32 = args.method == "blocks_tf32"
+        tf32 = args.method == "blocks_tf32"   # (the default method uses the BF16 split)
         roof = {"bound": "hbm", "kernel": "block_pipe_kernel<%s>" % ("TF32" if tf32 else "BF16"),
                 "unit": "GB/s", "peak": peaks["hbm_gbs"], "peak_source": "measured copy bandwidth",
                 "tensor_tflops": block_products(tf32) * 2.0 ** (n + 8) / (avg_ms * 1e-3) / 1e12,
@@ -708,8 +713,8 @@ def extra_other_method(qs, torch, method_name, steps=3):
     """The headline workload with the other complex64 method (tiled FP32 SIMT if the line
     used fused blocks, else fused blocks BF16): per-step time and its dominant kernel."""
     import workloads as W
-    other = "tiled" if method_name != "tiled" else "blocks_bf16"
-    method = {"tiled": qs.METHOD_TILED, "blocks_bf16": qs.METHOD_BLOCKS_BF16}[other]
+    other = "tiled" if method_name != "tiled" else "auto"
+    method = {"tiled": qs.METHOD_TILED, "auto": qs.METHOD_AUTO}[other]
     arr = qs.gates_array(W.layered_haar_cz(N_QUBITS, LAYERS, seed=SEED))
     st = qs.State(N_QUBITS, qs.QS_C64)
     probs = torch.empty(1 << N_QUBITS, dtype=torch.float32, device="cuda")
@@ -1205,9 +1210,9 @@ def main():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other rows' measurements")
-    ap.add_argument("--method", default="blocks_bf16", choices=["tiled", "plain", "blocks_tf32", "blocks_bf16"],
-                    help="state-vector method of the timed workload (default: the fastest, fused "
-                         "blocks with the BF16 split; the tiled path is reported as a row)")
+    ap.add_argument("--method", default="auto", choices=["auto", "tiled", "plain", "blocks_tf32", "blocks_bf16"],
+                    help="state-vector method of the timed workload (default: the library's default "
+                         "method; the tiled path is reported as a row)")
     ap.add_argument("--only", default=None,
                     choices=["dm", "serve", "blocks", "small", "qft", "fp64", "grad", "other",
                              "readout", "dense2q", "gst", "code422"],

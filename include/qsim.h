@@ -98,7 +98,7 @@ typedef struct {
 typedef struct qs_state_s* qs_state_t;
 
 typedef enum {
-  QS_METHOD_TILED = 0,       /* fused shared-memory tile passes (default) */
+  QS_METHOD_TILED = 0,       /* fused shared-memory tile passes */
   QS_METHOD_PLAIN = 1,       /* one kernel launch per gate (comparison baseline) */
   /* gates fused into dense 5-qubit blocks (32x32 unitaries, products of the
    * circuit's gates), each applied as a real [2^(n-5) x 64] x [64 x 64] GEMM
@@ -109,7 +109,15 @@ typedef enum {
    * (QS_EUNSUPPORTED otherwise); synchronous (the call checks the kernels'
    * bounded-wait status word). */
   QS_METHOD_BLOCKS_TF32 = 2, /* two TF32 parts, 4 products (~1e-6 relative over 100 blocks) */
-  QS_METHOD_BLOCKS_BF16 = 3  /* three BF16 parts, 6 products (~6e-7 relative over 100 blocks) */
+  QS_METHOD_BLOCKS_BF16 = 3, /* three BF16 parts, 6 products (~6e-7 relative over 100 blocks) */
+  /* the default (also when opts is NULL): for complex64 states with n >= 12
+   * the circuit is cut into 5-qubit blocks; a block with more than half of its
+   * 1024 entries nonzero is a dense contraction and runs as a BF16-split GEMM on
+   * the tensor cores, and each maximal run of sparser blocks (diagonal or nearly
+   * diagonal stretches, permutations) is replayed gate by gate through the tile
+   * passes; other states use QS_METHOD_TILED.  Synchronous like the block
+   * methods. */
+  QS_METHOD_AUTO = 4
 } qs_method;
 
 typedef struct {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libqsim.so")
 
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
 QS_C64, QS_C128 = 0, 1
-METHOD_TILED, METHOD_PLAIN, METHOD_BLOCKS_TF32, METHOD_BLOCKS_BF16 = 0, 1, 2, 3
+METHOD_TILED, METHOD_PLAIN, METHOD_BLOCKS_TF32, METHOD_BLOCKS_BF16, METHOD_AUTO = 0, 1, 2, 3, 4
 
 KIND = {
     "I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,
@@ -407,7 +407,7 @@ def sv_copy_out(st: State, out=None):
     return a
 
 
-def sv_apply_circuit(st: State, gates, method: int = METHOD_TILED, time_kernels: bool = False) -> dict:
+def sv_apply_circuit(st: State, gates, method: int = METHOD_AUTO, time_kernels: bool = False) -> dict:
     arr = gates if isinstance(gates, np.ndarray) else gates_array(gates)
     arr = np.ascontiguousarray(arr, dtype=GATE_DTYPE)
     opts = _Opts(method, OPT_TIME_KERNELS if time_kernels else 0)

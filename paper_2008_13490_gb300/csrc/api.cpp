@@ -550,10 +550,9 @@ qs_status adjoint_tiled_t(State* st, void* lam, const qs_gate* gates, size_t g0,
 }
 
 // Dense 5-qubit blocks on the tensor cores: one pass per block.
-qs_status run_blocks(State* st, const qs_gate* gates, size_t ngates, int mode, qs_stats* stats,
-                     KernelTimer& tm) {
-  std::vector<Block> blocks;
-  plan_blocks(gates, ngates, st->n, blocks);
+qs_status run_block_list(State* st, const std::vector<Block>& blocks, int mode, qs_stats* stats,
+                         KernelTimer& tm) {
+  if (blocks.empty()) return QS_OK;
   std::vector<unsigned char> blob(16, 0);   // status word of the bounded waits
   std::vector<BlockPass> passes(blocks.size());
   for (size_t i = 0; i < blocks.size(); ++i) {
@@ -592,17 +591,70 @@ qs_status run_blocks(State* st, const qs_gate* gates, size_t ngates, int mode, q
     return QS_ETIMEOUT;
   }
   if (stats) {
-    int64_t g = 0;
-    for (const Block& b : blocks) g += b.ngates;
-    stats->ops_fused = (int64_t)blocks.size();
-    stats->passes = (int64_t)blocks.size();
-    stats->launches = (int64_t)blocks.size();
+    stats->ops_fused += (int64_t)blocks.size();
+    stats->passes += (int64_t)blocks.size();
+    stats->launches += (int64_t)blocks.size();
     // 32 complex MACs per amplitude per block = 256 flops (the split precision triples the MMAs)
-    stats->flops = 256.0 * std::ldexp(1.0, st->n) * (double)blocks.size();
-    stats->upload_bytes = (int64_t)blob.size();
-    (void)g;
+    stats->flops += 256.0 * std::ldexp(1.0, st->n) * (double)blocks.size();
+    stats->upload_bytes += (int64_t)blob.size();
   }
   return QS_OK;
+}
+
+qs_status run_blocks(State* st, const qs_gate* gates, size_t ngates, int mode, qs_stats* stats,
+                     KernelTimer& tm) {
+  std::vector<Block> blocks;
+  plan_blocks(gates, ngates, st->n, blocks);
+  return run_block_list(st, blocks, mode, stats, tm);
+}
+
+// QS_METHOD_AUTO (complex64, n >= 12): the circuit is cut into 5-qubit blocks;
+// a dense block (more than half of its 1024 entries nonzero) is a real
+// contraction and goes to the tensor cores, and every maximal run of sparse
+// blocks (diagonal or nearly diagonal stretches such as the QFT's controlled
+// phases) goes back to its gates, which the tile planner fuses into shared-memory
+// passes of 12 qubits.  Both kinds of segment start and end in the canonical
+// layout, and applying the blocks in order equals the circuit, so the segments
+// compose.
+qs_status run_auto(State* st, const qs_gate* gates, size_t ngates, qs_stats* stats, KernelTimer& tm) {
+  std::vector<Block> blocks;
+  plan_blocks(gates, ngates, st->n, blocks);
+  size_t i = 0;
+  qs_status s = QS_OK;
+  while (i < blocks.size() && s == QS_OK) {
+    const bool dense = block_nonzeros(blocks[i]) > 512;
+    size_t j = i;
+    while (j < blocks.size() && (block_nonzeros(blocks[j]) > 512) == dense) ++j;
+    if (dense) {
+      std::vector<Block> seg(std::make_move_iterator(blocks.begin() + (long)i),
+                             std::make_move_iterator(blocks.begin() + (long)j));
+      s = run_block_list(st, seg, 1, stats, tm);
+    } else {
+      std::vector<qs_gate> seg;
+      for (size_t k = i; k < j; ++k)
+        for (size_t gi : blocks[k].gate_idx) seg.push_back(gates[gi]);
+      std::vector<FOp> fops;
+      std::vector<int> vmap;
+      build_fused_ops(seg.data(), seg.size(), st->n, fops, vmap, /*fuse=*/true, /*relabel=*/true);
+      qs_stats part;
+      std::memset(&part, 0, sizeof(part));
+      s = run_tiled<float>(st, fops, vmap, &part, tm);
+      if (stats) {
+        stats->ops_fused += part.ops_fused;
+        stats->passes += part.passes;
+        stats->launches += part.launches;
+        stats->tile_launches += part.tile_launches;
+        stats->tile_flops += part.tile_flops;
+        stats->flops += part.flops;
+        stats->upload_bytes += part.upload_bytes;
+      }
+    }
+    i = j;
+  }
+  if (s == QS_OK) {   // the tile segments run asynchronously; report their faults here too
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+  }
+  return s;
 }
 
 qs_status check_state(qs_state_t st) {
@@ -623,10 +675,13 @@ qs_status adjoint_tiled(State* st, void* lam, const qs_gate* gates, size_t g0, s
 qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats,
                       int flags) {
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  if (method < QS_METHOD_TILED || method > QS_METHOD_BLOCKS_BF16) {
+  if (method < QS_METHOD_TILED || method > QS_METHOD_AUTO) {
     set_error("unknown method %d", method);
     return QS_EINVAL;
   }
+  // AUTO: blocks and tile passes where the state allows the blocks, else tiles
+  const bool autom = method == QS_METHOD_AUTO && st->prec == QS_C64 && st->n >= kTileBits;
+  if (method == QS_METHOD_AUTO && !autom) method = QS_METHOD_TILED;
   const bool blocks = method == QS_METHOD_BLOCKS_TF32 || method == QS_METHOD_BLOCKS_BF16;
   if (blocks && (st->prec != QS_C64 || st->n < kTileBits)) {
     set_error("the tensor-core block method needs a complex64 state of at least %d qubits", kTileBits);
@@ -640,7 +695,9 @@ qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method
   tm.on = (flags & QS_OPT_TIME_KERNELS) != 0;
   tm.stream = st->stream;
   qs_status s;
-  if (blocks) {
+  if (autom) {
+    s = run_auto(st, gates, ngates, stats, tm);
+  } else if (blocks) {
     s = run_blocks(st, gates, ngates, method == QS_METHOD_BLOCKS_TF32 ? 0 : 1, stats, tm);
   } else if (method == QS_METHOD_PLAIN) {
     build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/false, /*relabel=*/false);
@@ -805,7 +862,7 @@ qs_status sv_apply_circuit(qs_state_t st, const qs_gate* gates, size_t ngates, c
   if (s != QS_OK) return s;
   s = validate_gates(gates, ngates, st->n);
   if (s != QS_OK) return s;
-  return apply_gates(st, gates, ngates, opts ? opts->method : QS_METHOD_TILED, stats,
+  return apply_gates(st, gates, ngates, opts ? opts->method : QS_METHOD_AUTO, stats,
                      opts ? opts->flags : 0);
 }
 

@@ -157,6 +157,7 @@ void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>&
       apply_to_block(b.U, m, dim, local(g.q[0]), dim == 4 ? local(g.q[1]) : -1);
     }
     b.ngates = (int)sel.size();
+    b.gate_idx = sel;
     out.push_back(std::move(b));
     // the rest, in order (sel is a subsequence of remaining)
     std::vector<size_t> rest;
@@ -171,6 +172,12 @@ void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>&
     }
     remaining.swap(rest);
   }
+}
+
+int block_nonzeros(const Block& b) {
+  int nz = 0;
+  for (const cd& u : b.U) nz += std::abs(u) > 0.0 ? 1 : 0;
+  return nz;
 }
 
 }  // namespace qs

@@ -209,7 +209,10 @@ struct Block {
   int q[5];              // qubits (bit positions); q[i] is bit i of the block's local index
   std::vector<cd> U;     // 32x32 row-major, U[out][in]
   int ngates = 0;
+  std::vector<size_t> gate_idx;   // the gates it absorbed (indices into the circuit, in order)
 };
+// entries of a block with |U_ij| > 0 (dense: more than half of the 1024)
+int block_nonzeros(const Block& b);
 // Greedy frontier fusion of the circuit into 5-qubit blocks (n >= 5).
 void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>& out);
 // Tile of a block pass: 12 positions = 5 block qubits + 7 row qubits; the

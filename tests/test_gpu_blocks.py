@@ -126,3 +126,52 @@ def test_blocks_reject_unsupported(qs):
         qs.sv_apply_circuit(st, [("H", (0,), (), None)], 2)
     assert e.value.status == qs.QS_EUNSUPPORTED
     st.close()
+
+
+# ---------------------------------------------------------------- the default method
+def test_auto_dense_circuit_uses_blocks(qs):
+    # layered Haar + CZ: every block is dense, so the default equals the BF16 blocks
+    n = 18
+    ops = W.layered_haar_cz(n, 20, seed=77)
+    ref = SV.apply_circuit(SV.basis(n), n, ops)
+    out, st = _run(qs, n, ops, qs.METHOD_AUTO)
+    outb, stb = _run(qs, n, ops, 3)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-5
+    assert np.linalg.norm(out - outb) / np.linalg.norm(ref) <= 2e-6
+    assert st["passes"] <= stb["passes"] + 2 and st["tile_launches"] <= 2
+
+
+@pytest.mark.parametrize("n", [13, 17])
+def test_auto_sparse_circuit_uses_tiles(qs, n):
+    # the QFT's blocks are nearly diagonal (one or two Hadamards among phases):
+    # tile passes only, as the tiled method
+    J = W.random_basis_index(n, 2002 + n)
+    ops = W.qft_circuit(n)
+    st = qs.State(n, qs.QS_C64)
+    qs.sv_set_basis(st, J)
+    stats = qs.sv_apply_circuit(st, ops, qs.METHOD_AUTO)
+    out = qs.sv_copy_out(st)
+    st.close()
+    ref = SV.qft_amplitudes(n, J)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-5
+    assert stats["tile_launches"] >= 1 and stats["passes"] <= 8
+
+
+def test_auto_mixed_circuit(qs):
+    # dense layers, then a QFT, then dense layers again: both segment kinds in one
+    # call, composed in the canonical layout; against the oracle
+    n = 16
+    g = W.rng(5)
+    psi0 = W.random_state(n, g)
+    ops = W.layered_haar_cz(n, 6, seed=1) + W.qft_circuit(n) + W.layered_haar_cz(n, 6, seed=2)
+    ref = SV.apply_circuit(psi0.astype(np.complex64).astype(np.complex128), n, ops)
+    out, stats = _run(qs, n, ops, qs.METHOD_AUTO, psi0=psi0)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-5
+    assert stats["tile_launches"] >= 1 and stats["passes"] > stats["tile_launches"]
+    # complex128 states take the tile path
+    st = qs.State(n, qs.QS_C128)
+    qs.sv_copy_in(st, psi0)
+    s128 = qs.sv_apply_circuit(st, ops, qs.METHOD_AUTO)
+    out128 = qs.sv_copy_out(st)
+    st.close()
+    assert np.max(np.abs(out128 - SV.apply_circuit(psi0, n, ops))) <= 1e-12

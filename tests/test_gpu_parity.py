@@ -118,7 +118,7 @@ def test_permutations_30_qubits_sampled_bit_exact(qs):
            + _perm_circuit(n, 60, 700))
     st = qs.State(n, 0)
     qs.sv_copy_in(st, buf)
-    qs.sv_apply_circuit(st, ops)
+    qs.sv_apply_circuit(st, ops, qs.METHOD_TILED)
     qs.sv_copy_out(st, buf)
     st.close()
     K = np.sort(W.rng(701).integers(0, N, size=1 << 16))
