@@ -569,7 +569,10 @@ def run_ours(args, world, rank, local, noisy_inputs=None):
 
 # ---------------------------------------------------------------- other rows (extra keys)
 def extra_small_circuits(qs, torch):
-    """10-qubit complex128 circuits (20 layers Haar + CNOT matching), all 1024 probabilities."""
+    """10-qubit complex128 circuits (20 layers Haar + CNOT matching, seed 1001), all 1024
+    probabilities: one circuit at a time through the state API (latency; the whole circuit
+    runs in one CTA, bound by that SM's FP64 rate), and 4000 submissions through a server
+    whose persistent packed kernel runs them side by side (throughput)."""
     import workloads as W
     ops = qs.gates_array(W.layered_haar_cnot(10, 20, seed=1001))
     st = qs.State(10, qs.QS_C128)
@@ -588,9 +591,23 @@ def extra_small_circuits(qs, torch):
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / reps
     st.close()
-    return {"workload": "10-qubit complex128, 20 layers Haar + CNOT matching, 1024 probabilities",
-            "us_per_circuit": dt * 1e6, "circuits_per_s": 1.0 / dt,
-            "note": "host-launch bound (planner + 3 launches per circuit)"}
+    res = {"workload": "10-qubit complex128, 20 layers Haar + CNOT matching, 1024 probabilities",
+           "one_at_a_time": {"us_per_circuit": dt * 1e6, "circuits_per_s": 1.0 / dt}}
+    count = 4000
+    for ctas in (16, 64):
+        srv = qs.Server(prec=qs.QS_C128, small_max_qubits=10, persistent_ctas=ctas)
+        srv.wait(srv.submit(10, ops, 0))     # first launch
+        t0 = time.perf_counter()
+        tickets = [srv.submit(10, ops, 0) for _ in range(count)]
+        for t in tickets:
+            srv.wait(t)
+        wall = time.perf_counter() - t0
+        stt = srv.stats()
+        srv.close()
+        res[f"server_{ctas}_ctas"] = {"circuits": count, "us_per_circuit": wall / count * 1e6,
+                                      "circuits_per_s": count / wall, "p50_ms": stt["p50_ms"],
+                                      "p99_ms": stt["p99_ms"], "packed_launches": stt["packed_launches"]}
+    return res
 
 
 def extra_noisy_batch(qs, torch, inputs):
@@ -1143,61 +1160,86 @@ def extra_fp64(qs, torch, seed=SEED):
     return out
 
 
-def extra_serving(qs, torch, count=40, seed=5001, rate_hz=None):
-    """Poisson stream of layered Haar+CZ circuits, n~U{8..28}, depth~U{10..200}."""
+def extra_serving(qs, torch, count=1000, pool=100, seed=5001, rate_hz=None):
+    """Poisson stream of `count` arrivals of layered Haar + brickwork-CZ circuits, n~U{8..28},
+    depth~U{10..200}, complex64, marginal over <= 10 qubits.  The arrivals draw (seeded) from a
+    pool of `pool` distinct circuits, which the host builds once.  Compared with a one-at-a-time
+    plain per-gate server under the same arrivals: its service times are measured on the first
+    40 pool circuits and, for the rest, taken from a least-squares fit of time against
+    gates x 2^n (the plain path sweeps the state once per gate)."""
     import numpy as np
 
     import workloads as W
-    stream = W.serving_stream(count, seed=seed, rate_hz=1.0)
-    circuits = [qs.gates_array(W.layered_haar_cz(n, d, seed=cs)) for _, n, d, cs in stream]
-    masks = [(1 << min(n, 10)) - 1 for _, n, _, _ in stream]
-    # one-at-a-time plain per-gate service times (same circuits, sequential)
-    service = []
-    for (_, n, _, _), g, m in zip(stream, circuits, masks):
+    spec = W.serving_stream(pool, seed=seed, rate_hz=1.0)
+    circuits = [qs.gates_array(W.layered_haar_cz(n, d, seed=cs)) for _, n, d, cs in spec]
+    nq = [n for _, n, _, _ in spec]
+    masks = [(1 << min(n, 10)) - 1 for n in nq]
+    pick = W.rng(seed + 1).integers(0, pool, size=count)
+    # one-at-a-time plain per-gate service times
+    service = {}
+    for i in range(min(40, pool)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = qs.State(n, qs.QS_C64)
-        qs.sv_apply_circuit(st, g, qs.METHOD_PLAIN)
-        qs.sv_probs(st, fp64=True, marg_mask=m if n > 10 else 0)
+        st = qs.State(nq[i], qs.QS_C64)
+        qs.sv_apply_circuit(st, circuits[i], qs.METHOD_PLAIN)
+        qs.sv_probs(st, fp64=True, marg_mask=masks[i] if nq[i] > 10 else 0)
         torch.cuda.synchronize()
-        service.append(time.perf_counter() - t0)
+        service[i] = time.perf_counter() - t0
         st.close()
-    cap = count / sum(service)
-    # fused server: warm up, then the stream at ~80% of the fused server's capacity
+    x = np.array([len(circuits[i]) * 2.0 ** nq[i] for i in service])
+    y = np.array([service[i] for i in service])
+    A = np.stack([x, np.ones_like(x)], axis=1)
+    coef = np.linalg.lstsq(A, y, rcond=None)[0]
+    for i in range(pool):
+        if i not in service:
+            service[i] = float(max(coef[0] * len(circuits[i]) * 2.0 ** nq[i] + coef[1], 1e-5))
+    plain_service = [service[int(c)] for c in pick]
+    # the fused server: capacity on a burst of the whole stream, then the Poisson stream at
+    # ~80% of it
     srv = qs.Server()
     t0 = time.perf_counter()
-    for (_, n, _, _), g, m in zip(stream, circuits, masks):
-        srv.wait(srv.submit(n, g, m))
-    fused_cap = count / (time.perf_counter() - t0)
+    for t in [srv.submit(nq[c], circuits[c], masks[c]) for c in pick[:200]]:
+        srv.wait(t)
+    fused_cap = 200 / (time.perf_counter() - t0)
     srv.close()
     rate = rate_hz or 0.8 * fused_cap
-    gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=count)
+    gaps = W.rng(seed + 2).exponential(1.0 / rate, size=count)
     srv = qs.Server()
-    tickets = []
+    tickets, arrivals = [], []
     t_start = time.perf_counter()
-    arrivals = []
-    for i, ((_, n, _, _), g, m) in enumerate(zip(stream, circuits, masks)):
+    for i, c in enumerate(pick):
         target = t_start + float(np.sum(gaps[: i + 1]))
         while time.perf_counter() < target:
             time.sleep(min(0.0005, max(0.0, target - time.perf_counter())))
         arrivals.append(time.perf_counter() - t_start)
-        tickets.append(srv.submit(n, g, m))
-    lats = [srv.wait(t)[1] for t in tickets]
+        tickets.append(srv.submit(nq[c], circuits[c], masks[c]))
+    results = [srv.wait(t) for t in tickets]
     stats = srv.stats()
     srv.close()
-    # one-at-a-time plain server under the same arrivals (FIFO queue, measured service times)
+    # each pool circuit's result is the same wherever it fell in the mix
+    first, worst = {}, 0.0
+    for c, (res, _) in zip(pick, results):
+        c = int(c)
+        if c in first:
+            worst = max(worst, float(np.max(np.abs(res - first[c]))))
+        else:
+            first[c] = res
     done, plain_lat = 0.0, []
-    for a, s in zip(arrivals, service):
-        done = max(done, a) + s
+    for a, sv in zip(arrivals, plain_service):
+        done = max(done, a) + sv
         plain_lat.append(1e3 * (done - a))
-    return {"workload": f"{count} Poisson arrivals at {rate:.1f}/s (80% of fused capacity), "
-                        f"n~U{{8..28}}, depth~U{{10..200}}, complex64, marginal over <=10 qubits",
+    return {"workload": f"{count} Poisson arrivals at {rate:.1f}/s (80% of the fused server's burst "
+                        f"capacity), drawn from {pool} circuits n~U{{8..28}}, depth~U{{10..200}}, complex64, "
+                        f"marginal over <=10 qubits",
             "circuits_per_s": stats["circuits_per_s"], "p50_ms": stats["p50_ms"],
-            "p99_ms": stats["p99_ms"], "packed_launches": stats["packed_launches"],
-            "packed_circuits": stats["packed_circuits"], "large_circuits": stats["large_circuits"],
-            "plain_one_at_a_time": {"capacity_circuits_per_s": cap,
+            "p99_ms": stats["p99_ms"], "mean_ms": stats["mean_ms"], "completed": stats["completed"],
+            "packed_launches": stats["packed_launches"], "packed_circuits": stats["packed_circuits"],
+            "large_circuits": stats["large_circuits"], "idle_timeouts": stats["idle_timeouts"],
+            "same_result_in_the_mix_max_abs": worst,
+            "plain_one_at_a_time": {"capacity_circuits_per_s": count / sum(plain_service),
                                     "p50_ms": float(np.percentile(plain_lat, 50)),
-                                    "p99_ms": float(np.percentile(plain_lat, 99))},
+                                    "p99_ms": float(np.percentile(plain_lat, 99)),
+                                    "service_times": "measured on 40 circuits, fitted for the rest"},
             "fused_capacity_circuits_per_s": fused_cap}
 
 

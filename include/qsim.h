@@ -267,25 +267,34 @@ qs_status dm_apply_channels(const qs_dm_batch* batch, float* probs, double* logl
                             void* stream);
 
 /* ---- serving: continuous batching of circuits ----------------------------
- * A server owns a scheduler thread.  Submitted circuits (each from |0...0>,
- * result = marginal outcome probabilities over marg_mask, the Born rule of
- * section "Quantum circuits") are admitted as device memory and slots free
- * up, while earlier ones are still running:
- *   - circuits with n <= small_max_qubits are packed into one launch (one CTA
- *     per circuit, its whole state in shared memory); a new packed launch
- *     starts whenever the previous one has finished and circuits wait;
+ * A server owns a scheduler thread and max_inflight worker threads.  Submitted
+ * circuits (each from |0...0>, result = marginal outcome probabilities over
+ * marg_mask, the Born rule of section "Quantum circuits") are admitted as device
+ * memory and slots free up, while earlier ones are still running:
+ *   - circuits with n <= small_max_qubits go through one persistent packed
+ *     kernel of persistent_ctas CTAs fed by a device-visible work queue in
+ *     mapped host memory: each CTA takes the next published circuit, runs it on
+ *     a state held in its shared memory and publishes the result; a CTA that
+ *     finds no work waits at most idle_ms, then the kernel ends reporting
+ *     QS_ETIMEOUT in its status word (counted in qs_server_stats.idle_timeouts)
+ *     and is launched again when work arrives.  It also ends after 50 ms, and
+ *     while it may run the tensor-core block passes of this library leave
+ *     persistent_ctas SMs (at most half of them) free;
  *   - larger circuits get a resident state (stream-ordered allocation within
- *     mem_budget) and run the tiled pass pipeline on one of max_inflight
- *     streams, overlapping with each other and with the packed launches.
- * Latency = completion seen by the scheduler - submission time. */
+ *     mem_budget) on a worker's stream and run the default method
+ *     (QS_METHOD_AUTO; QS_METHOD_TILED with large_tiled = 1), overlapping with
+ *     each other and with the packed kernel.
+ * Latency = completion seen by the server - submission time. */
 typedef struct qs_server_s* qs_server_t;
 
 typedef struct {
   int32_t prec;              /* QS_C64 or QS_C128 */
   int32_t small_max_qubits;  /* <= 14 (QS_C64) / 13 (QS_C128); 0 = largest allowed */
   int32_t max_inflight;      /* large circuits on the device at once; 0 = 4 */
-  int32_t max_batch;         /* circuits per packed launch; 0 = 1024 */
+  int32_t persistent_ctas;   /* CTAs of the persistent packed kernel; 0 = 16 */
   uint64_t mem_budget;       /* device bytes for resident states; 0 = 80% of free memory */
+  int32_t idle_ms;           /* the packed kernel's bounded wait for work; 0 = 5 ms */
+  int32_t large_tiled;       /* 1: large circuits on QS_METHOD_TILED instead of QS_METHOD_AUTO */
 } qs_server_config;
 
 typedef struct {
@@ -294,6 +303,7 @@ typedef struct {
   double wall_s;             /* first submission to last completion */
   double circuits_per_s;
   uint64_t peak_bytes;       /* largest resident-state footprint */
+  int64_t idle_timeouts;     /* launches of the packed kernel that ended by its idle limit */
 } qs_server_stats;
 
 qs_status qs_server_create(const qs_server_config* cfg, qs_server_t* out);
@@ -308,12 +318,12 @@ qs_status qs_server_wait(qs_server_t s, int64_t ticket, double* result, double* 
 qs_status qs_server_stats_get(qs_server_t s, qs_server_stats* out);
 /* Waits for all submitted circuits, stops the scheduler, frees everything. */
 qs_status qs_server_destroy(qs_server_t s);
-/* Testing hook for the scheduler's error path: the next completion query of a
- * running packed launch or large circuit reports cuda_error (a cudaError_t
- * value other than cudaSuccess and cudaErrorNotReady) instead of asking the
- * device.  A query that reports an error completes that work: its circuits'
- * qs_server_wait returns QS_ECUDA with the error's name, and their slot and
- * memory are released.  Errors: QS_EINVAL. */
+/* Testing hook for the scheduler's error path: the next completion query of the
+ * running persistent packed kernel reports cuda_error (a cudaError_t value other
+ * than cudaSuccess and cudaErrorNotReady) instead of asking the device.  A query
+ * that reports an error completes the queued small circuits with it: their
+ * qs_server_wait returns QS_ECUDA with the error's name, and the queue starts
+ * over.  Errors: QS_EINVAL. */
 qs_status qs_server_inject_query_error(qs_server_t s, int cuda_error);
 
 /* The check of QS_DM_VALIDATE on HOST arrays: count n-qubit PTMs (n = 1 or 2,

@@ -84,8 +84,9 @@ class GstBatch(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("small_max_qubits", ctypes.c_int32),
-                ("max_inflight", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("mem_budget", ctypes.c_uint64)]
+                ("max_inflight", ctypes.c_int32), ("persistent_ctas", ctypes.c_int32),
+                ("mem_budget", ctypes.c_uint64), ("idle_ms", ctypes.c_int32),
+                ("large_tiled", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -94,7 +95,8 @@ class ServerStats(ctypes.Structure):
                 ("large_circuits", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double),
-                ("circuits_per_s", ctypes.c_double), ("peak_bytes", ctypes.c_uint64)]
+                ("circuits_per_s", ctypes.c_double), ("peak_bytes", ctypes.c_uint64),
+                ("idle_timeouts", ctypes.c_int64)]
 
 
 _lib = None
@@ -169,10 +171,12 @@ class Server:
     """Continuous-batching circuit server (native scheduler thread; see qsim.h)."""
 
     def __init__(self, prec: int = QS_C64, small_max_qubits: int = 0, max_inflight: int = 0,
-                 max_batch: int = 0, mem_budget: int = 0):
+                 persistent_ctas: int = 0, mem_budget: int = 0, idle_ms: int = 0,
+                 large_tiled: bool = False):
         lib = load()
         _torch()
-        cfg = ServerConfig(prec, small_max_qubits, max_inflight, max_batch, mem_budget)
+        cfg = ServerConfig(prec, small_max_qubits, max_inflight, persistent_ctas, mem_budget, idle_ms,
+                           1 if large_tiled else 0)
         h = ctypes.c_void_p()
         _check(lib.qs_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "internal.h"
@@ -1157,7 +1158,8 @@ qs_status launch_block_pass(State* st, const BlockPass& host_pass, const void* p
   static_assert(pipe_smem_bytes<BM_BF16>() > 120 * 1024, "one CTA per SM");
   static_assert(pipe_smem_bytes<BM_TF32>() <= 224 * 1024, "shared memory per CTA");
   static_assert(pipe_smem_bytes<BM_BF16>() <= 224 * 1024, "shared memory per CTA");
-  uint64_t grid = (uint64_t)sms;
+  // a CTA needs a whole SM: leave the SMs a server's persistent kernel may hold
+  uint64_t grid = (uint64_t)std::max(1, sms - reserved_sms());
   if (grid > ntiles) grid = ntiles;
   const bool box = (host_pass.flags & 2) != 0;
   auto launch = [&](auto kern, size_t smem) -> qs_status {

@@ -263,6 +263,10 @@ double ptm_choi_min_eigenvalue(const double* G, int n);
 // first matrix that is not trace preserving or not completely positive.
 qs_status ptm_validate(const double* ptms, int n, int count, const char* what, int* bad_index);
 
+// SMs that block passes leave free while persistent packed kernels of servers
+// may run (serve.cu)
+int reserved_sms();
+
 // Applies gates to a state (the body of sv_apply_circuit; api.cpp).
 qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method, qs_stats* stats,
                       int flags = 0);

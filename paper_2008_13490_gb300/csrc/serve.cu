@@ -1,18 +1,33 @@
 // Serving loop: continuous batching of state-vector circuits on one GPU.
 //
-// A scheduler thread owns every CUDA call of a server.  Circuits arrive
-// through qs_server_submit at any time; each scheduler iteration
-//   1. retires finished work (CUDA events), records latencies, frees states;
-//   2. admits waiting circuits while slots and device memory allow:
-//      - small circuits (n <= small_max_qubits) go into the next packed launch,
-//        one CTA per circuit with the whole state in shared memory, started as
-//        soon as the previous packed launch has finished;
-//      - larger circuits get a resident state allocated stream-ordered on one
-//        of max_inflight streams, within mem_budget, and run the tiled pass
-//        pipeline there, overlapping with the other streams;
-//   3. sleeps briefly when nothing changed.
-// The result of a circuit is the marginal outcome distribution over its mask
-// (Born rule), copied to pinned host memory before its completion event.
+// Small circuits (n <= small_max_qubits) go through one persistent packed
+// kernel fed by a work queue that lives in page-locked, device-mapped host
+// memory:
+//   - the scheduler thread fuses a circuit's gates on the host, writes its ops
+//     into an op arena and a job descriptor into a ring, and publishes the job by
+//     advancing the ring's tail (a release store);
+//   - each CTA of the persistent kernel claims the next published job with an
+//     atomic on a device counter, stages its ops in shared memory, runs the
+//     whole circuit on a state held in shared memory, reduces the marginal
+//     outcome probabilities (Born rule, FP64 accumulation) into a result arena,
+//     and sets the job's done word (a release store at system scope), which the
+//     scheduler polls;
+//   - a CTA that finds no published job waits at most idle_ms (a globaltimer
+//     deadline), then ends and the kernel reports QS_ETIMEOUT in its status word;
+//     the scheduler counts it and launches the kernel again when work arrives.
+//     The kernel also ends after a maximum lifetime (50 ms), which offers its SMs
+//     to tensor-core block passes waiting for whole SMs.
+// While the persistent kernel may run it holds up to persistent_ctas SMs, and the
+// block passes of the library leave that many SMs free.
+//
+// Larger circuits are admitted as device memory and worker slots free up: each of
+// max_inflight worker threads owns a stream, creates a resident state (stream-
+// ordered allocation within mem_budget), applies the gates with the default
+// method (QS_METHOD_AUTO: dense blocks on the tensor cores, the rest in tile
+// passes; QS_METHOD_TILED when configured) and reads back the marginal.  The
+// packed kernel and the workers overlap on the device.
+// Latency = completion seen by the scheduler (small) or the worker (large) -
+// submission time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,45 +44,132 @@
 #include "internal.h"
 
 namespace qs {
+
+// SMs the block passes leave free for running persistent packed kernels
+std::atomic<int> g_reserved_sms{0};
+int reserved_sms() { return g_reserved_sms.load(); }
+
 namespace {
 
 constexpr int kMaxMargBits = 12;
+constexpr int kOpChunk = 32;             // ops staged in shared memory at a time
+constexpr int64_t kRing = 4096;          // job ring entries
+constexpr int64_t kOpArena = 1 << 19;    // ops in the op arena
+constexpr int64_t kResArena = 1 << 22;   // doubles in the result arena
+constexpr uint64_t kLifeNs = 50000000ull;
 
-struct SmallJob {
-  int32_t n, k;
-  int32_t op_begin, op_count;
-  int64_t out_off;
-  uint8_t bits[16];   // marginal bit positions
+struct alignas(16) PJob {
+  int32_t n, k, nops, pad;
+  int64_t op_off;    // first op of the job in the op arena
+  int64_t out_off;   // first double of its marginal in the result arena
+  uint8_t bits[16];  // bit positions of the marginal
 };
 
-// One CTA per small circuit: |0...0>, all its ops in shared memory, marginal
-// probabilities (fp64 accumulation) written to out.
+struct PCtl {        // written by the host, read by the kernel
+  uint64_t tail;     // jobs published so far
+  uint32_t stop;     // nonzero: CTAs end instead of waiting
+  uint32_t pad[13];
+};
+
+__device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_sys(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256)
-    packed_small_kernel(const SmallJob* __restrict__ jobs, const PlainOp<R>* __restrict__ ops,
-                        double* __restrict__ out, int max_n) {
+    packed_persistent_kernel(const PCtl* __restrict__ ctl, const PJob* __restrict__ jobs,
+                             const PlainOp<R>* __restrict__ ops, double* __restrict__ results,
+                             uint32_t* __restrict__ done, unsigned long long* __restrict__ head,
+                             int* __restrict__ status, int max_n, uint64_t idle_ns, uint64_t life_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<R>* sm = reinterpret_cast<C2<R>*>(smem_raw);
   double* hist = reinterpret_cast<double*>(smem_raw + (sizeof(C2<R>) << max_n));
-  const SmallJob job = jobs[blockIdx.x];
-  const int N = 1 << job.n, H = 1 << job.k;
-  for (int J = threadIdx.x; J < N; J += blockDim.x) {
-    C2<R> z;
-    z.x = R(J == 0 ? 1 : 0);
-    z.y = R(0);
-    sm[J] = z;
+  PlainOp<R>* chunk = reinterpret_cast<PlainOp<R>*>(smem_raw + (sizeof(C2<R>) << max_n) +
+                                                    (sizeof(double) << kMaxMargBits));
+  __shared__ long long s_job;
+  __shared__ PJob s_desc;
+  const uint64_t born = gtimer();
+  for (;;) {
+    if (threadIdx.x == 0) {
+      // claim the next published job; wait for one at most idle_ns
+      long long got = -1;
+      const uint64_t t0 = gtimer();
+      for (;;) {
+        const unsigned long long h = atomicAdd(head, 0ull);
+        const uint64_t tail = ld_acquire_sys(&ctl->tail);
+        if (h < tail) {
+          if (atomicCAS(head, h, h + 1ull) == h) {
+            got = (long long)h;
+            break;
+          }
+          continue;
+        }
+        const uint64_t now = gtimer();
+        if (ld_relaxed_sys(&ctl->stop) != 0u || now - born > life_ns) break;
+        if (now - t0 > idle_ns) {   // no producer within the limit
+          atomicMax(status, (int)QS_ETIMEOUT);
+          break;
+        }
+        __nanosleep(256);
+      }
+      s_job = got;
+      if (got >= 0) {   // written before the tail it was published with; read past the caches
+        const uint4* src = reinterpret_cast<const uint4*>(jobs + got % kRing);
+        uint4* dst = reinterpret_cast<uint4*>(&s_desc);
+        for (int w = 0; w < (int)(sizeof(PJob) / 16); ++w) dst[w] = __ldcv(src + w);
+      }
+    }
+    __syncthreads();
+    const long long j = s_job;
+    if (j < 0) return;
+    const PJob job = s_desc;
+    const int N = 1 << job.n, H = 1 << job.k;
+    for (int J = threadIdx.x; J < N; J += blockDim.x) {
+      C2<R> z;
+      z.x = R(J == 0 ? 1 : 0);
+      z.y = R(0);
+      sm[J] = z;
+    }
+    for (int i = threadIdx.x; i < H; i += blockDim.x) hist[i] = 0.0;
+    // the ops in chunks: a coalesced copy into shared memory, then applied in order
+    for (int o0 = 0; o0 < job.nops; o0 += kOpChunk) {
+      const int cnt = min(kOpChunk, job.nops - o0);
+      const uint4* src = reinterpret_cast<const uint4*>(ops + job.op_off + o0);
+      uint4* dst = reinterpret_cast<uint4*>(chunk);
+      const int words = cnt * (int)(sizeof(PlainOp<R>) / 16);
+      __syncthreads();   // nobody reads the previous chunk any more
+      for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = __ldcv(src + w);
+      __syncthreads();
+      small_apply_ops(sm, job.n, chunk, cnt);
+    }
+    __syncthreads();
+    for (int J = threadIdx.x; J < N; J += blockDim.x) {
+      const C2<R> a = sm[J];
+      int K = 0;
+      for (int i = 0; i < job.k; ++i) K |= ((J >> job.bits[i]) & 1) << i;
+      atomicAdd(hist + K, (double)a.x * (double)a.x + (double)a.y * (double)a.y);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < H; i += blockDim.x) results[job.out_off + i] = hist[i];
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release_sys(done + (j % kRing), (uint32_t)(j + 1));
   }
-  for (int i = threadIdx.x; i < H; i += blockDim.x) hist[i] = 0.0;
-  __syncthreads();
-  small_apply_ops(sm, job.n, ops + job.op_begin, job.op_count);
-  for (int J = threadIdx.x; J < N; J += blockDim.x) {
-    const C2<R> a = sm[J];
-    int K = 0;
-    for (int i = 0; i < job.k; ++i) K |= ((J >> job.bits[i]) & 1) << i;
-    atomicAdd(hist + K, (double)a.x * (double)a.x + (double)a.y * (double)a.y);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < H; i += blockDim.x) out[job.out_off + i] = hist[i];
 }
 
 double now_s() {
@@ -84,10 +186,17 @@ struct Req {
   qs_status status = QS_OK;
   std::string err;
   std::vector<double> result;
-  // large circuits in flight
-  qs_state_t st = nullptr;
-  int slot = -1;
-  size_t bytes = 0;
+  size_t bytes = 0;          // large circuits: admitted device bytes
+};
+
+// a published small job (the scheduler's own record; its Req may be gone once
+// the job is finished and waited for)
+struct QJob {
+  Req* r = nullptr;          // null once finished
+  int64_t job = 0;
+  int k = 0;
+  int64_t out_off = 0;
+  int64_t op_start = 0, res_start = 0;   // arena counters where its ranges began
 };
 
 // stream-ordered allocator for resident states
@@ -101,38 +210,56 @@ void* async_alloc(size_t bytes, void* stream, void*) {
 }
 void async_free(void* p, size_t, void* stream, void*) { cudaFreeAsync(p, (cudaStream_t)stream); }
 
+// a contiguous range of `want` entries of a ring arena of `cap` entries with
+// monotonic counters head (next free) and tail (oldest in use); a range never
+// wraps (it starts over at entry 0 instead)
+bool arena_take(int64_t& head, int64_t tail, int64_t cap, int64_t want, int64_t* at) {
+  const int64_t pos = head % cap;
+  const int64_t pad = pos + want > cap ? cap - pos : 0;
+  if (want > cap || head + pad + want - tail > cap) return false;
+  *at = (head + pad) % cap;
+  head += pad + want;
+  return true;
+}
+
 }  // namespace
 
 struct Server {
   qs_server_config cfg{};
-  int device = 0;
-  std::thread worker;
+  int device = 0, sms = 152;
+  std::thread scheduler;
+  std::vector<std::thread> workers;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  bool stop = false;
-  std::deque<Req*> pending;
+  std::condition_variable cv_work, cv_done, cv_large;
+  bool stop = false, stop_workers = false;
+  std::deque<Req*> pending;          // submitted, not yet admitted
+  std::deque<Req*> large_queue;      // admitted large circuits waiting for a worker
   std::unordered_map<int64_t, Req*> reqs;
   int64_t next_id = 1;
-  // large circuits
-  std::vector<cudaStream_t> streams;
-  std::vector<Req*> slot_req;
-  std::vector<cudaEvent_t> slot_ev;
-  std::vector<double*> slot_host;   // pinned results
   uint64_t bytes_in_use = 0, peak_bytes = 0;
-  // packed launches
-  cudaStream_t small_stream = nullptr;
-  cudaEvent_t batch_ev = nullptr;
-  std::vector<Req*> batch;
-  bool batch_busy = false;
-  void* d_buf = nullptr;
-  size_t d_buf_bytes = 0;
-  unsigned char* h_buf = nullptr;   // pinned: descriptors up, results down
-  size_t h_buf_bytes = 0;
-  size_t batch_out_off = 0;
+  int large_running = 0;
+  // persistent packed kernel and its queue
+  cudaStream_t pk_stream = nullptr;
+  cudaEvent_t pk_ev = nullptr;
+  bool pk_running = false;
+  int pk_reserved = 0;
+  size_t pk_smem = 0, op_size = 0;
+  PCtl* ctl = nullptr;               // mapped host memory from here ...
+  PJob* jobs = nullptr;
+  uint32_t* done_words = nullptr;
+  unsigned char* op_arena = nullptr;
+  double* res_arena = nullptr;       // ... to here
+  unsigned long long* d_head = nullptr;
+  int* d_status = nullptr;
+  int64_t published = 0;
+  std::deque<QJob> in_queue;         // published jobs in publish order, until retired from the front
+  int64_t op_head = 0, op_tail = 0, res_head = 0, res_tail = 0;
   // statistics
   std::vector<double> lat_ms;
   double t_first = -1, t_last = 0;
-  int64_t submitted = 0, completed = 0, packed_launches = 0, packed_circuits = 0, large_circuits = 0;
+  int64_t submitted = 0, completed = 0, packed_launches = 0, packed_circuits = 0, large_circuits = 0,
+          idle_timeouts = 0;
+  std::atomic<int> injected_error{0};
 
   void finish(Req* r, qs_status s) {
     r->status = s;
@@ -146,278 +273,264 @@ struct Server {
     cv_done.notify_all();
   }
 
-  qs_status grow_buffers(size_t dev_bytes, size_t host_bytes) {
-    if (dev_bytes > d_buf_bytes) {
-      if (d_buf) cudaFree(d_buf);
-      size_t want = std::max(dev_bytes, 2 * d_buf_bytes);
-      if (cudaMalloc(&d_buf, want) != cudaSuccess) {
-        cudaGetLastError();
-        d_buf = nullptr;
-        d_buf_bytes = 0;
-        set_error("packed-launch buffer allocation failed");
-        return QS_ENOMEM;
-      }
-      d_buf_bytes = want;
-    }
-    if (host_bytes > h_buf_bytes) {
-      if (h_buf) cudaFreeHost(h_buf);
-      size_t want = std::max(host_bytes, 2 * h_buf_bytes);
-      if (cudaMallocHost((void**)&h_buf, want) != cudaSuccess) {
-        cudaGetLastError();
-        h_buf = nullptr;
-        h_buf_bytes = 0;
-        set_error("pinned buffer allocation failed");
-        return QS_ENOMEM;
-      }
-      h_buf_bytes = want;
-    }
-    return QS_OK;
-  }
-
+  // ---------------------------------------------------------------- small circuits
   template <typename R>
-  qs_status start_batch_t(std::vector<Req*>& jobs_in) {
-    std::vector<SmallJob> jobs;
-    std::vector<PlainOp<R>> ops;
-    int max_n = 1, max_k = 0;
-    int64_t out = 0;
+  bool publish_t(Req* r) {
+    const int64_t oldest = in_queue.empty() ? published : in_queue.front().job;
+    if (published - oldest >= kRing) return false;   // ring full
+    std::vector<FOp> fops;
+    std::vector<int> vmap;
+    build_fused_ops(r->gates.data(), r->gates.size(), r->n, fops, vmap, true, false);
+    const int64_t nops = (int64_t)fops.size();
+    const int64_t H = (int64_t)1 << r->k;
+    int64_t oh = op_head, rh = res_head, op_at = 0, res_at = 0;
+    if (!arena_take(oh, op_tail, kOpArena, nops, &op_at) || !arena_take(rh, res_tail, kResArena, H, &res_at))
+      return false;   // wait for finished jobs to free arena space
     auto c2 = [](cd z) {
       C2<R> v;
       v.x = (R)z.real();
       v.y = (R)z.imag();
       return v;
     };
-    for (Req* r : jobs_in) {
-      std::vector<FOp> fops;
-      std::vector<int> vmap;
-      build_fused_ops(r->gates.data(), r->gates.size(), r->n, fops, vmap, true, false);
-      SmallJob j{};
-      j.n = r->n;
-      j.k = r->k;
-      j.op_begin = (int32_t)ops.size();
-      j.op_count = (int32_t)fops.size();
-      j.out_off = out;
-      int kk = 0;
-      for (int b = 0; b < r->n; ++b)
-        if ((r->mask >> b) & 1) j.bits[kk++] = (uint8_t)b;
-      jobs.push_back(j);
-      out += (int64_t)1 << r->k;
-      for (const FOp& o : fops) {
-        PlainOp<R> p;
-        std::memset(&p, 0, sizeof(p));
-        p.type = o.type;
-        p.t = o.t;
-        p.c = o.c;
-        p.a = o.a;
-        p.b = o.b;
-        if (o.type == F_G1) {
-          for (int i = 0; i < 4; ++i) p.m[i] = c2(o.m0[i]);
-        } else if (o.type == F_G1C) {
-          for (int i = 0; i < 4; ++i) p.m[i] = c2(o.m0[i]), p.m[4 + i] = c2(o.m1[i]);
-        } else if (o.type == F_D) {
-          for (int i = 0; i < 4; ++i) p.m[i] = c2(o.d[i]);
-        } else {
-          for (int i = 0; i < 16; ++i) p.m[i] = c2(o.g[i]);
-        }
-        ops.push_back(p);
+    PlainOp<R>* dst = reinterpret_cast<PlainOp<R>*>(op_arena) + op_at;
+    for (int64_t i = 0; i < nops; ++i) {
+      const FOp& o = fops[(size_t)i];
+      PlainOp<R> p;
+      std::memset(&p, 0, sizeof(p));
+      p.type = o.type;
+      p.t = o.t;
+      p.c = o.c;
+      p.a = o.a;
+      p.b = o.b;
+      if (o.type == F_G1) {
+        for (int q = 0; q < 4; ++q) p.m[q] = c2(o.m0[q]);
+      } else if (o.type == F_G1C) {
+        for (int q = 0; q < 4; ++q) p.m[q] = c2(o.m0[q]), p.m[4 + q] = c2(o.m1[q]);
+      } else if (o.type == F_D) {
+        for (int q = 0; q < 4; ++q) p.m[q] = c2(o.d[q]);
+      } else {
+        for (int q = 0; q < 16; ++q) p.m[q] = c2(o.g[q]);
       }
-      max_n = std::max(max_n, r->n);
-      max_k = std::max(max_k, r->k);
+      dst[i] = p;
     }
-    const size_t jb = (sizeof(SmallJob) * jobs.size() + 255) & ~size_t(255);
-    const size_t ob = (sizeof(PlainOp<R>) * ops.size() + 255) & ~size_t(255);
-    const size_t rb = sizeof(double) * (size_t)out;
-    qs_status s = grow_buffers(jb + ob + rb, std::max(jb + ob, rb));
-    if (s != QS_OK) return s;
-    std::memcpy(h_buf, jobs.data(), sizeof(SmallJob) * jobs.size());
-    if (!ops.empty()) std::memcpy(h_buf + jb, ops.data(), sizeof(PlainOp<R>) * ops.size());
-    unsigned char* d = (unsigned char*)d_buf;
-    QS_CUDA(cudaMemcpyAsync(d, h_buf, jb + ob, cudaMemcpyHostToDevice, small_stream));
-    const size_t smem = (sizeof(C2<R>) << max_n) + (sizeof(double) << max_k);
-    if (smem > 48 * 1024)
-      QS_CUDA(cudaFuncSetAttribute(packed_small_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-    packed_small_kernel<R><<<(unsigned)jobs.size(), 256, smem, small_stream>>>(
-        (const SmallJob*)d, (const PlainOp<R>*)(d + jb), (double*)(d + jb + ob), max_n);
-    QS_CUDA(cudaGetLastError());
-    QS_CUDA(cudaMemcpyAsync(h_buf, d + jb + ob, rb, cudaMemcpyDeviceToHost, small_stream));
-    QS_CUDA(cudaEventRecord(batch_ev, small_stream));
-    batch = jobs_in;
-    batch_busy = true;
+    QJob q;
+    q.r = r;
+    q.job = published;
+    q.k = r->k;
+    q.out_off = res_at;
+    q.op_start = op_head;
+    q.res_start = res_head;
+    op_head = oh;
+    res_head = rh;
+    PJob& jd = jobs[published % kRing];
+    jd.n = r->n;
+    jd.k = r->k;
+    jd.nops = (int32_t)nops;
+    jd.pad = 0;
+    jd.op_off = op_at;
+    jd.out_off = res_at;
+    std::memset(jd.bits, 0, sizeof(jd.bits));
+    for (int b = 0, kk = 0; b < r->n; ++b)
+      if ((r->mask >> b) & 1) jd.bits[kk++] = (uint8_t)b;
+    // ops, descriptor and the cleared done word are written before the tail
+    reinterpret_cast<std::atomic<uint32_t>*>(done_words + published % kRing)->store(0u, std::memory_order_relaxed);
+    ++published;
+    reinterpret_cast<std::atomic<uint64_t>*>(&ctl->tail)->store((uint64_t)published, std::memory_order_release);
+    in_queue.push_back(q);
+    ++packed_circuits;
+    return true;
+  }
+  bool publish(Req* r) { return cfg.prec == QS_C64 ? publish_t<float>(r) : publish_t<double>(r); }
+
+  // finished jobs (done word set), in any order; arena space is reclaimed over
+  // the finished prefix of the queue
+  bool retire_small() {
+    bool any = false;
+    // jobs are claimed in publish order and at most persistent_ctas run at a time,
+    // so only the first unfinished ones can have finished
+    int unfinished_seen = 0;
+    for (QJob& q : in_queue) {
+      if (!q.r) continue;
+      if (++unfinished_seen > 2 * cfg.persistent_ctas + 8) break;
+      const uint32_t w =
+          reinterpret_cast<std::atomic<uint32_t>*>(done_words + q.job % kRing)->load(std::memory_order_acquire);
+      if (w != (uint32_t)(q.job + 1)) continue;
+      Req* r = q.r;
+      q.r = nullptr;
+      r->result.assign(res_arena + q.out_off, res_arena + q.out_off + ((int64_t)1 << q.k));
+      finish(r, QS_OK);   // r may be freed by its waiter from here on
+      any = true;
+    }
+    while (!in_queue.empty() && !in_queue.front().r) in_queue.pop_front();
+    op_tail = in_queue.empty() ? op_head : in_queue.front().op_start;
+    res_tail = in_queue.empty() ? res_head : in_queue.front().res_start;
+    return any;
+  }
+
+  qs_status launch_persistent() {
+    QS_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), pk_stream));
+    const int P = cfg.persistent_ctas;
+    pk_reserved = std::min(P, sms / 2);
+    g_reserved_sms.fetch_add(pk_reserved);
+    const uint64_t idle_ns = (uint64_t)cfg.idle_ms * 1000000ull;
+    if (cfg.prec == QS_C64)
+      packed_persistent_kernel<float><<<P, 256, pk_smem, pk_stream>>>(
+          ctl, jobs, reinterpret_cast<const PlainOp<float>*>(op_arena), res_arena, done_words, d_head,
+          d_status, cfg.small_max_qubits, idle_ns, kLifeNs);
+    else
+      packed_persistent_kernel<double><<<P, 256, pk_smem, pk_stream>>>(
+          ctl, jobs, reinterpret_cast<const PlainOp<double>*>(op_arena), res_arena, done_words, d_head,
+          d_status, cfg.small_max_qubits, idle_ns, kLifeNs);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(pk_ev, pk_stream);
+    if (e != cudaSuccess) {
+      g_reserved_sms.fetch_sub(pk_reserved);
+      pk_reserved = 0;
+      return cuda_status(e, "persistent packed kernel launch");
+    }
+    pk_running = true;
     ++packed_launches;
-    packed_circuits += (int64_t)jobs_in.size();
     return QS_OK;
   }
 
-  void start_batch(std::vector<Req*>& jobs) {
-    qs_status s = cfg.prec == QS_C64 ? start_batch_t<float>(jobs) : start_batch_t<double>(jobs);
-    if (s != QS_OK) {
-      cudaStreamSynchronize(small_stream);
-      for (Req* r : jobs) finish(r, s);
-      batch.clear();
-      batch_busy = false;
-    }
-  }
-
-  void finish_batch() {
-    size_t off = 0;
-    for (Req* r : batch) {
-      const size_t H = (size_t)1 << r->k;
-      r->result.assign((double*)h_buf + off, (double*)h_buf + off + H);
-      off += H;
-      finish(r, QS_OK);
-    }
-    batch.clear();
-    batch_busy = false;
-  }
-
-  void start_large(Req* r, int slot) {
-    qs_allocator a{async_alloc, async_free, nullptr};
-    qs_status s = sv_create(r->n, cfg.prec, &a, streams[slot], &r->st);
-    if (s == QS_OK) s = apply_gates(r->st, r->gates.data(), r->gates.size(), QS_METHOD_TILED, nullptr);
-    if (s == QS_OK) {
-      unsigned char* sc = (unsigned char*)r->st->scratch;
-      double* marg = (double*)(sc + kScratchMarg);
-      // a mask covering all n bits is the plain distribution (written to the same place)
-      const bool all = r->k == r->n;
-      s = launch_probs(r->st, all ? marg : nullptr, 1, all ? 0 : r->mask,
-                       (double*)(sc + kScratchPartials), (uint8_t*)(sc + kScratchBits), marg);
-      if (s == QS_OK) {
-        cudaError_t e = cudaMemcpyAsync(slot_host[slot], sc + kScratchMarg, sizeof(double) << r->k,
-                                        cudaMemcpyDeviceToHost, streams[slot]);
-        if (e == cudaSuccess) e = cudaEventRecord(slot_ev[slot], streams[slot]);
-        if (e != cudaSuccess) s = cuda_status(e, "large circuit readout");
-      }
-    }
-    r->slot = slot;
-    slot_req[slot] = r;
-    ++large_circuits;
-    if (s != QS_OK) {
-      cudaStreamSynchronize(streams[slot]);
-      release_large(r);
-      finish(r, s);
-    }
-  }
-
-  void release_large(Req* r) {
-    if (r->st) sv_destroy(r->st);
-    r->st = nullptr;
-    if (r->slot >= 0) slot_req[r->slot] = nullptr;
-    {
-      std::lock_guard<std::mutex> g(mu);
-      bytes_in_use -= r->bytes;
-    }
-    r->slot = -1;
-  }
-
-  void finish_large(Req* r) {
-    const int slot = r->slot;
-    r->result.assign(slot_host[slot], slot_host[slot] + ((size_t)1 << r->k));
-    release_large(r);
-    finish(r, QS_OK);
-  }
-
-  // Event query with a testing hook: qs_server_inject_query_error makes the next
-  // query return a given error instead of asking the device.
-  std::atomic<int> injected_error{0};
   cudaError_t query(cudaEvent_t ev) {
     const int inj = injected_error.exchange(0);
     if (inj != 0) return (cudaError_t)inj;
     return cudaEventQuery(ev);
   }
 
-  void fail_large(Req* r, cudaError_t e) {
-    cudaGetLastError();   // clears a non-sticky error
-    const qs_status st = cuda_status(e, "completion of a large circuit");
-    const std::string msg = qs_last_error();
-    cudaStreamSynchronize(streams[r->slot]);   // nothing of it may still write its buffers
-    cudaGetLastError();
-    release_large(r);
-    set_error("%s", msg.c_str());
-    finish(r, st);
+  // fail every published job that is not finished and start the queue over
+  void fail_queue(qs_status st, const std::string& msg) {
+    for (QJob& q : in_queue)
+      if (q.r) {
+        Req* r = q.r;
+        q.r = nullptr;
+        set_error("%s", msg.c_str());
+        finish(r, st);
+      }
+    in_queue.clear();
+    op_tail = op_head;
+    res_tail = res_head;
+    cudaMemsetAsync(d_head, 0, sizeof(unsigned long long), pk_stream);
+    cudaStreamSynchronize(pk_stream);
+    published = 0;
+    reinterpret_cast<std::atomic<uint64_t>*>(&ctl->tail)->store(0, std::memory_order_release);
   }
 
-  void fail_batch(cudaError_t e) {
-    cudaGetLastError();
-    const qs_status st = cuda_status(e, "completion of a packed launch");
-    const std::string msg = qs_last_error();
-    cudaStreamSynchronize(small_stream);
-    cudaGetLastError();
-    for (Req* r : batch) {
-      set_error("%s", msg.c_str());
-      finish(r, st);
+  // the persistent kernel has ended: by the idle limit (status QS_ETIMEOUT), its
+  // lifetime, or an error; on an error its unfinished jobs fail with that error
+  bool poll_persistent() {
+    if (!pk_running) return false;
+    const cudaError_t e = query(pk_ev);
+    if (e == cudaErrorNotReady) return false;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      const qs_status st = cuda_status(e, "completion of the persistent packed kernel");
+      const std::string msg = qs_last_error();
+      cudaStreamSynchronize(pk_stream);   // nothing of it may still run when the queue starts over
+      cudaGetLastError();
+      pk_running = false;
+      g_reserved_sms.fetch_sub(pk_reserved);
+      pk_reserved = 0;
+      fail_queue(st, msg);
+      return true;
     }
-    batch.clear();
-    batch_busy = false;
+    pk_running = false;
+    g_reserved_sms.fetch_sub(pk_reserved);
+    pk_reserved = 0;
+    int status = 0;
+    if (cudaMemcpy(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        status == (int)QS_ETIMEOUT) {
+      std::lock_guard<std::mutex> g(mu);
+      ++idle_timeouts;
+    }
+    return true;
   }
 
-  void run() {
+  // ---------------------------------------------------------------- large circuits
+  void worker_loop() {
     cudaSetDevice(device);
+    cudaStream_t stream = nullptr;
+    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    double* hbuf = nullptr;
+    cudaMallocHost((void**)&hbuf, sizeof(double) << kMaxMargBits);
+    const int method = cfg.large_tiled ? QS_METHOD_TILED : QS_METHOD_AUTO;
     for (;;) {
-      bool progress = false;
-      // 1. retire finished work; a query that reports an error (neither done nor
-      // still running) completes the work with that error
-      for (size_t s = 0; s < slot_req.size(); ++s) {
-        Req* r = slot_req[s];
-        if (!r) continue;
-        const cudaError_t e = query(slot_ev[s]);
-        if (e == cudaSuccess) {
-          finish_large(r);
-          progress = true;
-        } else if (e != cudaErrorNotReady) {
-          fail_large(r, e);
-          progress = true;
-        }
+      Req* r = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_large.wait(lk, [&] { return stop_workers || !large_queue.empty(); });
+        if (large_queue.empty()) break;
+        r = large_queue.front();
+        large_queue.pop_front();
+        ++large_running;
       }
-      if (batch_busy) {
-        const cudaError_t e = query(batch_ev);
-        if (e == cudaSuccess) {
-          finish_batch();
-          progress = true;
-        } else if (e != cudaErrorNotReady) {
-          fail_batch(e);
-          progress = true;
+      qs_allocator a{async_alloc, async_free, nullptr};
+      qs_state_t st = nullptr;
+      qs_status s = (stream && hbuf) ? sv_create(r->n, cfg.prec, &a, stream, &st) : QS_ENOMEM;
+      if (s == QS_OK) s = apply_gates(st, r->gates.data(), r->gates.size(), method, nullptr);
+      if (s == QS_OK) {
+        unsigned char* sc = (unsigned char*)st->scratch;
+        double* marg = (double*)(sc + kScratchMarg);
+        const bool all = r->k == r->n;   // a mask of all n bits is the plain distribution
+        s = launch_probs(st, all ? marg : nullptr, 1, all ? 0 : r->mask, (double*)(sc + kScratchPartials),
+                         (uint8_t*)(sc + kScratchBits), marg);
+        if (s == QS_OK) {
+          cudaError_t e = cudaMemcpyAsync(hbuf, marg, sizeof(double) << r->k, cudaMemcpyDeviceToHost, stream);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+          if (e != cudaSuccess) s = cuda_status(e, "large circuit readout");
         }
+        if (s == QS_OK) r->result.assign(hbuf, hbuf + ((size_t)1 << r->k));
       }
-      // 2. admission
-      std::vector<Req*> to_batch, too_big;
-      std::vector<std::pair<Req*, int>> to_large;
+      if (st) sv_destroy(st);
       {
         std::lock_guard<std::mutex> g(mu);
-        bool idle = pending.empty() && !batch_busy &&
-                    std::all_of(slot_req.begin(), slot_req.end(), [](Req* x) { return x == nullptr; });
+        bytes_in_use -= r->bytes;
+        --large_running;
+        ++large_circuits;
+      }
+      finish(r, s);
+      cv_work.notify_one();
+    }
+    if (hbuf) cudaFreeHost(hbuf);
+    if (stream) cudaStreamDestroy(stream);
+  }
+
+  // ---------------------------------------------------------------- scheduler
+  void run() {
+    cudaSetDevice(device);
+    std::deque<Req*> small_wait;   // small circuits waiting for queue or arena space
+    for (;;) {
+      bool progress = retire_small();
+      if (poll_persistent()) progress = true;
+      std::vector<Req*> too_big;
+      {
+        std::lock_guard<std::mutex> g(mu);
+        const bool idle = pending.empty() && small_wait.empty() && in_queue.empty() && !pk_running &&
+                          large_queue.empty() && large_running == 0;
         if (stop && idle) return;
-        std::vector<bool> busy(slot_req.size());
-        for (size_t s = 0; s < slot_req.size(); ++s) busy[s] = slot_req[s] != nullptr;
         for (auto it = pending.begin(); it != pending.end();) {
           Req* r = *it;
           if (r->n <= cfg.small_max_qubits) {
-            if (!batch_busy && (int)to_batch.size() < cfg.max_batch) {
-              to_batch.push_back(r);
-              it = pending.erase(it);
-              continue;
-            }
-          } else {
-            int slot = -1;
-            for (size_t s = 0; s < busy.size(); ++s)
-              if (!busy[s]) {
-                slot = (int)s;
-                break;
-              }
-            const size_t need = ((size_t)(cfg.prec == QS_C64 ? 8 : 16) << r->n) + kScratchBytes + (4u << 20);
-            if (need > cfg.mem_budget) {   // can never be admitted
-              too_big.push_back(r);
-              it = pending.erase(it);
-              continue;
-            }
-            if (slot >= 0 && bytes_in_use + need <= cfg.mem_budget) {
-              busy[slot] = true;
-              r->bytes = need;
-              bytes_in_use += need;
-              peak_bytes = std::max(peak_bytes, bytes_in_use);
-              to_large.push_back({r, slot});
-              it = pending.erase(it);
-              continue;
-            }
+            small_wait.push_back(r);
+            it = pending.erase(it);
+            continue;
+          }
+          const size_t need = ((size_t)(cfg.prec == QS_C64 ? 8 : 16) << r->n) + kScratchBytes + (4u << 20);
+          if (need > cfg.mem_budget) {   // can never be admitted
+            too_big.push_back(r);
+            it = pending.erase(it);
+            continue;
+          }
+          if (bytes_in_use + need <= cfg.mem_budget &&
+              (int)large_queue.size() + large_running < cfg.max_inflight) {
+            r->bytes = need;
+            bytes_in_use += need;
+            peak_bytes = std::max(peak_bytes, bytes_in_use);
+            large_queue.push_back(r);
+            it = pending.erase(it);
+            cv_large.notify_one();
+            continue;
           }
           ++it;
         }
@@ -427,17 +540,20 @@ struct Server {
         finish(r, QS_ENOMEM);
         progress = true;
       }
-      if (!to_batch.empty()) {
-        start_batch(to_batch);
+      while (!small_wait.empty() && publish(small_wait.front())) {
+        small_wait.pop_front();
         progress = true;
       }
-      for (auto& p : to_large) {
-        start_large(p.first, p.second);
+      bool unfinished = false;
+      for (const QJob& q : in_queue) unfinished = unfinished || q.r != nullptr;
+      if (!pk_running && unfinished) {   // published jobs and no kernel to take them
+        const qs_status s = launch_persistent();
+        if (s != QS_OK) fail_queue(s, qs_last_error());
         progress = true;
       }
       if (!progress) {
         std::unique_lock<std::mutex> lk(mu);
-        cv_work.wait_for(lk, std::chrono::microseconds(20));
+        cv_work.wait_for(lk, std::chrono::microseconds(10));
       }
     }
   }
@@ -463,7 +579,7 @@ qs_status qs_server_create(const qs_server_config* cfg, qs_server_t* out) {
   }
   const int small_cap = cfg->prec == QS_C64 ? 14 : 13;
   if (cfg->small_max_qubits < 0 || cfg->small_max_qubits > small_cap || cfg->max_inflight < 0 ||
-      cfg->max_batch < 0) {
+      cfg->persistent_ctas < 0 || cfg->idle_ms < 0) {
     set_error("bad server configuration");
     return QS_EINVAL;
   }
@@ -472,32 +588,54 @@ qs_status qs_server_create(const qs_server_config* cfg, qs_server_t* out) {
   s->cfg = *cfg;
   if (s->cfg.small_max_qubits == 0) s->cfg.small_max_qubits = small_cap;
   if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 4;
-  if (s->cfg.max_batch == 0) s->cfg.max_batch = 1024;
+  if (s->cfg.persistent_ctas == 0) s->cfg.persistent_ctas = 16;
+  if (s->cfg.idle_ms == 0) s->cfg.idle_ms = 5;
   cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (s->cfg.persistent_ctas > s->sms) s->cfg.persistent_ctas = s->sms;
   if (s->cfg.mem_budget == 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     s->cfg.mem_budget = (uint64_t)(0.8 * (double)fr);
   }
-  const int m = s->cfg.max_inflight;
-  s->streams.resize(m);
-  s->slot_req.assign(m, nullptr);
-  s->slot_ev.resize(m);
-  s->slot_host.resize(m);
-  for (int i = 0; i < m; ++i) {
-    cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
-    cudaEventCreateWithFlags(&s->slot_ev[i], cudaEventDisableTiming);
-    cudaMallocHost((void**)&s->slot_host[i], sizeof(double) << kMaxMargBits);
+  // the persistent kernel's shared memory: the largest small state, the marginal
+  // histogram and the op chunk
+  const size_t amp = s->cfg.prec == QS_C64 ? sizeof(C2<float>) : sizeof(C2<double>);
+  s->op_size = s->cfg.prec == QS_C64 ? sizeof(PlainOp<float>) : sizeof(PlainOp<double>);
+  s->pk_smem = (amp << s->cfg.small_max_qubits) + (sizeof(double) << kMaxMargBits) + kOpChunk * s->op_size;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  chk(cudaStreamCreateWithFlags(&s->pk_stream, cudaStreamNonBlocking));
+  chk(cudaEventCreateWithFlags(&s->pk_ev, cudaEventDisableTiming));
+  const unsigned hflags = cudaHostAllocMapped | cudaHostAllocPortable;
+  chk(cudaHostAlloc((void**)&s->ctl, sizeof(PCtl), hflags));
+  chk(cudaHostAlloc((void**)&s->jobs, sizeof(PJob) * kRing, hflags));
+  chk(cudaHostAlloc((void**)&s->done_words, sizeof(uint32_t) * kRing, hflags));
+  chk(cudaHostAlloc((void**)&s->op_arena, s->op_size * (size_t)kOpArena, hflags));
+  chk(cudaHostAlloc((void**)&s->res_arena, sizeof(double) * (size_t)kResArena, hflags));
+  chk(cudaMalloc(&s->d_head, sizeof(unsigned long long)));
+  chk(cudaMalloc(&s->d_status, sizeof(int)));
+  if (e == cudaSuccess) {
+    std::memset(s->ctl, 0, sizeof(PCtl));
+    std::memset(s->done_words, 0, sizeof(uint32_t) * kRing);
+    chk(cudaMemset(s->d_head, 0, sizeof(unsigned long long)));
+    chk(cudaMemset(s->d_status, 0, sizeof(int)));
+    if (s->cfg.prec == QS_C64)
+      chk(cudaFuncSetAttribute(packed_persistent_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)s->pk_smem));
+    else
+      chk(cudaFuncSetAttribute(packed_persistent_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)s->pk_smem));
   }
-  cudaStreamCreateWithFlags(&s->small_stream, cudaStreamNonBlocking);
-  cudaEventCreateWithFlags(&s->batch_ev, cudaEventDisableTiming);
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     qs_status st = cuda_status(e, "server setup");
-    delete s;
+    qs_server_destroy(s);
     return st;
   }
-  s->worker = std::thread([s]() { s->run(); });
+  s->scheduler = std::thread([s]() { s->run(); });
+  for (int i = 0; i < s->cfg.max_inflight; ++i) s->workers.emplace_back([s]() { s->worker_loop(); });
   *out = s;
   return QS_OK;
 }
@@ -581,6 +719,7 @@ qs_status qs_server_stats_get(qs_server_t s, qs_server_stats* out) {
   out->packed_launches = s->packed_launches;
   out->packed_circuits = s->packed_circuits;
   out->large_circuits = s->large_circuits;
+  out->idle_timeouts = s->idle_timeouts;
   out->peak_bytes = s->peak_bytes;
   std::vector<double> l = s->lat_ms;
   if (!l.empty()) {
@@ -619,17 +758,27 @@ qs_status qs_server_destroy(qs_server_t s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
-  if (s->worker.joinable()) s->worker.join();
-  for (auto& kv : s->reqs) delete kv.second;
-  for (size_t i = 0; i < s->streams.size(); ++i) {
-    cudaStreamDestroy(s->streams[i]);
-    cudaEventDestroy(s->slot_ev[i]);
-    cudaFreeHost(s->slot_host[i]);
+  if (s->scheduler.joinable()) s->scheduler.join();
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop_workers = true;
   }
-  cudaStreamDestroy(s->small_stream);
-  cudaEventDestroy(s->batch_ev);
-  if (s->d_buf) cudaFree(s->d_buf);
-  if (s->h_buf) cudaFreeHost(s->h_buf);
+  s->cv_large.notify_all();
+  for (auto& w : s->workers)
+    if (w.joinable()) w.join();
+  if (s->ctl) reinterpret_cast<std::atomic<uint32_t>*>(&s->ctl->stop)->store(1u, std::memory_order_release);
+  if (s->pk_stream) cudaStreamSynchronize(s->pk_stream);   // the kernel ends at its next wait
+  if (s->pk_reserved) g_reserved_sms.fetch_sub(s->pk_reserved);
+  for (auto& kv : s->reqs) delete kv.second;
+  if (s->pk_stream) cudaStreamDestroy(s->pk_stream);
+  if (s->pk_ev) cudaEventDestroy(s->pk_ev);
+  if (s->ctl) cudaFreeHost(s->ctl);
+  if (s->jobs) cudaFreeHost(s->jobs);
+  if (s->done_words) cudaFreeHost(s->done_words);
+  if (s->op_arena) cudaFreeHost(s->op_arena);
+  if (s->res_arena) cudaFreeHost(s->res_arena);
+  if (s->d_head) cudaFree(s->d_head);
+  if (s->d_status) cudaFree(s->d_status);
   delete s;
   return QS_OK;
 }

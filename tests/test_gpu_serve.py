@@ -70,11 +70,11 @@ def test_admission_by_memory(qs):
     srv.close()
 
 
-@pytest.mark.parametrize("n", [8, 16])
+@pytest.mark.parametrize("n", [8, 12])
 def test_failed_completion_query_returns_error(qs, n):
-    # a completion query that reports an error (injected on the host: no device
-    # fault) ends that circuit's wait with QS_ECUDA (packed launch for n = 8, a
-    # resident state for n = 16); the server keeps serving afterwards
+    # a completion query of the persistent packed kernel that reports an error
+    # (injected on the host: no device fault) ends the queued circuits' waits with
+    # QS_ECUDA; the queue starts over and the server keeps serving
     srv = qs.Server(max_inflight=2)
     ops = W.layered_haar_cz(n, 4, seed=n)
     qs.server_inject_query_error(srv, 999)   # cudaErrorUnknown
@@ -85,4 +85,43 @@ def test_failed_completion_query_returns_error(qs, n):
     res, _ = srv.wait(srv.submit(n, ops, _mask(n)))
     np.testing.assert_allclose(res, _oracle_marginal(n, ops), atol=2e-6)
     assert srv.stats()["completed"] == 2
+    srv.close()
+
+
+def test_idle_limit_ends_the_persistent_kernel(qs):
+    # no producer: the packed kernel's bounded wait runs out (a host-side stall of
+    # 60 ms against a 2 ms limit), the kernel ends reporting QS_ETIMEOUT (counted),
+    # and the next circuit launches it again
+    srv = qs.Server(idle_ms=2)
+    ops = W.layered_haar_cz(9, 5, seed=3)
+    res, _ = srv.wait(srv.submit(9, ops, _mask(9)))
+    time.sleep(0.06)
+    st = srv.stats()
+    assert st["idle_timeouts"] >= 1 and st["packed_launches"] == 1
+    res2, _ = srv.wait(srv.submit(9, ops, _mask(9)))
+    np.testing.assert_array_equal(res, res2)
+    np.testing.assert_allclose(res, _oracle_marginal(9, ops), atol=2e-6)
+    assert srv.stats()["packed_launches"] == 2
+    srv.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_thousand_small_circuits_through_the_queue(qs, prec):
+    # 1200 circuits of 6..12 qubits submitted as fast as the host can: every one
+    # completes; a sample equals the oracle (complex128: 1e-12; complex64: 2e-6)
+    rng = np.random.default_rng(11 + prec)
+    count = 1200
+    specs = [(int(n), int(d)) for n, d in zip(rng.integers(6, 13, size=count), rng.integers(2, 12, size=count))]
+    circuits = [qs.gates_array(W.layered_haar_cz(n, d, seed=2000 + i)) for i, (n, d) in enumerate(specs)]
+    srv = qs.Server(prec=prec, small_max_qubits=12)
+    tickets = [srv.submit(n, c, _mask(n)) for (n, _), c in zip(specs, circuits)]
+    results = [srv.wait(t)[0] for t in tickets]
+    st = srv.stats()
+    assert st["completed"] == count and st["packed_circuits"] == count and st["large_circuits"] == 0
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    tol = 1e-12 if prec else 2e-6
+    for i in rng.choice(count, size=12, replace=False):
+        n, d = specs[i]
+        ops = W.layered_haar_cz(n, d, seed=2000 + int(i))
+        np.testing.assert_allclose(results[i], _oracle_marginal(n, ops), atol=tol)
     srv.close()
