@@ -153,6 +153,15 @@ typedef struct {
  * device and set it to |0...0>.  alloc may be NULL (cudaMalloc).  stream is a
  * cudaStream_t (NULL = legacy default stream). */
 qs_status sv_create(int n, int prec, const qs_allocator* alloc, void* stream, qs_state_t* out);
+/* A state over a caller-owned device buffer of 2^n interleaved amplitudes of
+ * precision prec (16-byte aligned), used in place and left as it is (no
+ * |0...0>): every state-vector entry point then reads and updates that buffer.
+ * The library allocates only its own scratch and op buffers (alloc may be
+ * NULL: cudaMalloc); sv_destroy frees those and never the buffer, which must
+ * outlive the state.  Used by the sharded executor, whose shards stay in their
+ * own memory across the exchange steps.  Errors: QS_EINVAL, QS_ENOMEM. */
+qs_status sv_wrap(int n, int prec, void* device_buf, const qs_allocator* alloc, void* stream,
+                  qs_state_t* out);
 qs_status sv_destroy(qs_state_t st);
 qs_status sv_set_stream(qs_state_t st, void* stream);
 qs_status sv_info(qs_state_t st, int* n, int* prec, void** device_ptr);

@@ -113,6 +113,7 @@ def load():
     vp, i32, u64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t
     sig = {
         "sv_create": (i32, [i32, i32, ctypes.POINTER(_Allocator), vp, ctypes.POINTER(vp)]),
+        "sv_wrap": (i32, [i32, i32, vp, ctypes.POINTER(_Allocator), vp, ctypes.POINTER(vp)]),
         "sv_destroy": (i32, [vp]),
         "sv_set_stream": (i32, [vp, vp]),
         "sv_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(vp)]),
@@ -158,7 +159,7 @@ def load():
 
 
 def exported_symbols():
-    return ["sv_create", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
+    return ["sv_create", "sv_wrap", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
             "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_probs_host", "sv_loglik", "sv_grad",
             "dm_apply_channels", "qs_ptm_check", "qs_probs_noalloc", "sv_bloch", "qs_meas_error", "sv_save", "sv_load",
             "dm_gst_series", "dm_gst_power", "dm_code422_eval",
@@ -375,6 +376,34 @@ class State:
 
 def sv_create(n: int, prec: int = QS_C64, stream=None) -> State:
     return State(n, prec, stream)
+
+
+class WrappedState(State):
+    """A state over a caller-owned device tensor (sv_wrap): the library updates the
+    tensor in place and never frees it; keep the tensor alive while this lives."""
+
+    def __init__(self, tensor, stream=None):   # noqa: super().__init__ is not called on purpose
+        lib = load()
+        torch = _torch()
+        if not tensor.is_cuda or not tensor.is_contiguous():
+            raise ValueError("a contiguous CUDA tensor is required")
+        if tensor.dtype not in (torch.complex64, torch.complex128):
+            raise ValueError("complex64 or complex128 amplitudes are required")
+        N = tensor.numel()
+        n = N.bit_length() - 1
+        if N != 1 << n:
+            raise ValueError("the tensor must hold 2^n amplitudes")
+        self.n = n
+        self.prec = QS_C64 if tensor.dtype == torch.complex64 else QS_C128
+        self.tensor = tensor
+        h = ctypes.c_void_p()
+        _check(lib.sv_wrap(n, self.prec, tensor.data_ptr(), ctypes.byref(torch_allocator()),
+                           _stream_ptr(stream), ctypes.byref(h)))
+        self.handle = h
+
+
+def sv_wrap(tensor, stream=None) -> WrappedState:
+    return WrappedState(tensor, stream)
 
 
 def sv_destroy(st: State):

@@ -784,13 +784,58 @@ qs_status sv_create(int n, int prec, const qs_allocator* alloc, void* stream, qs
   return QS_OK;
 }
 
+qs_status sv_wrap(int n, int prec, void* device_buf, const qs_allocator* alloc, void* stream, qs_state_t* out) {
+  if (!out || !device_buf) {
+    set_error("out and device_buf are required");
+    return QS_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 1 || n > 36 || (prec != QS_C64 && prec != QS_C128)) {
+    set_error("n = %d outside [1, 36] or bad precision %d", n, prec);
+    return QS_EINVAL;
+  }
+  if ((uintptr_t)device_buf & 15) {
+    set_error("device_buf must be 16-byte aligned");
+    return QS_EINVAL;
+  }
+  qs_state_s* st = new (std::nothrow) qs_state_s();
+  if (!st) return QS_ENOMEM;
+  st->n = n;
+  st->prec = prec;
+  st->amp_bytes = prec == QS_C64 ? 8 : 16;
+  st->stream = (cudaStream_t)stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    st->alloc = *alloc;
+    st->has_alloc = true;
+  }
+  cudaGetDevice(&st->device);
+  st->data_bytes = st->amp_bytes << n;
+  st->data = device_buf;
+  st->owns_data = false;
+  st->scratch_bytes = kScratchBytes;
+  st->scratch = dev_alloc(st, st->scratch_bytes);
+  if (!st->scratch) {
+    set_error("scratch allocation failed");
+    delete st;
+    return QS_ENOMEM;
+  }
+  if (cudaEventCreateWithFlags(&st->upload_done, cudaEventDisableTiming) != cudaSuccess) {
+    dev_free(st, st->scratch, st->scratch_bytes);
+    qs_status s = cuda_status(cudaGetLastError(), "cudaEventCreate");
+    delete st;
+    return s;
+  }
+  *out = st;
+  return QS_OK;
+}
+
 qs_status sv_destroy(qs_state_t st) {
   if (!st) return QS_OK;
   cudaStreamSynchronize(st->stream);
   dev_free(st, st->opbuf, st->opbuf_bytes);
   if (st->stage) dev_free(st, st->stage, st->stage_bytes);
   dev_free(st, st->scratch, st->scratch_bytes);
-  dev_free(st, st->data, st->data_bytes);
+  if (st->owns_data) dev_free(st, st->data, st->data_bytes);
   if (st->hostbuf) cudaFreeHost(st->hostbuf);
   if (st->upload_done) cudaEventDestroy(st->upload_done);
   delete st;

@@ -31,6 +31,7 @@ struct State {
   size_t amp_bytes = 8;         // bytes per amplitude
   void* data = nullptr;         // 2^n amplitudes
   size_t data_bytes = 0;
+  bool owns_data = true;        // false: a caller's buffer (sv_wrap), not freed here
   void* scratch = nullptr;      // reduction partials + small device tables
   size_t scratch_bytes = 0;
   cudaStream_t stream = nullptr;

@@ -105,13 +105,16 @@ def plan_sharded(ops, n: int, s: int) -> ShardPlan:
 class ShardedState:
     """One rank's shard.  ``shard`` is a complex torch tensor of 2^(n-s) values;
     ``apply_local(shard, n_local, records) -> shard`` applies gate records whose
-    qubits are local physical positions."""
+    qubits are local physical positions.  The half-shard exchanges go through the
+    process group directly, or, with ``stage_host=True`` (a CPU-only backend such as
+    gloo with shards in device memory), through host copies of the halves."""
 
-    def __init__(self, n: int, s: int, rank: int, shard, apply_local, group=None):
+    def __init__(self, n: int, s: int, rank: int, shard, apply_local, group=None, stage_host: bool = False):
         self.n, self.s, self.rank = n, s, rank
         self.shard = shard
         self.apply_local = apply_local
         self.group = group
+        self.stage_host = stage_host
 
     def run(self, plan: ShardPlan):
         for step in plan.steps:
@@ -131,29 +134,48 @@ class ShardedState:
         view = self.shard.view(1 << (nl - lpos - 1), 2, 1 << lpos)
         # send the half whose local bit differs from my global bit; receive the partner's
         send = view[:, 1 - mine, :].contiguous()
+        if self.stage_host:
+            send = send.cpu()
         recv = torch.empty_like(send)
         ops = [dist.P2POp(dist.isend, torch.view_as_real(send), partner, self.group),
                dist.P2POp(dist.irecv, torch.view_as_real(recv), partner, self.group)]
         for r in dist.batch_isend_irecv(ops):
             r.wait()
-        view[:, 1 - mine, :] = recv
+        view[:, 1 - mine, :] = recv.to(self.shard.device) if self.stage_host else recv
 
 
-def cuda_apply_local(prec: int = 0):
-    """Local gate engine backed by the CUDA library: the shard (a device tensor
-    of complex64/complex128) is copied into a state, the gates run as tiled
-    passes, and the result is copied back into the same tensor."""
-    from . import State, sv_apply_circuit, sv_copy_in, sv_copy_out
+class CudaLocalEngine:
+    """Local gate engine backed by the CUDA library, in place on the shard: the
+    shard tensor (complex64 / complex128 on the device) is wrapped once as a state
+    (sv_wrap) and every gate segment runs on it directly -- no state allocation and
+    no copy sweeps per segment.  ``wraps`` counts the wrappings (one per shard)."""
 
-    def apply(shard, n_local, records):
-        st = State(n_local, prec)
-        sv_copy_in(st, shard)
-        sv_apply_circuit(st, records)
-        sv_copy_out(st, out=shard)
-        st.close()
+    def __init__(self, method=None):
+        self.method = method
+        self.state = None
+        self.ptr = None
+        self.wraps = 0
+
+    def __call__(self, shard, n_local, records):
+        from . import METHOD_AUTO, WrappedState, sv_apply_circuit
+        if self.ptr != shard.data_ptr():
+            if self.state is not None:
+                self.state.close()
+            self.state = WrappedState(shard)
+            self.ptr = shard.data_ptr()
+            self.wraps += 1
+        sv_apply_circuit(self.state, records, METHOD_AUTO if self.method is None else self.method)
         return shard
 
-    return apply
+    def close(self):
+        if self.state is not None:
+            self.state.close()
+            self.state = None
+
+
+def cuda_apply_local(method=None):
+    """The in-place CUDA engine (see CudaLocalEngine)."""
+    return CudaLocalEngine(method)
 
 
 def scatter_state(full: np.ndarray, n: int, s: int, rank: int) -> np.ndarray:
