@@ -209,6 +209,86 @@ TileOp<R> cp_form(TileOp<R> t) {
   return t;
 }
 
+// Packs a run [i, j) of TK_CP ops into a TK_RUN header and its entries (see
+// tile_cp.h) at out[w..]; returns the next write index.
+template <typename R>
+int pack_run(const std::vector<TileOp<R>>& ops, size_t i, size_t j, TileOp<R>* out, int w) {
+  std::vector<RunEntry<R>> cat[6];   // scalar, slot 0..3, register pairs
+  for (size_t o = i; o < j; ++o) {
+    const TileOp<R>& t = ops[o];
+    RunEntry<R> e;
+    std::memset(&e, 0, sizeof(e));
+    e.p = t.m0[0];
+    const bool ra = t.csrc == CS_REG, rb = t.dsrc == CS_REG;
+    if (ra && rb) {
+      e.k = t.cbit;
+      e.l = t.dbit;
+      cat[5].push_back(e);
+    } else if (ra || rb) {   // the other bit decides: its context position
+      e.pa = ra ? t.pad[1] : t.pad[0];
+      cat[1 + (ra ? t.cbit : t.dbit)].push_back(e);
+    } else {
+      e.pa = t.pad[0];
+      e.pb = t.pad[1];
+      cat[0].push_back(e);
+    }
+  }
+  std::vector<RunEntry<R>> all;
+  TileOp<R> h;
+  std::memset(&h, 0, sizeof(h));
+  h.kind = TK_RUN;
+  uint16_t cnt[6];
+  for (int c = 0; c < 6; ++c) {
+    cnt[c] = (uint16_t)cat[c].size();
+    all.insert(all.end(), cat[c].begin(), cat[c].end());
+  }
+  std::memcpy(&h.m0[0], cnt, sizeof(cnt));
+  const size_t per = sizeof(TileOp<R>) / sizeof(RunEntry<R>);
+  const size_t nslots = (all.size() + per - 1) / per;
+  h.slot = (uint8_t)nslots;
+  out[w++] = h;
+  std::vector<TileOp<R>> slots(nslots);
+  std::memset(slots.data(), 0, sizeof(TileOp<R>) * nslots);
+  if (!all.empty()) std::memcpy((void*)slots.data(), all.data(), sizeof(RunEntry<R>) * all.size());
+  for (size_t k = 0; k < nslots; ++k) out[w++] = slots[k];
+  return w;
+}
+
+// The kernel-parameter image of one forward tile pass: ops converted per
+// precision, controlled phases in their TK_CP form, and runs of at least kRunMin
+// of them packed into TK_RUN entry lists (at most 255 op slots each, 5 entries per
+// slot for complex64); stage op ranges relative to the pass.
+constexpr size_t kRunMin = 3;
+template <typename R>
+void build_pass_params(const Plan& pl, const TilePass& pass, TileParams<R>* tp) {
+  std::memset(tp, 0, sizeof(TileParams<R>));
+  tp->pass = pass;
+  tp->pass.stage_begin = 0;
+  int w = 0;
+  std::vector<TileOp<R>> conv;
+  const size_t per = sizeof(TileOp<R>) / sizeof(RunEntry<R>);
+  for (int s2 = 0; s2 < pass.n_stages; ++s2) {
+    TileStage ts = pl.stages[pass.stage_begin + s2];
+    conv.clear();
+    for (int o = ts.op_begin; o < ts.op_end; ++o) conv.push_back(cp_form(to_tile<R>(pl, (size_t)o)));
+    ts.op_begin = w;
+    for (size_t i = 0; i < conv.size();) {
+      if (conv[i].kind == TK_CP) {
+        size_t j = i;
+        while (j < conv.size() && conv[j].kind == TK_CP && j - i < 255 * per) ++j;
+        if (j - i >= kRunMin) {
+          w = pack_run(conv, i, j, tp->ops, w);
+          i = j;
+          continue;
+        }
+      }
+      tp->ops[w++] = conv[i++];
+    }
+    ts.op_end = w;
+    tp->stages[s2] = ts;
+  }
+}
+
 template <typename T>
 size_t put(std::vector<unsigned char>& blob, const T* p, size_t count) {
   size_t off = align16(blob.size());
@@ -365,18 +445,7 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
   for (const PlanStep& step : pl.steps) {
     switch (step.kind) {
       case PlanStep::TILE: {
-        const TilePass& pass = pl.passes[step.index];
-        std::memset(tp.get(), 0, sizeof(TileParams<R>));
-        tp->pass = pass;
-        const int op0 = pl.stages[pass.stage_begin].op_begin;
-        for (int s2 = 0; s2 < pass.n_stages; ++s2) {
-          TileStage ts = pl.stages[pass.stage_begin + s2];
-          for (int o = ts.op_begin; o < ts.op_end; ++o) tp->ops[o - op0] = cp_form(to_tile<R>(pl, (size_t)o));
-          ts.op_begin -= op0;
-          ts.op_end -= op0;
-          tp->stages[s2] = ts;
-        }
-        tp->pass.stage_begin = 0;
+        build_pass_params<R>(pl, pl.passes[step.index], tp.get());
         tm.before(0);
         s = launch_tile_pass(st, tp.get());
         ++tile_launches;

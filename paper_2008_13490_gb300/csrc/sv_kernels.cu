@@ -360,6 +360,38 @@ struct DiagRun {
       s = cmul(s, e);
     }
   }
+  // TK_RUN: the packed entry lists of a run of controlled phases (tile_cp.h)
+  __device__ __forceinline__ void add_run(C2<R>* v, const TileOp<R>* __restrict__ opp, uint64_t ctx) {
+    const uint16_t* cnt = reinterpret_cast<const uint16_t*>(&opp->m0[0]);
+    const RunEntry<R>* __restrict__ e = reinterpret_cast<const RunEntry<R>*>(opp + 1);
+    const C2<R> one{R(1), R(0)};
+    int i = 0;
+    for (const int n = cnt[0]; i < n; ++i) {
+      const RunEntry<R> x = e[i];
+      s = cmul(s, csel(((ctx >> x.pa) & (ctx >> x.pb) & 1ull) != 0, x.p, one));
+    }
+    for (const int n = i + cnt[1]; i < n; ++i) {
+      const RunEntry<R> x = e[i];
+      f0[1] = cmul(f0[1], csel(((ctx >> x.pa) & 1ull) != 0, x.p, one));
+    }
+    for (const int n = i + cnt[2]; i < n; ++i) {
+      const RunEntry<R> x = e[i];
+      f1[1] = cmul(f1[1], csel(((ctx >> x.pa) & 1ull) != 0, x.p, one));
+    }
+    for (const int n = i + cnt[3]; i < n; ++i) {
+      const RunEntry<R> x = e[i];
+      f2[1] = cmul(f2[1], csel(((ctx >> x.pa) & 1ull) != 0, x.p, one));
+    }
+    for (const int n = i + cnt[4]; i < n; ++i) {
+      const RunEntry<R> x = e[i];
+      f3[1] = cmul(f3[1], csel(((ctx >> x.pa) & 1ull) != 0, x.p, one));
+    }
+    for (const int n = i + cnt[5]; i < n; ++i) {
+      const RunEntry<R> x = e[i];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], csel(((r >> x.k) & (r >> x.l) & 1) != 0, x.p, one));
+    }
+  }
   template <bool TWO = false>
   __device__ __forceinline__ void flush(C2<R>* v, C2<R>* v2 = nullptr) {
     // D(r) = s f0[r0] f1[r1] f2[r2] f3[r3] as (s f0 f1)[r & 3] * (f2 f3)[r >> 2]
@@ -377,7 +409,10 @@ struct DiagRun {
   }
 };
 
-template <typename R, bool G2>
+// G2: the pass holds dense two-qubit ops; RUNS: it holds packed diagonal runs
+// (TK_RUN).  Each combination is its own instantiation, so that a pass without
+// them keeps the leaner code and register allocation.
+template <typename R, bool G2, bool RUNS>
 __global__ void __launch_bounds__(kTileThreads)
     tile_pass_kernel(C2<R>* __restrict__ psi, const __grid_constant__ TileParams<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -463,21 +498,28 @@ __global__ void __launch_bounds__(kTileThreads)
       }
     }
     for (int o = cur.op_begin; o < cur.op_end;) {
-      if (ops[o].kind != TK_DIAG && ops[o].kind != TK_CP) {
+      const uint8_t k0 = ops[o].kind;
+      if (k0 != TK_DIAG && k0 != TK_CP && !(RUNS && k0 == TK_RUN)) {
         apply_tile_op<R, G2>(v, ops + o, tile, lane, warp);
-        o += (G2 && ops[o].kind == TK_G2) ? 2 : 1;   // a dense two-qubit op spans two entries
+        o += (G2 && k0 == TK_G2) ? 2 : 1;   // a dense two-qubit op spans two entries
         continue;
       }
       DiagRun<R> dr;   // live only over the run
       dr.reset();
       uint4 hdr = *reinterpret_cast<const uint4*>(ops + o);
       do {
-        if ((hdr.x & 0xffu) == TK_CP) dr.add_cp(v, ops + o, hdr, ctx);
-        else dr.add(v, ops + o, tile, lane, warp);
-        ++o;
+        const uint32_t kind = hdr.x & 0xffu;
+        if (RUNS && kind == TK_RUN) {
+          dr.add_run(v, ops + o, ctx);
+          o += 1 + (int)((hdr.x >> 8) & 0xffu);   // the header and its entry slots
+        } else {
+          if (kind == TK_CP) dr.add_cp(v, ops + o, hdr, ctx);
+          else dr.add(v, ops + o, tile, lane, warp);
+          ++o;
+        }
         if (o >= cur.op_end) break;
         hdr = *reinterpret_cast<const uint4*>(ops + o);
-      } while ((hdr.x & 0xffu) == TK_DIAG || (hdr.x & 0xffu) == TK_CP);
+      } while ((hdr.x & 0xffu) == TK_DIAG || (hdr.x & 0xffu) == TK_CP || (RUNS && (hdr.x & 0xffu) == TK_RUN));
       dr.flush(v);
     }
   }
@@ -1103,24 +1145,49 @@ static bool pass_has_g2(const TileParams<R>& P) {
   return false;
 }
 
-template <typename R, bool G2>
+// which op kinds a forward pass holds, walking op headers only (a dense
+// two-qubit op spans two slots; a TK_RUN header is followed by its entry slots,
+// whose bytes are not op headers)
+template <typename R>
+static void pass_kinds(const TileParams<R>& P, bool* g2, bool* runs) {
+  *g2 = *runs = false;
+  const int nops = P.pass.n_stages > 0 ? P.stages[P.pass.n_stages - 1].op_end : 0;
+  for (int o = 0; o < nops;) {
+    const uint8_t k = P.ops[o].kind;
+    if (k == TK_RUN) {
+      *runs = true;
+      o += 1 + P.ops[o].slot;
+    } else if (k == TK_G2) {
+      *g2 = true;
+      o += 2;
+    } else {
+      ++o;
+    }
+  }
+}
+
+template <typename R, bool G2, bool RUNS>
 static qs_status tile_launch_t(State* st, const TileParams<R>& P) {
   const uint64_t tiles = 1ull << (st->n - kTileBits);
   const size_t smem = sizeof(C2<R>) << kTileBits;
-  qs_status s = set_smem(tile_pass_kernel<R, G2>, smem);
+  qs_status s = set_smem(tile_pass_kernel<R, G2, RUNS>, smem);
   if (s != QS_OK) return s;
-  tile_pass_kernel<R, G2><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>((C2<R>*)st->data, P);
+  tile_pass_kernel<R, G2, RUNS><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>((C2<R>*)st->data, P);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }
 
+template <typename R>
+static qs_status tile_launch_any(State* st, const TileParams<R>& P) {
+  bool g2 = false, runs = false;
+  pass_kinds(P, &g2, &runs);
+  if (g2) return runs ? tile_launch_t<R, true, true>(st, P) : tile_launch_t<R, true, false>(st, P);
+  return runs ? tile_launch_t<R, false, true>(st, P) : tile_launch_t<R, false, false>(st, P);
+}
+
 qs_status launch_tile_pass(State* st, const void* params) {
-  if (st->prec == QS_C64) {
-    const TileParams<float>& P = *(const TileParams<float>*)params;
-    return pass_has_g2(P) ? tile_launch_t<float, true>(st, P) : tile_launch_t<float, false>(st, P);
-  }
-  const TileParams<double>& P = *(const TileParams<double>*)params;
-  return pass_has_g2(P) ? tile_launch_t<double, true>(st, P) : tile_launch_t<double, false>(st, P);
+  if (st->prec == QS_C64) return tile_launch_any(st, *(const TileParams<float>*)params);
+  return tile_launch_any(st, *(const TileParams<double>*)params);
 }
 
 template <typename R, bool G2>
