@@ -157,9 +157,37 @@ __device__ __forceinline__ int group_base(int g, int q) {
   return ((g >> (2 * q)) << (2 * q + 2)) | lo;
 }
 
+// Shared-memory layout of a Pauli vector: entry i sits at word swz(i) = i ^ m(i >> 5),
+// with m a fixed GF(2)-linear map of the index bits 5..11 into the bank bits 0..4.
+// The sweeps read the elements of a base-4 digit at strides 1, 4, 16, ... words, which
+// put up to four lanes of a warp on one bank in the plain layout; m was chosen by a
+// search over every access pattern of the sweeps below (one- and two-digit, 4..6
+// qubits) so that a warp's accesses meet 1856 wavefronts over 1760 patterns against
+// 7080 in the plain layout.  swz is linear over XOR, so the index of a group's base
+// and of its elements' offsets (disjoint bits) combine by XOR.  m(h) bit r = parity
+// of h & kSwzRow[r]; a CTA keeps m for h = 0..127 in s_swz.
+__shared__ uint8_t s_swz[128];
+__device__ __forceinline__ void swz_init() {
+  constexpr unsigned kSwzRow[5] = {0x4f, 0x15, 0x6d, 0x33, 0x67};
+  if (threadIdx.x < 128) {
+    const unsigned h = threadIdx.x;
+    unsigned m = 0;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) m |= (unsigned)(__popc(h & kSwzRow[r]) & 1) << r;
+    s_swz[h] = (uint8_t)m;
+  }
+}
+__device__ __forceinline__ int swz(int i) { return i ^ (int)s_swz[i >> 5]; }
+// the (swizzled) offsets of the four values of one digit at stride st; swz of
+// 3 st is swz(st) ^ swz(2 st) (disjoint bits), so a run-time digit (the CZ
+// permutation) costs two selects, no indexed load
+struct Off4 {
+  int o1, o2;
+  __device__ __forceinline__ explicit Off4(int st) : o1(swz(st)), o2(swz(2 * st)) {}
+  __device__ __forceinline__ int operator[](int d) const { return ((d & 1) ? o1 : 0) ^ ((d & 2) ? o2 : 0); }
+};
+
 // r <- G r (or G^T r) on digit q; G row-major 4x4 (output digit, input digit).
-// Digit 0: one 16-byte access per group (scalar accesses 4 floats apart would
-// fall 4 lanes to a bank).
 __device__ void apply4(float* r, int n, int q, const float* Gs, bool transpose) {
   const int groups = 1 << (2 * (n - 1));
   // the matrix in registers once per sweep
@@ -168,29 +196,13 @@ __device__ void apply4(float* r, int n, int q, const float* Gs, bool transpose) 
   for (int d = 0; d < 4; ++d)
 #pragma unroll
     for (int e = 0; e < 4; ++e) G[d * 4 + e] = transpose ? Gs[e * 4 + d] : Gs[d * 4 + e];
-  if (q == 0) {
-    float4* r4 = reinterpret_cast<float4*>(r);
-    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-      const float4 v = r4[g];
-      const float x[4] = {v.x, v.y, v.z, v.w};
-      float y[4];
-#pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        float acc = 0.f;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc = fmaf(G[d * 4 + e], x[e], acc);
-        y[d] = acc;
-      }
-      r4[g] = make_float4(y[0], y[1], y[2], y[3]);
-    }
-    return;
-  }
   const int st = 1 << (2 * q);
+  const Off4 od(st);
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-    const int base = group_base(g, q);
+    const int base = swz(group_base(g, q));
     float x[4], y[4];
 #pragma unroll
-    for (int d = 0; d < 4; ++d) x[d] = r[base + d * st];
+    for (int d = 0; d < 4; ++d) x[d] = r[base ^ od[d]];
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
       float acc = 0.f;
@@ -199,7 +211,7 @@ __device__ void apply4(float* r, int n, int q, const float* Gs, bool transpose) 
       y[d] = acc;
     }
 #pragma unroll
-    for (int d = 0; d < 4; ++d) r[base + d * st] = y[d];
+    for (int d = 0; d < 4; ++d) r[base ^ od[d]] = y[d];
   }
 }
 
@@ -234,29 +246,20 @@ __device__ __forceinline__ void adj4(float* lam, const float* x_src, int n, int 
 #pragma unroll
     for (int e = 0; e < 4; ++e) l[e] = y[e];
   };
-  if (q == 0) {
-    const float4* x4 = reinterpret_cast<const float4*>(x_src);
-    float4* l4 = reinterpret_cast<float4*>(lam);
-    for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
-      const float4 v = x4[gi], w = l4[gi];
-      const float x[4] = {v.x, v.y, v.z, v.w};
-      float l[4] = {w.x, w.y, w.z, w.w};
-      group(x, l);
-      l4[gi] = make_float4(l[0], l[1], l[2], l[3]);
-    }
-  } else {
+  {
     const int st = 1 << (2 * q);
+    const Off4 od(st);
     for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
-      const int base = group_base(gi, q);
+      const int base = swz(group_base(gi, q));
       float x[4], l[4];
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
-        x[d] = x_src[base + d * st];
-        l[d] = lam[base + d * st];
+        x[d] = x_src[base ^ od[d]];
+        l[d] = lam[base ^ od[d]];
       }
       group(x, l);
 #pragma unroll
-      for (int d = 0; d < 4; ++d) lam[base + d * st] = l[d];
+      for (int d = 0; d < 4; ++d) lam[base ^ od[d]] = l[d];
     }
   }
 #pragma unroll
@@ -279,8 +282,9 @@ __device__ void apply_cz(float* r, int n, int a, int b, const DmArgs& A, bool tr
   const int groups = 1 << (2 * (n - 2));
   const int lo = a < b ? a : b, hi = a < b ? b : a;
   const int sa = 1 << (2 * a), sb = 1 << (2 * b);
+  const Off4 oa(sa), ob(sb);
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-    const int base = group_base2(g, lo, hi);
+    const int base = swz(group_base2(g, lo, hi));
     // forward: y[l] = isgn[l] x[inv[l]]; transpose: y[j] = sgn[j] x[dst[j]] (the
     // permutation is applied through the shared-memory addresses of the loads, so
     // every register index stays a compile-time constant)
@@ -289,10 +293,10 @@ __device__ void apply_cz(float* r, int n, int a, int b, const DmArgs& A, bool tr
     for (int l = 0; l < 16; ++l) {
       const int src = transpose ? A.cz_dst[l] : A.cz_inv[l];
       const float sg = (float)(transpose ? A.cz_sgn[l] : A.cz_isgn[l]);
-      y[l] = sg * r[base + (src >> 2) * sa + (src & 3) * sb];
+      y[l] = sg * r[base ^ oa[src >> 2] ^ ob[src & 3]];
     }
 #pragma unroll
-    for (int l = 0; l < 16; ++l) r[base + (l >> 2) * sa + (l & 3) * sb] = y[l];
+    for (int l = 0; l < 16; ++l) r[base ^ oa[l >> 2] ^ ob[l & 3]] = y[l];
   }
 }
 
@@ -300,14 +304,15 @@ __device__ void apply16(float* r, int n, int a, int b, const double* G, bool tra
   const int groups = 1 << (2 * (n - 2));
   const int lo = a < b ? a : b, hi = a < b ? b : a;
   const int sa = 1 << (2 * a), sb = 1 << (2 * b);
+  const Off4 oa(sa), ob(sb);
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-    const int base = group_base2(g, lo, hi);
+    const int base = swz(group_base2(g, lo, hi));
     float x[16];
-    for (int l = 0; l < 16; ++l) x[l] = r[base + (l >> 2) * sa + (l & 3) * sb];
+    for (int l = 0; l < 16; ++l) x[l] = r[base ^ oa[l >> 2] ^ ob[l & 3]];
     for (int d = 0; d < 16; ++d) {
       float acc = 0.f;
       for (int e = 0; e < 16; ++e) acc = fmaf((float)(transpose ? G[e * 16 + d] : G[d * 16 + e]), x[e], acc);
-      r[base + (d >> 2) * sa + (d & 3) * sb] = acc;
+      r[base ^ oa[d >> 2] ^ ob[d & 3]] = acc;
     }
   }
 }
@@ -322,15 +327,16 @@ __device__ void pass2(float* r, int n, int a, const float* Ga, int b, const floa
   const int groups = 1 << (2 * (n - 2));
   const int lo = a < b ? a : b, hi = a < b ? b : a;
   const int sa = 1 << (2 * a), sb = 1 << (2 * b);
+  const Off4 oa(sa), ob(sb);
   const float* ga = Ga;   // shared memory (broadcast reads)
   const float* gb = Gb;
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-    const int base = group_base2(g, lo, hi);
+    const int base = swz(group_base2(g, lo, hi));
     float x[16], y[16];
 #pragma unroll
     for (int l = 0; l < 16; ++l) {
       const int src = CZ ? A.cz_inv[l] : l;
-      const float v = r[base + (src >> 2) * sa + (src & 3) * sb];
+      const float v = r[base ^ oa[src >> 2] ^ ob[src & 3]];
       x[l] = CZ ? (float)A.cz_isgn[l] * v : v;
     }
 #pragma unroll
@@ -352,7 +358,7 @@ __device__ void pass2(float* r, int n, int a, const float* Ga, int b, const floa
         x[4 * da + d] = acc;
       }
 #pragma unroll
-    for (int l = 0; l < 16; ++l) r[base + (l >> 2) * sa + (l & 3) * sb] = x[l];
+    for (int l = 0; l < 16; ++l) r[base ^ oa[l >> 2] ^ ob[l & 3]] = x[l];
   }
 }
 
@@ -512,7 +518,167 @@ __global__ void __launch_bounds__(1024) dm_order_kernel(const int32_t* __restric
 // dynamic shared memory: tables, user PTM, WHT buffer, then the Pauli vector r
 // (and, with the gradient, lambda and a scratch vector)
 constexpr int kDmHead = 16 * TB_COUNT + 16 + 128;   // floats before r (16-byte aligned)
-static_assert(kDmHead % 4 == 0, "r is accessed as float4");
+// One circuit c (validated, tables built) on one CTA.
+template <bool GRAD>
+__device__ __forceinline__ void dm_circuit(const DmArgs& A, int c, int n, int L, const int32_t* ops, int64_t out0,
+                                           int D, float* tabs, float* user4, double* z, float* r, float* lam,
+                                           float* tmp, double* red, int4* s_ops, float* ckpt, float* segbuf,
+                                           float* subst) {
+  constexpr bool want_grad = GRAD;
+  const int N = 1 << n;
+  const int Dn = 1 << (2 * n);
+  const float amp0 = 1.0f / sqrtf((float)N);
+  // rho_0 = |0..0><0..0|: r_i = 2^{-n/2} on {I,Z}^n, 0 elsewhere
+  for (int i = threadIdx.x; i < Dn; i += blockDim.x) {
+    bool iz = true;
+    for (int b = 0; b < n; ++b) {
+      const int d = (i >> (2 * b)) & 3;
+      iz = iz && (d == 0 || d == 3);
+    }
+    r[swz(i)] = iz ? amp0 : 0.f;
+  }
+  __syncthreads();
+  // ---------------- forward
+  const int4* ops4 = reinterpret_cast<const int4*>(ops);
+  if constexpr (!GRAD) {
+    for (int k = 0; k < L;) {
+      if ((k % kOpChunk) == 0) {   // stage the next chunk of ops (one coalesced read)
+        __syncthreads();
+        for (int t = threadIdx.x; t < kOpChunk && k + t < L; t += blockDim.x) s_ops[t] = ops4[k + t];
+        __syncthreads();
+      }
+      const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kOpChunk]);
+      const int code = op[0], a = op[1];
+      const int32_t* nx = reinterpret_cast<const int32_t*>(&s_ops[(k + 1) % kOpChunk]);
+      if ((code == QS_DM_X90 || code == QS_DM_Y90) && k + 1 < L && (k + 1) % kOpChunk != 0 &&
+          (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) && nx[1] != a) {
+        // this op and the next act on different qubits: one two-digit pass
+        pass2<false>(r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), nx[1],
+                     tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY), A);
+        __syncthreads();
+        k += 2;
+        continue;
+      }
+      if (code == QS_DM_PTM1) {
+        if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
+        __syncthreads();
+      }
+      apply_op_fused(r, n, op, tabs, user4, A);
+      ++k;
+    }
+  }
+  for (int k = 0; GRAD && k < L; ++k) {
+    if ((k % kOpChunk) == 0) {   // stage the next chunk of ops (one coalesced read)
+      __syncthreads();
+      for (int t = threadIdx.x; t < kOpChunk && k + t < L; t += blockDim.x) s_ops[t] = ops4[k + t];
+      __syncthreads();
+    }
+    if (want_grad && (k % A.K) == 0) {
+      float* dst = ckpt + (size_t)(k / A.K) * D;
+      for (int i = threadIdx.x; i < Dn; i += blockDim.x) dst[i] = r[i];
+      __syncthreads();   // copies done before r is updated in place
+    }
+    const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kOpChunk]);
+    if (op[0] == QS_DM_PTM1) {
+      if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
+      __syncthreads();
+    }
+    apply_op_fused(r, n, op, tabs, user4, A);
+  }
+  // ---------------- probabilities: p = 2^{-n/2} WHT(r on {I,Z}^n)
+  for (int S = threadIdx.x; S < N; S += blockDim.x) z[S] = (double)r[swz(zs_index(S, n))];
+  __syncthreads();
+  wht(z, N);
+  const double scale = 1.0 / sqrt((double)N);
+  double ll = 0.0;
+  for (int J = threadIdx.x; J < N; J += blockDim.x) {
+    double p = z[J] * scale;
+    if (A.probs) A.probs[out0 + J] = (float)p;
+    if (A.counts) {
+      const int cnt = A.counts[out0 + J];
+      if (!(p > 0.0)) p = 1e-300;
+      if (cnt > 0) ll += (double)cnt * log(p);
+      z[J] = cnt > 0 ? (double)cnt / p : 0.0;   // seed weights dl/dp_J
+    }
+  }
+  if (A.counts) {
+    const double tot = block_sum_dm(ll, red);
+    if (threadIdx.x == 0 && A.loglik) A.loglik[c] = tot;
+  }
+  if constexpr (!GRAD) return;
+  // ---------------- adjoint
+  __syncthreads();
+  wht(z, N);
+  // lambda is linear in the seed: keep it in fp32 as lambda / lmax (no
+  // overflow when some n_J / p_J is huge) and scale the fp64 sums back
+  double lmax = 0.0;
+  for (int S = 0; S < N; ++S) lmax = fmax(lmax, fabs(z[S]));
+  const double lscale = lmax > 0.0 ? scale / lmax : 0.0;
+  for (int i = threadIdx.x; i < Dn; i += blockDim.x) lam[i] = 0.f;
+  __syncthreads();
+  for (int S = threadIdx.x; S < N; S += blockDim.x) lam[swz(zs_index(S, n))] = (float)(z[S] * lscale);
+  __syncthreads();
+  double g[4] = {0, 0, 0, 0};
+  const int nseg = (L + A.K - 1) / A.K;
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int k0 = sgi * A.K, k1 = min(L, k0 + A.K);
+    // recompute the states before each op of the segment
+    const float* ck = ckpt + (size_t)sgi * D;
+    for (int i = threadIdx.x; i < Dn; i += blockDim.x) r[i] = ck[i];
+    __syncthreads();
+    for (int k = k0; k < k1; ++k) {
+      float* dst = segbuf + (size_t)(k - k0) * D;
+      for (int i = threadIdx.x; i < Dn; i += blockDim.x) dst[i] = r[i];
+      if (k + 1 == k1) break;
+      const int32_t* op = ops + 4 * k;
+      if (op[0] == QS_DM_PTM1) {
+        __syncthreads();
+        if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
+        __syncthreads();
+      }
+      __syncthreads();
+      apply_op_fused(r, n, op, tabs, user4, A);
+    }
+    __syncthreads();
+    for (int k = k1 - 1; k >= k0; --k) {
+      const int32_t* op = ops + 4 * k;
+      if (op[0] == QS_DM_PTM1) {
+        if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
+      }
+      const int ns = op_nsub(op, n);
+      const float* before = segbuf + (size_t)(k - k0) * D;
+      __syncthreads();
+      // the states before the sub-ops, once: s_0 = before, s_{j+1} = sub_j s_j;
+      // the last stays in tmp, the earlier ones with parameters go to subst
+      if (ns > 1) {
+        for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = before[i];
+        __syncthreads();
+        for (int j = 0; j + 1 < ns; ++j) {
+          apply_sub(tmp, n, op_subop(op, j), tabs, user4, A, false);
+          __syncthreads();
+          if (j + 2 < ns && op_subop(op, j + 1).kind == 0) {
+            for (int i = threadIdx.x; i < Dn; i += blockDim.x) subst[(size_t)(j + 1) * D + i] = tmp[i];
+            __syncthreads();   // copied before sub-op j + 1 rewrites tmp
+          }
+        }
+      }
+      for (int j = ns - 1; j >= 0; --j) {
+        const SubOp sj = op_subop(op, j);
+        if (sj.kind == 0) {
+          const float* sv = j + 1 == ns ? (ns > 1 ? tmp : before) : (j == 0 ? before : subst + (size_t)j * D);
+          adj4(lam, sv, n, sj.q, tabs + 16 * sj.table, tabs, sj.dtab, g);
+        } else {
+          apply_sub(lam, n, sj, tabs, user4, A, true);
+        }
+        __syncthreads();
+      }
+    }
+  }
+  for (int pidx = 0; pidx < 4; ++pidx) {
+    const double tot = block_sum_dm(g[pidx], red);
+    if (threadIdx.x == 0) A.grad[4 * c + pidx] = tot * lmax;
+  }
+}
 
 // GRAD: the gradient kernel (forward with checkpoints, then the adjoint sweep);
 // otherwise probabilities / log-likelihood only, with one-qubit gate pairs fused
@@ -530,12 +696,12 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
   __shared__ double red[kDmThreads / 32];
   __shared__ int s_c;
   __shared__ int4 s_ops[kOpChunk];   // the current chunk of the circuit's ops
-  constexpr bool want_grad = GRAD;
   float* my_scratch =
       A.scratch ? A.scratch + (size_t)blockIdx.x * (size_t)(A.nseg + A.K + kDmMaxQ) * D : nullptr;
   float* ckpt = my_scratch;
   float* segbuf = my_scratch ? my_scratch + (size_t)A.nseg * D : nullptr;
   float* subst = my_scratch ? my_scratch + (size_t)(A.nseg + A.K) * D : nullptr;
+  swz_init();   // read after the first barrier of the loop below
 
   for (;;) {
     if (threadIdx.x == 0) {
@@ -571,159 +737,7 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
         for (int J = threadIdx.x; J < N; J += blockDim.x) A.probs[out0 + J] = nanf_;
       continue;
     }
-    const int Dn = 1 << (2 * n);
-    const float amp0 = 1.0f / sqrtf((float)N);
-    // rho_0 = |0..0><0..0|: r_i = 2^{-n/2} on {I,Z}^n, 0 elsewhere
-    for (int i = threadIdx.x; i < Dn; i += blockDim.x) {
-      bool iz = true;
-      for (int b = 0; b < n; ++b) {
-        const int d = (i >> (2 * b)) & 3;
-        iz = iz && (d == 0 || d == 3);
-      }
-      r[i] = iz ? amp0 : 0.f;
-    }
-    __syncthreads();
-    // ---------------- forward
-    const int4* ops4 = reinterpret_cast<const int4*>(ops);
-    if constexpr (!GRAD) {
-      for (int k = 0; k < L;) {
-        if ((k % kOpChunk) == 0) {   // stage the next chunk of ops (one coalesced read)
-          __syncthreads();
-          for (int t = threadIdx.x; t < kOpChunk && k + t < L; t += blockDim.x) s_ops[t] = ops4[k + t];
-          __syncthreads();
-        }
-        const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kOpChunk]);
-        const int code = op[0], a = op[1];
-        const int32_t* nx = reinterpret_cast<const int32_t*>(&s_ops[(k + 1) % kOpChunk]);
-        if ((code == QS_DM_X90 || code == QS_DM_Y90) && k + 1 < L && (k + 1) % kOpChunk != 0 &&
-            (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) && nx[1] != a) {
-          // this op and the next act on different qubits: one two-digit pass
-          pass2<false>(r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), nx[1],
-                       tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY), A);
-          __syncthreads();
-          k += 2;
-          continue;
-        }
-        if (code == QS_DM_PTM1) {
-          if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
-          __syncthreads();
-        }
-        apply_op_fused(r, n, op, tabs, user4, A);
-        ++k;
-      }
-    }
-    for (int k = 0; GRAD && k < L; ++k) {
-      if ((k % kOpChunk) == 0) {   // stage the next chunk of ops (one coalesced read)
-        __syncthreads();
-        for (int t = threadIdx.x; t < kOpChunk && k + t < L; t += blockDim.x) s_ops[t] = ops4[k + t];
-        __syncthreads();
-      }
-      if (want_grad && (k % A.K) == 0) {
-        float* dst = ckpt + (size_t)(k / A.K) * D;
-        for (int i = threadIdx.x; i < Dn; i += blockDim.x) dst[i] = r[i];
-        __syncthreads();   // copies done before r is updated in place
-      }
-      const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kOpChunk]);
-      if (op[0] == QS_DM_PTM1) {
-        if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
-        __syncthreads();
-      }
-      apply_op_fused(r, n, op, tabs, user4, A);
-    }
-    // ---------------- probabilities: p = 2^{-n/2} WHT(r on {I,Z}^n)
-    for (int S = threadIdx.x; S < N; S += blockDim.x) z[S] = (double)r[zs_index(S, n)];
-    __syncthreads();
-    wht(z, N);
-    const double scale = 1.0 / sqrt((double)N);
-    double ll = 0.0;
-    for (int J = threadIdx.x; J < N; J += blockDim.x) {
-      double p = z[J] * scale;
-      if (A.probs) A.probs[out0 + J] = (float)p;
-      if (A.counts) {
-        const int cnt = A.counts[out0 + J];
-        if (!(p > 0.0)) p = 1e-300;
-        if (cnt > 0) ll += (double)cnt * log(p);
-        z[J] = cnt > 0 ? (double)cnt / p : 0.0;   // seed weights dl/dp_J
-      }
-    }
-    if (A.counts) {
-      const double tot = block_sum_dm(ll, red);
-      if (threadIdx.x == 0 && A.loglik) A.loglik[c] = tot;
-    }
-    if constexpr (!GRAD) {
-      __syncthreads();
-      continue;
-    }
-    // ---------------- adjoint
-    __syncthreads();
-    wht(z, N);
-    // lambda is linear in the seed: keep it in fp32 as lambda / lmax (no
-    // overflow when some n_J / p_J is huge) and scale the fp64 sums back
-    double lmax = 0.0;
-    for (int S = 0; S < N; ++S) lmax = fmax(lmax, fabs(z[S]));
-    const double lscale = lmax > 0.0 ? scale / lmax : 0.0;
-    for (int i = threadIdx.x; i < Dn; i += blockDim.x) lam[i] = 0.f;
-    __syncthreads();
-    for (int S = threadIdx.x; S < N; S += blockDim.x) lam[zs_index(S, n)] = (float)(z[S] * lscale);
-    __syncthreads();
-    double g[4] = {0, 0, 0, 0};
-    const int nseg = (L + A.K - 1) / A.K;
-    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
-      const int k0 = sgi * A.K, k1 = min(L, k0 + A.K);
-      // recompute the states before each op of the segment
-      const float* ck = ckpt + (size_t)sgi * D;
-      for (int i = threadIdx.x; i < Dn; i += blockDim.x) r[i] = ck[i];
-      __syncthreads();
-      for (int k = k0; k < k1; ++k) {
-        float* dst = segbuf + (size_t)(k - k0) * D;
-        for (int i = threadIdx.x; i < Dn; i += blockDim.x) dst[i] = r[i];
-        if (k + 1 == k1) break;
-        const int32_t* op = ops + 4 * k;
-        if (op[0] == QS_DM_PTM1) {
-          __syncthreads();
-          if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
-          __syncthreads();
-        }
-        __syncthreads();
-        apply_op_fused(r, n, op, tabs, user4, A);
-      }
-      __syncthreads();
-      for (int k = k1 - 1; k >= k0; --k) {
-        const int32_t* op = ops + 4 * k;
-        if (op[0] == QS_DM_PTM1) {
-          if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
-        }
-        const int ns = op_nsub(op, n);
-        const float* before = segbuf + (size_t)(k - k0) * D;
-        __syncthreads();
-        // the states before the sub-ops, once: s_0 = before, s_{j+1} = sub_j s_j;
-        // the last stays in tmp, the earlier ones with parameters go to subst
-        if (ns > 1) {
-          for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = before[i];
-          __syncthreads();
-          for (int j = 0; j + 1 < ns; ++j) {
-            apply_sub(tmp, n, op_subop(op, j), tabs, user4, A, false);
-            __syncthreads();
-            if (j + 2 < ns && op_subop(op, j + 1).kind == 0)
-              for (int i = threadIdx.x; i < Dn; i += blockDim.x) subst[(size_t)(j + 1) * D + i] = tmp[i];
-          }
-        }
-        for (int j = ns - 1; j >= 0; --j) {
-          const SubOp sj = op_subop(op, j);
-          if (sj.kind == 0) {
-            const float* sv = j + 1 == ns ? (ns > 1 ? tmp : before) : (j == 0 ? before : subst + (size_t)j * D);
-            adj4(lam, sv, n, sj.q, tabs + 16 * sj.table, tabs, sj.dtab, g);
-          } else {
-            apply_sub(lam, n, sj, tabs, user4, A, true);
-          }
-          __syncthreads();
-        }
-      }
-    }
-    for (int pidx = 0; pidx < 4; ++pidx) {
-      const double tot = block_sum_dm(g[pidx], red);
-      if (threadIdx.x == 0) A.grad[4 * c + pidx] = tot * lmax;
-    }
+    dm_circuit<GRAD>(A, c, n, L, ops, out0, D, tabs, user4, z, r, lam, tmp, red, s_ops, ckpt, segbuf, subst);
     __syncthreads();
   }
 }

@@ -168,6 +168,21 @@ def test_full_batch_4096_properties(qs):
                                    NZ.circuit_probabilities(n, ops, params), atol=2e-5)
 
 
+def test_gradient_is_reproducible(qs):
+    # one circuit's arithmetic does not depend on which CTA runs it or when: three
+    # runs of the full batch (circuits handed out by an atomic counter, so the
+    # assignment changes) give bit-identical gradients.  A missing barrier between
+    # the sub-op state copies and the next sub-op showed up here as ~1e-4 jitter.
+    batch = W.noisy_batch(count=4096, seed=4001)
+    batch.counts = W.synthetic_counts(batch, 1000, seed=4002)
+    dev = qs.NoisyBatchDevice(batch)
+    runs = [tuple(x.cpu().numpy().copy() for x in dev.run(grad=True)) for _ in range(3)]
+    for p, ll, g in runs[1:]:
+        assert np.array_equal(p, runs[0][0])
+        assert np.array_equal(ll, runs[0][1])
+        assert np.array_equal(g, runs[0][2])
+
+
 def test_long_circuits_five_and_six_qubits_vs_oracle(qs):
     # the largest registers at full length (L = 200..256): every outcome against the
     # Kraus-map oracle, within the fp32 bound L * u ~ 1.5e-5 of the docstring
