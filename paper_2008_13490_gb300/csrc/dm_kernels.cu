@@ -16,8 +16,8 @@
 //                     diag(1, f, f, f), f = 1 - 4p/3
 //   amplitude damping, decay parameter 1, rate g (Eqs. (singletAmplitudeDampingChannel1-2)):
 //                     I -> I + g z, x -> s x, y -> s y, z -> (1-g) z, s = sqrt(1-g)
-//   CZ: a signed permutation of the 16 two-qubit Paulis (computed on the host
-//       from the trace formula).
+//   CZ: a signed permutation of the 16 two-qubit Paulis (evaluated from the
+//       trace formula at compile time).
 // The noise channel after an op is C = AD(g) DEP(p) on each touched qubit.
 //
 // Gradient of l = sum_J n_J log p_J by an adjoint sweep: lambda_L = dl/dr =
@@ -28,9 +28,6 @@
 
 #include <cmath>
 #include <vector>
-
-#include <cmath>
-#include <mutex>
 
 #include "internal.h"
 
@@ -58,10 +55,6 @@ struct DmArgs {
   float* scratch;              // per CTA: (nseg + K) * 4^max_q floats
   int* work;                   // work counter (zeroed before launch)
   const int* order;            // circuits in the order they are handed out, or NULL
-  int8_t cz_dst[16];            // CZ: Pauli string j maps to +-(string cz_dst[j])
-  int8_t cz_sgn[16];
-  int8_t cz_inv[16];            // inverse: string l comes from cz_inv[l] with sign cz_isgn[l]
-  int8_t cz_isgn[16];
 };
 
 // tables in shared memory (16 floats each)
@@ -187,18 +180,166 @@ struct Off4 {
   __device__ __forceinline__ int operator[](int d) const { return ((d & 1) ? o1 : 0) ^ ((d & 2) ? o2 : 0); }
 };
 
-// r <- G r (or G^T r) on digit q; G row-major 4x4 (output digit, input digit).
-__device__ void apply4(float* r, int n, int q, const float* Gs, bool transpose) {
+// CZ conjugation as a signed permutation of the 16 two-qubit Pauli strings (index
+// 4 d_a + d_b, digits I, x, y, z): G_ij = Tr(P_i U P_j U^dagger) / 4 with
+// U = diag(1, 1, 1, -1), evaluated at compile time in Gaussian integers (the Pauli
+// matrices' entries are 0, +-1, +-i) and packed 4 bits (string) / 1 bit (sign)
+// per entry, so that the sweeps' loads and signs fold into constants.
+namespace czc {
+struct Gi {
+  int re, im;
+};
+constexpr Gi mul(Gi a, Gi b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+constexpr Gi pauli(int d, int r, int c) {   // I, X, Y = [[0, -i], [i, 0]], Z
+  return d == 0   ? Gi{r == c ? 1 : 0, 0}
+         : d == 1 ? Gi{r != c ? 1 : 0, 0}
+         : d == 2 ? Gi{0, r == c ? 0 : (r == 0 ? -1 : 1)}
+                  : Gi{r == c ? (r == 0 ? 1 : -1) : 0, 0};
+}
+constexpr Gi pauli2(int idx, int r, int c) {   // qubit a (digit idx >> 2) most significant
+  return mul(pauli(idx >> 2, r >> 1, c >> 1), pauli(idx & 3, r & 1, c & 1));
+}
+constexpr int trace4(int i, int j) {   // 4 G_ij = sum_{r,c} P_i[r][c] u_c P_j[c][r] u_r
+  int t = 0;
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) t += (r == 3 ? -1 : 1) * (c == 3 ? -1 : 1) * mul(pauli2(i, r, c), pauli2(j, c, r)).re;
+  return t;
+}
+constexpr int image(int j) {   // the string P_j goes to
+  for (int i = 0; i < 16; ++i)
+    if (trace4(i, j) != 0) return i;
+  return -1;
+}
+constexpr bool is_signed_permutation() {
+  bool hit[16] = {};
+  for (int j = 0; j < 16; ++j) {
+    int nz = 0;
+    for (int i = 0; i < 16; ++i) {
+      const int t = trace4(i, j);
+      if (t != 0) {
+        if (t != 4 && t != -4) return false;
+        ++nz;
+      }
+    }
+    if (nz != 1 || hit[image(j)]) return false;
+    hit[image(j)] = true;
+  }
+  return true;
+}
+constexpr uint64_t pack_dst() {
+  uint64_t p = 0;
+  for (int j = 0; j < 16; ++j) p |= (uint64_t)image(j) << (4 * j);
+  return p;
+}
+constexpr uint32_t pack_sgn() {
+  uint32_t p = 0;
+  for (int j = 0; j < 16; ++j) p |= (trace4(image(j), j) < 0 ? 1u : 0u) << j;
+  return p;
+}
+constexpr uint64_t pack_inv() {
+  uint64_t p = 0;
+  for (int j = 0; j < 16; ++j) p |= (uint64_t)j << (4 * image(j));
+  return p;
+}
+constexpr uint32_t pack_isgn() {
+  uint32_t p = 0;
+  for (int j = 0; j < 16; ++j) p |= (trace4(image(j), j) < 0 ? 1u : 0u) << image(j);
+  return p;
+}
+}  // namespace czc
+static_assert(czc::is_signed_permutation(), "CZ must permute the Pauli strings up to sign");
+constexpr uint64_t kCzDst = czc::pack_dst();    // string j -> +-(string dst(j))
+constexpr uint32_t kCzSgn = czc::pack_sgn();
+constexpr uint64_t kCzInv = czc::pack_inv();    // string l <- +-(string inv(l))
+constexpr uint32_t kCzISgn = czc::pack_isgn();
+__device__ __forceinline__ int cz_dst(int j) { return (int)((kCzDst >> (4 * j)) & 15); }
+__device__ __forceinline__ int cz_inv(int l) { return (int)((kCzInv >> (4 * l)) & 15); }
+__device__ __forceinline__ bool cz_neg(int j) { return (kCzSgn >> j) & 1; }
+__device__ __forceinline__ bool cz_ineg(int l) { return (kCzISgn >> l) & 1; }
+
+// The threads that share one circuit's Pauli vector: a whole CTA (registers of 5
+// and 6 qubits) or one warp (up to kWarpMaxQ qubits, four circuits per CTA, no
+// block barriers).  rank / kSize stride the sweeps, sync() orders the
+// shared-memory updates between sweeps, kChunk ops are staged at a time.
+constexpr int kWarpMaxQ = 4;
+constexpr int kWarpD = 1 << (2 * kWarpMaxQ);   // 256 floats per Pauli vector
+constexpr int kWarpChunk = 64;
+struct CtaTeam {
+  static constexpr int kSize = kDmThreads;
+  static constexpr int kChunk = kOpChunk;
+  double* red;   // kDmThreads / 32 doubles
+  __device__ __forceinline__ int rank() const { return threadIdx.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ bool all(bool v) const { return __syncthreads_and(v) != 0; }
+  __device__ double sum(double v) const {   // valid in every thread
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < kDmThreads / 32; ++i) s += red[i];
+    __syncthreads();
+    return s;
+  }
+};
+struct WarpTeam {
+  static constexpr int kSize = 32;
+  static constexpr int kChunk = kWarpChunk;
+  int lane;
+  __device__ __forceinline__ int rank() const { return lane; }
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+  __device__ __forceinline__ bool all(bool v) const { return __all_sync(0xffffffffu, v) != 0; }
+  __device__ __forceinline__ double sum(double v) const {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  }
+};
+
+// Nonzero pattern of a 4x4 table, known at compile time.  Every table that
+// build_tables writes (the gates with their channel, the channel alone, and all
+// their derivatives) has row 0 = (m00, 0, 0, 0) and m10 = m20 = 0 (trace
+// preservation; amplitude damping feeds I into z only): kTP, 11 entries.  The
+// channel alone is diag(1, sf, sf, hf) plus m30: kChan, 5 entries.  User PTMs are
+// kDense.  The sweeps skip the structural zeros, adding the other terms in the
+// same order as the dense sums, so the results are the same bits.
+enum { kDense = 0, kTP = 1, kChan = 2 };
+template <int F>
+__host__ __device__ constexpr bool nz(int d, int e) {
+  return F == kDense ? true
+         : F == kTP  ? (d == 0 ? e == 0 : (d == 3 || e != 0))
+                     : (d == e || (d == 3 && e == 0));
+}
+
+// A 4x4 table (shared memory, 16-byte aligned) into registers with four 16-byte
+// loads (the same address in every lane: one broadcast wavefront each).
+__device__ __forceinline__ void load16(const float* src, float (&G)[16]) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 v = s4[i];
+    G[4 * i] = v.x;
+    G[4 * i + 1] = v.y;
+    G[4 * i + 2] = v.z;
+    G[4 * i + 3] = v.w;
+  }
+}
+
+// r <- G r (or G^T r, F = kDense only) on digit q; G row-major 4x4 (output digit,
+// input digit) of pattern F.
+template <class T, int F = kDense>
+__device__ void apply4(const T& t, float* r, int n, int q, const float* Gs, bool transpose) {
   const int groups = 1 << (2 * (n - 1));
   // the matrix in registers once per sweep
-  float G[16];
+  float G0[16], G[16];
+  load16(Gs, G0);
 #pragma unroll
   for (int d = 0; d < 4; ++d)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) G[d * 4 + e] = transpose ? Gs[e * 4 + d] : Gs[d * 4 + e];
+    for (int e = 0; e < 4; ++e) G[d * 4 + e] = transpose ? G0[e * 4 + d] : G0[d * 4 + e];
   const int st = 1 << (2 * q);
   const Off4 od(st);
-  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+  for (int g = t.rank(); g < groups; g += T::kSize) {
     const int base = swz(group_base(g, q));
     float x[4], y[4];
 #pragma unroll
@@ -207,7 +348,8 @@ __device__ void apply4(float* r, int n, int q, const float* Gs, bool transpose) 
     for (int d = 0; d < 4; ++d) {
       float acc = 0.f;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc = fmaf(G[d * 4 + e], x[e], acc);
+      for (int e = 0; e < 4; ++e)
+        if (nz<F>(d, e)) acc = fmaf(G[d * 4 + e], x[e], acc);
       y[d] = acc;
     }
 #pragma unroll
@@ -215,52 +357,46 @@ __device__ void apply4(float* r, int n, int q, const float* Gs, bool transpose) 
   }
 }
 
-// Adjoint of one 4x4 sub-op on digit q in one sweep.  Every derivative term
+// Adjoint of one 4x4 sub-op on digit q in one sweep (a built-in table: pattern
+// kTP, the derivative tables too, so the other entries of M are never needed).  Every derivative term
 // lam . (dG x) (lam after the sub-op, x the state before it) equals
 // sum_{d,e} dG[d][e] M[d][e] with M = sum over groups of lam x^T, so the sweep
 // accumulates M (16 FP32 sums per thread), updates lam <- G^T lam in place, and
 // contracts M with each parameter's derivative table once at the end (per-thread
 // partials added to g in FP64).  x may be global (a stored state) or shared.
-__device__ __forceinline__ void adj4(float* lam, const float* x_src, int n, int q, const float* Gs,
+template <class T>
+__device__ __forceinline__ void adj4(const T& t, float* lam, const float* x_src, int n, int q, const float* Gs,
                                      const float* tabs, const int* dtab, double* g) {
   const int groups = 1 << (2 * (n - 1));
   float G[16], M[16];
+  load16(Gs, G);
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    G[i] = Gs[i];
-    M[i] = 0.f;
-  }
-  auto group = [&](const float (&x)[4], float (&l)[4]) {
+  for (int i = 0; i < 16; ++i) M[i] = 0.f;
+  const int st = 1 << (2 * q);
+  const Off4 od(st);
+  for (int gi = t.rank(); gi < groups; gi += T::kSize) {
+    const int base = swz(group_base(gi, q));
+    float x[4], l[4], y[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      x[d] = x_src[base ^ od[d]];
+      l[d] = lam[base ^ od[d]];
+    }
 #pragma unroll
     for (int d = 0; d < 4; ++d)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) M[d * 4 + e] = fmaf(l[d], x[e], M[d * 4 + e]);
-    float y[4];
+      for (int e = 0; e < 4; ++e)
+        if (nz<kTP>(d, e)) M[d * 4 + e] = fmaf(l[d], x[e], M[d * 4 + e]);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       float acc = 0.f;
 #pragma unroll
-      for (int d = 0; d < 4; ++d) acc = fmaf(G[d * 4 + e], l[d], acc);
+      for (int d = 0; d < 4; ++d)
+        if (nz<kTP>(d, e)) acc = fmaf(G[d * 4 + e], l[d], acc);
       y[e] = acc;
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) l[e] = y[e];
-  };
-  {
-    const int st = 1 << (2 * q);
-    const Off4 od(st);
-    for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
-      const int base = swz(group_base(gi, q));
-      float x[4], l[4];
-#pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        x[d] = x_src[base ^ od[d]];
-        l[d] = lam[base ^ od[d]];
-      }
-      group(x, l);
-#pragma unroll
-      for (int d = 0; d < 4; ++d) lam[base ^ od[d]] = l[d];
-    }
+    for (int d = 0; d < 4; ++d) lam[base ^ od[d]] = y[d];
   }
 #pragma unroll
   for (int pidx = 0; pidx < 4; ++pidx)
@@ -268,7 +404,8 @@ __device__ __forceinline__ void adj4(float* lam, const float* x_src, int n, int 
       const float* dG = tabs + 16 * dtab[pidx];
       float acc = 0.f;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) acc = fmaf(dG[i], M[i], acc);
+      for (int i = 0; i < 16; ++i)
+        if (nz<kTP>(i >> 2, i & 3)) acc = fmaf(dG[i], M[i], acc);
       g[pidx] += (double)acc;
     }
 }
@@ -277,35 +414,41 @@ __device__ __forceinline__ int group_base2(int g, int lo_q, int hi_q) {
   return group_base(group_base(g, lo_q), hi_q);
 }
 
-// two-digit ops: local index 4*d_a + d_b
-__device__ void apply_cz(float* r, int n, int a, int b, const DmArgs& A, bool transpose) {
+// two-digit ops: local index 4*d_a + d_b.  The CZ permutation goes through the
+// load addresses (forward: y[l] = +-x[inv(l)]; transpose: y[j] = +-x[dst(j)]),
+// so every register index stays a compile-time constant.
+template <class T, bool TR>
+__device__ void apply_cz_t(const T& t, float* r, int n, int a, int b) {
   const int groups = 1 << (2 * (n - 2));
   const int lo = a < b ? a : b, hi = a < b ? b : a;
-  const int sa = 1 << (2 * a), sb = 1 << (2 * b);
-  const Off4 oa(sa), ob(sb);
-  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+  const Off4 oa(1 << (2 * a)), ob(1 << (2 * b));
+  for (int g = t.rank(); g < groups; g += T::kSize) {
     const int base = swz(group_base2(g, lo, hi));
-    // forward: y[l] = isgn[l] x[inv[l]]; transpose: y[j] = sgn[j] x[dst[j]] (the
-    // permutation is applied through the shared-memory addresses of the loads, so
-    // every register index stays a compile-time constant)
     float y[16];
 #pragma unroll
     for (int l = 0; l < 16; ++l) {
-      const int src = transpose ? A.cz_dst[l] : A.cz_inv[l];
-      const float sg = (float)(transpose ? A.cz_sgn[l] : A.cz_isgn[l]);
-      y[l] = sg * r[base ^ oa[src >> 2] ^ ob[src & 3]];
+      const int src = TR ? cz_dst(l) : cz_inv(l);
+      const float v = r[base ^ oa[src >> 2] ^ ob[src & 3]];
+      y[l] = (TR ? cz_neg(l) : cz_ineg(l)) ? -v : v;
     }
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[base ^ oa[l >> 2] ^ ob[l & 3]] = y[l];
   }
 }
+template <class T>
+__device__ void apply_cz(const T& t, float* r, int n, int a, int b, bool transpose) {
+  if (transpose)
+    apply_cz_t<T, true>(t, r, n, a, b);
+  else
+    apply_cz_t<T, false>(t, r, n, a, b);
+}
 
-__device__ void apply16(float* r, int n, int a, int b, const double* G, bool transpose) {
+template <class T>
+__device__ void apply16(const T& t, float* r, int n, int a, int b, const double* G, bool transpose) {
   const int groups = 1 << (2 * (n - 2));
   const int lo = a < b ? a : b, hi = a < b ? b : a;
-  const int sa = 1 << (2 * a), sb = 1 << (2 * b);
-  const Off4 oa(sa), ob(sb);
-  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+  const Off4 oa(1 << (2 * a)), ob(1 << (2 * b));
+  for (int g = t.rank(); g < groups; g += T::kSize) {
     const int base = swz(group_base2(g, lo, hi));
     float x[16];
     for (int l = 0; l < 16; ++l) x[l] = r[base ^ oa[l >> 2] ^ ob[l & 3]];
@@ -322,102 +465,115 @@ __device__ void apply16(float* r, int n, int a, int b, const double* G, bool tra
 // addresses (CZ), then Ga on digit a, then Gb on digit b -- the same operations,
 // in the same order, as the separate one-digit passes, with one shared-memory
 // sweep and one barrier instead of two or three.
-template <bool CZ>
-__device__ void pass2(float* r, int n, int a, const float* Ga, int b, const float* Gb, const DmArgs& A) {
+template <class T, bool CZ, int FA, int FB>
+__device__ void pass2(const T& t, float* r, int n, int a, const float* Ga, int b, const float* Gb) {
   const int groups = 1 << (2 * (n - 2));
   const int lo = a < b ? a : b, hi = a < b ? b : a;
-  const int sa = 1 << (2 * a), sb = 1 << (2 * b);
-  const Off4 oa(sa), ob(sb);
-  const float* ga = Ga;   // shared memory (broadcast reads)
-  const float* gb = Gb;
-  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+  const Off4 oa(1 << (2 * a)), ob(1 << (2 * b));
+  // the tables' rows as 16-byte broadcast reads from shared memory, per group
+  // (both tables in registers for the whole sweep would not fit beside x and y)
+  const float4* ga = reinterpret_cast<const float4*>(Ga);
+  const float4* gb = reinterpret_cast<const float4*>(Gb);
+  for (int g = t.rank(); g < groups; g += T::kSize) {
     const int base = swz(group_base2(g, lo, hi));
     float x[16], y[16];
 #pragma unroll
     for (int l = 0; l < 16; ++l) {
-      const int src = CZ ? A.cz_inv[l] : l;
+      const int src = CZ ? cz_inv(l) : l;
       const float v = r[base ^ oa[src >> 2] ^ ob[src & 3]];
-      x[l] = CZ ? (float)A.cz_isgn[l] * v : v;
+      x[l] = (CZ && cz_ineg(l)) ? -v : v;
     }
 #pragma unroll
-    for (int db = 0; db < 4; ++db)
+    for (int d = 0; d < 4; ++d) {
+      const float4 row = ga[d];
+      const float gr[4] = {row.x, row.y, row.z, row.w};
 #pragma unroll
-      for (int d = 0; d < 4; ++d) {
+      for (int db = 0; db < 4; ++db) {
         float acc = 0.f;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc = fmaf(ga[d * 4 + e], x[4 * e + db], acc);
+        for (int e = 0; e < 4; ++e)
+          if (nz<FA>(d, e)) acc = fmaf(gr[e], x[4 * e + db], acc);
         y[4 * d + db] = acc;
       }
+    }
 #pragma unroll
-    for (int da = 0; da < 4; ++da)
+    for (int d = 0; d < 4; ++d) {
+      const float4 row = gb[d];
+      const float gr[4] = {row.x, row.y, row.z, row.w};
 #pragma unroll
-      for (int d = 0; d < 4; ++d) {
+      for (int da = 0; da < 4; ++da) {
         float acc = 0.f;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc = fmaf(gb[d * 4 + e], y[4 * da + e], acc);
+        for (int e = 0; e < 4; ++e)
+          if (nz<FB>(d, e)) acc = fmaf(gr[e], y[4 * da + e], acc);
         x[4 * da + d] = acc;
       }
+    }
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[base ^ oa[l >> 2] ^ ob[l & 3]] = x[l];
   }
 }
 
-__device__ void apply_sub(float* r, int n, const SubOp& s, const float* tabs, float* user4,
+template <class T>
+__device__ void apply_sub(const T& t, float* r, int n, const SubOp& s, const float* tabs, float* user4,
                           const DmArgs& A, bool transpose) {
   switch (s.kind) {
-    case 0: apply4(r, n, s.q, tabs + 16 * s.table, transpose); break;
-    case 1: apply_cz(r, n, s.q, s.b, A, transpose); break;
-    case 2: apply4(r, n, s.q, user4, transpose); break;
-    default: apply16(r, n, s.q, s.b, A.ptm2 + 256 * (size_t)s.table, transpose); break;
+    case 0: apply4<T, kTP>(t, r, n, s.q, tabs + 16 * s.table, false); break;   // never transposed
+    case 1: apply_cz(t, r, n, s.q, s.b, transpose); break;
+    case 2: apply4(t, r, n, s.q, user4, transpose); break;
+    default: apply16(t, r, n, s.q, s.b, A.ptm2 + 256 * (size_t)s.table, transpose); break;
   }
 }
 
-__device__ double block_sum_dm(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  __syncthreads();
-  return s;   // valid in every thread
-}
-
+// The circuit's PTM tables (forward and derivatives), by rank 0.  The products
+// C R^x and C R^y are written out entry by entry (C, R^x, R^y are sparse), in
+// FP64 and rounded once to FP32; the FP64 pipe is narrow, so the dense 4x4
+// products would hold the team for several microseconds per circuit.
 __device__ void build_tables(float* tabs, const double* prm) {
-  // thread 0 only
   const double tx = prm[0], ty = prm[1], p = prm[2], g = prm[3];
   const double f = 1.0 - 4.0 * p / 3.0, s = sqrt(1.0 - g);
-  double C[16] = {1, 0, 0, 0, 0, s * f, 0, 0, 0, 0, s * f, 0, g, 0, 0, (1 - g) * f};
-  double Cp[16] = {0, 0, 0, 0, 0, -4.0 * s / 3.0, 0, 0, 0, 0, -4.0 * s / 3.0, 0, 0, 0, 0,
-                   -(1 - g) * 4.0 / 3.0};
-  double Cg[16] = {0, 0, 0, 0, 0, -f / (2 * s), 0, 0, 0, 0, -f / (2 * s), 0, 1, 0, 0, -f};
-  const double cx = cos(tx), sx = sin(tx), cy = cos(ty), sy = sin(ty);
-  double RX[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, cx, -sx, 0, 0, sx, cx};
-  double dRX[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, -sx, -cx, 0, 0, cx, -sx};
-  double RY[16] = {1, 0, 0, 0, 0, cy, 0, sy, 0, 0, 1, 0, 0, -sy, 0, cy};
-  double dRY[16] = {0, 0, 0, 0, 0, -sy, 0, cy, 0, 0, 0, 0, 0, -cy, 0, -sy};
-  auto mul = [](const double* A, const double* B, float* out) {
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) {
-        double acc = 0;
-        for (int k = 0; k < 4; ++k) acc += A[i * 4 + k] * B[k * 4 + j];
-        out[i * 4 + j] = (float)acc;
-      }
+  const double sf = s * f, hf = (1.0 - g) * f;   // C = [[1,0,0,0],[0,sf,0,0],[0,0,sf,0],[g,0,0,hf]]
+  const double dsf_p = -4.0 * s / 3.0, dhf_p = -(1.0 - g) * 4.0 / 3.0;   // d/dp
+  const double dsf_g = -f / (2.0 * s), dhf_g = -f;                       // d/dgamma (and d g/dgamma = 1)
+  double cx, sx, cy, sy;
+  sincos(tx, &sx, &cx);
+  sincos(ty, &sy, &cy);
+  // row-major; row 0 is (m00, 0, 0, 0), column 0 below it (0, 0, m30)
+  auto put = [&](int tb, double m00, double m11, double m12, double m13, double m21, double m22,
+                 double m23, double m30, double m31, double m32, double m33) {
+    float* o = tabs + 16 * tb;
+    o[0] = (float)m00;
+    o[1] = 0.f;
+    o[2] = 0.f;
+    o[3] = 0.f;
+    o[4] = 0.f;
+    o[5] = (float)m11;
+    o[6] = (float)m12;
+    o[7] = (float)m13;
+    o[8] = 0.f;
+    o[9] = (float)m21;
+    o[10] = (float)m22;
+    o[11] = (float)m23;
+    o[12] = (float)m30;
+    o[13] = (float)m31;
+    o[14] = (float)m32;
+    o[15] = (float)m33;
   };
-  mul(C, RX, tabs + 16 * TB_GX);
-  mul(C, RY, tabs + 16 * TB_GY);
-  for (int i = 0; i < 16; ++i) tabs[16 * TB_C + i] = (float)C[i];
-  mul(C, dRX, tabs + 16 * TB_GX_T);
-  mul(Cp, RX, tabs + 16 * TB_GX_P);
-  mul(Cg, RX, tabs + 16 * TB_GX_G);
-  mul(C, dRY, tabs + 16 * TB_GY_T);
-  mul(Cp, RY, tabs + 16 * TB_GY_P);
-  mul(Cg, RY, tabs + 16 * TB_GY_G);
-  for (int i = 0; i < 16; ++i) {
-    tabs[16 * TB_C_P + i] = (float)Cp[i];
-    tabs[16 * TB_C_G + i] = (float)Cg[i];
-  }
+  // R^x = [[1,0,0,0],[0,1,0,0],[0,0,cx,-sx],[0,0,sx,cx]], dR^x/dtx = [[0..],[0..],[0,0,-sx,-cx],[0,0,cx,-sx]]
+  // C R^x: row 1 sf e1; row 2 sf (0,0,cx,-sx); row 3 (g, 0, hf sx, hf cx)
+  put(TB_GX, 1, sf, 0, 0, 0, sf * cx, -sf * sx, g, 0, hf * sx, hf * cx);
+  put(TB_GX_T, 0, 0, 0, 0, 0, -sf * sx, -sf * cx, 0, 0, hf * cx, -hf * sx);
+  put(TB_GX_P, 0, dsf_p, 0, 0, 0, dsf_p * cx, -dsf_p * sx, 0, 0, dhf_p * sx, dhf_p * cx);
+  put(TB_GX_G, 0, dsf_g, 0, 0, 0, dsf_g * cx, -dsf_g * sx, 1, 0, dhf_g * sx, dhf_g * cx);
+  // R^y = [[1,0,0,0],[0,cy,0,sy],[0,0,1,0],[0,-sy,0,cy]]
+  // C R^y: row 1 sf (0,cy,0,sy); row 2 sf e2; row 3 (g, -hf sy, 0, hf cy)
+  put(TB_GY, 1, sf * cy, 0, sf * sy, 0, sf, 0, g, -hf * sy, 0, hf * cy);
+  put(TB_GY_T, 0, -sf * sy, 0, sf * cy, 0, 0, 0, 0, -hf * cy, 0, -hf * sy);
+  put(TB_GY_P, 0, dsf_p * cy, 0, dsf_p * sy, 0, dsf_p, 0, 0, -dhf_p * sy, 0, dhf_p * cy);
+  put(TB_GY_G, 0, dsf_g * cy, 0, dsf_g * sy, 0, dsf_g, 0, 1, -dhf_g * sy, 0, dhf_g * cy);
+  put(TB_C, 1, sf, 0, 0, 0, sf, 0, g, 0, 0, hf);
+  put(TB_C_P, 0, dsf_p, 0, 0, 0, dsf_p, 0, 0, 0, 0, dhf_p);
+  put(TB_C_G, 0, dsf_g, 0, 0, 0, dsf_g, 0, 1, 0, 0, dhf_g);
 }
 
 // index of the Pauli string Z_S (digit 3 at the bits of S)
@@ -428,55 +584,87 @@ __device__ __forceinline__ int zs_index(int S, int n) {
   return idx;
 }
 
-__device__ void wht(double* z, int N) {
+template <class T>
+__device__ void wht(const T& t, double* z, int N) {
   for (int h = 1; h < N; h <<= 1) {
-    for (int i = threadIdx.x; i < N / 2; i += blockDim.x) {
+    for (int i = t.rank(); i < N / 2; i += T::kSize) {
       const int j = ((i & ~(h - 1)) << 1) | (i & (h - 1));
       const double a = z[j], b = z[j + h];
       z[j] = a + b;
       z[j + h] = a - b;
     }
-    __syncthreads();
+    t.sync();
   }
 }
 
 // One op forward with the fused two-digit passes: CZ as its permutation and both
 // channels in one pass, the idle op as channel pairs -- the operations of its
 // sub-ops in the same order, with the same arithmetic.  user4 holds the op's PTM
-// for QS_DM_PTM1.  Ends with a barrier.
-__device__ void apply_op_fused(float* r, int n, const int32_t* op, const float* tabs,
+// for QS_DM_PTM1.  Ends with a team sync.
+template <class T>
+__device__ void apply_op_fused(const T& t, float* r, int n, const int32_t* op, const float* tabs,
                                const float* user4, const DmArgs& A) {
   const int code = op[0], a = op[1], b = op[2];
   const float* C = tabs + 16 * TB_C;
   if (code == QS_DM_X90 || code == QS_DM_Y90) {
-    apply4(r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), false);
+    apply4<T, kTP>(t, r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), false);
   } else if (code == QS_DM_CZ) {
-    pass2<true>(r, n, a, C, b, C, A);
+    pass2<T, true, kChan, kChan>(t, r, n, a, C, b, C);
   } else if (code == QS_DM_IDLE) {
     for (int q = 0; q + 1 < n; q += 2) {
-      pass2<false>(r, n, q, C, q + 1, C, A);
-      __syncthreads();
+      pass2<T, false, kChan, kChan>(t, r, n, q, C, q + 1, C);
+      t.sync();
     }
-    if (n & 1) apply4(r, n, n - 1, C, false);
+    if (n & 1) apply4<T, kChan>(t, r, n, n - 1, C, false);
   } else if (code == QS_DM_PTM1) {
-    apply4(r, n, a, user4, false);
+    apply4(t, r, n, a, user4, false);
   } else {
-    apply16(r, n, a, b, A.ptm2 + 256 * (size_t)op[3], false);
+    apply16(t, r, n, a, b, A.ptm2 + 256 * (size_t)op[3], false);
   }
-  __syncthreads();
+  t.sync();
 }
 
-// Longest first: the persistent kernel hands out circuits in this order, so the
-// longest ones start in the first wave instead of setting the batch time at its
-// end.  Estimated cost (ops + 1) x (4^n + 64) (the Pauli-vector sweeps plus a
-// per-op floor), sorted descending with a bitonic network in shared memory
-// (keys: cost as float bits above the circuit index; one CTA, up to kOrderMax
-// circuits; padding keys 0 sort last).  Used for the gradient pass, whose
-// per-circuit time (forward, backward sweep, scratch traffic) makes its tail long;
-// the forward pass keeps index order, where long and short circuits mixed on one
-// SM overlap better (4096 mixed circuits: 1.40 ms in index order, 1.60 sorted;
-// the gradient 8.63 -> 6.51 ms sorted).
+// Hand-out order.  Circuits of up to kWarpMaxQ qubits come last (a CTA that
+// draws one switches to one circuit per warp for the rest of the launch).
+// Forward: the large circuits, then the small ones, each in index order (long and
+// short circuits mixed on one SM overlap better than longest first: 4096 mixed
+// circuits 1.40 ms in index order, 1.60 sorted by length); a one-CTA stable
+// partition.  Gradient: within each class longest first (estimated cost
+// (ops + 1) x (4^n + 64), the sweeps plus a per-op floor), sorted descending with
+// a bitonic network in shared memory (keys: class bit 63, bit 62 set, cost as
+// float bits in 32..61, circuit index; padding keys 0 sort last): the per-circuit
+// time of the gradient (forward, backward sweep, scratch traffic) makes its tail
+// long (8.63 -> 6.51 ms for 4096 circuits).  Up to kOrderMax circuits; larger
+// batches run in index order, every circuit on a whole CTA.
 constexpr int kOrderMax = 16384;
+
+__device__ __forceinline__ bool warp_sized(int q) { return q >= 1 && q <= kWarpMaxQ; }
+
+__global__ void __launch_bounds__(1024) dm_partition_kernel(const int32_t* __restrict__ nq, int n,
+                                                            int* __restrict__ order) {
+  __shared__ int cnt[1024];
+  const int per = (n + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(n, lo + per);
+  int big = 0;
+  for (int i = lo; i < hi; ++i) big += warp_sized(nq[i]) ? 0 : 1;
+  cnt[threadIdx.x] = big;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {   // inclusive scan (Hillis-Steele)
+    const int v = threadIdx.x >= o ? cnt[threadIdx.x - o] : 0;
+    __syncthreads();
+    cnt[threadIdx.x] += v;
+    __syncthreads();
+  }
+  const int nbig = cnt[1023];
+  int pb = cnt[threadIdx.x] - big;           // big circuits before this chunk
+  int ps = nbig + (lo < n ? lo : n) - pb;    // small circuits go after all big ones
+  for (int i = lo; i < hi; ++i) {
+    if (warp_sized(nq[i]))
+      order[ps++] = i;
+    else
+      order[pb++] = i;
+  }
+}
 
 __global__ void __launch_bounds__(1024) dm_order_kernel(const int32_t* __restrict__ nq,
                                                         const int64_t* __restrict__ op_off, int n,
@@ -487,12 +675,13 @@ __global__ void __launch_bounds__(1024) dm_order_kernel(const int32_t* __restric
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     unsigned long long k = 0;
     if (i < n) {
-      int q = nq[i];
-      q = q < 1 ? 1 : (q > kDmMaxQ ? kDmMaxQ : q);
+      const int q0 = nq[i];
+      const int q = q0 < 1 ? 1 : (q0 > kDmMaxQ ? kDmMaxQ : q0);
       long long L = op_off[i + 1] - op_off[i];
       L = L < 0 ? 0 : (L > (1 << 20) ? (1 << 20) : L);
-      const float cost = (float)(L + 1) * (float)((1 << (2 * q)) + 64);
-      k = ((unsigned long long)__float_as_uint(cost) << 32) | (unsigned)i;
+      const float cost = (float)(L + 1) * (float)((1 << (2 * q)) + 64);   // < 2^30 as float bits
+      k = ((unsigned long long)(warp_sized(q0) ? 0 : 1) << 63) | (1ull << 62) |
+          ((unsigned long long)__float_as_uint(cost) << 32) | (unsigned)i;
     }
     keys[i] = k;
   }
@@ -516,20 +705,30 @@ __global__ void __launch_bounds__(1024) dm_order_kernel(const int32_t* __restric
 }
 
 // dynamic shared memory: tables, user PTM, WHT buffer, then the Pauli vector r
-// (and, with the gradient, lambda and a scratch vector)
+// (and, with the gradient, lambda and a scratch vector); in warp mode the space
+// from r on holds four per-warp regions (tables, user PTM, WHT buffer, r[, lam,
+// tmp], staged ops)
 constexpr int kDmHead = 16 * TB_COUNT + 16 + 128;   // floats before r (16-byte aligned)
-// One circuit c (validated, tables built) on one CTA.
-template <bool GRAD>
-__device__ __forceinline__ void dm_circuit(const DmArgs& A, int c, int n, int L, const int32_t* ops, int64_t out0,
-                                           int D, float* tabs, float* user4, double* z, float* r, float* lam,
-                                           float* tmp, double* red, int4* s_ops, float* ckpt, float* segbuf,
-                                           float* subst) {
-  constexpr bool want_grad = GRAD;
+constexpr int kWarpHead = 16 * TB_COUNT + 16 + 32;  // tables, user PTM, 16 doubles
+constexpr int kWarpRegionFwd = kWarpHead + kWarpD + 4 * kWarpChunk;
+constexpr int kWarpRegionGrad = kWarpHead + 3 * kWarpD + 4 * kWarpChunk;
+static_assert(kDmHead % 4 == 0 && kWarpHead % 4 == 0 && kWarpRegionFwd % 4 == 0 && kWarpRegionGrad % 4 == 0,
+              "16-byte aligned regions");
+
+// One validated circuit c on team t (tables built).  stride: floats between the
+// stored states in scratch.
+template <bool GRAD, class T>
+__device__ __forceinline__ void dm_circuit(const T& t, const DmArgs& A, int c, int n, int L, const int32_t* ops,
+                                           int64_t out0, int stride, float* tabs, float* user4, double* z,
+                                           float* r, float* lam, float* tmp, int4* s_ops, float* ckpt,
+                                           float* segbuf, float* subst) {
+  constexpr int kC = T::kChunk;
   const int N = 1 << n;
   const int Dn = 1 << (2 * n);
+  const int tid = t.rank();
   const float amp0 = 1.0f / sqrtf((float)N);
   // rho_0 = |0..0><0..0|: r_i = 2^{-n/2} on {I,Z}^n, 0 elsewhere
-  for (int i = threadIdx.x; i < Dn; i += blockDim.x) {
+  for (int i = tid; i < Dn; i += T::kSize) {
     bool iz = true;
     for (int b = 0; b < n; ++b) {
       const int d = (i >> (2 * b)) & 3;
@@ -537,61 +736,61 @@ __device__ __forceinline__ void dm_circuit(const DmArgs& A, int c, int n, int L,
     }
     r[swz(i)] = iz ? amp0 : 0.f;
   }
-  __syncthreads();
+  t.sync();
   // ---------------- forward
   const int4* ops4 = reinterpret_cast<const int4*>(ops);
   if constexpr (!GRAD) {
     for (int k = 0; k < L;) {
-      if ((k % kOpChunk) == 0) {   // stage the next chunk of ops (one coalesced read)
-        __syncthreads();
-        for (int t = threadIdx.x; t < kOpChunk && k + t < L; t += blockDim.x) s_ops[t] = ops4[k + t];
-        __syncthreads();
+      if ((k % kC) == 0) {   // stage the next chunk of ops (one coalesced read)
+        t.sync();
+        for (int u = tid; u < kC && k + u < L; u += T::kSize) s_ops[u] = ops4[k + u];
+        t.sync();
       }
-      const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kOpChunk]);
+      const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kC]);
       const int code = op[0], a = op[1];
-      const int32_t* nx = reinterpret_cast<const int32_t*>(&s_ops[(k + 1) % kOpChunk]);
-      if ((code == QS_DM_X90 || code == QS_DM_Y90) && k + 1 < L && (k + 1) % kOpChunk != 0 &&
+      const int32_t* nx = reinterpret_cast<const int32_t*>(&s_ops[(k + 1) % kC]);
+      if ((code == QS_DM_X90 || code == QS_DM_Y90) && k + 1 < L && (k + 1) % kC != 0 &&
           (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) && nx[1] != a) {
         // this op and the next act on different qubits: one two-digit pass
-        pass2<false>(r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), nx[1],
-                     tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY), A);
-        __syncthreads();
+        pass2<T, false, kTP, kTP>(t, r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), nx[1],
+                        tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY));
+        t.sync();
         k += 2;
         continue;
       }
       if (code == QS_DM_PTM1) {
-        if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
-        __syncthreads();
+        if (tid < 16) user4[tid] = (float)A.ptm1[16 * (size_t)op[3] + tid];
+        t.sync();
       }
-      apply_op_fused(r, n, op, tabs, user4, A);
+      apply_op_fused(t, r, n, op, tabs, user4, A);
       ++k;
     }
   }
   for (int k = 0; GRAD && k < L; ++k) {
-    if ((k % kOpChunk) == 0) {   // stage the next chunk of ops (one coalesced read)
-      __syncthreads();
-      for (int t = threadIdx.x; t < kOpChunk && k + t < L; t += blockDim.x) s_ops[t] = ops4[k + t];
-      __syncthreads();
+    if ((k % kC) == 0) {   // stage the next chunk of ops (one coalesced read)
+      t.sync();
+      for (int u = tid; u < kC && k + u < L; u += T::kSize) s_ops[u] = ops4[k + u];
+      t.sync();
     }
-    if (want_grad && (k % A.K) == 0) {
-      float* dst = ckpt + (size_t)(k / A.K) * D;
-      for (int i = threadIdx.x; i < Dn; i += blockDim.x) dst[i] = r[i];
-      __syncthreads();   // copies done before r is updated in place
+    if ((k % A.K) == 0) {
+      float* dst = ckpt + (size_t)(k / A.K) * stride;
+      for (int i = tid; i < Dn; i += T::kSize) dst[i] = r[i];
+      t.sync();   // copies done before r is updated in place
     }
-    const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kOpChunk]);
+    const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kC]);
     if (op[0] == QS_DM_PTM1) {
-      if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
-      __syncthreads();
+      if (tid < 16) user4[tid] = (float)A.ptm1[16 * (size_t)op[3] + tid];
+      t.sync();
     }
-    apply_op_fused(r, n, op, tabs, user4, A);
+    apply_op_fused(t, r, n, op, tabs, user4, A);
   }
   // ---------------- probabilities: p = 2^{-n/2} WHT(r on {I,Z}^n)
-  for (int S = threadIdx.x; S < N; S += blockDim.x) z[S] = (double)r[swz(zs_index(S, n))];
-  __syncthreads();
-  wht(z, N);
+  for (int S = tid; S < N; S += T::kSize) z[S] = (double)r[swz(zs_index(S, n))];
+  t.sync();
+  wht(t, z, N);
   const double scale = 1.0 / sqrt((double)N);
   double ll = 0.0;
-  for (int J = threadIdx.x; J < N; J += blockDim.x) {
+  for (int J = tid; J < N; J += T::kSize) {
     double p = z[J] * scale;
     if (A.probs) A.probs[out0 + J] = (float)p;
     if (A.counts) {
@@ -602,91 +801,161 @@ __device__ __forceinline__ void dm_circuit(const DmArgs& A, int c, int n, int L,
     }
   }
   if (A.counts) {
-    const double tot = block_sum_dm(ll, red);
-    if (threadIdx.x == 0 && A.loglik) A.loglik[c] = tot;
+    const double tot = t.sum(ll);
+    if (tid == 0 && A.loglik) A.loglik[c] = tot;
   }
   if constexpr (!GRAD) return;
   // ---------------- adjoint
-  __syncthreads();
-  wht(z, N);
+  t.sync();
+  wht(t, z, N);
   // lambda is linear in the seed: keep it in fp32 as lambda / lmax (no
   // overflow when some n_J / p_J is huge) and scale the fp64 sums back
   double lmax = 0.0;
   for (int S = 0; S < N; ++S) lmax = fmax(lmax, fabs(z[S]));
   const double lscale = lmax > 0.0 ? scale / lmax : 0.0;
-  for (int i = threadIdx.x; i < Dn; i += blockDim.x) lam[i] = 0.f;
-  __syncthreads();
-  for (int S = threadIdx.x; S < N; S += blockDim.x) lam[swz(zs_index(S, n))] = (float)(z[S] * lscale);
-  __syncthreads();
+  for (int i = tid; i < Dn; i += T::kSize) lam[i] = 0.f;
+  t.sync();
+  for (int S = tid; S < N; S += T::kSize) lam[swz(zs_index(S, n))] = (float)(z[S] * lscale);
+  t.sync();
   double g[4] = {0, 0, 0, 0};
   const int nseg = (L + A.K - 1) / A.K;
   for (int sgi = nseg - 1; sgi >= 0; --sgi) {
     const int k0 = sgi * A.K, k1 = min(L, k0 + A.K);
     // recompute the states before each op of the segment
-    const float* ck = ckpt + (size_t)sgi * D;
-    for (int i = threadIdx.x; i < Dn; i += blockDim.x) r[i] = ck[i];
-    __syncthreads();
+    const float* ck = ckpt + (size_t)sgi * stride;
+    for (int i = tid; i < Dn; i += T::kSize) r[i] = ck[i];
+    t.sync();
     for (int k = k0; k < k1; ++k) {
-      float* dst = segbuf + (size_t)(k - k0) * D;
-      for (int i = threadIdx.x; i < Dn; i += blockDim.x) dst[i] = r[i];
+      float* dst = segbuf + (size_t)(k - k0) * stride;
+      for (int i = tid; i < Dn; i += T::kSize) dst[i] = r[i];
       if (k + 1 == k1) break;
       const int32_t* op = ops + 4 * k;
       if (op[0] == QS_DM_PTM1) {
-        __syncthreads();
-        if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
-        __syncthreads();
+        t.sync();
+        if (tid < 16) user4[tid] = (float)A.ptm1[16 * (size_t)op[3] + tid];
+        t.sync();
       }
-      __syncthreads();
-      apply_op_fused(r, n, op, tabs, user4, A);
+      t.sync();
+      apply_op_fused(t, r, n, op, tabs, user4, A);
     }
-    __syncthreads();
+    t.sync();
     for (int k = k1 - 1; k >= k0; --k) {
       const int32_t* op = ops + 4 * k;
       if (op[0] == QS_DM_PTM1) {
-        if (threadIdx.x < 16) user4[threadIdx.x] = (float)A.ptm1[16 * (size_t)op[3] + threadIdx.x];
+        if (tid < 16) user4[tid] = (float)A.ptm1[16 * (size_t)op[3] + tid];
       }
       const int ns = op_nsub(op, n);
-      const float* before = segbuf + (size_t)(k - k0) * D;
-      __syncthreads();
+      const float* before = segbuf + (size_t)(k - k0) * stride;
+      t.sync();
       // the states before the sub-ops, once: s_0 = before, s_{j+1} = sub_j s_j;
       // the last stays in tmp, the earlier ones with parameters go to subst
       if (ns > 1) {
-        for (int i = threadIdx.x; i < Dn; i += blockDim.x) tmp[i] = before[i];
-        __syncthreads();
+        for (int i = tid; i < Dn; i += T::kSize) tmp[i] = before[i];
+        t.sync();
         for (int j = 0; j + 1 < ns; ++j) {
-          apply_sub(tmp, n, op_subop(op, j), tabs, user4, A, false);
-          __syncthreads();
+          apply_sub(t, tmp, n, op_subop(op, j), tabs, user4, A, false);
+          t.sync();
           if (j + 2 < ns && op_subop(op, j + 1).kind == 0) {
-            for (int i = threadIdx.x; i < Dn; i += blockDim.x) subst[(size_t)(j + 1) * D + i] = tmp[i];
-            __syncthreads();   // copied before sub-op j + 1 rewrites tmp
+            for (int i = tid; i < Dn; i += T::kSize) subst[(size_t)(j + 1) * stride + i] = tmp[i];
+            t.sync();   // copied before sub-op j + 1 rewrites tmp
           }
         }
       }
       for (int j = ns - 1; j >= 0; --j) {
         const SubOp sj = op_subop(op, j);
         if (sj.kind == 0) {
-          const float* sv = j + 1 == ns ? (ns > 1 ? tmp : before) : (j == 0 ? before : subst + (size_t)j * D);
-          adj4(lam, sv, n, sj.q, tabs + 16 * sj.table, tabs, sj.dtab, g);
+          const float* sv =
+              j + 1 == ns ? (ns > 1 ? tmp : before) : (j == 0 ? before : subst + (size_t)j * stride);
+          adj4(t, lam, sv, n, sj.q, tabs + 16 * sj.table, tabs, sj.dtab, g);
         } else {
-          apply_sub(lam, n, sj, tabs, user4, A, true);
+          apply_sub(t, lam, n, sj, tabs, user4, A, true);
         }
-        __syncthreads();
+        t.sync();
       }
     }
   }
   for (int pidx = 0; pidx < 4; ++pidx) {
-    const double tot = block_sum_dm(g[pidx], red);
-    if (threadIdx.x == 0) A.grad[4 * c + pidx] = tot * lmax;
+    const double tot = t.sum(g[pidx]);
+    if (tid == 0) A.grad[4 * c + pidx] = tot * lmax;
+  }
+}
+
+// Circuit c on team t: device-side validation (the arrays are caller-supplied
+// device memory; ops checked by the team in parallel), tables, then the circuit;
+// an invalid circuit gets NaN outputs.  Ends with a team sync.
+template <bool GRAD, class T>
+__device__ void run_circuit(const T& t, const DmArgs& A, int c, int stride, float* tabs, float* user4, double* z,
+                            float* r, float* lam, float* tmp, int4* s_ops, float* ckpt, float* segbuf,
+                            float* subst) {
+  const int tid = t.rank();
+  const int n = A.nq[c];
+  const int64_t o0 = A.op_off[c];
+  const int L = (int)(A.op_off[c + 1] - o0);
+  const int32_t* ops = A.ops + 4 * o0;
+  const int64_t out0 = A.out_off[c];
+  const int N = 1 << n;
+  bool ok = n >= 1 && n <= A.max_q && L >= 0 && L <= A.max_ops && A.out_off[c + 1] - out0 == N;
+  if (ok)
+    for (int k = tid; k < L; k += T::kSize) ok = ok && op_valid(ops + 4 * k, n, A);
+  const bool all_ok = t.all(ok);
+  if (all_ok && tid == 0) build_tables(tabs, A.params + 4 * c);
+  t.sync();
+  if (!all_ok) {
+    const float nanf_ = __int_as_float(0x7fc00000);
+    if (tid == 0) {
+      if (A.loglik) A.loglik[c] = __longlong_as_double(0x7ff8000000000000ll);
+      if (A.grad)
+        for (int k = 0; k < 4; ++k) A.grad[4 * c + k] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    if (A.probs && n >= 1 && n <= kDmMaxQ && A.out_off[c + 1] - out0 == N)
+      for (int J = tid; J < N; J += T::kSize) A.probs[out0 + J] = nanf_;
+  } else {
+    dm_circuit<GRAD>(t, A, c, n, L, ops, out0, stride, tabs, user4, z, r, lam, tmp, s_ops, ckpt, segbuf, subst);
+  }
+  t.sync();
+}
+
+// Warp mode: every warp of the CTA runs small circuits on its own, drawing the
+// next one from the hand-out counter; warp 0 starts with c (drawn by the CTA).
+template <bool GRAD>
+__device__ void dm_warps(const DmArgs& A, int c, float* base, float* scratch) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WarpTeam t{lane};
+  float* reg = base + (size_t)w * (GRAD ? kWarpRegionGrad : kWarpRegionFwd);
+  float* tabs = reg;
+  float* user4 = reg + 16 * TB_COUNT;
+  double* z = reinterpret_cast<double*>(user4 + 16);
+  float* r = reg + kWarpHead;
+  float* lam = r + kWarpD;
+  float* tmp = r + 2 * kWarpD;
+  int4* s_ops = reinterpret_cast<int4*>(r + (GRAD ? 3 : 1) * kWarpD);
+  const size_t per = (size_t)(A.nseg + A.K + kDmMaxQ) * kWarpD;
+  float* ckpt = scratch ? scratch + (size_t)w * per : nullptr;
+  float* segbuf = ckpt ? ckpt + (size_t)A.nseg * kWarpD : nullptr;
+  float* subst = ckpt ? ckpt + (size_t)(A.nseg + A.K) * kWarpD : nullptr;
+  auto draw = [&]() {
+    int v = 0;
+    if (lane == 0) v = atomicAdd(A.work, 1);
+    v = __shfl_sync(0xffffffffu, v, 0);
+    return v < A.n_circuits ? A.order[v] : A.n_circuits;
+  };
+  if (w != 0) c = draw();
+  while (c < A.n_circuits) {
+    run_circuit<GRAD>(t, A, c, kWarpD, tabs, user4, z, r, lam, tmp, s_ops, ckpt, segbuf, subst);
+    c = draw();
   }
 }
 
 // GRAD: the gradient kernel (forward with checkpoints, then the adjoint sweep);
 // otherwise probabilities / log-likelihood only, with one-qubit gate pairs fused
-// too and a third of the shared memory (more CTAs per SM)
+// too and a third of the shared memory (more CTAs per SM).  A CTA draws circuits
+// from the hand-out order; the first small one (up to kWarpMaxQ qubits; with an
+// order, all later ones are small too) switches it to warp mode.
 template <bool GRAD>
 __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmArgs A) {
   extern __shared__ __align__(16) float dsm[];
   const int D = 1 << (2 * A.max_q);
+  const int Dscr = D > 4 * kWarpD ? D : 4 * kWarpD;   // scratch floats per stored state and CTA
   float* tabs = dsm;                         // TB_COUNT * 16
   float* user4 = tabs + 16 * TB_COUNT;       // 16
   double* z = (double*)(user4 + 16);         // 64 doubles (8-byte aligned: offsets are multiples of 16 floats)
@@ -697,10 +966,11 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
   __shared__ int s_c;
   __shared__ int4 s_ops[kOpChunk];   // the current chunk of the circuit's ops
   float* my_scratch =
-      A.scratch ? A.scratch + (size_t)blockIdx.x * (size_t)(A.nseg + A.K + kDmMaxQ) * D : nullptr;
+      A.scratch ? A.scratch + (size_t)blockIdx.x * (size_t)(A.nseg + A.K + kDmMaxQ) * Dscr : nullptr;
   float* ckpt = my_scratch;
   float* segbuf = my_scratch ? my_scratch + (size_t)A.nseg * D : nullptr;
   float* subst = my_scratch ? my_scratch + (size_t)(A.nseg + A.K) * D : nullptr;
+  const CtaTeam t{red};
   swz_init();   // read after the first barrier of the loop below
 
   for (;;) {
@@ -712,64 +982,11 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
     const int c = s_c;
     __syncthreads();
     if (c >= A.n_circuits) break;
-    const int n = A.nq[c];
-    const int64_t o0 = A.op_off[c];
-    const int L = (int)(A.op_off[c + 1] - o0);
-    const int32_t* ops = A.ops + 4 * o0;
-    const int64_t out0 = A.out_off[c];
-    const int N = 1 << n;
-    // validation (device side: the arrays are caller-supplied device memory),
-    // ops checked by all threads in parallel
-    bool ok = n >= 1 && n <= A.max_q && L >= 0 && L <= A.max_ops && A.out_off[c + 1] - out0 == N;
-    if (ok)
-      for (int k = threadIdx.x; k < L; k += blockDim.x) ok = ok && op_valid(ops + 4 * k, n, A);
-    const bool all_ok = __syncthreads_and(ok) != 0;
-    if (all_ok && threadIdx.x == 0) build_tables(tabs, A.params + 4 * c);
-    __syncthreads();
-    if (!all_ok) {
-      const float nanf_ = __int_as_float(0x7fc00000);
-      if (threadIdx.x == 0) {
-        if (A.loglik) A.loglik[c] = __longlong_as_double(0x7ff8000000000000ll);
-        if (A.grad)
-          for (int k = 0; k < 4; ++k) A.grad[4 * c + k] = __longlong_as_double(0x7ff8000000000000ll);
-      }
-      if (A.probs && n >= 1 && n <= kDmMaxQ && A.out_off[c + 1] - out0 == N)
-        for (int J = threadIdx.x; J < N; J += blockDim.x) A.probs[out0 + J] = nanf_;
-      continue;
+    if (GRAD && A.order && warp_sized(A.nq[c])) {
+      dm_warps<GRAD>(A, c, r, my_scratch);
+      return;
     }
-    dm_circuit<GRAD>(A, c, n, L, ops, out0, D, tabs, user4, z, r, lam, tmp, red, s_ops, ckpt, segbuf, subst);
-    __syncthreads();
-  }
-}
-
-// CZ as a signed permutation of two-qubit Pauli strings, from
-// G_ij = Tr(P_i U P_j U^dagger) / 4 with U = diag(1, 1, 1, -1).
-void cz_table(int8_t* dst, int8_t* sgn) {
-  const cd I(0, 1);
-  const cd P[4][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}, {0, -I, I, 0}, {1, 0, 0, -1}};
-  const double u[4] = {1, 1, 1, -1};
-  auto pauli2 = [&](int idx, cd* M) {   // idx = 4*d_a + d_b, qubit a most significant
-    const cd* A = P[idx >> 2];
-    const cd* B = P[idx & 3];
-    for (int r = 0; r < 4; ++r)
-      for (int c = 0; c < 4; ++c) M[r * 4 + c] = A[(r >> 1) * 2 + (c >> 1)] * B[(r & 1) * 2 + (c & 1)];
-  };
-  for (int j = 0; j < 16; ++j) {
-    cd Pj[16], Pi[16], img[16];
-    pauli2(j, Pj);
-    for (int r = 0; r < 4; ++r)
-      for (int c = 0; c < 4; ++c) img[r * 4 + c] = u[r] * Pj[r * 4 + c] * u[c];
-    for (int i = 0; i < 16; ++i) {
-      pauli2(i, Pi);
-      cd tr = 0;
-      for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) tr += Pi[r * 4 + c] * img[c * 4 + r];
-      const double v = tr.real() / 4.0;
-      if (std::fabs(v) > 0.5) {
-        dst[j] = (int8_t)i;
-        sgn[j] = (int8_t)(v > 0 ? 1 : -1);
-      }
-    }
+    run_circuit<GRAD>(t, A, c, D, tabs, user4, z, r, lam, tmp, s_ops, ckpt, segbuf, subst);
   }
 }
 
@@ -858,18 +1075,15 @@ extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, doubl
   A.probs = probs;
   A.loglik = loglik;
   A.grad = grad;
-  cz_table(A.cz_dst, A.cz_sgn);
-  for (int j = 0; j < 16; ++j) {
-    A.cz_inv[A.cz_dst[j]] = (int8_t)j;
-    A.cz_isgn[A.cz_dst[j]] = A.cz_sgn[j];
-  }
 
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int D = 1 << (2 * A.max_q);
   const bool with_grad = grad != nullptr;
-  const size_t smem = (size_t)(kDmHead + (with_grad ? 3 : 1) * D) * sizeof(float);
+  const int warp_need = 4 * (with_grad ? kWarpRegionGrad : kWarpRegionFwd);
+  const int cta_need = (with_grad ? 3 : 1) * D;
+  const size_t smem = (size_t)(kDmHead + (cta_need > warp_need ? cta_need : warp_need)) * sizeof(float);
   auto kern = with_grad ? dm_batch_kernel<true> : dm_batch_kernel<false>;
   if (smem > 48 * 1024) {
     cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -881,15 +1095,20 @@ extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, doubl
   int grid = sms * per_sm;
   if (grid > b->n_circuits) grid = b->n_circuits;
 
-  const size_t scratch_floats = grad ? (size_t)grid * (A.nseg + A.K + kDmMaxQ) * D : 0;
+  const size_t Dscr = (size_t)(D > 4 * kWarpD ? D : 4 * kWarpD);
+  const size_t scratch_floats = grad ? (size_t)grid * (A.nseg + A.K + kDmMaxQ) * Dscr : 0;
+  // hand-out order: the gradient sorted (up to kOrderMax circuits), otherwise the
+  // stable partition large | small
   const bool sort = grad && A.n_circuits > 1 && A.n_circuits <= kOrderMax;
-  const size_t order_bytes = sort ? ((sizeof(int) * (size_t)A.n_circuits + 255) & ~size_t(255)) : 0;
+  const bool part = !sort && A.n_circuits > 1;
+  const size_t order_bytes =
+      (sort || part) ? ((sizeof(int) * (size_t)A.n_circuits + 255) & ~size_t(255)) : 0;
   const size_t bytes = 256 + order_bytes + scratch_floats * sizeof(float);
   void* mem = nullptr;
   cudaError_t e = cudaMallocAsync(&mem, bytes, stream);
   if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync (dm scratch)");
   A.work = (int*)mem;
-  A.order = sort ? (const int*)((char*)mem + 256) : nullptr;
+  A.order = (sort || part) ? (const int*)((char*)mem + 256) : nullptr;
   A.scratch = grad ? (float*)((char*)mem + 256 + order_bytes) : nullptr;
   e = cudaMemsetAsync(mem, 0, 256, stream);
   if (e != cudaSuccess) return cuda_status(e, "cudaMemsetAsync");
@@ -902,6 +1121,8 @@ extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, doubl
       if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute");
     }
     dm_order_kernel<<<1, 1024, osmem, stream>>>(A.nq, A.op_off, A.n_circuits, (int*)A.order);
+  } else if (part) {
+    dm_partition_kernel<<<1, 1024, 0, stream>>>(A.nq, A.n_circuits, (int*)A.order);
   }
   kern<<<grid, kDmThreads, smem, stream>>>(A);
   e = cudaGetLastError();
