@@ -460,20 +460,57 @@ __device__ void apply16(const T& t, float* r, int n, int a, int b, const double*
   }
 }
 
+// One 4x4 table of pattern F on digit a (stage_a: out[4d + j] = sum_e G[d][e] in[4e + j])
+// or digit b (stage_b: out[4j + d] = sum_e G[d][e] in[4j + e]) of a 16-element group
+// in registers; the table's rows are 16-byte broadcast reads from shared memory.
+template <int F>
+__device__ __forceinline__ void stage_a(const float* G, const float (&in)[16], float (&out)[16]) {
+  const float4* g4 = reinterpret_cast<const float4*>(G);
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const float4 row = g4[d];
+    const float gr[4] = {row.x, row.y, row.z, row.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (nz<F>(d, e)) acc = fmaf(gr[e], in[4 * e + j], acc);
+      out[4 * d + j] = acc;
+    }
+  }
+}
+template <int F>
+__device__ __forceinline__ void stage_b(const float* G, const float (&in)[16], float (&out)[16]) {
+  const float4* g4 = reinterpret_cast<const float4*>(G);
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const float4 row = g4[d];
+    const float gr[4] = {row.x, row.y, row.z, row.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (nz<F>(d, e)) acc = fmaf(gr[e], in[4 * j + e], acc);
+      out[4 * j + d] = acc;
+    }
+  }
+}
+
 // Forward passes over two digits a != b at once (16-element groups, local index
-// 4 d_a + d_b): an optional signed permutation applied through the load
-// addresses (CZ), then Ga on digit a, then Gb on digit b -- the same operations,
-// in the same order, as the separate one-digit passes, with one shared-memory
-// sweep and one barrier instead of two or three.
-template <class T, bool CZ, int FA, int FB>
-__device__ void pass2(const T& t, float* r, int n, int a, const float* Ga, int b, const float* Gb) {
+// 4 d_a + d_b), in this order: an optional table H on digit a (PRE, pattern kTP),
+// an optional signed permutation applied through the load addresses (CZ), Ga on
+// digit a, Gb on digit b, and optionally the table P on digit a and then on digit b
+// (POST, pattern kChan) -- the operations of the separate one-digit passes, in the
+// same order, with one shared-memory sweep and one barrier instead of several.
+template <class T, bool CZ, int FA, int FB, bool PRE = false, bool POST = false>
+__device__ void pass2(const T& t, float* r, int n, int a, const float* Ga, int b, const float* Gb,
+                      const float* H = nullptr, const float* P = nullptr) {
+  static_assert(!(CZ && PRE), "the permutation is applied at the loads");
   const int groups = 1 << (2 * (n - 2));
   const int lo = a < b ? a : b, hi = a < b ? b : a;
   const Off4 oa(1 << (2 * a)), ob(1 << (2 * b));
-  // the tables' rows as 16-byte broadcast reads from shared memory, per group
-  // (both tables in registers for the whole sweep would not fit beside x and y)
-  const float4* ga = reinterpret_cast<const float4*>(Ga);
-  const float4* gb = reinterpret_cast<const float4*>(Gb);
   for (int g = t.rank(); g < groups; g += T::kSize) {
     const int base = swz(group_base2(g, lo, hi));
     float x[16], y[16];
@@ -483,34 +520,40 @@ __device__ void pass2(const T& t, float* r, int n, int a, const float* Ga, int b
       const float v = r[base ^ oa[src >> 2] ^ ob[src & 3]];
       x[l] = (CZ && cz_ineg(l)) ? -v : v;
     }
+    if constexpr (PRE) {
+      stage_a<kTP>(H, x, y);
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const float4 row = ga[d];
-      const float gr[4] = {row.x, row.y, row.z, row.w};
-#pragma unroll
-      for (int db = 0; db < 4; ++db) {
-        float acc = 0.f;
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (nz<FA>(d, e)) acc = fmaf(gr[e], x[4 * e + db], acc);
-        y[4 * d + db] = acc;
-      }
+      for (int l = 0; l < 16; ++l) x[l] = y[l];
     }
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const float4 row = gb[d];
-      const float gr[4] = {row.x, row.y, row.z, row.w};
-#pragma unroll
-      for (int da = 0; da < 4; ++da) {
-        float acc = 0.f;
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (nz<FB>(d, e)) acc = fmaf(gr[e], y[4 * da + e], acc);
-        x[4 * da + d] = acc;
-      }
+    stage_a<FA>(Ga, x, y);
+    stage_b<FB>(Gb, y, x);
+    if constexpr (POST) {
+      stage_a<kChan>(P, x, y);
+      stage_b<kChan>(P, y, x);
     }
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[base ^ oa[l >> 2] ^ ob[l & 3]] = x[l];
+  }
+}
+
+// The idle op's channel C on every qubit but u and v, pairs of digits per sweep, a
+// single last digit alone; each sweep followed by a team sync.
+template <class T>
+__device__ void idle_rest(const T& t, float* r, int n, int u, int v, const float* C) {
+  int pend = -1;
+  for (int q = 0; q < n; ++q) {
+    if (q == u || q == v) continue;
+    if (pend < 0) {
+      pend = q;
+      continue;
+    }
+    pass2<T, false, kChan, kChan>(t, r, n, pend, C, q, C);
+    t.sync();
+    pend = -1;
+  }
+  if (pend >= 0) {
+    apply4<T, kChan>(t, r, n, pend, C, false);
+    t.sync();
   }
 }
 
@@ -624,45 +667,300 @@ __device__ void apply_op_fused(const T& t, float* r, int n, const int32_t* op, c
   t.sync();
 }
 
-// Hand-out order.  Circuits of up to kWarpMaxQ qubits come last (a CTA that
-// draws one switches to one circuit per warp for the rest of the launch).
-// Forward: the large circuits, then the small ones, each in index order (long and
-// short circuits mixed on one SM overlap better than longest first: 4096 mixed
-// circuits 1.40 ms in index order, 1.60 sorted by length); a one-CTA stable
-// partition.  Gradient: within each class longest first (estimated cost
-// (ops + 1) x (4^n + 64), the sweeps plus a per-op floor), sorted descending with
-// a bitonic network in shared memory (keys: class bit 63, bit 62 set, cost as
-// float bits in 32..61, circuit index; padding keys 0 sort last): the per-circuit
-// time of the gradient (forward, backward sweep, scratch traffic) makes its tail
-// long (8.63 -> 6.51 ms for 4096 circuits).  Up to kOrderMax circuits; larger
-// batches run in index order, every circuit on a whole CTA.
+// Hand-out order.  Small circuits come last: a CTA that draws one switches for the
+// rest of the launch to one circuit per warp (lane mode in the forward pass for 1
+// and 2 qubits, warp mode in the gradient pass for up to kWarpMaxQ qubits).
+// Forward: 5 and 6 qubits, then 3 and 4, then 1 and 2, each class in index order
+// (a one-CTA stable partition; longest first within the classes ran slower, 0.55
+// against 0.52 ms for 4096 mixed circuits: all long 6-qubit circuits then share
+// the SMs at once).  Gradient: small (up to kWarpMaxQ qubits) after large, longest
+// first within each (estimated cost (ops + 1) x (4^n + 64), the sweeps plus a
+// per-op floor), sorted descending with a bitonic network in shared memory (keys:
+// class bit 63, bit 62 set, cost as float bits in 32..61, circuit index; padding
+// keys 0 sort last): the per-circuit time of the gradient (forward, backward sweep,
+// scratch traffic) makes its tail long (8.63 -> 6.51 ms for 4096 circuits).  The
+// sort takes up to kOrderMax circuits; larger gradient batches use the partition.
 constexpr int kOrderMax = 16384;
 
 __device__ __forceinline__ bool warp_sized(int q) { return q >= 1 && q <= kWarpMaxQ; }
 
+// ---------------------------------------------------------------------------
+// Lane mode (forward, registers of one or two qubits): a warp runs one circuit
+// with the whole Pauli vector (4 or 16 floats) in registers, the same values in
+// every lane (no shared state, no divergence, no barrier per op); the lanes only
+// share the staging of the op stream (kWarpChunk ops per coalesced load into the
+// warp's slice of shared memory).  Each warp draws its next circuit from the
+// hand-out counter.  The arithmetic is that of the team sweeps: the same table
+// entries (built in FP64, rounded once), the same FP32 fused multiply-adds in the
+// same order per element, the probabilities and log-likelihood in FP64.
+constexpr int kThreadMaxQ = 2;
+__device__ __forceinline__ bool thread_sized(int q) { return q >= 1 && q <= kThreadMaxQ; }
+
+// The nonzero entries of the three built-in tables (rows/columns I, x, y, z), from
+// the same FP64 expressions as build_tables: C (channel), GX = C R^x, GY = C R^y.
+struct ThreadTabs {
+  float sf, hf, g;                       // C: m11 = m22 = sf, m30 = g, m33 = hf
+  float x22, x23, x32, x33;              // GX: m11 = sf, m30 = g, and these
+  float y11, y13, y31, y33;              // GY: m22 = sf, m30 = g, and these
+};
+__device__ ThreadTabs thread_tabs(const double* prm) {
+  const double tx = prm[0], ty = prm[1], p = prm[2], g = prm[3];
+  const double f = 1.0 - 4.0 * p / 3.0, s = sqrt(1.0 - g);
+  const double sf = s * f, hf = (1.0 - g) * f;
+  double cx, sx, cy, sy;
+  sincos(tx, &sx, &cx);
+  sincos(ty, &sy, &cy);
+  ThreadTabs T;
+  T.sf = (float)sf;
+  T.hf = (float)hf;
+  T.g = (float)g;
+  T.x22 = (float)(sf * cx);
+  T.x23 = (float)(-sf * sx);
+  T.x32 = (float)(hf * sx);
+  T.x33 = (float)(hf * cx);
+  T.y11 = (float)(sf * cy);
+  T.y13 = (float)(sf * sy);
+  T.y31 = (float)(-hf * sy);
+  T.y33 = (float)(hf * cy);
+  return T;
+}
+
+// Built-in table K (0 GX, 1 GY, 2 C) on the four values v of one digit, in place:
+// each output the FMA chain over its nonzero inputs in index order (the skipped
+// terms are exact zeros of the dense sum).
+template <int K>
+__device__ __forceinline__ void tab4(const ThreadTabs& T, float& v0, float& v1, float& v2, float& v3) {
+  const float x0 = v0, x1 = v1, x2 = v2, x3 = v3;
+  v0 = fmaf(1.0f, x0, 0.f);
+  if (K == 0) {        // GX rows: (1,0,0,0) (0,sf,0,0) (0,0,x22,x23) (g,0,x32,x33)
+    v1 = fmaf(T.sf, x1, 0.f);
+    v2 = fmaf(T.x23, x3, fmaf(T.x22, x2, 0.f));
+    v3 = fmaf(T.x33, x3, fmaf(T.x32, x2, fmaf(T.g, x0, 0.f)));
+  } else if (K == 1) { // GY rows: (1,0,0,0) (0,y11,0,y13) (0,0,sf,0) (g,y31,0,y33)
+    v1 = fmaf(T.y13, x3, fmaf(T.y11, x1, 0.f));
+    v2 = fmaf(T.sf, x2, 0.f);
+    v3 = fmaf(T.y33, x3, fmaf(T.y31, x1, fmaf(T.g, x0, 0.f)));
+  } else {             // C rows: (1,0,0,0) (0,sf,0,0) (0,0,sf,0) (g,0,0,hf)
+    v1 = fmaf(T.sf, x1, 0.f);
+    v2 = fmaf(T.sf, x2, 0.f);
+    v3 = fmaf(T.hf, x3, fmaf(T.g, x0, 0.f));
+  }
+}
+// A dense user table (FP64 in global memory, rounded to FP32 per entry) on v.
+__device__ __forceinline__ void user4(const double* G, float& v0, float& v1, float& v2, float& v3) {
+  const float x[4] = {v0, v1, v2, v3};
+  float y[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    float acc = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc = fmaf((float)G[4 * d + e], x[e], acc);
+    y[d] = acc;
+  }
+  v0 = y[0];
+  v1 = y[1];
+  v2 = y[2];
+  v3 = y[3];
+}
+
+// One-digit op on qubit q of an NQ-qubit register x (index sum_q d_q 4^q): K as in
+// tab4, K = 3 a user table.
+template <int NQ, int K>
+__device__ __forceinline__ void thread_digit(float* x, int q, const ThreadTabs& T, const double* U) {
+  auto one = [&](float& a, float& b, float& c, float& d) {
+    if (K == 3)
+      user4(U, a, b, c, d);
+    else
+      tab4<K>(T, a, b, c, d);
+  };
+  if (NQ == 1) {
+    one(x[0], x[1], x[2], x[3]);
+  } else if (q == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) one(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) one(x[j], x[4 + j], x[8 + j], x[12 + j]);
+  }
+}
+
+// Two-qubit ops of a two-qubit register (local index 4 d_a + d_b; A1 = (a == 1):
+// local index l sits at register l, else at its digit transpose).
+template <bool A1>
+__device__ __forceinline__ int loc(int l) { return A1 ? l : ((l & 3) << 2) | (l >> 2); }
+template <bool A1>
+__device__ __forceinline__ void thread_cz(float* x) {
+  float y[16];
+#pragma unroll
+  for (int l = 0; l < 16; ++l) {
+    const float v = x[loc<A1>(cz_inv(l))];
+    y[loc<A1>(l)] = cz_ineg(l) ? -v : v;
+  }
+#pragma unroll
+  for (int l = 0; l < 16; ++l) x[l] = y[l];
+}
+template <bool A1>
+__device__ __forceinline__ void thread_ptm2(float* x, const double* G) {
+  float in[16], y[16];
+#pragma unroll
+  for (int l = 0; l < 16; ++l) in[l] = x[loc<A1>(l)];
+  for (int d = 0; d < 16; ++d) {
+    float acc = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc = fmaf((float)G[d * 16 + e], in[e], acc);
+    y[d] = acc;
+  }
+#pragma unroll
+  for (int l = 0; l < 16; ++l) x[loc<A1>(l)] = y[l];
+}
+
+// Circuit c (n = NQ) on this warp (s_ops: the warp's kWarpChunk staged ops);
+// invalid circuits get NaN outputs.
+template <int NQ>
+__device__ void lane_circuit(const DmArgs& A, int c, int lane, int4* s_ops) {
+  constexpr int N = 1 << NQ, Dn = 1 << (2 * NQ);
+  const int64_t o0 = A.op_off[c];
+  const int L = (int)(A.op_off[c + 1] - o0);
+  const int64_t out0 = A.out_off[c];
+  bool ok = NQ <= A.max_q && L >= 0 && L <= A.max_ops && A.out_off[c + 1] - out0 == N;
+  float x[Dn];
+  const float amp0 = 1.0f / sqrtf((float)N);
+#pragma unroll
+  for (int i = 0; i < Dn; ++i) {
+    bool iz = true;
+#pragma unroll
+    for (int b = 0; b < NQ; ++b) {
+      const int d = (i >> (2 * b)) & 3;
+      iz = iz && (d == 0 || d == 3);
+    }
+    x[i] = iz ? amp0 : 0.f;
+  }
+  const ThreadTabs T = thread_tabs(A.params + 4 * c);
+  const int4* ops = reinterpret_cast<const int4*>(A.ops + 4 * o0);
+  for (int k = 0; ok && k < L; ++k) {
+    if ((k % kWarpChunk) == 0) {
+      __syncwarp();
+      for (int u = lane; u < kWarpChunk && k + u < L; u += 32) s_ops[u] = ops[k + u];
+      __syncwarp();
+    }
+    const int4 op = s_ops[k % kWarpChunk];
+    ok = op_valid(reinterpret_cast<const int32_t*>(&op), NQ, A);
+    if (!ok) break;
+    switch (op.x) {
+      case QS_DM_X90: thread_digit<NQ, 0>(x, op.y, T, nullptr); break;
+      case QS_DM_Y90: thread_digit<NQ, 1>(x, op.y, T, nullptr); break;
+      case QS_DM_PTM1: thread_digit<NQ, 3>(x, op.y, T, A.ptm1 + 16 * (size_t)op.w); break;
+      case QS_DM_IDLE:
+        thread_digit<NQ, 2>(x, 0, T, nullptr);
+        if (NQ == 2) thread_digit<NQ, 2>(x, 1, T, nullptr);
+        break;
+      default:   // CZ or a user two-qubit PTM (NQ == 2: validated)
+        if (NQ == 2) {
+          if (op.x == QS_DM_CZ) {
+            if (op.y == 1) thread_cz<true>(x); else thread_cz<false>(x);
+            thread_digit<NQ, 2>(x, op.y, T, nullptr);
+            thread_digit<NQ, 2>(x, op.z, T, nullptr);
+          } else {
+            const double* G = A.ptm2 + 256 * (size_t)op.w;
+            if (op.y == 1) thread_ptm2<true>(x, G); else thread_ptm2<false>(x, G);
+          }
+        }
+    }
+  }
+  __syncwarp();   // the staged ops are read before the next circuit restages them
+  if (!ok) {
+    if (A.loglik && lane == 0) A.loglik[c] = __longlong_as_double(0x7ff8000000000000ll);
+    if (A.probs && lane < N && A.out_off[c + 1] - out0 == N) A.probs[out0 + lane] = __int_as_float(0x7fc00000);
+    return;
+  }
+  // probabilities: p = 2^{-n/2} WHT(r on {I,Z}^n), the butterflies of wht()
+  double z[N];
+#pragma unroll
+  for (int S = 0; S < N; ++S) {
+    int idx = 0;
+#pragma unroll
+    for (int b = 0; b < NQ; ++b)
+      if ((S >> b) & 1) idx |= 3 << (2 * b);
+    z[S] = (double)x[idx];
+  }
+#pragma unroll
+  for (int h = 1; h < N; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const int j = ((i & ~(h - 1)) << 1) | (i & (h - 1));
+      const double a = z[j], b = z[j + h];
+      z[j] = a + b;
+      z[j + h] = a - b;
+    }
+  const double scale = 1.0 / sqrt((double)N);
+  double ll = 0.0;
+#pragma unroll
+  for (int J = 0; J < N; ++J) {
+    double p = z[J] * scale;
+    if (A.probs && lane == J) A.probs[out0 + J] = (float)p;
+    if (A.counts) {
+      const int cnt = A.counts[out0 + J];
+      if (!(p > 0.0)) p = 1e-300;
+      if (cnt > 0) ll += (double)cnt * log(p);
+    }
+  }
+  if (A.counts && A.loglik && lane == 0) A.loglik[c] = ll;
+}
+
+// Every warp of the CTA runs small circuits on its own; warp 0 starts with c.
+// s_ops: 4 x kWarpChunk staged ops.
+__device__ void dm_lanes(const DmArgs& A, int c, int4* s_ops) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto draw = [&]() {
+    int v = 0;
+    if (lane == 0) v = atomicAdd(A.work, 1);
+    v = __shfl_sync(0xffffffffu, v, 0);
+    return v < A.n_circuits ? A.order[v] : A.n_circuits;
+  };
+  if (w != 0) c = draw();
+  while (c < A.n_circuits) {
+    if (A.nq[c] == 1)
+      lane_circuit<1>(A, c, lane, s_ops + w * kWarpChunk);
+    else
+      lane_circuit<2>(A, c, lane, s_ops + w * kWarpChunk);
+    c = draw();
+  }
+}
+
+
+// class of a circuit in the forward hand-out order: 0 team (5, 6 qubits or
+// invalid), 1 team (3, 4 qubits), 2 lane mode (1, 2 qubits)
+__device__ __forceinline__ int fwd_class(int q) { return thread_sized(q) ? 2 : (warp_sized(q) ? 1 : 0); }
+
 __global__ void __launch_bounds__(1024) dm_partition_kernel(const int32_t* __restrict__ nq, int n,
                                                             int* __restrict__ order) {
-  __shared__ int cnt[1024];
+  __shared__ int cnt0[1024], cnt1[1024];
   const int per = (n + 1023) / 1024;
-  const int lo = threadIdx.x * per, hi = min(n, lo + per);
-  int big = 0;
-  for (int i = lo; i < hi; ++i) big += warp_sized(nq[i]) ? 0 : 1;
-  cnt[threadIdx.x] = big;
+  const int lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
+  int c0 = 0, c1 = 0;
+  for (int i = lo; i < hi; ++i) {
+    const int k = fwd_class(nq[i]);
+    c0 += k == 0;
+    c1 += k == 1;
+  }
+  cnt0[threadIdx.x] = c0;
+  cnt1[threadIdx.x] = c1;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {   // inclusive scan (Hillis-Steele)
-    const int v = threadIdx.x >= o ? cnt[threadIdx.x - o] : 0;
+  for (int o = 1; o < 1024; o <<= 1) {   // inclusive scans (Hillis-Steele)
+    const int v0 = threadIdx.x >= o ? cnt0[threadIdx.x - o] : 0;
+    const int v1 = threadIdx.x >= o ? cnt1[threadIdx.x - o] : 0;
     __syncthreads();
-    cnt[threadIdx.x] += v;
+    cnt0[threadIdx.x] += v0;
+    cnt1[threadIdx.x] += v1;
     __syncthreads();
   }
-  const int nbig = cnt[1023];
-  int pb = cnt[threadIdx.x] - big;           // big circuits before this chunk
-  int ps = nbig + (lo < n ? lo : n) - pb;    // small circuits go after all big ones
+  const int n0 = cnt0[1023], n1 = cnt1[1023];
+  int p0 = cnt0[threadIdx.x] - c0, p1 = cnt1[threadIdx.x] - c1;   // before this chunk
+  int p2 = n0 + n1 + (lo - p0 - p1);
+  p1 += n0;
   for (int i = lo; i < hi; ++i) {
-    if (warp_sized(nq[i]))
-      order[ps++] = i;
-    else
-      order[pb++] = i;
+    const int k = fwd_class(nq[i]);
+    order[k == 0 ? p0++ : (k == 1 ? p1++ : p2++)] = i;
   }
 }
 
@@ -748,13 +1046,39 @@ __device__ __forceinline__ void dm_circuit(const T& t, const DmArgs& A, int c, i
       }
       const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kC]);
       const int code = op[0], a = op[1];
+      // look-ahead within the staged chunk
+      const bool has1 = k + 1 < L && (k + 1) % kC != 0, has2 = has1 && k + 2 < L && (k + 2) % kC != 0;
       const int32_t* nx = reinterpret_cast<const int32_t*>(&s_ops[(k + 1) % kC]);
-      if ((code == QS_DM_X90 || code == QS_DM_Y90) && k + 1 < L && (k + 1) % kC != 0 &&
-          (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) && nx[1] != a) {
-        // this op and the next act on different qubits: one two-digit pass
-        pass2<T, false, kTP, kTP>(t, r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), nx[1],
-                        tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY));
+      const bool xy = code == QS_DM_X90 || code == QS_DM_Y90;
+      const float* C = tabs + 16 * TB_C;
+      if (xy && has1 && (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) && nx[1] != a) {
+        // this op and the next act on different qubits: one two-digit pass, which
+        // also takes the idle op's channels on both digits when one follows
+        const float* Ga = tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY);
+        const float* Gb = tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY);
+        const bool idle = has2 && s_ops[(k + 2) % kC].x == QS_DM_IDLE;
+        if (idle)
+          pass2<T, false, kTP, kTP, false, true>(t, r, n, a, Ga, nx[1], Gb, nullptr, C);
+        else
+          pass2<T, false, kTP, kTP>(t, r, n, a, Ga, nx[1], Gb);
         t.sync();
+        if (idle) idle_rest(t, r, n, a, nx[1], C);
+        k += idle ? 3 : 2;
+        continue;
+      }
+      if ((xy || code == QS_DM_CZ) && n >= 2 && has1 && nx[0] == QS_DM_IDLE) {
+        // a gate, then the idle op: the idle op's channels on the gate's digits
+        // (a and a partner for a one-qubit gate) go into the gate's pass
+        if (xy) {
+          const int pb = a == 0 ? 1 : 0;
+          pass2<T, false, kChan, kChan, true>(t, r, n, a, C, pb, C, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY));
+          t.sync();
+          idle_rest(t, r, n, a, pb, C);
+        } else {
+          pass2<T, true, kChan, kChan, false, true>(t, r, n, a, C, op[2], C, nullptr, C);
+          t.sync();
+          idle_rest(t, r, n, a, op[2], C);
+        }
         k += 2;
         continue;
       }
@@ -949,8 +1273,9 @@ __device__ void dm_warps(const DmArgs& A, int c, float* base, float* scratch) {
 // GRAD: the gradient kernel (forward with checkpoints, then the adjoint sweep);
 // otherwise probabilities / log-likelihood only, with one-qubit gate pairs fused
 // too and a third of the shared memory (more CTAs per SM).  A CTA draws circuits
-// from the hand-out order; the first small one (up to kWarpMaxQ qubits; with an
-// order, all later ones are small too) switches it to warp mode.
+// from the hand-out order; with an order, the first small one (all later ones are
+// small too) switches it to warp mode (gradient, up to kWarpMaxQ qubits) or lane
+// mode (forward, up to kThreadMaxQ qubits).
 template <bool GRAD>
 __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmArgs A) {
   extern __shared__ __align__(16) float dsm[];
@@ -984,6 +1309,10 @@ __global__ void __launch_bounds__(kDmThreads, GRAD ? 4 : 6) dm_batch_kernel(DmAr
     if (c >= A.n_circuits) break;
     if (GRAD && A.order && warp_sized(A.nq[c])) {
       dm_warps<GRAD>(A, c, r, my_scratch);
+      return;
+    }
+    if (!GRAD && A.order && thread_sized(A.nq[c])) {
+      dm_lanes(A, c, reinterpret_cast<int4*>(r));
       return;
     }
     run_circuit<GRAD>(t, A, c, D, tabs, user4, z, r, lam, tmp, s_ops, ckpt, segbuf, subst);

@@ -117,6 +117,40 @@ def test_user_ptms_match_unitary_evolution(qs):
     np.testing.assert_allclose(probs.cpu().numpy(), ref, atol=1e-6)
 
 
+def test_user_ptms_on_small_registers_in_every_orientation(qs):
+    # one- and two-qubit registers run one circuit per warp with the Pauli vector in
+    # registers: user PTMs on either qubit and both orientations of a two-qubit PTM
+    # (local digit order a, b), beside a 3-qubit circuit on a whole CTA
+    H = D.ptm_unitary(G.matrix("H"))
+    CN = D.ptm_unitary(G.CNOT)
+    ptm1 = torch.tensor(H.reshape(1, 16), device="cuda")
+    ptm2 = torch.tensor(CN.reshape(1, 256), device="cuda")
+    circuits = [
+        (2, [[4, 0, 0, 0], [5, 0, 1, 0], [4, 1, 0, 0]], [("H", (0,)), ("CNOT", (0, 1)), ("H", (1,))]),
+        (2, [[4, 1, 0, 0], [5, 1, 0, 0], [4, 0, 0, 0], [5, 0, 1, 0]],
+         [("H", (1,)), ("CNOT", (1, 0)), ("H", (0,)), ("CNOT", (0, 1))]),
+        (1, [[4, 0, 0, 0]], [("H", (0,))]),
+        (3, [[4, 2, 0, 0], [5, 2, 0, 0]], [("H", (2,)), ("CNOT", (2, 0))]),
+        (2, [], []),
+    ]
+    nq = torch.tensor([c[0] for c in circuits], dtype=torch.int32, device="cuda")
+    lens = [len(c[1]) for c in circuits]
+    op_off = torch.tensor(np.concatenate([[0], np.cumsum(lens)]), dtype=torch.int64, device="cuda")
+    sizes = [1 << c[0] for c in circuits]
+    out_off = torch.tensor(np.concatenate([[0], np.cumsum(sizes)]), dtype=torch.int64, device="cuda")
+    ops = torch.tensor(np.array([o for c in circuits for o in c[1]], dtype=np.int32), device="cuda")
+    params = torch.tensor([[1.0, 1.0, 1e-3, 1e-3]] * len(circuits), dtype=torch.float64, device="cuda")
+    probs = torch.empty(sum(sizes), dtype=torch.float32, device="cuda")
+    qs.dm_apply_channels(nq, op_off, ops, params, out_off, ptm1=ptm1, ptm2=ptm2, probs=probs, max_qubits=3)
+    p = probs.cpu().numpy()
+    o = 0
+    for n, _, gates in circuits:
+        circ = [(g, q, (), None) for g, q in gates]
+        ref = SV.probabilities(SV.apply_circuit(SV.basis(n), n, circ))
+        np.testing.assert_allclose(p[o:o + (1 << n)], ref, atol=1e-6)
+        o += 1 << n
+
+
 def test_invalid_ops_give_nan_and_do_not_disturb_others(qs):
     batch, _ = _with_counts(W.noisy_batch(count=3, seed=5, n_range=(2, 2), len_range=(3, 3)), 1)
     good = batch.ops.copy()
