@@ -1,6 +1,7 @@
 // C ABI entry points of the state-vector path (see include/qsim.h).
 #include <cstdarg>
 #include <cstdio>
+#include <complex>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -212,37 +213,104 @@ TileOp<R> cp_form(TileOp<R> t) {
 // Packs a run [i, j) of TK_CP ops into a TK_RUN header and its entries (see
 // tile_cp.h) at out[w..]; returns the next write index.
 template <typename R>
-int pack_run(const std::vector<TileOp<R>>& ops, size_t i, size_t j, TileOp<R>* out, int w) {
-  std::vector<RunEntry<R>> cat[6];   // scalar, slot 0..3, register pairs
+int pack_run(const std::vector<TileOp<R>>& ops, size_t i, size_t j, TileOp<R>* out, int w,
+             std::vector<C2<R>>& tabs, std::vector<RunJob>& jobs) {
+  using cd = std::complex<double>;
+  // context positions: 0 tile bit (the same for the whole CTA), 1 the constant
+  // one, 2 a lane or warp bit; bit value of a non-tile position for (lane, warp)
+  auto cls = [](int pos) { return pos < kCtxOne ? 0 : (pos == kCtxOne ? 1 : 2); };
+  auto bit = [](int pos, int lw) -> int {
+    if (pos == kCtxOne) return 1;
+    if (pos < kCtxWarp) return ((lw & 31) >> (pos - kCtxLane)) & 1;
+    return ((lw >> 5) >> (pos - kCtxWarp)) & 1;
+  };
+  std::vector<RunEntry<R>> res_s, res_f[4], job_s, job_f[4];
+  std::vector<cd> S, N[4], RR;
+  auto ones = [](std::vector<cd>& t, size_t n) {
+    if (t.empty()) t.assign(n, cd(1.0, 0.0));
+  };
   for (size_t o = i; o < j; ++o) {
     const TileOp<R>& t = ops[o];
     RunEntry<R> e;
     std::memset(&e, 0, sizeof(e));
     e.p = t.m0[0];
+    const cd p((double)t.m0[0].x, (double)t.m0[0].y);
     const bool ra = t.csrc == CS_REG, rb = t.dsrc == CS_REG;
     if (ra && rb) {
-      e.k = t.cbit;
-      e.l = t.dbit;
-      cat[5].push_back(e);
-    } else if (ra || rb) {   // the other bit decides: its context position
-      e.pa = ra ? t.pad[1] : t.pad[0];
-      cat[1 + (ra ? t.cbit : t.dbit)].push_back(e);
+      ones(RR, 16);
+      for (int r = 0; r < 16; ++r)
+        if ((r >> t.cbit) & (r >> t.dbit) & 1) RR[r] *= p;
+    } else if (ra || rb) {   // register slot k; the other bit decides
+      const int k = ra ? t.cbit : t.dbit, pa = ra ? t.pad[1] : t.pad[0];
+      if (cls(pa) != 0) {
+        ones(N[k], kRunTable);
+        for (int lw = 0; lw < kRunTable; ++lw)
+          if (bit(pa, lw)) N[k][lw] *= p;
+      } else {
+        e.pa = (uint8_t)pa;
+        job_f[k].push_back(e);
+      }
     } else {
-      e.pa = t.pad[0];
-      e.pb = t.pad[1];
-      cat[0].push_back(e);
+      const int pa = t.pad[0], pb = t.pad[1];
+      e.pa = (uint8_t)pa;
+      e.pb = (uint8_t)pb;
+      if (cls(pa) != 0 && cls(pb) != 0) {
+        ones(S, kRunTable);
+        for (int lw = 0; lw < kRunTable; ++lw)
+          if (bit(pa, lw) & bit(pb, lw)) S[lw] *= p;
+      } else if (cls(pa) != 2 && cls(pb) != 2) {
+        job_s.push_back(e);
+      } else {
+        res_s.push_back(e);
+      }
     }
   }
-  std::vector<RunEntry<R>> all;
+  // prologue jobs while they fit; the rest go to the per-thread lists
+  size_t need = !job_s.empty();
+  for (int k = 0; k < 4; ++k) need += !job_f[k].empty();
+  if (jobs.size() + need > (size_t)kMaxRunJobs) {
+    res_s.insert(res_s.end(), job_s.begin(), job_s.end());
+    job_s.clear();
+    for (int k = 0; k < 4; ++k) {
+      res_f[k].insert(res_f[k].end(), job_f[k].begin(), job_f[k].end());
+      job_f[k].clear();
+    }
+  }
+  RunHeader rh;
+  std::memset(&rh, 0, sizeof(rh));
+  rh.n_s = (uint16_t)res_s.size();
+  for (int k = 0; k < 4; ++k) rh.n_f[k] = (uint16_t)res_f[k].size();
+  rh.ubase = (uint16_t)jobs.size();
+  std::vector<RunEntry<R>> all(res_s);
+  for (int k = 0; k < 4; ++k) all.insert(all.end(), res_f[k].begin(), res_f[k].end());
+  auto add_job = [&](std::vector<RunEntry<R>>& list, bool scalar, int bitno) {
+    if (list.empty()) return;
+    RunJob jb;
+    std::memset(&jb, 0, sizeof(jb));
+    jb.op = (uint16_t)w;
+    jb.first = (uint16_t)all.size();
+    jb.count = (uint16_t)list.size();
+    jb.scalar = scalar ? 1 : 0;
+    jobs.push_back(jb);
+    rh.umask |= (uint8_t)(1u << bitno);
+    all.insert(all.end(), list.begin(), list.end());
+  };
+  add_job(job_s, true, 0);
+  for (int k = 0; k < 4; ++k) add_job(job_f[k], false, 1 + k);
+  rh.toff = (uint32_t)tabs.size();
+  auto add_tab = [&](const std::vector<cd>& t, int bitno) {
+    if (t.empty()) return;
+    rh.tmask |= (uint8_t)(1u << bitno);
+    for (const cd& x : t) tabs.push_back(C2<R>{(R)x.real(), (R)x.imag()});
+  };
+  add_tab(S, 0);
+  for (int k = 0; k < 4; ++k) add_tab(N[k], 1 + k);
+  add_tab(RR, 5);
   TileOp<R> h;
   std::memset(&h, 0, sizeof(h));
   h.kind = TK_RUN;
-  uint16_t cnt[6];
-  for (int c = 0; c < 6; ++c) {
-    cnt[c] = (uint16_t)cat[c].size();
-    all.insert(all.end(), cat[c].begin(), cat[c].end());
-  }
-  std::memcpy(&h.m0[0], cnt, sizeof(cnt));
+  static_assert(sizeof(RunHeader) <= sizeof(h.m0), "run header fits the op's matrix");
+  std::memcpy(&h.m0[0], &rh, sizeof(rh));
   const size_t per = sizeof(TileOp<R>) / sizeof(RunEntry<R>);
   const size_t nslots = (all.size() + per - 1) / per;
   h.slot = (uint8_t)nslots;
@@ -256,14 +324,17 @@ int pack_run(const std::vector<TileOp<R>>& ops, size_t i, size_t j, TileOp<R>* o
 
 // The kernel-parameter image of one forward tile pass: ops converted per
 // precision, controlled phases in their TK_CP form, and runs of at least kRunMin
-// of them packed into TK_RUN entry lists (at most 255 op slots each, 5 entries per
-// slot for complex64); stage op ranges relative to the pass.
+// of them packed into TK_RUN entry lists and tables (at most 255 op slots each, 5
+// entries per slot for complex64); stage op ranges relative to the pass.  tabs
+// receives the pass's run tables (offsets relative to its start).
 constexpr size_t kRunMin = 3;
 template <typename R>
-void build_pass_params(const Plan& pl, const TilePass& pass, TileParams<R>* tp) {
+void build_pass_params(const Plan& pl, const TilePass& pass, TileParams<R>* tp, std::vector<C2<R>>& tabs) {
   std::memset(tp, 0, sizeof(TileParams<R>));
   tp->pass = pass;
   tp->pass.stage_begin = 0;
+  tabs.clear();
+  std::vector<RunJob> jobs;
   int w = 0;
   std::vector<TileOp<R>> conv;
   const size_t per = sizeof(TileOp<R>) / sizeof(RunEntry<R>);
@@ -277,7 +348,7 @@ void build_pass_params(const Plan& pl, const TilePass& pass, TileParams<R>* tp) 
         size_t j = i;
         while (j < conv.size() && conv[j].kind == TK_CP && j - i < 255 * per) ++j;
         if (j - i >= kRunMin) {
-          w = pack_run(conv, i, j, tp->ops, w);
+          w = pack_run(conv, i, j, tp->ops, w, tabs, jobs);
           i = j;
           continue;
         }
@@ -287,6 +358,9 @@ void build_pass_params(const Plan& pl, const TilePass& pass, TileParams<R>* tp) 
     ts.op_end = w;
     tp->stages[s2] = ts;
   }
+  tp->n_jobs = (int32_t)jobs.size();
+  static_assert(sizeof(tp->jobs) >= sizeof(RunJob) * kMaxRunJobs, "job table fits");
+  if (!jobs.empty()) std::memcpy(tp->jobs, jobs.data(), sizeof(RunJob) * jobs.size());
 }
 
 template <typename T>
@@ -432,6 +506,21 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
   plan_circuit(fops, st->n, vmap, pl, TileLimits<R>::kMaxOps, kMaxTileStages);
   std::vector<unsigned char> blob;
   const size_t off_remap = put(blob, pl.remaps.data(), pl.remaps.size());
+  // every pass's kernel-parameter image first, its run tables into the upload
+  std::vector<TileParams<R>> tps;
+  std::vector<size_t> tab_off;
+  {
+    size_t ntile = 0;
+    for (const PlanStep& step : pl.steps) ntile += step.kind == PlanStep::TILE;
+    tps.resize(ntile);
+    std::vector<C2<R>> tabs;
+    size_t ti = 0;
+    for (const PlanStep& step : pl.steps) {
+      if (step.kind != PlanStep::TILE) continue;
+      build_pass_params<R>(pl, pl.passes[step.index], &tps[ti++], tabs);
+      tab_off.push_back(tabs.empty() ? SIZE_MAX : put(blob, tabs.data(), tabs.size()));
+    }
+  }
   qs_status s = upload(st, blob);
   if (s != QS_OK) return s;
   unsigned char* dev = (unsigned char*)st->opbuf;
@@ -440,14 +529,15 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
   double tile_flops = 0.0, plain_flops = 0.0;
   for (size_t i = 0; i < pl.tile_fops.size(); ++i)   // a dense two-qubit op has two entries
     if (pl.tile_kind[i] != TK_G2C) tile_flops += op_flops_per_amp(pl.tile_fops[i]) * N;
-  // kernel-parameter image of one pass (stage op ranges relative to the pass)
-  std::unique_ptr<TileParams<R>> tp(new TileParams<R>());
+  size_t ti = 0;
   for (const PlanStep& step : pl.steps) {
     switch (step.kind) {
       case PlanStep::TILE: {
-        build_pass_params<R>(pl, pl.passes[step.index], tp.get());
+        TileParams<R>& tp = tps[ti];
+        tp.tabs = tab_off[ti] == SIZE_MAX ? nullptr : (const C2<R>*)(dev + tab_off[ti]);
+        ++ti;
         tm.before(0);
-        s = launch_tile_pass(st, tp.get());
+        s = launch_tile_pass(st, &tp);
         ++tile_launches;
         break;
       }

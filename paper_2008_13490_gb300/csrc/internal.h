@@ -160,6 +160,9 @@ struct TileParams {
   TilePass pass;
   TileStage stages[kMaxTileStages];
   TileOp<R> ops[TileLimits<R>::kMaxOps];
+  const C2<R>* tabs;            // the pass's run tables (device; forward passes with TK_RUN)
+  int32_t n_jobs;               // run prologue jobs (RunJob, tile_cp.h)
+  uint8_t jobs[64 * 8];
 };
 
 // Device-side plain op (one launch per op; also the small-state kernel's op).

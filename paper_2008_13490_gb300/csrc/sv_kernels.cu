@@ -360,36 +360,70 @@ struct DiagRun {
       s = cmul(s, e);
     }
   }
-  // TK_RUN: the packed entry lists of a run of controlled phases (tile_cp.h)
-  __device__ __forceinline__ void add_run(C2<R>* v, const TileOp<R>* __restrict__ opp, uint64_t ctx) {
-    const uint16_t* cnt = reinterpret_cast<const uint16_t*>(&opp->m0[0]);
+  // TK_RUN (tile_cp.h): the residual entries, the CTA's prologue factors U of the
+  // run's jobs, and the (lane, warp) / register tables of the pass (lw = warp * 32 +
+  // lane)
+  __device__ __forceinline__ void add_run(C2<R>* v, const TileOp<R>* __restrict__ opp, uint64_t ctx, int lw,
+                                          const C2<R>* U, const C2<R>* __restrict__ tabs) {
+    RunHeader h;
+    memcpy(&h, &opp->m0[0], sizeof(h));
     const RunEntry<R>* __restrict__ e = reinterpret_cast<const RunEntry<R>*>(opp + 1);
     const C2<R> one{R(1), R(0)};
     int i = 0;
-    for (const int n = cnt[0]; i < n; ++i) {
+    for (const int n = h.n_s; i < n; ++i) {
       const RunEntry<R> x = e[i];
       s = cmul(s, csel(((ctx >> x.pa) & (ctx >> x.pb) & 1ull) != 0, x.p, one));
     }
-    for (const int n = i + cnt[1]; i < n; ++i) {
+    for (const int n = i + h.n_f[0]; i < n; ++i) {
       const RunEntry<R> x = e[i];
       f0[1] = cmul(f0[1], csel(((ctx >> x.pa) & 1ull) != 0, x.p, one));
     }
-    for (const int n = i + cnt[2]; i < n; ++i) {
+    for (const int n = i + h.n_f[1]; i < n; ++i) {
       const RunEntry<R> x = e[i];
       f1[1] = cmul(f1[1], csel(((ctx >> x.pa) & 1ull) != 0, x.p, one));
     }
-    for (const int n = i + cnt[3]; i < n; ++i) {
+    for (const int n = i + h.n_f[2]; i < n; ++i) {
       const RunEntry<R> x = e[i];
       f2[1] = cmul(f2[1], csel(((ctx >> x.pa) & 1ull) != 0, x.p, one));
     }
-    for (const int n = i + cnt[4]; i < n; ++i) {
+    for (const int n = i + h.n_f[3]; i < n; ++i) {
       const RunEntry<R> x = e[i];
       f3[1] = cmul(f3[1], csel(((ctx >> x.pa) & 1ull) != 0, x.p, one));
     }
-    for (const int n = i + cnt[5]; i < n; ++i) {
-      const RunEntry<R> x = e[i];
+    if (h.umask) {
+      int u = h.ubase;
+      if (h.umask & 1) s = cmul(s, U[u++]);
+      if (h.umask & 2) f0[1] = cmul(f0[1], U[u++]);
+      if (h.umask & 4) f1[1] = cmul(f1[1], U[u++]);
+      if (h.umask & 8) f2[1] = cmul(f2[1], U[u++]);
+      if (h.umask & 16) f3[1] = cmul(f3[1], U[u++]);
+    }
+    if (h.tmask) {
+      const C2<R>* __restrict__ T = tabs + h.toff;
+      if (h.tmask & 1) {
+        s = cmul(s, T[lw]);
+        T += kRunTable;
+      }
+      if (h.tmask & 2) {
+        f0[1] = cmul(f0[1], T[lw]);
+        T += kRunTable;
+      }
+      if (h.tmask & 4) {
+        f1[1] = cmul(f1[1], T[lw]);
+        T += kRunTable;
+      }
+      if (h.tmask & 8) {
+        f2[1] = cmul(f2[1], T[lw]);
+        T += kRunTable;
+      }
+      if (h.tmask & 16) {
+        f3[1] = cmul(f3[1], T[lw]);
+        T += kRunTable;
+      }
+      if (h.tmask & 32) {
 #pragma unroll
-      for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], csel(((r >> x.k) & (r >> x.l) & 1) != 0, x.p, one));
+        for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], T[r]);
+      }
     }
   }
   template <bool TWO = false>
@@ -422,6 +456,7 @@ __global__ void __launch_bounds__(kTileThreads)
 
   __shared__ uint8_t s_pos[kTileBits];
   __shared__ uint64_t s_base;
+  __shared__ C2<R> s_U[RUNS ? kMaxRunJobs : 1];   // the CTA's run-job factors
   if (tid == 0) {
     const int n_nt = P.pass.n_nt;
     uint64_t base = 0;
@@ -429,6 +464,24 @@ __global__ void __launch_bounds__(kTileThreads)
     s_base = base;
   }
   if (tid < kTileBits) s_pos[tid] = P.pass.pos[tid];
+  if constexpr (RUNS) {
+    // one job per thread: the product of its entries' phases at this tile (bits
+    // below kCtxOne are tile bits, kCtxOne the constant 1)
+    if (tid < P.n_jobs) {
+      RunJob jb;
+      memcpy(&jb, P.jobs + sizeof(RunJob) * tid, sizeof(jb));
+      const uint64_t tctx = tile | (1ull << kCtxOne);
+      const RunEntry<R>* __restrict__ e = reinterpret_cast<const RunEntry<R>*>(P.ops + jb.op + 1) + jb.first;
+      const C2<R> one{R(1), R(0)};
+      C2<R> u = one;
+      for (int i = 0; i < jb.count; ++i) {
+        const RunEntry<R> x = e[i];
+        const uint64_t b = jb.scalar ? ((tctx >> x.pa) & (tctx >> x.pb)) : (tctx >> x.pa);
+        u = cmul(u, csel((b & 1ull) != 0, x.p, one));
+      }
+      s_U[tid] = u;
+    }
+  }
   __syncthreads();
   const uint64_t base = s_base;
   uint64_t loff = 0;
@@ -510,7 +563,7 @@ __global__ void __launch_bounds__(kTileThreads)
       do {
         const uint32_t kind = hdr.x & 0xffu;
         if (RUNS && kind == TK_RUN) {
-          dr.add_run(v, ops + o, ctx);
+          dr.add_run(v, ops + o, ctx, tid, s_U, P.tabs);
           o += 1 + (int)((hdr.x >> 8) & 0xffu);   // the header and its entry slots
         } else {
           if (kind == TK_CP) dr.add_cp(v, ops + o, hdr, ctx);

@@ -15,21 +15,46 @@ namespace qs {
 constexpr uint8_t TK_CP = 5;
 constexpr int kCtxOne = 47, kCtxLane = 48, kCtxWarp = 56;
 
-// TK_RUN: a run of TK_CP ops of one stage packed by the host into entry lists
-// (forward passes only).  Diagonal ops commute, so the run's ops are regrouped by
-// where their factor goes: n_s entries whose two bits are both context bits
-// (factor into the thread's scalar), then, for register slot k = 0..3, n_f[k]
-// entries with one bit in slot k and the other a context bit (factor into the
-// slot's factor for bit value 1), then n_rr entries with both bits in register
-// slots k and l.  The header op's m0 bytes hold the counts (uint16 n_s, n_f[4],
-// n_rr); slot = the number of op slots the entries fill after the header.
+// TK_RUN: a run of TK_CP ops of one stage packed by the host (forward passes
+// only).  Diagonal ops commute, so the run's ops are regrouped by what their
+// factor depends on; with positions in the context word, a bit is a tile bit
+// (< kCtxOne: the same for the whole CTA) or a thread bit (the constant 1, lane or
+// warp bits):
+//   thread x thread          -> table S over (lane, warp): a factor of the scalar
+//   register slot k x thread -> table N_k over (lane, warp): a factor of f_k[1]
+//   register x register      -> table RR over the 16 register indices: into v
+//   tile x tile              -> one factor of the scalar per CTA (a job)
+//   register slot k x tile   -> one factor of f_k[1] per CTA (a job)
+//   tile x thread            -> entries each thread applies (n_s, the residual)
+// The tables do not depend on the tile: the host builds them (FP64 products,
+// rounded once) into the pass's table buffer.  A job's product is formed once per
+// CTA in the kernel's prologue from its entries.  Entries follow the header in
+// the run's op slots: the residual ones, then the jobs' (slot = the number of op
+// slots they fill).  Header fields (in m0):
+struct RunHeader {
+  uint16_t n_s;        // residual entries (per thread)
+  uint16_t n_f[4];     // residual register-slot entries (per thread; jobs that did not fit)
+  uint16_t ubase;      // first prologue factor of the run's jobs
+  uint8_t umask;       // jobs present: bit 0 scalar, bit 1 + k slot k
+  uint8_t tmask;       // tables present: bit 0 S, bit 1 + k N_k, bit 5 RR
+  uint32_t toff;       // first table entry (complex index into the pass's table buffer)
+};
 constexpr uint8_t TK_RUN = 6;
 template <typename R>
 struct alignas(8) RunEntry {
   C2<R> p;          // the phase of the ops' all-ones entry
   uint8_t pa, pb;   // context-word positions of the op's bits (pb = kCtxOne for a one-bit op)
-  uint8_t k, l;     // register slots (n_rr entries)
+  uint8_t k, l;     // register slots
   uint8_t pad[4];
 };
+// A prologue job: the product over count entries of the run whose header is op
+// `op`, starting at entry `first`: scalar (both bits tile bits) or slot (pa the
+// tile bit); the CTA's factor goes to U[index of the job in the pass].
+struct RunJob {
+  uint16_t op, first, count;
+  uint8_t scalar, pad;
+};
+constexpr int kMaxRunJobs = 64;
+constexpr int kRunTable = 1 << (kLaneBits + kWarpBits);   // (lane, warp) entries of S and N_k
 
 }  // namespace qs
