@@ -505,8 +505,8 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
   Plan pl;
   plan_circuit(fops, st->n, vmap, pl, TileLimits<R>::kMaxOps, kMaxTileStages);
   std::vector<unsigned char> blob;
-  const size_t off_remap = put(blob, pl.remaps.data(), pl.remaps.size());
   // every pass's kernel-parameter image first, its run tables into the upload
+  // (remap descriptors go by value as kernel parameters)
   std::vector<TileParams<R>> tps;
   std::vector<size_t> tab_off;
   {
@@ -550,7 +550,7 @@ qs_status run_tiled(State* st, const std::vector<FOp>& fops, const std::vector<i
       }
       case PlanStep::REMAP:
         tm.before(2);
-        s = launch_remap(st, dev + off_remap + sizeof(RemapDesc) * step.index, nullptr);
+        s = launch_remap(st, pl.remaps[step.index]);
         break;
       default:
         break;

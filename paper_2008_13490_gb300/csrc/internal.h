@@ -294,7 +294,7 @@ qs_status launch_adjoint_pass(State* st, void* lam, const void* params, void* pa
 qs_status launch_term_reduce(State* st, const void* partial, int nterm, const int* slots, double* dth);
 qs_status launch_plain_op(State* st, const void* op_dev, int type);
 qs_status launch_small(State* st, const void* ops_dev, int nops);
-qs_status launch_remap(State* st, const void* desc_dev, void* tmp);
+qs_status launch_remap(State* st, const RemapDesc& desc);
 qs_status launch_probs(State* st, void* out, int out_fp64, uint64_t mask, double* partials,
                        uint8_t* bits_dev, double* marg_acc);
 // probabilities of amplitudes [off, off + count) of the state into out (device;

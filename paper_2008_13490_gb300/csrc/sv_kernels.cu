@@ -897,9 +897,12 @@ __global__ void __launch_bounds__(256)
 
 // ------------------------------------------------------------------ remap
 
+__device__ __forceinline__ uint64_t tiles_of(const RemapDesc& d) { return 1ull << d.n_nt; }
+
 template <typename R>
-__global__ void __launch_bounds__(kTileThreads)
-    remap_kernel(C2<R>* __restrict__ psi, const RemapDesc* __restrict__ d) {
+__global__ void __launch_bounds__(kTileThreads, sizeof(R) == 4 ? 3 : 2)
+    remap_kernel(C2<R>* __restrict__ psi, const __grid_constant__ RemapDesc D) {
+  const RemapDesc* d = &D;   // kernel parameter (constant bank)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<R>* sm = reinterpret_cast<C2<R>*>(smem_raw);
   // Every map below is linear over GF(2) in the bits of a 12-bit local index, so
@@ -920,13 +923,14 @@ __global__ void __launch_bounds__(kTileThreads)
   __shared__ uint64_t s_alo[64], s_ahi[64];
   __shared__ uint16_t s_slo[64], s_shi[64], s_glo[64], s_ghi[64];
   __shared__ uint16_t s_m[kTileBits];
-  __shared__ uint64_t s_base;
   const int tid = threadIdx.x;
-  const uint64_t tile = blockIdx.x;
-  if (tid == 0) {
+  // the tile's bits outside the tile positions, deposited at nt_pos
+  auto base_of = [&](uint64_t tile) {
     uint64_t base = 0;
     for (int j = 0; j < d->n_nt; ++j) base |= ((tile >> j) & 1ull) << d->nt_pos[j];
-    s_base = base;
+    return base;
+  };
+  if (tid == 0) {
     int used = 0;
     for (int k = kK0; k < kK0 + kB; ++k)
       if (d->src[k] < kB) used |= 1 << d->src[k];
@@ -956,41 +960,90 @@ __global__ void __launch_bounds__(kTileThreads)
     (h ? s_ghi : s_glo)[v] = (uint16_t)gather;
   }
   __syncthreads();
-  const uint64_t base = s_base;
+  // Persistent over tiles (grid = a few CTAs per SM): the next tile's loads are
+  // issued into registers before the current tile is gathered and stored, so a
+  // CTA keeps reads in flight through its exchange and store phases.
+  const uint64_t tiles = tiles_of(D);
+  uint64_t tile = blockIdx.x;
+  if (tile >= tiles) return;
   if (kPairs && d->pos[0] == 0) {
     // slot(L ^ 1) = slot(L) ^ 1: a pair fills one aligned 16-byte slot pair
+    constexpr int kPer = (1 << kTileBits) / (2 * kTileThreads);
     float4* sm4 = reinterpret_cast<float4*>(smem_raw);
     const float* smf = reinterpret_cast<const float*>(smem_raw);
     float4* psi4 = reinterpret_cast<float4*>(psi);
     const int g1 = s_glo[1];   // gather(L ^ 1) = gather(L) ^ g1
+    uint64_t base = base_of(tile);
+    float4 q[kPer];
 #pragma unroll
-    for (int r = 0; r < (1 << kTileBits) / (2 * kTileThreads); ++r) {
+    for (int r = 0; r < kPer; ++r) {
       const int L = 2 * (tid + r * kTileThreads);
-      const float4 q = __ldcs(psi4 + ((base | s_alo[L & 63] | s_ahi[L >> 6]) >> 1));
-      const int sl = s_slo[L & 63] ^ s_shi[L >> 6];
-      sm4[sl >> 1] = (sl & 1) ? make_float4(q.z, q.w, q.x, q.y) : q;
+      q[r] = __ldcs(psi4 + ((base | s_alo[L & 63] | s_ahi[L >> 6]) >> 1));
+    }
+    for (;;) {
+#pragma unroll
+      for (int r = 0; r < kPer; ++r) {
+        const int L = 2 * (tid + r * kTileThreads);
+        const int sl = s_slo[L & 63] ^ s_shi[L >> 6];
+        sm4[sl >> 1] = (sl & 1) ? make_float4(q[r].z, q[r].w, q[r].x, q[r].y) : q[r];
+      }
+      __syncthreads();
+      const uint64_t next = tile + gridDim.x;
+      const uint64_t nbase = next < tiles ? base_of(next) : 0;
+      if (next < tiles) {
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+          const int L = 2 * (tid + r * kTileThreads);
+          q[r] = __ldcs(psi4 + ((nbase | s_alo[L & 63] | s_ahi[L >> 6]) >> 1));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kPer; ++r) {
+        const int L = 2 * (tid + r * kTileThreads);
+        const int g = s_glo[L & 63] ^ s_ghi[L >> 6];
+        const float2 a0 = *reinterpret_cast<const float2*>(smf + 2 * g);
+        const float2 a1 = *reinterpret_cast<const float2*>(smf + 2 * (g ^ g1));
+        __stcs(psi4 + ((base | s_alo[L & 63] | s_ahi[L >> 6]) >> 1), make_float4(a0.x, a0.y, a1.x, a1.y));
+      }
+      if (next >= tiles) return;
+      __syncthreads();   // the tile is gathered before the next one is written to shared memory
+      tile = next;
+      base = nbase;
+    }
+  }
+  constexpr int kPer = (1 << kTileBits) / kTileThreads;
+  uint64_t base = base_of(tile);
+  C2<R> q[kPer];
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int L = tid + r * kTileThreads;
+    q[r] = psi[base | s_alo[L & 63] | s_ahi[L >> 6]];
+  }
+  for (;;) {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int L = tid + r * kTileThreads;
+      sm[s_slo[L & 63] ^ s_shi[L >> 6]] = q[r];
     }
     __syncthreads();
+    const uint64_t next = tile + gridDim.x;
+    const uint64_t nbase = next < tiles ? base_of(next) : 0;
+    if (next < tiles) {
 #pragma unroll
-    for (int r = 0; r < (1 << kTileBits) / (2 * kTileThreads); ++r) {
-      const int L = 2 * (tid + r * kTileThreads);
-      const int g = s_glo[L & 63] ^ s_ghi[L >> 6];
-      const float2 a0 = *reinterpret_cast<const float2*>(smf + 2 * g);
-      const float2 a1 = *reinterpret_cast<const float2*>(smf + 2 * (g ^ g1));
-      __stcs(psi4 + ((base | s_alo[L & 63] | s_ahi[L >> 6]) >> 1), make_float4(a0.x, a0.y, a1.x, a1.y));
+      for (int r = 0; r < kPer; ++r) {
+        const int L = tid + r * kTileThreads;
+        q[r] = psi[nbase | s_alo[L & 63] | s_ahi[L >> 6]];
+      }
     }
-    return;
-  }
-#pragma unroll 4
-  for (int r = 0; r < (1 << kTileBits) / kTileThreads; ++r) {
-    const int L = tid + r * kTileThreads;
-    sm[s_slo[L & 63] ^ s_shi[L >> 6]] = psi[base | s_alo[L & 63] | s_ahi[L >> 6]];
-  }
-  __syncthreads();
-#pragma unroll 4
-  for (int r = 0; r < (1 << kTileBits) / kTileThreads; ++r) {
-    const int L = tid + r * kTileThreads;
-    psi[base | s_alo[L & 63] | s_ahi[L >> 6]] = sm[s_glo[L & 63] ^ s_ghi[L >> 6]];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int L = tid + r * kTileThreads;
+      psi[base | s_alo[L & 63] | s_ahi[L >> 6]] = sm[s_glo[L & 63] ^ s_ghi[L >> 6]];
+    }
+    if (next >= tiles) return;
+    __syncthreads();
+    tile = next;
+    base = nbase;
   }
 }
 
@@ -1313,17 +1366,27 @@ qs_status launch_small(State* st, const void* ops_dev, int nops) {
   return QS_OK;
 }
 
-qs_status launch_remap(State* st, const void* desc_dev, void* /*tmp*/) {
+qs_status launch_remap(State* st, const RemapDesc& d) {
   const uint64_t tiles = 1ull << (st->n - kTileBits);
+  // persistent: as many CTAs as fit on the SMs (shared memory: one tile each)
+  auto grid_for = [&](const void* kern, size_t smem) {
+    int dev = 0, sms = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTileThreads, smem);
+    const uint64_t g = (uint64_t)sms * (uint64_t)(per < 1 ? 1 : per);
+    return (unsigned)(g < tiles ? g : tiles);
+  };
   if (st->prec == QS_C64) {
-    remap_kernel<float><<<(unsigned)tiles, kTileThreads, sizeof(C2<float>) << kTileBits, st->stream>>>(
-        (C2<float>*)st->data, (const RemapDesc*)desc_dev);
+    const size_t smem = sizeof(C2<float>) << kTileBits;
+    remap_kernel<float><<<grid_for((const void*)remap_kernel<float>, smem), kTileThreads, smem, st->stream>>>(
+        (C2<float>*)st->data, d);
   } else {
     const size_t smem = sizeof(C2<double>) << kTileBits;
     qs_status s = set_smem(remap_kernel<double>, smem);
     if (s != QS_OK) return s;
-    remap_kernel<double><<<(unsigned)tiles, kTileThreads, smem, st->stream>>>(
-        (C2<double>*)st->data, (const RemapDesc*)desc_dev);
+    remap_kernel<double><<<grid_for((const void*)remap_kernel<double>, smem), kTileThreads, smem, st->stream>>>(
+        (C2<double>*)st->data, d);
   }
   QS_CUDA(cudaGetLastError());
   return QS_OK;
