@@ -967,43 +967,43 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(R) == 4 ? 3 : 2)
   uint64_t tile = blockIdx.x;
   if (tile >= tiles) return;
   if (kPairs && d->pos[0] == 0) {
-    // slot(L ^ 1) = slot(L) ^ 1: a pair fills one aligned 16-byte slot pair
+    // slot(L ^ 1) = slot(L) ^ 1: a pair fills one aligned 16-byte slot pair.  A
+    // thread's offsets, slots and gathers are the same for every tile: read from
+    // the tables once, kept in registers.
     constexpr int kPer = (1 << kTileBits) / (2 * kTileThreads);
     float4* sm4 = reinterpret_cast<float4*>(smem_raw);
     const float* smf = reinterpret_cast<const float*>(smem_raw);
     float4* psi4 = reinterpret_cast<float4*>(psi);
     const int g1 = s_glo[1];   // gather(L ^ 1) = gather(L) ^ g1
-    uint64_t base = base_of(tile);
-    float4 q[kPer];
+    uint64_t ad[kPer];
+    int sl[kPer], ga[kPer];
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
       const int L = 2 * (tid + r * kTileThreads);
-      q[r] = __ldcs(psi4 + ((base | s_alo[L & 63] | s_ahi[L >> 6]) >> 1));
+      ad[r] = (s_alo[L & 63] | s_ahi[L >> 6]) >> 1;
+      sl[r] = s_slo[L & 63] ^ s_shi[L >> 6];
+      ga[r] = s_glo[L & 63] ^ s_ghi[L >> 6];
     }
+    uint64_t base = base_of(tile) >> 1;
+    float4 q[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) q[r] = __ldcs(psi4 + (base | ad[r]));
     for (;;) {
 #pragma unroll
-      for (int r = 0; r < kPer; ++r) {
-        const int L = 2 * (tid + r * kTileThreads);
-        const int sl = s_slo[L & 63] ^ s_shi[L >> 6];
-        sm4[sl >> 1] = (sl & 1) ? make_float4(q[r].z, q[r].w, q[r].x, q[r].y) : q[r];
-      }
+      for (int r = 0; r < kPer; ++r)
+        sm4[sl[r] >> 1] = (sl[r] & 1) ? make_float4(q[r].z, q[r].w, q[r].x, q[r].y) : q[r];
       __syncthreads();
       const uint64_t next = tile + gridDim.x;
-      const uint64_t nbase = next < tiles ? base_of(next) : 0;
+      const uint64_t nbase = next < tiles ? base_of(next) >> 1 : 0;
       if (next < tiles) {
 #pragma unroll
-        for (int r = 0; r < kPer; ++r) {
-          const int L = 2 * (tid + r * kTileThreads);
-          q[r] = __ldcs(psi4 + ((nbase | s_alo[L & 63] | s_ahi[L >> 6]) >> 1));
-        }
+        for (int r = 0; r < kPer; ++r) q[r] = __ldcs(psi4 + (nbase | ad[r]));
       }
 #pragma unroll
       for (int r = 0; r < kPer; ++r) {
-        const int L = 2 * (tid + r * kTileThreads);
-        const int g = s_glo[L & 63] ^ s_ghi[L >> 6];
-        const float2 a0 = *reinterpret_cast<const float2*>(smf + 2 * g);
-        const float2 a1 = *reinterpret_cast<const float2*>(smf + 2 * (g ^ g1));
-        __stcs(psi4 + ((base | s_alo[L & 63] | s_ahi[L >> 6]) >> 1), make_float4(a0.x, a0.y, a1.x, a1.y));
+        const float2 a0 = *reinterpret_cast<const float2*>(smf + 2 * ga[r]);
+        const float2 a1 = *reinterpret_cast<const float2*>(smf + 2 * (ga[r] ^ g1));
+        __stcs(psi4 + (base | ad[r]), make_float4(a0.x, a0.y, a1.x, a1.y));
       }
       if (next >= tiles) return;
       __syncthreads();   // the tile is gathered before the next one is written to shared memory
