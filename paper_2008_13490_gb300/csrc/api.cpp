@@ -1133,10 +1133,24 @@ qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t ma
       for (size_t i = 0; i < h.size(); ++i) ((float*)host_out)[i] = (float)h[i];
     return QS_OK;
   }
-  // the whole distribution: formed chunk by chunk in a device staging buffer (kept
-  // by the state) and copied to the host buffer after each chunk
   const size_t es = out_fp64 ? sizeof(double) : sizeof(float);
   const uint64_t N = 1ull << st->n;
+  {
+    // a page-locked host buffer the device can address: the kernel writes the
+    // probabilities into it directly (one launch, no staging copies; 4 GiB in 22.2 ms
+    // against 24.9 ms through the copy engine on GB300)
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, host_out) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+      s = launch_probs_range(st, 0, N, pa.devicePointer, out_fp64, partials);
+      if (s == QS_OK && norm_out) s = sv_probs(st, nullptr, out_fp64, 0, norm_out);
+      const cudaError_t e = cudaStreamSynchronize(st->stream);
+      if (s == QS_OK && e != cudaSuccess) s = cuda_status(e, "sv_probs_host");
+      return s;
+    }
+    cudaGetLastError();   // a plain host pointer: not an error
+  }
+  // otherwise formed chunk by chunk in a device staging buffer (kept by the state)
+  // and copied to the host buffer after each chunk
   const uint64_t chunk = std::min<uint64_t>(N, (uint64_t)(kStageBytes / es));
   if (!st->stage) {
     st->stage = dev_alloc(st, kStageBytes);
