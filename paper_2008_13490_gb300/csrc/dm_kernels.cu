@@ -499,15 +499,15 @@ __device__ __forceinline__ void stage_b(const float* G, const float (&in)[16], f
 }
 
 // Forward passes over two digits a != b at once (16-element groups, local index
-// 4 d_a + d_b), in this order: an optional table H on digit a (PRE, pattern kTP),
-// an optional signed permutation applied through the load addresses (CZ), Ga on
-// digit a, Gb on digit b, and optionally the table P on digit a and then on digit b
-// (POST, pattern kChan) -- the operations of the separate one-digit passes, in the
-// same order, with one shared-memory sweep and one barrier instead of several.
-template <class T, bool CZ, int FA, int FB, bool PRE = false, bool POST = false>
-__device__ void pass2(const T& t, float* r, int n, int a, const float* Ga, int b, const float* Gb,
-                      const float* H = nullptr, const float* P = nullptr) {
-  static_assert(!(CZ && PRE), "the permutation is applied at the loads");
+// 4 d_a + d_b): an optional signed permutation applied through the load addresses
+// (CZ), then Ga on digit a, then Gb on digit b -- the operations of the separate
+// one-digit passes, in the same order, with one shared-memory sweep and one
+// barrier instead of two or three.  (Folding a following idle op's channels into
+// the same pass saved a sweep on 5- and 6-qubit circuits but made the mixed
+// 4096-circuit batch slower, 0.49-0.51 against 0.53 ms: three more pass variants
+// in the instruction stream of every SM.)
+template <class T, bool CZ, int FA, int FB>
+__device__ void pass2(const T& t, float* r, int n, int a, const float* Ga, int b, const float* Gb) {
   const int groups = 1 << (2 * (n - 2));
   const int lo = a < b ? a : b, hi = a < b ? b : a;
   const Off4 oa(1 << (2 * a)), ob(1 << (2 * b));
@@ -520,40 +520,10 @@ __device__ void pass2(const T& t, float* r, int n, int a, const float* Ga, int b
       const float v = r[base ^ oa[src >> 2] ^ ob[src & 3]];
       x[l] = (CZ && cz_ineg(l)) ? -v : v;
     }
-    if constexpr (PRE) {
-      stage_a<kTP>(H, x, y);
-#pragma unroll
-      for (int l = 0; l < 16; ++l) x[l] = y[l];
-    }
     stage_a<FA>(Ga, x, y);
     stage_b<FB>(Gb, y, x);
-    if constexpr (POST) {
-      stage_a<kChan>(P, x, y);
-      stage_b<kChan>(P, y, x);
-    }
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[base ^ oa[l >> 2] ^ ob[l & 3]] = x[l];
-  }
-}
-
-// The idle op's channel C on every qubit but u and v, pairs of digits per sweep, a
-// single last digit alone; each sweep followed by a team sync.
-template <class T>
-__device__ void idle_rest(const T& t, float* r, int n, int u, int v, const float* C) {
-  int pend = -1;
-  for (int q = 0; q < n; ++q) {
-    if (q == u || q == v) continue;
-    if (pend < 0) {
-      pend = q;
-      continue;
-    }
-    pass2<T, false, kChan, kChan>(t, r, n, pend, C, q, C);
-    t.sync();
-    pend = -1;
-  }
-  if (pend >= 0) {
-    apply4<T, kChan>(t, r, n, pend, C, false);
-    t.sync();
   }
 }
 
@@ -1046,39 +1016,13 @@ __device__ __forceinline__ void dm_circuit(const T& t, const DmArgs& A, int c, i
       }
       const int32_t* op = reinterpret_cast<const int32_t*>(&s_ops[k % kC]);
       const int code = op[0], a = op[1];
-      // look-ahead within the staged chunk
-      const bool has1 = k + 1 < L && (k + 1) % kC != 0, has2 = has1 && k + 2 < L && (k + 2) % kC != 0;
       const int32_t* nx = reinterpret_cast<const int32_t*>(&s_ops[(k + 1) % kC]);
-      const bool xy = code == QS_DM_X90 || code == QS_DM_Y90;
-      const float* C = tabs + 16 * TB_C;
-      if (xy && has1 && (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) && nx[1] != a) {
-        // this op and the next act on different qubits: one two-digit pass, which
-        // also takes the idle op's channels on both digits when one follows
-        const float* Ga = tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY);
-        const float* Gb = tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY);
-        const bool idle = has2 && s_ops[(k + 2) % kC].x == QS_DM_IDLE;
-        if (idle)
-          pass2<T, false, kTP, kTP, false, true>(t, r, n, a, Ga, nx[1], Gb, nullptr, C);
-        else
-          pass2<T, false, kTP, kTP>(t, r, n, a, Ga, nx[1], Gb);
+      if ((code == QS_DM_X90 || code == QS_DM_Y90) && k + 1 < L && (k + 1) % kC != 0 &&
+          (nx[0] == QS_DM_X90 || nx[0] == QS_DM_Y90) && nx[1] != a) {
+        // this op and the next act on different qubits: one two-digit pass
+        pass2<T, false, kTP, kTP>(t, r, n, a, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY), nx[1],
+                                  tabs + 16 * (nx[0] == QS_DM_X90 ? TB_GX : TB_GY));
         t.sync();
-        if (idle) idle_rest(t, r, n, a, nx[1], C);
-        k += idle ? 3 : 2;
-        continue;
-      }
-      if ((xy || code == QS_DM_CZ) && n >= 2 && has1 && nx[0] == QS_DM_IDLE) {
-        // a gate, then the idle op: the idle op's channels on the gate's digits
-        // (a and a partner for a one-qubit gate) go into the gate's pass
-        if (xy) {
-          const int pb = a == 0 ? 1 : 0;
-          pass2<T, false, kChan, kChan, true>(t, r, n, a, C, pb, C, tabs + 16 * (code == QS_DM_X90 ? TB_GX : TB_GY));
-          t.sync();
-          idle_rest(t, r, n, a, pb, C);
-        } else {
-          pass2<T, true, kChan, kChan, false, true>(t, r, n, a, C, op[2], C, nullptr, C);
-          t.sync();
-          idle_rest(t, r, n, a, op[2], C);
-        }
         k += 2;
         continue;
       }
