@@ -1,7 +1,8 @@
 // Batched density matrices in the Pauli basis (Pauli transfer matrices).
 //
 // A circuit's state is its Pauli vector r_i = Tr(P^_i rho), P^_i = P_i/sqrt(N)
-// (Eq. (GSTVectorizedRho)), 4^n reals kept in one CTA's shared memory.  An op
+// (Eq. (GSTVectorizedRho)), 4^n reals kept in shared memory (one CTA or one warp per
+// circuit) or, for 1 and 2 qubits in the forward pass, in registers.  An op
 // is a PTM acting on the base-4 digit(s) of its qubit(s); composition of maps
 // is the product of their PTMs (section "Quantum operations").  Outcome
 // probabilities p_J = <<E_J| r>> (Eq. (GSTBornRuleVectorized)): for
@@ -257,9 +258,9 @@ __device__ __forceinline__ int cz_inv(int l) { return (int)((kCzInv >> (4 * l)) 
 __device__ __forceinline__ bool cz_neg(int j) { return (kCzSgn >> j) & 1; }
 __device__ __forceinline__ bool cz_ineg(int l) { return (kCzISgn >> l) & 1; }
 
-// The threads that share one circuit's Pauli vector: a whole CTA (registers of 5
-// and 6 qubits) or one warp (up to kWarpMaxQ qubits, four circuits per CTA, no
-// block barriers).  rank / kSize stride the sweeps, sync() orders the
+// The threads that share one circuit's Pauli vector: a whole CTA (3 to 6 qubits in
+// the forward pass, 5 and 6 with the gradient) or one warp (the gradient pass, up
+// to kWarpMaxQ qubits, four circuits per CTA, no block barriers).  rank / kSize stride the sweeps, sync() orders the
 // shared-memory updates between sweeps, kChunk ops are staged at a time.
 constexpr int kWarpMaxQ = 4;
 constexpr int kWarpD = 1 << (2 * kWarpMaxQ);   // 256 floats per Pauli vector
