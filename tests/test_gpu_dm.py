@@ -217,6 +217,29 @@ def test_gradient_is_reproducible(qs):
         assert np.array_equal(g, runs[0][2])
 
 
+def test_batch_beyond_the_sort_limit(qs):
+    # more circuits than the one-CTA sort takes (16384): the gradient pass hands
+    # them out through the stable partition too (small registers one per warp); a
+    # sample of circuits against the oracle, the gradients against the oracle's
+    # adjoint within their derived FP32 bound
+    batch = W.noisy_batch(count=20000, seed=4501, n_range=(1, 4), len_range=(1, 24))
+    batch.counts = W.synthetic_counts(batch, 1000, seed=4502)
+    dev = qs.NoisyBatchDevice(batch)
+    p, ll, g = dev.run(grad=True)
+    p, ll, g = p.cpu().numpy(), ll.cpu().numpy(), g.cpu().numpy()
+    assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
+    p_fwd, ll_fwd, _ = dev.run()
+    np.testing.assert_allclose(p_fwd.cpu().numpy(), p, atol=1e-6)   # the forward pass agrees
+    for c in W.rng(4503).choice(batch.size, size=6, replace=False):
+        c = int(c)
+        n, ops, params = batch.circuit(c)
+        cnt = batch.counts[batch.cnt_off[c]:batch.cnt_off[c + 1]]
+        np.testing.assert_allclose(p[batch.cnt_off[c]:batch.cnt_off[c + 1]],
+                                   NZ.circuit_probabilities(n, ops, params), atol=2e-5)
+        _, _, ref = NZ.grad_adjoint(n, ops, params, cnt)
+        assert np.all(np.abs(g[c] - ref) <= _gradient_bound(n, ops, params, cnt)), (c, g[c], ref)
+
+
 def test_long_circuits_five_and_six_qubits_vs_oracle(qs):
     # the largest registers at full length (L = 200..256): every outcome against the
     # Kraus-map oracle, within the fp32 bound L * u ~ 1.5e-5 of the docstring
