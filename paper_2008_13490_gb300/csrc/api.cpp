@@ -826,6 +826,15 @@ qs_status check_state(qs_state_t st) {
 
 }  // namespace
 
+// The kernel-parameter image of a forward tile pass and its run tables (tile_cp.h).
+template <typename R>
+void tile_pass_image(const Plan& pl, const TilePass& pass, TileParams<R>* tp, std::vector<C2<R>>& tabs) {
+  build_pass_params<R>(pl, pass, tp, tabs);
+}
+template void tile_pass_image<float>(const Plan&, const TilePass&, TileParams<float>*, std::vector<C2<float>>&);
+template void tile_pass_image<double>(const Plan&, const TilePass&, TileParams<double>*, std::vector<C2<double>>&);
+
+
 qs_status adjoint_tiled(State* st, void* lam, const qs_gate* gates, size_t g0, size_t g1, double* dth) {
   return st->prec == QS_C64 ? adjoint_tiled_t<float>(st, lam, gates, g0, g1, dth)
                             : adjoint_tiled_t<double>(st, lam, gates, g0, g1, dth);

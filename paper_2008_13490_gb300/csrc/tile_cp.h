@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 #include "internal.h"
 
@@ -56,5 +57,11 @@ struct RunJob {
 };
 constexpr int kMaxRunJobs = 64;
 constexpr int kRunTable = 1 << (kLaneBits + kWarpBits);   // (lane, warp) entries of S and N_k
+
+// The kernel-parameter image of one forward tile pass (ops in their TK_CP / TK_RUN
+// forms, stage op ranges relative to the pass) and its run tables, as the library
+// launches it; offsets in the run headers are relative to the start of tabs.
+template <typename R>
+void tile_pass_image(const Plan& pl, const TilePass& pass, TileParams<R>* tp, std::vector<C2<R>>& tabs);
 
 }  // namespace qs

@@ -194,3 +194,220 @@ def test_tile_plan_reproduces_the_circuit(dump_exe, tmp_path, name):
     ref = SV.apply_circuit(psi0.copy(), n, ops)
     out = _execute(plan, n, psi0.copy())
     assert np.max(np.abs(out - ref)) < 1e-12
+
+
+# ---------------------------------------------------------------- kernel images
+# The forward tile pass as the library launches it: ops in their controlled-phase
+# forms (TK_CP: a phase on the amplitudes whose two bits are 1, bit positions in
+# the thread's context word) and runs of them packed (TK_RUN: per-thread entries,
+# per-CTA jobs over tile bits, and host-built tables over (lane, warp) and over the
+# 16 register indices).  Executing those images with numpy, in the meaning the
+# kernel gives each field, must reproduce the oracle: this pins the packing (which
+# factor goes to which table, job or entry list) on the CPU.
+TK_CP, TK_RUN = 5, 6
+CTX_ONE, CTX_LANE, CTX_WARP = 47, 48, 56
+
+
+@pytest.fixture(scope="module")
+def image_exe(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    from paper_2008_13490_gb300 import _build
+    lib = _build.build()
+    libdir = os.path.dirname(lib)
+    exe = tmp_path_factory.mktemp("timage") / "tile_image_dump"
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    subprocess.run(["g++", "-O1", "-std=c++17", os.path.join(ROOT, "tests", "tile_image_dump.cpp"),
+                    "-I", os.path.join(ROOT, "paper_2008_13490_gb300", "csrc"), "-I", os.path.join(ROOT, "include"),
+                    "-I", cuda_inc, "-o", str(exe), "-L", libdir, "-lqsim", f"-Wl,-rpath,{libdir}"],
+                   check=True, capture_output=True, text=True)
+    return exe
+
+
+def _images(exe, tmp_path, n, ops, fuse, relabel):
+    import paper_2008_13490_gb300 as qs
+    gin, out = tmp_path / "g.bin", tmp_path / "images.txt"
+    qs.gates_array(ops).tofile(gin)
+    subprocess.run([str(exe), str(gin), str(n), str(int(fuse)), str(int(relabel)), str(out)], check=True)
+    lines = [l.split() for l in open(out).read().split("\n") if l.strip()]
+    res = {"passes": [], "plainops": [], "remaps": []}
+    i = 0
+    assert lines[i][0] == "steps"
+    res["steps"] = [tuple(int(x) for x in r) for r in lines[i + 1:i + 1 + int(lines[i][1])]]
+    i += 1 + int(lines[i][1])
+    while lines[i][0] == "pass":
+        _, _, ns, nj, nt = lines[i]
+        geo = [int(x) for x in lines[i + 1]]
+        p = {"n_nt": geo[0], "pos": geo[1:13], "nt_pos": geo[13:13 + geo[0]], "stages": [], "jobs": [], "tabs": None}
+        i += 2
+        for _ in range(int(ns)):
+            st = [int(x) for x in lines[i][1:]]
+            stage = {"reg": st[0:4], "warp": st[4:7], "ops": []}
+            i += 1
+            while i < len(lines) and lines[i][0] in ("op", "run"):
+                if lines[i][0] == "op":
+                    r = lines[i]
+                    ints = [int(x) for x in r[1:10]]
+                    vals = np.asarray([float(x) for x in r[10:]])
+                    c = vals[0::2] + 1j * vals[1::2]
+                    stage["ops"].append(("op", ints, c[:4], c[4:8]))
+                    i += 1
+                else:
+                    hdr = [int(x) for x in lines[i][1:]]
+                    ents = [(complex(float(e[1]), float(e[2])), int(e[3]), int(e[4]), int(e[5]), int(e[6]))
+                            for e in lines[i + 1:i + 1 + hdr[-1]]]
+                    stage["ops"].append(("run", hdr, ents))
+                    i += 1 + hdr[-1]
+            p["stages"].append(stage)
+        for _ in range(int(nj)):
+            p["jobs"].append([int(x) for x in lines[i][1:]])
+            i += 1
+        p["tabs"] = np.asarray([complex(float(r[1]), float(r[2])) for r in lines[i:i + int(nt)]])
+        i += int(nt)
+        res["passes"].append(p)
+    assert lines[i][0] == "plainops"
+    res["plainops"] = lines[i + 1:i + 1 + int(lines[i][1])]
+    i += 1 + int(lines[i][1])
+    assert lines[i][0] == "remaps"
+    res["remaps"] = lines[i + 1:i + 1 + int(lines[i][1])]
+    return res
+
+
+def _execute_images(img, n, psi):
+    N = 1 << n
+    J = np.arange(N)
+    for kind, index in img["steps"]:
+        if kind == 1:
+            row = img["plainops"][index]
+            typ, t, c, a, b = (int(x) for x in row[:5])
+            m = _op([float(x) for x in row[5:]])
+            if typ == F_G1:
+                _apply_1q(psi, n, t, m["m0"])
+            elif typ == F_G1C:
+                _apply_1q(psi, n, t, m["m0"], m["m1"], c)
+            elif typ == F_D:
+                _apply_diag(psi, n, a, None if b < 0 else b, m["d"])
+            else:
+                _apply_2q(psi, n, a, b, m["g"])
+            continue
+        if kind == 2:
+            r = [int(x) for x in img["remaps"][index]]
+            psi = _remap(psi, n, r[0:12], r[12:24])
+            continue
+        assert kind == 0
+        p = img["passes"][index]
+        pos, nt_pos = p["pos"], p["nt_pos"]
+        tile = np.zeros(N, dtype=np.int64)
+        for j, q in enumerate(nt_pos):
+            tile |= ((J >> q) & 1) << j
+        lane = np.zeros(N, dtype=np.int64)
+        for b in range(5):
+            lane |= ((J >> pos[b]) & 1) << b
+        jobs_by_op = {}
+        for op, first, count, scalar in p["jobs"]:
+            jobs_by_op.setdefault(op, []).append((first, count, scalar))
+        for st in p["stages"]:
+            reg, warpb = st["reg"], st["warp"]
+            warp = np.zeros(N, dtype=np.int64)
+            for b in range(3):
+                warp |= ((J >> pos[warpb[b]]) & 1) << b
+            rix = np.zeros(N, dtype=np.int64)
+            for k in range(4):
+                rix |= ((J >> pos[reg[k]]) & 1) << k
+            ctx = tile | (1 << CTX_ONE) | (lane << CTX_LANE) | (warp << CTX_WARP)
+            lw = warp * 32 + lane
+
+            def cbit(x):   # bit of the context word at position x
+                return (ctx >> x) & 1
+
+            def phys(src, bit):
+                return {CS_TILE: lambda: nt_pos[bit], CS_LANE: lambda: pos[bit],
+                        CS_WARP: lambda: pos[warpb[bit]], CS_REG: lambda: pos[reg[bit]]}[src]()
+
+            ops = st["ops"]
+            k2 = 0
+            while k2 < len(ops):
+                rec = ops[k2]
+                if rec[0] == "run":
+                    hdr, ents = rec[1], rec[2]
+                    opi, n_s, nf, umask, tmask, toff = hdr[0], hdr[1], hdr[2:6], hdr[7], hdr[8], hdr[9]
+                    f = np.ones(N, dtype=np.complex128)
+                    e = 0
+                    for _ in range(n_s):   # residual: both context bits
+                        ph, pa, pb, _, _ = ents[e]
+                        f *= np.where((cbit(pa) & cbit(pb)) == 1, ph, 1)
+                        e += 1
+                    for k in range(4):     # residual: register slot k and a context bit
+                        for _ in range(nf[k]):
+                            ph, pa, _, _, _ = ents[e]
+                            f *= np.where((((rix >> k) & 1) & cbit(pa)) == 1, ph, 1)
+                            e += 1
+                    jl = iter(jobs_by_op.get(opi, []))
+                    for b in range(5):     # jobs: scalar (bit 0), then slots 0..3
+                        if not (umask >> b) & 1:
+                            continue
+                        first, count, scalar = next(jl)
+                        u = np.ones(N, dtype=np.complex128)
+                        for ph, pa, pb, _, _ in ents[first:first + count]:
+                            assert pa <= CTX_ONE and (not scalar or pb <= CTX_ONE)
+                            on = (cbit(pa) & cbit(pb)) if scalar else cbit(pa)
+                            u *= np.where(on == 1, ph, 1)
+                        f *= u if b == 0 else np.where(((rix >> (b - 1)) & 1) == 1, u, 1)
+                    t = toff
+                    if tmask & 1:
+                        f *= p["tabs"][t + lw]
+                        t += 256
+                    for k in range(4):
+                        if (tmask >> (1 + k)) & 1:
+                            f *= np.where(((rix >> k) & 1) == 1, p["tabs"][t + lw], 1)
+                            t += 256
+                    if tmask & 32:
+                        f *= p["tabs"][t + rix]
+                    psi *= f
+                    k2 += 1
+                    continue
+                _, ints, m0, m1 = rec
+                _, kind_, slot, csrc, cb, dsrc, db, pad0, pad1 = ints
+                if kind_ == TK_CP:
+                    ra, rb = csrc == CS_REG, dsrc == CS_REG
+                    on_a = ((rix >> cb) & 1) if ra else cbit(pad0)
+                    on_b = ((rix >> db) & 1) if rb else cbit(pad1)
+                    psi *= np.where((on_a & on_b) == 1, m0[0], 1)
+                elif kind_ == TK_DIAG:
+                    _apply_diag(psi, n, phys(csrc, cb), None if dsrc == CS_NONE else phys(dsrc, db), m0)
+                elif kind_ == TK_G2:
+                    nxt = ops[k2 + 1]
+                    g = np.concatenate([m0, m1, nxt[2], nxt[3]])
+                    _apply_2q(psi, n, phys(csrc, cb), phys(dsrc, db), g)
+                    k2 += 1
+                else:
+                    t = pos[reg[slot]] if kind_ == TK_REG else pos[slot]
+                    if csrc == CS_NONE:
+                        _apply_1q(psi, n, t, m0)
+                    else:
+                        _apply_1q(psi, n, t, m0, m1, phys(csrc, cb))
+                k2 += 1
+    return psi
+
+
+IMAGE_CASES = {
+    "qft": (14, lambda: W.qft_circuit(14), True, True),
+    "diagonals": (14, lambda: W.random_gate_mix(14, 400, seed=81, two_q_fraction=0.7,
+                                               names1=["RZ", "S", "T", "U1", "RK", "Z", "H"],
+                                               names2=["CZ", "CP"]), True, True),
+    "layered": (14, lambda: W.layered_haar_cz(14, 12, seed=82), True, True),
+}
+
+
+@pytest.mark.parametrize("name", list(IMAGE_CASES))
+def test_tile_pass_images_reproduce_the_circuit(image_exe, tmp_path, name):
+    n, make, fuse, relabel = IMAGE_CASES[name]
+    ops = make()
+    img = _images(image_exe, tmp_path, n, ops, fuse, relabel)
+    runs = [r for p in img["passes"] for st in p["stages"] for r in st["ops"] if r[0] == "run"]
+    if name != "layered":
+        assert runs, "the case should pack controlled-phase runs"
+    psi0 = W.random_state(n, W.rng(83))
+    ref = SV.apply_circuit(psi0.copy(), n, ops)
+    out = _execute_images(img, n, psi0.copy())
+    assert np.max(np.abs(out - ref)) < 1e-12
