@@ -194,12 +194,17 @@ def test_full_batch_4096_properties(qs):
     sums = np.add.reduceat(p, batch.cnt_off[:-1])
     assert np.all(np.abs(sums - 1) < 1e-4)
     assert np.all(np.isfinite(ll.cpu().numpy())) and np.all(np.isfinite(g.cpu().numpy()))
-    # sampled circuits against the oracle
+    # sampled circuits against the oracle: two of every register size, from the
+    # gradient pass (one circuit per warp up to 4 qubits, per CTA above) and from the
+    # forward pass (one per warp in registers for 1-2 qubits, per CTA above)
+    p_fwd = dev.run()[0].cpu().numpy()
     rng = np.random.default_rng(0)
-    for c in rng.choice(np.where(batch.nq <= 2)[0], size=6, replace=False):
-        n, ops, params = batch.circuit(int(c))
-        np.testing.assert_allclose(p[batch.cnt_off[c]:batch.cnt_off[c + 1]],
-                                   NZ.circuit_probabilities(n, ops, params), atol=2e-5)
+    for nq in range(1, 7):
+        for c in rng.choice(np.where(batch.nq == nq)[0], size=2, replace=False):
+            n, ops, params = batch.circuit(int(c))
+            ref = NZ.circuit_probabilities(n, ops, params)
+            np.testing.assert_allclose(p[batch.cnt_off[c]:batch.cnt_off[c + 1]], ref, atol=2e-5)
+            np.testing.assert_allclose(p_fwd[batch.cnt_off[c]:batch.cnt_off[c + 1]], ref, atol=2e-5)
 
 
 def test_gradient_is_reproducible(qs):
