@@ -539,19 +539,20 @@ __device__ void apply_sub(const T& t, float* r, int n, const SubOp& s, const flo
   }
 }
 
-// The circuit's PTM tables (forward and derivatives), by rank 0.  The products
+// The circuit's PTM tables (forward and derivatives), by rank 0 (sc: sin and cos of
+// theta_x, then of theta_y).  The products
 // C R^x and C R^y are written out entry by entry (C, R^x, R^y are sparse), in
 // FP64 and rounded once to FP32; the FP64 pipe is narrow, so the dense 4x4
 // products would hold the team for several microseconds per circuit.
-__device__ void build_tables(float* tabs, const double* prm) {
+__device__ void build_tables(float* tabs, const double* prm, const double* sc) {
   const double tx = prm[0], ty = prm[1], p = prm[2], g = prm[3];
   const double f = 1.0 - 4.0 * p / 3.0, s = sqrt(1.0 - g);
   const double sf = s * f, hf = (1.0 - g) * f;   // C = [[1,0,0,0],[0,sf,0,0],[0,0,sf,0],[g,0,0,hf]]
   const double dsf_p = -4.0 * s / 3.0, dhf_p = -(1.0 - g) * 4.0 / 3.0;   // d/dp
   const double dsf_g = -f / (2.0 * s), dhf_g = -f;                       // d/dgamma (and d g/dgamma = 1)
-  double cx, sx, cy, sy;
-  sincos(tx, &sx, &cx);
-  sincos(ty, &sy, &cy);
+  (void)tx;
+  (void)ty;
+  const double sx = sc[0], cx = sc[1], sy = sc[2], cy = sc[3];   // sincos(tx), sincos(ty)
   // row-major; row 0 is (m00, 0, 0, 0), column 0 below it (0, 0, m30)
   auto put = [&](int tb, double m00, double m11, double m12, double m13, double m21, double m22,
                  double m23, double m30, double m31, double m32, double m33) {
@@ -1066,7 +1067,7 @@ __device__ __forceinline__ void dm_circuit(const T& t, const DmArgs& A, int c, i
       const int cnt = A.counts[out0 + J];
       if (!(p > 0.0)) p = 1e-300;
       if (cnt > 0) ll += (double)cnt * log(p);
-      z[J] = cnt > 0 ? (double)cnt / p : 0.0;   // seed weights dl/dp_J
+      if constexpr (GRAD) z[J] = cnt > 0 ? (double)cnt / p : 0.0;   // seed weights dl/dp_J
     }
   }
   if (A.counts) {
@@ -1167,7 +1168,14 @@ __device__ void run_circuit(const T& t, const DmArgs& A, int c, int stride, floa
   if (ok)
     for (int k = tid; k < L; k += T::kSize) ok = ok && op_valid(ops + 4 * k, n, A);
   const bool all_ok = t.all(ok);
-  if (all_ok && tid == 0) build_tables(tabs, A.params + 4 * c);
+  if (all_ok && tid < 2) {   // the two angles' sincos side by side (lanes 0 and 1), into z
+    double sn, cs;
+    sincos(A.params[4 * c + tid], &sn, &cs);
+    z[2 * tid] = sn;
+    z[2 * tid + 1] = cs;
+  }
+  t.sync();
+  if (all_ok && tid == 0) build_tables(tabs, A.params + 4 * c, z);
   t.sync();
   if (!all_ok) {
     const float nanf_ = __int_as_float(0x7fc00000);
