@@ -305,6 +305,12 @@ struct WarpTeam {
 // kDense.  The sweeps skip the structural zeros, adding the other terms in the
 // same order as the dense sums, so the results are the same bits.
 enum { kDense = 0, kTP = 1, kChan = 2 };
+// Row 0 of every table applied through kTP or kChan is exactly (1, 0, 0, 0): they are
+// the gates with their channel and the channel alone (the derivative tables, whose
+// row 0 is zero, are only contracted with M, never applied), so the sweeps copy
+// the I entry instead of forming 1 * x.
+template <int F>
+__host__ __device__ constexpr bool unit_row0() { return F != kDense; }
 template <int F>
 __host__ __device__ constexpr bool nz(int d, int e) {
   return F == kDense ? true
@@ -347,6 +353,10 @@ __device__ void apply4(const T& t, float* r, int n, int q, const float* Gs, bool
     for (int d = 0; d < 4; ++d) x[d] = r[base ^ od[d]];
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
+      if (d == 0 && unit_row0<F>()) {
+        y[0] = x[0];
+        continue;
+      }
       float acc = 0.f;
 #pragma unroll
       for (int e = 0; e < 4; ++e)
@@ -469,6 +479,11 @@ __device__ __forceinline__ void stage_a(const float* G, const float (&in)[16], f
   const float4* g4 = reinterpret_cast<const float4*>(G);
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
+    if (d == 0 && unit_row0<F>()) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[j] = in[j];
+      continue;
+    }
     const float4 row = g4[d];
     const float gr[4] = {row.x, row.y, row.z, row.w};
 #pragma unroll
@@ -486,6 +501,11 @@ __device__ __forceinline__ void stage_b(const float* G, const float (&in)[16], f
   const float4* g4 = reinterpret_cast<const float4*>(G);
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
+    if (d == 0 && unit_row0<F>()) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[4 * j] = in[4 * j];
+      continue;
+    }
     const float4 row = g4[d];
     const float gr[4] = {row.x, row.y, row.z, row.w};
 #pragma unroll
