@@ -300,7 +300,9 @@ struct WarpTeam {
 // Nonzero pattern of a 4x4 table, known at compile time.  Every table that
 // build_tables writes (the gates with their channel, the channel alone, and all
 // their derivatives) has row 0 = (m00, 0, 0, 0) and m10 = m20 = 0 (trace
-// preservation; amplitude damping feeds I into z only): kTP, 11 entries.  The
+// preservation; amplitude damping feeds I into z only), and m12 = m21 = 0 (R^x
+// mixes y with z, R^y mixes x with z, the channel keeps x and y apart): kTP, 9
+// entries.  The
 // channel alone is diag(1, sf, sf, hf) plus m30: kChan, 5 entries.  User PTMs are
 // kDense.  The sweeps skip the structural zeros, adding the other terms in the
 // same order as the dense sums, so the results are the same bits.
@@ -314,7 +316,7 @@ __host__ __device__ constexpr bool unit_row0() { return F != kDense; }
 template <int F>
 __host__ __device__ constexpr bool nz(int d, int e) {
   return F == kDense ? true
-         : F == kTP  ? (d == 0 ? e == 0 : (d == 3 || e != 0))
+         : F == kTP  ? (d == 0 ? e == 0 : d == 1 ? (e == 1 || e == 3) : d == 2 ? (e == 2 || e == 3) : true)
                      : (d == e || (d == 3 && e == 0));
 }
 
