@@ -134,6 +134,7 @@ bool commutes_with_diag(const FOp& X, const FOp& D) {
 void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp>& out,
                      std::vector<int>& vmap_out, bool fuse, bool relabel) {
   out.clear();
+  out.reserve(ngates);
   std::vector<int> cur(n);
   for (int q = 0; q < n; ++q) cur[q] = q;
   for (size_t i = 0; i < ngates; ++i) {
@@ -207,17 +208,19 @@ void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp
   vmap_out = cur;
   if (!fuse) return;
 
-  // (1) multiply runs of one-qubit ops (G1 / one-qubit D) on the same qubit
+  // (1) multiply runs of one-qubit ops (G1 / one-qubit D) on the same qubit;
+  // the merged list is compacted in place (it never runs ahead of the input)
   {
-    std::vector<FOp> merged;
-    std::vector<int> last1(n, -1);   // index in merged of the open one-qubit op on q
-    for (const FOp& o : out) {
+    size_t w = 0;
+    std::vector<int> last1(n, -1);   // index in the merged prefix of the open one-qubit op on q
+    for (size_t i = 0; i < out.size(); ++i) {
+      const FOp& o = out[i];
       bool one_q = (o.type == F_G1) || (o.type == F_D && o.b < 0);
       if (one_q) {
         int q = (o.type == F_G1) ? o.t : o.a;
         int j = last1[q];
         if (j >= 0) {
-          FOp& p = merged[j];
+          FOp& p = out[j];
           cd A[4], B[4];
           if (p.type == F_G1) for (int k = 0; k < 4; ++k) A[k] = p.m0[k];
           else { A[0] = p.d[0]; A[1] = 0; A[2] = 0; A[3] = p.d[1]; }
@@ -232,16 +235,17 @@ void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp
           }
           continue;
         }
-        merged.push_back(o);
-        last1[q] = (int)merged.size() - 1;
+        if (w != i) out[w] = o;
+        last1[q] = (int)w++;
         continue;
       }
       uint64_t touched = nd_mask(o) | d_mask(o);
       for (int q = 0; q < n; ++q)
         if ((touched >> q) & 1) last1[q] = -1;
-      merged.push_back(o);
+      if (w != i) out[w] = o;
+      ++w;
     }
-    out.swap(merged);
+    out.resize(w);
   }
 
   // (2) fold diagonal ops into a neighbouring non-diagonal one-qubit op
@@ -270,10 +274,13 @@ void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp
       }
       if (done) dead[i] = 1;
     }
-    std::vector<FOp> kept;
+    size_t w = 0;
     for (size_t i = 0; i < out.size(); ++i)
-      if (!dead[i]) kept.push_back(out[i]);
-    out.swap(kept);
+      if (!dead[i]) {
+        if (w != i) out[w] = out[i];
+        ++w;
+      }
+    out.resize(w);
   }
 }
 

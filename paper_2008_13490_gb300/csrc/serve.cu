@@ -253,6 +253,8 @@ struct Server {
   int* d_status = nullptr;
   int64_t published = 0;
   std::deque<QJob> in_queue;         // published jobs in publish order, until retired from the front
+  std::vector<FOp> fops_scratch;     // fused ops of the circuit being published
+  std::vector<int> vmap_scratch;
   int64_t op_head = 0, op_tail = 0, res_head = 0, res_tail = 0;
   // statistics
   std::vector<double> lat_ms;
@@ -278,9 +280,8 @@ struct Server {
   bool publish_t(Req* r) {
     const int64_t oldest = in_queue.empty() ? published : in_queue.front().job;
     if (published - oldest >= kRing) return false;   // ring full
-    std::vector<FOp> fops;
-    std::vector<int> vmap;
-    build_fused_ops(r->gates.data(), r->gates.size(), r->n, fops, vmap, true, false);
+    std::vector<FOp>& fops = fops_scratch;   // the scheduler thread's, reused across circuits
+    build_fused_ops(r->gates.data(), r->gates.size(), r->n, fops, vmap_scratch, true, false);
     const int64_t nops = (int64_t)fops.size();
     const int64_t H = (int64_t)1 << r->k;
     int64_t oh = op_head, rh = res_head, op_at = 0, res_at = 0;

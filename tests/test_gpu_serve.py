@@ -74,11 +74,14 @@ def test_admission_by_memory(qs):
 def test_failed_completion_query_returns_error(qs, n):
     # a completion query of the persistent packed kernel that reports an error
     # (injected on the host: no device fault) ends the queued circuits' waits with
-    # QS_ECUDA; the queue starts over and the server keeps serving
+    # QS_ECUDA; the queue starts over and the server keeps serving.  The failing
+    # circuit is deep (milliseconds in the kernel), so the scheduler's first
+    # completion query comes while its job still runs: a short job could finish
+    # and be retired before that query.
     srv = qs.Server(max_inflight=2)
     ops = W.layered_haar_cz(n, 4, seed=n)
     qs.server_inject_query_error(srv, 999)   # cudaErrorUnknown
-    t = srv.submit(n, ops, _mask(n))
+    t = srv.submit(n, W.layered_haar_cz(n, 100, seed=n + 1), _mask(n))
     with pytest.raises(qs.QsimError) as e:
         srv.wait(t)
     assert e.value.status == qs.QS_ECUDA
