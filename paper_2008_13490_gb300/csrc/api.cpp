@@ -8,6 +8,7 @@
 #include <new>
 #include <utility>
 
+#include "host_par.h"
 #include "internal.h"
 #include "tile_cp.h"
 
@@ -716,21 +717,27 @@ qs_status run_block_list(State* st, const std::vector<Block>& blocks, int mode, 
   std::vector<BlockPass> passes(blocks.size());
   for (size_t i = 0; i < blocks.size(); ++i) {
     block_pass_desc(st->n, blocks[i].q, passes[i]);
-    if (block_is_unitary(blocks[i].U.data())) passes[i].flags |= 1;
     if (!block_pass_runs_contiguous(passes[i])) {
       set_error("block pass: tile layout without contiguous low bits");
       return QS_EUNSUPPORTED;
     }
   }
-  const size_t off_pass = put(blob, passes.data(), passes.size());
+  // per block (independent, on host threads): the unitarity flag and the split B operand
   const size_t bb = block_b_bytes(mode);
-  const size_t off_b = align16(blob.size());
-  blob.resize(off_b + bb * blocks.size());
-  std::vector<unsigned char> tmp;
-  for (size_t i = 0; i < blocks.size(); ++i) {
+  std::vector<unsigned char> bops(bb * blocks.size());
+  std::vector<char> unitary(blocks.size(), 0);
+  parallel_for(blocks.size(), 4, [&](size_t i) {
+    unitary[i] = block_is_unitary(blocks[i].U.data()) ? 1 : 0;
+    std::vector<unsigned char> tmp;
     block_b_operand(blocks[i].U.data(), mode, tmp);
-    std::memcpy(blob.data() + off_b + i * bb, tmp.data(), bb);
-  }
+    std::memcpy(bops.data() + i * bb, tmp.data(), bb);
+  });
+  for (size_t i = 0; i < blocks.size(); ++i)
+    if (unitary[i]) passes[i].flags |= 1;
+  const size_t off_pass = put(blob, passes.data(), passes.size());
+  const size_t off_b = align16(blob.size());
+  blob.resize(off_b + bops.size());
+  std::memcpy(blob.data() + off_b, bops.data(), bops.size());
   qs_status s = upload(st, blob);
   if (s != QS_OK) return s;
   unsigned char* dev = (unsigned char*)st->opbuf;

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "host_par.h"
 #include "internal.h"
 
 namespace qs {
@@ -15,8 +16,12 @@ namespace qs {
 namespace {
 
 // U <- G U, G acting on the block-local bits ia (and ib, the less significant
-// bit of G's 4x4 local index) of the 32-dimensional block space.
-void apply_to_block(std::vector<cd>& U, const cd* g, int dim, int ia, int ib) {
+// bit of G's 4x4 local index) of the 32-dimensional block space.  Written out in
+// real arithmetic along a row's 32 columns; every complex product is
+// (x_re y_re - x_im y_im, x_re y_im + x_im y_re) and the sums run in gate-entry
+// order, as the complex-typed expressions would compute them.
+void apply_to_block(std::vector<cd>& Uv, const cd* g, int dim, int ia, int ib) {
+  double* U = reinterpret_cast<double*>(Uv.data());   // row r: 32 (re, im) pairs from U + 64 r
   // a diagonal gate scales rows (entries exactly 1 leave them alone)
   bool diag = true;
   for (int o = 0; o < dim; ++o)
@@ -27,33 +32,50 @@ void apply_to_block(std::vector<cd>& U, const cd* g, int dim, int ia, int ib) {
       const int l = dim == 2 ? ((r >> ia) & 1) : (((r >> ia) & 1) << 1) | ((r >> ib) & 1);
       const cd d = g[l * dim + l];
       if (d == cd(1)) continue;
-      for (int c = 0; c < 32; ++c) U[r * 32 + c] *= d;
-    }
-    return;
-  }
-  if (dim == 2) {
-    for (int r = 0; r < 32; ++r) {
-      if ((r >> ia) & 1) continue;
-      const int r1 = r | (1 << ia);
+      const double dr = d.real(), di = d.imag();
+      double* u = U + 64 * r;
       for (int c = 0; c < 32; ++c) {
-        const cd a = U[r * 32 + c], b = U[r1 * 32 + c];
-        U[r * 32 + c] = g[0] * a + g[1] * b;
-        U[r1 * 32 + c] = g[2] * a + g[3] * b;
+        const double ur = u[2 * c], ui = u[2 * c + 1];
+        u[2 * c] = ur * dr - ui * di;
+        u[2 * c + 1] = ur * di + ui * dr;
       }
     }
     return;
   }
+  if (dim == 2) {
+    const double g0r = g[0].real(), g0i = g[0].imag(), g1r = g[1].real(), g1i = g[1].imag();
+    const double g2r = g[2].real(), g2i = g[2].imag(), g3r = g[3].real(), g3i = g[3].imag();
+    for (int r = 0; r < 32; ++r) {
+      if ((r >> ia) & 1) continue;
+      double* A = U + 64 * r;
+      double* B = U + 64 * (r | (1 << ia));
+      for (int c = 0; c < 32; ++c) {
+        const double ar = A[2 * c], ai = A[2 * c + 1], br = B[2 * c], bi = B[2 * c + 1];
+        A[2 * c] = (g0r * ar - g0i * ai) + (g1r * br - g1i * bi);
+        A[2 * c + 1] = (g0r * ai + g0i * ar) + (g1r * bi + g1i * br);
+        B[2 * c] = (g2r * ar - g2i * ai) + (g3r * br - g3i * bi);
+        B[2 * c + 1] = (g2r * ai + g2i * ar) + (g3r * bi + g3i * br);
+      }
+    }
+    return;
+  }
+  double gr[16], gi[16];
+  for (int k = 0; k < 16; ++k) gr[k] = g[k].real(), gi[k] = g[k].imag();
   for (int r = 0; r < 32; ++r) {
     if (((r >> ia) & 1) || ((r >> ib) & 1)) continue;
-    int idx[4];
-    for (int l = 0; l < 4; ++l) idx[l] = r | ((l >> 1) << ia) | ((l & 1) << ib);
+    double* row[4];
+    for (int l = 0; l < 4; ++l) row[l] = U + 64 * (r | ((l >> 1) << ia) | ((l & 1) << ib));
     for (int c = 0; c < 32; ++c) {
-      cd x[4];
-      for (int l = 0; l < 4; ++l) x[l] = U[idx[l] * 32 + c];
+      double xr[4], xi[4];
+      for (int l = 0; l < 4; ++l) xr[l] = row[l][2 * c], xi[l] = row[l][2 * c + 1];
       for (int o = 0; o < 4; ++o) {
-        cd acc = 0;
-        for (int l = 0; l < 4; ++l) acc += g[o * 4 + l] * x[l];
-        U[idx[o] * 32 + c] = acc;
+        double sr = 0.0, si = 0.0;
+        for (int l = 0; l < 4; ++l) {
+          sr += gr[o * 4 + l] * xr[l] - gi[o * 4 + l] * xi[l];
+          si += gr[o * 4 + l] * xi[l] + gi[o * 4 + l] * xr[l];
+        }
+        row[o][2 * c] = sr;
+        row[o][2 * c + 1] = si;
       }
     }
   }
@@ -67,29 +89,31 @@ uint64_t gate_mask(const qs_gate& g) {
 
 // The gates a block on qubit set S absorbs: in circuit order, every remaining gate
 // whose qubits lie in S and that no skipped earlier gate on a shared qubit
-// precedes.  Stops once every qubit of S is blocked.
-int absorb(const qs_gate* gates, const std::vector<size_t>& rem, uint64_t S, std::vector<size_t>* sel) {
+// precedes.  Stops once every qubit of S is blocked.  rem_m[i] is the qubit mask
+// of remaining gate rem[i].
+int absorb(const std::vector<uint64_t>& rem_m, const std::vector<size_t>& rem, uint64_t S,
+           std::vector<size_t>* sel) {
   uint64_t blocked = 0;
   int cnt = 0;
-  for (size_t gi : rem) {
-    const uint64_t qm = gate_mask(gates[gi]);
+  for (size_t i = 0; i < rem_m.size(); ++i) {
+    const uint64_t qm = rem_m[i];
     if ((qm & blocked) || (qm & ~S)) {
       blocked |= qm;
       if ((blocked & S) == S) break;
       continue;
     }
     ++cnt;
-    if (sel) sel->push_back(gi);
+    if (sel) sel->push_back(rem[i]);
   }
   return cnt;
 }
 
 // qubit set grown in circuit order from remaining gate `start` (the gates that
 // are ready and fit), filled up to 5 with the lowest free qubits
-uint64_t grown_set(const qs_gate* gates, const std::vector<size_t>& rem, size_t start, int n) {
+uint64_t grown_set(const std::vector<uint64_t>& rem_m, size_t start, int n) {
   uint64_t S = 0, blocked = 0;
-  for (size_t i = start; i < rem.size() && __builtin_popcountll(S) < 5; ++i) {
-    const uint64_t qm = gate_mask(gates[rem[i]]);
+  for (size_t i = start; i < rem_m.size() && __builtin_popcountll(S) < 5; ++i) {
+    const uint64_t qm = rem_m[i];
     if (qm & blocked) {
       blocked |= qm;
       continue;
@@ -99,6 +123,24 @@ uint64_t grown_set(const qs_gate* gates, const std::vector<size_t>& rem, size_t 
   }
   for (int q = 0; q < n && __builtin_popcountll(S) < 5; ++q) S |= 1ull << q;
   return S;
+}
+
+// U of block b: the product of its gates, in circuit order
+void block_product(const qs_gate* gates, Block& b) {
+  b.U.assign(32 * 32, cd(0));
+  for (int i = 0; i < 32; ++i) b.U[i * 32 + i] = 1.0;
+  auto local = [&](int q) {
+    for (int i = 0; i < 5; ++i)
+      if (b.q[i] == q) return i;
+    return -1;
+  };
+  for (size_t gi : b.gate_idx) {
+    const qs_gate& g = gates[gi];
+    cd m[16];
+    int dim = 0;
+    gate_matrix(g, m, &dim);
+    apply_to_block(b.U, m, dim, local(g.q[0]), dim == 4 ? local(g.q[1]) : -1);
+  }
 }
 
 }  // namespace
@@ -113,12 +155,16 @@ void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>&
   constexpr int kSeeds = 64;
   out.clear();
   std::vector<size_t> remaining(ngates);
-  for (size_t i = 0; i < ngates; ++i) remaining[i] = i;
+  std::vector<uint64_t> rem_m(ngates);   // qubit masks of the remaining gates, in the same order
+  for (size_t i = 0; i < ngates; ++i) {
+    remaining[i] = i;
+    rem_m[i] = gate_mask(gates[i]);
+  }
   std::vector<uint64_t> cands;
   while (!remaining.empty()) {
     cands.clear();
     for (int k = 0; k < kSeeds && k < (int)remaining.size(); ++k) {
-      const uint64_t S = grown_set(gates, remaining, (size_t)k, n);
+      const uint64_t S = grown_set(rem_m, (size_t)k, n);
       if (std::find(cands.begin(), cands.end(), S) == cands.end()) cands.push_back(S);
     }
     for (int a = 0; a + 5 <= n; ++a) {
@@ -128,50 +174,38 @@ void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>&
     uint64_t best = cands[0];
     int best_cnt = -1;
     for (uint64_t S : cands) {
-      const int c = absorb(gates, remaining, S, nullptr);
+      const int c = absorb(rem_m, remaining, S, nullptr);
       if (c > best_cnt) {
         best_cnt = c;
         best = S;
       }
     }
     std::vector<size_t> sel;
-    absorb(gates, remaining, best, &sel);
+    absorb(rem_m, remaining, best, &sel);
     // ascending positions: local bit i of the block = its i-th lowest qubit (the
     // kernel relies on the block qubits among the 4 lowest positions being its
     // lowest local bits)
     Block b;
     for (int q = 0, i = 0; q < n && i < 5; ++q)
       if ((best >> q) & 1) b.q[i++] = q;
-    b.U.assign(32 * 32, cd(0));
-    for (int i = 0; i < 32; ++i) b.U[i * 32 + i] = 1.0;
-    for (size_t gi : sel) {
-      const qs_gate& g = gates[gi];
-      cd m[16];
-      int dim = 0;
-      gate_matrix(g, m, &dim);
-      auto local = [&](int q) {
-        for (int i = 0; i < 5; ++i)
-          if (b.q[i] == q) return i;
-        return -1;
-      };
-      apply_to_block(b.U, m, dim, local(g.q[0]), dim == 4 ? local(g.q[1]) : -1);
-    }
     b.ngates = (int)sel.size();
     b.gate_idx = sel;
     out.push_back(std::move(b));
     // the rest, in order (sel is a subsequence of remaining)
-    std::vector<size_t> rest;
-    rest.reserve(remaining.size() - sel.size());
-    size_t j = 0;
-    for (size_t gi : remaining) {
-      if (j < sel.size() && sel[j] == gi) {
+    size_t w = 0, j = 0;
+    for (size_t i = 0; i < remaining.size(); ++i) {
+      if (j < sel.size() && sel[j] == remaining[i]) {
         ++j;
         continue;
       }
-      rest.push_back(gi);
+      remaining[w] = remaining[i];
+      rem_m[w++] = rem_m[i];
     }
-    remaining.swap(rest);
+    remaining.resize(w);
+    rem_m.resize(w);
   }
+  // each block's product of its gates (blocks are independent)
+  parallel_for(out.size(), 8, [&](size_t bi) { block_product(gates, out[bi]); });
 }
 
 int block_nonzeros(const Block& b) {
