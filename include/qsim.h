@@ -187,14 +187,33 @@ qs_status sv_apply_circuit(qs_state_t st, const qs_gate* gates, size_t ngates,
 qs_status sv_probs(qs_state_t st, void* out, int out_fp64, uint64_t marg_mask, double* norm_out);
 
 /* sv_probs into a HOST buffer: the same values (2^n, or 2^popcount(mask) for a
- * marginal; float or double as out_fp64).  The full distribution is formed in
- * 64 MiB chunks in a device staging buffer (obtained from the state's allocator
- * at the first call and kept until sv_destroy) and each chunk copied to host_out
- * (page-locked host memory gives the full link bandwidth; pageable memory works,
- * slower).
+ * marginal; float or double as out_fp64).  Into page-locked host memory that the
+ * device can address (cudaHostAlloc / pinned), the kernel writes the full
+ * distribution directly; into any other host memory it is formed in 64 MiB
+ * chunks in a device staging buffer (obtained from the state's allocator at the
+ * first call and kept until sv_destroy) and each chunk copied to host_out.
+ * Copies queued by sv_probs_host_async on this state are waited for first.
  * norm_out as in sv_probs.  Synchronises.  Errors: QS_EINVAL, QS_ENOMEM,
  * QS_EUNSUPPORTED (marginal over more than 16 qubits), QS_ECUDA. */
 qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t marg_mask, double* norm_out);
+
+/* The full distribution p_J = |a_J|^2 (Born rule, as sv_probs) into a HOST
+ * buffer without waiting for the copy, so that it overlaps whatever the caller
+ * queues next on the state.  The probabilities are formed on the state's stream
+ * into one of two device buffers that the state keeps (2 x 2^n floats or
+ * doubles, from the state's allocator at the first call, released by
+ * sv_destroy), then copied to host_out on a copy stream of the state's own.  The
+ * call returns once both steps are queued: the state may be changed at once (the
+ * copy reads the buffer, not the amplitudes), but host_out (2^n floats when
+ * out_fp64 = 0, else doubles; page-locked for the copy to run asynchronously)
+ * must stay allocated and unread until sv_probs_wait returns.  The two buffers
+ * are used in turn; a call whose buffer still feeds an earlier copy makes the
+ * state's stream wait for that copy on the device.  Errors: QS_EINVAL (NULL
+ * state or host_out), QS_ENOMEM (the buffers), QS_ECUDA. */
+qs_status sv_probs_host_async(qs_state_t st, void* host_out, int out_fp64);
+/* Waits for every copy that sv_probs_host_async queued on this state; returns
+ * QS_ECUDA with the message if one of them failed.  sv_destroy waits too. */
+qs_status sv_probs_wait(qs_state_t st);
 
 /* Multinomial log-likelihood l = sum_J n_J log p_J (terms with n_J = 0 are 0;
  * p_J <= 0 with n_J > 0 is clamped to 1e-300 and counted).  counts: DEVICE,

@@ -123,6 +123,8 @@ def load():
         "sv_apply_circuit": (i32, [vp, vp, sz, ctypes.POINTER(_Opts), ctypes.POINTER(_Stats)]),
         "sv_probs": (i32, [vp, vp, i32, u64, ctypes.POINTER(ctypes.c_double)]),
         "sv_probs_host": (i32, [vp, vp, i32, u64, ctypes.POINTER(ctypes.c_double)]),
+        "sv_probs_host_async": (i32, [vp, vp, i32]),
+        "sv_probs_wait": (i32, [vp]),
         "sv_loglik": (i32, [vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
         "sv_grad": (i32, [vp, vp, sz, vp, i32, i32, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double)]),
@@ -160,7 +162,8 @@ def load():
 
 def exported_symbols():
     return ["sv_create", "sv_wrap", "sv_destroy", "sv_set_stream", "sv_info", "sv_set_basis", "sv_copy_in",
-            "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_probs_host", "sv_loglik", "sv_grad",
+            "sv_copy_out", "sv_apply_circuit", "sv_probs", "sv_probs_host", "sv_probs_host_async", "sv_probs_wait",
+            "sv_loglik", "sv_grad",
             "dm_apply_channels", "qs_ptm_check", "qs_probs_noalloc", "sv_bloch", "qs_meas_error", "sv_save", "sv_load",
             "dm_gst_series", "dm_gst_power", "dm_code422_eval",
             "qs_profile_begin", "qs_profile_end", "qs_alu_peak",
@@ -478,6 +481,20 @@ def sv_probs_host(st: State, out=None, fp64: bool = False, marg_mask: int = 0, w
     _check(load().sv_probs_host(st.handle, ptr, 1 if fp64 else 0, int(marg_mask),
                                 ctypes.byref(norm) if want_norm else None))
     return out, (norm.value if want_norm else None)
+
+
+def sv_probs_host_async(st: State, out, fp64: bool = False):
+    """The full Born-rule distribution into a HOST buffer ``out`` (a numpy array, or a
+    pinned CPU torch tensor; 2^n float32, or float64 with ``fp64``) without waiting
+    for the copy: ``out`` holds it once ``sv_probs_wait(st)`` has returned.  Returns out."""
+    ptr = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+    _check(load().sv_probs_host_async(st.handle, ptr, 1 if fp64 else 0))
+    return out
+
+
+def sv_probs_wait(st: State):
+    """Waits for the host copies queued on the state by sv_probs_host_async."""
+    _check(load().sv_probs_wait(st.handle))
 
 
 def _gst_batch(n, ptms, rho, effects, gate, prep, r_max=0, validate=False):

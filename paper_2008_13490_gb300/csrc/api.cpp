@@ -6,6 +6,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <utility>
 
 #include "host_par.h"
@@ -893,6 +894,98 @@ qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method
   return s;
 }
 
+// Copies of probabilities to host memory queued by sv_probs_host_async, per
+// state: two device buffers used in turn, a non-blocking copy stream, and per
+// buffer an event when its probabilities are formed (state's stream) and one
+// when its copy has ended (copy stream).  Kept beside the state, keyed by it.
+struct HostCopies {
+  void* buf = nullptr;   // 2 * half bytes
+  size_t half = 0;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t formed[2] = {nullptr, nullptr};
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  bool queued[2] = {false, false};
+  int next = 0;
+};
+std::mutex g_copies_mu;
+std::unordered_map<const State*, HostCopies*> g_copies;
+
+HostCopies* find_copies(const State* st) {
+  std::lock_guard<std::mutex> g(g_copies_mu);
+  auto it = g_copies.find(st);
+  return it == g_copies.end() ? nullptr : it->second;
+}
+
+// waits for the state's queued copies (if any); the first error is returned
+qs_status wait_copies(State* st) {
+  HostCopies* hc = find_copies(st);
+  if (!hc) return QS_OK;
+  const cudaError_t e = cudaStreamSynchronize(hc->cs);
+  hc->queued[0] = hc->queued[1] = false;
+  return e == cudaSuccess ? QS_OK : cuda_status(e, "copy of probabilities to the host");
+}
+
+void release_copies(State* st) {
+  HostCopies* hc = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_copies_mu);
+    auto it = g_copies.find(st);
+    if (it == g_copies.end()) return;
+    hc = it->second;
+    g_copies.erase(it);
+  }
+  if (hc->cs) cudaStreamSynchronize(hc->cs);
+  if (hc->buf) dev_free(st, hc->buf, 2 * hc->half);
+  for (int k = 0; k < 2; ++k) {
+    if (hc->formed[k]) cudaEventDestroy(hc->formed[k]);
+    if (hc->copied[k]) cudaEventDestroy(hc->copied[k]);
+  }
+  if (hc->cs) cudaStreamDestroy(hc->cs);
+  delete hc;
+}
+
+// the state's copy pipeline with buffers of at least `half` bytes each
+qs_status copies_for(State* st, size_t half, HostCopies** out) {
+  HostCopies* hc = find_copies(st);
+  if (hc && hc->half < half) {   // buffers too small (an fp64 call after fp32 ones): start over
+    release_copies(st);
+    hc = nullptr;
+  }
+  if (!hc) {
+    hc = new (std::nothrow) HostCopies();
+    if (!hc) {
+      set_error("host copy pipeline: out of host memory");
+      return QS_ENOMEM;
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&hc->cs, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&hc->formed[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hc->copied[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) {
+      hc->buf = dev_alloc(st, 2 * half);
+      hc->half = half;
+    }
+    {
+      std::lock_guard<std::mutex> g(g_copies_mu);
+      g_copies[st] = hc;   // released by release_copies on every path below
+    }
+    if (e != cudaSuccess) {
+      const qs_status s = cuda_status(e, "host copy pipeline");
+      release_copies(st);
+      return s;
+    }
+    if (!hc->buf) {
+      hc->half = 0;
+      release_copies(st);
+      set_error("device buffers for the host copies of the probabilities could not be allocated");
+      return QS_ENOMEM;
+    }
+  }
+  *out = hc;
+  return QS_OK;
+}
+
 }  // namespace qs
 
 using namespace qs;
@@ -1007,6 +1100,7 @@ qs_status sv_wrap(int n, int prec, void* device_buf, const qs_allocator* alloc, 
 qs_status sv_destroy(qs_state_t st) {
   if (!st) return QS_OK;
   cudaStreamSynchronize(st->stream);
+  release_copies(st);
   dev_free(st, st->opbuf, st->opbuf_bytes);
   if (st->stage) dev_free(st, st->stage, st->stage_bytes);
   dev_free(st, st->scratch, st->scratch_bytes);
@@ -1129,6 +1223,8 @@ qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t ma
     set_error("marginal mask has bits beyond n = %d", st->n);
     return QS_EINVAL;
   }
+  s = wait_copies(st);
+  if (s != QS_OK) return s;
   const int k = __builtin_popcountll(marg_mask);
   unsigned char* sc = (unsigned char*)st->scratch;
   double* partials = (double*)(sc + kScratchPartials);
@@ -1189,6 +1285,40 @@ qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t ma
   const cudaError_t e = cudaStreamSynchronize(st->stream);
   if (s == QS_OK && e != cudaSuccess) s = cuda_status(e, "sv_probs_host");
   return s;
+}
+
+qs_status sv_probs_host_async(qs_state_t st, void* host_out, int out_fp64) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (!host_out) {
+    set_error("host_out is required");
+    return QS_EINVAL;
+  }
+  const uint64_t N = 1ull << st->n;
+  const size_t bytes = (size_t)N * (out_fp64 ? sizeof(double) : sizeof(float));
+  HostCopies* hc = nullptr;
+  s = copies_for(st, bytes, &hc);
+  if (s != QS_OK) return s;
+  const int k = hc->next;
+  unsigned char* dst = (unsigned char*)hc->buf + (size_t)k * hc->half;
+  // the buffer's earlier copy has to end before the buffer is rewritten
+  if (hc->queued[k]) QS_CUDA(cudaStreamWaitEvent(st->stream, hc->copied[k], 0));
+  double* partials = (double*)((unsigned char*)st->scratch + kScratchPartials);
+  s = launch_probs_range(st, 0, N, dst, out_fp64, partials);
+  if (s != QS_OK) return s;
+  QS_CUDA(cudaEventRecord(hc->formed[k], st->stream));
+  QS_CUDA(cudaStreamWaitEvent(hc->cs, hc->formed[k], 0));
+  QS_CUDA(cudaMemcpyAsync(host_out, dst, bytes, cudaMemcpyDeviceToHost, hc->cs));
+  QS_CUDA(cudaEventRecord(hc->copied[k], hc->cs));
+  hc->queued[k] = true;
+  hc->next = k ^ 1;
+  return QS_OK;
+}
+
+qs_status sv_probs_wait(qs_state_t st) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  return wait_copies(st);
 }
 
 qs_status sv_loglik(qs_state_t st, const uint32_t* counts, double* out, int64_t* clamped) {

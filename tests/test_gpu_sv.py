@@ -266,6 +266,42 @@ def test_probs_to_host_buffer(qs, prec):
     st.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_probs_to_host_without_waiting(qs, prec):
+    # sv_probs_host_async: three distributions queued back to back while the state
+    # changes after each call (the third call reuses the first device buffer, so the
+    # state's stream waits for the first copy); after sv_probs_wait every host buffer
+    # holds its own step's values, equal to sv_probs bit for bit.  Then pageable
+    # memory, and an fp64 call after fp32 ones (larger buffers)
+    import torch
+    n = 16
+    st = qs.State(n, prec)
+    steps = [W.random_gate_mix(n, 50, seed=700 + i) for i in range(3)]
+    bufs = [torch.full((1 << n,), -1.0, dtype=torch.float32, pin_memory=True) for _ in steps]
+    refs = []
+    for ops, buf in zip(steps, bufs):
+        qs.sv_apply_circuit(st, ops)
+        refs.append(qs.sv_probs(st, want_norm=False)[0])   # device values, no synchronisation
+        qs.sv_probs_host_async(st, buf)
+    qs.sv_probs_wait(st)
+    for ref, buf in zip(refs, bufs):
+        np.testing.assert_array_equal(buf.numpy(), ref.cpu().numpy())
+    psi = SV.basis(n)
+    for ops in steps:
+        psi = SV.apply_circuit(psi, n, ops)
+    np.testing.assert_allclose(bufs[2].numpy(), SV.probabilities(psi), atol=2e-6)
+    page = np.full(1 << n, -1.0, dtype=np.float32)
+    qs.sv_probs_host_async(st, page)
+    qs.sv_probs_wait(st)
+    np.testing.assert_array_equal(page, refs[2].cpu().numpy())
+    p64 = torch.empty(1 << n, dtype=torch.float64, pin_memory=True)
+    qs.sv_probs_host_async(st, p64, fp64=True)
+    qs.sv_set_basis(st, 5)
+    qs.sv_probs_wait(st)
+    np.testing.assert_allclose(p64.numpy(), SV.probabilities(psi), atol=1e-12 if prec else 2e-6)
+    st.close()
+
+
 def test_alu_peak_microbenchmark(qs):
     # the measured FP32 / FP64 peaks used as roofline denominators: plausible and
     # consistent with the device's SM count (FP32 at most 128 FMA lanes per SM at 2.1 GHz)
