@@ -468,25 +468,18 @@ def run_ours(args, world, rank, local):
     ms_per_step = ms_max / args.steps
 
     # ---- end to end through the C ABI with host buffers: the gate array from host
-    # memory (planner + descriptor upload inside sv_apply_circuit), each step's
-    # probabilities copied into pinned host memory (sv_probs_host_async: the copy of
-    # step k runs while step k + 1's circuit does; before step k + 1's copy is queued
-    # into the same host buffer, sv_probs_wait has returned, so step k's values were
-    # in host memory), the same number of steps as `value`; the last copy ends
-    # inside the timed region
+    # memory (planner + descriptor upload inside sv_apply_circuit), the probabilities
+    # into a pinned host buffer (sv_probs_host: the kernel writes them straight into
+    # it), the same number of steps as `value`
     host_probs = torch.empty(1 << n, dtype=torch.float32, pin_memory=True)
-    for _ in range(2):                                  # warm the two device buffers of the copies
-        qs.sv_probs_host_async(st, host_probs)
-    qs.sv_probs_wait(st)
+    qs.sv_probs_host(st, out=host_probs)               # warm the path of the copy
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         qs.sv_set_basis(st, 0)
         s2 = qs.sv_apply_circuit(st, arr, method)
-        qs.sv_probs_wait(st)
-        qs.sv_probs_host_async(st, host_probs)
-    qs.sv_probs_wait(st)
+        qs.sv_probs_host(st, out=host_probs)
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_s = max_over_ranks(world, e2e_s)
 
@@ -547,9 +540,8 @@ def run_ours(args, world, rank, local):
                 "h2d_bytes_per_step": int(s2["upload_bytes"]),
                 "d2h_bytes_per_step": (1 << n) * 4, "steps": args.steps,
                 "path": "sv_apply_circuit (host gate array, planner, descriptor upload) + "
-                        "sv_probs_host_async (4 GiB of probabilities into pinned host memory, "
-                        "copied while the next step's circuit runs; sv_probs_wait before the "
-                        "next copy and after the last step)"},
+                        "sv_probs_host (4 GiB of probabilities written by the kernel into pinned "
+                        "host memory)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "norm": norm,
