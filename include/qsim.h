@@ -210,9 +210,9 @@ qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t ma
  * are used in turn; a call whose buffer still feeds an earlier copy makes the
  * state's stream wait for that copy on the device.  The copy runs on a copy
  * engine, which shares HBM with the kernels queued after the call: beside kernels
- * that keep HBM busy (the 5-qubit block passes) it slows down to about their
- * length, and the synchronous sv_probs_host, whose kernel writes into the host
- * buffer itself, is the faster choice there.  Errors: QS_EINVAL (NULL state or
+ * that keep HBM busy (the 5-qubit block passes) it runs far slower than alone,
+ * and the synchronous sv_probs_host, whose kernel writes into the host buffer
+ * itself, is the faster choice there.  Errors: QS_EINVAL (NULL state or
  * host_out), QS_ENOMEM (the buffers), QS_ECUDA. */
 qs_status sv_probs_host_async(qs_state_t st, void* host_out, int out_fp64);
 /* Waits for every copy that sv_probs_host_async queued on this state; returns
