@@ -7,11 +7,11 @@ state), 40 layers of Haar-random SU(2) on every qubit plus brickwork CZ
 probabilities (4 GiB fp32) and their fp64 norm.  One step = one such circuit,
 by default through the library's default method (QS_METHOD_AUTO: dense 5-qubit
 blocks on the tcgen05 tensor cores with the BF16 three-part split and FP32
-accumulation, sparse stretches on tile passes; for this circuit every block is
-dense; --method selects another), the tiled FP32 SIMT path reported as a row
-of the same line.
+accumulation, sparse stretches on tile passes; for this circuit 93 of the 100
+blocks are dense and the gates of the other 7 take 3 tile passes; --method
+selects another), the tiled FP32 SIMT path reported as a row of the same line.
 
-metric (BASELINE's): reported in "gates/s" = gates of the circuit applied to the
+metric: reported in "gates/s" = gates of the circuit applied to the
 full 2^30-amplitude state per second (the real HBM sweeps per second are in
 hbm.sweeps_per_s: fused methods apply many gates per sweep).
 The JSON line also carries the real HBM sweeps and bytes, the roofline of the
