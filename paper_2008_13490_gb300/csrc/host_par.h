@@ -4,21 +4,35 @@
 #include <algorithm>
 #include <atomic>
 #include <cstddef>
+#include <cstdlib>
 #include <thread>
 #include <vector>
 
 namespace qs {
 
-// Runs f(i) for every i in [0, n): on the calling thread and up to 7 more, one
-// thread per min_items items at most, each claiming the next item from a shared
-// counter.  The items must be independent (each f(i) writes only its own
-// outputs), so the results do not depend on the thread count.  If a thread
-// cannot be started, the threads already running (the caller among them) do the
-// rest.
+// Host threads the planners may use: the environment variable QS_HOST_THREADS
+// (1 = the calling thread only) if set to a positive number, else the hardware
+// threads; at most 8 either way.
+inline size_t host_threads() {
+  static const size_t cap = [] {
+    const char* e = std::getenv("QS_HOST_THREADS");
+    const long v = e ? std::strtol(e, nullptr, 10) : 0;
+    const unsigned hw = std::thread::hardware_concurrency();
+    const size_t t = v > 0 ? (size_t)v : (size_t)(hw ? hw : 1);
+    return std::min<size_t>(t, 8);
+  }();
+  return cap;
+}
+
+// Runs f(i) for every i in [0, n): on the calling thread and up to
+// host_threads() - 1 more, one thread per min_items items at most, each claiming
+// the next item from a shared counter.  The items must be independent (each f(i)
+// writes only its own outputs), so the results do not depend on the thread
+// count.  If a thread cannot be started, the threads already running (the caller
+// among them) do the rest.
 template <class F>
 void parallel_for(size_t n, size_t min_items, F&& f) {
-  const unsigned hw = std::thread::hardware_concurrency();
-  const size_t nt = std::min<size_t>({(size_t)(hw ? hw : 1), (size_t)8, n / std::max<size_t>(min_items, 1)});
+  const size_t nt = std::min<size_t>(host_threads(), n / std::max<size_t>(min_items, 1));
   if (nt <= 1) {
     for (size_t i = 0; i < n; ++i) f(i);
     return;

@@ -81,3 +81,20 @@ def test_blocks_reproduce_the_circuit(dump_exe, tmp_path, name):
         np.testing.assert_allclose(U.conj().T @ U, np.eye(32), atol=1e-12)
         psi = _apply_block(psi, n, q, U)
     assert np.max(np.abs(psi - ref)) < 1e-12
+
+
+def test_block_plan_does_not_depend_on_host_threads(dump_exe, tmp_path):
+    # the blocks' products run on host threads (QS_HOST_THREADS caps them): the plan of
+    # the 30-qubit layered circuit (100 blocks) is byte for byte the same on one
+    # thread as on eight
+    import paper_2008_13490_gb300 as qs
+    gin = tmp_path / "g.bin"
+    qs.gates_array(W.layered_haar_cz(30, 40, seed=2001)).tofile(gin)
+    outs = []
+    for threads in ("1", "8"):
+        bout = tmp_path / f"b{threads}.bin"
+        env = dict(os.environ, QS_HOST_THREADS=threads)
+        subprocess.run([str(dump_exe), str(gin), "30", str(bout)], check=True, env=env)
+        outs.append(bout.read_bytes())
+    assert len(outs[0]) == 100 * (24 + 1024 * 16)
+    assert outs[0] == outs[1]
