@@ -142,7 +142,11 @@ void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp
     cd m[16];
     int dim = 0;
     gate_matrix(g, m, &dim);
-    FOp o{};
+    if (dim != 2 && g.kind == QS_SWAP && relabel) {
+      std::swap(cur[g.q[0]], cur[g.q[1]]);
+      continue;
+    }
+    FOp& o = out.emplace_back();   // built in place
     if (dim == 2) {
       int v = cur[g.q[0]];
       if (is_zero(m[1]) && is_zero(m[2])) {
@@ -156,11 +160,6 @@ void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp
         o.t = v;
         for (int k = 0; k < 4; ++k) o.m0[k] = m[k];
       }
-      out.push_back(o);
-      continue;
-    }
-    if (g.kind == QS_SWAP && relabel) {
-      std::swap(cur[g.q[0]], cur[g.q[1]]);
       continue;
     }
     int v0 = cur[g.q[0]], v1 = cur[g.q[1]];
@@ -203,7 +202,6 @@ void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp
         o.c = -1;
       }
     }
-    out.push_back(o);
   }
   vmap_out = cur;
   if (!fuse) return;
