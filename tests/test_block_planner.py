@@ -98,3 +98,28 @@ def test_block_plan_does_not_depend_on_host_threads(dump_exe, tmp_path):
         outs.append(bout.read_bytes())
     assert len(outs[0]) == 100 * (24 + 1024 * 16)
     assert outs[0] == outs[1]
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_random_circuits_blocks_reproduce_the_circuit(dump_exe, tmp_path, case):
+    # seed sweep over widths 6..12 and gate mixes (dense, diagonal-heavy, permutations
+    # and user matrices): the blocks applied in order give the oracle's state
+    n = 6 + (case * 5) % 7
+    mix = case % 3
+    if mix == 0:
+        ops = W.random_gate_mix(n, 250, seed=960 + case)
+    elif mix == 1:
+        ops = W.random_gate_mix(n, 250, seed=960 + case, two_q_fraction=0.7,
+                                names1=["RZ", "T", "S", "H", "U3"], names2=["CP", "CZ", "CNOT"])
+    else:
+        ops = W.random_gate_mix(n, 200, seed=960 + case, two_q_fraction=0.5,
+                                names2=["SWAP", "MAT2", "CNOT"])
+    blocks = _blocks(dump_exe, tmp_path, n, ops)
+    psi0 = W.random_state(n, W.rng(980 + case))
+    ref = SV.apply_circuit(psi0.copy(), n, ops)
+    psi = psi0.copy()
+    for q, unitary, U in blocks:
+        assert sorted(q) == q and len(set(q)) == 5 and max(q) < n
+        assert unitary == 1
+        psi = _apply_block(psi, n, q, U)
+    assert np.max(np.abs(psi - ref)) < 1e-12

@@ -411,3 +411,33 @@ def test_tile_pass_images_reproduce_the_circuit(image_exe, tmp_path, name):
     ref = SV.apply_circuit(psi0.copy(), n, ops)
     out = _execute_images(img, n, psi0.copy())
     assert np.max(np.abs(out - ref)) < 1e-12
+
+
+# Seed sweep: random circuits of several widths and gate mixes through the plan
+# and through the kernel images (the fixed cases above pin the named structures;
+# these reach other tile sets, stage splits and controlled-phase run layouts)
+SWEEP = [(12, "phases"), (13, "mix"), (14, "swaps"), (15, "phases"), (16, "mix"), (13, "phases"),
+         (14, "mix"), (12, "swaps"), (16, "phases"), (15, "swaps")]
+
+
+def _sweep_ops(n, kind, seed):
+    if kind == "phases":
+        return W.random_gate_mix(n, 400, seed=seed, two_q_fraction=0.8,
+                                 names1=["H", "RZ", "T", "RK", "U1"], names2=["CP", "CZ"])
+    if kind == "swaps":
+        return W.random_gate_mix(n, 250, seed=seed, two_q_fraction=0.5,
+                                 names2=["SWAP", "CP", "CNOT", "MAT2"])
+    return W.random_gate_mix(n, 300, seed=seed)
+
+
+@pytest.mark.parametrize("case", range(len(SWEEP)))
+def test_random_circuits_through_plan_and_images(dump_exe, image_exe, tmp_path, case):
+    n, kind = SWEEP[case]
+    ops = _sweep_ops(n, kind, 900 + case)
+    psi0 = W.random_state(n, W.rng(950 + case))
+    ref = SV.apply_circuit(psi0.copy(), n, ops)
+    for fuse, relabel in ((True, True), (True, False), (False, False)):
+        plan = _plan(dump_exe, tmp_path, n, ops, fuse, relabel)
+        assert np.max(np.abs(_execute(plan, n, psi0.copy()) - ref)) < 1e-12, (fuse, relabel)
+        img = _images(image_exe, tmp_path, n, ops, fuse, relabel)
+        assert np.max(np.abs(_execute_images(img, n, psi0.copy()) - ref)) < 1e-12, (fuse, relabel)
