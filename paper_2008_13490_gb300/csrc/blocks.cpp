@@ -125,6 +125,24 @@ uint64_t grown_set(const std::vector<uint64_t>& rem_m, size_t start, int n) {
   return S;
 }
 
+// The distinct candidate sets of one block, in first-seen order: a set of nonzero
+// qubit masks (at most kSeeds + 60 of them) by open addressing in 256 slots
+// (multiplicative hashing), cleared per block.
+struct MaskSet {
+  uint64_t slot[256];
+  MaskSet() { clear(); }
+  void clear() { std::memset(slot, 0, sizeof(slot)); }
+  bool insert(uint64_t m) {   // true if m was not in the set yet
+    unsigned h = (unsigned)((m * 0x9E3779B97F4A7C15ull) >> 56);
+    while (slot[h]) {
+      if (slot[h] == m) return false;
+      h = (h + 1) & 255;
+    }
+    slot[h] = m;
+    return true;
+  }
+};
+
 // U of block b: the product of its gates, in circuit order
 void block_product(const qs_gate* gates, Block& b) {
   b.U.assign(32 * 32, cd(0));
@@ -161,15 +179,17 @@ void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>&
     rem_m[i] = gate_mask(gates[i]);
   }
   std::vector<uint64_t> cands;
+  MaskSet seen;
   while (!remaining.empty()) {
     cands.clear();
+    seen.clear();
     for (int k = 0; k < kSeeds && k < (int)remaining.size(); ++k) {
       const uint64_t S = grown_set(rem_m, (size_t)k, n);
-      if (std::find(cands.begin(), cands.end(), S) == cands.end()) cands.push_back(S);
+      if (seen.insert(S)) cands.push_back(S);
     }
     for (int a = 0; a + 5 <= n; ++a) {
       const uint64_t S = 31ull << a;
-      if (std::find(cands.begin(), cands.end(), S) == cands.end()) cands.push_back(S);
+      if (seen.insert(S)) cands.push_back(S);
     }
     uint64_t best = cands[0];
     int best_cnt = -1;
