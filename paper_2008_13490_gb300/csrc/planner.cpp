@@ -123,12 +123,6 @@ bool fold_into(const FOp& D, FOp& G, bool after) {
   return false;
 }
 
-// Does op X commute with diagonal op D?  (shared qubits must all be diagonal in X)
-bool commutes_with_diag(const FOp& X, const FOp& D) {
-  uint64_t dq = d_mask(D);
-  return (nd_mask(X) & dq) == 0;
-}
-
 }  // namespace
 
 void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp>& out,
@@ -246,30 +240,38 @@ void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp
     out.resize(w);
   }
 
-  // (2) fold diagonal ops into a neighbouring non-diagonal one-qubit op
-  {
+  // (2) fold diagonal ops into a neighbouring non-diagonal one-qubit op: the
+  // nearest op in each direction that does not commute with D (one acting
+  // non-diagonally on a qubit of D) is the only candidate.  The scans read the
+  // ops' non-diagonal qubit masks, which folding leaves unchanged.
+  bool any_diag = false;
+  for (const FOp& o : out) any_diag = any_diag || o.type == F_D;
+  if (any_diag) {
     std::vector<char> dead(out.size(), 0);
+    // per qubit, in increasing order, the ops acting non-diagonally on it (diagonal
+    // ops, folded or not, are in none of the lists)
+    std::vector<std::vector<int>> on(n);
+    for (size_t i = 0; i < out.size(); ++i) {
+      const uint64_t m = nd_mask(out[i]);
+      for (int q = 0; q < n; ++q)
+        if ((m >> q) & 1) on[q].push_back((int)i);
+    }
     for (size_t i = 0; i < out.size(); ++i) {
       if (out[i].type != F_D) continue;
       const FOp D = out[i];
-      uint64_t dq = d_mask(D);
-      bool done = false;
-      for (size_t j = i + 1; j < out.size() && !done; ++j) {      // forward
-        if (dead[j]) continue;
-        FOp& X = out[j];
-        if (((nd_mask(X) | d_mask(X)) & dq) == 0) continue;
-        if (commutes_with_diag(X, D)) continue;
-        done = fold_into(D, X, /*after=*/false);
-        break;
+      const int qa = D.a, qb = D.b;
+      // the nearest ops after and before D on D's qubits
+      int after = -1, before = -1;
+      for (int q : {qa, qb}) {
+        if (q < 0) continue;
+        const std::vector<int>& L = on[q];
+        auto it = std::upper_bound(L.begin(), L.end(), (int)i);
+        if (it != L.end() && (after < 0 || *it < after)) after = *it;
+        auto jt = std::lower_bound(L.begin(), L.end(), (int)i);
+        if (jt != L.begin() && *(jt - 1) > before) before = *(jt - 1);
       }
-      for (size_t j = i; j-- > 0 && !done;) {                      // backward
-        if (dead[j]) continue;
-        FOp& X = out[j];
-        if (((nd_mask(X) | d_mask(X)) & dq) == 0) continue;
-        if (commutes_with_diag(X, D)) continue;
-        done = fold_into(D, X, /*after=*/true);
-        break;
-      }
+      bool done = after >= 0 && fold_into(D, out[(size_t)after], /*after=*/false);
+      if (!done && before >= 0) done = fold_into(D, out[(size_t)before], /*after=*/true);
       if (done) dead[i] = 1;
     }
     size_t w = 0;
