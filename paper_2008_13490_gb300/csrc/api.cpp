@@ -948,6 +948,7 @@ void release_copies(State* st) {
 qs_status copies_for(State* st, size_t half, HostCopies** out) {
   HostCopies* hc = find_copies(st);
   if (hc && hc->half < half) {   // buffers too small (an fp64 call after fp32 ones): start over
+    cudaStreamSynchronize(st->stream);   // no kernel of the state may still write them
     release_copies(st);
     hc = nullptr;
   }
