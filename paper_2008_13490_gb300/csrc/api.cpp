@@ -9,6 +9,7 @@
 #include <unordered_map>
 #include <utility>
 
+#include "abi_guard.h"
 #include "host_par.h"
 #include "internal.h"
 #include "tile_cp.h"
@@ -998,396 +999,428 @@ const char* qs_last_error(void) { return g_err.c_str(); }
 const char* qs_version(void) { return "qsim-gb300 0.5 (sm_103a)"; }
 
 qs_status sv_create(int n, int prec, const qs_allocator* alloc, void* stream, qs_state_t* out) {
-  if (!out) {
-    set_error("out is NULL");
-    return QS_EINVAL;
-  }
-  *out = nullptr;
-  if (n < 1 || n > 36) {
-    set_error("n = %d outside [1, 36]", n);
-    return QS_EINVAL;
-  }
-  if (prec != QS_C64 && prec != QS_C128) {
-    set_error("bad precision %d", prec);
-    return QS_EINVAL;
-  }
-  qs_state_s* st = new (std::nothrow) qs_state_s();
-  if (!st) return QS_ENOMEM;
-  st->n = n;
-  st->prec = prec;
-  st->amp_bytes = prec == QS_C64 ? 8 : 16;
-  st->stream = (cudaStream_t)stream;
-  if (alloc && alloc->alloc && alloc->free) {
-    st->alloc = *alloc;
-    st->has_alloc = true;
-  }
-  cudaGetDevice(&st->device);
-  st->data_bytes = st->amp_bytes << n;
-  st->data = dev_alloc(st, st->data_bytes);
-  if (!st->data) {
-    set_error("device allocation of %zu bytes for a %d-qubit state failed", st->data_bytes, n);
-    delete st;
-    return QS_ENOMEM;
-  }
-  st->scratch_bytes = kScratchBytes;
-  st->scratch = dev_alloc(st, st->scratch_bytes);
-  if (!st->scratch) {
-    dev_free(st, st->data, st->data_bytes);
-    set_error("scratch allocation failed");
-    delete st;
-    return QS_ENOMEM;
-  }
-  if (cudaEventCreateWithFlags(&st->upload_done, cudaEventDisableTiming) != cudaSuccess) {
-    dev_free(st, st->scratch, st->scratch_bytes);
-    dev_free(st, st->data, st->data_bytes);
-    qs_status s = cuda_status(cudaGetLastError(), "cudaEventCreate");
-    delete st;
-    return s;
-  }
-  qs_status s = launch_set_basis(st, 0);
-  if (s != QS_OK) {
-    sv_destroy(st);
-    return s;
-  }
-  *out = st;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!out) {
+      set_error("out is NULL");
+      return QS_EINVAL;
+    }
+    *out = nullptr;
+    if (n < 1 || n > 36) {
+      set_error("n = %d outside [1, 36]", n);
+      return QS_EINVAL;
+    }
+    if (prec != QS_C64 && prec != QS_C128) {
+      set_error("bad precision %d", prec);
+      return QS_EINVAL;
+    }
+    qs_state_s* st = new (std::nothrow) qs_state_s();
+    if (!st) return QS_ENOMEM;
+    st->n = n;
+    st->prec = prec;
+    st->amp_bytes = prec == QS_C64 ? 8 : 16;
+    st->stream = (cudaStream_t)stream;
+    if (alloc && alloc->alloc && alloc->free) {
+      st->alloc = *alloc;
+      st->has_alloc = true;
+    }
+    cudaGetDevice(&st->device);
+    st->data_bytes = st->amp_bytes << n;
+    st->data = dev_alloc(st, st->data_bytes);
+    if (!st->data) {
+      set_error("device allocation of %zu bytes for a %d-qubit state failed", st->data_bytes, n);
+      delete st;
+      return QS_ENOMEM;
+    }
+    st->scratch_bytes = kScratchBytes;
+    st->scratch = dev_alloc(st, st->scratch_bytes);
+    if (!st->scratch) {
+      dev_free(st, st->data, st->data_bytes);
+      set_error("scratch allocation failed");
+      delete st;
+      return QS_ENOMEM;
+    }
+    if (cudaEventCreateWithFlags(&st->upload_done, cudaEventDisableTiming) != cudaSuccess) {
+      dev_free(st, st->scratch, st->scratch_bytes);
+      dev_free(st, st->data, st->data_bytes);
+      qs_status s = cuda_status(cudaGetLastError(), "cudaEventCreate");
+      delete st;
+      return s;
+    }
+    qs_status s = launch_set_basis(st, 0);
+    if (s != QS_OK) {
+      sv_destroy(st);
+      return s;
+    }
+    *out = st;
+    return QS_OK;
+  });
 }
 
 qs_status sv_wrap(int n, int prec, void* device_buf, const qs_allocator* alloc, void* stream, qs_state_t* out) {
-  if (!out || !device_buf) {
-    set_error("out and device_buf are required");
-    return QS_EINVAL;
-  }
-  *out = nullptr;
-  if (n < 1 || n > 36 || (prec != QS_C64 && prec != QS_C128)) {
-    set_error("n = %d outside [1, 36] or bad precision %d", n, prec);
-    return QS_EINVAL;
-  }
-  if ((uintptr_t)device_buf & 15) {
-    set_error("device_buf must be 16-byte aligned");
-    return QS_EINVAL;
-  }
-  qs_state_s* st = new (std::nothrow) qs_state_s();
-  if (!st) return QS_ENOMEM;
-  st->n = n;
-  st->prec = prec;
-  st->amp_bytes = prec == QS_C64 ? 8 : 16;
-  st->stream = (cudaStream_t)stream;
-  if (alloc && alloc->alloc && alloc->free) {
-    st->alloc = *alloc;
-    st->has_alloc = true;
-  }
-  cudaGetDevice(&st->device);
-  st->data_bytes = st->amp_bytes << n;
-  st->data = device_buf;
-  st->owns_data = false;
-  st->scratch_bytes = kScratchBytes;
-  st->scratch = dev_alloc(st, st->scratch_bytes);
-  if (!st->scratch) {
-    set_error("scratch allocation failed");
-    delete st;
-    return QS_ENOMEM;
-  }
-  if (cudaEventCreateWithFlags(&st->upload_done, cudaEventDisableTiming) != cudaSuccess) {
-    dev_free(st, st->scratch, st->scratch_bytes);
-    qs_status s = cuda_status(cudaGetLastError(), "cudaEventCreate");
-    delete st;
-    return s;
-  }
-  *out = st;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!out || !device_buf) {
+      set_error("out and device_buf are required");
+      return QS_EINVAL;
+    }
+    *out = nullptr;
+    if (n < 1 || n > 36 || (prec != QS_C64 && prec != QS_C128)) {
+      set_error("n = %d outside [1, 36] or bad precision %d", n, prec);
+      return QS_EINVAL;
+    }
+    if ((uintptr_t)device_buf & 15) {
+      set_error("device_buf must be 16-byte aligned");
+      return QS_EINVAL;
+    }
+    qs_state_s* st = new (std::nothrow) qs_state_s();
+    if (!st) return QS_ENOMEM;
+    st->n = n;
+    st->prec = prec;
+    st->amp_bytes = prec == QS_C64 ? 8 : 16;
+    st->stream = (cudaStream_t)stream;
+    if (alloc && alloc->alloc && alloc->free) {
+      st->alloc = *alloc;
+      st->has_alloc = true;
+    }
+    cudaGetDevice(&st->device);
+    st->data_bytes = st->amp_bytes << n;
+    st->data = device_buf;
+    st->owns_data = false;
+    st->scratch_bytes = kScratchBytes;
+    st->scratch = dev_alloc(st, st->scratch_bytes);
+    if (!st->scratch) {
+      set_error("scratch allocation failed");
+      delete st;
+      return QS_ENOMEM;
+    }
+    if (cudaEventCreateWithFlags(&st->upload_done, cudaEventDisableTiming) != cudaSuccess) {
+      dev_free(st, st->scratch, st->scratch_bytes);
+      qs_status s = cuda_status(cudaGetLastError(), "cudaEventCreate");
+      delete st;
+      return s;
+    }
+    *out = st;
+    return QS_OK;
+  });
 }
 
 qs_status sv_destroy(qs_state_t st) {
-  if (!st) return QS_OK;
-  cudaStreamSynchronize(st->stream);
-  release_copies(st);
-  dev_free(st, st->opbuf, st->opbuf_bytes);
-  if (st->stage) dev_free(st, st->stage, st->stage_bytes);
-  dev_free(st, st->scratch, st->scratch_bytes);
-  if (st->owns_data) dev_free(st, st->data, st->data_bytes);
-  if (st->hostbuf) cudaFreeHost(st->hostbuf);
-  if (st->upload_done) cudaEventDestroy(st->upload_done);
-  delete st;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!st) return QS_OK;
+    cudaStreamSynchronize(st->stream);
+    release_copies(st);
+    dev_free(st, st->opbuf, st->opbuf_bytes);
+    if (st->stage) dev_free(st, st->stage, st->stage_bytes);
+    dev_free(st, st->scratch, st->scratch_bytes);
+    if (st->owns_data) dev_free(st, st->data, st->data_bytes);
+    if (st->hostbuf) cudaFreeHost(st->hostbuf);
+    if (st->upload_done) cudaEventDestroy(st->upload_done);
+    delete st;
+    return QS_OK;
+  });
 }
 
 qs_status sv_set_stream(qs_state_t st, void* stream) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  QS_CUDA(cudaStreamSynchronize(st->stream));
-  st->stream = (cudaStream_t)stream;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    st->stream = (cudaStream_t)stream;
+    return QS_OK;
+  });
 }
 
 qs_status sv_info(qs_state_t st, int* n, int* prec, void** device_ptr) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  if (n) *n = st->n;
-  if (prec) *prec = st->prec;
-  if (device_ptr) *device_ptr = st->data;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    if (n) *n = st->n;
+    if (prec) *prec = st->prec;
+    if (device_ptr) *device_ptr = st->data;
+    return QS_OK;
+  });
 }
 
 qs_status sv_set_basis(qs_state_t st, uint64_t J) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  if (J >> st->n) {
-    set_error("basis index %llu out of range for n = %d", (unsigned long long)J, st->n);
-    return QS_EINVAL;
-  }
-  return launch_set_basis(st, J);
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    if (J >> st->n) {
+      set_error("basis index %llu out of range for n = %d", (unsigned long long)J, st->n);
+      return QS_EINVAL;
+    }
+    return launch_set_basis(st, J);
+  });
 }
 
 qs_status sv_copy_in(qs_state_t st, const void* buf, int on_device) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  if (!buf) {
-    set_error("buf is NULL");
-    return QS_EINVAL;
-  }
-  if (on_device) {
-    QS_CUDA(cudaMemcpyAsync(st->data, buf, st->data_bytes, cudaMemcpyDeviceToDevice, st->stream));
-  } else {
-    QS_CUDA(cudaMemcpyAsync(st->data, buf, st->data_bytes, cudaMemcpyHostToDevice, st->stream));
-    QS_CUDA(cudaStreamSynchronize(st->stream));
-  }
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    if (!buf) {
+      set_error("buf is NULL");
+      return QS_EINVAL;
+    }
+    if (on_device) {
+      QS_CUDA(cudaMemcpyAsync(st->data, buf, st->data_bytes, cudaMemcpyDeviceToDevice, st->stream));
+    } else {
+      QS_CUDA(cudaMemcpyAsync(st->data, buf, st->data_bytes, cudaMemcpyHostToDevice, st->stream));
+      QS_CUDA(cudaStreamSynchronize(st->stream));
+    }
+    return QS_OK;
+  });
 }
 
 qs_status sv_copy_out(qs_state_t st, void* buf, int on_device) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  if (!buf) {
-    set_error("buf is NULL");
-    return QS_EINVAL;
-  }
-  if (on_device) {
-    QS_CUDA(cudaMemcpyAsync(buf, st->data, st->data_bytes, cudaMemcpyDeviceToDevice, st->stream));
-  } else {
-    QS_CUDA(cudaMemcpyAsync(buf, st->data, st->data_bytes, cudaMemcpyDeviceToHost, st->stream));
-    QS_CUDA(cudaStreamSynchronize(st->stream));
-  }
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    if (!buf) {
+      set_error("buf is NULL");
+      return QS_EINVAL;
+    }
+    if (on_device) {
+      QS_CUDA(cudaMemcpyAsync(buf, st->data, st->data_bytes, cudaMemcpyDeviceToDevice, st->stream));
+    } else {
+      QS_CUDA(cudaMemcpyAsync(buf, st->data, st->data_bytes, cudaMemcpyDeviceToHost, st->stream));
+      QS_CUDA(cudaStreamSynchronize(st->stream));
+    }
+    return QS_OK;
+  });
 }
 
 qs_status sv_apply_circuit(qs_state_t st, const qs_gate* gates, size_t ngates, const qs_opts* opts,
                            qs_stats* stats) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  s = validate_gates(gates, ngates, st->n);
-  if (s != QS_OK) return s;
-  return apply_gates(st, gates, ngates, opts ? opts->method : QS_METHOD_AUTO, stats,
-                     opts ? opts->flags : 0);
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    s = validate_gates(gates, ngates, st->n);
+    if (s != QS_OK) return s;
+    return apply_gates(st, gates, ngates, opts ? opts->method : QS_METHOD_AUTO, stats,
+                       opts ? opts->flags : 0);
+  });
 }
 
 qs_status sv_probs(qs_state_t st, void* out, int out_fp64, uint64_t marg_mask, double* norm_out) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  if (marg_mask >> st->n) {
-    set_error("marginal mask has bits beyond n = %d", st->n);
-    return QS_EINVAL;
-  }
-  int k = __builtin_popcountll(marg_mask);
-  const bool marginal = marg_mask != 0 && k != st->n;
-  if (marginal && k > kScratchMargLog2) {
-    set_error("marginal over %d qubits exceeds the %d-qubit scratch limit", k, kScratchMargLog2);
-    return QS_EUNSUPPORTED;
-  }
-  if (!marginal && out && !out_fp64 && st->prec == QS_C64 && ((uintptr_t)out & 7)) {
-    set_error("float output buffer must be 8-byte aligned");
-    return QS_EINVAL;
-  }
-  unsigned char* sc = (unsigned char*)st->scratch;
-  double* partials = (double*)(sc + kScratchPartials);
-  s = launch_probs(st, out, out_fp64, marginal ? marg_mask : 0, partials,
-                   (uint8_t*)(sc + kScratchBits), (double*)(sc + kScratchMarg));
-  if (s != QS_OK) return s;
-  if (norm_out) {
-    double* res = (double*)(sc + kScratchResult);
-    s = launch_reduce_partials(st, partials, kReduceBlocks, res);
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
     if (s != QS_OK) return s;
-    QS_CUDA(cudaMemcpyAsync(norm_out, res, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
-    QS_CUDA(cudaStreamSynchronize(st->stream));
-  }
-  return QS_OK;
-}
-
-qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t marg_mask, double* norm_out) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  if (!host_out) {
-    set_error("host_out is required");
-    return QS_EINVAL;
-  }
-  if (marg_mask >> st->n) {
-    set_error("marginal mask has bits beyond n = %d", st->n);
-    return QS_EINVAL;
-  }
-  s = wait_copies(st);
-  if (s != QS_OK) return s;
-  const int k = __builtin_popcountll(marg_mask);
-  unsigned char* sc = (unsigned char*)st->scratch;
-  double* partials = (double*)(sc + kScratchPartials);
-  if (marg_mask != 0 && k != st->n) {
-    // a marginal (at most 2^16 values) stays in the scratch accumulators as doubles
-    if (k > kScratchMargLog2) {
+    if (marg_mask >> st->n) {
+      set_error("marginal mask has bits beyond n = %d", st->n);
+      return QS_EINVAL;
+    }
+    int k = __builtin_popcountll(marg_mask);
+    const bool marginal = marg_mask != 0 && k != st->n;
+    if (marginal && k > kScratchMargLog2) {
       set_error("marginal over %d qubits exceeds the %d-qubit scratch limit", k, kScratchMargLog2);
       return QS_EUNSUPPORTED;
     }
-    s = sv_probs(st, nullptr, 1, marg_mask, norm_out);
+    if (!marginal && out && !out_fp64 && st->prec == QS_C64 && ((uintptr_t)out & 7)) {
+      set_error("float output buffer must be 8-byte aligned");
+      return QS_EINVAL;
+    }
+    unsigned char* sc = (unsigned char*)st->scratch;
+    double* partials = (double*)(sc + kScratchPartials);
+    s = launch_probs(st, out, out_fp64, marginal ? marg_mask : 0, partials,
+                     (uint8_t*)(sc + kScratchBits), (double*)(sc + kScratchMarg));
     if (s != QS_OK) return s;
-    std::vector<double> h((size_t)1 << k);
-    QS_CUDA(cudaMemcpyAsync(h.data(), sc + kScratchMarg, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                            st->stream));
-    QS_CUDA(cudaStreamSynchronize(st->stream));
-    if (out_fp64) std::memcpy(host_out, h.data(), h.size() * sizeof(double));
-    else
-      for (size_t i = 0; i < h.size(); ++i) ((float*)host_out)[i] = (float)h[i];
+    if (norm_out) {
+      double* res = (double*)(sc + kScratchResult);
+      s = launch_reduce_partials(st, partials, kReduceBlocks, res);
+      if (s != QS_OK) return s;
+      QS_CUDA(cudaMemcpyAsync(norm_out, res, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+      QS_CUDA(cudaStreamSynchronize(st->stream));
+    }
     return QS_OK;
-  }
-  const size_t es = out_fp64 ? sizeof(double) : sizeof(float);
-  const uint64_t N = 1ull << st->n;
-  {
-    // a page-locked host buffer the device can address: the kernel writes the
-    // probabilities into it directly (one launch, no staging copies; 4 GiB in 22.2 ms
-    // against 24.9 ms through the copy engine on GB300)
-    cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, host_out) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
-      s = launch_probs_range(st, 0, N, pa.devicePointer, out_fp64, partials);
-      if (s == QS_OK && norm_out) s = sv_probs(st, nullptr, out_fp64, 0, norm_out);
-      const cudaError_t e = cudaStreamSynchronize(st->stream);
-      if (s == QS_OK && e != cudaSuccess) s = cuda_status(e, "sv_probs_host");
-      return s;
+  });
+}
+
+qs_status sv_probs_host(qs_state_t st, void* host_out, int out_fp64, uint64_t marg_mask, double* norm_out) {
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    if (!host_out) {
+      set_error("host_out is required");
+      return QS_EINVAL;
     }
-    cudaGetLastError();   // a plain host pointer: not an error
-  }
-  // otherwise formed chunk by chunk in a device staging buffer (kept by the state)
-  // and copied to the host buffer after each chunk
-  const uint64_t chunk = std::min<uint64_t>(N, (uint64_t)(kStageBytes / es));
-  if (!st->stage) {
-    st->stage = dev_alloc(st, kStageBytes);
+    if (marg_mask >> st->n) {
+      set_error("marginal mask has bits beyond n = %d", st->n);
+      return QS_EINVAL;
+    }
+    s = wait_copies(st);
+    if (s != QS_OK) return s;
+    const int k = __builtin_popcountll(marg_mask);
+    unsigned char* sc = (unsigned char*)st->scratch;
+    double* partials = (double*)(sc + kScratchPartials);
+    if (marg_mask != 0 && k != st->n) {
+      // a marginal (at most 2^16 values) stays in the scratch accumulators as doubles
+      if (k > kScratchMargLog2) {
+        set_error("marginal over %d qubits exceeds the %d-qubit scratch limit", k, kScratchMargLog2);
+        return QS_EUNSUPPORTED;
+      }
+      s = sv_probs(st, nullptr, 1, marg_mask, norm_out);
+      if (s != QS_OK) return s;
+      std::vector<double> h((size_t)1 << k);
+      QS_CUDA(cudaMemcpyAsync(h.data(), sc + kScratchMarg, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                              st->stream));
+      QS_CUDA(cudaStreamSynchronize(st->stream));
+      if (out_fp64) std::memcpy(host_out, h.data(), h.size() * sizeof(double));
+      else
+        for (size_t i = 0; i < h.size(); ++i) ((float*)host_out)[i] = (float)h[i];
+      return QS_OK;
+    }
+    const size_t es = out_fp64 ? sizeof(double) : sizeof(float);
+    const uint64_t N = 1ull << st->n;
+    {
+      // a page-locked host buffer the device can address: the kernel writes the
+      // probabilities into it directly (one launch, no staging copies; 4 GiB in 22.2 ms
+      // against 24.9 ms through the copy engine on GB300)
+      cudaPointerAttributes pa;
+      if (cudaPointerGetAttributes(&pa, host_out) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+        s = launch_probs_range(st, 0, N, pa.devicePointer, out_fp64, partials);
+        if (s == QS_OK && norm_out) s = sv_probs(st, nullptr, out_fp64, 0, norm_out);
+        const cudaError_t e = cudaStreamSynchronize(st->stream);
+        if (s == QS_OK && e != cudaSuccess) s = cuda_status(e, "sv_probs_host");
+        return s;
+      }
+      cudaGetLastError();   // a plain host pointer: not an error
+    }
+    // otherwise formed chunk by chunk in a device staging buffer (kept by the state)
+    // and copied to the host buffer after each chunk
+    const uint64_t chunk = std::min<uint64_t>(N, (uint64_t)(kStageBytes / es));
     if (!st->stage) {
-      set_error("staging buffer for the probabilities could not be allocated");
-      return QS_ENOMEM;
+      st->stage = dev_alloc(st, kStageBytes);
+      if (!st->stage) {
+        set_error("staging buffer for the probabilities could not be allocated");
+        return QS_ENOMEM;
+      }
+      st->stage_bytes = kStageBytes;
     }
-    st->stage_bytes = kStageBytes;
-  }
-  for (uint64_t off = 0; off < N && s == QS_OK; off += chunk) {
-    const uint64_t cnt = std::min<uint64_t>(chunk, N - off);
-    s = launch_probs_range(st, off, cnt, st->stage, out_fp64, partials);
-    if (s == QS_OK) {
-      const cudaError_t e = cudaMemcpyAsync((unsigned char*)host_out + off * es, st->stage, cnt * es,
-                                            cudaMemcpyDeviceToHost, st->stream);
-      if (e != cudaSuccess) s = cuda_status(e, "probabilities to the host");
+    for (uint64_t off = 0; off < N && s == QS_OK; off += chunk) {
+      const uint64_t cnt = std::min<uint64_t>(chunk, N - off);
+      s = launch_probs_range(st, off, cnt, st->stage, out_fp64, partials);
+      if (s == QS_OK) {
+        const cudaError_t e = cudaMemcpyAsync((unsigned char*)host_out + off * es, st->stage, cnt * es,
+                                              cudaMemcpyDeviceToHost, st->stream);
+        if (e != cudaSuccess) s = cuda_status(e, "probabilities to the host");
+      }
     }
-  }
-  if (s == QS_OK && norm_out) s = sv_probs(st, nullptr, out_fp64, 0, norm_out);
-  const cudaError_t e = cudaStreamSynchronize(st->stream);
-  if (s == QS_OK && e != cudaSuccess) s = cuda_status(e, "sv_probs_host");
-  return s;
+    if (s == QS_OK && norm_out) s = sv_probs(st, nullptr, out_fp64, 0, norm_out);
+    const cudaError_t e = cudaStreamSynchronize(st->stream);
+    if (s == QS_OK && e != cudaSuccess) s = cuda_status(e, "sv_probs_host");
+    return s;
+  });
 }
 
 qs_status sv_probs_host_async(qs_state_t st, void* host_out, int out_fp64) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  if (!host_out) {
-    set_error("host_out is required");
-    return QS_EINVAL;
-  }
-  const uint64_t N = 1ull << st->n;
-  const size_t bytes = (size_t)N * (out_fp64 ? sizeof(double) : sizeof(float));
-  HostCopies* hc = nullptr;
-  s = copies_for(st, bytes, &hc);
-  if (s != QS_OK) return s;
-  const int k = hc->next;
-  unsigned char* dst = (unsigned char*)hc->buf + (size_t)k * hc->half;
-  // the buffer's earlier copy has to end before the buffer is rewritten
-  if (hc->queued[k]) QS_CUDA(cudaStreamWaitEvent(st->stream, hc->copied[k], 0));
-  double* partials = (double*)((unsigned char*)st->scratch + kScratchPartials);
-  s = launch_probs_range(st, 0, N, dst, out_fp64, partials);
-  if (s != QS_OK) return s;
-  QS_CUDA(cudaEventRecord(hc->formed[k], st->stream));
-  QS_CUDA(cudaStreamWaitEvent(hc->cs, hc->formed[k], 0));
-  QS_CUDA(cudaMemcpyAsync(host_out, dst, bytes, cudaMemcpyDeviceToHost, hc->cs));
-  QS_CUDA(cudaEventRecord(hc->copied[k], hc->cs));
-  hc->queued[k] = true;
-  hc->next = k ^ 1;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    if (!host_out) {
+      set_error("host_out is required");
+      return QS_EINVAL;
+    }
+    const uint64_t N = 1ull << st->n;
+    const size_t bytes = (size_t)N * (out_fp64 ? sizeof(double) : sizeof(float));
+    HostCopies* hc = nullptr;
+    s = copies_for(st, bytes, &hc);
+    if (s != QS_OK) return s;
+    const int k = hc->next;
+    unsigned char* dst = (unsigned char*)hc->buf + (size_t)k * hc->half;
+    // the buffer's earlier copy has to end before the buffer is rewritten
+    if (hc->queued[k]) QS_CUDA(cudaStreamWaitEvent(st->stream, hc->copied[k], 0));
+    double* partials = (double*)((unsigned char*)st->scratch + kScratchPartials);
+    s = launch_probs_range(st, 0, N, dst, out_fp64, partials);
+    if (s != QS_OK) return s;
+    QS_CUDA(cudaEventRecord(hc->formed[k], st->stream));
+    QS_CUDA(cudaStreamWaitEvent(hc->cs, hc->formed[k], 0));
+    QS_CUDA(cudaMemcpyAsync(host_out, dst, bytes, cudaMemcpyDeviceToHost, hc->cs));
+    QS_CUDA(cudaEventRecord(hc->copied[k], hc->cs));
+    hc->queued[k] = true;
+    hc->next = k ^ 1;
+    return QS_OK;
+  });
 }
 
 qs_status sv_probs_wait(qs_state_t st) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  return wait_copies(st);
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    return wait_copies(st);
+  });
 }
 
 qs_status sv_loglik(qs_state_t st, const uint32_t* counts, double* out, int64_t* clamped) {
-  qs_status s = check_state(st);
-  if (s != QS_OK) return s;
-  if (!counts || !out) {
-    set_error("counts and out are required");
-    return QS_EINVAL;
-  }
-  unsigned char* sc = (unsigned char*)st->scratch;
-  double* partials = (double*)(sc + kScratchPartials);
-  s = launch_loglik(st, counts, partials, (unsigned long long*)(sc + kScratchClamps));
-  if (s != QS_OK) return s;
-  double* res = (double*)(sc + kScratchResult);
-  s = launch_reduce_partials(st, partials, kReduceBlocks, res);
-  if (s != QS_OK) return s;
-  unsigned long long nc = 0;
-  QS_CUDA(cudaMemcpyAsync(out, res, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
-  QS_CUDA(cudaMemcpyAsync(&nc, sc + kScratchClamps, sizeof(nc), cudaMemcpyDeviceToHost, st->stream));
-  QS_CUDA(cudaStreamSynchronize(st->stream));
-  if (clamped) *clamped = (int64_t)nc;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    qs_status s = check_state(st);
+    if (s != QS_OK) return s;
+    if (!counts || !out) {
+      set_error("counts and out are required");
+      return QS_EINVAL;
+    }
+    unsigned char* sc = (unsigned char*)st->scratch;
+    double* partials = (double*)(sc + kScratchPartials);
+    s = launch_loglik(st, counts, partials, (unsigned long long*)(sc + kScratchClamps));
+    if (s != QS_OK) return s;
+    double* res = (double*)(sc + kScratchResult);
+    s = launch_reduce_partials(st, partials, kReduceBlocks, res);
+    if (s != QS_OK) return s;
+    unsigned long long nc = 0;
+    QS_CUDA(cudaMemcpyAsync(out, res, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+    QS_CUDA(cudaMemcpyAsync(&nc, sc + kScratchClamps, sizeof(nc), cudaMemcpyDeviceToHost, st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    if (clamped) *clamped = (int64_t)nc;
+    return QS_OK;
+  });
 }
 
 qs_status qs_profile_begin(void) {
-  ProfileSession& ps = profile();
-  std::lock_guard<std::mutex> g(ps.mu);
-  if (ps.active) {
-    set_error("a profiling session is already active");
-    return QS_EINVAL;
-  }
-  ps.ev.clear();
-  ps.kind.clear();
-  ps.active = true;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    ProfileSession& ps = profile();
+    std::lock_guard<std::mutex> g(ps.mu);
+    if (ps.active) {
+      set_error("a profiling session is already active");
+      return QS_EINVAL;
+    }
+    ps.ev.clear();
+    ps.kind.clear();
+    ps.active = true;
+    return QS_OK;
+  });
 }
 
 qs_status qs_profile_end(double* kernel_ms, int64_t* launches) {
-  ProfileSession& ps = profile();
-  std::lock_guard<std::mutex> g(ps.mu);
-  if (!ps.active) {
-    set_error("no active profiling session");
-    return QS_EINVAL;
-  }
-  ps.active = false;
-  double ms[5] = {0, 0, 0, 0, 0};
-  int64_t cnt[5] = {0, 0, 0, 0, 0};
-  qs_status s = QS_OK;
-  for (size_t i = 0; i < ps.kind.size(); ++i) {
-    cudaEvent_t a = ps.ev[2 * i], b = ps.ev[2 * i + 1];
-    if (a && b) {
-      cudaError_t e = cudaEventSynchronize(b);
-      float t = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
-      if (e != cudaSuccess && s == QS_OK) s = cuda_status(e, "profile events");
-      ms[ps.kind[i]] += t;
-      cnt[ps.kind[i]] += 1;
+  return abi_guard(__func__, [&]() -> qs_status {
+    ProfileSession& ps = profile();
+    std::lock_guard<std::mutex> g(ps.mu);
+    if (!ps.active) {
+      set_error("no active profiling session");
+      return QS_EINVAL;
     }
-    if (a) cudaEventDestroy(a);
-    if (b) cudaEventDestroy(b);
-  }
-  ps.ev.clear();
-  ps.kind.clear();
-  for (int k = 0; k < 5; ++k) {
-    if (kernel_ms) kernel_ms[k] = ms[k];
-    if (launches) launches[k] = cnt[k];
-  }
-  return s;
+    ps.active = false;
+    double ms[5] = {0, 0, 0, 0, 0};
+    int64_t cnt[5] = {0, 0, 0, 0, 0};
+    qs_status s = QS_OK;
+    for (size_t i = 0; i < ps.kind.size(); ++i) {
+      cudaEvent_t a = ps.ev[2 * i], b = ps.ev[2 * i + 1];
+      if (a && b) {
+        cudaError_t e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e != cudaSuccess && s == QS_OK) s = cuda_status(e, "profile events");
+        ms[ps.kind[i]] += t;
+        cnt[ps.kind[i]] += 1;
+      }
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+    ps.ev.clear();
+    ps.kind.clear();
+    for (int k = 0; k < 5; ++k) {
+      if (kernel_ms) kernel_ms[k] = ms[k];
+      if (launches) launches[k] = cnt[k];
+    }
+    return s;
+  });
 }
 
 }  // extern "C"

@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace qs {
@@ -113,115 +114,119 @@ struct File {
 using namespace qs;
 
 extern "C" qs_status sv_save(qs_state_t h, const char* path) {
-  State* st = h;
-  if (!st || !path) {
-    set_error("state and path are required");
-    return QS_EINVAL;
-  }
-  SvHeader hd;
-  std::memset(&hd, 0, sizeof(hd));
-  std::memcpy(hd.magic, kMagic, 8);
-  hd.n = (uint32_t)st->n;
-  hd.prec = (uint32_t)st->prec;
-  hd.bytes = st->data_bytes;
-  qs_status s = device_checksum(st, &hd.checksum);
-  if (s != QS_OK) return s;
-  Pinned pin;
-  s = pin.init();
-  if (s != QS_OK) return s;
-  File file;
-  file.f = std::fopen(path, "wb");
-  if (!file.f) {
-    set_error("cannot open %s for writing", path);
-    return QS_EINVAL;
-  }
-  if (std::fwrite(&hd, sizeof(hd), 1, file.f) != 1) {
-    set_error("write to %s failed", path);
-    return QS_EINVAL;
-  }
-  const unsigned char* src = (const unsigned char*)st->data;
-  const size_t total = st->data_bytes, nchunks = (total + kChunk - 1) / kChunk;
-  auto issue = [&](size_t c) -> qs_status {
-    const size_t off = c * kChunk, len = total - off < kChunk ? total - off : kChunk;
-    QS_CUDA(cudaMemcpyAsync(pin.buf[c & 1], src + off, len, cudaMemcpyDeviceToHost, st->stream));
-    QS_CUDA(cudaEventRecord(pin.ev[c & 1], st->stream));
-    return QS_OK;
-  };
-  if (nchunks) s = issue(0);
-  for (size_t c = 0; c < nchunks && s == QS_OK; ++c) {
-    if (c + 1 < nchunks) s = issue(c + 1);   // the next copy runs while this chunk is written
-    if (s != QS_OK) break;
-    QS_CUDA(cudaEventSynchronize(pin.ev[c & 1]));
-    const size_t off = c * kChunk, len = total - off < kChunk ? total - off : kChunk;
-    if (std::fwrite(pin.buf[c & 1], 1, len, file.f) != len) {
+  return abi_guard(__func__, [&]() -> qs_status {
+    State* st = h;
+    if (!st || !path) {
+      set_error("state and path are required");
+      return QS_EINVAL;
+    }
+    SvHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, kMagic, 8);
+    hd.n = (uint32_t)st->n;
+    hd.prec = (uint32_t)st->prec;
+    hd.bytes = st->data_bytes;
+    qs_status s = device_checksum(st, &hd.checksum);
+    if (s != QS_OK) return s;
+    Pinned pin;
+    s = pin.init();
+    if (s != QS_OK) return s;
+    File file;
+    file.f = std::fopen(path, "wb");
+    if (!file.f) {
+      set_error("cannot open %s for writing", path);
+      return QS_EINVAL;
+    }
+    if (std::fwrite(&hd, sizeof(hd), 1, file.f) != 1) {
+      set_error("write to %s failed", path);
+      return QS_EINVAL;
+    }
+    const unsigned char* src = (const unsigned char*)st->data;
+    const size_t total = st->data_bytes, nchunks = (total + kChunk - 1) / kChunk;
+    auto issue = [&](size_t c) -> qs_status {
+      const size_t off = c * kChunk, len = total - off < kChunk ? total - off : kChunk;
+      QS_CUDA(cudaMemcpyAsync(pin.buf[c & 1], src + off, len, cudaMemcpyDeviceToHost, st->stream));
+      QS_CUDA(cudaEventRecord(pin.ev[c & 1], st->stream));
+      return QS_OK;
+    };
+    if (nchunks) s = issue(0);
+    for (size_t c = 0; c < nchunks && s == QS_OK; ++c) {
+      if (c + 1 < nchunks) s = issue(c + 1);   // the next copy runs while this chunk is written
+      if (s != QS_OK) break;
+      QS_CUDA(cudaEventSynchronize(pin.ev[c & 1]));
+      const size_t off = c * kChunk, len = total - off < kChunk ? total - off : kChunk;
+      if (std::fwrite(pin.buf[c & 1], 1, len, file.f) != len) {
+        set_error("write to %s failed", path);
+        s = QS_EINVAL;
+      }
+    }
+    if (s == QS_OK && std::fflush(file.f) != 0) {
       set_error("write to %s failed", path);
       s = QS_EINVAL;
     }
-  }
-  if (s == QS_OK && std::fflush(file.f) != 0) {
-    set_error("write to %s failed", path);
-    s = QS_EINVAL;
-  }
-  // a late write error (full disk, network file system) shows up at close
-  const int closed = std::fclose(file.f);
-  file.f = nullptr;
-  if (s == QS_OK && closed != 0) {
-    set_error("closing %s failed: the checkpoint may be incomplete", path);
-    s = QS_EINVAL;
-  }
-  return s;
+    // a late write error (full disk, network file system) shows up at close
+    const int closed = std::fclose(file.f);
+    file.f = nullptr;
+    if (s == QS_OK && closed != 0) {
+      set_error("closing %s failed: the checkpoint may be incomplete", path);
+      s = QS_EINVAL;
+    }
+    return s;
+  });
 }
 
 extern "C" qs_status sv_load(qs_state_t h, const char* path) {
-  State* st = h;
-  if (!st || !path) {
-    set_error("state and path are required");
-    return QS_EINVAL;
-  }
-  File file;
-  file.f = std::fopen(path, "rb");
-  if (!file.f) {
-    set_error("cannot open %s", path);
-    return QS_EINVAL;
-  }
-  SvHeader hd;
-  if (std::fread(&hd, sizeof(hd), 1, file.f) != 1 || std::memcmp(hd.magic, kMagic, 8) != 0) {
-    set_error("%s is not a state checkpoint", path);
-    return QS_EINVAL;
-  }
-  if ((int)hd.n != st->n || (int)hd.prec != st->prec || hd.bytes != st->data_bytes) {
-    set_error("checkpoint holds n = %u, prec = %u; the state has n = %d, prec = %d", hd.n, hd.prec,
-              st->n, st->prec);
-    return QS_EINVAL;
-  }
-  Pinned pin;
-  qs_status s = pin.init();
-  if (s != QS_OK) return s;
-  unsigned char* dst = (unsigned char*)st->data;
-  const size_t total = st->data_bytes, nchunks = (total + kChunk - 1) / kChunk;
-  bool short_read = false;
-  for (size_t c = 0; c < nchunks && s == QS_OK; ++c) {
-    // the copy that last used this buffer (chunk c - 2) must have finished
-    if (c >= 2) QS_CUDA(cudaEventSynchronize(pin.ev[c & 1]));
-    const size_t off = c * kChunk, len = total - off < kChunk ? total - off : kChunk;
-    if (std::fread(pin.buf[c & 1], 1, len, file.f) != len) {
-      short_read = true;
-      break;
+  return abi_guard(__func__, [&]() -> qs_status {
+    State* st = h;
+    if (!st || !path) {
+      set_error("state and path are required");
+      return QS_EINVAL;
     }
-    QS_CUDA(cudaMemcpyAsync(dst + off, pin.buf[c & 1], len, cudaMemcpyHostToDevice, st->stream));
-    QS_CUDA(cudaEventRecord(pin.ev[c & 1], st->stream));
-  }
-  QS_CUDA(cudaStreamSynchronize(st->stream));
-  uint64_t sum = 0;
-  if (s == QS_OK && !short_read) s = device_checksum(st, &sum);
-  if (s == QS_OK && (short_read || sum != hd.checksum)) {
-    // a partly loaded state must not pass for the checkpoint
-    launch_set_basis(st, 0);
-    cudaStreamSynchronize(st->stream);
-    set_error(short_read ? "%s is truncated; the state was reset to |0...0>"
-                         : "checksum mismatch in %s; the state was reset to |0...0>",
-              path);
-    return QS_EINVAL;
-  }
-  return s;
+    File file;
+    file.f = std::fopen(path, "rb");
+    if (!file.f) {
+      set_error("cannot open %s", path);
+      return QS_EINVAL;
+    }
+    SvHeader hd;
+    if (std::fread(&hd, sizeof(hd), 1, file.f) != 1 || std::memcmp(hd.magic, kMagic, 8) != 0) {
+      set_error("%s is not a state checkpoint", path);
+      return QS_EINVAL;
+    }
+    if ((int)hd.n != st->n || (int)hd.prec != st->prec || hd.bytes != st->data_bytes) {
+      set_error("checkpoint holds n = %u, prec = %u; the state has n = %d, prec = %d", hd.n, hd.prec,
+                st->n, st->prec);
+      return QS_EINVAL;
+    }
+    Pinned pin;
+    qs_status s = pin.init();
+    if (s != QS_OK) return s;
+    unsigned char* dst = (unsigned char*)st->data;
+    const size_t total = st->data_bytes, nchunks = (total + kChunk - 1) / kChunk;
+    bool short_read = false;
+    for (size_t c = 0; c < nchunks && s == QS_OK; ++c) {
+      // the copy that last used this buffer (chunk c - 2) must have finished
+      if (c >= 2) QS_CUDA(cudaEventSynchronize(pin.ev[c & 1]));
+      const size_t off = c * kChunk, len = total - off < kChunk ? total - off : kChunk;
+      if (std::fread(pin.buf[c & 1], 1, len, file.f) != len) {
+        short_read = true;
+        break;
+      }
+      QS_CUDA(cudaMemcpyAsync(dst + off, pin.buf[c & 1], len, cudaMemcpyHostToDevice, st->stream));
+      QS_CUDA(cudaEventRecord(pin.ev[c & 1], st->stream));
+    }
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    uint64_t sum = 0;
+    if (s == QS_OK && !short_read) s = device_checksum(st, &sum);
+    if (s == QS_OK && (short_read || sum != hd.checksum)) {
+      // a partly loaded state must not pass for the checkpoint
+      launch_set_basis(st, 0);
+      cudaStreamSynchronize(st->stream);
+      set_error(short_read ? "%s is truncated; the state was reset to |0...0>"
+                           : "checksum mismatch in %s; the state was reset to |0...0>",
+                path);
+      return QS_EINVAL;
+    }
+    return s;
+  });
 }

@@ -9,6 +9,7 @@
 // thread per circuit, FP64 sums.
 #include <cuda_runtime.h>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace qs {
@@ -53,13 +54,15 @@ using namespace qs;
 
 extern "C" qs_status dm_code422_eval(int count, const float* enc, const float* bare, const float* ideal,
                                      float* p_enc, float* ratio, float* d_bare, float* d_enc, void* stream) {
-  if (count < 0 || (count > 0 && (!enc || !bare || !ideal || !p_enc || !ratio || !d_bare || !d_enc))) {
-    set_error("dm_code422_eval: count < 0 or an array is NULL");
-    return QS_EINVAL;
-  }
-  if (count == 0) return QS_OK;
-  code422_eval_kernel<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(count, enc, bare, ideal, p_enc,
-                                                                             ratio, d_bare, d_enc);
-  QS_CUDA(cudaGetLastError());
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (count < 0 || (count > 0 && (!enc || !bare || !ideal || !p_enc || !ratio || !d_bare || !d_enc))) {
+      set_error("dm_code422_eval: count < 0 or an array is NULL");
+      return QS_EINVAL;
+    }
+    if (count == 0) return QS_OK;
+    code422_eval_kernel<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(count, enc, bare, ideal, p_enc,
+                                                                               ratio, d_bare, d_enc);
+    QS_CUDA(cudaGetLastError());
+    return QS_OK;
+  });
 }

@@ -30,6 +30,7 @@
 #include <cmath>
 #include <vector>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace qs {
@@ -1332,105 +1333,107 @@ using namespace qs;
 
 extern "C" qs_status dm_apply_channels(const qs_dm_batch* b, float* probs, double* loglik,
                                        double* grad, void* stream_) {
-  if (!b) {
-    set_error("batch is NULL");
-    return QS_EINVAL;
-  }
-  if (b->n_circuits < 0 || b->max_qubits < 1 || b->max_qubits > kDmMaxQ || b->max_ops < 0) {
-    set_error("bad batch sizes (n_circuits %d, max_qubits %d, max_ops %d)", b->n_circuits,
-              b->max_qubits, b->max_ops);
-    return QS_EINVAL;
-  }
-  if (!b->nq || !b->op_off || !b->params || !b->out_off || (b->max_ops > 0 && !b->ops)) {
-    set_error("batch arrays missing");
-    return QS_EINVAL;
-  }
-  if ((loglik || grad) && !b->counts) {
-    set_error("loglik / grad need counts");
-    return QS_EINVAL;
-  }
-  if (b->flags & ~QS_DM_VALIDATE) {
-    set_error("unknown batch flags 0x%x", b->flags);
-    return QS_EINVAL;
-  }
-  if (b->n_circuits == 0) return QS_OK;
-  cudaStream_t stream = (cudaStream_t)stream_;
-  if (b->flags & QS_DM_VALIDATE) {
-    const qs_status vs = dm_validate_batch(b, stream);
-    if (vs != QS_OK) return vs;
-  }
-  DmArgs A{};
-  A.n_circuits = b->n_circuits;
-  A.max_q = b->max_qubits;
-  A.max_ops = b->max_ops;
-  A.K = 1;
-  while (A.K * A.K < b->max_ops) ++A.K;
-  A.nseg = (b->max_ops + A.K - 1) / A.K + 1;
-  A.n_ptm1 = b->n_ptm1;
-  A.n_ptm2 = b->n_ptm2;
-  A.nq = b->nq;
-  A.op_off = b->op_off;
-  A.ops = b->ops;
-  A.params = b->params;
-  A.out_off = b->out_off;
-  A.counts = b->counts;
-  A.ptm1 = b->ptm1;
-  A.ptm2 = b->ptm2;
-  A.probs = probs;
-  A.loglik = loglik;
-  A.grad = grad;
-
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int D = 1 << (2 * A.max_q);
-  const bool with_grad = grad != nullptr;
-  const int warp_need = 4 * (with_grad ? kWarpRegionGrad : kWarpRegionFwd);
-  const int cta_need = (with_grad ? 3 : 1) * D;
-  const size_t smem = (size_t)(kDmHead + (cta_need > warp_need ? cta_need : warp_need)) * sizeof(float);
-  auto kern = with_grad ? dm_batch_kernel<true> : dm_batch_kernel<false>;
-  if (smem > 48 * 1024) {
-    cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (ea != cudaSuccess) return cuda_status(ea, "cudaFuncSetAttribute");
-  }
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDmThreads, smem);
-  if (per_sm < 1) per_sm = 1;
-  int grid = sms * per_sm;
-  if (grid > b->n_circuits) grid = b->n_circuits;
-
-  const size_t Dscr = (size_t)(D > 4 * kWarpD ? D : 4 * kWarpD);
-  const size_t scratch_floats = grad ? (size_t)grid * (A.nseg + A.K + kDmMaxQ) * Dscr : 0;
-  // hand-out order: the gradient sorted (up to kOrderMax circuits), otherwise the
-  // stable partition large | small
-  const bool sort = grad && A.n_circuits > 1 && A.n_circuits <= kOrderMax;
-  const bool part = !sort && A.n_circuits > 1;
-  const size_t order_bytes =
-      (sort || part) ? ((sizeof(int) * (size_t)A.n_circuits + 255) & ~size_t(255)) : 0;
-  const size_t bytes = 256 + order_bytes + scratch_floats * sizeof(float);
-  void* mem = nullptr;
-  cudaError_t e = cudaMallocAsync(&mem, bytes, stream);
-  if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync (dm scratch)");
-  A.work = (int*)mem;
-  A.order = (sort || part) ? (const int*)((char*)mem + 256) : nullptr;
-  A.scratch = grad ? (float*)((char*)mem + 256 + order_bytes) : nullptr;
-  e = cudaMemsetAsync(mem, 0, 256, stream);
-  if (e != cudaSuccess) return cuda_status(e, "cudaMemsetAsync");
-  if (sort) {
-    int P = 1;
-    while (P < A.n_circuits) P <<= 1;
-    const size_t osmem = sizeof(unsigned long long) * (size_t)P;
-    if (osmem > 48 * 1024) {
-      e = cudaFuncSetAttribute(dm_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
-      if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute");
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!b) {
+      set_error("batch is NULL");
+      return QS_EINVAL;
     }
-    dm_order_kernel<<<1, 1024, osmem, stream>>>(A.nq, A.op_off, A.n_circuits, (int*)A.order);
-  } else if (part) {
-    dm_partition_kernel<<<1, 1024, 0, stream>>>(A.nq, A.n_circuits, (int*)A.order);
-  }
-  kern<<<grid, kDmThreads, smem, stream>>>(A);
-  e = cudaGetLastError();
-  cudaFreeAsync(mem, stream);
-  if (e != cudaSuccess) return cuda_status(e, "dm_batch_kernel launch");
-  return QS_OK;
+    if (b->n_circuits < 0 || b->max_qubits < 1 || b->max_qubits > kDmMaxQ || b->max_ops < 0) {
+      set_error("bad batch sizes (n_circuits %d, max_qubits %d, max_ops %d)", b->n_circuits,
+                b->max_qubits, b->max_ops);
+      return QS_EINVAL;
+    }
+    if (!b->nq || !b->op_off || !b->params || !b->out_off || (b->max_ops > 0 && !b->ops)) {
+      set_error("batch arrays missing");
+      return QS_EINVAL;
+    }
+    if ((loglik || grad) && !b->counts) {
+      set_error("loglik / grad need counts");
+      return QS_EINVAL;
+    }
+    if (b->flags & ~QS_DM_VALIDATE) {
+      set_error("unknown batch flags 0x%x", b->flags);
+      return QS_EINVAL;
+    }
+    if (b->n_circuits == 0) return QS_OK;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (b->flags & QS_DM_VALIDATE) {
+      const qs_status vs = dm_validate_batch(b, stream);
+      if (vs != QS_OK) return vs;
+    }
+    DmArgs A{};
+    A.n_circuits = b->n_circuits;
+    A.max_q = b->max_qubits;
+    A.max_ops = b->max_ops;
+    A.K = 1;
+    while (A.K * A.K < b->max_ops) ++A.K;
+    A.nseg = (b->max_ops + A.K - 1) / A.K + 1;
+    A.n_ptm1 = b->n_ptm1;
+    A.n_ptm2 = b->n_ptm2;
+    A.nq = b->nq;
+    A.op_off = b->op_off;
+    A.ops = b->ops;
+    A.params = b->params;
+    A.out_off = b->out_off;
+    A.counts = b->counts;
+    A.ptm1 = b->ptm1;
+    A.ptm2 = b->ptm2;
+    A.probs = probs;
+    A.loglik = loglik;
+    A.grad = grad;
+
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int D = 1 << (2 * A.max_q);
+    const bool with_grad = grad != nullptr;
+    const int warp_need = 4 * (with_grad ? kWarpRegionGrad : kWarpRegionFwd);
+    const int cta_need = (with_grad ? 3 : 1) * D;
+    const size_t smem = (size_t)(kDmHead + (cta_need > warp_need ? cta_need : warp_need)) * sizeof(float);
+    auto kern = with_grad ? dm_batch_kernel<true> : dm_batch_kernel<false>;
+    if (smem > 48 * 1024) {
+      cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (ea != cudaSuccess) return cuda_status(ea, "cudaFuncSetAttribute");
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDmThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    int grid = sms * per_sm;
+    if (grid > b->n_circuits) grid = b->n_circuits;
+
+    const size_t Dscr = (size_t)(D > 4 * kWarpD ? D : 4 * kWarpD);
+    const size_t scratch_floats = grad ? (size_t)grid * (A.nseg + A.K + kDmMaxQ) * Dscr : 0;
+    // hand-out order: the gradient sorted (up to kOrderMax circuits), otherwise the
+    // stable partition large | small
+    const bool sort = grad && A.n_circuits > 1 && A.n_circuits <= kOrderMax;
+    const bool part = !sort && A.n_circuits > 1;
+    const size_t order_bytes =
+        (sort || part) ? ((sizeof(int) * (size_t)A.n_circuits + 255) & ~size_t(255)) : 0;
+    const size_t bytes = 256 + order_bytes + scratch_floats * sizeof(float);
+    void* mem = nullptr;
+    cudaError_t e = cudaMallocAsync(&mem, bytes, stream);
+    if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync (dm scratch)");
+    A.work = (int*)mem;
+    A.order = (sort || part) ? (const int*)((char*)mem + 256) : nullptr;
+    A.scratch = grad ? (float*)((char*)mem + 256 + order_bytes) : nullptr;
+    e = cudaMemsetAsync(mem, 0, 256, stream);
+    if (e != cudaSuccess) return cuda_status(e, "cudaMemsetAsync");
+    if (sort) {
+      int P = 1;
+      while (P < A.n_circuits) P <<= 1;
+      const size_t osmem = sizeof(unsigned long long) * (size_t)P;
+      if (osmem > 48 * 1024) {
+        e = cudaFuncSetAttribute(dm_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
+        if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute");
+      }
+      dm_order_kernel<<<1, 1024, osmem, stream>>>(A.nq, A.op_off, A.n_circuits, (int*)A.order);
+    } else if (part) {
+      dm_partition_kernel<<<1, 1024, 0, stream>>>(A.nq, A.n_circuits, (int*)A.order);
+    }
+    kern<<<grid, kDmThreads, smem, stream>>>(A);
+    e = cudaGetLastError();
+    cudaFreeAsync(mem, stream);
+    if (e != cudaSuccess) return cuda_status(e, "dm_batch_kernel launch");
+    return QS_OK;
+  });
 }

@@ -23,6 +23,7 @@
 
 #include <cstring>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace qs {
@@ -426,18 +427,20 @@ using namespace qs;
 
 extern "C" qs_status sv_grad(qs_state_t h, const qs_gate* gates, size_t ngates, const double* weights,
                              int mode, int checkpoint_every, double* dtheta, double* loss) {
-  State* st = h;
-  if (!st) {
-    set_error("state is NULL");
-    return QS_EINVAL;
-  }
-  if (!weights || (ngates > 0 && !dtheta) || (mode != 0 && mode != 1) || checkpoint_every < 0) {
-    set_error("bad sv_grad arguments");
-    return QS_EINVAL;
-  }
-  qs_status s = validate_gates(gates, ngates, st->n);
-  if (s != QS_OK) return s;
-  if (st->prec == QS_C64)
-    return run_grad<float>(st, gates, ngates, weights, mode, checkpoint_every, dtheta, loss);
-  return run_grad<double>(st, gates, ngates, weights, mode, checkpoint_every, dtheta, loss);
+  return abi_guard(__func__, [&]() -> qs_status {
+    State* st = h;
+    if (!st) {
+      set_error("state is NULL");
+      return QS_EINVAL;
+    }
+    if (!weights || (ngates > 0 && !dtheta) || (mode != 0 && mode != 1) || checkpoint_every < 0) {
+      set_error("bad sv_grad arguments");
+      return QS_EINVAL;
+    }
+    qs_status s = validate_gates(gates, ngates, st->n);
+    if (s != QS_OK) return s;
+    if (st->prec == QS_C64)
+      return run_grad<float>(st, gates, ngates, weights, mode, checkpoint_every, dtheta, loss);
+    return run_grad<double>(st, gates, ngates, weights, mode, checkpoint_every, dtheta, loss);
+  });
 }

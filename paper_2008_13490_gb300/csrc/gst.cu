@@ -14,6 +14,7 @@
 
 #include <vector>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace qs {
@@ -211,30 +212,34 @@ qs_status gst_args(const qs_gst_batch* b, GstArgs* A, cudaStream_t stream) {
 using namespace qs;
 
 extern "C" qs_status dm_gst_series(const qs_gst_batch* b, float* probs, void* stream) {
-  GstArgs A;
-  qs_status s = gst_args(b, &A, (cudaStream_t)stream);
-  if (s != QS_OK) return s;
-  if (A.r_max < 1 || !probs) {
-    set_error("GST series needs r_max >= 1 and an output");
-    return QS_EINVAL;
-  }
-  if (A.count == 0) return QS_OK;
-  const int warps = 8;
-  gst_series_kernel<<<(A.count + warps - 1) / warps, 32 * warps, 0, (cudaStream_t)stream>>>(A, probs);
-  QS_CUDA(cudaGetLastError());
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    GstArgs A;
+    qs_status s = gst_args(b, &A, (cudaStream_t)stream);
+    if (s != QS_OK) return s;
+    if (A.r_max < 1 || !probs) {
+      set_error("GST series needs r_max >= 1 and an output");
+      return QS_EINVAL;
+    }
+    if (A.count == 0) return QS_OK;
+    const int warps = 8;
+    gst_series_kernel<<<(A.count + warps - 1) / warps, 32 * warps, 0, (cudaStream_t)stream>>>(A, probs);
+    QS_CUDA(cudaGetLastError());
+    return QS_OK;
+  });
 }
 
 extern "C" qs_status dm_gst_power(const qs_gst_batch* b, const int64_t* reps, double* probs, void* stream) {
-  GstArgs A;
-  qs_status s = gst_args(b, &A, (cudaStream_t)stream);
-  if (s != QS_OK) return s;
-  if (!reps || !probs) {
-    set_error("GST power needs reps and an output");
-    return QS_EINVAL;
-  }
-  if (A.count == 0) return QS_OK;
-  gst_power_kernel<<<A.count, 256, 0, (cudaStream_t)stream>>>(A, reps, probs);
-  QS_CUDA(cudaGetLastError());
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    GstArgs A;
+    qs_status s = gst_args(b, &A, (cudaStream_t)stream);
+    if (s != QS_OK) return s;
+    if (!reps || !probs) {
+      set_error("GST power needs reps and an output");
+      return QS_EINVAL;
+    }
+    if (A.count == 0) return QS_OK;
+    gst_power_kernel<<<A.count, 256, 0, (cudaStream_t)stream>>>(A, reps, probs);
+    QS_CUDA(cudaGetLastError());
+    return QS_OK;
+  });
 }

@@ -5,6 +5,8 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdlib>
+#include <exception>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -29,7 +31,8 @@ inline size_t host_threads() {
 // the next item from a shared counter.  The items must be independent (each f(i)
 // writes only its own outputs), so the results do not depend on the thread
 // count.  If a thread cannot be started, the threads already running (the caller
-// among them) do the rest.
+// among them) do the rest.  An exception from f stops the hand-out and, once every
+// thread has finished, is rethrown on the calling thread (the first one caught).
 template <class F>
 void parallel_for(size_t n, size_t min_items, F&& f) {
   const size_t nt = std::min<size_t>(host_threads(), n / std::max<size_t>(min_items, 1));
@@ -38,20 +41,27 @@ void parallel_for(size_t n, size_t min_items, F&& f) {
     return;
   }
   std::atomic<size_t> next{0};
+  std::mutex mu;
+  std::exception_ptr failure;
   auto work = [&]() {
-    for (size_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i);
+    try {
+      for (size_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i);
+    } catch (...) {
+      next.store(n);
+      std::lock_guard<std::mutex> g(mu);
+      if (!failure) failure = std::current_exception();
+    }
   };
   std::vector<std::thread> th;
-  th.reserve(nt - 1);
-  for (size_t t = 1; t < nt; ++t) {
-    try {
-      th.emplace_back(work);
-    } catch (...) {
-      break;
-    }
+  try {
+    th.reserve(nt - 1);
+    for (size_t t = 1; t < nt; ++t) th.emplace_back(work);
+  } catch (...) {
+    // fewer threads: the ones started (and the caller) take the rest
   }
   work();
   for (std::thread& t : th) t.join();
+  if (failure) std::rethrow_exception(failure);
 }
 
 }  // namespace qs

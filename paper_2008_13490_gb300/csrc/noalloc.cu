@@ -19,6 +19,7 @@
 // without ordering) race on it.
 #include <cuda_runtime.h>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace qs {
@@ -150,40 +151,42 @@ using namespace qs;
 
 extern "C" qs_status qs_probs_noalloc(const void* amps, int n, int prec, void* out, int out_fp64,
                                       uint64_t marg_mask, double* norm_out, void* stream) {
-  if (!amps) {
-    set_error("amps is NULL");
-    return QS_EINVAL;
-  }
-  if (n < 1 || n > kNaMaxQubits) {
-    set_error("n = %d outside [1, %d]", n, kNaMaxQubits);
-    return QS_EINVAL;
-  }
-  if (prec != QS_C64 && prec != QS_C128) {
-    set_error("bad precision %d", prec);
-    return QS_EINVAL;
-  }
-  if (marg_mask >> n) {
-    set_error("marginal mask has bits beyond n = %d", n);
-    return QS_EINVAL;
-  }
-  int k = __builtin_popcountll(marg_mask);
-  if (k == n) k = 0;   // all bits: plain probabilities
-  if (k > kNaMaxMargBits) {
-    set_error("qs_probs_noalloc: marginal over %d qubits exceeds its fixed scratch limit of %d qubits",
-              k, kNaMaxMargBits);
-    return QS_EINVAL;
-  }
-  double* scratch = nullptr;
-  qs_status s = na_scratch(&scratch);
-  if (s != QS_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
-  const uint64_t mask = k ? marg_mask : 0;
-  s = prec == QS_C64 ? na_run<float>(amps, n, out, out_fp64, mask, k, scratch, st)
-                     : na_run<double>(amps, n, out, out_fp64, mask, k, scratch, st);
-  if (s != QS_OK) return s;
-  if (norm_out) {
-    QS_CUDA(cudaMemcpyAsync(norm_out, scratch + kNaResult, sizeof(double), cudaMemcpyDeviceToHost, st));
-    QS_CUDA(cudaStreamSynchronize(st));
-  }
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!amps) {
+      set_error("amps is NULL");
+      return QS_EINVAL;
+    }
+    if (n < 1 || n > kNaMaxQubits) {
+      set_error("n = %d outside [1, %d]", n, kNaMaxQubits);
+      return QS_EINVAL;
+    }
+    if (prec != QS_C64 && prec != QS_C128) {
+      set_error("bad precision %d", prec);
+      return QS_EINVAL;
+    }
+    if (marg_mask >> n) {
+      set_error("marginal mask has bits beyond n = %d", n);
+      return QS_EINVAL;
+    }
+    int k = __builtin_popcountll(marg_mask);
+    if (k == n) k = 0;   // all bits: plain probabilities
+    if (k > kNaMaxMargBits) {
+      set_error("qs_probs_noalloc: marginal over %d qubits exceeds its fixed scratch limit of %d qubits",
+                k, kNaMaxMargBits);
+      return QS_EINVAL;
+    }
+    double* scratch = nullptr;
+    qs_status s = na_scratch(&scratch);
+    if (s != QS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t mask = k ? marg_mask : 0;
+    s = prec == QS_C64 ? na_run<float>(amps, n, out, out_fp64, mask, k, scratch, st)
+                       : na_run<double>(amps, n, out, out_fp64, mask, k, scratch, st);
+    if (s != QS_OK) return s;
+    if (norm_out) {
+      QS_CUDA(cudaMemcpyAsync(norm_out, scratch + kNaResult, sizeof(double), cudaMemcpyDeviceToHost, st));
+      QS_CUDA(cudaStreamSynchronize(st));
+    }
+    return QS_OK;
+  });
 }

@@ -10,6 +10,7 @@
 // plain DFMA.  flops = 2 per FMA.
 #include <cuda_runtime.h>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace qs {
@@ -53,42 +54,44 @@ __global__ void __launch_bounds__(kPeakThreads) peak_fp64_kernel(double* out, do
 using namespace qs;
 
 extern "C" qs_status qs_alu_peak(int kind, double* flops_per_s, int* sm_count, double* ms_out, void* stream_) {
-  if (!flops_per_s || (kind != 0 && kind != 1)) {
-    set_error("qs_alu_peak: kind 0 (FP32) or 1 (FP64) and an output are required");
-    return QS_EINVAL;
-  }
-  int dev = 0, sms = 0;
-  QS_CUDA(cudaGetDevice(&dev));
-  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  cudaStream_t stream = (cudaStream_t)stream_;
-  const int blocks = sms * (2048 / kPeakThreads);
-  // about 30 ms per launch at the nominal rates (FP32 ~80 TFLOP/s, FP64 ~1.3 TFLOP/s)
-  const int iters = kind == 0 ? (1 << 18) : (1 << 13);
-  cudaEvent_t e0, e1;
-  QS_CUDA(cudaEventCreate(&e0));
-  QS_CUDA(cudaEventCreate(&e1));
-  float best = 1e30f;
-  for (int rep = 0; rep < 4; ++rep) {   // the first launch warms up; the best of the rest counts
-    cudaEventRecord(e0, stream);
-    if (kind == 0) peak_fp32_kernel<<<blocks, kPeakThreads, 0, stream>>>(nullptr, 0.999f, 1e-3f, iters);
-    else peak_fp64_kernel<<<blocks, kPeakThreads, 0, stream>>>(nullptr, 0.999, 1e-3, iters);
-    cudaEventRecord(e1, stream);
-    cudaError_t e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return cuda_status(e, "qs_alu_peak");
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!flops_per_s || (kind != 0 && kind != 1)) {
+      set_error("qs_alu_peak: kind 0 (FP32) or 1 (FP64) and an output are required");
+      return QS_EINVAL;
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (rep > 0 && ms < best) best = ms;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  const double fmas = (double)blocks * kPeakThreads * iters * kChains * (kind == 0 ? 2.0 : 1.0);
-  *flops_per_s = 2.0 * fmas / (best * 1e-3);
-  if (sm_count) *sm_count = sms;
-  if (ms_out) *ms_out = best;
-  return QS_OK;
+    int dev = 0, sms = 0;
+    QS_CUDA(cudaGetDevice(&dev));
+    QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int blocks = sms * (2048 / kPeakThreads);
+    // about 30 ms per launch at the nominal rates (FP32 ~80 TFLOP/s, FP64 ~1.3 TFLOP/s)
+    const int iters = kind == 0 ? (1 << 18) : (1 << 13);
+    cudaEvent_t e0, e1;
+    QS_CUDA(cudaEventCreate(&e0));
+    QS_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {   // the first launch warms up; the best of the rest counts
+      cudaEventRecord(e0, stream);
+      if (kind == 0) peak_fp32_kernel<<<blocks, kPeakThreads, 0, stream>>>(nullptr, 0.999f, 1e-3f, iters);
+      else peak_fp64_kernel<<<blocks, kPeakThreads, 0, stream>>>(nullptr, 0.999, 1e-3, iters);
+      cudaEventRecord(e1, stream);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_status(e, "qs_alu_peak");
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double fmas = (double)blocks * kPeakThreads * iters * kChains * (kind == 0 ? 2.0 : 1.0);
+    *flops_per_s = 2.0 * fmas / (best * 1e-3);
+    if (sm_count) *sm_count = sms;
+    if (ms_out) *ms_out = best;
+    return QS_OK;
+  });
 }

@@ -20,6 +20,7 @@
 #include <cstring>
 #include <vector>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace qs {
@@ -164,10 +165,12 @@ qs_status ptm_validate(const double* ptms, int n, int count, const char* what, i
 using namespace qs;
 
 extern "C" qs_status qs_ptm_check(const double* ptms, int n, int count, int* bad_index) {
-  if (bad_index) *bad_index = -1;
-  if (!ptms || n < 1 || n > 2 || count < 0) {
-    set_error("qs_ptm_check: ptms required, n in {1, 2}, count >= 0");
-    return QS_EINVAL;
-  }
-  return ptm_validate(ptms, n, count, "PTM", bad_index);
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (bad_index) *bad_index = -1;
+    if (!ptms || n < 1 || n > 2 || count < 0) {
+      set_error("qs_ptm_check: ptms required, n in {1, 2}, count >= 0");
+      return QS_EINVAL;
+    }
+    return ptm_validate(ptms, n, count, "PTM", bad_index);
+  });
 }

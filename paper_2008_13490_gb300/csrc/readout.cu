@@ -29,6 +29,7 @@
 #include <cstring>
 #include <vector>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace qs {
@@ -585,42 +586,46 @@ qs_status bloch_launch(State* st, double* dev_out) {
 using namespace qs;
 
 extern "C" qs_status sv_bloch(qs_state_t st_, double* r_out) {
-  State* st = st_;
-  if (!st || !r_out) {
-    set_error("state and r_out are required");
-    return QS_EINVAL;
-  }
-  const int n = st->n;
-  // the result (3n doubles) at the end of the marginal scratch
-  double* dev_out = (double*)((unsigned char*)st->scratch + kScratchMarg) + ((size_t)1 << kScratchMargLog2) - 256;
-  qs_status s = st->prec == QS_C64 ? bloch_launch<float>(st, dev_out) : bloch_launch<double>(st, dev_out);
-  if (s != QS_OK) return s;
-  QS_CUDA(cudaMemcpyAsync(r_out, dev_out, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, st->stream));
-  QS_CUDA(cudaStreamSynchronize(st->stream));
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    State* st = st_;
+    if (!st || !r_out) {
+      set_error("state and r_out are required");
+      return QS_EINVAL;
+    }
+    const int n = st->n;
+    // the result (3n doubles) at the end of the marginal scratch
+    double* dev_out = (double*)((unsigned char*)st->scratch + kScratchMarg) + ((size_t)1 << kScratchMargLog2) - 256;
+    qs_status s = st->prec == QS_C64 ? bloch_launch<float>(st, dev_out) : bloch_launch<double>(st, dev_out);
+    if (s != QS_OK) return s;
+    QS_CUDA(cudaMemcpyAsync(r_out, dev_out, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    return QS_OK;
+  });
 }
 
 extern "C" qs_status qs_meas_error(void* probs, int n, int fp64, const double* e01, const double* e10,
                                    void* stream) {
-  if (!probs || !e01) {
-    set_error("probs and e01 are required");
-    return QS_EINVAL;
-  }
-  if (n < 1 || n > 40) {
-    set_error("n = %d out of range [1, 40]", n);
-    return QS_EINVAL;
-  }
-  if ((uintptr_t)probs & 15) {
-    set_error("probs must be 16-byte aligned");
-    return QS_EINVAL;
-  }
-  if (!e10) e10 = e01;
-  for (int q = 0; q < n; ++q)
-    if (!(e01[q] >= 0.0 && e01[q] <= 1.0 && e10[q] >= 0.0 && e10[q] <= 1.0)) {
-      set_error("misread rates of qubit %d are not in [0, 1]", q);
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!probs || !e01) {
+      set_error("probs and e01 are required");
       return QS_EINVAL;
     }
-  cudaStream_t s = (cudaStream_t)stream;
-  return fp64 ? meas_error_launch<double>((double*)probs, n, e01, e10, s)
-              : meas_error_launch<float>((float*)probs, n, e01, e10, s);
+    if (n < 1 || n > 40) {
+      set_error("n = %d out of range [1, 40]", n);
+      return QS_EINVAL;
+    }
+    if ((uintptr_t)probs & 15) {
+      set_error("probs must be 16-byte aligned");
+      return QS_EINVAL;
+    }
+    if (!e10) e10 = e01;
+    for (int q = 0; q < n; ++q)
+      if (!(e01[q] >= 0.0 && e01[q] <= 1.0 && e10[q] >= 0.0 && e10[q] <= 1.0)) {
+        set_error("misread rates of qubit %d are not in [0, 1]", q);
+        return QS_EINVAL;
+      }
+    cudaStream_t s = (cudaStream_t)stream;
+    return fp64 ? meas_error_launch<double>((double*)probs, n, e01, e10, s)
+                : meas_error_launch<float>((float*)probs, n, e01, e10, s);
+  });
 }

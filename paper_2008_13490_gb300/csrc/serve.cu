@@ -40,6 +40,7 @@
 #include <thread>
 #include <unordered_map>
 
+#include "abi_guard.h"
 #include "dev_common.cuh"
 #include "internal.h"
 
@@ -341,7 +342,20 @@ struct Server {
     ++packed_circuits;
     return true;
   }
-  bool publish(Req* r) { return cfg.prec == QS_C64 ? publish_t<float>(r) : publish_t<double>(r); }
+  // true once r is taken (published, or failed: a host allocation in the fusion
+  // failed before anything was written, and r's wait returns that error)
+  bool publish(Req* r) {
+    bool taken = false;
+    const qs_status s = abi_guard("publishing a small circuit", [&]() -> qs_status {
+      taken = cfg.prec == QS_C64 ? publish_t<float>(r) : publish_t<double>(r);
+      return QS_OK;
+    });
+    if (s != QS_OK) {
+      finish(r, s);
+      return true;
+    }
+    return taken;
+  }
 
   // finished jobs (done word set), in any order; arena space is reclaimed over
   // the finished prefix of the queue
@@ -469,20 +483,23 @@ struct Server {
       qs_allocator a{async_alloc, async_free, nullptr};
       qs_state_t st = nullptr;
       qs_status s = (stream && hbuf) ? sv_create(r->n, cfg.prec, &a, stream, &st) : QS_ENOMEM;
-      if (s == QS_OK) s = apply_gates(st, r->gates.data(), r->gates.size(), method, nullptr);
-      if (s == QS_OK) {
-        unsigned char* sc = (unsigned char*)st->scratch;
-        double* marg = (double*)(sc + kScratchMarg);
-        const bool all = r->k == r->n;   // a mask of all n bits is the plain distribution
-        s = launch_probs(st, all ? marg : nullptr, 1, all ? 0 : r->mask, (double*)(sc + kScratchPartials),
-                         (uint8_t*)(sc + kScratchBits), marg);
-        if (s == QS_OK) {
-          cudaError_t e = cudaMemcpyAsync(hbuf, marg, sizeof(double) << r->k, cudaMemcpyDeviceToHost, stream);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-          if (e != cudaSuccess) s = cuda_status(e, "large circuit readout");
-        }
-        if (s == QS_OK) r->result.assign(hbuf, hbuf + ((size_t)1 << r->k));
-      }
+      if (s == QS_OK)   // a host exception (planner allocation) fails this circuit, not the server
+        s = abi_guard("large circuit", [&]() -> qs_status {
+          qs_status s2 = apply_gates(st, r->gates.data(), r->gates.size(), method, nullptr);
+          if (s2 != QS_OK) return s2;
+          unsigned char* sc = (unsigned char*)st->scratch;
+          double* marg = (double*)(sc + kScratchMarg);
+          const bool all = r->k == r->n;   // a mask of all n bits is the plain distribution
+          s2 = launch_probs(st, all ? marg : nullptr, 1, all ? 0 : r->mask, (double*)(sc + kScratchPartials),
+                            (uint8_t*)(sc + kScratchBits), marg);
+          if (s2 == QS_OK) {
+            cudaError_t e = cudaMemcpyAsync(hbuf, marg, sizeof(double) << r->k, cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) s2 = cuda_status(e, "large circuit readout");
+          }
+          if (s2 == QS_OK) r->result.assign(hbuf, hbuf + ((size_t)1 << r->k));
+          return s2;
+        });
       if (st) sv_destroy(st);
       {
         std::lock_guard<std::mutex> g(mu);
@@ -569,219 +586,231 @@ struct qs_server_s : public qs::Server {};
 extern "C" {
 
 qs_status qs_server_create(const qs_server_config* cfg, qs_server_t* out) {
-  if (!cfg || !out) {
-    set_error("cfg and out are required");
-    return QS_EINVAL;
-  }
-  *out = nullptr;
-  if (cfg->prec != QS_C64 && cfg->prec != QS_C128) {
-    set_error("bad precision");
-    return QS_EINVAL;
-  }
-  const int small_cap = cfg->prec == QS_C64 ? 14 : 13;
-  if (cfg->small_max_qubits < 0 || cfg->small_max_qubits > small_cap || cfg->max_inflight < 0 ||
-      cfg->persistent_ctas < 0 || cfg->idle_ms < 0) {
-    set_error("bad server configuration");
-    return QS_EINVAL;
-  }
-  qs_server_s* s = new (std::nothrow) qs_server_s();
-  if (!s) return QS_ENOMEM;
-  s->cfg = *cfg;
-  if (s->cfg.small_max_qubits == 0) s->cfg.small_max_qubits = small_cap;
-  if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 4;
-  if (s->cfg.persistent_ctas == 0) s->cfg.persistent_ctas = 16;
-  if (s->cfg.idle_ms == 0) s->cfg.idle_ms = 5;
-  cudaGetDevice(&s->device);
-  cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
-  if (s->cfg.persistent_ctas > s->sms) s->cfg.persistent_ctas = s->sms;
-  if (s->cfg.mem_budget == 0) {
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
-    s->cfg.mem_budget = (uint64_t)(0.8 * (double)fr);
-  }
-  // the persistent kernel's shared memory: the largest small state, the marginal
-  // histogram and the op chunk
-  const size_t amp = s->cfg.prec == QS_C64 ? sizeof(C2<float>) : sizeof(C2<double>);
-  s->op_size = s->cfg.prec == QS_C64 ? sizeof(PlainOp<float>) : sizeof(PlainOp<double>);
-  s->pk_smem = (amp << s->cfg.small_max_qubits) + (sizeof(double) << kMaxMargBits) + kOpChunk * s->op_size;
-  cudaError_t e = cudaSuccess;
-  auto chk = [&](cudaError_t x) {
-    if (e == cudaSuccess) e = x;
-  };
-  chk(cudaStreamCreateWithFlags(&s->pk_stream, cudaStreamNonBlocking));
-  chk(cudaEventCreateWithFlags(&s->pk_ev, cudaEventDisableTiming));
-  const unsigned hflags = cudaHostAllocMapped | cudaHostAllocPortable;
-  chk(cudaHostAlloc((void**)&s->ctl, sizeof(PCtl), hflags));
-  chk(cudaHostAlloc((void**)&s->jobs, sizeof(PJob) * kRing, hflags));
-  chk(cudaHostAlloc((void**)&s->done_words, sizeof(uint32_t) * kRing, hflags));
-  chk(cudaHostAlloc((void**)&s->op_arena, s->op_size * (size_t)kOpArena, hflags));
-  chk(cudaHostAlloc((void**)&s->res_arena, sizeof(double) * (size_t)kResArena, hflags));
-  chk(cudaMalloc(&s->d_head, sizeof(unsigned long long)));
-  chk(cudaMalloc(&s->d_status, sizeof(int)));
-  if (e == cudaSuccess) {
-    std::memset(s->ctl, 0, sizeof(PCtl));
-    std::memset(s->done_words, 0, sizeof(uint32_t) * kRing);
-    chk(cudaMemset(s->d_head, 0, sizeof(unsigned long long)));
-    chk(cudaMemset(s->d_status, 0, sizeof(int)));
-    if (s->cfg.prec == QS_C64)
-      chk(cudaFuncSetAttribute(packed_persistent_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)s->pk_smem));
-    else
-      chk(cudaFuncSetAttribute(packed_persistent_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)s->pk_smem));
-  }
-  if (e != cudaSuccess) {
-    qs_status st = cuda_status(e, "server setup");
-    qs_server_destroy(s);
-    return st;
-  }
-  s->scheduler = std::thread([s]() { s->run(); });
-  for (int i = 0; i < s->cfg.max_inflight; ++i) s->workers.emplace_back([s]() { s->worker_loop(); });
-  *out = s;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!cfg || !out) {
+      set_error("cfg and out are required");
+      return QS_EINVAL;
+    }
+    *out = nullptr;
+    if (cfg->prec != QS_C64 && cfg->prec != QS_C128) {
+      set_error("bad precision");
+      return QS_EINVAL;
+    }
+    const int small_cap = cfg->prec == QS_C64 ? 14 : 13;
+    if (cfg->small_max_qubits < 0 || cfg->small_max_qubits > small_cap || cfg->max_inflight < 0 ||
+        cfg->persistent_ctas < 0 || cfg->idle_ms < 0) {
+      set_error("bad server configuration");
+      return QS_EINVAL;
+    }
+    qs_server_s* s = new (std::nothrow) qs_server_s();
+    if (!s) return QS_ENOMEM;
+    s->cfg = *cfg;
+    if (s->cfg.small_max_qubits == 0) s->cfg.small_max_qubits = small_cap;
+    if (s->cfg.max_inflight == 0) s->cfg.max_inflight = 4;
+    if (s->cfg.persistent_ctas == 0) s->cfg.persistent_ctas = 16;
+    if (s->cfg.idle_ms == 0) s->cfg.idle_ms = 5;
+    cudaGetDevice(&s->device);
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (s->cfg.persistent_ctas > s->sms) s->cfg.persistent_ctas = s->sms;
+    if (s->cfg.mem_budget == 0) {
+      size_t fr = 0, tot = 0;
+      cudaMemGetInfo(&fr, &tot);
+      s->cfg.mem_budget = (uint64_t)(0.8 * (double)fr);
+    }
+    // the persistent kernel's shared memory: the largest small state, the marginal
+    // histogram and the op chunk
+    const size_t amp = s->cfg.prec == QS_C64 ? sizeof(C2<float>) : sizeof(C2<double>);
+    s->op_size = s->cfg.prec == QS_C64 ? sizeof(PlainOp<float>) : sizeof(PlainOp<double>);
+    s->pk_smem = (amp << s->cfg.small_max_qubits) + (sizeof(double) << kMaxMargBits) + kOpChunk * s->op_size;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) {
+      if (e == cudaSuccess) e = x;
+    };
+    chk(cudaStreamCreateWithFlags(&s->pk_stream, cudaStreamNonBlocking));
+    chk(cudaEventCreateWithFlags(&s->pk_ev, cudaEventDisableTiming));
+    const unsigned hflags = cudaHostAllocMapped | cudaHostAllocPortable;
+    chk(cudaHostAlloc((void**)&s->ctl, sizeof(PCtl), hflags));
+    chk(cudaHostAlloc((void**)&s->jobs, sizeof(PJob) * kRing, hflags));
+    chk(cudaHostAlloc((void**)&s->done_words, sizeof(uint32_t) * kRing, hflags));
+    chk(cudaHostAlloc((void**)&s->op_arena, s->op_size * (size_t)kOpArena, hflags));
+    chk(cudaHostAlloc((void**)&s->res_arena, sizeof(double) * (size_t)kResArena, hflags));
+    chk(cudaMalloc(&s->d_head, sizeof(unsigned long long)));
+    chk(cudaMalloc(&s->d_status, sizeof(int)));
+    if (e == cudaSuccess) {
+      std::memset(s->ctl, 0, sizeof(PCtl));
+      std::memset(s->done_words, 0, sizeof(uint32_t) * kRing);
+      chk(cudaMemset(s->d_head, 0, sizeof(unsigned long long)));
+      chk(cudaMemset(s->d_status, 0, sizeof(int)));
+      if (s->cfg.prec == QS_C64)
+        chk(cudaFuncSetAttribute(packed_persistent_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s->pk_smem));
+      else
+        chk(cudaFuncSetAttribute(packed_persistent_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s->pk_smem));
+    }
+    if (e != cudaSuccess) {
+      qs_status st = cuda_status(e, "server setup");
+      qs_server_destroy(s);
+      return st;
+    }
+    s->scheduler = std::thread([s]() { s->run(); });
+    for (int i = 0; i < s->cfg.max_inflight; ++i) s->workers.emplace_back([s]() { s->worker_loop(); });
+    *out = s;
+    return QS_OK;
+  });
 }
 
 qs_status qs_server_submit(qs_server_t s, int n, const qs_gate* gates, size_t ngates,
                            uint64_t marg_mask, int64_t* ticket) {
-  if (!s || !ticket) {
-    set_error("server and ticket are required");
-    return QS_EINVAL;
-  }
-  if (n < 1 || n > 30) {
-    set_error("n = %d outside [1, 30]", n);
-    return QS_EINVAL;
-  }
-  if (marg_mask >> n) {
-    set_error("mask has bits beyond n");
-    return QS_EINVAL;
-  }
-  uint64_t mask = marg_mask ? marg_mask : (n <= kMaxMargBits ? ((1ull << n) - 1) : 0);
-  const int k = __builtin_popcountll(mask);
-  if (k == 0 || k > kMaxMargBits) {
-    set_error("marginal over %d qubits: must be 1..%d", k, kMaxMargBits);
-    return QS_EINVAL;
-  }
-  qs_status st = validate_gates(gates, ngates, n);
-  if (st != QS_OK) return st;
-  Req* r = new (std::nothrow) Req();
-  if (!r) return QS_ENOMEM;
-  r->n = n;
-  r->mask = mask;
-  r->k = k;
-  r->gates.assign(gates, gates + ngates);
-  r->t_submit = now_s();
-  {
-    std::lock_guard<std::mutex> g(s->mu);
-    r->id = s->next_id++;
-    s->reqs[r->id] = r;
-    s->pending.push_back(r);
-    ++s->submitted;
-    if (s->t_first < 0) s->t_first = r->t_submit;
-  }
-  s->cv_work.notify_one();
-  *ticket = r->id;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!s || !ticket) {
+      set_error("server and ticket are required");
+      return QS_EINVAL;
+    }
+    if (n < 1 || n > 30) {
+      set_error("n = %d outside [1, 30]", n);
+      return QS_EINVAL;
+    }
+    if (marg_mask >> n) {
+      set_error("mask has bits beyond n");
+      return QS_EINVAL;
+    }
+    uint64_t mask = marg_mask ? marg_mask : (n <= kMaxMargBits ? ((1ull << n) - 1) : 0);
+    const int k = __builtin_popcountll(mask);
+    if (k == 0 || k > kMaxMargBits) {
+      set_error("marginal over %d qubits: must be 1..%d", k, kMaxMargBits);
+      return QS_EINVAL;
+    }
+    qs_status st = validate_gates(gates, ngates, n);
+    if (st != QS_OK) return st;
+    Req* r = new (std::nothrow) Req();
+    if (!r) return QS_ENOMEM;
+    r->n = n;
+    r->mask = mask;
+    r->k = k;
+    r->gates.assign(gates, gates + ngates);
+    r->t_submit = now_s();
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      r->id = s->next_id++;
+      s->reqs[r->id] = r;
+      s->pending.push_back(r);
+      ++s->submitted;
+      if (s->t_first < 0) s->t_first = r->t_submit;
+    }
+    s->cv_work.notify_one();
+    *ticket = r->id;
+    return QS_OK;
+  });
 }
 
 qs_status qs_server_wait(qs_server_t s, int64_t ticket, double* result, double* latency_ms) {
-  if (!s) {
-    set_error("server is NULL");
-    return QS_EINVAL;
-  }
-  Req* r = nullptr;
-  {
-    std::unique_lock<std::mutex> lk(s->mu);
-    auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end()) {
-      set_error("unknown ticket %lld", (long long)ticket);
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!s) {
+      set_error("server is NULL");
       return QS_EINVAL;
     }
-    r = it->second;
-    s->cv_done.wait(lk, [r]() { return r->done; });
-    s->reqs.erase(it);
-  }
-  qs_status st = r->status;
-  if (st != QS_OK) set_error("%s", r->err.c_str());
-  if (st == QS_OK && result) std::memcpy(result, r->result.data(), sizeof(double) * r->result.size());
-  if (latency_ms) *latency_ms = 1e3 * (r->t_done - r->t_submit);
-  delete r;
-  return st;
+    Req* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      auto it = s->reqs.find(ticket);
+      if (it == s->reqs.end()) {
+        set_error("unknown ticket %lld", (long long)ticket);
+        return QS_EINVAL;
+      }
+      r = it->second;
+      s->cv_done.wait(lk, [r]() { return r->done; });
+      s->reqs.erase(it);
+    }
+    qs_status st = r->status;
+    if (st != QS_OK) set_error("%s", r->err.c_str());
+    if (st == QS_OK && result) std::memcpy(result, r->result.data(), sizeof(double) * r->result.size());
+    if (latency_ms) *latency_ms = 1e3 * (r->t_done - r->t_submit);
+    delete r;
+    return st;
+  });
 }
 
 qs_status qs_server_stats_get(qs_server_t s, qs_server_stats* out) {
-  if (!s || !out) {
-    set_error("server and out are required");
-    return QS_EINVAL;
-  }
-  std::lock_guard<std::mutex> g(s->mu);
-  std::memset(out, 0, sizeof(*out));
-  out->submitted = s->submitted;
-  out->completed = s->completed;
-  out->packed_launches = s->packed_launches;
-  out->packed_circuits = s->packed_circuits;
-  out->large_circuits = s->large_circuits;
-  out->idle_timeouts = s->idle_timeouts;
-  out->peak_bytes = s->peak_bytes;
-  std::vector<double> l = s->lat_ms;
-  if (!l.empty()) {
-    std::sort(l.begin(), l.end());
-    auto pct = [&](double q) {
-      const double pos = q * (double)(l.size() - 1);
-      const size_t i = (size_t)pos;
-      const double f = pos - (double)i;
-      return i + 1 < l.size() ? l[i] * (1 - f) + l[i + 1] * f : l[i];
-    };
-    out->p50_ms = pct(0.50);
-    out->p99_ms = pct(0.99);
-    double sum = 0;
-    for (double x : l) sum += x;
-    out->mean_ms = sum / (double)l.size();
-    out->max_ms = l.back();
-    out->wall_s = s->t_last - s->t_first;
-    out->circuits_per_s = out->wall_s > 0 ? (double)s->completed / out->wall_s : 0.0;
-  }
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!s || !out) {
+      set_error("server and out are required");
+      return QS_EINVAL;
+    }
+    std::lock_guard<std::mutex> g(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->packed_launches = s->packed_launches;
+    out->packed_circuits = s->packed_circuits;
+    out->large_circuits = s->large_circuits;
+    out->idle_timeouts = s->idle_timeouts;
+    out->peak_bytes = s->peak_bytes;
+    std::vector<double> l = s->lat_ms;
+    if (!l.empty()) {
+      std::sort(l.begin(), l.end());
+      auto pct = [&](double q) {
+        const double pos = q * (double)(l.size() - 1);
+        const size_t i = (size_t)pos;
+        const double f = pos - (double)i;
+        return i + 1 < l.size() ? l[i] * (1 - f) + l[i + 1] * f : l[i];
+      };
+      out->p50_ms = pct(0.50);
+      out->p99_ms = pct(0.99);
+      double sum = 0;
+      for (double x : l) sum += x;
+      out->mean_ms = sum / (double)l.size();
+      out->max_ms = l.back();
+      out->wall_s = s->t_last - s->t_first;
+      out->circuits_per_s = out->wall_s > 0 ? (double)s->completed / out->wall_s : 0.0;
+    }
+    return QS_OK;
+  });
 }
 
 qs_status qs_server_inject_query_error(qs_server_t s, int cuda_error) {
-  if (!s || cuda_error <= 0 || cuda_error == (int)cudaErrorNotReady) {
-    set_error("server and a CUDA error code other than cudaErrorNotReady are required");
-    return QS_EINVAL;
-  }
-  s->injected_error.store(cuda_error);
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!s || cuda_error <= 0 || cuda_error == (int)cudaErrorNotReady) {
+      set_error("server and a CUDA error code other than cudaErrorNotReady are required");
+      return QS_EINVAL;
+    }
+    s->injected_error.store(cuda_error);
+    return QS_OK;
+  });
 }
 
 qs_status qs_server_destroy(qs_server_t s) {
-  if (!s) return QS_OK;
-  {
-    std::lock_guard<std::mutex> g(s->mu);
-    s->stop = true;
-  }
-  s->cv_work.notify_all();
-  if (s->scheduler.joinable()) s->scheduler.join();
-  {
-    std::lock_guard<std::mutex> g(s->mu);
-    s->stop_workers = true;
-  }
-  s->cv_large.notify_all();
-  for (auto& w : s->workers)
-    if (w.joinable()) w.join();
-  if (s->ctl) reinterpret_cast<std::atomic<uint32_t>*>(&s->ctl->stop)->store(1u, std::memory_order_release);
-  if (s->pk_stream) cudaStreamSynchronize(s->pk_stream);   // the kernel ends at its next wait
-  if (s->pk_reserved) g_reserved_sms.fetch_sub(s->pk_reserved);
-  for (auto& kv : s->reqs) delete kv.second;
-  if (s->pk_stream) cudaStreamDestroy(s->pk_stream);
-  if (s->pk_ev) cudaEventDestroy(s->pk_ev);
-  if (s->ctl) cudaFreeHost(s->ctl);
-  if (s->jobs) cudaFreeHost(s->jobs);
-  if (s->done_words) cudaFreeHost(s->done_words);
-  if (s->op_arena) cudaFreeHost(s->op_arena);
-  if (s->res_arena) cudaFreeHost(s->res_arena);
-  if (s->d_head) cudaFree(s->d_head);
-  if (s->d_status) cudaFree(s->d_status);
-  delete s;
-  return QS_OK;
+  return abi_guard(__func__, [&]() -> qs_status {
+    if (!s) return QS_OK;
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->scheduler.joinable()) s->scheduler.join();
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      s->stop_workers = true;
+    }
+    s->cv_large.notify_all();
+    for (auto& w : s->workers)
+      if (w.joinable()) w.join();
+    if (s->ctl) reinterpret_cast<std::atomic<uint32_t>*>(&s->ctl->stop)->store(1u, std::memory_order_release);
+    if (s->pk_stream) cudaStreamSynchronize(s->pk_stream);   // the kernel ends at its next wait
+    if (s->pk_reserved) g_reserved_sms.fetch_sub(s->pk_reserved);
+    for (auto& kv : s->reqs) delete kv.second;
+    if (s->pk_stream) cudaStreamDestroy(s->pk_stream);
+    if (s->pk_ev) cudaEventDestroy(s->pk_ev);
+    if (s->ctl) cudaFreeHost(s->ctl);
+    if (s->jobs) cudaFreeHost(s->jobs);
+    if (s->done_words) cudaFreeHost(s->done_words);
+    if (s->op_arena) cudaFreeHost(s->op_arena);
+    if (s->res_arena) cudaFreeHost(s->res_arena);
+    if (s->d_head) cudaFree(s->d_head);
+    if (s->d_status) cudaFree(s->d_status);
+    delete s;
+    return QS_OK;
+  });
 }
 
 }  // extern "C"
