@@ -1,4 +1,4 @@
-"""Sharded state vector on CPU ranks (gloo, world sizes 2 and 4).
+"""Sharded state vector on CPU ranks (gloo, world sizes 2, 4 and 8).
 
 Each rank holds 2^(n-s) amplitudes; gates on rank bits trigger pairwise
 half-shard exchanges planned by ``plan_sharded``.  The gathered result must equal
@@ -46,7 +46,7 @@ def _worker(rank, world, port, n, s, seed, out_dir):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("n,s,seed", [(7, 1, 3), (8, 2, 4)])
+@pytest.mark.parametrize("n,s,seed", [(7, 1, 3), (8, 2, 4), (10, 3, 5)])
 def test_sharded_matches_oracle(tmp_path, n, s, seed):
     world = 1 << s
     mp.spawn(_worker, args=(world, _free_port(), n, s, seed, str(tmp_path)), nprocs=world, join=True)
