@@ -10,6 +10,7 @@
 #include <utility>
 
 #include "abi_guard.h"
+#include "fuse_merge.h"
 #include "host_par.h"
 #include "internal.h"
 #include "tile_cp.h"
@@ -881,6 +882,7 @@ qs_status apply_gates(State* st, const qs_gate* gates, size_t ngates, int method
     s = c64 ? run_plain<float>(st, fops, stats, tm) : run_plain<double>(st, fops, stats, tm);
   } else if (st->n < kTileBits) {
     build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/false);
+    merge_one_qubit_ops(fops, st->n, nullptr);   // one CTA runs them all: no passes to keep
     s = c64 ? run_small<float>(st, fops, stats, tm) : run_small<double>(st, fops, stats, tm);
   } else {
     build_fused_ops(gates, ngates, st->n, fops, vmap, /*fuse=*/true, /*relabel=*/true);

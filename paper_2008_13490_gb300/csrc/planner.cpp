@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "fuse_merge.h"
 #include "internal.h"
 
 namespace qs {
@@ -284,6 +285,71 @@ void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp
   }
 }
 
+void merge_one_qubit_ops(std::vector<FOp>& ops, int n, std::vector<int>* group) {
+  const size_t m = ops.size();
+  std::vector<int> into(m, -1);   // input op -> the later op it was merged into
+  std::vector<int> open(n, -1);   // per target qubit: the movable one-qubit op, or -1
+  for (size_t i = 0; i < m; ++i) {
+    FOp& Y = ops[i];
+    const bool one = (Y.type == F_G1 || Y.type == F_G1C) && Y.term < 0;
+    const int t = one ? Y.t : -1;
+    // Y fixes the ops on every qubit it touches (but for a merge partner on its own
+    // target) and those whose choice bit it changes
+    const uint64_t nd = nd_mask(Y), touched = nd | d_mask(Y);
+    for (int q = 0; q < n; ++q) {
+      const int x = open[q];
+      if (x < 0 || q == t) continue;
+      const FOp& X = ops[(size_t)x];
+      if (((touched >> q) & 1) || (X.type == F_G1C && ((nd >> X.c) & 1))) open[q] = -1;
+    }
+    if (!one) {
+      if (Y.type == F_G1 || Y.type == F_G1C) open[Y.t] = -1;   // a term op
+      continue;
+    }
+    const int x = open[t];
+    if (x >= 0) {
+      FOp& X = ops[(size_t)x];
+      const int cx = X.type == F_G1C ? X.c : -1, cy = Y.type == F_G1C ? Y.c : -1;
+      if (cx < 0 || cy < 0 || cx == cy) {
+        cd A0[4], A1[4], B0[4], B1[4], C0[4], C1[4];
+        for (int k = 0; k < 4; ++k) {
+          A0[k] = X.m0[k];
+          A1[k] = cx >= 0 ? X.m1[k] : X.m0[k];
+          B0[k] = Y.m0[k];
+          B1[k] = cy >= 0 ? Y.m1[k] : Y.m0[k];
+        }
+        mat2_mul(B0, A0, C0);   // the later op on the left
+        mat2_mul(B1, A1, C1);
+        const int c = cy >= 0 ? cy : cx;
+        for (int k = 0; k < 4; ++k) {
+          Y.m0[k] = C0[k];
+          Y.m1[k] = c >= 0 ? C1[k] : cd(0);
+        }
+        if (c >= 0) {
+          Y.type = F_G1C;
+          Y.c = c;
+        }
+        into[(size_t)x] = (int)i;
+      }
+    }
+    open[t] = (int)i;
+  }
+  // compact; inputs follow their merge chains to the op that survives
+  std::vector<int> pos(m, -1);
+  size_t w = 0;
+  for (size_t i = 0; i < m; ++i)
+    if (into[i] < 0) {
+      pos[i] = (int)w;
+      if (w != i) ops[w] = ops[i];
+      ++w;
+    }
+  if (group) {
+    group->assign(m, -1);
+    for (size_t i = m; i-- > 0;) (*group)[i] = into[i] < 0 ? pos[i] : (*group)[(size_t)into[i]];
+  }
+  ops.resize(w);
+}
+
 // ---------------------------------------------------------------------------
 // tile-pass planning
 // ---------------------------------------------------------------------------
@@ -345,6 +411,9 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
   for (size_t i = 0; i < ops.size(); ++i) remaining.push_back((int)i);
 
   const int kLow = 2;   // physical bits always in a tile (contiguous 32-byte sectors)
+  // plans of adjoint sweeps (ops with derivative terms) keep every op as it is
+  bool merge = true;
+  for (const FOp& o : ops) merge = merge && o.term < 0;
 
   while (!remaining.empty()) {
     // ---- choose the tile's qubits and the ops of this pass (a dense two-qubit
@@ -398,13 +467,27 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
     }
     tp.stage_begin = (int)plan.stages.size();
 
+    // ---- the pass's ops, one-qubit ops on a target merged inside the pass (its
+    // ops commute with every op deferred to a later pass, so they form a program
+    // of their own); grp[j] = the merged op that op sel[j] went into
+    std::vector<FOp> pv;
+    pv.reserve(sel.size());
+    for (int idx : sel) pv.push_back(ops[idx]);
+    std::vector<int> grp(sel.size());
+    if (merge) merge_one_qubit_ops(pv, n, &grp);
+    else
+      for (size_t j = 0; j < sel.size(); ++j) grp[j] = (int)j;
+
     // ---- stages
-    std::vector<int> pending = sel;
+    std::vector<int> pending(pv.size());
+    for (size_t k = 0; k < pv.size(); ++k) pending[k] = (int)k;
     while (!pending.empty()) {
       if ((int)plan.stages.size() - tp.stage_begin >= max_stages_per_pass) {
-        // stage budget of the pass used up: the rest waits for the next pass
-        // (merging by op index keeps program order)
-        rest.insert(rest.end(), pending.begin(), pending.end());
+        // stage budget of the pass used up: the rest waits for the next pass as
+        // the original ops it was made of (merging by op index keeps program order)
+        for (int k : pending)
+          for (size_t j = 0; j < sel.size(); ++j)
+            if (grp[j] == k) rest.push_back(sel[j]);
         std::sort(rest.begin(), rest.end());
         break;
       }
@@ -413,7 +496,7 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
       uint64_t snd = 0, sd = 0;
       std::vector<int> stage_ops, later;
       for (int idx : pending) {
-        const FOp& o = ops[idx];
+        const FOp& o = pv[idx];
         uint64_t ndq = nd_mask(o), dq = d_mask(o);
         bool conflict = (ndq & (snd | sd)) || (dq & snd);
         bool ok = false;
@@ -459,7 +542,7 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
       // complete the register set (prefer targets needed next)
       for (int idx : later) {
         if (nR >= kRegBits) break;
-        const FOp& o = ops[idx];
+        const FOp& o = pv[idx];
         if (o.type == F_D) continue;
         for (int v : {o.type == F_G2 ? o.a : o.t, o.type == F_G2 ? o.b : -1}) {
           if (v < 0 || nR >= kRegBits) continue;
@@ -490,7 +573,7 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
       }
       ts.op_begin = (int)plan.tile_fops.size();
       for (int idx : stage_ops) {
-        const FOp& o = ops[idx];
+        const FOp& o = pv[idx];
         uint8_t kind = TK_DIAG, slot = 0, csrc = CS_NONE, cbit = 0, dsrc = CS_NONE, dbit = 0;
         if (o.type == F_G2) {
           // sources (lane or register) of qubit a (local index msb) and b; the op's

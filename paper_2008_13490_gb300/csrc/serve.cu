@@ -41,6 +41,7 @@
 #include <unordered_map>
 
 #include "abi_guard.h"
+#include "fuse_merge.h"
 #include "dev_common.cuh"
 #include "internal.h"
 
@@ -283,6 +284,7 @@ struct Server {
     if (published - oldest >= kRing) return false;   // ring full
     std::vector<FOp>& fops = fops_scratch;   // the scheduler thread's, reused across circuits
     build_fused_ops(r->gates.data(), r->gates.size(), r->n, fops, vmap_scratch, true, false);
+    merge_one_qubit_ops(fops, r->n, nullptr);   // one CTA runs the whole circuit
     const int64_t nops = (int64_t)fops.size();
     const int64_t H = (int64_t)1 << r->k;
     int64_t oh = op_head, rh = res_head, op_at = 0, res_at = 0;

@@ -50,11 +50,12 @@ def _op(vals):
     return out
 
 
-def _plan(exe, tmp_path, n, ops, fuse, relabel):
+def _plan(exe, tmp_path, n, ops, fuse, relabel, limits=()):
     import paper_2008_13490_gb300 as qs
     gin, out = tmp_path / "g.bin", tmp_path / "plan.txt"
     qs.gates_array(ops).tofile(gin)
-    subprocess.run([str(exe), str(gin), str(n), str(int(fuse)), str(int(relabel)), str(out)], check=True)
+    subprocess.run([str(exe), str(gin), str(n), str(int(fuse)), str(int(relabel)), str(out)]
+                   + [str(x) for x in limits], check=True)
     lines = open(out).read().split("\n")
     plan, i = {}, 0
     for sec in ("steps", "passes", "stages", "tileops", "plainops", "remaps"):
@@ -441,3 +442,88 @@ def test_random_circuits_through_plan_and_images(dump_exe, image_exe, tmp_path, 
         assert np.max(np.abs(_execute(plan, n, psi0.copy()) - ref)) < 1e-12, (fuse, relabel)
         img = _images(image_exe, tmp_path, n, ops, fuse, relabel)
         assert np.max(np.abs(_execute_images(img, n, psi0.copy()) - ref)) < 1e-12, (fuse, relabel)
+
+
+@pytest.mark.parametrize("limits", [(1,), (2,), (3, 12), (48, 6)])
+def test_tight_pass_limits(dump_exe, tmp_path, limits):
+    # small stage and op budgets per pass: ops (and one-qubit ops merged inside a
+    # pass) that do not fit go back to later passes as the original ops, in order
+    for case, (n, kind) in enumerate([(13, "mix"), (14, "phases"), (12, "swaps")]):
+        ops = _sweep_ops(n, kind, 990 + case)
+        psi0 = W.random_state(n, W.rng(995 + case))
+        ref = SV.apply_circuit(psi0.copy(), n, ops)
+        for fuse in (True, False):
+            plan = _plan(dump_exe, tmp_path, n, ops, fuse, fuse, limits)
+            for p in plan["passes"]:
+                assert int(p[0]) <= limits[0]
+            assert np.max(np.abs(_execute(plan, n, psi0.copy()) - ref)) < 1e-12, (limits, n, kind, fuse)
+
+
+# ---------------------------------------------------------------- one-CTA op lists
+# Circuits on fewer than 12 qubits (and the server's packed circuits) run their
+# fused op list whole on one CTA, with one-qubit ops on a target merged across the
+# ops between them: the list, applied with numpy in order, must give the oracle's
+# state, and the merge must not lengthen it.
+@pytest.fixture(scope="module")
+def fused_exe(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    from paper_2008_13490_gb300 import _build
+    lib = _build.build()
+    libdir = os.path.dirname(lib)
+    exe = tmp_path_factory.mktemp("fused") / "fused_ops_dump"
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    subprocess.run(["g++", "-O1", "-std=c++17", os.path.join(ROOT, "tests", "fused_ops_dump.cpp"),
+                    "-I", os.path.join(ROOT, "paper_2008_13490_gb300", "csrc"), "-I", os.path.join(ROOT, "include"),
+                    "-I", cuda_inc, "-o", str(exe), "-L", libdir, "-lqsim", f"-Wl,-rpath,{libdir}"],
+                   check=True, capture_output=True, text=True)
+    return exe
+
+
+def _fused(exe, tmp_path, n, ops, merge):
+    import paper_2008_13490_gb300 as qs
+    gin, out = tmp_path / "g.bin", tmp_path / "fused.txt"
+    qs.gates_array(ops).tofile(gin)
+    subprocess.run([str(exe), str(gin), str(n), str(int(merge)), str(out)], check=True)
+    lines = open(out).read().split("\n")
+    head, cnt = lines[0].split()
+    assert head == "ops"
+    return [lines[1 + k].split() for k in range(int(cnt))]
+
+
+def _run_fused(rows, n, psi):
+    for row in rows:
+        typ, t, c, a, b = (int(x) for x in row[:5])
+        m = _op([float(x) for x in row[5:]])
+        if typ == F_G1:
+            _apply_1q(psi, n, t, m["m0"])
+        elif typ == F_G1C:
+            _apply_1q(psi, n, t, m["m0"], m["m1"], c)
+        elif typ == F_D:
+            _apply_diag(psi, n, a, None if b < 0 else b, m["d"])
+        else:
+            _apply_2q(psi, n, a, b, m["g"])
+    return psi
+
+
+SMALL = [(4, "mix"), (6, "phases"), (8, "swaps"), (10, "mix"), (11, "phases"), (10, "cnot"), (9, "layered")]
+
+
+@pytest.mark.parametrize("case", range(len(SMALL)))
+def test_merged_one_cta_op_lists(fused_exe, tmp_path, case):
+    n, kind = SMALL[case]
+    if kind == "cnot":
+        ops = W.layered_haar_cnot(n, 20, seed=1001)
+    elif kind == "layered":
+        ops = W.layered_haar_cz(n, 12, seed=1002)
+    else:
+        ops = _sweep_ops(n, kind, 970 + case)
+    psi0 = W.random_state(n, W.rng(975 + case))
+    ref = SV.apply_circuit(psi0.copy(), n, ops)
+    plain = _fused(fused_exe, tmp_path, n, ops, False)
+    merged = _fused(fused_exe, tmp_path, n, ops, True)
+    assert len(merged) <= len(plain)
+    if kind in ("cnot", "layered"):
+        assert len(merged) < 0.7 * len(plain)   # one-qubit layers ride on the two-qubit ops
+    for rows in (plain, merged):
+        assert np.max(np.abs(_run_fused(rows, n, psi0.copy()) - ref)) < 1e-12

@@ -1,5 +1,6 @@
 // Writes, as text, the tile-pass plan the library makes of a gate list (host
-// side only): usage: tile_plan_dump gates.bin n fuse relabel out.txt.
+// side only): usage: tile_plan_dump gates.bin n fuse relabel out.txt [max_stages [max_ops]]
+// (the pass limits; the library's own by default).
 // Sections (one record per line, numbers separated by blanks):
 //   steps K      / kind index                       (0 tile, 1 plain, 2 remap, 3 small)
 //   passes P     / n_stages stage_begin n_nt pos[12] nt_pos[n_nt]
@@ -21,7 +22,7 @@ static void put_c(FILE* o, const cd* v, int k) {
 }
 
 int main(int argc, char** argv) {
-  if (argc != 6) return 2;
+  if (argc < 6 || argc > 8) return 2;
   FILE* f = std::fopen(argv[1], "rb");
   if (!f) return 2;
   std::vector<qs_gate> g;
@@ -33,7 +34,9 @@ int main(int argc, char** argv) {
   std::vector<int> vmap;
   build_fused_ops(g.data(), g.size(), n, fops, vmap, std::atoi(argv[3]) != 0, std::atoi(argv[4]) != 0);
   Plan pl;
-  plan_circuit(fops, n, vmap, pl, TileLimits<float>::kMaxOps, kMaxTileStages);
+  const int max_stages = argc > 6 ? std::atoi(argv[6]) : kMaxTileStages;
+  const int max_ops = argc > 7 ? std::atoi(argv[7]) : TileLimits<float>::kMaxOps;
+  plan_circuit(fops, n, vmap, pl, max_ops, max_stages);
   FILE* o = std::fopen(argv[5], "w");
   if (!o) return 2;
   std::fprintf(o, "steps %zu\n", pl.steps.size());
