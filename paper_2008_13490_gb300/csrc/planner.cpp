@@ -15,6 +15,7 @@
 // A tile pass then applies every op whose non-diagonal qubit lies in a set of
 // 12 qubits (the tile) in one read+write of the state.
 #include <algorithm>
+#include <utility>
 #include <cstring>
 
 #include "fuse_merge.h"
@@ -417,31 +418,56 @@ void plan_circuit(const std::vector<FOp>& ops, int n, const std::vector<int>& vm
 
   while (!remaining.empty()) {
     // ---- choose the tile's qubits and the ops of this pass (a dense two-qubit
-    // op takes two op slots: its 16 entries span two tile ops)
-    uint64_t T = 0;
-    for (int p = 0; p < kLow; ++p) T |= 1ull << p2l[p];
-    uint64_t nd_blk = 0, d_blk = 0;
+    // op takes two op slots: its 16 entries span two tile ops).  The ops of a pass
+    // are, in order, those whose non-diagonal qubits lie in the tile set and that
+    // no skipped earlier op conflicts with.  Candidate tile sets: the set grown
+    // from the ops in the order they become ready, and every window of
+    // consecutive qubits (with the qubits at the low physical positions, which
+    // every tile holds); a window keeps the deep light cone of a nearest-neighbour
+    // circuit (the 30-qubit layered circuit: 20 passes instead of 47).  The
+    // candidate that takes the most ops wins (ties: the grown set).
+    uint64_t low = 0;
+    for (int p = 0; p < kLow; ++p) low |= 1ull << p2l[p];
+    // fixed == 0: grow the set from `low`; otherwise the set is `fixed`
+    auto select = [&](uint64_t fixed, std::vector<int>* sel_out, std::vector<int>* rest_out) {
+      uint64_t T = fixed ? fixed : low;
+      uint64_t nd_blk = 0, d_blk = 0;
+      int slots_used = 0;
+      for (int idx : remaining) {
+        const FOp& o = ops[idx];
+        uint64_t ndq = nd_mask(o), dq = d_mask(o);
+        bool conflict = (ndq & (nd_blk | d_blk)) || (dq & nd_blk);
+        const int cost = o.type == F_G2 ? 2 : 1;
+        if (!conflict && slots_used + cost <= max_ops_per_pass) {
+          uint64_t need = ndq & ~T;
+          if (fixed ? need == 0 : popc(T | need) <= kTileBits) {
+            T |= need;
+            if (sel_out) sel_out->push_back(idx);
+            slots_used += cost;
+            continue;
+          }
+        }
+        nd_blk |= ndq;
+        d_blk |= dq;
+        if (rest_out) rest_out->push_back(idx);
+      }
+      return std::make_pair(slots_used, T);
+    };
+    uint64_t best_set = 0;
+    int best = select(0, nullptr, nullptr).first;
+    for (int a = 0; a < n; ++a) {
+      uint64_t W = low;
+      for (int q = a; q < n && popc(W) < kTileBits; ++q) W |= 1ull << q;
+      for (int q = a - 1; q >= 0 && popc(W) < kTileBits; --q) W |= 1ull << q;
+      const int c = select(W, nullptr, nullptr).first;
+      if (c > best) {
+        best = c;
+        best_set = W;
+      }
+    }
     std::vector<int> sel;
     std::vector<int> rest;
-    int slots_used = 0;
-    for (int idx : remaining) {
-      const FOp& o = ops[idx];
-      uint64_t ndq = nd_mask(o), dq = d_mask(o);
-      bool conflict = (ndq & (nd_blk | d_blk)) || (dq & nd_blk);
-      const int cost = o.type == F_G2 ? 2 : 1;
-      if (!conflict && slots_used + cost <= max_ops_per_pass) {
-        uint64_t need = ndq & ~T;
-        if (popc(T | need) <= kTileBits) {
-          T |= need;
-          sel.push_back(idx);
-          slots_used += cost;
-          continue;
-        }
-      }
-      nd_blk |= ndq;
-      d_blk |= dq;
-      rest.push_back(idx);
-    }
+    uint64_t T = select(best_set, &sel, &rest).second;
     // fill the tile up to kTileBits with the lowest remaining physical positions
     for (int p = 0; p < n && popc(T) < kTileBits; ++p) T |= 1ull << p2l[p];
 
