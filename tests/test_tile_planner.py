@@ -527,3 +527,45 @@ def test_merged_one_cta_op_lists(fused_exe, tmp_path, case):
         assert len(merged) < 0.7 * len(plain)   # one-qubit layers ride on the two-qubit ops
     for rows in (plain, merged):
         assert np.max(np.abs(_run_fused(rows, n, psi0.copy()) - ref)) < 1e-12
+
+
+# ---------------------------------------------------------------- plan structure
+# What the tile kernel relies on in every pass, whichever tile set the planner
+# chose: 12 distinct tile positions that include physical bits 0 and 1; per stage,
+# 4 register bits and 3 warp bits that split local bits 5..11; lane and register
+# slots in range; choice and diagonal bits with a source the kernel can read; the
+# pass within the op and stage budgets; stages covering the pass's ops in order.
+@pytest.mark.parametrize("case", range(len(SWEEP)))
+def test_plan_structure(dump_exe, tmp_path, case):
+    n, kind = SWEEP[case]
+    ops = _sweep_ops(n, kind, 900 + case)
+    for fuse, relabel in ((True, True), (False, False)):
+        plan = _plan(dump_exe, tmp_path, n, ops, fuse, relabel)
+        stages = [[int(x) for x in r] for r in plan["stages"]]
+        kinds = [[int(x) for x in r[:7]] for r in plan["tileops"]]
+        next_op = 0
+        for p in plan["passes"]:
+            n_st, st0, n_nt = (int(x) for x in p[:3])
+            pos = [int(x) for x in p[3:15]]
+            nt = [int(x) for x in p[15:15 + n_nt]]
+            assert len(set(pos)) == 12 and {0, 1} <= set(pos) and sorted(pos) == pos
+            assert sorted(pos + nt) == list(range(n))
+            assert 1 <= n_st <= 48
+            n_ops = 0
+            for s in stages[st0:st0 + n_st]:
+                reg, warp, b, e = s[0:4], s[4:7], s[7], s[8]
+                assert sorted(reg + warp) == list(range(5, 12))
+                assert b == next_op and e >= b
+                next_op = e
+                n_ops += e - b
+                for kd, slot, csrc, cbit, dsrc, dbit, typ in kinds[b:e]:
+                    if kd == TK_REG:
+                        assert 0 <= slot < 4
+                    elif kd == TK_LANE:
+                        assert 0 <= slot < 5
+                    for src, bit in ((csrc, cbit), (dsrc, dbit)):
+                        assert src in (CS_NONE, CS_TILE, CS_LANE, CS_WARP, CS_REG)
+                        limit = {CS_NONE: 1, CS_TILE: n_nt, CS_LANE: 5, CS_WARP: 3, CS_REG: 4}[src]
+                        assert 0 <= bit < max(limit, 1)
+            assert n_ops <= 352
+        assert next_op == len(kinds)
