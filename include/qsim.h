@@ -115,8 +115,10 @@ typedef enum {
    * 1024 entries nonzero is a dense contraction and runs as a BF16-split GEMM on
    * the tensor cores, and each maximal run of sparser blocks (diagonal or nearly
    * diagonal stretches, permutations) is replayed gate by gate through the tile
-   * passes; other states use QS_METHOD_TILED.  Synchronous like the block
-   * methods. */
+   * passes.  With only one or two dense blocks, the whole circuit runs on tile
+   * passes when that takes no more tile passes and remaps than the sparse runs
+   * alone (the blocks' sweeps are saved).  Other states use QS_METHOD_TILED.
+   * Synchronous like the block methods. */
   QS_METHOD_AUTO = 4
 } qs_method;
 

@@ -10,6 +10,7 @@
 #include <utility>
 
 #include "abi_guard.h"
+#include "auto_plan.h"
 #include "fuse_merge.h"
 #include "host_par.h"
 #include "internal.h"
@@ -788,6 +789,28 @@ qs_status run_blocks(State* st, const qs_gate* gates, size_t ngates, int mode, q
 qs_status run_auto(State* st, const qs_gate* gates, size_t ngates, qs_stats* stats, KernelTimer& tm) {
   std::vector<Block> blocks;
   plan_blocks(gates, ngates, st->n, blocks);
+  // one or two dense blocks among sparse ones (the QFT's Hadamards among its
+  // phases) may run on tile passes alone (auto_plan.h)
+  {
+    std::vector<FOp> fops;
+    std::vector<int> vmap;
+    if (auto_all_tiles(gates, ngates, st->n, blocks, &fops, &vmap)) {
+      qs_stats part;
+      std::memset(&part, 0, sizeof(part));
+      qs_status s = run_tiled<float>(st, fops, vmap, &part, tm);
+      if (stats) {
+        stats->ops_fused = part.ops_fused;
+        stats->passes = part.passes;
+        stats->launches = part.launches;
+        stats->tile_launches = part.tile_launches;
+        stats->tile_flops = part.tile_flops;
+        stats->flops = part.flops;
+        stats->upload_bytes = part.upload_bytes;
+      }
+      if (s == QS_OK) QS_CUDA(cudaStreamSynchronize(st->stream));
+      return s;
+    }
+  }
   size_t i = 0;
   qs_status s = QS_OK;
   while (i < blocks.size() && s == QS_OK) {

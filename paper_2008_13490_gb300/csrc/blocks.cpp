@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "auto_plan.h"
 #include "host_par.h"
 #include "internal.h"
 
@@ -226,6 +227,35 @@ void plan_blocks(const qs_gate* gates, size_t ngates, int n, std::vector<Block>&
   }
   // each block's product of its gates (blocks are independent)
   parallel_for(out.size(), 8, [&](size_t bi) { block_product(gates, out[bi]); });
+}
+
+bool auto_all_tiles(const qs_gate* gates, size_t ngates, int n, const std::vector<Block>& blocks,
+                    std::vector<FOp>* fops, std::vector<int>* vmap) {
+  int dense = 0;
+  for (const Block& b : blocks) dense += block_nonzeros(b) > 512 ? 1 : 0;
+  if (dense < 1 || dense > 2 || dense == (int)blocks.size()) return false;
+  // tile passes and remaps of a gate list, fused as the default method fuses it
+  auto count = [&](const std::vector<qs_gate>& seg, int* passes, int* remaps) {
+    build_fused_ops(seg.data(), seg.size(), n, *fops, *vmap, /*fuse=*/true, /*relabel=*/true);
+    Plan pl;
+    plan_circuit(*fops, n, *vmap, pl, TileLimits<float>::kMaxOps, kMaxTileStages);
+    *passes += (int)pl.passes.size();
+    *remaps += (int)pl.remaps.size();
+  };
+  int seg_passes = 0, seg_remaps = 0;
+  for (size_t i = 0; i < blocks.size();) {   // the runs of sparse blocks
+    std::vector<qs_gate> seg;
+    size_t j = i;
+    while (j < blocks.size() && block_nonzeros(blocks[j]) <= 512) {
+      for (size_t gi : blocks[j].gate_idx) seg.push_back(gates[gi]);
+      ++j;
+    }
+    if (!seg.empty()) count(seg, &seg_passes, &seg_remaps);
+    i = j == i ? i + 1 : j;
+  }
+  int all_passes = 0, all_remaps = 0;   // the whole circuit (its ops stay in *fops)
+  count(std::vector<qs_gate>(gates, gates + ngates), &all_passes, &all_remaps);
+  return all_passes <= seg_passes && all_remaps <= seg_remaps;
 }
 
 int block_nonzeros(const Block& b) {

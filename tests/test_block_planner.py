@@ -123,3 +123,43 @@ def test_random_circuits_blocks_reproduce_the_circuit(dump_exe, tmp_path, case):
         assert unitary == 1
         psi = _apply_block(psi, n, q, U)
     assert np.max(np.abs(psi - ref)) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def auto_exe(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    from paper_2008_13490_gb300 import _build
+    lib = _build.build()
+    libdir = os.path.dirname(lib)
+    exe = tmp_path_factory.mktemp("autoplan") / "auto_plan_check"
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    subprocess.run(["g++", "-O1", "-std=c++17", os.path.join(ROOT, "tests", "auto_plan_check.cpp"),
+                    "-I", os.path.join(ROOT, "paper_2008_13490_gb300", "csrc"), "-I", os.path.join(ROOT, "include"),
+                    "-I", cuda_inc, "-o", str(exe), "-L", libdir, "-lqsim", f"-Wl,-rpath,{libdir}"],
+                   check=True, capture_output=True, text=True)
+    return exe
+
+
+@pytest.mark.parametrize("name,n,expect", [
+    ("qft", 30, 1),        # one dense block; the whole QFT takes the same 3 tile passes and 3 remaps
+    ("qft", 13, 0),        # its whole-circuit plan would add a tile pass
+    ("qft", 17, 0),
+    ("layered", 30, 0),    # 93 dense blocks
+    ("mixed", 16, 0),      # dense layers around a QFT: 14 dense blocks
+    ("phases", 14, 0),     # no dense block at all
+])
+def test_default_method_runs_lone_dense_blocks_on_tiles_when_free(auto_exe, tmp_path, name, n, expect):
+    import paper_2008_13490_gb300 as qs
+    ops = {
+        "qft": lambda: W.qft_circuit(n),
+        "layered": lambda: W.layered_haar_cz(n, 40, seed=2001),
+        "mixed": lambda: W.layered_haar_cz(n, 6, seed=1) + W.qft_circuit(n) + W.layered_haar_cz(n, 6, seed=2),
+        "phases": lambda: W.random_gate_mix(n, 300, seed=3, two_q_fraction=0.9, names1=["RZ", "T"],
+                                            names2=["CP", "CZ"]),
+    }[name]()
+    gin = tmp_path / "g.bin"
+    qs.gates_array(ops).tofile(gin)
+    r = subprocess.run([str(auto_exe), str(gin), str(n)], check=True, capture_output=True, text=True)
+    tiles, dense = (int(x) for x in r.stdout.split())
+    assert tiles == expect, (name, n, dense)
