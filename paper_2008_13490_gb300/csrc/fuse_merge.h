@@ -17,5 +17,8 @@ namespace qs {
 // never merged.  On return ops holds the surviving ops in order; if group is not
 // NULL, (*group)[i] is the index in the result of the op that input op i went into.
 void merge_one_qubit_ops(std::vector<FOp>& ops, int n, std::vector<int>* group);
+// The same merge without moving the ops: on return (*into)[i] is the index of the
+// later op that op i was merged into, or -1 for the ops that remain (in order).
+void mark_one_qubit_merges(std::vector<FOp>& ops, int n, std::vector<int>* into);
 
 }  // namespace qs

@@ -286,10 +286,13 @@ void build_fused_ops(const qs_gate* gates, size_t ngates, int n, std::vector<FOp
   }
 }
 
-void merge_one_qubit_ops(std::vector<FOp>& ops, int n, std::vector<int>* group) {
+void mark_one_qubit_merges(std::vector<FOp>& ops, int n, std::vector<int>* into_out) {
   const size_t m = ops.size();
-  std::vector<int> into(m, -1);   // input op -> the later op it was merged into
+  std::vector<int>& into = *into_out;   // input op -> the later op it was merged into
+  into.assign(m, -1);
   std::vector<int> open(n, -1);   // per target qubit: the movable one-qubit op, or -1
+  std::vector<int> open_c(n, -1); // its choice bit (-1: none)
+  uint64_t open_mask = 0;         // targets with a movable op
   for (size_t i = 0; i < m; ++i) {
     FOp& Y = ops[i];
     const bool one = (Y.type == F_G1 || Y.type == F_G1C) && Y.term < 0;
@@ -297,31 +300,23 @@ void merge_one_qubit_ops(std::vector<FOp>& ops, int n, std::vector<int>* group) 
     // Y fixes the ops on every qubit it touches (but for a merge partner on its own
     // target) and those whose choice bit it changes
     const uint64_t nd = nd_mask(Y), touched = nd | d_mask(Y);
-    for (int q = 0; q < n; ++q) {
-      const int x = open[q];
-      if (x < 0 || q == t) continue;
-      const FOp& X = ops[(size_t)x];
-      if (((touched >> q) & 1) || (X.type == F_G1C && ((nd >> X.c) & 1))) open[q] = -1;
+    for (uint64_t cand = open_mask & ~(t >= 0 ? 1ull << t : 0ull); cand; cand &= cand - 1) {
+      const int q = __builtin_ctzll(cand);
+      if (((touched >> q) & 1) || (open_c[q] >= 0 && ((nd >> open_c[q]) & 1))) {
+        open[q] = -1;
+        open_mask &= ~(1ull << q);
+      }
     }
-    if (!one) {
-      if (Y.type == F_G1 || Y.type == F_G1C) open[Y.t] = -1;   // a term op
-      continue;
-    }
+    if (!one) continue;   // (a term op is in its own touched set: its target is closed)
     const int x = open[t];
     if (x >= 0) {
       FOp& X = ops[(size_t)x];
       const int cx = X.type == F_G1C ? X.c : -1, cy = Y.type == F_G1C ? Y.c : -1;
       if (cx < 0 || cy < 0 || cx == cy) {
-        cd A0[4], A1[4], B0[4], B1[4], C0[4], C1[4];
-        for (int k = 0; k < 4; ++k) {
-          A0[k] = X.m0[k];
-          A1[k] = cx >= 0 ? X.m1[k] : X.m0[k];
-          B0[k] = Y.m0[k];
-          B1[k] = cy >= 0 ? Y.m1[k] : Y.m0[k];
-        }
-        mat2_mul(B0, A0, C0);   // the later op on the left
-        mat2_mul(B1, A1, C1);
         const int c = cy >= 0 ? cy : cx;
+        cd C0[4], C1[4];
+        mat2_mul(Y.m0, X.m0, C0);   // the later op on the left
+        if (c >= 0) mat2_mul(cy >= 0 ? Y.m1 : Y.m0, cx >= 0 ? X.m1 : X.m0, C1);
         for (int k = 0; k < 4; ++k) {
           Y.m0[k] = C0[k];
           Y.m1[k] = c >= 0 ? C1[k] : cd(0);
@@ -334,7 +329,15 @@ void merge_one_qubit_ops(std::vector<FOp>& ops, int n, std::vector<int>* group) 
       }
     }
     open[t] = (int)i;
+    open_c[t] = Y.type == F_G1C ? Y.c : -1;
+    open_mask |= 1ull << t;
   }
+}
+
+void merge_one_qubit_ops(std::vector<FOp>& ops, int n, std::vector<int>* group) {
+  const size_t m = ops.size();
+  std::vector<int> into;
+  mark_one_qubit_merges(ops, n, &into);
   // compact; inputs follow their merge chains to the op that survives
   std::vector<int> pos(m, -1);
   size_t w = 0;

@@ -257,6 +257,7 @@ struct Server {
   std::deque<QJob> in_queue;         // published jobs in publish order, until retired from the front
   std::vector<FOp> fops_scratch;     // fused ops of the circuit being published
   std::vector<int> vmap_scratch;
+  std::vector<int> merge_scratch;    // its merge marks
   int64_t op_head = 0, op_tail = 0, res_head = 0, res_tail = 0;
   // statistics
   std::vector<double> lat_ms;
@@ -284,8 +285,12 @@ struct Server {
     if (published - oldest >= kRing) return false;   // ring full
     std::vector<FOp>& fops = fops_scratch;   // the scheduler thread's, reused across circuits
     build_fused_ops(r->gates.data(), r->gates.size(), r->n, fops, vmap_scratch, true, false);
-    merge_one_qubit_ops(fops, r->n, nullptr);   // one CTA runs the whole circuit
-    const int64_t nops = (int64_t)fops.size();
+    // one CTA runs the whole circuit: one-qubit ops merged over the whole list
+    // (marked in place; the merged ones are skipped below)
+    std::vector<int>& into = merge_scratch;
+    mark_one_qubit_merges(fops, r->n, &into);
+    int64_t nops = 0;
+    for (int v : into) nops += v < 0 ? 1 : 0;
     const int64_t H = (int64_t)1 << r->k;
     int64_t oh = op_head, rh = res_head, op_at = 0, res_at = 0;
     if (!arena_take(oh, op_tail, kOpArena, nops, &op_at) || !arena_take(rh, res_tail, kResArena, H, &res_at))
@@ -297,8 +302,9 @@ struct Server {
       return v;
     };
     PlainOp<R>* dst = reinterpret_cast<PlainOp<R>*>(op_arena) + op_at;
-    for (int64_t i = 0; i < nops; ++i) {
-      const FOp& o = fops[(size_t)i];
+    for (size_t i = 0, k = 0; i < fops.size(); ++i) {
+      if (into[i] >= 0) continue;
+      const FOp& o = fops[i];
       PlainOp<R> p;
       std::memset(&p, 0, sizeof(p));
       p.type = o.type;
@@ -315,7 +321,7 @@ struct Server {
       } else {
         for (int q = 0; q < 16; ++q) p.m[q] = c2(o.g[q]);
       }
-      dst[i] = p;
+      dst[k++] = p;
     }
     QJob q;
     q.r = r;
